@@ -1,0 +1,212 @@
+/*
+ * recogs.h -- C ABI of librecogs.so: per-Gaussian region selection,
+ * recolouring and forward rendering of 3D Gaussian splatting scenes on one
+ * NVIDIA B300 (sm_103a).
+ *
+ * Method: ReCoGS, arXiv 2511.18441.
+ *   - Scene model: Eq. 1 (covariance Sigma = R S S^T R^T from a rotation and a
+ *     scale), Eq. 2 (view-dependent colour from degree-3 spherical harmonics),
+ *     opacity sigma (Sec. 3.1).
+ *   - Rendering: Eq. 3, front-to-back alpha blending with T_1 = 1,
+ *     T_{i+1} = T_i (1 - alpha_i) (Sec. 3.1); HWC output layout (Sec. 4.2).
+ *   - Edit: tinting c* = t . c of the selected region, refit of the SH
+ *     coefficients only with geometry frozen (Sec. 3.3). Selection: a
+ *     screen-space region drawn on one view (Sec. 3.2.1).
+ *
+ * Conventions (shared by every entry point):
+ *   - All arrays are structure-of-arrays, row-major, float32 unless stated.
+ *   - Device pointers are CUDA device (or managed) memory of the context's
+ *     device; host pointers are ordinary (preferably pinned) host memory.
+ *   - The caller owns every buffer passed in. The context owns its scratch
+ *     memory, which grows on demand and is released by recogs_ctx_destroy.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t, NULL = the legacy
+ *     default stream) unless stated otherwise; a context must not be used
+ *     from two host threads at once.
+ *   - Errors are returned as status codes; nothing is thrown across the ABI.
+ *     recogs_last_error() gives a message for the last failure.
+ *   - Pixel (i, j) has its centre at continuous coordinates (i, j). View
+ *     space is +x right, +y down, +z forward.
+ */
+#ifndef RECOGS_H
+#define RECOGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RECOGS_API __attribute__((visibility("default")))
+#else
+#define RECOGS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RECOGS_OK = 0,
+    RECOGS_EINVAL = 1,    /* a NULL, misaligned or inconsistent argument */
+    RECOGS_ENOMEM = 2,    /* device or pinned-host allocation failed */
+    RECOGS_ECUDA = 3,     /* a CUDA runtime call failed (message has the CUDA error) */
+    RECOGS_ECAPACITY = 4, /* a size exceeds a fixed limit (pairs >= 2^31, image too large) */
+    RECOGS_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+    RECOGS_EDEVICE = 6    /* no usable CUDA device, or not an sm_103 device */
+} recogs_status;
+
+typedef enum { RECOGS_F32 = 0, RECOGS_F16 = 1, RECOGS_BF16 = 2 } recogs_dtype;
+
+typedef struct recogs_ctx recogs_ctx;
+
+/* A Gaussian scene on the device (Sec. 3.1). n may be 0. */
+typedef struct {
+    int64_t n;                  /* number of Gaussians, 0 <= n < 2^31 */
+    const float* xyz;           /* [3][n] centres mu */
+    const float* log_scale;     /* [3][n] S = diag(exp(log_scale)) (Eq. 1) */
+    const float* quat;          /* [4][n] rotation R as (w, x, y, z), normalised on use */
+    const float* opacity_logit; /* [n] opacity sigma = sigmoid(logit) */
+    void* sh;                   /* [16][3][n] SH coefficients C_l^m (Eq. 2), k = l*l+l+m, then RGB */
+    int32_t sh_dtype;           /* recogs_dtype of sh; geometry is always float32 */
+    int32_t reserved;
+} recogs_scene;
+
+/* Pinhole camera: u = fx x/z + cx, v = fy y/z + cy in view space. */
+typedef struct {
+    int32_t width, height;      /* pixels, 1 .. 16384 each */
+    float fx, fy, cx, cy;
+    float world_to_view[12];    /* row-major 3x4 [W | t]: p_view = W p + t, W a rotation */
+    float cam_pos[3];           /* world-space camera centre (origin of SH view directions) */
+    float z_near;               /* Gaussians with view depth <= z_near are culled (0.2 typical) */
+} recogs_camera;
+
+#define RECOGS_MAX_POLYGON 64
+
+typedef enum { RECOGS_REGION_BOX = 1, RECOGS_REGION_POLYGON = 2 } recogs_region_kind;
+
+/* Screen-space selection region in continuous pixel coordinates of the
+ * selection camera (stand-in for the brush mask of Sec. 3.2.1). */
+typedef struct {
+    int32_t kind;               /* recogs_region_kind */
+    int32_t n_vertices;         /* polygon: 3 .. RECOGS_MAX_POLYGON; box: ignored */
+    const float* xy;            /* HOST memory, copied at the call. box: u0 v0 u1 v1, the
+                                   half-open [u0,u1) x [v0,v1); polygon: u v per vertex,
+                                   even-odd rule */
+} recogs_region;
+
+/* Colour matrix M acting on RGB (row-major). A tint t (Sec. 3.3) is
+ * diag(t0, t1, t2); a hue shift is a rotation about the grey axis. */
+typedef struct {
+    float color_matrix[9];
+} recogs_tint;
+
+/* A fused edit for recogs_render: select with `region` as seen from
+ * `select_camera` and recolour the selected Gaussians with `tint`. */
+typedef struct {
+    const recogs_camera* select_camera; /* HOST pointer; NULL = the render camera */
+    recogs_region region;
+    recogs_tint tint;
+} recogs_edit;
+
+typedef struct {
+    int64_t n_visible;          /* Gaussians with a non-empty footprint */
+    int64_t n_pairs;            /* (tile, Gaussian) pairs P */
+    int64_t n_pairs_read;       /* pairs the blend fetched before its tiles finished */
+    int32_t n_tiles;            /* 16x16 tiles of the image */
+    int32_t reserved;
+} recogs_render_stats;
+
+/* ---------------------------------------------------------------------------
+ * Context
+ */
+
+/* Create a context on CUDA device `device`. Fails with RECOGS_EDEVICE when
+ * no device is usable or it is not compute capability 10.3 (the library's
+ * kernels are built for sm_103a only). *out is NULL on failure. */
+RECOGS_API recogs_status recogs_ctx_create(recogs_ctx** out, int device);
+
+/* Release the context and its scratch memory (synchronises the device). NULL is a no-op. */
+RECOGS_API void recogs_ctx_destroy(recogs_ctx* ctx);
+
+/* Message for the last failure on ctx (never NULL; "" if none). With
+ * ctx == NULL, the message of the last failed recogs_ctx_create. */
+RECOGS_API const char* recogs_last_error(const recogs_ctx* ctx);
+
+/* Static name of a status code. */
+RECOGS_API const char* recogs_status_string(recogs_status s);
+
+/* ---------------------------------------------------------------------------
+ * The three operations of the method
+ */
+
+/* Region selection (Sec. 3.2.1 stand-in). Gaussian i is selected iff its
+ * centre lies in front of `camera` (view depth > 0) and projects into
+ * `region`. Writes bit (i % 32) of mask_out[i / 32] (device, ceil(n/32)
+ * words; padding bits of the last word are 0). near_boundary_out (device, n
+ * bytes, may be NULL) is set to 1 where the float32 centre lies within
+ * 1e-6 * max(width, height) px of the region's boundary or the depth is
+ * within 1e-6 of 0, i.e. where rounding may decide the bit. */
+RECOGS_API recogs_status recogs_select(recogs_ctx* ctx, const recogs_scene* scene,
+                            const recogs_camera* camera, const recogs_region* region,
+                            uint32_t* mask_out, uint8_t* near_boundary_out, void* stream);
+
+/* Recolour (Sec. 3.3, SH-only edit) in place: for every Gaussian whose mask
+ * bit is set, each SH coefficient triple becomes M C_k, and the DC triple
+ * additionally gains (M 1 - 1) 0.5 / Y_0 so that the shown colour before the
+ * clamp becomes M (f + 0.5): the tint c* = t . c for M = diag(t), t >= 0.
+ * Unselected Gaussians are not touched. 16-bit SH are recoloured in float32
+ * and rounded to nearest even on store. mask: device, ceil(n/32) words. */
+RECOGS_API recogs_status recogs_recolor(recogs_ctx* ctx, recogs_scene* scene, const uint32_t* mask,
+                             const recogs_tint* tint, void* stream);
+
+/* Forward render (Eq. 1-3) of `scene` from `camera` into image_hwc_out
+ * (device, height*width*3 float32, HWC, Sec. 4.2) and final_T_out (device,
+ * height*width, may be NULL). With edit != NULL the selection and recolour
+ * are fused into the per-Gaussian pass (the scene is not modified); the
+ * result equals recogs_select + recogs_recolor + recogs_render(edit=NULL)
+ * bit for bit. bg: host, 3 floats added as T_final * bg (NULL = black).
+ * stats: host, may be NULL; if given the call waits for the stream.
+ * The call reads the visible and pair counts back to the host once per
+ * frame (a stream synchronisation) to size its scratch. */
+RECOGS_API recogs_status recogs_render(recogs_ctx* ctx, const recogs_scene* scene,
+                            const recogs_camera* camera, const recogs_edit* edit,
+                            const float* bg, float* image_hwc_out, float* final_T_out,
+                            recogs_render_stats* stats, void* stream);
+
+/* recogs_render with every scene array and both outputs in HOST memory:
+ * the call copies the scene to context-owned device memory, renders, copies
+ * the image (and T if non-NULL) back and returns after the stream is done.
+ * Pinned host memory makes the copies asynchronous and fast. */
+RECOGS_API recogs_status recogs_render_host(recogs_ctx* ctx, const recogs_scene* host_scene,
+                                 const recogs_camera* camera, const recogs_edit* edit,
+                                 const float* bg, float* image_hwc_host, float* final_T_host,
+                                 recogs_render_stats* stats, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Introspection (tests and measurement)
+ */
+
+/* Copy the depth-sorted per-tile lists of the last recogs_render on ctx:
+ * ranges_out (device, 2*n_tiles uint32: [begin, end) per tile, row-major
+ * tiles) and ids_out (device, capacity uint32 Gaussian indices). Fails with
+ * RECOGS_ECAPACITY if capacity < n_pairs. */
+RECOGS_API recogs_status recogs_tile_lists(recogs_ctx* ctx, uint32_t* ranges_out, uint32_t* ids_out,
+                                int64_t capacity, void* stream);
+
+/* Enable (1) or disable (0) CUDA-event timing of each pipeline stage on the
+ * stream each stage runs on. */
+RECOGS_API recogs_status recogs_set_timing(recogs_ctx* ctx, int enable);
+
+/* Read accumulated stage timings (waits for recorded events). For up to
+ * max_stages stages writes names[i] (static strings), total_ms[i] and
+ * launches[i] (kernel launches of that stage); *n_stages = stages written.
+ * reset != 0 clears the accumulators afterwards. */
+RECOGS_API recogs_status recogs_stage_times(recogs_ctx* ctx, int32_t max_stages, int32_t* n_stages,
+                                 const char** names, double* total_ms, int64_t* launches,
+                                 int reset);
+
+/* Total kernel launches issued by ctx since creation. */
+RECOGS_API int64_t recogs_launch_count(const recogs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RECOGS_H */

@@ -53,7 +53,8 @@ class Edit(C.Structure):
 
 class Margins(C.Structure):
     _fields_ = [("eps_pos", C.c_double), ("eps_rel", C.c_double), ("eps_k", C.c_double),
-                ("impact", C.c_double)]
+                ("eps_pix", C.c_double), ("eps_cov", C.c_double), ("eps_exp", C.c_double),
+                ("eps_depth", C.c_double), ("impact", C.c_double)]
 
 
 class Splats(C.Structure):
@@ -132,13 +133,27 @@ def edit_struct(edit, cam):
     return e, [xy]
 
 
-def margins(cam, eps_pos=None, eps_rel=1e-5, eps_k=1e-6, impact=5e-5) -> Margins:
-    """Decision margins. eps_pos defaults to 1e-6 * max(W, H) px (the
-    selection-boundary width read relative to the image size)."""
+def margins(cam, eps_pos=None, eps_rel=1e-5, eps_k=1e-6, eps_pix=2e-5, eps_cov=1e-5,
+            eps_exp=4e-6, eps_depth=1e-6, impact=5e-5) -> Margins:
+    """Decision margins: how far float32 arithmetic may move each quantity.
+
+    eps_pos (selection and tile-range decisions) defaults to 1e-6 * max(W, H)
+    px, the selection-boundary width read relative to the image size. The
+    pixel-level margins bound a float32 implementation that keeps the
+    pixel-to-centre offset to ~1e-6 px, covariance entries to ~1e-6 of their
+    scale and the exponent to a few ulp; each default is 2.5-10x that bound.
+    eps_depth: two contributors whose depths differ by less (relative) may
+    share a float32 depth key, so their order, and the pixel's colour, is
+    not unique; such pixels are flagged.
+    """
     m = Margins()
     m.eps_pos = float(1e-6 * max(cam.width, cam.height) if eps_pos is None else eps_pos)
     m.eps_rel = float(eps_rel)
     m.eps_k = float(eps_k)
+    m.eps_pix = float(eps_pix)
+    m.eps_cov = float(eps_cov)
+    m.eps_exp = float(eps_exp)
+    m.eps_depth = float(eps_depth)
     m.impact = float(impact)
     return m
 

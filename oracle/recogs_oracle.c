@@ -529,6 +529,10 @@ static void blend_pixel(const oracle_splats* s, const int64_t* list, int64_t len
     int32_t count = 0;
     const double a_min = 1.0 / 255.0;
     double bgmax = fmax(fabs(bg[0]), fmax(fabs(bg[1]), fabs(bg[2])));
+    /* previous contributor, to flag colours that depend on the order of two
+     * Gaussians whose depths a float32 key may not separate */
+    int64_t prev = -1;
+    double prev_alpha = 0.0, prev_T = 0.0;
     for (int64_t k = 0; k < len; ++k) {
         int64_t i = list[k];
         double dx = px - s->u[i], dy = py - s->v[i];
@@ -538,17 +542,22 @@ static void blend_pixel(const oracle_splats* s, const int64_t* list, int64_t len
             /* For fixed dx the smallest d^T conic d is dx^2 / a; if that exceeds
              * k + 1 then alpha < exp(-1/2)/255 for every dy: no contribution and
              * no decision near the threshold. */
-            double a = s->cov2d[3 * i], c = s->cov2d[3 * i + 2];
-            if (dx * dx > a * (kk + 1.0) || dy * dy > c * (kk + 1.0)) continue;
+            double sa = s->cov2d[3 * i], sc = s->cov2d[3 * i + 2];
+            if (dx * dx > sa * (kk + 1.0) || dy * dy > sc * (kk + 1.0)) continue;
         }
         double A = s->conic[3 * i], B = s->conic[3 * i + 1], Cc = s->conic[3 * i + 2];
         double p = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy;
         if (p > 0.0) p = 0.0;
         double alpha = sigma * exp(p);
         if (alpha > 0.99) alpha = 0.99;
-        /* uncertainty of the exponent */
-        double g = fabs(A * dx + B * dy) + fabs(B * dx + Cc * dy);
-        double ep = mg->eps_pos * g + mg->eps_rel * (fabs(p) + 1.0);
+        /* Uncertainty of the exponent p = -d^T conic d / 2: an offset error
+         * moves it by |conic d| . delta; covariance errors dSigma move it by
+         * (conic d)^T dSigma (conic d) / 2 (derivative of the inverse). */
+        double gx = A * dx + B * dy, gy = B * dx + Cc * dy;
+        double a = s->cov2d[3 * i], c = s->cov2d[3 * i + 2];
+        double sg = sqrt(a) * fabs(gx) + sqrt(c) * fabs(gy);
+        double ep = mg->eps_pix * (fabs(gx) + fabs(gy)) + 0.5 * mg->eps_cov * sg * sg +
+                    mg->eps_exp * (fabs(p) + 1.0);
         double K = fmax(1.0, bgmax);
         for (int ch = 0; ch < 3; ++ch) K = fmax(K, s->rgb[3 * i + ch]);
         int is_valid = s->valid[i];
@@ -566,6 +575,16 @@ static void blend_pixel(const oracle_splats* s, const int64_t* list, int64_t len
         double eT_next = eT + alpha * ea / (1.0 - alpha) + 2.4e-7;
         if (fabs(log(testT / 1e-4)) <= eT_next) flag |= 2;
         if (testT < 1e-4) break;
+        if (prev >= 0 && fabs(s->depth[i] - s->depth[prev]) <= mg->eps_depth * fabs(s->depth[i])) {
+            /* swapping the two changes the colour by a_p a_i T_p (c_i - c_p) */
+            double dc = 0.0;
+            for (int ch = 0; ch < 3; ++ch)
+                dc = fmax(dc, fabs(s->rgb[3 * i + ch] - s->rgb[3 * prev + ch]));
+            if (prev_alpha * alpha * prev_T * dc > mg->impact) flag |= 16;
+        }
+        prev = i;
+        prev_alpha = alpha;
+        prev_T = T;
         for (int ch = 0; ch < 3; ++ch) C[ch] += s->rgb[3 * i + ch] * alpha * T;
         T = testT;
         eT = eT_next;

@@ -52,9 +52,13 @@ typedef struct {
 /* Uncertainty model used only to flag decisions that float32 arithmetic may
  * take the other way; flagged items are excluded from exact comparisons. */
 typedef struct {
-    double eps_pos;          /* px: uncertainty of projected positions and extents */
-    double eps_rel;          /* relative uncertainty of covariances, exponents and depths */
+    double eps_pos;          /* px: uncertainty of projected centres for selection and tile ranges */
+    double eps_rel;          /* relative uncertainty of extents and view depths */
     double eps_k;            /* absolute uncertainty of 2 ln(255 sigma) */
+    double eps_pix;          /* px: uncertainty of the pixel-to-centre offset inside alpha */
+    double eps_cov;          /* uncertainty of 2D covariance entries relative to sqrt(a_ii a_jj) */
+    double eps_exp;          /* relative uncertainty of the exponent and of alpha */
+    double eps_depth;        /* relative depth difference below which a float32 key may tie */
     double impact;           /* a pixel decision is flagged only if it can move a channel by more */
 } oracle_margins;
 

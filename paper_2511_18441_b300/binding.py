@@ -1,0 +1,326 @@
+"""ctypes binding of librecogs.so (declared in include/recogs.h).
+
+Argument marshalling only: torch tensors supply device memory and streams,
+every step of selection, recolouring and rendering runs in the library's
+CUDA kernels. There is no CPU fallback: if the library is missing or the
+device is not an sm_103 GPU, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librecogs.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ECAPACITY, ETIMEOUT, EDEVICE = range(7)
+F32, F16, BF16 = 0, 1, 2
+REGION_BOX, REGION_POLYGON = 1, 2
+MAX_POLYGON = 64
+
+
+class RecogsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+class CScene(C.Structure):
+    _fields_ = [("n", C.c_int64), ("xyz", C.c_void_p), ("log_scale", C.c_void_p),
+                ("quat", C.c_void_p), ("opacity_logit", C.c_void_p), ("sh", C.c_void_p),
+                ("sh_dtype", C.c_int32), ("reserved", C.c_int32)]
+
+
+class CCamera(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("world_to_view", C.c_float * 12),
+                ("cam_pos", C.c_float * 3), ("z_near", C.c_float)]
+
+
+class CRegion(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_vertices", C.c_int32), ("xy", C.POINTER(C.c_float))]
+
+
+class CTint(C.Structure):
+    _fields_ = [("color_matrix", C.c_float * 9)]
+
+
+class CEdit(C.Structure):
+    _fields_ = [("select_camera", C.POINTER(CCamera)), ("region", CRegion), ("tint", CTint)]
+
+
+class CStats(C.Structure):
+    _fields_ = [("n_visible", C.c_int64), ("n_pairs", C.c_int64), ("n_pairs_read", C.c_int64),
+                ("n_tiles", C.c_int32), ("reserved", C.c_int32)]
+
+
+# Every entry point of include/recogs.h with its ctypes signature.
+SIGNATURES = {
+    "recogs_ctx_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
+    "recogs_ctx_destroy": (None, [C.c_void_p]),
+    "recogs_last_error": (C.c_char_p, [C.c_void_p]),
+    "recogs_status_string": (C.c_char_p, [C.c_int]),
+    "recogs_select": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.POINTER(CCamera),
+                                C.POINTER(CRegion), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "recogs_recolor": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.c_void_p, C.POINTER(CTint),
+                                 C.c_void_p]),
+    "recogs_render": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.POINTER(CCamera),
+                                C.POINTER(CEdit), C.POINTER(C.c_float), C.c_void_p, C.c_void_p,
+                                C.POINTER(CStats), C.c_void_p]),
+    "recogs_render_host": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.POINTER(CCamera),
+                                     C.POINTER(CEdit), C.POINTER(C.c_float), C.c_void_p,
+                                     C.c_void_p, C.POINTER(CStats), C.c_void_p]),
+    "recogs_tile_lists": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "recogs_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "recogs_stage_times": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_char_p), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_int64), C.c_int]),
+    "recogs_launch_count": (C.c_int64, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def load():
+    """Load librecogs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2511_18441_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _status_name(s):
+    try:
+        return load().recogs_status_string(s).decode()
+    except Exception:
+        return f"status {s}"
+
+
+# ---------------------------------------------------------------------------
+# struct builders (host side, from scenegen objects)
+
+def camera_struct(cam) -> CCamera:
+    c = CCamera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    v = np.asarray(cam.world_to_view, np.float32).reshape(12)
+    for k in range(12):
+        c.world_to_view[k] = float(v[k])
+    p = np.asarray(cam.cam_pos, np.float32).reshape(3)
+    for k in range(3):
+        c.cam_pos[k] = float(p[k])
+    c.z_near = float(cam.z_near)
+    return c
+
+
+def region_struct(region):
+    """Returns (CRegion, keep-alive array)."""
+    xy = np.ascontiguousarray(np.asarray(region.xy, np.float32).reshape(-1))
+    r = CRegion()
+    r.kind = REGION_BOX if region.kind == "box" else REGION_POLYGON
+    r.n_vertices = len(xy) // 2
+    r.xy = xy.ctypes.data_as(C.POINTER(C.c_float))
+    return r, xy
+
+
+def tint_struct(M) -> CTint:
+    t = CTint()
+    m = np.asarray(M, np.float32).reshape(9)
+    for k in range(9):
+        t.color_matrix[k] = float(m[k])
+    return t
+
+
+def edit_struct(edit):
+    """Returns (CEdit, keep-alive list) for a scenegen.Edit (or None)."""
+    if edit is None:
+        return None, []
+    e = CEdit()
+    keep = []
+    if edit.select_camera is not None:
+        sc = camera_struct(edit.select_camera)
+        keep.append(sc)
+        e.select_camera = C.pointer(sc)
+    r, xy = region_struct(edit.region)
+    keep.append(xy)
+    e.region = r
+    e.tint = tint_struct(edit.color_matrix)
+    return e, keep
+
+
+# ---------------------------------------------------------------------------
+# scenes in device (or pinned host) memory
+
+_TORCH_SH = {"f32": (F32, "float32"), "f16": (F16, "float16"), "bf16": (BF16, "bfloat16")}
+
+
+class DeviceScene:
+    """A scene's arrays as torch tensors (CUDA or pinned host)."""
+
+    def __init__(self, xyz, log_scale, quat, opacity_logit, sh, sh_kind="f32"):
+        self.xyz, self.log_scale, self.quat = xyz, log_scale, quat
+        self.opacity_logit, self.sh, self.sh_kind = opacity_logit, sh, sh_kind
+
+    @property
+    def n(self):
+        return int(self.xyz.shape[1])
+
+    @classmethod
+    def from_numpy(cls, scene, device="cuda", sh_kind="f32", pin=False):
+        import torch
+        dt = getattr(torch, _TORCH_SH[sh_kind][1])
+
+        def t(a, dtype=torch.float32):
+            x = torch.from_numpy(np.ascontiguousarray(a))
+            if x.dtype != dtype:
+                x = x.to(dtype)
+            if device == "cpu":
+                return x.pin_memory() if pin else x.contiguous()
+            return x.to(device, non_blocking=False).contiguous()
+
+        return cls(t(scene.xyz), t(scene.log_scale), t(scene.quat), t(scene.opacity_logit),
+                   t(scene.sh, dt), sh_kind)
+
+    def struct(self) -> CScene:
+        s = CScene()
+        s.n = self.n
+        s.xyz = self.xyz.data_ptr()
+        s.log_scale = self.log_scale.data_ptr()
+        s.quat = self.quat.data_ptr()
+        s.opacity_logit = self.opacity_logit.data_ptr()
+        s.sh = self.sh.data_ptr()
+        s.sh_dtype = _TORCH_SH[self.sh_kind][0]
+        return s
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Context:
+    """One librecogs context (scratch memory) on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        L = load()
+        h = C.c_void_p()
+        s = L.recogs_ctx_create(C.byref(h), int(device))
+        if s != OK:
+            raise RecogsError(s, L.recogs_last_error(None).decode())
+        self._h = h
+        self._L = L
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.recogs_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, s):
+        if s != OK:
+            raise RecogsError(s, self._L.recogs_last_error(self._h).decode())
+
+    # -- the three operations ------------------------------------------------
+
+    def select(self, scene: DeviceScene, cam, region, mask_out, near_out=None, stream=None):
+        cs = scene.struct()
+        cc = camera_struct(cam)
+        r, keep = region_struct(region)
+        self._check(self._L.recogs_select(
+            self._h, C.byref(cs), C.byref(cc), C.byref(r), mask_out.data_ptr(),
+            near_out.data_ptr() if near_out is not None else None, _stream_ptr(stream)))
+
+    def recolor(self, scene: DeviceScene, mask, color_matrix, stream=None):
+        cs = scene.struct()
+        t = tint_struct(color_matrix)
+        self._check(self._L.recogs_recolor(self._h, C.byref(cs), mask.data_ptr(), C.byref(t),
+                                           _stream_ptr(stream)))
+
+    def render(self, scene: DeviceScene, cam, edit=None, bg=None, image_out=None, T_out=None,
+               stats=False, stream=None):
+        import torch
+        H, W = int(cam.height), int(cam.width)
+        dev = scene.xyz.device
+        if image_out is None:
+            image_out = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+        cs = scene.struct()
+        cc = camera_struct(cam)
+        e, keep = edit_struct(edit)
+        bgv = (C.c_float * 3)(*(np.asarray(bg if bg is not None else (0, 0, 0), np.float32)))
+        st = CStats()
+        self._check(self._L.recogs_render(
+            self._h, C.byref(cs), C.byref(cc), C.byref(e) if e is not None else None, bgv,
+            image_out.data_ptr(), T_out.data_ptr() if T_out is not None else None,
+            C.byref(st) if stats else None, _stream_ptr(stream)))
+        if stats:
+            return image_out, dict(n_visible=st.n_visible, n_pairs=st.n_pairs,
+                                   n_pairs_read=st.n_pairs_read, n_tiles=st.n_tiles)
+        return image_out
+
+    def render_host(self, scene: DeviceScene, cam, edit=None, bg=None, image_out=None, T_out=None,
+                    stats=False, stream=None):
+        """Scene tensors and outputs in host memory (pinned for speed)."""
+        import torch
+        H, W = int(cam.height), int(cam.width)
+        if image_out is None:
+            image_out = torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
+        cs = scene.struct()
+        cc = camera_struct(cam)
+        e, keep = edit_struct(edit)
+        bgv = (C.c_float * 3)(*(np.asarray(bg if bg is not None else (0, 0, 0), np.float32)))
+        st = CStats()
+        self._check(self._L.recogs_render_host(
+            self._h, C.byref(cs), C.byref(cc), C.byref(e) if e is not None else None, bgv,
+            image_out.data_ptr(), T_out.data_ptr() if T_out is not None else None,
+            C.byref(st) if stats else None, _stream_ptr(stream)))
+        if stats:
+            return image_out, dict(n_visible=st.n_visible, n_pairs=st.n_pairs,
+                                   n_pairs_read=st.n_pairs_read, n_tiles=st.n_tiles)
+        return image_out
+
+    # -- introspection --------------------------------------------------------
+
+    def tile_lists(self, n_tiles, n_pairs, device="cuda", stream=None):
+        import torch
+        ranges = torch.empty((n_tiles, 2), dtype=torch.int32, device=device)
+        ids = torch.empty((max(n_pairs, 1),), dtype=torch.int32, device=device)
+        self._check(self._L.recogs_tile_lists(self._h, ranges.data_ptr(), ids.data_ptr(),
+                                              max(n_pairs, 1), _stream_ptr(stream)))
+        return ranges, ids[:n_pairs]
+
+    def set_timing(self, enable: bool):
+        self._check(self._L.recogs_set_timing(self._h, 1 if enable else 0))
+
+    def stage_times(self, reset=False):
+        n = C.c_int32()
+        names = (C.c_char_p * 32)()
+        ms = (C.c_double * 32)()
+        cnt = (C.c_int64 * 32)()
+        self._check(self._L.recogs_stage_times(self._h, 32, C.byref(n), names, ms, cnt,
+                                               1 if reset else 0))
+        return {names[k].decode(): (ms[k], cnt[k]) for k in range(n.value)}
+
+    def launch_count(self) -> int:
+        return int(self._L.recogs_launch_count(self._h))
+
+
+def mask_words(n: int) -> int:
+    return (n + 31) // 32

@@ -1,0 +1,366 @@
+// Per-Gaussian kernels: region selection, SH recolour and the fused
+// select + recolour + projection pass that feeds the tile sort and blend.
+//
+// Paper: ReCoGS (arXiv 2511.18441). Covariance Sigma = R S S^T R^T (Eq. 1),
+// SH colour (Eq. 2), opacity (Sec. 3.1); tint c* = t.c applied through the SH
+// coefficients only (Sec. 3.3).
+//
+// Data layout: every per-Gaussian attribute is structure-of-arrays, so one
+// warp reads 32 consecutive floats (128 B, one fully used line) per
+// attribute row; the 48 SH rows are the bulk of the traffic.
+#include "recogs_internal.cuh"
+
+namespace recogs {
+
+// ---------------------------------------------------------------------------
+// SH storage types
+
+template <int D> struct ShType;
+template <> struct ShType<RECOGS_F32> { using T = float; };
+template <> struct ShType<RECOGS_F16> { using T = __half; };
+template <> struct ShType<RECOGS_BF16> { using T = __nv_bfloat16; };
+
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T> __device__ __forceinline__ T from_f32(float v);
+template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+
+// Recolour the 16 coefficient triples of one Gaussian (Sec. 3.3): C_k <- M C_k,
+// then the DC triple gains the offset correction. 16-bit storage rounds the
+// result exactly as a store would, so the fused path matches recolour-then-render.
+template <typename T>
+__device__ __forceinline__ void recolor_coeffs(const float* M, const float* dc_fix, float* C) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) recolor_triple(M, C[3 * k], C[3 * k + 1], C[3 * k + 2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) C[c] = __fadd_rn(C[c], dc_fix[c]);
+#pragma unroll
+    for (int k = 0; k < 48; ++k) C[k] = to_f32(from_f32<T>(C[k]));
+}
+
+// ---------------------------------------------------------------------------
+// select
+
+__global__ void __launch_bounds__(256) select_kernel(int n, const float* __restrict__ xyz,
+                                                      DevCamera cam, DevRegion reg,
+                                                      uint32_t* __restrict__ mask,
+                                                      uint8_t* __restrict__ near_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool sel = false, nb = false;
+    if (i < n)
+        sel = select_centre(cam, reg, __ldg(xyz + i), __ldg(xyz + n + i), __ldg(xyz + 2 * n + i),
+                            near_out ? &nb : nullptr);
+    const uint32_t bits = __ballot_sync(0xffffffffu, sel);
+    if ((threadIdx.x & 31) == 0 && i < n) mask[i >> 5] = bits;
+    if (near_out && i < n) near_out[i] = nb ? 1 : 0;
+}
+
+int launch_select(const recogs_scene& s, const DevCamera& cam, const DevRegion& reg,
+                  uint32_t* mask, uint8_t* near_out, cudaStream_t st) {
+    const int n = (int)s.n;
+    if (n == 0) return 0;
+    select_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, s.xyz, cam, reg, mask, near_out);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// recolour in place
+
+struct RecolorParams {
+    float M[9];
+    float dc_fix[3];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) recolor_kernel(int n, T* __restrict__ sh,
+                                                       const uint32_t* __restrict__ mask,
+                                                       RecolorParams p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (!((__ldg(mask + (i >> 5)) >> (i & 31)) & 1u)) return;
+    float C[48];
+#pragma unroll
+    for (int k = 0; k < 48; ++k) C[k] = to_f32(sh[(size_t)k * n + i]);
+    recolor_coeffs<T>(p.M, p.dc_fix, C);
+#pragma unroll
+    for (int k = 0; k < 48; ++k) sh[(size_t)k * n + i] = from_f32<T>(C[k]);
+}
+
+int launch_recolor(recogs_scene& s, const uint32_t* mask, const float M[9], const float dc_fix[3],
+                   cudaStream_t st) {
+    const int n = (int)s.n;
+    if (n == 0) return 0;
+    RecolorParams p;
+    for (int k = 0; k < 9; ++k) p.M[k] = M[k];
+    for (int k = 0; k < 3; ++k) p.dc_fix[k] = dc_fix[k];
+    const int g = (n + 255) / 256;
+    switch (s.sh_dtype) {
+        case RECOGS_F32: recolor_kernel<float><<<g, 256, 0, st>>>(n, (float*)s.sh, mask, p); break;
+        case RECOGS_F16: recolor_kernel<__half><<<g, 256, 0, st>>>(n, (__half*)s.sh, mask, p); break;
+        default:
+            recolor_kernel<__nv_bfloat16><<<g, 256, 0, st>>>(n, (__nv_bfloat16*)s.sh, mask, p);
+    }
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// fused select + recolour + preprocess
+
+// Real SH basis of degree 3 at the unit direction (x, y, z) (Eq. 2), index
+// k = l*l + l + m, Condon-Shortley phase kept in the real combinations.
+// Constants: sqrt2 N_l^|m| times the polynomial factor of P_l^|m|, with
+// N_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!).
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = 0.28209479177387814f;
+    Y[1] = -0.4886025119029199f * y;
+    Y[2] = 0.4886025119029199f * z;
+    Y[3] = -0.4886025119029199f * x;
+    Y[4] = 1.0925484305920792f * x * y;
+    Y[5] = -1.0925484305920792f * y * z;
+    Y[6] = 0.31539156525252005f * (3.0f * zz - 1.0f);
+    Y[7] = -1.0925484305920792f * x * z;
+    Y[8] = 0.5462742152960396f * (xx - yy);
+    Y[9] = -0.5900435899266436f * y * (3.0f * xx - yy);
+    Y[10] = 2.8906114426405547f * x * y * z;
+    Y[11] = -0.4570457994644658f * y * (5.0f * zz - 1.0f);
+    Y[12] = 0.3731763325901154f * z * (5.0f * zz - 3.0f);
+    Y[13] = -0.4570457994644658f * x * (5.0f * zz - 1.0f);
+    Y[14] = 1.4453057213202773f * z * (xx - yy);
+    Y[15] = -0.5900435899266436f * x * (xx - 3.0f * yy);
+}
+
+// Error-free transformations for the projected centre. The blend needs the
+// offset from a pixel to the centre to ~1e-6 px: at 1080p a float32 centre
+// rounded near u ~ 1000 carries ~1e-4 px, which moves alpha of a 1 px
+// Gaussian by ~2e-4. The view transform is a compensated dot product
+// (Dot2 of Ogita, Rump and Oishi, 2005: FMA-based TwoProd plus Knuth's
+// TwoSum), the perspective division carries its exact FMA residual, and the
+// centre is stored relative to the Gaussian's first tile.
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
+__device__ __forceinline__ float two_prod(float a, float b, float& err) {
+    const float p = __fmul_rn(a, b);
+    err = __fmaf_rn(a, b, -p);
+    return p;
+}
+
+// w0 x + w1 y + w2 z + c as an unevaluated pair hi + lo
+__device__ __forceinline__ float dot3c(float w0, float w1, float w2, float x, float y, float z,
+                                       float c, float& lo) {
+    float s, e, q;
+    float p = two_prod(w0, x, s);
+    float h = two_prod(w1, y, e);
+    p = two_sum(p, h, q);
+    s = __fadd_rn(s, __fadd_rn(q, e));
+    h = two_prod(w2, z, e);
+    p = two_sum(p, h, q);
+    s = __fadd_rn(s, __fadd_rn(q, e));
+    p = two_sum(p, c, q);
+    lo = __fadd_rn(s, q);
+    return p;
+}
+
+// (xh + xl) / (zh + zl) as hi + lo
+__device__ __forceinline__ float div2(float xh, float xl, float zh, float zl, float& lo) {
+    const float q = __fdiv_rn(xh, zh);
+    const float r = __fmaf_rn(-q, zh, xh);
+    lo = __fdiv_rn(__fsub_rn(__fadd_rn(r, xl), __fmul_rn(q, zl)), zh);
+    return q;
+}
+
+// Tile range of the pixel-centre interval [c - e, c + e]: tiles t with
+// 16t <= c + e and 16t + 15 >= c - e, clamped to [0, tiles - 1].
+__device__ __forceinline__ void tile_span(float c, float e, int tiles, int& t0, int& t1) {
+    float a = ceilf((c - e - 15.0f) * (1.0f / 16.0f));
+    float b = floorf((c + e) * (1.0f / 16.0f));
+    a = fminf(fmaxf(a, 0.0f), (float)tiles);
+    b = fminf(fmaxf(b, -1.0f), (float)(tiles - 1));
+    t0 = (int)a;
+    t1 = (int)b;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPrepThreads)
+    preprocess_kernel(int n, const float* __restrict__ xyz, const float* __restrict__ lsc,
+                      const float* __restrict__ quat, const float* __restrict__ opl,
+                      const T* __restrict__ sh, DevCamera cam, DevEdit edit, PrepOut out) {
+    const int i = blockIdx.x * kPrepThreads + threadIdx.x;
+    uint32_t cnt = 0;
+    uint32_t zbits = 0;
+    if (i < n) {
+        const float mx = __ldg(xyz + i), my = __ldg(xyz + n + i), mz = __ldg(xyz + 2 * n + i);
+        float C[48];
+#pragma unroll
+        for (int k = 0; k < 48; ++k) C[k] = to_f32(sh[(size_t)k * n + i]);
+        const float ls0 = __ldg(lsc + i), ls1 = __ldg(lsc + n + i), ls2 = __ldg(lsc + 2 * n + i);
+        const float qw = __ldg(quat + i), qx = __ldg(quat + n + i), qy = __ldg(quat + 2 * n + i),
+                    qz = __ldg(quat + 3 * n + i);
+        const float logit = __ldg(opl + i);
+
+        // selection and recolour (Sec. 3.3): the SH coefficients change, geometry does not
+        if (edit.enabled && select_centre(edit.cam, edit.region, mx, my, mz, nullptr))
+            recolor_coeffs<T>(edit.M, edit.dc_fix, C);
+
+        float txl, tyl, tzl;
+        const float tx = dot3c(cam.W[0], cam.W[1], cam.W[2], mx, my, mz, cam.t[0], txl);
+        const float ty = dot3c(cam.W[3], cam.W[4], cam.W[5], mx, my, mz, cam.t[1], tyl);
+        const float tz = dot3c(cam.W[6], cam.W[7], cam.W[8], mx, my, mz, cam.t[2], tzl);
+        bool valid = tz > cam.z_near;
+        float u = 0.f, v = 0.f, A = 0.f, B = 0.f, Cc = 0.f, sa = 0.f, sc = 0.f;
+        float qxh = 0.f, qxl = 0.f, qyh = 0.f, qyl = 0.f;
+        if (valid) {
+            const float iz = 1.0f / tz;
+            qxh = div2(tx, txl, tz, tzl, qxl);
+            qyh = div2(ty, tyl, tz, tzl, qyl);
+            u = __fadd_rn(__fmaf_rn(cam.fx, qxh, cam.cx), __fmul_rn(cam.fx, qxl));
+            v = __fadd_rn(__fmaf_rn(cam.fy, qyh, cam.cy), __fmul_rn(cam.fy, qyl));
+            // Eq. 1 with the EWA projection: Sigma' = (J W R S)(J W R S)^T + 0.3 I.
+            const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+            const float w = qw * qn, x = qx * qn, y = qy * qn, z = qz * qn;
+            const float R[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
+                                2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
+                                2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
+            const float s[3] = {expf(ls0), expf(ls1), expf(ls2)};
+            const float rx = fminf(fmaxf(tx * iz, -cam.limx), cam.limx);
+            const float ry = fminf(fmaxf(ty * iz, -cam.limy), cam.limy);
+            const float j00 = cam.fx * iz, j02 = -cam.fx * rx * iz;
+            const float j11 = cam.fy * iz, j12 = -cam.fy * ry * iz;
+            float T0[3], T1[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                T0[c] = j00 * cam.W[c] + j02 * cam.W[6 + c];
+                T1[c] = j11 * cam.W[3 + c] + j12 * cam.W[6 + c];
+            }
+            float a = 0.f, b = 0.f, c2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float A0 = (T0[0] * R[k] + T0[1] * R[3 + k] + T0[2] * R[6 + k]) * s[k];
+                const float A1 = (T1[0] * R[k] + T1[1] * R[3 + k] + T1[2] * R[6 + k]) * s[k];
+                a += A0 * A0;
+                b += A0 * A1;
+                c2 += A1 * A1;
+            }
+            a += 0.3f;
+            c2 += 0.3f;
+            const float det = a * c2 - b * b;
+            valid = det > 0.f;
+            if (valid) {
+                const float idet = 1.0f / det;
+                A = c2 * idet;
+                B = -b * idet;
+                Cc = a * idet;
+                sa = a;
+                sc = c2;
+            }
+        }
+        if (valid) {
+            // opacity sigma = sigmoid(logit); footprint: the alpha >= 1/255 ellipse
+            // d^T conic d <= k, k = 2 ln(255 sigma) = 2 (ln 255 - ln(1 + e^-logit))
+            const float sigma = 1.0f / (1.0f + expf(-logit));
+            const float kk = 2.0f * (5.541263545158426f - log1pf(expf(-logit)));
+            if (kk >= 0.f) {
+                const float ex = sqrtf(kk * sa), ey = sqrtf(kk * sc);
+                int tx0, tx1, ty0, ty1;
+                tile_span(u, ex, cam.tiles_x, tx0, tx1);
+                tile_span(v, ey, cam.tiles_y, ty0, ty1);
+                if (tx0 <= tx1 && ty0 <= ty1) {
+                    cnt = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+                    zbits = __float_as_uint(tz);
+                    // Eq. 2 at d = (mu - camera) / |mu - camera|, shown colour max(f + 0.5, 0)
+                    float dx = mx - cam.pos[0], dy = my - cam.pos[1], dz = mz - cam.pos[2];
+                    const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
+                    dx *= dn; dy *= dn; dz *= dn;
+                    float Y[16];
+                    sh_basis(dx, dy, dz, Y);
+                    float f[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) acc = fmaf(Y[k], C[3 * k + c], acc);
+                        f[c] = fmaxf(acc + 0.5f, 0.f);
+                    }
+                    // centre relative to the first tile's origin: cx - 16 tx0 is exact,
+                    // so one rounding at the end of a value of a few pixels
+                    const float ul = __fadd_rn(__fmaf_rn(cam.fx, qxh, cam.cx - 16.0f * (float)tx0),
+                                               __fmul_rn(cam.fx, qxl));
+                    const float vl = __fadd_rn(__fmaf_rn(cam.fy, qyh, cam.cy - 16.0f * (float)ty0),
+                                               __fmul_rn(cam.fy, qyl));
+                    const uint32_t origin = (uint32_t)tx0 | ((uint32_t)ty0 << 16);
+                    out.rec[3 * (size_t)i + 0] = make_float4(ul, vl, A, B);
+                    out.rec[3 * (size_t)i + 1] = make_float4(Cc, sigma, ex, ey);
+                    out.rec[3 * (size_t)i + 2] = make_float4(f[0], f[1], f[2], __uint_as_float(origin));
+                    out.rect[i] = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16),
+                                             (uint32_t)ty0 | ((uint32_t)ty1 << 16));
+                }
+            }
+        }
+        out.count[i] = cnt;
+        out.zkey[i] = zbits;
+    }
+    // block totals of visible Gaussians and pairs; depth range of visible ones
+    const unsigned full = 0xffffffffu;
+    const uint32_t vis = cnt > 0 ? 1u : 0u;
+    const uint32_t wv = __reduce_add_sync(full, vis);
+    const uint32_t wp = __reduce_add_sync(full, cnt);
+    const uint32_t wzmin = __reduce_min_sync(full, cnt > 0 ? zbits : 0xffffffffu);
+    const uint32_t wzmax = __reduce_max_sync(full, cnt > 0 ? zbits : 0u);
+    __shared__ uint32_t s_v[kPrepThreads / 32], s_p[kPrepThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_v[warp] = wv;
+        s_p[warp] = wp;
+        if (wv) {
+            atomicMax(&out.counters->zmin_inv, ~wzmin);
+            atomicMax(&out.counters->zmax, wzmax);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t tv = 0, tp = 0;
+#pragma unroll
+        for (int w = 0; w < kPrepThreads / 32; ++w) {
+            tv += s_v[w];
+            tp += s_p[w];
+        }
+        out.block_sums[blockIdx.x] = tv;
+        out.block_sums[gridDim.x + blockIdx.x] = tp;
+    }
+}
+
+int launch_preprocess(const recogs_scene& s, const DevCamera& cam, const DevEdit& edit,
+                      const PrepOut& out, cudaStream_t st) {
+    const int n = (int)s.n;
+    if (n == 0) return 0;
+    const int g = (n + kPrepThreads - 1) / kPrepThreads;
+    const float* x = s.xyz;
+    switch (s.sh_dtype) {
+        case RECOGS_F32:
+            preprocess_kernel<float><<<g, kPrepThreads, 0, st>>>(
+                n, x, s.log_scale, s.quat, s.opacity_logit, (const float*)s.sh, cam, edit, out);
+            break;
+        case RECOGS_F16:
+            preprocess_kernel<__half><<<g, kPrepThreads, 0, st>>>(
+                n, x, s.log_scale, s.quat, s.opacity_logit, (const __half*)s.sh, cam, edit, out);
+            break;
+        default:
+            preprocess_kernel<__nv_bfloat16><<<g, kPrepThreads, 0, st>>>(
+                n, x, s.log_scale, s.quat, s.opacity_logit, (const __nv_bfloat16*)s.sh, cam, edit,
+                out);
+    }
+    return 1;
+}
+
+}  // namespace recogs

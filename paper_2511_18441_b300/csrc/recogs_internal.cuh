@@ -1,0 +1,173 @@
+// Internal declarations shared by the kernels and the C ABI of librecogs.so.
+// Paper: ReCoGS (arXiv 2511.18441). Eq. 1-3 of Sec. 3.1, the tint and the
+// SH-only edit of Sec. 3.3, HWC output of Sec. 4.2.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/recogs.h"
+
+namespace recogs {
+
+constexpr int kTile = 16;               // 16x16 pixel tiles
+constexpr int kBlendThreads = 256;      // one thread per tile pixel
+constexpr int kPrepThreads = 256;       // Gaussians per preprocess block
+constexpr int kSortThreads = 256;
+constexpr int kSortItemsPerThread = 16;
+constexpr int kSortTile = kSortThreads * kSortItemsPerThread;   // 4096 keys per sort block
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+
+// Camera as the kernels see it.
+struct DevCamera {
+    int width, height, tiles_x, tiles_y;
+    float fx, fy, cx, cy;
+    float W[9];          // world -> view rotation, row-major
+    float t[3];
+    float pos[3];        // camera centre in world space
+    float z_near;
+    float limx, limy;    // 1.3 x tan(half field of view): clamp of x/z, y/z in the Jacobian
+};
+
+struct DevRegion {
+    int kind;            // RECOGS_REGION_BOX / RECOGS_REGION_POLYGON, 0 = none
+    int n;               // polygon vertices
+    float eps;           // near-boundary width in px
+    float xy[2 * RECOGS_MAX_POLYGON];
+};
+
+struct DevEdit {
+    int enabled;
+    DevCamera cam;       // selection camera
+    DevRegion region;
+    float M[9];          // colour matrix
+    float dc_fix[3];     // (row sum of M - 1) * 0.5 / Y_0, the DC offset correction
+};
+
+// Counters written by the kernels of one frame (zeroed at its start).
+struct DevCounters {
+    uint32_t zmin_inv;   // ~(smallest depth bits) of visible Gaussians (atomicMax)
+    uint32_t zmax;       // largest depth bits of visible Gaussians
+    uint32_t n_visible;
+    uint32_t n_pairs;
+    unsigned long long pairs_read;
+    uint32_t error;
+    uint32_t pad;
+};
+
+// --------------------------------------------------------------------------
+// Exact-rounding helpers shared by the selection and recolour code so that
+// the fused and the stand-alone paths produce identical bits.
+
+__device__ __forceinline__ void view_point(const DevCamera& c, float x, float y, float z,
+                                           float& tx, float& ty, float& tz) {
+    tx = __fadd_rn(__fmaf_rn(c.W[2], z, __fmaf_rn(c.W[1], y, __fmul_rn(c.W[0], x))), c.t[0]);
+    ty = __fadd_rn(__fmaf_rn(c.W[5], z, __fmaf_rn(c.W[4], y, __fmul_rn(c.W[3], x))), c.t[1]);
+    tz = __fadd_rn(__fmaf_rn(c.W[8], z, __fmaf_rn(c.W[7], y, __fmul_rn(c.W[6], x))), c.t[2]);
+}
+
+// Selection of one centre (Sec. 3.2.1 stand-in): in front of the camera and
+// inside the region. near_out: within eps px of the boundary, or depth ~ 0.
+__device__ __forceinline__ bool select_centre(const DevCamera& c, const DevRegion& r, float x,
+                                              float y, float z, bool* near_out) {
+    float tx, ty, tz;
+    view_point(c, x, y, z, tx, ty, tz);
+    float zs = fabsf(c.W[6] * x) + fabsf(c.W[7] * y) + fabsf(c.W[8] * z) + fabsf(c.t[2]);
+    bool near_b = fabsf(tz) <= 1e-6f * zs;
+    bool in = false;
+    if (tz > 0.0f) {
+        float u = __fmaf_rn(c.fx, __fdiv_rn(tx, tz), c.cx);
+        float v = __fmaf_rn(c.fy, __fdiv_rn(ty, tz), c.cy);
+        if (r.kind == RECOGS_REGION_BOX) {
+            in = (u >= r.xy[0]) && (u < r.xy[2]) && (v >= r.xy[1]) && (v < r.xy[3]);
+            if (near_out)
+                near_b = near_b || fabsf(u - r.xy[0]) <= r.eps || fabsf(u - r.xy[2]) <= r.eps ||
+                         fabsf(v - r.xy[1]) <= r.eps || fabsf(v - r.xy[3]) <= r.eps;
+        } else if (r.kind == RECOGS_REGION_POLYGON) {
+            // even-odd rule: an edge counts when one end is above the line v and
+            // the other is not, and the crossing lies to the right of u
+            bool inside = false;
+            for (int i = 0, j = r.n - 1; i < r.n; j = i++) {
+                float xi = r.xy[2 * i], yi = r.xy[2 * i + 1];
+                float xj = r.xy[2 * j], yj = r.xy[2 * j + 1];
+                if ((yi > v) != (yj > v)) {
+                    float xc = __fadd_rn(xi, __fdiv_rn(__fmul_rn(__fsub_rn(v, yi), __fsub_rn(xj, xi)),
+                                                       __fsub_rn(yj, yi)));
+                    if (u < xc) inside = !inside;
+                }
+                if (near_out) {
+                    float ex = xi - xj, ey = yi - yj;
+                    float l2 = ex * ex + ey * ey;
+                    float s = l2 > 0.f ? ((u - xj) * ex + (v - yj) * ey) / l2 : 0.f;
+                    s = fminf(fmaxf(s, 0.f), 1.f);
+                    float dx = u - (xj + s * ex), dy = v - (yj + s * ey);
+                    near_b = near_b || (dx * dx + dy * dy <= r.eps * r.eps);
+                }
+            }
+            in = inside;
+        }
+    }
+    if (near_out) *near_out = near_b;
+    return in;
+}
+
+// Colour-matrix recolour of one coefficient triple (Sec. 3.3), fixed rounding.
+__device__ __forceinline__ void recolor_triple(const float* M, float& r, float& g, float& b) {
+    float r2 = __fmaf_rn(M[2], b, __fmaf_rn(M[1], g, __fmul_rn(M[0], r)));
+    float g2 = __fmaf_rn(M[5], b, __fmaf_rn(M[4], g, __fmul_rn(M[3], r)));
+    float b2 = __fmaf_rn(M[8], b, __fmaf_rn(M[7], g, __fmul_rn(M[6], r)));
+    r = r2; g = g2; b = b2;
+}
+
+// --------------------------------------------------------------------------
+// Launchers (defined in the .cu files). Each returns the number of kernel
+// launches it issued.
+
+struct PrepOut {
+    float4* rec;          // [3*n]: (u', v', A, B), (C, sigma, ex, ey), (r, g, b, origin):
+                          // centre (u', v') relative to tile (tx0, ty0), origin = tx0 | ty0 << 16
+    uint32_t* count;      // [n] tiles covered (0 = culled)
+    uint2* rect;          // [n] (tx0 | tx1 << 16, ty0 | ty1 << 16)
+    uint32_t* zkey;       // [n] float bits of the view depth
+    uint32_t* block_sums; // [2 * blocks]: visible count, pair count
+    DevCounters* counters;
+};
+
+int launch_select(const recogs_scene& s, const DevCamera& cam, const DevRegion& reg,
+                  uint32_t* mask, uint8_t* near_out, cudaStream_t st);
+int launch_recolor(recogs_scene& s, const uint32_t* mask, const float M[9], const float dc_fix[3],
+                   cudaStream_t st);
+int launch_preprocess(const recogs_scene& s, const DevCamera& cam, const DevEdit& edit,
+                      const PrepOut& out, cudaStream_t st);
+
+// Exclusive scan of n <= 2^24 uint32 values in one block; total -> *total.
+int launch_scan_small(const uint32_t* in, uint32_t* out, int n, int stride_in, uint32_t* total,
+                      cudaStream_t st);
+int launch_compact(const uint32_t* count, const uint32_t* zkey, int n, const uint32_t* block_offsets,
+                   const DevCounters* counters, uint32_t* keys_out, uint32_t* vals_out,
+                   cudaStream_t st);
+
+struct SortBuffers {
+    uint32_t *keys[2], *vals[2];
+    uint32_t* table;       // [kRadix * max_blocks]
+    uint32_t* digit_totals;
+    int max_blocks;
+};
+// Stable LSD radix sort of n (key, value) pairs on bits [0, bits). Result in
+// buffer index returned (0 or 1).
+int radix_sort_pairs(SortBuffers& b, int n, int bits, cudaStream_t st, int* launches);
+
+int launch_pair_block_sums(const uint32_t* sorted_ids, const uint32_t* count, int v, uint32_t* sums,
+                           cudaStream_t st);
+int launch_emit(const uint32_t* sorted_ids, const uint32_t* count, const uint2* rect, int v,
+                const uint32_t* block_offsets, int tiles_x, uint32_t* tile_keys, uint32_t* vals,
+                cudaStream_t st);
+int launch_ranges(const uint32_t* sorted_tiles, int p, uint2* ranges, cudaStream_t st);
+int launch_blend(const uint2* ranges, const uint32_t* ids, const float4* rec, const DevCamera& cam,
+                 const float bg[3], float* image, float* final_T, DevCounters* counters,
+                 cudaStream_t st);
+
+}  // namespace recogs
