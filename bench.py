@@ -1,0 +1,476 @@
+#!/usr/bin/env python3
+"""Benchmark: recolour + render frames/s of a 3M-Gaussian SH3 scene at 1080p.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--sh-dtype f32|f16|bf16] [--no-cpu-baseline] [--no-e2e]
+
+One step is one frame through the C ABI (recogs_render with the fused edit):
+select the Gaussians whose centres fall in a 12-vertex polygon covering 15%
+of the view, recolour their SH coefficients with a 90-degree hue rotation,
+project, bin, sort and blend into a 1920x1080 HWC float32 image. Inputs are
+seeded synthetic scenes (the paper's MipNeRF360 captures are not available).
+The scene (708 MB of float32 attributes) is larger than the 126 MB L2, so no
+explicit flush is needed between frames.
+
+With N > 1 (torchrun, one process per GPU) every rank renders its own replica
+of the workload; the path has no cross-GPU exchange. ``--impl reference``
+times the FP64 CPU oracle on the same workload instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "recolor+render frames/s at 1080p, 3M SH3 splats; % HBM roofline; vs plain FP32"
+N_SPLATS = 3_000_000
+SEED = 2
+WIDTH, HEIGHT = 1920, 1080
+PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
+
+
+def workload_config(sh_dtype):
+    return {
+        "workload": (f"recolor+render, {N_SPLATS // 1_000_000}M SH3 Gaussians ({sh_dtype} SH), "
+                     f"{WIDTH}x{HEIGHT}, 12-gon selection covering 15%, 90 deg hue rotation"),
+        "n_gaussians": N_SPLATS, "width": WIDTH, "height": HEIGHT, "seed": SEED,
+        "sh_dtype": sh_dtype,
+        "generator": "40 spheres + 20 planes in a 10^3 box, camera at distance 14, fovy 60",
+        "l2": "inputs larger than L2 (708 MB scene vs 126 MB L2); no flush",
+        "parallelism": "replicas (one independent frame stream per GPU)",
+    }
+
+
+def make_workload():
+    from paper_2511_18441_b300 import scenegen as sg
+    return sg.paper_scale_workload(n=N_SPLATS, seed=SEED, width=WIDTH, height=HEIGHT)
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = os.environ.get("RECOGS_DIST_BACKEND")
+        if backend is None:
+            import torch
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(steps: int, world: int, max_ms: float) -> float:
+    """Whole-job frames/s: frames of all ranks over the slowest rank's time."""
+    return steps * world / (max_ms / 1000.0)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}", "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        if self.gpu_id is not None:
+            cmd += ["-i", str(self.gpu_id)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark_begin(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=5)
+        rows = []
+        for ts, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            rows.append((ts, parts))
+        if not rows:
+            return None
+        inside = [r for ts, r in rows if self.t0 is not None and self.t0 - 0.15 <= ts <= self.t1 + 0.15]
+        use = inside or [r for _, r in rows]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+
+        sm = [num(r[1]) for r in use]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in use for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(num(r[2]) for r in use),
+                "reasons": reasons, "samples": len(use),
+                "power_w_max": max(num(r[3]) for r in use)}
+
+
+def gpu_id_for_smi(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return local_rank
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def kernel_source_sha(kernel_file):
+    with open(os.path.join(ROOT, "paper_2511_18441_b300", "csrc", kernel_file), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic(stage):
+    """DRAM bytes per launch from a committed ncu summary, or None if absent
+    or taken on a different version of the kernel's source."""
+    files = {"blend": "blend.cu", "preprocess": "preprocess.cu"}
+    if stage not in files:
+        return None
+    path = os.path.join(ROOT, "profiles", f"traffic_{stage}_3m_1080p.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+    if kv.get("source_sha256_16") != kernel_source_sha(files[stage]):
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def algorithmic_bytes(stage, stats, n, sh_bytes):
+    """Bytes a launch of `stage` must move at minimum (per-unit figures of the
+    design notes x units per launch)."""
+    W, H = WIDTH, HEIGHT
+    tiles = stats["n_tiles"]
+    if stage == "blend":
+        # per consumed pair: 4 B index + 36 B record; image 12 B/pixel; 8 B range per tile
+        return stats["n_pairs_read"] * 40 + 12 * W * H + 8 * tiles
+    if stage == "preprocess":
+        # per Gaussian: 44 B geometry + 48 SH coefficients read, 44 B record written
+        return n * (44 + 48 * sh_bytes + 44)
+    return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline leg)
+
+def oracle_frame_sample(w, tile_stride, threads=None):
+    """One FP64 oracle frame on a bounded sample: the full per-Gaussian pass,
+    depth order and tile lists, then every tile_stride-th tile blended. Returns
+    (estimated seconds per full frame, seconds spent)."""
+    import oracle
+    t0 = time.perf_counter()
+    sp = oracle.preprocess(w.scene, w.camera, w.edit, threads=threads)
+    order = oracle.depth_order(sp)
+    tx, ty = (WIDTH + 15) // 16, (HEIGHT + 15) // 16
+    off, ids = oracle.tile_lists(sp, order, tx, ty)
+    t1 = time.perf_counter()
+    tiles = np.arange(0, tx * ty, tile_stride, dtype=np.int32)
+    oracle.render_tiles(sp, off, ids, tiles, threads=threads)
+    t2 = time.perf_counter()
+    frame = (t1 - t0) + (t2 - t1) * (tx * ty) / len(tiles)
+    return frame, t2 - t0
+
+
+def cpu_baseline(w, budget_s=20.0):
+    cores = os.cpu_count() or 1
+    frames = []
+    spent = 0.0
+    stride = 4
+    while spent < budget_s * 0.5 or not frames:
+        f, s = oracle_frame_sample(w, stride, threads=cores)
+        frames.append(f)
+        spent += s
+        if spent > budget_s:
+            break
+    est = statistics.median(frames)
+    return {"value": 1.0 / est, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": (f"{len(frames)} oracle frame(s): full per-Gaussian pass, depth order and "
+                       f"tile lists over all {N_SPLATS} Gaussians, every {stride}th of "
+                       f"{((WIDTH + 15) // 16) * ((HEIGHT + 15) // 16)} tiles blended, scaled "
+                       f"to a full frame; {spent:.1f} s of CPU wall time")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = make_workload()
+    cores = os.cpu_count() or 1
+    stride = 16
+    for _ in range(args.warmup):
+        oracle_frame_sample(w, stride, threads=cores)
+    frames = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, _ = oracle_frame_sample(w, stride, threads=cores)
+        frames.append(f)
+    spent = time.perf_counter() - t0
+    total = sum(frames)
+    value = args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config("f32"),
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                         "sample": (f"per step: full per-Gaussian pass, depth order and tile "
+                                    f"lists over all {N_SPLATS} Gaussians, every {stride}th tile "
+                                    f"blended, scaled to a full frame ({spent:.1f} s total)")},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2511_18441_b300 import binding, build
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the library has no CPU path)")
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = make_workload()
+    ds = binding.DeviceScene.from_numpy(w.scene, dev, args.sh_dtype)
+    ctx = binding.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    img = torch.empty((HEIGHT, WIDTH, 3), dtype=torch.float32, device=dev)
+
+    def frame():
+        ctx.render(ds, w.camera, w.edit, image_out=img, stream=stream)
+
+    sampler = ClockSampler(gpu_id_for_smi(local))
+    sampler.start()
+    for _ in range(args.warmup):
+        frame()
+    torch.cuda.synchronize(dev)
+    _, stats = ctx.render(ds, w.camera, w.edit, image_out=img, stats=True, stream=stream)
+
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    ctx.set_timing(True)
+    ctx.stage_times(reset=True)
+    l0 = ctx.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sampler.mark_begin()
+    e0.record(stream)
+    for _ in range(args.steps):
+        frame()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    sampler.mark_end()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    launches = ctx.launch_count() - l0
+    stages = ctx.stage_times(reset=True)
+    ctx.set_timing(False)
+    clocks = sampler.stop()
+    max_ms = max_over_ranks(ms, world, dev)
+    value = aggregate_value(args.steps, world, max_ms)
+
+    # roofline of the dominant kernel (stage events are recorded on `stream`)
+    peaks, peaks_src = load_peaks()
+    per_stage = {k: v for k, v in stages.items() if v[1] > 0 and k not in ("h2d", "d2h")}
+    dom = max(per_stage, key=lambda k: per_stage[k][0])
+    dom_ms = per_stage[dom][0] / max(per_stage[dom][1], 1)
+    sh_bytes = 4 if args.sh_dtype == "f32" else 2
+    alg = algorithmic_bytes(dom, stats, N_SPLATS, sh_bytes)
+    roof = None
+    if alg is not None:
+        achieved = alg / (dom_ms / 1000.0) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "peak_source": f"{peaks_src} copy bandwidth", "traffic": profiled_traffic(dom),
+                "algorithmic_bytes": alg, "ms_per_launch": dom_ms}
+    stage_ms = {k: round(v[0] / args.steps, 4) for k, v in per_stage.items()}
+
+    # other stages' HBM fractions for context
+    other = {}
+    for k in ("preprocess", "blend"):
+        if k in per_stage and k != dom:
+            a = algorithmic_bytes(k, stats, N_SPLATS, sh_bytes)
+            t = per_stage[k][0] / max(per_stage[k][1], 1)
+            other[k] = {"achieved_gbs": a / (t / 1000.0) / 1e9,
+                        "frac": a / (t / 1000.0) / 1e9 / peaks["hbm_gbs"], "ms_per_launch": t}
+
+    # end to end through the public API: pinned host scene in, host image out
+    e2e = None
+    if not args.no_e2e:
+        hs = binding.DeviceScene.from_numpy(w.scene, "cpu", args.sh_dtype, pin=True)
+        himg = torch.empty((HEIGHT, WIDTH, 3), dtype=torch.float32).pin_memory()
+        n_e2e = max(3, min(args.steps, 20))
+        ctx.render_host(hs, w.camera, w.edit, image_out=himg, stream=stream)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            ctx.render_host(hs, w.camera, w.edit, image_out=himg, stream=stream)
+        el = time.perf_counter() - t0
+        el = max_over_ranks(el, world, dev)
+        h2d = sum(t.numel() * t.element_size() for t in (hs.xyz, hs.log_scale, hs.quat,
+                                                          hs.opacity_logit, hs.sh))
+        e2e = {"value": n_e2e * world / el, "unit": "frames/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": himg.numel() * 4, "steps": n_e2e,
+               "api": "recogs_render_host (pinned host buffers)"}
+
+    # the same frame with 16-bit SH storage, for context
+    variants = {}
+    if args.sh_dtype == "f32" and not args.no_variants:
+        for kind in ("bf16", "f16"):
+            dv = binding.DeviceScene.from_numpy(w.scene, dev, kind)
+            for _ in range(3):
+                ctx.render(dv, w.camera, w.edit, image_out=img, stream=stream)
+            torch.cuda.synchronize(dev)
+            k = max(10, args.steps // 2)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(k):
+                ctx.render(dv, w.camera, w.edit, image_out=img, stream=stream)
+            a1.record(stream)
+            torch.cuda.synchronize(dev)
+            variants[kind] = {"frames_per_s": k / (a0.elapsed_time(a1) / 1000.0),
+                              "ms_per_step": a0.elapsed_time(a1) / k}
+            del dv
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.sh_dtype if args.sh_dtype != "f32" else "f32",
+            "data": "synthetic (seeded generator; MipNeRF360 captures unavailable)",
+            "config": workload_config(args.sh_dtype),
+            "gaussians_per_s": value * N_SPLATS,
+            "frame_stats": stats,
+            "stage_ms_per_step": stage_ms,
+            "roofline": roof,
+            "roofline_other": other,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--sh-dtype", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_init()
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
