@@ -181,6 +181,47 @@ RECOGS_API recogs_status recogs_render_host(recogs_ctx* ctx, const recogs_scene*
                                  recogs_render_stats* stats, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Rendering without allocation
+ */
+
+#define RECOGS_NOALLOC_MAX_GAUSSIANS 65536
+#define RECOGS_NOALLOC_MAX_PAIRS 524288
+#define RECOGS_NOALLOC_MAX_TILES 4096
+
+/* The frame of recogs_render for small scenes, for callers that cannot
+ * allocate device memory while rendering: a real-time or interrupt-like host
+ * thread that must not block inside the CUDA allocator, a host application
+ * or framework that owns all device memory and forbids other allocators, or
+ * code that cannot create and keep a recogs_ctx. The paper has no
+ * counterpart to this entry point; it is a packaging of the same kernels.
+ *
+ * It takes no context and calls no cudaMalloc, cudaFree, cudaMallocHost or
+ * allocating library routine. Every intermediate buffer lives in one
+ * file-scope device array of about 13 MiB inside librecogs.so, which every
+ * GPU that loads the library holds until the process exits. The first call
+ * on each device looks up that array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.
+ *
+ * Limits: at most RECOGS_NOALLOC_MAX_GAUSSIANS Gaussians, at most
+ * RECOGS_NOALLOC_MAX_TILES 16x16 tiles (e.g. 1024x1024 px) and at most
+ * RECOGS_NOALLOC_MAX_PAIRS (tile, Gaussian) pairs. Larger inputs return
+ * RECOGS_ECAPACITY with a message and render nothing (a pair overflow is only
+ * known after the per-Gaussian pass; the image is then left unwritten).
+ *
+ * Arguments and results are those of recogs_render (device scene, device
+ * image_hwc_out and optional final_T_out, host bg and edit); error_out
+ * (host, may be NULL) receives a message of at most error_len bytes. The
+ * call reads two counts back to the host (a stream synchronisation).
+ * All calls share the one array: calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Each call clears the parts that must start at zero. */
+RECOGS_API recogs_status recogs_render_noalloc(const recogs_scene* scene,
+                                               const recogs_camera* camera,
+                                               const recogs_edit* edit, const float* bg,
+                                               float* image_hwc_out, float* final_T_out,
+                                               char* error_out, size_t error_len, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Introspection (tests and measurement)
  */
 

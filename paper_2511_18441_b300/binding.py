@@ -72,6 +72,9 @@ SIGNATURES = {
     "recogs_render_host": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.POINTER(CCamera),
                                      C.POINTER(CEdit), C.POINTER(C.c_float), C.c_void_p,
                                      C.c_void_p, C.POINTER(CStats), C.c_void_p]),
+    "recogs_render_noalloc": (C.c_int, [C.POINTER(CScene), C.POINTER(CCamera), C.POINTER(CEdit),
+                                        C.POINTER(C.c_float), C.c_void_p, C.c_void_p, C.c_char_p,
+                                        C.c_size_t, C.c_void_p]),
     "recogs_tile_lists": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "recogs_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "recogs_stage_times": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
@@ -324,3 +327,32 @@ class Context:
 
 def mask_words(n: int) -> int:
     return (n + 31) // 32
+
+
+NOALLOC_MAX_GAUSSIANS = 65536
+NOALLOC_MAX_PAIRS = 524288
+NOALLOC_MAX_TILES = 4096
+
+
+def render_noalloc(scene: DeviceScene, cam, edit=None, bg=None, image_out=None, T_out=None,
+                   stream=None):
+    """recogs_render_noalloc: render a small scene without any allocation in
+    the library (no context; scratch in a fixed device array). Returns the
+    image; raises RecogsError with the library's message on failure."""
+    import torch
+    L = load()
+    H, W = int(cam.height), int(cam.width)
+    if image_out is None:
+        image_out = torch.empty((H, W, 3), dtype=torch.float32, device=scene.xyz.device)
+    cs = scene.struct()
+    cc = camera_struct(cam)
+    e, keep = edit_struct(edit)
+    bgv = (C.c_float * 3)(*(np.asarray(bg if bg is not None else (0, 0, 0), np.float32)))
+    msg = C.create_string_buffer(512)
+    s = L.recogs_render_noalloc(C.byref(cs), C.byref(cc), C.byref(e) if e is not None else None,
+                                bgv, image_out.data_ptr(),
+                                T_out.data_ptr() if T_out is not None else None, msg, 512,
+                                _stream_ptr(stream))
+    if s != OK:
+        raise RecogsError(s, msg.value.decode())
+    return image_out

@@ -1,0 +1,274 @@
+// recogs_render_noalloc: the frame of recogs_render for bounded sizes, with
+// every intermediate buffer carved from one file-scope device array instead
+// of context-owned cudaMalloc memory. For callers that must not allocate
+// device memory at call time (a real-time thread that cannot block in the
+// allocator, a host framework that owns all device memory and forbids other
+// allocators, code that runs without a library context). The kernels are the
+// same ones recogs_render launches.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "recogs_internal.cuh"
+
+using namespace recogs;
+
+namespace {
+
+constexpr size_t kMaxN = RECOGS_NOALLOC_MAX_GAUSSIANS;
+constexpr size_t kMaxP = RECOGS_NOALLOC_MAX_PAIRS;
+constexpr size_t kMaxTiles = RECOGS_NOALLOC_MAX_TILES;
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t cdiv(size_t a, size_t b) { return (a + b - 1) / b; }
+
+// Byte offsets of each buffer inside the scratch array.
+constexpr size_t kPrepBlocks = cdiv(kMaxN, kPrepThreads);
+constexpr size_t kSortBlocks = cdiv(kMaxN > kMaxP ? kMaxN : kMaxP, kSortTile);
+constexpr size_t kVisBlocks = cdiv(kMaxN, kSortTile);
+constexpr size_t oRec = 0;
+constexpr size_t oCount = align256(oRec + 3 * kMaxN * sizeof(float4));
+constexpr size_t oZkey = align256(oCount + kMaxN * 4);
+constexpr size_t oRect = align256(oZkey + kMaxN * 4);
+constexpr size_t oBlockSums = align256(oRect + kMaxN * sizeof(uint2));
+constexpr size_t oBlockOffsets = align256(oBlockSums + 2 * kPrepBlocks * 4);
+constexpr size_t oCounters = align256(oBlockOffsets + kPrepBlocks * 4);
+constexpr size_t oDkeys0 = align256(oCounters + sizeof(DevCounters));
+constexpr size_t oDkeys1 = align256(oDkeys0 + kMaxN * 4);
+constexpr size_t oDvals0 = align256(oDkeys1 + kMaxN * 4);
+constexpr size_t oDvals1 = align256(oDvals0 + kMaxN * 4);
+constexpr size_t oTkeys0 = align256(oDvals1 + kMaxN * 4);
+constexpr size_t oTkeys1 = align256(oTkeys0 + kMaxP * 4);
+constexpr size_t oTvals0 = align256(oTkeys1 + kMaxP * 4);
+constexpr size_t oTvals1 = align256(oTvals0 + kMaxP * 4);
+constexpr size_t oTable = align256(oTvals1 + kMaxP * 4);
+constexpr size_t oDigits = align256(oTable + (size_t)kRadix * kSortBlocks * 4);
+constexpr size_t oPairSums = align256(oDigits + (size_t)kRadix * 4);
+constexpr size_t oPairOffsets = align256(oPairSums + kVisBlocks * 4);
+constexpr size_t oRanges = align256(oPairOffsets + kVisBlocks * 4);
+constexpr size_t kScratchBytes = align256(oRanges + kMaxTiles * sizeof(uint2));
+static_assert(kScratchBytes < (16u << 20), "no-alloc scratch should stay under 16 MiB");
+
+// The scratch itself: one copy on every device that loads the library, kept
+// until the process exits. Host code must not use this name as a pointer:
+// its device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+unsigned char* g_addr[kMaxDevices] = {nullptr};
+
+recogs_status report(char* err, size_t len, recogs_status s, const char* fmt, ...) {
+    if (err && len > 0) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(err, len, fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+// Device address of g_scratch on the current device; looked up once per
+// device (the first call on each device does this set-up).
+recogs_status scratch_address(unsigned char** out, char* err, size_t len) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return report(err, len, RECOGS_EDEVICE, "no current CUDA device (%s)",
+                      e != cudaSuccess ? cudaGetErrorString(e) : "index out of range");
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!g_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess || !p)
+            return report(err, len, RECOGS_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s",
+                          cudaGetErrorString(e));
+        g_addr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_addr[dev];
+    return RECOGS_OK;
+}
+
+bool finite3(const float* v, int k) {
+    for (int i = 0; i < k; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+bool camera_ok(const recogs_camera* c) {
+    return c && c->width >= 1 && c->height >= 1 && c->width <= 16384 && c->height <= 16384 &&
+           c->fx > 0.f && c->fy > 0.f && std::isfinite(c->fx) && std::isfinite(c->fy) &&
+           std::isfinite(c->cx) && std::isfinite(c->cy) && c->z_near >= 0.f &&
+           std::isfinite(c->z_near) &&
+           finite3(c->world_to_view, 12) && finite3(c->cam_pos, 3);
+}
+
+DevCamera to_dev(const recogs_camera& c) {
+    DevCamera d;
+    d.width = c.width;
+    d.height = c.height;
+    d.tiles_x = (c.width + kTile - 1) / kTile;
+    d.tiles_y = (c.height + kTile - 1) / kTile;
+    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) d.W[r * 3 + k] = c.world_to_view[r * 4 + k];
+        d.t[r] = c.world_to_view[r * 4 + 3];
+        d.pos[r] = c.cam_pos[r];
+    }
+    d.z_near = c.z_near;
+    d.limx = (float)(1.3 * c.width / (2.0 * c.fx));
+    d.limy = (float)(1.3 * c.height / (2.0 * c.fy));
+    return d;
+}
+
+}  // namespace
+
+extern "C" RECOGS_API recogs_status recogs_render_noalloc(
+    const recogs_scene* scene, const recogs_camera* camera, const recogs_edit* edit,
+    const float* bg, float* image_hwc_out, float* final_T_out, char* error_out, size_t error_len,
+    void* stream) {
+    char* err = error_out;
+    const size_t el = error_len;
+    if (err && el) err[0] = '\0';
+    if (!scene || !camera_ok(camera) || !image_hwc_out)
+        return report(err, el, RECOGS_EINVAL, "scene, camera or image_hwc_out invalid");
+    if (scene->n < 0 || (scene->sh_dtype != RECOGS_F32 && scene->sh_dtype != RECOGS_F16 &&
+                         scene->sh_dtype != RECOGS_BF16))
+        return report(err, el, RECOGS_EINVAL, "scene.n or scene.sh_dtype invalid");
+    if (scene->n > 0 && (!scene->xyz || !scene->log_scale || !scene->quat ||
+                         !scene->opacity_logit || !scene->sh))
+        return report(err, el, RECOGS_EINVAL, "a scene array is NULL");
+    const int tiles = ((camera->width + kTile - 1) / kTile) * ((camera->height + kTile - 1) / kTile);
+    if ((size_t)scene->n > kMaxN)
+        return report(err, el, RECOGS_ECAPACITY,
+                      "%lld Gaussians exceed the no-alloc limit of %d (use recogs_render)",
+                      (long long)scene->n, RECOGS_NOALLOC_MAX_GAUSSIANS);
+    if ((size_t)tiles > kMaxTiles)
+        return report(err, el, RECOGS_ECAPACITY,
+                      "%d tiles (%dx%d px) exceed the no-alloc limit of %d tiles", tiles,
+                      camera->width, camera->height, RECOGS_NOALLOC_MAX_TILES);
+    float bgv[3] = {0.f, 0.f, 0.f};
+    if (bg) {
+        if (!finite3(bg, 3)) return report(err, el, RECOGS_EINVAL, "bg not finite");
+        for (int k = 0; k < 3; ++k) bgv[k] = bg[k];
+    }
+    DevEdit de;
+    memset(&de, 0, sizeof(de));
+    if (edit) {
+        const recogs_camera* sc = edit->select_camera ? edit->select_camera : camera;
+        if (!camera_ok(sc)) return report(err, el, RECOGS_EINVAL, "edit.select_camera invalid");
+        if (!finite3(edit->tint.color_matrix, 9))
+            return report(err, el, RECOGS_EINVAL, "colour matrix not finite");
+        const recogs_region& r = edit->region;
+        if (!r.xy) return report(err, el, RECOGS_EINVAL, "region.xy is NULL");
+        de.region.kind = r.kind;
+        de.region.eps = 1e-6f * (float)(sc->width > sc->height ? sc->width : sc->height);
+        if (r.kind == RECOGS_REGION_BOX) {
+            if (!finite3(r.xy, 4)) return report(err, el, RECOGS_EINVAL, "box not finite");
+            for (int k = 0; k < 4; ++k) de.region.xy[k] = r.xy[k];
+            de.region.n = 2;
+        } else if (r.kind == RECOGS_REGION_POLYGON) {
+            if (r.n_vertices < 3 || r.n_vertices > RECOGS_MAX_POLYGON || !finite3(r.xy, 2 * r.n_vertices))
+                return report(err, el, RECOGS_EINVAL, "polygon invalid");
+            for (int k = 0; k < 2 * r.n_vertices; ++k) de.region.xy[k] = r.xy[k];
+            de.region.n = r.n_vertices;
+        } else {
+            return report(err, el, RECOGS_EINVAL, "unknown region kind %d", r.kind);
+        }
+        de.enabled = 1;
+        de.cam = to_dev(*sc);
+        for (int k = 0; k < 9; ++k) de.M[k] = edit->tint.color_matrix[k];
+        for (int c = 0; c < 3; ++c) {
+            const double row = (double)de.M[3 * c] + de.M[3 * c + 1] + de.M[3 * c + 2];
+            de.dc_fix[c] = (float)((row - 1.0) * 1.7724538509055159);  // (row - 1) 0.5 / Y_0
+        }
+    }
+
+    unsigned char* base = nullptr;
+    recogs_status s = scratch_address(&base, err, el);
+    if (s != RECOGS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)scene->n;
+    const DevCamera dc = to_dev(*camera);
+    auto U32 = [&](size_t o) { return reinterpret_cast<uint32_t*>(base + o); };
+    DevCounters* dctr = reinterpret_cast<DevCounters*>(base + oCounters);
+    uint2* ranges = reinterpret_cast<uint2*>(base + oRanges);
+    float4* rec = reinterpret_cast<float4*>(base + oRec);
+
+#define NA_CK(expr)                                                                          \
+    do {                                                                                     \
+        cudaError_t _e = (expr);                                                             \
+        if (_e != cudaSuccess)                                                               \
+            return report(err, el, RECOGS_ECUDA, "%s: %s", #expr, cudaGetErrorString(_e)); \
+    } while (0)
+
+    // the array keeps the previous call's contents: zero what must start at zero
+    NA_CK(cudaMemsetAsync(dctr, 0, sizeof(DevCounters), st));
+    NA_CK(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)tiles, st));
+
+    uint32_t V = 0, P = 0;
+    DevCounters hc;
+    memset(&hc, 0, sizeof(hc));
+    const int nb = (n + kPrepThreads - 1) / kPrepThreads;
+    if (n > 0) {
+        PrepOut po;
+        po.rec = rec;
+        po.count = U32(oCount);
+        po.rect = reinterpret_cast<uint2*>(base + oRect);
+        po.zkey = U32(oZkey);
+        po.block_sums = U32(oBlockSums);
+        po.counters = dctr;
+        launch_preprocess(*scene, dc, de, po, st);
+        launch_scan_small(po.block_sums, U32(oBlockOffsets), nb, 1, &dctr->n_visible, st);
+        launch_scan_small(po.block_sums + nb, nullptr, nb, 1, &dctr->n_pairs, st);
+        NA_CK(cudaGetLastError());
+        NA_CK(cudaMemcpyAsync(&hc, dctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+        NA_CK(cudaStreamSynchronize(st));
+        V = hc.n_visible;
+        P = hc.n_pairs;
+        if ((size_t)P > kMaxP)
+            return report(err, el, RECOGS_ECAPACITY,
+                          "%u (tile, Gaussian) pairs exceed the no-alloc limit of %d; the image "
+                          "was not written (use recogs_render)",
+                          P, RECOGS_NOALLOC_MAX_PAIRS);
+    }
+    const uint32_t* ids = U32(oTvals0);
+    if (V > 0) {
+        launch_compact(U32(oCount), U32(oZkey), n, U32(oBlockOffsets), dctr, U32(oDkeys0),
+                       U32(oDvals0), st);
+        SortBuffers sb;
+        sb.keys[0] = U32(oDkeys0);
+        sb.keys[1] = U32(oDkeys1);
+        sb.vals[0] = U32(oDvals0);
+        sb.vals[1] = U32(oDvals1);
+        sb.table = U32(oTable);
+        sb.digit_totals = U32(oDigits);
+        sb.max_blocks = (int)kSortBlocks;
+        const uint32_t span = hc.zmax - ~hc.zmin_inv;
+        const int dbits = span == 0 ? 0 : 32 - __builtin_clz(span);
+        int l = 0;
+        const int dcur = radix_sort_pairs(sb, (int)V, dbits, st, &l);
+        const uint32_t* sorted = sb.vals[dcur];
+        const int vb = ((int)V + kSortTile - 1) / kSortTile;
+        launch_pair_block_sums(sorted, U32(oCount), (int)V, U32(oPairSums), st);
+        launch_scan_small(U32(oPairSums), U32(oPairOffsets), vb, 1, nullptr, st);
+        launch_emit(sorted, U32(oCount), reinterpret_cast<const uint2*>(base + oRect), (int)V,
+                    U32(oPairOffsets), dc.tiles_x, U32(oTkeys0), U32(oTvals0), st);
+        SortBuffers tb = sb;
+        tb.keys[0] = U32(oTkeys0);
+        tb.keys[1] = U32(oTkeys1);
+        tb.vals[0] = U32(oTvals0);
+        tb.vals[1] = U32(oTvals1);
+        const int tbits = tiles <= 1 ? 0 : 32 - __builtin_clz((uint32_t)(tiles - 1));
+        const int tcur = radix_sort_pairs(tb, (int)P, tbits, st, &l);
+        launch_ranges(tb.keys[tcur], (int)P, ranges, st);
+        ids = tb.vals[tcur];
+        NA_CK(cudaGetLastError());
+    }
+    launch_blend(ranges, ids, rec, dc, bgv, image_hwc_out, final_T_out, dctr, st);
+    NA_CK(cudaGetLastError());
+#undef NA_CK
+    return RECOGS_OK;
+}
