@@ -35,7 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "recolor+render frames/s at 1080p, 3M SH3 splats; % HBM roofline; vs plain FP32"
-N_SPLATS = 3_000_000
+N_SPLATS = 3_000_000  # --gaussians overrides it for small profiling cases
 SEED = 2
 WIDTH, HEIGHT = 1920, 1080
 PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
@@ -43,7 +43,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustain
 
 def workload_config(sh_dtype):
     return {
-        "workload": (f"recolor+render, {N_SPLATS // 1_000_000}M SH3 Gaussians ({sh_dtype} SH), "
+        "workload": (f"recolor+render, {N_SPLATS / 1e6:g}M SH3 Gaussians ({sh_dtype} SH), "
                      f"{WIDTH}x{HEIGHT}, 12-gon selection covering 15%, 90 deg hue rotation"),
         "n_gaussians": N_SPLATS, "width": WIDTH, "height": HEIGHT, "seed": SEED,
         "sh_dtype": sh_dtype,
@@ -457,7 +457,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--gaussians", type=int, default=None,
+                    help="scene size for small profiling cases (default 3,000,000)")
     args = ap.parse_args(argv)
+    if args.gaussians is not None:
+        global N_SPLATS
+        N_SPLATS = args.gaussians
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local = dist_init()

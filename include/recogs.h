@@ -247,6 +247,14 @@ RECOGS_API recogs_status recogs_stage_times(recogs_ctx* ctx, int32_t max_stages,
 /* Total kernel launches issued by ctx since creation. */
 RECOGS_API int64_t recogs_launch_count(const recogs_ctx* ctx);
 
+/* How recogs_render orders each tile's list by (depth, index) (the order of
+ * Eq. 3): 0 = automatic (per-tile shared-memory sort when the most crowded
+ * tile has at most 16384 pairs, else the global path), 1 = per-tile sort
+ * (falls back to the global path above 16384 pairs), 2 = global path (radix
+ * sort by depth, pair expansion in depth order, stable radix sort by tile).
+ * Both give identical lists. */
+RECOGS_API recogs_status recogs_set_sort_path(recogs_ctx* ctx, int path);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,7 @@ SIGNATURES = {
                                      C.POINTER(C.c_char_p), C.POINTER(C.c_double),
                                      C.POINTER(C.c_int64), C.c_int]),
     "recogs_launch_count": (C.c_int64, [C.c_void_p]),
+    "recogs_set_sort_path": (C.c_int, [C.c_void_p, C.c_int]),
 }
 
 _lib = None
@@ -323,6 +324,10 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self._L.recogs_launch_count(self._h))
+
+    def set_sort_path(self, path: int):
+        """0 automatic, 1 per-tile shared-memory sort, 2 global radix path."""
+        self._check(self._L.recogs_set_sort_path(self._h, int(path)))
 
 
 def mask_words(n: int) -> int:

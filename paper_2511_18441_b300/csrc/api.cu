@@ -24,11 +24,12 @@ namespace {
 
 enum Stage {
     ST_PREPROCESS, ST_SCAN, ST_COMPACT, ST_SORT_DEPTH, ST_PAIR_OFFSETS, ST_EMIT, ST_SORT_TILE,
-    ST_RANGES, ST_BLEND, ST_SELECT, ST_RECOLOR, ST_H2D, ST_D2H, ST_COUNT
+    ST_RANGES, ST_BLEND, ST_SELECT, ST_RECOLOR, ST_H2D, ST_D2H, ST_TILE_ORDER, ST_SCATTER,
+    ST_TILE_SORT, ST_COUNT
 };
 const char* const kStageNames[ST_COUNT] = {
     "preprocess", "scan", "compact", "sort_depth", "pair_offsets", "emit", "sort_tile",
-    "ranges", "blend", "select", "recolor", "h2d", "d2h"};
+    "ranges", "blend", "select", "recolor", "h2d", "d2h", "tile_order", "scatter", "tile_sort"};
 
 struct DevBuf {
     void* p = nullptr;
@@ -50,8 +51,10 @@ struct recogs_ctx {
     std::string err;
     // scratch
     DevBuf rec, count, rect, zkey, block_sums, block_offsets, counters;
-    DevBuf dkeys[2], dvals[2], table, digit_totals, pair_sums, pair_offsets;
-    DevBuf tkeys[2], tvals[2], ranges;
+    DevBuf dkeys[2], dvals[2], sort_scratch, pair_sums, pair_offsets;
+    bool counters_ready = false;
+    DevBuf tkeys[2], tvals[2], ranges, order, tile_count, cursor, tile_totals, pair_keys;
+    int sort_path = 0;   // 0 auto, 1 per-tile shared-memory sort, 2 global radix sort
     // host-memory render staging
     DevBuf hs_xyz, hs_ls, hs_q, hs_op, hs_sh, hs_img, hs_T;
     DevCounters* h_counters = nullptr;   // pinned
@@ -298,10 +301,20 @@ recogs_status render_device(recogs_ctx* ctx, const recogs_scene& s, const recogs
     const int nb = (n + kPrepThreads - 1) / kPrepThreads;
     CKS(ensure(ctx, ctx->counters, sizeof(DevCounters)));
     CKS(ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)tiles));
+    CKS(ensure(ctx, ctx->order, sizeof(uint32_t) * (size_t)tiles));
+    CKS(ensure(ctx, ctx->tile_count, sizeof(uint32_t) * kTileParts * (size_t)tiles));
+    CKS(ensure(ctx, ctx->cursor, sizeof(uint32_t) * kTileParts * (size_t)tiles));
+    CKS(ensure(ctx, ctx->tile_totals, sizeof(uint32_t) * (size_t)tiles));
     DevCounters* dctr = P<DevCounters>(ctx->counters);
-    CK(cudaMemsetAsync(dctr, 0, sizeof(DevCounters), st));
+    if (!ctx->counters_ready) {
+        CK(cudaMemsetAsync(dctr, 0, sizeof(DevCounters), st));
+        ctx->counters_ready = true;
+    }
+    CK(cudaMemsetAsync(dctr, 0, kCountersClearBytes, st));
+    CK(cudaMemsetAsync(ctx->tile_count.p, 0, sizeof(uint32_t) * kTileParts * (size_t)tiles, st));
 
-    uint32_t V = 0, Pn = 0, zmin = 0, zmax = 0;
+    // 1. per-Gaussian pass and per-tile pair counts
+    uint32_t V = 0, Pn = 0, zmin = 0, zmax = 0, max_tile = 0;
     if (n > 0) {
         CKS(ensure(ctx, ctx->rec, sizeof(float4) * 3 * (size_t)n));
         CKS(ensure(ctx, ctx->count, sizeof(uint32_t) * (size_t)n));
@@ -315,49 +328,84 @@ recogs_status render_device(recogs_ctx* ctx, const recogs_scene& s, const recogs
         po.rect = P<uint2>(ctx->rect);
         po.zkey = P<uint32_t>(ctx->zkey);
         po.block_sums = P<uint32_t>(ctx->block_sums);
+        po.tile_count = P<uint32_t>(ctx->tile_count);
+        po.parts = kTileParts;
         po.counters = dctr;
         stage_begin(ctx, st);
         int l = launch_preprocess(s, dc, de, po, st);
         stage_end(ctx, ST_PREPROCESS, l, st);
         CK(cudaGetLastError());
-
-        stage_begin(ctx, st);
-        l = launch_scan_small(po.block_sums, P<uint32_t>(ctx->block_offsets), nb, 1, &dctr->n_visible,
-                              st);
-        l += launch_scan_small(po.block_sums + nb, nullptr, nb, 1, &dctr->n_pairs, st);
-        stage_end(ctx, ST_SCAN, l, st);
-        CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(ctx->h_counters, dctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        V = ctx->h_counters->n_visible;
-        Pn = ctx->h_counters->n_pairs;
-        zmin = ~ctx->h_counters->zmin_inv;
-        zmax = ctx->h_counters->zmax;
-        if (Pn >= (1u << 31))
-            return fail(ctx, RECOGS_ECAPACITY, "%u (tile, Gaussian) pairs exceed 2^31", Pn);
     }
+    // 2. visible count (and offsets for the global path), tile ranges, pair total
+    stage_begin(ctx, st);
+    int l = 0;
+    if (n > 0)
+        l += launch_scan_small(P<uint32_t>(ctx->block_sums), P<uint32_t>(ctx->block_offsets), nb, 1,
+                               &dctr->n_visible, st);
+    l += launch_tile_totals(P<uint32_t>(ctx->tile_count), tiles, kTileParts,
+                            P<uint32_t>(ctx->cursor), P<uint32_t>(ctx->tile_totals), st);
+    l += launch_tile_scan(P<uint32_t>(ctx->tile_totals), tiles, P<uint2>(ctx->ranges), dctr, st);
+    stage_end(ctx, ST_SCAN, l, st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->h_counters, dctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    V = ctx->h_counters->n_visible;
+    Pn = ctx->h_counters->n_pairs;
+    zmin = ~ctx->h_counters->zmin_inv;
+    zmax = ctx->h_counters->zmax;
+    max_tile = ctx->h_counters->max_tile;
+    if (ctx->h_counters->error) {
+        CK(cudaMemsetAsync(&dctr->error, 0, sizeof(uint32_t), st));
+        return fail(ctx, RECOGS_ETIMEOUT,
+                    "a bounded device wait of an earlier sort gave up; that frame is invalid");
+    }
+    if (Pn >= (1u << 30))
+        return fail(ctx, RECOGS_ECAPACITY, "%u (tile, Gaussian) pairs exceed 2^30", Pn);
 
-    CK(cudaMemsetAsync(P<uint2>(ctx->ranges), 0, sizeof(uint2) * (size_t)tiles, st));
     const uint32_t* ids = nullptr;
-    if (V > 0) {
+    const bool smem_path = ctx->sort_path == 1 || (ctx->sort_path == 0 && max_tile <= kMaxSmemTile);
+    if (V > 0 && smem_path && (int)max_tile <= kMaxSmemTile) {
+        // 3a. scatter (depth, index) keys into the tile ranges, sort each tile in shared memory
+        CKS(ensure(ctx, ctx->pair_keys, sizeof(unsigned long long) * (size_t)Pn));
+        CKS(ensure(ctx, ctx->tvals[0], sizeof(uint32_t) * (size_t)Pn));
+        stage_begin(ctx, st);
+        l = launch_scatter(P<uint32_t>(ctx->count), P<uint2>(ctx->rect), P<uint32_t>(ctx->zkey), n,
+                           dc.tiles_x, P<uint2>(ctx->ranges), P<uint32_t>(ctx->cursor), kTileParts,
+                           P<unsigned long long>(ctx->pair_keys), st);
+        stage_end(ctx, ST_SCATTER, l, st);
+        stage_begin(ctx, st);
+        l = launch_tile_order(P<uint2>(ctx->ranges), tiles, P<uint32_t>(ctx->order), st);
+        stage_end(ctx, ST_TILE_ORDER, l, st);
+        stage_begin(ctx, st);
+        uint32_t classes[kSortClasses];
+        for (int c = 0; c < kSortClasses; ++c) classes[c] = ctx->h_counters->class_tiles[c];
+        const uint32_t span = zmax - zmin;
+        const int dbits = span == 0 ? 0 : 32 - __builtin_clz(span);
+        l = launch_tile_sort(P<uint2>(ctx->ranges), P<uint32_t>(ctx->order), classes,
+                             P<unsigned long long>(ctx->pair_keys), P<uint32_t>(ctx->tvals[0]),
+                             zmin, dbits, st);
+        stage_end(ctx, ST_TILE_SORT, l, st);
+        ids = P<uint32_t>(ctx->tvals[0]);
+        CK(cudaGetLastError());
+    } else if (V > 0) {
+        // 3b. global path: radix sort by depth, expand pairs in depth order,
+        // stable radix sort by tile (any tile size)
         const int max_items = (int)(V > Pn ? V : Pn);
-        const int max_blocks = (max_items + kSortTile - 1) / kSortTile;
         for (int k = 0; k < 2; ++k) {
             CKS(ensure(ctx, ctx->dkeys[k], sizeof(uint32_t) * (size_t)V));
             CKS(ensure(ctx, ctx->dvals[k], sizeof(uint32_t) * (size_t)V));
             CKS(ensure(ctx, ctx->tkeys[k], sizeof(uint32_t) * (size_t)Pn));
             CKS(ensure(ctx, ctx->tvals[k], sizeof(uint32_t) * (size_t)Pn));
         }
-        CKS(ensure(ctx, ctx->table, sizeof(uint32_t) * kRadix * (size_t)max_blocks));
-        CKS(ensure(ctx, ctx->digit_totals, sizeof(uint32_t) * kRadix));
-        const int vb = ((int)V + kSortTile - 1) / kSortTile;
+        CKS(ensure(ctx, ctx->sort_scratch, sizeof(uint32_t) * sort_scratch_words(max_items)));
+        const int vb = ((int)V + kEmitBlock - 1) / kEmitBlock;
         CKS(ensure(ctx, ctx->pair_sums, sizeof(uint32_t) * (size_t)vb));
         CKS(ensure(ctx, ctx->pair_offsets, sizeof(uint32_t) * (size_t)vb));
 
         stage_begin(ctx, st);
-        int l = launch_compact(P<uint32_t>(ctx->count), P<uint32_t>(ctx->zkey), n,
-                               P<uint32_t>(ctx->block_offsets), dctr, P<uint32_t>(ctx->dkeys[0]),
-                               P<uint32_t>(ctx->dvals[0]), st);
+        l = launch_compact(P<uint32_t>(ctx->count), P<uint32_t>(ctx->zkey), n,
+                           P<uint32_t>(ctx->block_offsets), dctr, P<uint32_t>(ctx->dkeys[0]),
+                           P<uint32_t>(ctx->dvals[0]), st);
         stage_end(ctx, ST_COMPACT, l, st);
 
         SortBuffers sb;
@@ -365,9 +413,8 @@ recogs_status render_device(recogs_ctx* ctx, const recogs_scene& s, const recogs
         sb.keys[1] = P<uint32_t>(ctx->dkeys[1]);
         sb.vals[0] = P<uint32_t>(ctx->dvals[0]);
         sb.vals[1] = P<uint32_t>(ctx->dvals[1]);
-        sb.table = P<uint32_t>(ctx->table);
-        sb.digit_totals = P<uint32_t>(ctx->digit_totals);
-        sb.max_blocks = max_blocks;
+        sb.scratch = P<uint32_t>(ctx->sort_scratch);
+        sb.error = &dctr->error;
         const uint32_t span = zmax - zmin;
         const int dbits = span == 0 ? 0 : 32 - __builtin_clz(span);
         stage_begin(ctx, st);
@@ -377,14 +424,16 @@ recogs_status render_device(recogs_ctx* ctx, const recogs_scene& s, const recogs
         const uint32_t* sorted = sb.vals[dcur];
 
         stage_begin(ctx, st);
-        l = launch_pair_block_sums(sorted, P<uint32_t>(ctx->count), (int)V,
+        // the depth sort's spare key buffer holds the counts in depth order
+        uint32_t* counts_sorted = sb.keys[dcur ^ 1];
+        l = launch_pair_block_sums(sorted, P<uint32_t>(ctx->count), (int)V, counts_sorted,
                                    P<uint32_t>(ctx->pair_sums), st);
         l += launch_scan_small(P<uint32_t>(ctx->pair_sums), P<uint32_t>(ctx->pair_offsets), vb, 1,
                                nullptr, st);
         stage_end(ctx, ST_PAIR_OFFSETS, l, st);
 
         stage_begin(ctx, st);
-        l = launch_emit(sorted, P<uint32_t>(ctx->count), P<uint2>(ctx->rect), (int)V,
+        l = launch_emit(sorted, counts_sorted, P<uint2>(ctx->rect), (int)V,
                         P<uint32_t>(ctx->pair_offsets), dc.tiles_x, P<uint32_t>(ctx->tkeys[0]),
                         P<uint32_t>(ctx->tvals[0]), st);
         stage_end(ctx, ST_EMIT, l, st);
@@ -399,12 +448,15 @@ recogs_status render_device(recogs_ctx* ctx, const recogs_scene& s, const recogs
         l = 0;
         const int tcur = radix_sort_pairs(tb, (int)Pn, tbits, st, &l);
         stage_end(ctx, ST_SORT_TILE, l, st);
-
-        stage_begin(ctx, st);
-        l = launch_ranges(tb.keys[tcur], (int)Pn, P<uint2>(ctx->ranges), st);
-        stage_end(ctx, ST_RANGES, l, st);
         ids = tb.vals[tcur];
+        stage_begin(ctx, st);
+        l = launch_tile_order(P<uint2>(ctx->ranges), tiles, P<uint32_t>(ctx->order), st);
+        stage_end(ctx, ST_TILE_ORDER, l, st);
         CK(cudaGetLastError());
+    } else {
+        stage_begin(ctx, st);
+        l = launch_tile_order(P<uint2>(ctx->ranges), tiles, P<uint32_t>(ctx->order), st);
+        stage_end(ctx, ST_TILE_ORDER, l, st);
     }
     if (!ids) {
         CKS(ensure(ctx, ctx->tvals[0], 16));
@@ -412,9 +464,10 @@ recogs_status render_device(recogs_ctx* ctx, const recogs_scene& s, const recogs
     }
     if (n == 0) CKS(ensure(ctx, ctx->rec, 16 * 3));
 
+    // 4. blend
     stage_begin(ctx, st);
-    int l = launch_blend(P<uint2>(ctx->ranges), ids, P<float4>(ctx->rec), dc, bgv, image, final_T,
-                         dctr, st);
+    l = launch_blend(P<uint2>(ctx->ranges), P<uint32_t>(ctx->order), ids, P<float4>(ctx->rec), dc,
+                     bgv, image, final_T, dctr, st);
     stage_end(ctx, ST_BLEND, l, st);
     CK(cudaGetLastError());
 
@@ -493,9 +546,11 @@ void recogs_ctx_destroy(recogs_ctx* ctx) {
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&ctx->rec, &ctx->count, &ctx->rect, &ctx->zkey, &ctx->block_sums,
                       &ctx->block_offsets, &ctx->counters, &ctx->dkeys[0], &ctx->dkeys[1],
-                      &ctx->dvals[0], &ctx->dvals[1], &ctx->table, &ctx->digit_totals,
+                      &ctx->dvals[0], &ctx->dvals[1], &ctx->sort_scratch,
                       &ctx->pair_sums, &ctx->pair_offsets, &ctx->tkeys[0], &ctx->tkeys[1],
-                      &ctx->tvals[0], &ctx->tvals[1], &ctx->ranges, &ctx->hs_xyz, &ctx->hs_ls,
+                      &ctx->tvals[0], &ctx->tvals[1], &ctx->ranges, &ctx->order, &ctx->tile_count,
+                      &ctx->cursor, &ctx->tile_totals, &ctx->pair_keys, &ctx->hs_xyz,
+                      &ctx->hs_ls,
                       &ctx->hs_q, &ctx->hs_op, &ctx->hs_sh, &ctx->hs_img, &ctx->hs_T};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
@@ -677,5 +732,12 @@ recogs_status recogs_stage_times(recogs_ctx* ctx, int32_t max_stages, int32_t* n
 }
 
 int64_t recogs_launch_count(const recogs_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+recogs_status recogs_set_sort_path(recogs_ctx* ctx, int path) {
+    if (!ctx) return RECOGS_EINVAL;
+    if (path < 0 || path > 2) return fail(ctx, RECOGS_EINVAL, "sort path must be 0, 1 or 2");
+    ctx->sort_path = path;
+    return RECOGS_OK;
+}
 
 }  // extern "C"

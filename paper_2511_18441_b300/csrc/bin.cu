@@ -1,0 +1,528 @@
+// Tile binning and per-tile depth ordering for the front-to-back blend of
+// Eq. 3 (ReCoGS, arXiv 2511.18441, Sec. 3.1).
+//
+// The per-Gaussian pass counts the (tile, Gaussian) pairs of every tile (on
+// kTileParts counter partitions). An exclusive scan over tiles gives each
+// tile's range in the pair array. Every visible Gaussian then writes the
+// 64-bit key (depth bits << 32 | index) of each of its pairs into its tiles'
+// ranges through per-tile cursors (block-aggregated atomics: arbitrary order
+// inside a range), and one CTA per tile sorts its range with a bitonic
+// network held in registers. The result is
+// every tile's list in (float32 depth, index) order -- the order a stable LSD
+// radix sort of (tile, depth) keys of index-ordered pairs produces -- without
+// sorting all pairs globally. Tiles with more pairs than shared memory holds
+// take the global radix path instead (see api.cu).
+#include "recogs_internal.cuh"
+
+namespace recogs {
+
+// ---------------------------------------------------------------------------
+// per-tile totals over the counter partitions
+
+// One warp per tile: lane l holds partition l (lanes beyond PARTS hold 0).
+template <int PARTS>
+__global__ void __launch_bounds__(256) tile_totals_kernel(const uint32_t* __restrict__ tile_count,
+                                                          int tiles, uint32_t* __restrict__ cursor,
+                                                          uint32_t* __restrict__ totals) {
+    static_assert(PARTS <= 32, "one partition per lane");
+    const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (t >= tiles) return;
+    const uint32_t c = lane < PARTS ? tile_count[(size_t)t * PARTS + lane] : 0u;
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane < PARTS) cursor[(size_t)t * PARTS + lane] = inc - c;
+    if (lane == 31) totals[t] = inc;
+}
+
+int launch_tile_totals(const uint32_t* tile_count, int tiles, int parts, uint32_t* cursor,
+                       uint32_t* totals, cudaStream_t st) {
+    if (parts == kTileParts)
+        tile_totals_kernel<kTileParts><<<(tiles + 7) / 8, 256, 0, st>>>(tile_count, tiles, cursor,
+                                                                        totals);
+    else
+        tile_totals_kernel<kTilePartsSmall><<<(tiles + 7) / 8, 256, 0, st>>>(tile_count, tiles,
+                                                                             cursor, totals);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// scan over tiles: ranges, total pairs, the largest tile, tiles per sort class
+
+// Sort class of a tile with c > 0 pairs: the tile order groups tiles in
+// buckets of 8 pairs (b = c >> 3, capped at 1023); a class is a run of whole
+// buckets whose largest member, 8 (b + 1) - 1 pairs, fits 8 keys per thread.
+__device__ __forceinline__ int sort_class(uint32_t c) {
+    const uint32_t b = min(c >> 3, 1023u) + 1u;            // 1 .. 1024
+    const int lg = b <= 1u ? 0 : 32 - __clz((int)(b - 1u)); // ceil(log2 b)
+    return kSortClasses - 1 - min(max(lg - 5, 0), kSortClasses - 1);
+}
+
+__global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restrict__ totals,
+                                                         int tiles, uint2* __restrict__ ranges,
+                                                         DevCounters* __restrict__ ctr) {
+    __shared__ uint32_t s_warp[33];
+    __shared__ uint32_t s_max[32];
+    __shared__ uint32_t s_cls[kSortClasses];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < kSortClasses) s_cls[threadIdx.x] = 0;
+    __syncthreads();
+    unsigned long long carry = 0;
+    uint32_t mx = 0;
+    for (int base = 0; base < tiles; base += 1024) {
+        const int t = base + threadIdx.x;
+        const uint32_t c = t < tiles ? totals[t] : 0u;
+        mx = max(mx, c);
+        if (c) atomicAdd(&s_cls[sort_class(c)], 1u);
+        uint32_t inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t w = s_warp[lane];
+            uint32_t wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            s_warp[lane] = wi - w;
+            if (lane == 31) s_warp[32] = wi;
+        }
+        __syncthreads();
+        const uint32_t start = (uint32_t)carry + s_warp[warp] + inc - c;
+        if (t < tiles) ranges[t] = make_uint2(start, start + c);
+        carry += s_warp[32];
+        __syncthreads();
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) s_max[warp] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t m = 0;
+        for (int w = 0; w < 32; ++w) m = max(m, s_max[w]);
+        ctr->max_tile = m;
+        ctr->n_pairs = carry > 0xffffffffull ? 0xffffffffu : (uint32_t)carry;
+        for (int c = 0; c < kSortClasses; ++c) ctr->class_tiles[c] = s_cls[c];
+    }
+}
+
+int launch_tile_scan(const uint32_t* totals, int tiles, uint2* ranges, DevCounters* counters,
+                     cudaStream_t st) {
+    tile_scan_kernel<<<1, 1024, 0, st>>>(totals, tiles, ranges, counters);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// pair scatter: per visible Gaussian, one key per covered tile
+//
+// Consecutive Gaussians lie on the same surfaces and share tiles, so the
+// pairs of a block are first counted per tile in a shared-memory hash table
+// (one shared atomic per pair, which also gives the pair its rank among the
+// block's pairs of that tile); then one global atomic per distinct tile of
+// the block reserves the block's slots inside that tile's range, on the
+// counter partition of the block (the per-Gaussian pass counted the same
+// pairs on the same partition). Pairs that do not fit the table (or beyond a
+// Gaussian's first kScatterLocal tiles) take one global atomic each.
+
+constexpr int kScatterThreads = 256;
+constexpr int kHashSlots = 2048;
+constexpr int kScatterLocal = 8;
+constexpr uint32_t kEmptySlot = 0xffffffffu;
+static_assert(kScatterThreads == kPrepThreads, "scatter blocks mirror the per-Gaussian blocks");
+
+__global__ void __launch_bounds__(kScatterThreads)
+    scatter_kernel(const uint32_t* __restrict__ count, const uint2* __restrict__ rect,
+                   const uint32_t* __restrict__ zkey, int n, int tiles_x,
+                   const uint2* __restrict__ ranges, uint32_t* __restrict__ cursor, int parts,
+                   unsigned long long* __restrict__ keys) {
+    __shared__ uint32_t s_tile[kHashSlots];
+    __shared__ uint32_t s_cnt[kHashSlots];
+    for (int k = threadIdx.x; k < kHashSlots; k += kScatterThreads) {
+        s_tile[k] = kEmptySlot;
+        s_cnt[k] = 0;
+    }
+    __syncthreads();
+    const uint32_t part = blockIdx.x & (uint32_t)(parts - 1);
+    const int i = blockIdx.x * kScatterThreads + threadIdx.x;
+    uint32_t c = 0, x0 = 0, y0 = 0, w = 1;
+    unsigned long long key = 0;
+    if (i < n) {
+        c = count[i];
+        if (c) {
+            const uint2 r = rect[i];
+            x0 = r.x & 0xffffu;
+            y0 = r.y & 0xffffu;
+            w = (r.x >> 16) - x0 + 1;
+            key = ((unsigned long long)zkey[i] << 32) | (uint32_t)i;
+        }
+    }
+    // phase 1: count per tile in the block's table; remember (slot, rank)
+    uint32_t slot[kScatterLocal], rank[kScatterLocal];
+    const uint32_t nloc = min(c, (uint32_t)kScatterLocal);
+#pragma unroll
+    for (int k = 0; k < kScatterLocal; ++k) {
+        slot[k] = kEmptySlot;
+        rank[k] = 0;
+        if ((uint32_t)k < nloc) {
+            const uint32_t dy = (uint32_t)k / w;
+            const uint32_t t = (y0 + dy) * (uint32_t)tiles_x + x0 + ((uint32_t)k - dy * w);
+            uint32_t h = (t * 2654435761u) >> 21;   // 11-bit multiplicative hash
+            for (int probe = 0; probe < 32; ++probe) {
+                const uint32_t prev = atomicCAS(&s_tile[h], kEmptySlot, t);
+                if (prev == kEmptySlot || prev == t) {
+                    slot[k] = h;
+                    rank[k] = atomicAdd(&s_cnt[h], 1u);
+                    break;
+                }
+                h = (h + 1) & (kHashSlots - 1);
+            }
+        }
+    }
+    __syncthreads();
+    // phase 2: reserve each distinct tile's slots in its range
+    for (int k = threadIdx.x; k < kHashSlots; k += kScatterThreads) {
+        const uint32_t t = s_tile[k];
+        if (t != kEmptySlot)
+            s_cnt[k] = ranges[t].x + atomicAdd(&cursor[(size_t)t * parts + part], s_cnt[k]);
+    }
+    __syncthreads();
+    // phase 3: write the keys
+#pragma unroll
+    for (int k = 0; k < kScatterLocal; ++k) {
+        if ((uint32_t)k >= nloc) break;
+        uint32_t pos;
+        if (slot[k] != kEmptySlot) {
+            pos = s_cnt[slot[k]] + rank[k];
+        } else {
+            const uint32_t dy = (uint32_t)k / w;
+            const uint32_t t = (y0 + dy) * (uint32_t)tiles_x + x0 + ((uint32_t)k - dy * w);
+            pos = ranges[t].x + atomicAdd(&cursor[(size_t)t * parts + part], 1u);
+        }
+        keys[pos] = key;
+    }
+    for (uint32_t k = kScatterLocal; k < c; ++k) {
+        const uint32_t dy = k / w;
+        const uint32_t t = (y0 + dy) * (uint32_t)tiles_x + x0 + (k - dy * w);
+        keys[ranges[t].x + atomicAdd(&cursor[(size_t)t * parts + part], 1u)] = key;
+    }
+}
+
+int launch_scatter(const uint32_t* count, const uint2* rect, const uint32_t* zkey, int n,
+                   int tiles_x, const uint2* ranges, uint32_t* cursor, int parts,
+                   unsigned long long* keys, cudaStream_t st) {
+    if (n == 0) return 0;
+    scatter_kernel<<<(n + kScatterThreads - 1) / kScatterThreads, kScatterThreads, 0, st>>>(
+        count, rect, zkey, n, tiles_x, ranges, cursor, parts, keys);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// per-tile bitonic sort, register resident
+//
+// A CTA of THREADS threads sorts one tile of up to 8 * THREADS keys: thread t
+// holds keys 8t .. 8t+7 in registers. Compare-exchange stages whose partner
+// is in the same thread run in registers, stages across lanes use warp
+// shuffles, and only stages across warps go through shared memory. Tiles are
+// grouped by size so that every class is launched with a CTA just large
+// enough for it (32 .. 1024 threads).
+
+// Compare-exchange of the pairs (e, e + J) among a thread's 8 keys, whose
+// global positions are base + e; ascending where bit k of the position is 0.
+template <int J>
+__device__ __forceinline__ void in_thread_stage(unsigned long long (&v)[8], int base, int k) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        if (e & J) continue;
+        const bool up = ((base + e) & k) == 0;
+        const unsigned long long x = v[e], y = v[e + J];
+        const bool swap = (x > y) == up;
+        v[e] = swap ? y : x;
+        v[e + J] = swap ? x : y;
+    }
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+    tile_sort_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+                     const unsigned long long* __restrict__ keys, uint32_t* __restrict__ ids) {
+    constexpr int E = 8;
+    constexpr int NPAD = E * THREADS;
+    extern __shared__ unsigned long long s[];   // NPAD keys when THREADS > 32
+    const int tile = (int)order[blockIdx.x];
+    const uint2 r = ranges[tile];
+    const int n = (int)(r.y - r.x);
+    const int t = threadIdx.x;
+    unsigned long long v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int idx = E * t + e;
+        v[e] = idx < n ? keys[r.x + idx] : ~0ull;
+    }
+    bool in_smem = false;
+    for (int k = 2; k <= NPAD; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32 * E) {
+                // partner in another warp: shared memory
+                if (!in_smem) {
+                    __syncthreads();
+#pragma unroll
+                    for (int e = 0; e < E; ++e) s[E * t + e] = v[e];
+                    in_smem = true;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int q = 0; q < E / 2; ++q) {
+                    const int p = t + THREADS * q;
+                    const int a = ((p & ~(j - 1)) << 1) | (p & (j - 1));
+                    const int b = a + j;
+                    const unsigned long long x = s[a], y = s[b];
+                    if ((x > y) == ((a & k) == 0)) {
+                        s[a] = y;
+                        s[b] = x;
+                    }
+                }
+                __syncthreads();
+                continue;
+            }
+            if (in_smem) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) v[e] = s[E * t + e];
+                in_smem = false;
+            }
+            if (j >= E) {
+                // partner in another lane of this warp
+                const int lm = j / E;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[e], lm);
+                    const int idx = E * t + e;
+                    const bool keep_min = ((idx & j) == 0) == ((idx & k) == 0);
+                    v[e] = keep_min ? (v[e] < o ? v[e] : o) : (v[e] < o ? o : v[e]);
+                }
+            } else if (j == 4) {
+                in_thread_stage<4>(v, E * t, k);
+            } else if (j == 2) {
+                in_thread_stage<2>(v, E * t, k);
+            } else {
+                in_thread_stage<1>(v, E * t, k);
+            }
+        }
+    }
+    if (in_smem) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = s[E * t + e];
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int idx = E * t + e;
+        if (idx < n) ids[r.x + idx] = (uint32_t)v[e];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-tile LSD radix sort in shared memory (tiles of 512 .. 8192 pairs)
+//
+// Sorts a tile's pairs by the 32-bit depth key relative to the frame's
+// smallest depth, 8 bits per pass, carrying the Gaussian index. Each pass is
+// a stable split: warp w owns positions 256w .. 256w+255 of the current
+// sequence (8 rounds of 32), ranks its items with warp match and per-warp
+// digit counters, and all items move to their digit's run in shared memory.
+// Pairs with equal depth keys are put in index order afterwards (runs of
+// equal keys are rare and short), so the result is (depth, index) order.
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+    tile_radix_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+                      const unsigned long long* __restrict__ keys, uint32_t* __restrict__ ids,
+                      uint32_t zmin, int passes) {
+    constexpr int W = THREADS / 32;
+    constexpr int ITEMS = 8;
+    constexpr int MAXN = THREADS * ITEMS;
+    extern __shared__ uint32_t smem[];
+    uint32_t* s_key = smem;                      // MAXN
+    uint32_t* s_val = s_key + MAXN;              // MAXN
+    uint32_t* s_wcnt = s_val + MAXN;             // W * 256
+    __shared__ uint32_t s_dstart[256];
+    __shared__ uint32_t s_part[W + 1];
+
+    const int tile = (int)order[blockIdx.x];
+    const uint2 r = ranges[tile];
+    const int n = (int)(r.y - r.x);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+
+    uint32_t key[ITEMS], val[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const int p = warp * 256 + i * 32 + lane;
+        if (p < n) {
+            const unsigned long long k = keys[r.x + p];
+            key[i] = (uint32_t)(k >> 32) - zmin;
+            val[i] = (uint32_t)k;
+        } else {
+            key[i] = 0xffffffffu;
+            val[i] = 0u;
+        }
+    }
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        for (int d = threadIdx.x; d < W * 256; d += THREADS) s_wcnt[d] = 0;
+        __syncthreads();
+        uint32_t rank[ITEMS];
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const int p = warp * 256 + i * 32 + lane;
+            const bool ok = p < n;
+            const uint32_t dg = ok ? ((key[i] >> shift) & 0xffu) : 256u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+            const uint32_t before = ok ? s_wcnt[warp * 256 + dg] : 0u;
+            __syncwarp();
+            if (ok && (peers & lt) == 0) s_wcnt[warp * 256 + dg] = before + __popc(peers);
+            __syncwarp();
+            rank[i] = before + __popc(peers & lt);
+        }
+        __syncthreads();
+        // per digit: offsets of the warps, then the digit's start in the tile
+        for (int d = threadIdx.x; d < 256; d += THREADS) {
+            uint32_t run = 0;
+            for (int w = 0; w < W; ++w) {
+                const uint32_t c = s_wcnt[w * 256 + d];
+                s_wcnt[w * 256 + d] = run;
+                run += c;
+            }
+            s_dstart[d] = run;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // exclusive scan of the 256 digit totals: 8 per lane
+            uint32_t v[8], sum = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                v[q] = s_dstart[lane * 8 + q];
+                sum += v[q];
+            }
+            uint32_t inc = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            uint32_t run = inc - sum;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                s_dstart[lane * 8 + q] = run;
+                run += v[q];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const int p = warp * 256 + i * 32 + lane;
+            if (p < n) {
+                const uint32_t dg = (key[i] >> shift) & 0xffu;
+                const uint32_t q = s_dstart[dg] + s_wcnt[warp * 256 + dg] + rank[i];
+                s_key[q] = key[i];
+                s_val[q] = val[i];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const int p = warp * 256 + i * 32 + lane;
+            if (p < n) {
+                key[i] = s_key[p];
+                val[i] = s_val[p];
+            }
+        }
+    }
+    if (passes == 0) {
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const int p = warp * 256 + i * 32 + lane;
+            if (p < n) {
+                s_key[p] = key[i];
+                s_val[p] = val[i];
+            }
+        }
+    }
+    __syncthreads();
+    // equal depth keys: order each run by index (insertion sort by the run's first position)
+    for (int p = threadIdx.x; p < n; p += THREADS) {
+        const bool starts = (p == 0 || s_key[p - 1] != s_key[p]) && p + 1 < n && s_key[p + 1] == s_key[p];
+        if (starts) {
+            int e = p + 1;
+            while (e + 1 < n && s_key[e + 1] == s_key[p]) ++e;
+            for (int a = p + 1; a <= e; ++a) {
+                const uint32_t x = s_val[a];
+                int b = a - 1;
+                while (b >= p && s_val[b] > x) {
+                    s_val[b + 1] = s_val[b];
+                    --b;
+                }
+                s_val[b + 1] = x;
+            }
+        }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < n; p += THREADS) ids[r.x + p] = s_val[p];
+    (void)s_part;
+}
+
+template <int THREADS>
+static void radix_class_launch(unsigned g, const uint2* ranges, const uint32_t* o,
+                               const unsigned long long* keys, uint32_t* ids, uint32_t zmin,
+                               int passes, cudaStream_t st) {
+    const size_t smem = sizeof(uint32_t) * (2 * 8 * THREADS + (THREADS / 32) * 256);
+    // dynamic plus static shared memory above the 48 KiB default needs the opt-in
+    if (smem + 2048 > 48 * 1024)
+        cudaFuncSetAttribute(tile_radix_kernel<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    tile_radix_kernel<THREADS><<<g, THREADS, smem, st>>>(ranges, o, keys, ids, zmin, passes);
+}
+
+template <int THREADS>
+static void sort_class_launch(unsigned g, const uint2* ranges, const uint32_t* o,
+                              const unsigned long long* keys, uint32_t* ids, cudaStream_t st) {
+    const size_t smem = THREADS > 32 ? sizeof(unsigned long long) * 8 * THREADS : 0;
+    if (smem + 2048 > 48 * 1024)
+        cudaFuncSetAttribute(tile_sort_kernel<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    tile_sort_kernel<THREADS><<<g, THREADS, smem, st>>>(ranges, o, keys, ids);
+}
+
+int launch_tile_sort(const uint2* ranges, const uint32_t* order, const uint32_t* class_tiles,
+                     const unsigned long long* keys, uint32_t* ids, uint32_t zmin, int depth_bits,
+                     cudaStream_t st) {
+    // the tile order lists the classes from the largest CTA (1024 threads) down;
+    // tiles of 512 pairs or more use the radix sort, smaller ones the bitonic network
+    const int passes = (depth_bits + 7) / 8;
+    int launches = 0;
+    uint32_t off = 0;
+    for (int c = 0; c < kSortClasses; ++c) {
+        const uint32_t g = class_tiles[c];
+        if (g == 0) continue;
+        const uint32_t* o = order + off;
+        switch (c) {
+            case 0: radix_class_launch<1024>(g, ranges, o, keys, ids, zmin, passes, st); break;
+            case 1: radix_class_launch<512>(g, ranges, o, keys, ids, zmin, passes, st); break;
+            case 2: radix_class_launch<256>(g, ranges, o, keys, ids, zmin, passes, st); break;
+            case 3: radix_class_launch<128>(g, ranges, o, keys, ids, zmin, passes, st); break;
+            case 4: sort_class_launch<64>(g, ranges, o, keys, ids, st); break;
+            default: sort_class_launch<32>(g, ranges, o, keys, ids, st); break;
+        }
+        off += g;
+        ++launches;
+    }
+    return launches;
+}
+
+}  // namespace recogs

@@ -26,8 +26,7 @@ constexpr size_t cdiv(size_t a, size_t b) { return (a + b - 1) / b; }
 
 // Byte offsets of each buffer inside the scratch array.
 constexpr size_t kPrepBlocks = cdiv(kMaxN, kPrepThreads);
-constexpr size_t kSortBlocks = cdiv(kMaxN > kMaxP ? kMaxN : kMaxP, kSortTile);
-constexpr size_t kVisBlocks = cdiv(kMaxN, kSortTile);
+constexpr size_t kVisBlocks = cdiv(kMaxN, kEmitBlock);
 constexpr size_t oRec = 0;
 constexpr size_t oCount = align256(oRec + 3 * kMaxN * sizeof(float4));
 constexpr size_t oZkey = align256(oCount + kMaxN * 4);
@@ -43,12 +42,18 @@ constexpr size_t oTkeys0 = align256(oDvals1 + kMaxN * 4);
 constexpr size_t oTkeys1 = align256(oTkeys0 + kMaxP * 4);
 constexpr size_t oTvals0 = align256(oTkeys1 + kMaxP * 4);
 constexpr size_t oTvals1 = align256(oTvals0 + kMaxP * 4);
-constexpr size_t oTable = align256(oTvals1 + kMaxP * 4);
-constexpr size_t oDigits = align256(oTable + (size_t)kRadix * kSortBlocks * 4);
-constexpr size_t oPairSums = align256(oDigits + (size_t)kRadix * 4);
+constexpr size_t kSortScratchWords = 4 * 256 + 32 + 4 * cdiv(kMaxN > kMaxP ? kMaxN : kMaxP, 2048) * 256;
+constexpr size_t oSortScratch = align256(oTvals1 + kMaxP * 4);
+constexpr size_t oPairSums = align256(oSortScratch + kSortScratchWords * 4);
 constexpr size_t oPairOffsets = align256(oPairSums + kVisBlocks * 4);
 constexpr size_t oRanges = align256(oPairOffsets + kVisBlocks * 4);
-constexpr size_t kScratchBytes = align256(oRanges + kMaxTiles * sizeof(uint2));
+constexpr size_t oOrder = align256(oRanges + kMaxTiles * sizeof(uint2));
+constexpr size_t oTileCount = align256(oOrder + kMaxTiles * 4);
+constexpr size_t oCursor = align256(oTileCount + kMaxTiles * kTilePartsSmall * 4);
+constexpr size_t oTileTotals = align256(oCursor + kMaxTiles * kTilePartsSmall * 4);
+constexpr size_t kScratchBytes = align256(oTileTotals + kMaxTiles * 4);
+// the per-tile sort's 64-bit keys reuse the two tile-key buffers of the global path
+static_assert(oTkeys1 == oTkeys0 + kMaxP * 4, "tile-key buffers must be contiguous");
 static_assert(kScratchBytes < (16u << 20), "no-alloc scratch should stay under 16 MiB");
 
 // The scratch itself: one copy on every device that loads the library, kept
@@ -205,8 +210,8 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
     } while (0)
 
     // the array keeps the previous call's contents: zero what must start at zero
-    NA_CK(cudaMemsetAsync(dctr, 0, sizeof(DevCounters), st));
-    NA_CK(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)tiles, st));
+    NA_CK(cudaMemsetAsync(dctr, 0, kCountersClearBytes, st));
+    NA_CK(cudaMemsetAsync(U32(oTileCount), 0, sizeof(uint32_t) * kTilePartsSmall * (size_t)tiles, st));
 
     uint32_t V = 0, P = 0;
     DevCounters hc;
@@ -219,23 +224,41 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
         po.rect = reinterpret_cast<uint2*>(base + oRect);
         po.zkey = U32(oZkey);
         po.block_sums = U32(oBlockSums);
+        po.tile_count = U32(oTileCount);
+        po.parts = kTilePartsSmall;
         po.counters = dctr;
         launch_preprocess(*scene, dc, de, po, st);
         launch_scan_small(po.block_sums, U32(oBlockOffsets), nb, 1, &dctr->n_visible, st);
-        launch_scan_small(po.block_sums + nb, nullptr, nb, 1, &dctr->n_pairs, st);
-        NA_CK(cudaGetLastError());
-        NA_CK(cudaMemcpyAsync(&hc, dctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
-        NA_CK(cudaStreamSynchronize(st));
-        V = hc.n_visible;
-        P = hc.n_pairs;
-        if ((size_t)P > kMaxP)
-            return report(err, el, RECOGS_ECAPACITY,
-                          "%u (tile, Gaussian) pairs exceed the no-alloc limit of %d; the image "
-                          "was not written (use recogs_render)",
-                          P, RECOGS_NOALLOC_MAX_PAIRS);
     }
+    launch_tile_totals(U32(oTileCount), tiles, kTilePartsSmall, U32(oCursor), U32(oTileTotals), st);
+    launch_tile_scan(U32(oTileTotals), tiles, ranges, dctr, st);
+    NA_CK(cudaGetLastError());
+    NA_CK(cudaMemcpyAsync(&hc, dctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+    NA_CK(cudaStreamSynchronize(st));
+    V = hc.n_visible;
+    P = hc.n_pairs;
+    if (hc.error) {
+        NA_CK(cudaMemsetAsync(&dctr->error, 0, sizeof(uint32_t), st));
+        return report(err, el, RECOGS_ETIMEOUT,
+                      "a bounded device wait of an earlier call's sort gave up; that image "
+                      "is invalid");
+    }
+    if ((size_t)P > kMaxP)
+        return report(err, el, RECOGS_ECAPACITY,
+                      "%u (tile, Gaussian) pairs exceed the no-alloc limit of %d; the image "
+                      "was not written (use recogs_render)",
+                      P, RECOGS_NOALLOC_MAX_PAIRS);
     const uint32_t* ids = U32(oTvals0);
-    if (V > 0) {
+    if (V > 0 && (int)hc.max_tile <= kMaxSmemTile) {
+        unsigned long long* keys = reinterpret_cast<unsigned long long*>(base + oTkeys0);
+        launch_scatter(U32(oCount), reinterpret_cast<const uint2*>(base + oRect), U32(oZkey), n,
+                       dc.tiles_x, ranges, U32(oCursor), kTilePartsSmall, keys, st);
+        launch_tile_order(ranges, tiles, U32(oOrder), st);
+        const uint32_t span = hc.zmax - ~hc.zmin_inv;
+        const int dbits = span == 0 ? 0 : 32 - __builtin_clz(span);
+        launch_tile_sort(ranges, U32(oOrder), hc.class_tiles, keys, U32(oTvals0), ~hc.zmin_inv,
+                         dbits, st);
+    } else if (V > 0) {
         launch_compact(U32(oCount), U32(oZkey), n, U32(oBlockOffsets), dctr, U32(oDkeys0),
                        U32(oDvals0), st);
         SortBuffers sb;
@@ -243,18 +266,18 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
         sb.keys[1] = U32(oDkeys1);
         sb.vals[0] = U32(oDvals0);
         sb.vals[1] = U32(oDvals1);
-        sb.table = U32(oTable);
-        sb.digit_totals = U32(oDigits);
-        sb.max_blocks = (int)kSortBlocks;
+        sb.scratch = U32(oSortScratch);
+        sb.error = &dctr->error;
         const uint32_t span = hc.zmax - ~hc.zmin_inv;
         const int dbits = span == 0 ? 0 : 32 - __builtin_clz(span);
         int l = 0;
         const int dcur = radix_sort_pairs(sb, (int)V, dbits, st, &l);
         const uint32_t* sorted = sb.vals[dcur];
-        const int vb = ((int)V + kSortTile - 1) / kSortTile;
-        launch_pair_block_sums(sorted, U32(oCount), (int)V, U32(oPairSums), st);
+        const int vb = ((int)V + kEmitBlock - 1) / kEmitBlock;
+        uint32_t* counts_sorted = sb.keys[dcur ^ 1];
+        launch_pair_block_sums(sorted, U32(oCount), (int)V, counts_sorted, U32(oPairSums), st);
         launch_scan_small(U32(oPairSums), U32(oPairOffsets), vb, 1, nullptr, st);
-        launch_emit(sorted, U32(oCount), reinterpret_cast<const uint2*>(base + oRect), (int)V,
+        launch_emit(sorted, counts_sorted, reinterpret_cast<const uint2*>(base + oRect), (int)V,
                     U32(oPairOffsets), dc.tiles_x, U32(oTkeys0), U32(oTvals0), st);
         SortBuffers tb = sb;
         tb.keys[0] = U32(oTkeys0);
@@ -263,11 +286,13 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
         tb.vals[1] = U32(oTvals1);
         const int tbits = tiles <= 1 ? 0 : 32 - __builtin_clz((uint32_t)(tiles - 1));
         const int tcur = radix_sort_pairs(tb, (int)P, tbits, st, &l);
-        launch_ranges(tb.keys[tcur], (int)P, ranges, st);
         ids = tb.vals[tcur];
-        NA_CK(cudaGetLastError());
+        launch_tile_order(ranges, tiles, U32(oOrder), st);
+    } else {
+        launch_tile_order(ranges, tiles, U32(oOrder), st);
     }
-    launch_blend(ranges, ids, rec, dc, bgv, image_hwc_out, final_T_out, dctr, st);
+    NA_CK(cudaGetLastError());
+    launch_blend(ranges, U32(oOrder), ids, rec, dc, bgv, image_hwc_out, final_T_out, dctr, st);
     NA_CK(cudaGetLastError());
 #undef NA_CK
     return RECOGS_OK;

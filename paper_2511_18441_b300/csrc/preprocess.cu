@@ -199,6 +199,7 @@ __global__ void __launch_bounds__(kPrepThreads)
     const int i = blockIdx.x * kPrepThreads + threadIdx.x;
     uint32_t cnt = 0;
     uint32_t zbits = 0;
+    int rx0 = 0, ry0 = 0, rw = 1;   // first tile and width of the tile range
     if (i < n) {
         const float mx = __ldg(xyz + i), my = __ldg(xyz + n + i), mz = __ldg(xyz + 2 * n + i);
         float C[48];
@@ -268,8 +269,8 @@ __global__ void __launch_bounds__(kPrepThreads)
         if (valid) {
             // opacity sigma = sigmoid(logit); footprint: the alpha >= 1/255 ellipse
             // d^T conic d <= k, k = 2 ln(255 sigma) = 2 (ln 255 - ln(1 + e^-logit))
-            const float sigma = 1.0f / (1.0f + expf(-logit));
-            const float kk = 2.0f * (5.541263545158426f - log1pf(expf(-logit)));
+            const float softplus = log1pf(expf(-logit));  // -ln(sigma)
+            const float kk = 2.0f * (5.541263545158426f - softplus);
             if (kk >= 0.f) {
                 const float ex = sqrtf(kk * sa), ey = sqrtf(kk * sc);
                 int tx0, tx1, ty0, ty1;
@@ -278,6 +279,9 @@ __global__ void __launch_bounds__(kPrepThreads)
                 if (tx0 <= tx1 && ty0 <= ty1) {
                     cnt = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
                     zbits = __float_as_uint(tz);
+                    rx0 = tx0;
+                    ry0 = ty0;
+                    rw = tx1 - tx0 + 1;
                     // Eq. 2 at d = (mu - camera) / |mu - camera|, shown colour max(f + 0.5, 0)
                     float dx = mx - cam.pos[0], dy = my - cam.pos[1], dz = mz - cam.pos[2];
                     const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
@@ -299,8 +303,13 @@ __global__ void __launch_bounds__(kPrepThreads)
                     const float vl = __fadd_rn(__fmaf_rn(cam.fy, qyh, cam.cy - 16.0f * (float)ty0),
                                                __fmul_rn(cam.fy, qyl));
                     const uint32_t origin = (uint32_t)tx0 | ((uint32_t)ty0 << 16);
-                    out.rec[3 * (size_t)i + 0] = make_float4(ul, vl, A, B);
-                    out.rec[3 * (size_t)i + 1] = make_float4(Cc, sigma, ex, ey);
+                    // the blend evaluates alpha = 2^(q0 dx^2 + q1 dx dy + q2 dy^2 + log2 sigma):
+                    // the conic scaled by -log2(e)/2 (cross term by -log2(e))
+                    const float L2E = 1.4426950408889634f;
+                    out.rec[3 * (size_t)i + 0] =
+                        make_float4(ul, vl, -0.5f * L2E * A, -L2E * B);
+                    out.rec[3 * (size_t)i + 1] =
+                        make_float4(-0.5f * L2E * Cc, -L2E * softplus, ex, ey);
                     out.rec[3 * (size_t)i + 2] = make_float4(f[0], f[1], f[2], __uint_as_float(origin));
                     out.rect[i] = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16),
                                              (uint32_t)ty0 | ((uint32_t)ty1 << 16));
@@ -310,8 +319,24 @@ __global__ void __launch_bounds__(kPrepThreads)
         out.count[i] = cnt;
         out.zkey[i] = zbits;
     }
-    // block totals of visible Gaussians and pairs; depth range of visible ones
     const unsigned full = 0xffffffffu;
+    // pairs per tile: round k adds every lane's k-th tile, one atomic per
+    // distinct tile of the warp
+    if (out.tile_count) {
+        const uint32_t rounds = __reduce_max_sync(full, cnt);
+        for (uint32_t k = 0; k < rounds; ++k) {
+            uint32_t t = 0xffffffffu;
+            if (k < cnt) {
+                const uint32_t dy = k / (uint32_t)rw;
+                t = (uint32_t)(ry0 + (int)dy) * (uint32_t)cam.tiles_x + (uint32_t)rx0 + (k - dy * rw);
+            }
+            const uint32_t peers = __match_any_sync(full, t);
+            if (t != 0xffffffffu && (threadIdx.x & 31) == __ffs(peers) - 1)
+                atomicAdd(&out.tile_count[(size_t)t * out.parts + (blockIdx.x & (out.parts - 1))],
+                          (uint32_t)__popc(peers));
+        }
+    }
+    // block totals of visible Gaussians and pairs; depth range of visible ones
     const uint32_t vis = cnt > 0 ? 1u : 0u;
     const uint32_t wv = __reduce_add_sync(full, vis);
     const uint32_t wp = __reduce_add_sync(full, cnt);

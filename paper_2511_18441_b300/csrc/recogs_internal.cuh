@@ -17,7 +17,8 @@ constexpr int kBlendThreads = 256;      // one thread per tile pixel
 constexpr int kPrepThreads = 256;       // Gaussians per preprocess block
 constexpr int kSortThreads = 256;
 constexpr int kSortItemsPerThread = 16;
-constexpr int kSortTile = kSortThreads * kSortItemsPerThread;   // 4096 keys per sort block
+constexpr int kSortTile = kSortThreads * kSortItemsPerThread;   // 4096 items per scan block
+constexpr int kEmitBlock = 256;                // sorted Gaussians per pair-expansion block
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 
@@ -47,16 +48,33 @@ struct DevEdit {
     float dc_fix[3];     // (row sum of M - 1) * 0.5 / Y_0, the DC offset correction
 };
 
-// Counters written by the kernels of one frame (zeroed at its start).
+// Size classes of the per-tile sort (CTAs of 1024, 512, 256, 128, 64, 32 threads).
+constexpr int kSortClasses = 6;
+
+// Counters written by the kernels of one frame (zeroed at its start, except `error`).
 struct DevCounters {
     uint32_t zmin_inv;   // ~(smallest depth bits) of visible Gaussians (atomicMax)
     uint32_t zmax;       // largest depth bits of visible Gaussians
     uint32_t n_visible;
     uint32_t n_pairs;
     unsigned long long pairs_read;
-    uint32_t error;
-    uint32_t pad;
+    uint32_t max_tile;   // pairs of the most crowded tile
+    uint32_t class_tiles[kSortClasses];  // non-empty tiles per per-tile-sort class
+    uint32_t pad0;
+    uint32_t error;      // not cleared per frame: set by a bounded wait that gave up
+    uint32_t pad1;
 };
+constexpr size_t kCountersClearBytes = 56;  // the fields before `error`
+static_assert(sizeof(DevCounters) == 64, "DevCounters layout");
+
+// Largest tile list sorted by the per-tile sort (8192 keys for a CTA of 1024
+// threads); a frame with a larger tile takes the global radix path.
+constexpr int kMaxSmemTile = 8192;
+// Per-tile pair counters are split into partitions (by block index) so that
+// concurrent blocks rarely update the same counter: kTileParts for the
+// context path, kTilePartsSmall where scratch must stay small.
+constexpr int kTileParts = 16;
+constexpr int kTilePartsSmall = 32;
 
 // --------------------------------------------------------------------------
 // Exact-rounding helpers shared by the selection and recolour code so that
@@ -127,12 +145,15 @@ __device__ __forceinline__ void recolor_triple(const float* M, float& r, float& 
 // launches it issued.
 
 struct PrepOut {
-    float4* rec;          // [3*n]: (u', v', A, B), (C, sigma, ex, ey), (r, g, b, origin):
-                          // centre (u', v') relative to tile (tx0, ty0), origin = tx0 | ty0 << 16
+    float4* rec;          // [3*n]: (u', v', q0, q1), (q2, log2 sigma, ex, ey), (r, g, b, origin):
+                          // centre (u', v') relative to tile (tx0, ty0), origin = tx0 | ty0 << 16;
+                          // (q0, q1, q2) = -log2(e) (A/2, B, C/2) for conic (A, B, C)
     uint32_t* count;      // [n] tiles covered (0 = culled)
     uint2* rect;          // [n] (tx0 | tx1 << 16, ty0 | ty1 << 16)
     uint32_t* zkey;       // [n] float bits of the view depth
     uint32_t* block_sums; // [2 * blocks]: visible count, pair count
+    uint32_t* tile_count; // [tiles][parts] pairs per tile and partition (zeroed first)
+    int parts;            // kTileParts or kTilePartsSmall
     DevCounters* counters;
 };
 
@@ -152,22 +173,42 @@ int launch_compact(const uint32_t* count, const uint32_t* zkey, int n, const uin
 
 struct SortBuffers {
     uint32_t *keys[2], *vals[2];
-    uint32_t* table;       // [kRadix * max_blocks]
-    uint32_t* digit_totals;
-    int max_blocks;
+    uint32_t* scratch;     // sort_scratch_words(max items) words, cleared by each sort
+    uint32_t* error;       // set non-zero if a look-back wait gave up
 };
-// Stable LSD radix sort of n (key, value) pairs on bits [0, bits). Result in
-// buffer index returned (0 or 1).
+// Scratch words a sort of up to max_items pairs needs.
+size_t sort_scratch_words(int max_items);
+// Stable LSD radix sort of n (key, value) pairs on bits [0, bits), keys < 2^bits.
+// Result in the buffer index returned (0 or 1).
 int radix_sort_pairs(SortBuffers& b, int n, int bits, cudaStream_t st, int* launches);
 
-int launch_pair_block_sums(const uint32_t* sorted_ids, const uint32_t* count, int v, uint32_t* sums,
-                           cudaStream_t st);
-int launch_emit(const uint32_t* sorted_ids, const uint32_t* count, const uint2* rect, int v,
+// Pair expansion in depth order, kEmitBlock sorted Gaussians per block:
+// counts_sorted[j] = tile count of sorted Gaussian j, sums[b] = block totals;
+// after an exclusive scan of sums into block_offsets, emit writes the pairs.
+int launch_pair_block_sums(const uint32_t* sorted_ids, const uint32_t* count, int v,
+                           uint32_t* counts_sorted, uint32_t* sums, cudaStream_t st);
+int launch_emit(const uint32_t* sorted_ids, const uint32_t* counts_sorted, const uint2* rect, int v,
                 const uint32_t* block_offsets, int tiles_x, uint32_t* tile_keys, uint32_t* vals,
                 cudaStream_t st);
-int launch_ranges(const uint32_t* sorted_tiles, int p, uint2* ranges, cudaStream_t st);
-int launch_blend(const uint2* ranges, const uint32_t* ids, const float4* rec, const DevCamera& cam,
-                 const float bg[3], float* image, float* final_T, DevCounters* counters,
-                 cudaStream_t st);
+// Tile binning (bin.cu). tile_totals: per tile, the total and each
+// partition's exclusive offset (into cursor); tile_scan: ranges, the pair
+// total, the largest tile and the tile count of every sort class; scatter:
+// 64-bit (depth << 32 | index) keys into the ranges; tile_sort: per-tile sort
+// of the keys, writing the ordered Gaussian indices (class_tiles from the
+// host copy of the counters).
+int launch_tile_totals(const uint32_t* tile_count, int tiles, int parts, uint32_t* cursor,
+                       uint32_t* totals, cudaStream_t st);
+int launch_tile_scan(const uint32_t* totals, int tiles, uint2* ranges, DevCounters* counters,
+                     cudaStream_t st);
+int launch_scatter(const uint32_t* count, const uint2* rect, const uint32_t* zkey, int n,
+                   int tiles_x, const uint2* ranges, uint32_t* cursor, int parts,
+                   unsigned long long* keys, cudaStream_t st);
+int launch_tile_sort(const uint2* ranges, const uint32_t* order, const uint32_t* class_tiles,
+                     const unsigned long long* keys, uint32_t* ids, uint32_t zmin, int depth_bits,
+                     cudaStream_t st);
+int launch_tile_order(const uint2* ranges, int tiles, uint32_t* order, cudaStream_t st);
+int launch_blend(const uint2* ranges, const uint32_t* order, const uint32_t* ids, const float4* rec,
+                 const DevCamera& cam, const float bg[3], float* image, float* final_T,
+                 DevCounters* counters, cudaStream_t st);
 
 }  // namespace recogs

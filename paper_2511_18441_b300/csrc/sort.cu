@@ -10,10 +10,9 @@
 // bytes moved: 32-bit depth keys over V Gaussians plus ~13 tile bits over
 // P pairs instead of ~45 bits over P pairs.
 //
-// Radix pass = upsweep (per-block digit counts) + per-digit scan over blocks
-// + downsweep (stable block-local ranking with warp match, then a
-// digit-ordered scatter). No pass waits on another block: there is no
-// inter-block spinning anywhere in this file.
+// Radix pass = stable tile-local ranking with warp match + decoupled
+// look-back for the tile's global digit offsets + digit-ordered scatter (see
+// the radix sort section for the bounded waits).
 #include "recogs_internal.cuh"
 
 namespace recogs {
@@ -106,223 +105,236 @@ int launch_compact(const uint32_t* count, const uint32_t* zkey, int n, const uin
 }
 
 // ---------------------------------------------------------------------------
-// radix sort passes
+// radix sort: one histogram pass, then one kernel per 8-bit digit
+//
+// Each pass kernel takes a tile of 2048 (key, value) pairs, ranks them
+// stably inside the tile, and finds where each digit's run starts globally
+// from the histogram (all tiles) plus the counts of that digit in earlier
+// tiles, obtained by a decoupled look-back: every tile publishes its local
+// count (flag A), then its inclusive prefix (flag P) once known; a tile walks
+// back over its predecessors' published words until it meets a P. Tiles are
+// numbered in the order their CTAs start (an atomic counter), so every
+// predecessor a CTA waits on is already running and publishes its count
+// without waiting itself. Each wait is bounded: after kSpinLimit polls the
+// CTA records an error for the host and carries on (the host reports
+// RECOGS_ETIMEOUT); no wait can hang the GPU.
 
-__global__ void __launch_bounds__(kSortThreads)
-    radix_upsweep(const uint32_t* __restrict__ keys, int n, int shift, int nbits,
-                  uint32_t* __restrict__ table) {
-    __shared__ uint32_t hist[kRadix];
-    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) hist[d] = 0;
-    __syncthreads();
-    const uint32_t mask = (1u << nbits) - 1u;
-    const int base = blockIdx.x * kSortTile;
-#pragma unroll 4
-    for (int k = 0; k < kSortItemsPerThread; ++k) {
-        const int i = base + k * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&hist[(keys[i] >> shift) & mask], 1u);
-    }
-    __syncthreads();
-    const int nb = gridDim.x;
-    for (int d = threadIdx.x; d < (1 << nbits); d += kSortThreads)
-        table[d * nb + blockIdx.x] = hist[d];
+constexpr int kOsThreads = 256;
+constexpr int kOsItems = 8;
+constexpr int kOsTile = kOsThreads * kOsItems;   // 2048 pairs per tile
+constexpr uint32_t kFlagA = 1u << 30;            // local count published
+constexpr uint32_t kFlagP = 2u << 30;            // inclusive prefix published
+constexpr uint32_t kValueMask = (1u << 30) - 1u;
+constexpr uint32_t kSpinLimit = 1u << 20;
+constexpr int kHistWords = 4 * kRadix;           // up to 4 passes of 8 bits
+constexpr int kCounterWords = 32;
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// One block per digit: exclusive scan of that digit's counts across blocks,
-// digit total to digit_totals[d].
-__global__ void __launch_bounds__(1024) radix_scan(uint32_t* __restrict__ table, int nb,
-                                                   uint32_t* __restrict__ digit_totals) {
-    __shared__ uint32_t s_warp[33];
-    uint32_t* row = table + (size_t)blockIdx.x * nb;
-    uint32_t carry = 0;
-    for (int base = 0; base < nb; base += 1024) {
-        const int i = base + threadIdx.x;
-        const uint32_t x = i < nb ? row[i] : 0u;
-        uint32_t t;
-        const uint32_t e = block_exclusive_scan<1024>(x, s_warp, &t);
-        if (i < nb) row[i] = carry + e;
-        carry += t;
-    }
-    if (threadIdx.x == 0) digit_totals[blockIdx.x] = carry;
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__global__ void __launch_bounds__(kSortThreads)
-    radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-                    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int n,
-                    int shift, int nbits, const uint32_t* __restrict__ table,
-                    const uint32_t* __restrict__ digit_totals) {
-    constexpr int W = kSortThreads / 32;
-    constexpr int PER_WARP = kSortTile / W;       // 512 consecutive items per warp
-    __shared__ uint32_t s_keys[kSortTile];
-    __shared__ uint32_t s_vals[kSortTile];
-    __shared__ uint32_t s_wcnt[W][kRadix];        // per-warp digit counters -> warp offsets
+// Digit counts of every pass over all keys (keys are < 2^(8 passes)).
+__global__ void __launch_bounds__(kOsThreads)
+    os_histogram(const uint32_t* __restrict__ keys, int n, int passes, uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[kHistWords];
+    for (int i = threadIdx.x; i < kHistWords; i += kOsThreads) h[i] = 0;
+    __syncthreads();
+    for (int i = blockIdx.x * kOsThreads + threadIdx.x; i < n; i += gridDim.x * kOsThreads) {
+        const uint32_t k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p * kRadix + ((k >> (8 * p)) & 0xffu)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * kRadix; i += kOsThreads)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+__global__ void __launch_bounds__(kOsThreads)
+    os_pass(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+            uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int n, int shift,
+            const uint32_t* __restrict__ hist, uint32_t* __restrict__ status,
+            uint32_t* __restrict__ tile_counter, uint32_t* __restrict__ error) {
+    constexpr int W = kOsThreads / 32;
+    constexpr int PER_WARP = kOsTile / W;         // 256 consecutive pairs per warp
+    __shared__ uint32_t s_keys[kOsTile];
+    __shared__ uint32_t s_vals[kOsTile];
+    __shared__ uint32_t s_wcnt[W][kRadix];        // per-warp digit counts -> offsets
     __shared__ uint32_t s_bstart[kRadix];         // block-local start of each digit
-    __shared__ uint32_t s_gbase[kRadix];          // global start of each digit for this block
+    __shared__ uint32_t s_gbase[kRadix];          // global start of each digit for this tile
     __shared__ uint32_t s_warp[33];
+    __shared__ uint32_t s_tile;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t mask = (1u << nbits) - 1u;
-    const int nb = gridDim.x;
-    const int base = blockIdx.x * kSortTile;
-    const int nblk = min(kSortTile, n - base);
-
-    // global digit bases: exclusive scan of digit totals + this block's offset
-    {
-        const int d = threadIdx.x;  // kSortThreads == kRadix
-        const uint32_t tot = d < (1 << nbits) ? digit_totals[d] : 0u;
-        const uint32_t ex = block_exclusive_scan<kSortThreads>(tot, s_warp, nullptr);
-        s_gbase[d] = d < (1 << nbits) ? ex + table[d * nb + blockIdx.x] : 0u;
-        for (int w = 0; w < W; ++w) s_wcnt[w][d] = 0;
-    }
+    const int d = threadIdx.x;                    // kOsThreads == kRadix: one digit per thread
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
+#pragma unroll
+    for (int w = 0; w < W; ++w) s_wcnt[w][d] = 0;
     __syncthreads();
+    const uint32_t t = s_tile;
+    const int base = (int)t * kOsTile;
+    const int nblk = min(kOsTile, n - base);
 
     // stable warp-local ranking: item order = (iteration, lane) within the warp
-    uint32_t key[kSortItemsPerThread], val[kSortItemsPerThread], rank[kSortItemsPerThread];
+    uint32_t key[kOsItems], val[kOsItems], rank[kOsItems];
     const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
-    for (int k = 0; k < kSortItemsPerThread; ++k) {
+    for (int k = 0; k < kOsItems; ++k) {
         const int li = warp * PER_WARP + k * 32 + lane;
         const bool ok = li < nblk;
         key[k] = ok ? keys_in[base + li] : 0u;
         val[k] = ok ? vals_in[base + li] : 0u;
-        const uint32_t d = ok ? ((key[k] >> shift) & mask) : (uint32_t)kRadix;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t before = ok ? s_wcnt[warp][d] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kOsItems; ++k) {
+        const int li = warp * PER_WARP + k * 32 + lane;
+        const bool ok = li < nblk;
+        const uint32_t dg = ok ? ((key[k] >> shift) & 0xffu) : (uint32_t)kRadix;
+        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        const uint32_t before = ok ? s_wcnt[warp][dg] : 0u;
         __syncwarp();
-        if (ok && (peers & lt) == 0) s_wcnt[warp][d] = before + __popc(peers);
+        if (ok && (peers & lt) == 0) s_wcnt[warp][dg] = before + __popc(peers);
         __syncwarp();
         rank[k] = before + __popc(peers & lt);
     }
     __syncthreads();
-    // per digit: exclusive offsets across warps, block totals, block-local starts
-    {
-        const int d = threadIdx.x;
-        uint32_t run = 0;
+    uint32_t cnt = 0;
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            const uint32_t c = s_wcnt[w][d];
-            s_wcnt[w][d] = run;
-            run += c;
-        }
-        s_bstart[d] = block_exclusive_scan<kSortThreads>(run, s_warp, nullptr);
+    for (int w = 0; w < W; ++w) {
+        const uint32_t c = s_wcnt[w][d];
+        s_wcnt[w][d] = cnt;
+        cnt += c;
     }
+    // publish this tile's count of digit d, then find the count in earlier tiles
+    uint32_t* my = status + (size_t)t * kRadix + d;
+    uint32_t excl = 0;
+    if (t == 0) {
+        st_relaxed(my, kFlagP | cnt);
+    } else {
+        st_relaxed(my, kFlagA | cnt);
+        int j = (int)t - 1;
+        uint32_t spins = 0;
+        while (true) {
+            const uint32_t v = ld_relaxed(status + (size_t)j * kRadix + d);
+            const uint32_t f = v & ~kValueMask;
+            if (f == 0u) {
+                if (++spins > kSpinLimit) {
+                    atomicOr(error, 1u);
+                    break;
+                }
+                continue;
+            }
+            excl += v & kValueMask;
+            if (f == kFlagP || j == 0) break;
+            --j;
+        }
+        st_relaxed(my, kFlagP | (excl + cnt));
+    }
+    const uint32_t gex = block_exclusive_scan<kOsThreads>(hist[d], s_warp, nullptr);
+    s_gbase[d] = gex + excl;
+    s_bstart[d] = block_exclusive_scan<kOsThreads>(cnt, s_warp, nullptr);
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kSortItemsPerThread; ++k) {
+    for (int k = 0; k < kOsItems; ++k) {
         const int li = warp * PER_WARP + k * 32 + lane;
         if (li < nblk) {
-            const uint32_t d = (key[k] >> shift) & mask;
-            const uint32_t p = s_bstart[d] + s_wcnt[warp][d] + rank[k];
+            const uint32_t dg = (key[k] >> shift) & 0xffu;
+            const uint32_t p = s_bstart[dg] + s_wcnt[warp][dg] + rank[k];
             s_keys[p] = key[k];
             s_vals[p] = val[k];
         }
     }
     __syncthreads();
     // digit-ordered scatter: consecutive slots of one digit go to consecutive addresses
-    for (int j = threadIdx.x; j < nblk; j += kSortThreads) {
+    for (int j = threadIdx.x; j < nblk; j += kOsThreads) {
         const uint32_t k = s_keys[j];
-        const uint32_t d = (k >> shift) & mask;
-        const uint32_t g = s_gbase[d] + (uint32_t)j - s_bstart[d];
+        const uint32_t dg = (k >> shift) & 0xffu;
+        const uint32_t g = s_gbase[dg] + (uint32_t)j - s_bstart[dg];
         keys_out[g] = k;
         vals_out[g] = s_vals[j];
     }
 }
 
+size_t sort_scratch_words(int max_items) {
+    const size_t tiles = ((size_t)max_items + kOsTile - 1) / kOsTile;
+    return kHistWords + kCounterWords + 4 * tiles * kRadix;
+}
+
 int radix_sort_pairs(SortBuffers& b, int n, int bits, cudaStream_t st, int* launches) {
-    int cur = 0;
     if (n <= 1 || bits <= 0) return 0;
-    const int nb = (n + kSortTile - 1) / kSortTile;
-    for (int shift = 0; shift < bits; shift += kRadixBits) {
-        const int nbits = min(kRadixBits, bits - shift);
-        radix_upsweep<<<nb, kSortThreads, 0, st>>>(b.keys[cur], n, shift, nbits, b.table);
-        radix_scan<<<1 << nbits, 1024, 0, st>>>(b.table, nb, b.digit_totals);
-        radix_downsweep<<<nb, kSortThreads, 0, st>>>(b.keys[cur], b.vals[cur], b.keys[cur ^ 1],
-                                                      b.vals[cur ^ 1], n, shift, nbits, b.table,
-                                                      b.digit_totals);
-        *launches += 3;
+    const int passes = (bits + kRadixBits - 1) / kRadixBits;
+    const int tiles = (n + kOsTile - 1) / kOsTile;
+    uint32_t* hist = b.scratch;
+    uint32_t* counters = b.scratch + kHistWords;
+    uint32_t* status = counters + kCounterWords;
+    const size_t words = kHistWords + kCounterWords + (size_t)passes * tiles * kRadix;
+    cudaMemsetAsync(b.scratch, 0, words * sizeof(uint32_t), st);
+    const int hb = min((n + kOsThreads - 1) / kOsThreads, 148 * 4);
+    os_histogram<<<hb, kOsThreads, 0, st>>>(b.keys[0], n, passes, hist);
+    int cur = 0;
+    for (int p = 0; p < passes; ++p) {
+        os_pass<<<tiles, kOsThreads, 0, st>>>(b.keys[cur], b.vals[cur], b.keys[cur ^ 1],
+                                              b.vals[cur ^ 1], n, kRadixBits * p, hist + p * kRadix,
+                                              status + (size_t)p * tiles * kRadix, counters + p,
+                                              b.error);
         cur ^= 1;
     }
+    *launches += 1 + passes;
     return cur;
 }
 
 // ---------------------------------------------------------------------------
-// pair expansion in depth order
+// pair expansion in depth order (one sorted Gaussian per thread)
 
-// Blocked assignment: thread t of block b owns sorted Gaussians
-// b*4096 + t*16 .. +15.
-__global__ void __launch_bounds__(kSortThreads)
+// counts_sorted[j] = tile count of the j-th Gaussian in depth order; per-block totals.
+__global__ void __launch_bounds__(kEmitBlock)
     pair_block_sums(const uint32_t* __restrict__ ids, const uint32_t* __restrict__ count, int v,
-                    uint32_t* __restrict__ sums) {
+                    uint32_t* __restrict__ counts_sorted, uint32_t* __restrict__ sums) {
     __shared__ uint32_t s_warp[33];
-    const int base = blockIdx.x * kSortTile + threadIdx.x * kSortItemsPerThread;
-    uint32_t acc = 0;
-#pragma unroll 4
-    for (int k = 0; k < kSortItemsPerThread; ++k) {
-        const int j = base + k;
-        if (j < v) acc += count[ids[j]];
-    }
+    const int j = blockIdx.x * kEmitBlock + threadIdx.x;
+    const uint32_t c = j < v ? __ldg(count + __ldg(ids + j)) : 0u;
+    if (j < v) counts_sorted[j] = c;
     uint32_t tot;
-    block_exclusive_scan<kSortThreads>(acc, s_warp, &tot);
+    block_exclusive_scan<kEmitBlock>(c, s_warp, &tot);
     if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
-int launch_pair_block_sums(const uint32_t* sorted_ids, const uint32_t* count, int v, uint32_t* sums,
-                           cudaStream_t st) {
-    pair_block_sums<<<(v + kSortTile - 1) / kSortTile, kSortThreads, 0, st>>>(sorted_ids, count, v,
-                                                                                 sums);
+int launch_pair_block_sums(const uint32_t* sorted_ids, const uint32_t* count, int v,
+                           uint32_t* counts_sorted, uint32_t* sums, cudaStream_t st) {
+    pair_block_sums<<<(v + kEmitBlock - 1) / kEmitBlock, kEmitBlock, 0, st>>>(
+        sorted_ids, count, v, counts_sorted, sums);
     return 1;
 }
 
-__global__ void __launch_bounds__(kSortThreads)
-    emit_kernel(const uint32_t* __restrict__ ids, const uint32_t* __restrict__ count,
+__global__ void __launch_bounds__(kEmitBlock)
+    emit_kernel(const uint32_t* __restrict__ ids, const uint32_t* __restrict__ counts_sorted,
                 const uint2* __restrict__ rect, int v, const uint32_t* __restrict__ block_offsets,
                 int tiles_x, uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ vals) {
     __shared__ uint32_t s_warp[33];
-    const int base = blockIdx.x * kSortTile + threadIdx.x * kSortItemsPerThread;
-    uint32_t acc = 0;
-#pragma unroll 4
-    for (int k = 0; k < kSortItemsPerThread; ++k) {
-        const int j = base + k;
-        if (j < v) acc += count[ids[j]];
-    }
-    uint32_t o = block_offsets[blockIdx.x] + block_exclusive_scan<kSortThreads>(acc, s_warp, nullptr);
-    for (int k = 0; k < kSortItemsPerThread; ++k) {
-        const int j = base + k;
-        if (j >= v) break;
-        const uint32_t id = ids[j];
-        const uint2 r = rect[id];
-        const uint32_t x0 = r.x & 0xffffu, x1 = r.x >> 16, y0 = r.y & 0xffffu, y1 = r.y >> 16;
-        for (uint32_t y = y0; y <= y1; ++y)
-            for (uint32_t x = x0; x <= x1; ++x) {
-                tile_keys[o] = y * (uint32_t)tiles_x + x;
-                vals[o] = id;
-                ++o;
-            }
-    }
+    const int j = blockIdx.x * kEmitBlock + threadIdx.x;
+    const uint32_t c = j < v ? counts_sorted[j] : 0u;
+    uint32_t o = block_offsets[blockIdx.x] + block_exclusive_scan<kEmitBlock>(c, s_warp, nullptr);
+    if (j >= v) return;
+    const uint32_t id = __ldg(ids + j);
+    const uint2 r = __ldg(rect + id);
+    const uint32_t x0 = r.x & 0xffffu, x1 = r.x >> 16, y0 = r.y & 0xffffu, y1 = r.y >> 16;
+    for (uint32_t y = y0; y <= y1; ++y)
+        for (uint32_t x = x0; x <= x1; ++x) {
+            tile_keys[o] = y * (uint32_t)tiles_x + x;
+            vals[o] = id;
+            ++o;
+        }
 }
 
-int launch_emit(const uint32_t* sorted_ids, const uint32_t* count, const uint2* rect, int v,
+int launch_emit(const uint32_t* sorted_ids, const uint32_t* counts_sorted, const uint2* rect, int v,
                 const uint32_t* block_offsets, int tiles_x, uint32_t* tile_keys, uint32_t* vals,
                 cudaStream_t st) {
-    emit_kernel<<<(v + kSortTile - 1) / kSortTile, kSortThreads, 0, st>>>(
-        sorted_ids, count, rect, v, block_offsets, tiles_x, tile_keys, vals);
-    return 1;
-}
-
-// ---------------------------------------------------------------------------
-// tile ranges [begin, end) from the sorted tile keys (ranges pre-zeroed)
-
-__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict__ tiles, int p,
-                                                     uint2* __restrict__ ranges) {
-    const int j = blockIdx.x * 256 + threadIdx.x;
-    if (j >= p) return;
-    const uint32_t t = tiles[j];
-    if (j == 0 || tiles[j - 1] != t) ranges[t].x = (uint32_t)j;
-    if (j == p - 1 || tiles[j + 1] != t) ranges[t].y = (uint32_t)(j + 1);
-}
-
-int launch_ranges(const uint32_t* sorted_tiles, int p, uint2* ranges, cudaStream_t st) {
-    if (p == 0) return 0;
-    ranges_kernel<<<(p + 255) / 256, 256, 0, st>>>(sorted_tiles, p, ranges);
+    emit_kernel<<<(v + kEmitBlock - 1) / kEmitBlock, kEmitBlock, 0, st>>>(
+        sorted_ids, counts_sorted, rect, v, block_offsets, tiles_x, tile_keys, vals);
     return 1;
 }
 
