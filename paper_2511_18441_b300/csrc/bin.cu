@@ -339,8 +339,15 @@ __global__ void __launch_bounds__(THREADS)
 // Pairs with equal depth keys are put in index order afterwards (runs of
 // equal keys are rare and short), so the result is (depth, index) order.
 
+// Resident CTAs per SM the register allocation of the per-tile radix sort is held to.
+#ifndef RECOGS_RADIX_WARPS_PER_SM
+#define RECOGS_RADIX_WARPS_PER_SM 32
+#endif
+
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, (RECOGS_RADIX_WARPS_PER_SM * 32 / THREADS) > 0
+                                               ? (RECOGS_RADIX_WARPS_PER_SM * 32 / THREADS)
+                                               : 1)
     tile_radix_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
                       const unsigned long long* __restrict__ keys, uint32_t* __restrict__ ids,
                       uint32_t zmin, int passes) {
