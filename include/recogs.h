@@ -249,11 +249,96 @@ RECOGS_API int64_t recogs_launch_count(const recogs_ctx* ctx);
 
 /* How recogs_render orders each tile's list by (depth, index) (the order of
  * Eq. 3): 0 = automatic (per-tile shared-memory sort when the most crowded
- * tile has at most 16384 pairs, else the global path), 1 = per-tile sort
- * (falls back to the global path above 16384 pairs), 2 = global path (radix
+ * tile has at most 8192 pairs, else the global path), 1 = per-tile sort
+ * (falls back to the global path above 8192 pairs), 2 = global path (radix
  * sort by depth, pair expansion in depth order, stable radix sort by tile).
  * Both give identical lists. */
 RECOGS_API recogs_status recogs_set_sort_path(recogs_ctx* ctx, int path);
+
+/* Schedule knobs of recogs_render (the batch autotuner searches the same
+ * ones; every setting gives the same image bit for bit):
+ * radix_classes (0..5) = how many of the per-tile sort's size classes, from
+ * the largest tiles (up to 8192 pairs) down, are sorted by the shared-memory
+ * radix sort rather than the register bitonic network (default 4);
+ * blend_batch (128 or 256) = depth-sorted Gaussians staged in shared memory
+ * per step of the blend (default 256). */
+RECOGS_API recogs_status recogs_set_schedule(recogs_ctx* ctx, int32_t radix_classes,
+                                             int32_t blend_batch);
+
+/* ---------------------------------------------------------------------------
+ * Frames without a read back, batches of views, CUDA graphs
+ */
+
+/* pairs > 0: recogs_render no longer reads the visible and pair counts back
+ * in the middle of a frame (no stream synchronisation; the call can be
+ * captured into a CUDA graph once its scratch has grown, e.g. after one
+ * call of the same size). The pair buffers then hold `pairs` (tile, Gaussian)
+ * pairs and the per-tile sort is always used. A frame with more pairs, or
+ * with a tile above 8192 pairs, is not rendered: its image is the background
+ * only (T = 1) and an error is recorded on the device, reported by the next
+ * recogs_check (or by recogs_render when stats are requested).
+ * pairs = 0 restores the read back (the default). At most 2^28 - 1. */
+RECOGS_API recogs_status recogs_set_pair_capacity(recogs_ctx* ctx, int64_t pairs);
+
+/* Wait for `stream` and for the context's batch lanes, then report and clear
+ * the errors recorded on the device by frames without a read back:
+ * RECOGS_ECAPACITY (pairs above the capacity, or a tile above the per-tile
+ * limit), RECOGS_ETIMEOUT (a bounded device wait gave up). */
+RECOGS_API recogs_status recogs_check(recogs_ctx* ctx, void* stream);
+
+/* One view of a batch: scenes[scene] rendered from `camera` with an optional
+ * fused edit, as recogs_render would (same image bit for bit). */
+typedef struct {
+    int32_t scene;              /* index into the batch's scenes */
+    int32_t reserved;
+    recogs_camera camera;
+    const recogs_edit* edit;    /* HOST, may be NULL */
+    float bg[3];                /* background added as T_final * bg */
+    float* image_hwc_out;       /* device, height*width*3 float32 */
+    float* final_T_out;         /* device, height*width float32, may be NULL */
+} recogs_view;
+
+#define RECOGS_BATCH_GRAPH 1u   /* capture the batch as a CUDA graph and replay it */
+#define RECOGS_BATCH_TUNE 2u    /* autotune the schedule when the batch is planned */
+#define RECOGS_BATCH_NOWAIT 4u  /* return without waiting; errors via recogs_check */
+
+/* Render many views of many scenes (views and scenes are independent,
+ * Sec. 3.1; the concurrent streams of Sec. 4.2). The first call with a given
+ * batch description (the scene structs, the view structs and the edits'
+ * contents, compared byte for byte) plans the batch: it renders each view
+ * once with the read back (the images of this call), records its pair
+ * count, spreads the views over lanes (each with its own scratch and
+ * stream; views run concurrently across lanes) and, with RECOGS_BATCH_GRAPH,
+ * captures all lanes as one CUDA graph. With RECOGS_BATCH_TUNE the planning
+ * also times candidate schedules (lane count 1/2/4, the per-tile sort's radix
+ * classes, the blend batch) and keeps the fastest. Planning waits for the
+ * device. Later calls with the same description replay the plan (one graph
+ * launch) without any read back; the scenes' and regions' contents may
+ * change between calls, their sizes and pointers may not.
+ * Without RECOGS_BATCH_NOWAIT the call waits for the batch and, if a view
+ * outgrew its lane's pair buffers, plans again (rendering every view again).
+ * With it, the call returns at once and recogs_check reports overflows (the
+ * affected images hold the background only). Views with a tile above 8192
+ * pairs are rendered with the read back after the lanes. */
+RECOGS_API recogs_status recogs_render_batch(recogs_ctx* ctx, const recogs_scene* scenes,
+                                             int32_t n_scenes, const recogs_view* views,
+                                             int32_t n_views, uint32_t flags, void* stream);
+
+typedef struct {
+    int32_t planned;            /* 1 once a batch has been planned */
+    int32_t graph;              /* 1 if the plan replays a CUDA graph */
+    int32_t lanes;
+    int32_t radix_classes;
+    int32_t blend_batch;
+    int32_t tune_trials;        /* schedules timed by the autotuner */
+    int32_t views_outside_lanes;
+    int32_t reserved;
+    int64_t graph_launches;     /* kernel launches in one replay of the graph */
+    double tuned_ms;            /* best batch time the autotuner measured (0 if not tuned) */
+} recogs_batch_info_t;
+
+/* The plan of the last batch: lanes, chosen schedule, graph size. */
+RECOGS_API recogs_status recogs_batch_info(recogs_ctx* ctx, recogs_batch_info_t* info);
 
 #ifdef __cplusplus
 }

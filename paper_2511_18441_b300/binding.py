@@ -56,6 +56,21 @@ class CStats(C.Structure):
                 ("n_tiles", C.c_int32), ("reserved", C.c_int32)]
 
 
+class CView(C.Structure):
+    _fields_ = [("scene", C.c_int32), ("reserved", C.c_int32), ("camera", CCamera),
+                ("edit", C.POINTER(CEdit)), ("bg", C.c_float * 3), ("image_hwc_out", C.c_void_p),
+                ("final_T_out", C.c_void_p)]
+
+
+class CBatchInfo(C.Structure):
+    _fields_ = [("planned", C.c_int32), ("graph", C.c_int32), ("lanes", C.c_int32),
+                ("radix_classes", C.c_int32), ("blend_batch", C.c_int32),
+                ("tune_trials", C.c_int32), ("views_outside_lanes", C.c_int32),
+                ("reserved", C.c_int32), ("graph_launches", C.c_int64), ("tuned_ms", C.c_double)]
+
+
+BATCH_GRAPH, BATCH_TUNE, BATCH_NOWAIT = 1, 2, 4
+
 # Every entry point of include/recogs.h with its ctypes signature.
 SIGNATURES = {
     "recogs_ctx_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
@@ -82,6 +97,12 @@ SIGNATURES = {
                                      C.POINTER(C.c_int64), C.c_int]),
     "recogs_launch_count": (C.c_int64, [C.c_void_p]),
     "recogs_set_sort_path": (C.c_int, [C.c_void_p, C.c_int]),
+    "recogs_set_schedule": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "recogs_set_pair_capacity": (C.c_int, [C.c_void_p, C.c_int64]),
+    "recogs_check": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "recogs_render_batch": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.c_int32,
+                                      C.POINTER(CView), C.c_int32, C.c_uint32, C.c_void_p]),
+    "recogs_batch_info": (C.c_int, [C.c_void_p, C.POINTER(CBatchInfo)]),
 }
 
 _lib = None
@@ -328,6 +349,78 @@ class Context:
     def set_sort_path(self, path: int):
         """0 automatic, 1 per-tile shared-memory sort, 2 global radix path."""
         self._check(self._L.recogs_set_sort_path(self._h, int(path)))
+
+    def set_schedule(self, radix_classes: int = 4, blend_batch: int = 256):
+        self._check(self._L.recogs_set_schedule(self._h, int(radix_classes), int(blend_batch)))
+
+    def set_pair_capacity(self, pairs: int):
+        """> 0: frames without the mid-frame read back (see recogs.h)."""
+        self._check(self._L.recogs_set_pair_capacity(self._h, int(pairs)))
+
+    def check(self, stream=None):
+        """Wait and raise the errors recorded by frames without a read back."""
+        self._check(self._L.recogs_check(self._h, _stream_ptr(stream)))
+
+    def batch(self, scenes, views, graph=True, tune=False):
+        """A Batch of views (see Batch)."""
+        return Batch(self, scenes, views, graph=graph, tune=tune)
+
+    def batch_info(self) -> dict:
+        info = CBatchInfo()
+        self._check(self._L.recogs_batch_info(self._h, C.byref(info)))
+        return {name: getattr(info, name) for name, _ in CBatchInfo._fields_
+                if name != "reserved"}
+
+
+class Batch:
+    """recogs_render_batch over fixed scenes and views.
+
+    scenes: list of DeviceScene; views: list of dicts with keys scene (index),
+    camera, and optional edit, bg, image_out, T_out (torch CUDA tensors;
+    allocated here when absent). The ctypes arrays are built once, so each
+    call passes the same batch description and replays the plan.
+    """
+
+    def __init__(self, ctx: Context, scenes, views, graph=True, tune=False):
+        import torch
+        self.ctx = ctx
+        self.scenes = list(scenes)
+        self._cs = (CScene * max(1, len(self.scenes)))(*[sc.struct() for sc in self.scenes])
+        self._cv = (CView * max(1, len(views)))()
+        self._keep = []
+        self.images, self.T = [], []
+        for i, v in enumerate(views):
+            cam = v["camera"]
+            si = int(v["scene"])
+            sc = self.scenes[si if 0 <= si < len(self.scenes) else 0]
+            img = v.get("image_out")
+            if img is None:
+                img = torch.empty((int(cam.height), int(cam.width), 3), dtype=torch.float32,
+                                  device=sc.xyz.device)
+            T = v.get("T_out")
+            cv = self._cv[i]
+            cv.scene = int(v["scene"])
+            cv.camera = camera_struct(cam)
+            e, keep = edit_struct(v.get("edit"))
+            if e is not None:
+                self._keep.append((e, keep))
+                cv.edit = C.pointer(e)
+            bg = np.asarray(v.get("bg", (0.0, 0.0, 0.0)), np.float32)
+            for k in range(3):
+                cv.bg[k] = float(bg[k])
+            cv.image_hwc_out = img.data_ptr()
+            cv.final_T_out = T.data_ptr() if T is not None else None
+            self.images.append(img)
+            self.T.append(T)
+        self.n_views = len(views)
+        self.flags = (BATCH_GRAPH if graph else 0) | (BATCH_TUNE if tune else 0)
+
+    def __call__(self, nowait=False, stream=None):
+        f = self.flags | (BATCH_NOWAIT if nowait else 0)
+        self.ctx._check(self.ctx._L.recogs_render_batch(
+            self.ctx._h, self._cs, len(self.scenes), self._cv, self.n_views, f,
+            _stream_ptr(stream)))
+        return self.images
 
 
 def mask_words(n: int) -> int:

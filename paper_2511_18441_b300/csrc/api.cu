@@ -8,6 +8,7 @@
 //   -> compaction of visible Gaussians -> radix sort by depth
 //   -> pair offsets in depth order -> pair expansion -> radix sort by tile
 //   -> tile ranges -> per-tile blend (HWC image, Sec. 4.2).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -46,15 +47,68 @@ std::string g_create_error;
 
 }  // namespace
 
+// The device scratch of one frame in flight.
+struct Scratch {
+    DevBuf rec, count, rect, zkey, block_sums, block_offsets, counters;
+    DevBuf dkeys[2], dvals[2], sort_scratch, pair_sums, pair_offsets;
+    DevBuf tkeys[2], tvals[2], ranges, order, tile_count, cursor, tile_totals, pair_keys;
+    bool counters_ready = false;
+    void release() {
+        DevBuf* bufs[] = {&rec, &count, &rect, &zkey, &block_sums, &block_offsets, &counters,
+                          &dkeys[0], &dkeys[1], &dvals[0], &dvals[1], &sort_scratch, &pair_sums,
+                          &pair_offsets, &tkeys[0], &tkeys[1], &tvals[0], &tvals[1], &ranges,
+                          &order, &tile_count, &cursor, &tile_totals, &pair_keys};
+        for (DevBuf* b : bufs) {
+            if (b->p) cudaFree(b->p);
+            b->p = nullptr;
+            b->cap = 0;
+        }
+        counters_ready = false;
+    }
+};
+
+// How one frame is scheduled (the knobs the batch autotuner searches).
+struct Schedule {
+    int sort_path = 0;          // 0 auto, 1 per-tile shared-memory sort, 2 global radix sort
+    int64_t pair_capacity = 0;  // > 0: no mid-frame read back, pair buffers of this size
+    int radix_classes = 4;      // per-tile sort classes (largest first) sorted by radix
+    int blend_batch = 256;      // Gaussians staged per blend batch (128 or 256)
+};
+
+// One lane of a batch: its own scratch and stream, so that the frames of
+// different lanes can run concurrently.
+struct Lane {
+    Scratch sc;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    int64_t pair_capacity = 0;
+};
+
+struct ViewPlan {
+    int64_t pairs = 0;
+    uint32_t max_tile = 0;
+    double ms = 0.0;     // measured time of its planning render
+    int lane = -1;       // -1: rendered outside the graph (a tile above the per-tile limit)
+};
+
 struct recogs_ctx {
     int device = 0;
     std::string err;
-    // scratch
-    DevBuf rec, count, rect, zkey, block_sums, block_offsets, counters;
-    DevBuf dkeys[2], dvals[2], sort_scratch, pair_sums, pair_offsets;
-    bool counters_ready = false;
-    DevBuf tkeys[2], tvals[2], ranges, order, tile_count, cursor, tile_totals, pair_keys;
-    int sort_path = 0;   // 0 auto, 1 per-tile shared-memory sort, 2 global radix sort
+    Scratch main;        // scratch of recogs_render / recogs_render_host
+    Schedule sched;      // schedule of recogs_render
+    // batch planning, lanes and the captured graph
+    bool capturing = false;
+    std::vector<unsigned char> batch_sig;
+    std::vector<ViewPlan> plan;
+    std::vector<Lane> lanes;
+    Schedule batch_sched;
+    int batch_lanes = 1;
+    cudaGraphExec_t batch_exec = nullptr;
+    int64_t batch_graph_launches = 0;   // kernel launches in one replay of the graph
+    cudaStream_t origin = nullptr;      // stream the batch graph is captured on
+    cudaEvent_t fork = nullptr;
+    double batch_tuned_ms = 0.0;
+    int batch_tune_trials = 0;
     // host-memory render staging
     DevBuf hs_xyz, hs_ls, hs_q, hs_op, hs_sh, hs_img, hs_T;
     DevCounters* h_counters = nullptr;   // pinned
@@ -120,6 +174,8 @@ recogs_status cuda_check(recogs_ctx* c, cudaError_t e, const char* what) {
 recogs_status ensure(recogs_ctx* ctx, DevBuf& b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.cap >= bytes) return RECOGS_OK;
+    if (ctx->capturing)
+        return fail(ctx, RECOGS_ECAPACITY, "scratch would grow while a batch is being captured");
     if (b.p) {
         CK(cudaDeviceSynchronize());
         CK(cudaFree(b.p));
@@ -153,12 +209,17 @@ cudaEvent_t get_event(recogs_ctx* ctx) {
 }
 
 void stage_begin(recogs_ctx* ctx, cudaStream_t st) {
-    if (!ctx->timing) return;
+    if (!ctx->timing || ctx->capturing) return;
     ctx->cur_start = get_event(ctx);
     cudaEventRecord(ctx->cur_start, st);
 }
 
 void stage_end(recogs_ctx* ctx, int stage, int launches, cudaStream_t st) {
+    if (ctx->capturing) {
+        // counted once per replay of the captured graph
+        ctx->batch_graph_launches += launches;
+        return;
+    }
     ctx->launches += launches;
     ctx->stage_launches[stage] += launches;
     if (!ctx->timing || !ctx->cur_start) return;
@@ -278,9 +339,11 @@ recogs_status check_scene(recogs_ctx* ctx, const recogs_scene* s) {
 }
 
 // The frame pipeline on device-resident inputs.
-recogs_status render_device(recogs_ctx* ctx, const recogs_scene& s, const recogs_camera& cam,
+recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
+                            const recogs_scene& s, const recogs_camera& cam,
                             const recogs_edit* edit, const float bgv[3], float* image,
-                            float* final_T, recogs_render_stats* stats, cudaStream_t st) {
+                            float* final_T, recogs_render_stats* stats, cudaStream_t st,
+                            ViewPlan* plan_out = nullptr) {
     const int n = (int)s.n;
     const DevCamera dc = dev_camera(cam);
     const int tiles = dc.tiles_x * dc.tiles_y;
@@ -299,36 +362,36 @@ recogs_status render_device(recogs_ctx* ctx, const recogs_scene& s, const recogs
     }
 
     const int nb = (n + kPrepThreads - 1) / kPrepThreads;
-    CKS(ensure(ctx, ctx->counters, sizeof(DevCounters)));
-    CKS(ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)tiles));
-    CKS(ensure(ctx, ctx->order, sizeof(uint32_t) * (size_t)tiles));
-    CKS(ensure(ctx, ctx->tile_count, sizeof(uint32_t) * kTileParts * (size_t)tiles));
-    CKS(ensure(ctx, ctx->cursor, sizeof(uint32_t) * kTileParts * (size_t)tiles));
-    CKS(ensure(ctx, ctx->tile_totals, sizeof(uint32_t) * (size_t)tiles));
-    DevCounters* dctr = P<DevCounters>(ctx->counters);
-    if (!ctx->counters_ready) {
+    CKS(ensure(ctx, sc.counters, sizeof(DevCounters)));
+    CKS(ensure(ctx, sc.ranges, sizeof(uint2) * (size_t)tiles));
+    CKS(ensure(ctx, sc.order, sizeof(uint32_t) * (size_t)tiles));
+    CKS(ensure(ctx, sc.tile_count, sizeof(uint32_t) * kTileParts * (size_t)tiles));
+    CKS(ensure(ctx, sc.cursor, sizeof(uint32_t) * kTileParts * (size_t)tiles));
+    CKS(ensure(ctx, sc.tile_totals, sizeof(uint32_t) * (size_t)tiles));
+    DevCounters* dctr = P<DevCounters>(sc.counters);
+    if (!sc.counters_ready) {
         CK(cudaMemsetAsync(dctr, 0, sizeof(DevCounters), st));
-        ctx->counters_ready = true;
+        sc.counters_ready = true;
     }
     CK(cudaMemsetAsync(dctr, 0, kCountersClearBytes, st));
-    CK(cudaMemsetAsync(ctx->tile_count.p, 0, sizeof(uint32_t) * kTileParts * (size_t)tiles, st));
+    CK(cudaMemsetAsync(sc.tile_count.p, 0, sizeof(uint32_t) * kTileParts * (size_t)tiles, st));
 
     // 1. per-Gaussian pass and per-tile pair counts
     uint32_t V = 0, Pn = 0, zmin = 0, zmax = 0, max_tile = 0;
     if (n > 0) {
-        CKS(ensure(ctx, ctx->rec, sizeof(float4) * 3 * (size_t)n));
-        CKS(ensure(ctx, ctx->count, sizeof(uint32_t) * (size_t)n));
-        CKS(ensure(ctx, ctx->rect, sizeof(uint2) * (size_t)n));
-        CKS(ensure(ctx, ctx->zkey, sizeof(uint32_t) * (size_t)n));
-        CKS(ensure(ctx, ctx->block_sums, sizeof(uint32_t) * 2 * (size_t)nb));
-        CKS(ensure(ctx, ctx->block_offsets, sizeof(uint32_t) * (size_t)nb));
+        CKS(ensure(ctx, sc.rec, sizeof(float4) * 3 * (size_t)n));
+        CKS(ensure(ctx, sc.count, sizeof(uint32_t) * (size_t)n));
+        CKS(ensure(ctx, sc.rect, sizeof(uint2) * (size_t)n));
+        CKS(ensure(ctx, sc.zkey, sizeof(uint32_t) * (size_t)n));
+        CKS(ensure(ctx, sc.block_sums, sizeof(uint32_t) * 2 * (size_t)nb));
+        CKS(ensure(ctx, sc.block_offsets, sizeof(uint32_t) * (size_t)nb));
         PrepOut po;
-        po.rec = P<float4>(ctx->rec);
-        po.count = P<uint32_t>(ctx->count);
-        po.rect = P<uint2>(ctx->rect);
-        po.zkey = P<uint32_t>(ctx->zkey);
-        po.block_sums = P<uint32_t>(ctx->block_sums);
-        po.tile_count = P<uint32_t>(ctx->tile_count);
+        po.rec = P<float4>(sc.rec);
+        po.count = P<uint32_t>(sc.count);
+        po.rect = P<uint2>(sc.rect);
+        po.zkey = P<uint32_t>(sc.zkey);
+        po.block_sums = P<uint32_t>(sc.block_sums);
+        po.tile_count = P<uint32_t>(sc.tile_count);
         po.parts = kTileParts;
         po.counters = dctr;
         stage_begin(ctx, st);
@@ -340,80 +403,99 @@ recogs_status render_device(recogs_ctx* ctx, const recogs_scene& s, const recogs
     stage_begin(ctx, st);
     int l = 0;
     if (n > 0)
-        l += launch_scan_small(P<uint32_t>(ctx->block_sums), P<uint32_t>(ctx->block_offsets), nb, 1,
+        l += launch_scan_small(P<uint32_t>(sc.block_sums), P<uint32_t>(sc.block_offsets), nb, 1,
                                &dctr->n_visible, st);
-    l += launch_tile_totals(P<uint32_t>(ctx->tile_count), tiles, kTileParts,
-                            P<uint32_t>(ctx->cursor), P<uint32_t>(ctx->tile_totals), st);
-    l += launch_tile_scan(P<uint32_t>(ctx->tile_totals), tiles, P<uint2>(ctx->ranges), dctr, st);
+    l += launch_tile_totals(P<uint32_t>(sc.tile_count), tiles, kTileParts,
+                            P<uint32_t>(sc.cursor), P<uint32_t>(sc.tile_totals), st);
+    const bool async = sched.pair_capacity > 0;
+    l += launch_tile_scan(P<uint32_t>(sc.tile_totals), tiles, P<uint2>(sc.ranges), dctr,
+                          async ? (uint32_t)sched.pair_capacity : 0xffffffffu, st);
     stage_end(ctx, ST_SCAN, l, st);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(ctx->h_counters, dctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    V = ctx->h_counters->n_visible;
-    Pn = ctx->h_counters->n_pairs;
-    zmin = ~ctx->h_counters->zmin_inv;
-    zmax = ctx->h_counters->zmax;
-    max_tile = ctx->h_counters->max_tile;
-    if (ctx->h_counters->error) {
-        CK(cudaMemsetAsync(&dctr->error, 0, sizeof(uint32_t), st));
-        return fail(ctx, RECOGS_ETIMEOUT,
-                    "a bounded device wait of an earlier sort gave up; that frame is invalid");
+    if (!async) {
+        CK(cudaMemcpyAsync(ctx->h_counters, dctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        V = ctx->h_counters->n_visible;
+        Pn = ctx->h_counters->n_pairs;
+        zmin = ~ctx->h_counters->zmin_inv;
+        zmax = ctx->h_counters->zmax;
+        max_tile = ctx->h_counters->max_tile;
+        const uint32_t err = ctx->h_counters->error;
+        if (err) {
+            // a crowded tile of this frame only selects the global path below; a
+            // timed-out wait or an overflow belongs to an earlier asynchronous frame
+            CK(cudaMemsetAsync(&dctr->error, 0, sizeof(uint32_t), st));
+            if (err & kErrTimeout)
+                return fail(ctx, RECOGS_ETIMEOUT,
+                            "a bounded device wait of an earlier sort gave up; that frame is invalid");
+            if (err & kErrCapacity)
+                return fail(ctx, RECOGS_ECAPACITY,
+                            "an earlier asynchronous frame had more pairs than the pair capacity");
+        }
+        if (Pn >= (1u << 30))
+            return fail(ctx, RECOGS_ECAPACITY, "%u (tile, Gaussian) pairs exceed 2^30", Pn);
+        if (plan_out) {
+            plan_out->pairs = Pn;
+            plan_out->max_tile = max_tile;
+        }
+    } else {
+        // no read back: buffers sized by the pair capacity, sizes read on the device
+        V = (uint32_t)n;
+        Pn = (uint32_t)sched.pair_capacity;
+        max_tile = 0;
     }
-    if (Pn >= (1u << 30))
-        return fail(ctx, RECOGS_ECAPACITY, "%u (tile, Gaussian) pairs exceed 2^30", Pn);
 
     const uint32_t* ids = nullptr;
-    const bool smem_path = ctx->sort_path == 1 || (ctx->sort_path == 0 && max_tile <= kMaxSmemTile);
+    const bool smem_path =
+        async || sched.sort_path == 1 || (sched.sort_path == 0 && max_tile <= kMaxSmemTile);
     if (V > 0 && smem_path && (int)max_tile <= kMaxSmemTile) {
         // 3a. scatter (depth, index) keys into the tile ranges, sort each tile in shared memory
-        CKS(ensure(ctx, ctx->pair_keys, sizeof(unsigned long long) * (size_t)Pn));
-        CKS(ensure(ctx, ctx->tvals[0], sizeof(uint32_t) * (size_t)Pn));
+        CKS(ensure(ctx, sc.pair_keys, sizeof(unsigned long long) * (size_t)Pn));
+        CKS(ensure(ctx, sc.tvals[0], sizeof(uint32_t) * (size_t)Pn));
         stage_begin(ctx, st);
-        l = launch_scatter(P<uint32_t>(ctx->count), P<uint2>(ctx->rect), P<uint32_t>(ctx->zkey), n,
-                           dc.tiles_x, P<uint2>(ctx->ranges), P<uint32_t>(ctx->cursor), kTileParts,
-                           P<unsigned long long>(ctx->pair_keys), st);
+        l = launch_scatter(P<uint32_t>(sc.count), P<uint2>(sc.rect), P<uint32_t>(sc.zkey), n,
+                           dc.tiles_x, P<uint2>(sc.ranges), P<uint32_t>(sc.cursor), kTileParts,
+                           P<unsigned long long>(sc.pair_keys), dctr, st);
         stage_end(ctx, ST_SCATTER, l, st);
         stage_begin(ctx, st);
-        l = launch_tile_order(P<uint2>(ctx->ranges), tiles, P<uint32_t>(ctx->order), st);
+        l = launch_tile_order(P<uint2>(sc.ranges), tiles, P<uint32_t>(sc.order), st);
         stage_end(ctx, ST_TILE_ORDER, l, st);
         stage_begin(ctx, st);
         uint32_t classes[kSortClasses];
         for (int c = 0; c < kSortClasses; ++c) classes[c] = ctx->h_counters->class_tiles[c];
-        const uint32_t span = zmax - zmin;
-        const int dbits = span == 0 ? 0 : 32 - __builtin_clz(span);
-        l = launch_tile_sort(P<uint2>(ctx->ranges), P<uint32_t>(ctx->order), classes,
-                             P<unsigned long long>(ctx->pair_keys), P<uint32_t>(ctx->tvals[0]),
-                             zmin, dbits, st);
+        l = launch_tile_sort(P<uint2>(sc.ranges), P<uint32_t>(sc.order),
+                             async ? nullptr : classes, tiles, P<unsigned long long>(sc.pair_keys),
+                             P<uint32_t>(sc.tvals[0]), dctr, sched.radix_classes, st);
         stage_end(ctx, ST_TILE_SORT, l, st);
-        ids = P<uint32_t>(ctx->tvals[0]);
+        ids = P<uint32_t>(sc.tvals[0]);
         CK(cudaGetLastError());
     } else if (V > 0) {
         // 3b. global path: radix sort by depth, expand pairs in depth order,
         // stable radix sort by tile (any tile size)
         const int max_items = (int)(V > Pn ? V : Pn);
         for (int k = 0; k < 2; ++k) {
-            CKS(ensure(ctx, ctx->dkeys[k], sizeof(uint32_t) * (size_t)V));
-            CKS(ensure(ctx, ctx->dvals[k], sizeof(uint32_t) * (size_t)V));
-            CKS(ensure(ctx, ctx->tkeys[k], sizeof(uint32_t) * (size_t)Pn));
-            CKS(ensure(ctx, ctx->tvals[k], sizeof(uint32_t) * (size_t)Pn));
+            CKS(ensure(ctx, sc.dkeys[k], sizeof(uint32_t) * (size_t)V));
+            CKS(ensure(ctx, sc.dvals[k], sizeof(uint32_t) * (size_t)V));
+            CKS(ensure(ctx, sc.tkeys[k], sizeof(uint32_t) * (size_t)Pn));
+            CKS(ensure(ctx, sc.tvals[k], sizeof(uint32_t) * (size_t)Pn));
         }
-        CKS(ensure(ctx, ctx->sort_scratch, sizeof(uint32_t) * sort_scratch_words(max_items)));
+        CKS(ensure(ctx, sc.sort_scratch, sizeof(uint32_t) * sort_scratch_words(max_items)));
         const int vb = ((int)V + kEmitBlock - 1) / kEmitBlock;
-        CKS(ensure(ctx, ctx->pair_sums, sizeof(uint32_t) * (size_t)vb));
-        CKS(ensure(ctx, ctx->pair_offsets, sizeof(uint32_t) * (size_t)vb));
+        CKS(ensure(ctx, sc.pair_sums, sizeof(uint32_t) * (size_t)vb));
+        CKS(ensure(ctx, sc.pair_offsets, sizeof(uint32_t) * (size_t)vb));
 
         stage_begin(ctx, st);
-        l = launch_compact(P<uint32_t>(ctx->count), P<uint32_t>(ctx->zkey), n,
-                           P<uint32_t>(ctx->block_offsets), dctr, P<uint32_t>(ctx->dkeys[0]),
-                           P<uint32_t>(ctx->dvals[0]), st);
+        l = launch_compact(P<uint32_t>(sc.count), P<uint32_t>(sc.zkey), n,
+                           P<uint32_t>(sc.block_offsets), dctr, P<uint32_t>(sc.dkeys[0]),
+                           P<uint32_t>(sc.dvals[0]), st);
         stage_end(ctx, ST_COMPACT, l, st);
 
         SortBuffers sb;
-        sb.keys[0] = P<uint32_t>(ctx->dkeys[0]);
-        sb.keys[1] = P<uint32_t>(ctx->dkeys[1]);
-        sb.vals[0] = P<uint32_t>(ctx->dvals[0]);
-        sb.vals[1] = P<uint32_t>(ctx->dvals[1]);
-        sb.scratch = P<uint32_t>(ctx->sort_scratch);
+        sb.keys[0] = P<uint32_t>(sc.dkeys[0]);
+        sb.keys[1] = P<uint32_t>(sc.dkeys[1]);
+        sb.vals[0] = P<uint32_t>(sc.dvals[0]);
+        sb.vals[1] = P<uint32_t>(sc.dvals[1]);
+        sb.scratch = P<uint32_t>(sc.sort_scratch);
         sb.error = &dctr->error;
         const uint32_t span = zmax - zmin;
         const int dbits = span == 0 ? 0 : 32 - __builtin_clz(span);
@@ -426,23 +508,23 @@ recogs_status render_device(recogs_ctx* ctx, const recogs_scene& s, const recogs
         stage_begin(ctx, st);
         // the depth sort's spare key buffer holds the counts in depth order
         uint32_t* counts_sorted = sb.keys[dcur ^ 1];
-        l = launch_pair_block_sums(sorted, P<uint32_t>(ctx->count), (int)V, counts_sorted,
-                                   P<uint32_t>(ctx->pair_sums), st);
-        l += launch_scan_small(P<uint32_t>(ctx->pair_sums), P<uint32_t>(ctx->pair_offsets), vb, 1,
+        l = launch_pair_block_sums(sorted, P<uint32_t>(sc.count), (int)V, counts_sorted,
+                                   P<uint32_t>(sc.pair_sums), st);
+        l += launch_scan_small(P<uint32_t>(sc.pair_sums), P<uint32_t>(sc.pair_offsets), vb, 1,
                                nullptr, st);
         stage_end(ctx, ST_PAIR_OFFSETS, l, st);
 
         stage_begin(ctx, st);
-        l = launch_emit(sorted, counts_sorted, P<uint2>(ctx->rect), (int)V,
-                        P<uint32_t>(ctx->pair_offsets), dc.tiles_x, P<uint32_t>(ctx->tkeys[0]),
-                        P<uint32_t>(ctx->tvals[0]), st);
+        l = launch_emit(sorted, counts_sorted, P<uint2>(sc.rect), (int)V,
+                        P<uint32_t>(sc.pair_offsets), dc.tiles_x, P<uint32_t>(sc.tkeys[0]),
+                        P<uint32_t>(sc.tvals[0]), st);
         stage_end(ctx, ST_EMIT, l, st);
 
         SortBuffers tb = sb;
-        tb.keys[0] = P<uint32_t>(ctx->tkeys[0]);
-        tb.keys[1] = P<uint32_t>(ctx->tkeys[1]);
-        tb.vals[0] = P<uint32_t>(ctx->tvals[0]);
-        tb.vals[1] = P<uint32_t>(ctx->tvals[1]);
+        tb.keys[0] = P<uint32_t>(sc.tkeys[0]);
+        tb.keys[1] = P<uint32_t>(sc.tkeys[1]);
+        tb.vals[0] = P<uint32_t>(sc.tvals[0]);
+        tb.vals[1] = P<uint32_t>(sc.tvals[1]);
         const int tbits = tiles <= 1 ? 0 : 32 - __builtin_clz((uint32_t)(tiles - 1));
         stage_begin(ctx, st);
         l = 0;
@@ -450,41 +532,376 @@ recogs_status render_device(recogs_ctx* ctx, const recogs_scene& s, const recogs
         stage_end(ctx, ST_SORT_TILE, l, st);
         ids = tb.vals[tcur];
         stage_begin(ctx, st);
-        l = launch_tile_order(P<uint2>(ctx->ranges), tiles, P<uint32_t>(ctx->order), st);
+        l = launch_tile_order(P<uint2>(sc.ranges), tiles, P<uint32_t>(sc.order), st);
         stage_end(ctx, ST_TILE_ORDER, l, st);
         CK(cudaGetLastError());
     } else {
         stage_begin(ctx, st);
-        l = launch_tile_order(P<uint2>(ctx->ranges), tiles, P<uint32_t>(ctx->order), st);
+        l = launch_tile_order(P<uint2>(sc.ranges), tiles, P<uint32_t>(sc.order), st);
         stage_end(ctx, ST_TILE_ORDER, l, st);
     }
     if (!ids) {
-        CKS(ensure(ctx, ctx->tvals[0], 16));
-        ids = P<uint32_t>(ctx->tvals[0]);
+        CKS(ensure(ctx, sc.tvals[0], 16));
+        ids = P<uint32_t>(sc.tvals[0]);
     }
-    if (n == 0) CKS(ensure(ctx, ctx->rec, 16 * 3));
+    if (n == 0) CKS(ensure(ctx, sc.rec, 16 * 3));
 
     // 4. blend
     stage_begin(ctx, st);
-    l = launch_blend(P<uint2>(ctx->ranges), P<uint32_t>(ctx->order), ids, P<float4>(ctx->rec), dc,
-                     bgv, image, final_T, dctr, st);
+    l = launch_blend(P<uint2>(sc.ranges), P<uint32_t>(sc.order), ids, P<float4>(sc.rec), dc,
+                     bgv, image, final_T, dctr, sched.blend_batch, st);
     stage_end(ctx, ST_BLEND, l, st);
     CK(cudaGetLastError());
 
     ctx->last_pairs = Pn;
     ctx->last_tiles = tiles;
     ctx->last_ids = ids;
-    ctx->last_ranges = P<uint2>(ctx->ranges);
+    ctx->last_ranges = P<uint2>(sc.ranges);
 
     if (stats) {
         CK(cudaMemcpyAsync(ctx->h_counters, dctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        if (async) {
+            V = ctx->h_counters->n_visible;
+            Pn = ctx->h_counters->n_pairs;
+            ctx->last_pairs = Pn;
+            const uint32_t err = ctx->h_counters->error;
+            if (err) {
+                CK(cudaMemsetAsync(&dctr->error, 0, sizeof(uint32_t), st));
+                return fail(ctx, (err & kErrTimeout) ? RECOGS_ETIMEOUT : RECOGS_ECAPACITY,
+                            "this frame overflowed the pair capacity or a tile's sort limit");
+            }
+        }
         stats->n_visible = V;
         stats->n_pairs = Pn;
         stats->n_pairs_read = (int64_t)ctx->h_counters->pairs_read;
         stats->n_tiles = tiles;
         stats->reserved = 0;
     }
+    return RECOGS_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batches of views (recogs_render_batch)
+//
+// A batch is planned once per distinct batch description (its signature: the
+// scene structs, the view structs and the edits' contents). Planning renders
+// every view once on the context's own scratch with the per-frame read back;
+// that gives each view's pair count and most crowded tile. The views are then
+// spread over lanes (longest measured first, each to the least loaded lane);
+// a lane owns scratch sized for its largest view, with headroom, and a stream.
+// In a lane the views run one after the other without any read back (the
+// tile-scan kernel raises a flag that makes the later kernels skip a frame
+// whose pairs exceed the lane's buffers, and records the error); lanes run
+// concurrently. The whole enqueue is captured once as a CUDA graph and each
+// later call replays it. Views with a tile above the per-tile sort's limit
+// need the read back and the global sort; they are rendered after the graph
+// on the context's scratch.
+
+void release_batch(recogs_ctx* ctx) {
+    if (ctx->batch_exec) {
+        cudaGraphExecDestroy(ctx->batch_exec);
+        ctx->batch_exec = nullptr;
+    }
+    for (Lane& l : ctx->lanes) {
+        if (l.stream) cudaStreamSynchronize(l.stream);
+        l.sc.release();
+        if (l.stream) cudaStreamDestroy(l.stream);
+        if (l.done) cudaEventDestroy(l.done);
+    }
+    ctx->lanes.clear();
+    ctx->batch_sig.clear();
+    ctx->plan.clear();
+    ctx->batch_graph_launches = 0;
+}
+
+void sig_put(std::vector<unsigned char>& v, const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    v.insert(v.end(), b, b + n);
+}
+
+std::vector<unsigned char> batch_signature(const recogs_scene* scenes, int n_scenes,
+                                           const recogs_view* views, int n_views, uint32_t flags) {
+    std::vector<unsigned char> v;
+    const uint32_t f = flags & (RECOGS_BATCH_GRAPH | RECOGS_BATCH_TUNE);
+    sig_put(v, &f, sizeof(f));
+    sig_put(v, &n_scenes, sizeof(n_scenes));
+    sig_put(v, scenes, sizeof(recogs_scene) * (size_t)n_scenes);
+    sig_put(v, &n_views, sizeof(n_views));
+    for (int i = 0; i < n_views; ++i) {
+        recogs_view w = views[i];
+        const recogs_edit* e = w.edit;
+        w.edit = nullptr;
+        sig_put(v, &w, sizeof(w));
+        const unsigned char has = e ? 1 : 0;
+        sig_put(v, &has, 1);
+        if (!e) continue;
+        const unsigned char has_cam = e->select_camera ? 1 : 0;
+        sig_put(v, &has_cam, 1);
+        if (e->select_camera) sig_put(v, e->select_camera, sizeof(recogs_camera));
+        sig_put(v, &e->region.kind, sizeof(int32_t));
+        sig_put(v, &e->region.n_vertices, sizeof(int32_t));
+        const int nf = e->region.kind == RECOGS_REGION_BOX ? 4
+                       : (e->region.n_vertices > 0 && e->region.n_vertices <= RECOGS_MAX_POLYGON)
+                           ? 2 * e->region.n_vertices
+                           : 0;
+        if (e->region.xy && nf) sig_put(v, e->region.xy, sizeof(float) * nf);
+        sig_put(v, &e->tint, sizeof(recogs_tint));
+    }
+    return v;
+}
+
+recogs_status check_view(recogs_ctx* ctx, const recogs_view& v, int n_scenes, int i) {
+    if (v.scene < 0 || v.scene >= n_scenes)
+        return fail(ctx, RECOGS_EINVAL, "view %d: scene index %d outside 0..%d", i, v.scene,
+                    n_scenes - 1);
+    CKS(check_camera(ctx, &v.camera, "view camera"));
+    if (!v.image_hwc_out || !aligned(v.image_hwc_out, 4))
+        return fail(ctx, RECOGS_EINVAL, "view %d: image_hwc_out is NULL or misaligned", i);
+    if (v.final_T_out && !aligned(v.final_T_out, 4))
+        return fail(ctx, RECOGS_EINVAL, "view %d: final_T_out is misaligned", i);
+    for (int k = 0; k < 3; ++k)
+        if (!finite(v.bg[k])) return fail(ctx, RECOGS_EINVAL, "view %d: bg not finite", i);
+    return RECOGS_OK;
+}
+
+// Enqueue every lane's views on `origin`: the lanes fork from and join back
+// into it. Works both eagerly and under stream capture.
+recogs_status enqueue_lanes(recogs_ctx* ctx, const recogs_scene* scenes, const recogs_view* views,
+                            int n_views, cudaStream_t origin) {
+    CK(cudaEventRecord(ctx->fork, origin));
+    for (Lane& l : ctx->lanes) CK(cudaStreamWaitEvent(l.stream, ctx->fork, 0));
+    for (size_t li = 0; li < ctx->lanes.size(); ++li) {
+        Lane& l = ctx->lanes[li];
+        Schedule sched = ctx->batch_sched;
+        sched.pair_capacity = l.pair_capacity;
+        sched.sort_path = 1;
+        for (int i = 0; i < n_views; ++i) {
+            if (ctx->plan[i].lane != (int)li) continue;
+            const recogs_view& v = views[i];
+            CKS(render_device(ctx, l.sc, sched, scenes[v.scene], v.camera, v.edit, v.bg,
+                              v.image_hwc_out, v.final_T_out, nullptr, l.stream));
+        }
+        CK(cudaEventRecord(l.done, l.stream));
+        CK(cudaStreamWaitEvent(origin, l.done, 0));
+    }
+    return RECOGS_OK;
+}
+
+// Views outside the lanes (a tile above the per-tile sort's limit): rendered
+// with the read back on the context's scratch.
+recogs_status render_crowded(recogs_ctx* ctx, const recogs_scene* scenes, const recogs_view* views,
+                             int n_views, cudaStream_t st) {
+    Schedule sched = ctx->sched;
+    sched.pair_capacity = 0;
+    for (int i = 0; i < n_views; ++i) {
+        if (ctx->plan[i].lane >= 0) continue;
+        const recogs_view& v = views[i];
+        CKS(render_device(ctx, ctx->main, sched, scenes[v.scene], v.camera, v.edit, v.bg,
+                          v.image_hwc_out, v.final_T_out, nullptr, st));
+    }
+    return RECOGS_OK;
+}
+
+// Read and clear the error bits of every lane (waits for the lanes).
+recogs_status lane_errors(recogs_ctx* ctx, uint32_t* bits) {
+    *bits = 0;
+    for (Lane& l : ctx->lanes) {
+        if (!l.sc.counters.p) continue;
+        CK(cudaStreamSynchronize(l.stream));
+        DevCounters* d = P<DevCounters>(l.sc.counters);
+        CK(cudaMemcpyAsync(ctx->h_counters, d, sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                           l.stream));
+        CK(cudaStreamSynchronize(l.stream));
+        const uint32_t e = ctx->h_counters->error;
+        if (e) {
+            CK(cudaMemsetAsync(&d->error, 0, sizeof(uint32_t), l.stream));
+            CK(cudaStreamSynchronize(l.stream));
+        }
+        *bits |= e;
+    }
+    return RECOGS_OK;
+}
+
+recogs_status lane_error_status(recogs_ctx* ctx, uint32_t bits) {
+    if (bits & kErrTimeout)
+        return fail(ctx, RECOGS_ETIMEOUT, "a bounded device wait gave up; the batch is invalid");
+    if (bits & (kErrCapacity | kErrCrowded))
+        return fail(ctx, RECOGS_ECAPACITY,
+                    "a view outgrew its lane's pair buffers or the per-tile sort limit; "
+                    "its image holds the background only");
+    return RECOGS_OK;
+}
+
+// Assign the lane views to `n_lanes` lanes (longest first to the least
+// loaded lane) and size each lane's pair buffers.
+recogs_status make_lanes(recogs_ctx* ctx, int n_lanes, int n_views) {
+    for (Lane& l : ctx->lanes) {
+        if (l.stream) cudaStreamSynchronize(l.stream);
+        l.sc.release();
+        if (l.stream) cudaStreamDestroy(l.stream);
+        if (l.done) cudaEventDestroy(l.done);
+    }
+    ctx->lanes.assign((size_t)n_lanes, Lane());
+    for (Lane& l : ctx->lanes) {
+        CK(cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming));
+    }
+    std::vector<int> idx;
+    for (int i = 0; i < n_views; ++i)
+        if (ctx->plan[i].max_tile <= (uint32_t)kMaxSmemTile) idx.push_back(i);
+        else ctx->plan[i].lane = -1;
+    std::sort(idx.begin(), idx.end(),
+              [&](int a, int b) { return ctx->plan[a].ms > ctx->plan[b].ms; });
+    std::vector<double> load((size_t)n_lanes, 0.0);
+    for (int i : idx) {
+        int best = 0;
+        for (int k = 1; k < n_lanes; ++k)
+            if (load[k] < load[best]) best = k;
+        ctx->plan[i].lane = best;
+        load[best] += ctx->plan[i].ms;
+        Lane& l = ctx->lanes[best];
+        const int64_t want = ctx->plan[i].pairs + ctx->plan[i].pairs / 16 + 4096;
+        if (want > l.pair_capacity) l.pair_capacity = want;
+    }
+    for (Lane& l : ctx->lanes)
+        if (l.pair_capacity > 0xfffffffell) l.pair_capacity = 0xfffffffell;
+    return RECOGS_OK;
+}
+
+// Render the lanes once eagerly (allocates their scratch) and capture the
+// graph if asked.
+recogs_status build_lanes(recogs_ctx* ctx, const recogs_scene* scenes, const recogs_view* views,
+                          int n_views, bool graph) {
+    if (ctx->batch_exec) {
+        cudaGraphExecDestroy(ctx->batch_exec);
+        ctx->batch_exec = nullptr;
+    }
+    CKS(enqueue_lanes(ctx, scenes, views, n_views, ctx->origin));
+    CK(cudaStreamSynchronize(ctx->origin));
+    uint32_t bits = 0;
+    CKS(lane_errors(ctx, &bits));
+    CKS(lane_error_status(ctx, bits));
+    if (!graph) return RECOGS_OK;
+    ctx->batch_graph_launches = 0;
+    ctx->capturing = true;
+    CK(cudaStreamBeginCapture(ctx->origin, cudaStreamCaptureModeThreadLocal));
+    const recogs_status s = enqueue_lanes(ctx, scenes, views, n_views, ctx->origin);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->origin, &g);
+    ctx->capturing = false;
+    if (s != RECOGS_OK) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return s;
+    }
+    CK(e);
+    const cudaError_t ei = cudaGraphInstantiate(&ctx->batch_exec, g, 0);
+    cudaGraphDestroy(g);
+    CK(ei);
+    return RECOGS_OK;
+}
+
+// One timed run of the planned batch on the origin stream (ms).
+recogs_status time_batch(recogs_ctx* ctx, const recogs_scene* scenes, const recogs_view* views,
+                         int n_views, int reps, double* ms) {
+    cudaEvent_t a = get_event(ctx), b = get_event(ctx);
+    float best = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+        CK(cudaEventRecord(a, ctx->origin));
+        if (ctx->batch_exec) CK(cudaGraphLaunch(ctx->batch_exec, ctx->origin));
+        else CKS(enqueue_lanes(ctx, scenes, views, n_views, ctx->origin));
+        CK(cudaEventRecord(b, ctx->origin));
+        CK(cudaEventSynchronize(b));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, a, b));
+        if (t < best) best = t;
+    }
+    ctx->event_pool.push_back(a);
+    ctx->event_pool.push_back(b);
+    *ms = best;
+    return RECOGS_OK;
+}
+
+recogs_status plan_batch(recogs_ctx* ctx, const recogs_scene* scenes, int n_scenes,
+                         const recogs_view* views, int n_views, uint32_t flags, cudaStream_t st) {
+    release_batch(ctx);
+    if (!ctx->origin) CK(cudaStreamCreateWithFlags(&ctx->origin, cudaStreamNonBlocking));
+    if (!ctx->fork) CK(cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming));
+    // 1. planning renders (these also produce this call's images)
+    ctx->plan.assign((size_t)n_views, ViewPlan());
+    Schedule plain;
+    cudaEvent_t a = get_event(ctx), b = get_event(ctx);
+    for (int i = 0; i < n_views; ++i) {
+        const recogs_view& v = views[i];
+        CK(cudaEventRecord(a, st));
+        CKS(render_device(ctx, ctx->main, plain, scenes[v.scene], v.camera, v.edit, v.bg,
+                          v.image_hwc_out, v.final_T_out, nullptr, st, &ctx->plan[i]));
+        CK(cudaEventRecord(b, st));
+        CK(cudaEventSynchronize(b));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, a, b));
+        ctx->plan[i].ms = t;
+    }
+    ctx->event_pool.push_back(a);
+    ctx->event_pool.push_back(b);
+    (void)n_scenes;
+    // 2. lanes, schedule and graph; the autotuner searches the lane count,
+    // the per-tile sort's radix classes and the blend batch, one knob at a time
+    int lane_views = 0;
+    for (int i = 0; i < n_views; ++i)
+        if (ctx->plan[i].max_tile <= (uint32_t)kMaxSmemTile) ++lane_views;
+    const bool graph = (flags & RECOGS_BATCH_GRAPH) != 0;
+    ctx->batch_sched = Schedule();
+    ctx->batch_lanes = lane_views >= 2 ? 2 : 1;
+    ctx->batch_tune_trials = 0;
+    ctx->batch_tuned_ms = 0.0;
+    if (lane_views > 0 && (flags & RECOGS_BATCH_TUNE)) {
+        double best_ms = 1e300;
+        auto trial = [&](int lanes, const Schedule& sc, bool* better) -> recogs_status {
+            ctx->batch_sched = sc;
+            CKS(make_lanes(ctx, lanes, n_views));
+            CKS(build_lanes(ctx, scenes, views, n_views, graph));
+            double ms = 0.0;
+            CKS(time_batch(ctx, scenes, views, n_views, 3, &ms));
+            ++ctx->batch_tune_trials;
+            *better = ms < best_ms;
+            if (*better) best_ms = ms;
+            return RECOGS_OK;
+        };
+        int best_lanes = 1;
+        Schedule best = Schedule();
+        bool better = false;
+        const int lane_opts[3] = {1, 2, 4};
+        for (int lanes : lane_opts) {
+            if (lanes > 1 && lanes > lane_views) break;
+            CKS(trial(lanes, best, &better));
+            if (better) best_lanes = lanes;
+        }
+        const int radix_opts[2] = {3, 5};
+        for (int rc : radix_opts) {
+            Schedule sc = best;
+            sc.radix_classes = rc;
+            CKS(trial(best_lanes, sc, &better));
+            if (better) best.radix_classes = rc;
+        }
+        {
+            Schedule sc = best;
+            sc.blend_batch = 128;
+            CKS(trial(best_lanes, sc, &better));
+            if (better) best.blend_batch = 128;
+        }
+        ctx->batch_sched = best;
+        ctx->batch_lanes = best_lanes;
+        ctx->batch_tuned_ms = best_ms;
+    }
+    CKS(make_lanes(ctx, ctx->batch_lanes, n_views));
+    CKS(build_lanes(ctx, scenes, views, n_views, graph));
+    ctx->batch_sig = batch_signature(scenes, n_scenes, views, n_views, flags);
+    // the lane renders ran on the origin stream: order the caller's stream after them
+    CK(cudaEventRecord(ctx->fork, ctx->origin));
+    CK(cudaStreamWaitEvent(st, ctx->fork, 0));
     return RECOGS_OK;
 }
 
@@ -544,14 +961,12 @@ void recogs_ctx_destroy(recogs_ctx* ctx) {
     if (!ctx) return;
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
-    DevBuf* bufs[] = {&ctx->rec, &ctx->count, &ctx->rect, &ctx->zkey, &ctx->block_sums,
-                      &ctx->block_offsets, &ctx->counters, &ctx->dkeys[0], &ctx->dkeys[1],
-                      &ctx->dvals[0], &ctx->dvals[1], &ctx->sort_scratch,
-                      &ctx->pair_sums, &ctx->pair_offsets, &ctx->tkeys[0], &ctx->tkeys[1],
-                      &ctx->tvals[0], &ctx->tvals[1], &ctx->ranges, &ctx->order, &ctx->tile_count,
-                      &ctx->cursor, &ctx->tile_totals, &ctx->pair_keys, &ctx->hs_xyz,
-                      &ctx->hs_ls,
-                      &ctx->hs_q, &ctx->hs_op, &ctx->hs_sh, &ctx->hs_img, &ctx->hs_T};
+    ctx->main.release();
+    release_batch(ctx);
+    if (ctx->origin) cudaStreamDestroy(ctx->origin);
+    if (ctx->fork) cudaEventDestroy(ctx->fork);
+    DevBuf* bufs[] = {&ctx->hs_xyz, &ctx->hs_ls, &ctx->hs_q, &ctx->hs_op, &ctx->hs_sh,
+                      &ctx->hs_img, &ctx->hs_T};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
@@ -627,8 +1042,8 @@ recogs_status recogs_render(recogs_ctx* ctx, const recogs_scene* scene,
             bgv[k] = bg[k];
         }
     DeviceGuard g(ctx->device);
-    return render_device(ctx, *scene, *camera, edit, bgv, image_hwc_out, final_T_out, stats,
-                         (cudaStream_t)stream);
+    return render_device(ctx, ctx->main, ctx->sched, *scene, *camera, edit, bgv, image_hwc_out,
+                         final_T_out, stats, (cudaStream_t)stream);
 }
 
 recogs_status recogs_render_host(recogs_ctx* ctx, const recogs_scene* hs,
@@ -673,7 +1088,7 @@ recogs_status recogs_render_host(recogs_ctx* ctx, const recogs_scene* hs,
         CK(cudaMemcpyAsync(ds.sh, hs->sh, shb, cudaMemcpyHostToDevice, st));
     }
     stage_end(ctx, ST_H2D, 0, st);
-    CKS(render_device(ctx, ds, *camera, edit, bgv, P<float>(ctx->hs_img),
+    CKS(render_device(ctx, ctx->main, ctx->sched, ds, *camera, edit, bgv, P<float>(ctx->hs_img),
                       final_T_host ? P<float>(ctx->hs_T) : nullptr, stats, st));
     stage_begin(ctx, st);
     CK(cudaMemcpyAsync(image_hwc_host, ctx->hs_img.p, 12 * npix, cudaMemcpyDeviceToHost, st));
@@ -736,7 +1151,109 @@ int64_t recogs_launch_count(const recogs_ctx* ctx) { return ctx ? ctx->launches 
 recogs_status recogs_set_sort_path(recogs_ctx* ctx, int path) {
     if (!ctx) return RECOGS_EINVAL;
     if (path < 0 || path > 2) return fail(ctx, RECOGS_EINVAL, "sort path must be 0, 1 or 2");
-    ctx->sort_path = path;
+    ctx->sched.sort_path = path;
+    return RECOGS_OK;
+}
+
+recogs_status recogs_set_pair_capacity(recogs_ctx* ctx, int64_t pairs) {
+    if (!ctx) return RECOGS_EINVAL;
+    if (pairs < 0 || pairs > 0xfffffffell)
+        return fail(ctx, RECOGS_EINVAL, "pair capacity %lld outside 0..2^28-1", (long long)pairs);
+    ctx->sched.pair_capacity = pairs;
+    return RECOGS_OK;
+}
+
+recogs_status recogs_set_schedule(recogs_ctx* ctx, int32_t radix_classes, int32_t blend_batch) {
+    if (!ctx) return RECOGS_EINVAL;
+    if (radix_classes < 0 || radix_classes > 5)
+        return fail(ctx, RECOGS_EINVAL, "radix_classes must be 0..5, got %d", radix_classes);
+    if (blend_batch != 128 && blend_batch != 256)
+        return fail(ctx, RECOGS_EINVAL, "blend_batch must be 128 or 256, got %d", blend_batch);
+    ctx->sched.radix_classes = radix_classes;
+    ctx->sched.blend_batch = blend_batch;
+    return RECOGS_OK;
+}
+
+recogs_status recogs_check(recogs_ctx* ctx, void* stream) {
+    if (!ctx) return RECOGS_EINVAL;
+    DeviceGuard g(ctx->device);
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    uint32_t bits = 0;
+    if (ctx->main.counters.p) {
+        DevCounters* d = P<DevCounters>(ctx->main.counters);
+        CK(cudaMemcpy(ctx->h_counters, d, sizeof(DevCounters), cudaMemcpyDeviceToHost));
+        bits = ctx->h_counters->error;
+        if (bits) CK(cudaMemset(&d->error, 0, sizeof(uint32_t)));
+        // a crowded tile of a frame with the read back took the global path
+        if (ctx->sched.pair_capacity == 0) bits &= ~kErrCrowded;
+    }
+    uint32_t lb = 0;
+    CKS(lane_errors(ctx, &lb));
+    bits |= lb;
+    if (bits & kErrTimeout)
+        return fail(ctx, RECOGS_ETIMEOUT, "a bounded device wait gave up; that frame is invalid");
+    if (bits & (kErrCapacity | kErrCrowded))
+        return fail(ctx, RECOGS_ECAPACITY,
+                    "a frame without read back had more pairs than its pair buffers, or a tile "
+                    "above the per-tile sort limit; that image holds the background only");
+    return RECOGS_OK;
+}
+
+recogs_status recogs_render_batch(recogs_ctx* ctx, const recogs_scene* scenes, int32_t n_scenes,
+                                  const recogs_view* views, int32_t n_views, uint32_t flags,
+                                  void* stream) {
+    if (!ctx) return RECOGS_EINVAL;
+    if (n_scenes < 0 || n_views < 0 || (n_scenes > 0 && !scenes) || (n_views > 0 && !views))
+        return fail(ctx, RECOGS_EINVAL, "scenes or views NULL or counts negative");
+    if (flags & ~(uint32_t)(RECOGS_BATCH_GRAPH | RECOGS_BATCH_TUNE | RECOGS_BATCH_NOWAIT))
+        return fail(ctx, RECOGS_EINVAL, "unknown batch flags 0x%x", flags);
+    for (int k = 0; k < n_scenes; ++k) CKS(check_scene(ctx, &scenes[k]));
+    for (int i = 0; i < n_views; ++i) CKS(check_view(ctx, views[i], n_scenes, i));
+    if (n_views == 0) return RECOGS_OK;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const std::vector<unsigned char> sig = batch_signature(scenes, n_scenes, views, n_views, flags);
+    if (sig != ctx->batch_sig) return plan_batch(ctx, scenes, n_scenes, views, n_views, flags, st);
+    // replay: the lanes (graph or eager) after the caller's earlier work, then
+    // the views that need the read back
+    if (ctx->batch_exec) {
+        CK(cudaGraphLaunch(ctx->batch_exec, st));
+        ctx->launches += ctx->batch_graph_launches;
+    } else {
+        CK(cudaEventRecord(ctx->fork, st));
+        CK(cudaStreamWaitEvent(ctx->origin, ctx->fork, 0));
+        CKS(enqueue_lanes(ctx, scenes, views, n_views, ctx->origin));
+        CK(cudaEventRecord(ctx->fork, ctx->origin));
+        CK(cudaStreamWaitEvent(st, ctx->fork, 0));
+    }
+    CKS(render_crowded(ctx, scenes, views, n_views, st));
+    if (flags & RECOGS_BATCH_NOWAIT) return RECOGS_OK;
+    CK(cudaStreamSynchronize(st));
+    uint32_t bits = 0;
+    CKS(lane_errors(ctx, &bits));
+    if (bits & (kErrCapacity | kErrCrowded)) {
+        // a view outgrew its lane: plan again (which renders every view again)
+        ctx->batch_sig.clear();
+        return plan_batch(ctx, scenes, n_scenes, views, n_views, flags, st);
+    }
+    return lane_error_status(ctx, bits);
+}
+
+recogs_status recogs_batch_info(recogs_ctx* ctx, recogs_batch_info_t* info) {
+    if (!ctx || !info) return RECOGS_EINVAL;
+    memset(info, 0, sizeof(*info));
+    info->planned = ctx->batch_sig.empty() ? 0 : 1;
+    info->graph = ctx->batch_exec ? 1 : 0;
+    info->lanes = (int32_t)ctx->lanes.size();
+    info->radix_classes = ctx->batch_sched.radix_classes;
+    info->blend_batch = ctx->batch_sched.blend_batch;
+    info->tune_trials = ctx->batch_tune_trials;
+    info->graph_launches = ctx->batch_graph_launches;
+    info->tuned_ms = ctx->batch_tuned_ms;
+    int crowded = 0;
+    for (const ViewPlan& p : ctx->plan)
+        if (p.lane < 0) ++crowded;
+    info->views_outside_lanes = crowded;
     return RECOGS_OK;
 }
 

@@ -64,7 +64,8 @@ __device__ __forceinline__ int sort_class(uint32_t c) {
 
 __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restrict__ totals,
                                                          int tiles, uint2* __restrict__ ranges,
-                                                         DevCounters* __restrict__ ctr) {
+                                                         DevCounters* __restrict__ ctr,
+                                                         uint32_t capacity) {
     __shared__ uint32_t s_warp[33];
     __shared__ uint32_t s_max[32];
     __shared__ uint32_t s_cls[kSortClasses];
@@ -112,12 +113,22 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restr
         ctr->max_tile = m;
         ctr->n_pairs = carry > 0xffffffffull ? 0xffffffffu : (uint32_t)carry;
         for (int c = 0; c < kSortClasses; ++c) ctr->class_tiles[c] = s_cls[c];
+        // the pair buffers hold `capacity` pairs: more and the frame is skipped
+        if (carry > (unsigned long long)capacity) {
+            ctr->skip = 1u;
+            atomicOr(&ctr->error, kErrCapacity);
+        }
+        if (m > (uint32_t)kMaxSmemTile) {
+            atomicOr(&ctr->error, kErrCrowded);
+            // without a read back there is no switch to the global path: skip
+            if (capacity != 0xffffffffu) ctr->skip = 1u;
+        }
     }
 }
 
 int launch_tile_scan(const uint32_t* totals, int tiles, uint2* ranges, DevCounters* counters,
-                     cudaStream_t st) {
-    tile_scan_kernel<<<1, 1024, 0, st>>>(totals, tiles, ranges, counters);
+                     uint32_t capacity, cudaStream_t st) {
+    tile_scan_kernel<<<1, 1024, 0, st>>>(totals, tiles, ranges, counters, capacity);
     return 1;
 }
 
@@ -143,9 +154,10 @@ __global__ void __launch_bounds__(kScatterThreads)
     scatter_kernel(const uint32_t* __restrict__ count, const uint2* __restrict__ rect,
                    const uint32_t* __restrict__ zkey, int n, int tiles_x,
                    const uint2* __restrict__ ranges, uint32_t* __restrict__ cursor, int parts,
-                   unsigned long long* __restrict__ keys) {
+                   unsigned long long* __restrict__ keys, const DevCounters* __restrict__ ctr) {
     __shared__ uint32_t s_tile[kHashSlots];
     __shared__ uint32_t s_cnt[kHashSlots];
+    if (*reinterpret_cast<const volatile uint32_t*>(&ctr->skip)) return;  // pairs exceed the buffers
     for (int k = threadIdx.x; k < kHashSlots; k += kScatterThreads) {
         s_tile[k] = kEmptySlot;
         s_cnt[k] = 0;
@@ -218,10 +230,10 @@ __global__ void __launch_bounds__(kScatterThreads)
 
 int launch_scatter(const uint32_t* count, const uint2* rect, const uint32_t* zkey, int n,
                    int tiles_x, const uint2* ranges, uint32_t* cursor, int parts,
-                   unsigned long long* keys, cudaStream_t st) {
+                   unsigned long long* keys, const DevCounters* counters, cudaStream_t st) {
     if (n == 0) return 0;
     scatter_kernel<<<(n + kScatterThreads - 1) / kScatterThreads, kScatterThreads, 0, st>>>(
-        count, rect, zkey, n, tiles_x, ranges, cursor, parts, keys);
+        count, rect, zkey, n, tiles_x, ranges, cursor, parts, keys, counters);
     return 1;
 }
 
@@ -250,16 +262,25 @@ __device__ __forceinline__ void in_thread_stage(unsigned long long (&v)[8], int 
     }
 }
 
+// Tiles of sort class `cls`: their count and their first position in the
+// tile order (classes follow each other from the largest CTA down).
+__device__ __forceinline__ void class_span(const DevCounters* ctr, int cls, uint32_t& count,
+                                           uint32_t& first) {
+    first = 0;
+    for (int c = 0; c < cls; ++c) first += ctr->class_tiles[c];
+    count = ctr->class_tiles[cls];
+}
+
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS)
-    tile_sort_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
-                     const unsigned long long* __restrict__ keys, uint32_t* __restrict__ ids) {
+__device__ __forceinline__ void tile_sort_one(const uint2* __restrict__ ranges, int tile,
+                                              const unsigned long long* __restrict__ keys,
+                                              uint32_t* __restrict__ ids) {
     constexpr int E = 8;
     constexpr int NPAD = E * THREADS;
     extern __shared__ unsigned long long s[];   // NPAD keys when THREADS > 32
-    const int tile = (int)order[blockIdx.x];
     const uint2 r = ranges[tile];
     const int n = (int)(r.y - r.x);
+    if (n > NPAD) return;  // a crowded tile (flagged by the tile scan): no sort
     const int t = threadIdx.x;
     unsigned long long v[E];
 #pragma unroll
@@ -328,6 +349,21 @@ __global__ void __launch_bounds__(THREADS)
     }
 }
 
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+    tile_sort_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+                     const unsigned long long* __restrict__ keys, uint32_t* __restrict__ ids,
+                     const DevCounters* __restrict__ ctr, int cls) {
+    if (ctr->skip) return;
+    uint32_t count, first;
+    class_span(ctr, cls, count, first);
+    for (uint32_t item = blockIdx.x; item < count; item += gridDim.x) {
+        tile_sort_one<THREADS>(ranges, (int)order[first + item], keys, ids);
+        __syncthreads();
+    }
+}
+
+
 // ---------------------------------------------------------------------------
 // per-tile LSD radix sort in shared memory (tiles of 512 .. 8192 pairs)
 //
@@ -345,12 +381,10 @@ __global__ void __launch_bounds__(THREADS)
 #endif
 
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, (RECOGS_RADIX_WARPS_PER_SM * 32 / THREADS) > 0
-                                               ? (RECOGS_RADIX_WARPS_PER_SM * 32 / THREADS)
-                                               : 1)
-    tile_radix_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
-                      const unsigned long long* __restrict__ keys, uint32_t* __restrict__ ids,
-                      uint32_t zmin, int passes) {
+__device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges, int tile,
+                                               const unsigned long long* __restrict__ keys,
+                                               uint32_t* __restrict__ ids, uint32_t zmin,
+                                               int passes) {
     constexpr int W = THREADS / 32;
     constexpr int ITEMS = 8;
     constexpr int MAXN = THREADS * ITEMS;
@@ -361,9 +395,9 @@ __global__ void __launch_bounds__(THREADS, (RECOGS_RADIX_WARPS_PER_SM * 32 / THR
     __shared__ uint32_t s_dstart[256];
     __shared__ uint32_t s_part[W + 1];
 
-    const int tile = (int)order[blockIdx.x];
     const uint2 r = ranges[tile];
     const int n = (int)(r.y - r.x);
+    if (n > MAXN) return;  // a crowded tile (flagged by the tile scan): no sort
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
 
@@ -485,48 +519,105 @@ __global__ void __launch_bounds__(THREADS, (RECOGS_RADIX_WARPS_PER_SM * 32 / THR
 }
 
 template <int THREADS>
-static void radix_class_launch(unsigned g, const uint2* ranges, const uint32_t* o,
-                               const unsigned long long* keys, uint32_t* ids, uint32_t zmin,
-                               int passes, cudaStream_t st) {
+__global__ void __launch_bounds__(THREADS, (RECOGS_RADIX_WARPS_PER_SM * 32 / THREADS) > 0
+                                               ? (RECOGS_RADIX_WARPS_PER_SM * 32 / THREADS)
+                                               : 1)
+    tile_radix_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+                      const unsigned long long* __restrict__ keys, uint32_t* __restrict__ ids,
+                      const DevCounters* __restrict__ ctr, int cls) {
+    if (ctr->skip) return;
+    uint32_t count, first;
+    class_span(ctr, cls, count, first);
+    const uint32_t zmin = ~ctr->zmin_inv;
+    const uint32_t span = ctr->zmax - zmin;
+    const int passes = span == 0u ? 0 : (32 - __clz((int)span) + 7) / 8;
+    for (uint32_t item = blockIdx.x; item < count; item += gridDim.x) {
+        tile_radix_one<THREADS>(ranges, (int)order[first + item], keys, ids, zmin, passes);
+        __syncthreads();
+    }
+}
+
+// Persistent grid for a sort class: as many CTAs as fit on the GPU at once
+// (at most `bound`), each looping over the class's tiles.
+template <typename K>
+static int persistent_grid(K kernel, int threads, size_t smem, uint32_t bound) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const uint32_t g = (uint32_t)sms * (uint32_t)per_sm;
+    return (int)(bound < g ? (bound > 0 ? bound : 1) : g);
+}
+
+template <int THREADS>
+static void radix_class_launch(uint32_t bound, const uint2* ranges, const uint32_t* order,
+                               const unsigned long long* keys, uint32_t* ids,
+                               const DevCounters* ctr, int cls, cudaStream_t st) {
     const size_t smem = sizeof(uint32_t) * (2 * 8 * THREADS + (THREADS / 32) * 256);
     // dynamic plus static shared memory above the 48 KiB default needs the opt-in
     if (smem + 2048 > 48 * 1024)
         cudaFuncSetAttribute(tile_radix_kernel<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-    tile_radix_kernel<THREADS><<<g, THREADS, smem, st>>>(ranges, o, keys, ids, zmin, passes);
+    const int g = persistent_grid(tile_radix_kernel<THREADS>, THREADS, smem, bound);
+    tile_radix_kernel<THREADS><<<g, THREADS, smem, st>>>(ranges, order, keys, ids, ctr, cls);
 }
 
 template <int THREADS>
-static void sort_class_launch(unsigned g, const uint2* ranges, const uint32_t* o,
-                              const unsigned long long* keys, uint32_t* ids, cudaStream_t st) {
+static void sort_class_launch(uint32_t bound, const uint2* ranges, const uint32_t* order,
+                              const unsigned long long* keys, uint32_t* ids,
+                              const DevCounters* ctr, int cls, cudaStream_t st) {
     const size_t smem = THREADS > 32 ? sizeof(unsigned long long) * 8 * THREADS : 0;
     if (smem + 2048 > 48 * 1024)
         cudaFuncSetAttribute(tile_sort_kernel<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-    tile_sort_kernel<THREADS><<<g, THREADS, smem, st>>>(ranges, o, keys, ids);
+    const int g = persistent_grid(tile_sort_kernel<THREADS>, THREADS, smem, bound);
+    tile_sort_kernel<THREADS><<<g, THREADS, smem, st>>>(ranges, order, keys, ids, ctr, cls);
 }
 
 int launch_tile_sort(const uint2* ranges, const uint32_t* order, const uint32_t* class_tiles,
-                     const unsigned long long* keys, uint32_t* ids, uint32_t zmin, int depth_bits,
-                     cudaStream_t st) {
-    // the tile order lists the classes from the largest CTA (1024 threads) down;
-    // tiles of 512 pairs or more use the radix sort, smaller ones the bitonic network
-    const int passes = (depth_bits + 7) / 8;
+                     int tiles, const unsigned long long* keys, uint32_t* ids,
+                     const DevCounters* counters, int radix_classes, cudaStream_t st) {
+    // Classes follow each other in the tile order from the largest CTA (1024
+    // threads) down. With host-known class sizes (class_tiles != NULL) empty
+    // classes are skipped; otherwise every class is launched with a persistent
+    // grid and reads its size on the device.
     int launches = 0;
-    uint32_t off = 0;
     for (int c = 0; c < kSortClasses; ++c) {
-        const uint32_t g = class_tiles[c];
-        if (g == 0) continue;
-        const uint32_t* o = order + off;
+        const uint32_t bound = class_tiles ? class_tiles[c] : (uint32_t)tiles;
+        if (bound == 0) continue;
+        const bool radix = c < radix_classes;
         switch (c) {
-            case 0: radix_class_launch<1024>(g, ranges, o, keys, ids, zmin, passes, st); break;
-            case 1: radix_class_launch<512>(g, ranges, o, keys, ids, zmin, passes, st); break;
-            case 2: radix_class_launch<256>(g, ranges, o, keys, ids, zmin, passes, st); break;
-            case 3: radix_class_launch<128>(g, ranges, o, keys, ids, zmin, passes, st); break;
-            case 4: sort_class_launch<64>(g, ranges, o, keys, ids, st); break;
-            default: sort_class_launch<32>(g, ranges, o, keys, ids, st); break;
+            case 0:
+                if (radix) radix_class_launch<1024>(bound, ranges, order, keys, ids, counters, c, st);
+                else sort_class_launch<1024>(bound, ranges, order, keys, ids, counters, c, st);
+                break;
+            case 1:
+                if (radix) radix_class_launch<512>(bound, ranges, order, keys, ids, counters, c, st);
+                else sort_class_launch<512>(bound, ranges, order, keys, ids, counters, c, st);
+                break;
+            case 2:
+                if (radix) radix_class_launch<256>(bound, ranges, order, keys, ids, counters, c, st);
+                else sort_class_launch<256>(bound, ranges, order, keys, ids, counters, c, st);
+                break;
+            case 3:
+                if (radix) radix_class_launch<128>(bound, ranges, order, keys, ids, counters, c, st);
+                else sort_class_launch<128>(bound, ranges, order, keys, ids, counters, c, st);
+                break;
+            case 4:
+                if (radix) radix_class_launch<64>(bound, ranges, order, keys, ids, counters, c, st);
+                else sort_class_launch<64>(bound, ranges, order, keys, ids, counters, c, st);
+                break;
+            default:
+                sort_class_launch<32>(bound, ranges, order, keys, ids, counters, c, st);
+                break;
         }
-        off += g;
         ++launches;
     }
     return launches;

@@ -4,7 +4,7 @@
 // One CTA of 256 threads per 16x16 tile, one thread per pixel; tiles are
 // launched heaviest first (tile_order_kernel). Each warp owns an 8x4-pixel
 // sub-tile made of four 4x2-pixel groups of 8 lanes. Each batch of up to 256
-// depth-sorted Gaussians is gathered by one thread per Gaussian (the next
+// (or 128) depth-sorted Gaussians is gathered by one thread per Gaussian (the next
 // batch is prefetched into registers while the current one is blended) and
 // staged in shared memory with a 32-bit mask of the groups its alpha >= 1/255
 // box meets. The four groups of a warp then walk their own hit lists in
@@ -54,15 +54,19 @@ __device__ __forceinline__ uint32_t group_mask(float u, float v, float ex, float
     return mask;
 }
 
+// BATCH (128 or 256) Gaussians are staged per batch; threads below BATCH
+// gather them.
+template <int BATCH>
 __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
     blend_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
                  const uint32_t* __restrict__ ids, const float4* __restrict__ rec, int width,
                  int height, int tiles_x, float bg0, float bg1, float bg2, float* __restrict__ image,
-                 float* __restrict__ final_T, unsigned long long* __restrict__ pairs_read) {
-    __shared__ float4 s_a[kBlendThreads];     // (u, v, q0, q1), centre in this tile's frame
-    __shared__ float4 s_b[kBlendThreads];     // (q2, log2 sigma, r, g)
-    __shared__ float s_c[kBlendThreads];      // b
-    __shared__ uint32_t s_m[kBlendThreads];   // group mask
+                 float* __restrict__ final_T, DevCounters* __restrict__ ctr) {
+    static_assert(BATCH == 128 || BATCH == 256, "blend batch");
+    __shared__ float4 s_a[BATCH];     // (u, v, q0, q1), centre in this tile's frame
+    __shared__ float4 s_b[BATCH];     // (q2, log2 sigma, r, g)
+    __shared__ float s_c[BATCH];      // b
+    __shared__ uint32_t s_m[BATCH];   // group mask
 
     const int tile = (int)order[blockIdx.x];
     const int tx = tile % tiles_x, ty = tile / tiles_x;
@@ -76,7 +80,8 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
     const float fpx = (float)lx, fpy = (float)ly;
     const int mbit = 4 * warp + (grp & 1) + 2 * (grp >> 1);   // this lane's group bit
 
-    const uint2 rg = ranges[tile];
+    uint2 rg = ranges[tile];
+    if (ctr && ctr->skip) rg = make_uint2(0u, 0u);  // pairs exceed the buffers: background only
     const uint32_t begin = rg.x, end = rg.y;
 
     float T = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f;
@@ -86,16 +91,17 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
 
     // prefetch the first batch
     float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra;
-    if (begin + threadIdx.x < end) {
+    const bool gatherer = threadIdx.x < BATCH;
+    if (gatherer && begin + threadIdx.x < end) {
         const uint32_t id = __ldg(ids + begin + threadIdx.x);
         ra = __ldg(rec + 3 * (size_t)id);
         rb = __ldg(rec + 3 * (size_t)id + 1);
         rc = __ldg(rec + 3 * (size_t)id + 2);
     }
 
-    for (uint32_t b = begin; b < end; b += kBlendThreads) {
+    for (uint32_t b = begin; b < end; b += BATCH) {
         if (__syncthreads_count(done) == kBlendThreads) break;
-        if (b + threadIdx.x < end) {
+        if (gatherer && b + threadIdx.x < end) {
             // move the centre from its first tile's frame into this tile's frame
             const uint32_t o = __float_as_uint(rc.w);
             const float u = ra.x + (float)(kTile * ((int)(o & 0xffffu) - tx));
@@ -105,17 +111,17 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
             s_c[threadIdx.x] = rc.z;
             s_m[threadIdx.x] = group_mask(u, v, rb.z, rb.w);
         }
-        fetched = min(end, b + kBlendThreads);
+        fetched = min(end, b + BATCH);
         __syncthreads();
         // prefetch the next batch while this one is blended
-        const uint32_t jn = b + kBlendThreads + threadIdx.x;
-        if (jn < end) {
+        const uint32_t jn = b + BATCH + threadIdx.x;
+        if (gatherer && jn < end) {
             const uint32_t id = __ldg(ids + jn);
             ra = __ldg(rec + 3 * (size_t)id);
             rb = __ldg(rec + 3 * (size_t)id + 1);
             rc = __ldg(rec + 3 * (size_t)id + 2);
         }
-        const int cnt = (int)min((uint32_t)kBlendThreads, end - b);
+        const int cnt = (int)min((uint32_t)BATCH, end - b);
         if (__all_sync(0xffffffffu, done)) continue;
 #pragma unroll 1
         for (int g = 0; g * 32 < cnt; ++g) {
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
         image[3 * p + 2] = cb + T * bg2;
         if (final_T) final_T[p] = T;
     }
-    if (threadIdx.x == 0 && pairs_read) atomicAdd(pairs_read, (unsigned long long)(fetched - begin));
+    if (threadIdx.x == 0 && ctr) atomicAdd(&ctr->pairs_read, (unsigned long long)(fetched - begin));
 }
 
 // Position bucket of a tile with c pairs in the tile order: descending pair
@@ -243,11 +249,16 @@ int launch_tile_order(const uint2* ranges, int tiles, uint32_t* order, cudaStrea
 
 int launch_blend(const uint2* ranges, const uint32_t* order, const uint32_t* ids, const float4* rec,
                  const DevCamera& cam, const float bg[3], float* image, float* final_T,
-                 DevCounters* counters, cudaStream_t st) {
+                 DevCounters* counters, int batch, cudaStream_t st) {
     const int tiles = cam.tiles_x * cam.tiles_y;
-    blend_kernel<<<tiles, kBlendThreads, 0, st>>>(ranges, order, ids, rec, cam.width, cam.height,
-                                                  cam.tiles_x, bg[0], bg[1], bg[2], image, final_T,
-                                                  counters ? &counters->pairs_read : nullptr);
+    if (batch == 128)
+        blend_kernel<128><<<tiles, kBlendThreads, 0, st>>>(ranges, order, ids, rec, cam.width,
+                                                           cam.height, cam.tiles_x, bg[0], bg[1],
+                                                           bg[2], image, final_T, counters);
+    else
+        blend_kernel<256><<<tiles, kBlendThreads, 0, st>>>(ranges, order, ids, rec, cam.width,
+                                                           cam.height, cam.tiles_x, bg[0], bg[1],
+                                                           bg[2], image, final_T, counters);
     return 1;
 }
 

@@ -231,13 +231,13 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
         launch_scan_small(po.block_sums, U32(oBlockOffsets), nb, 1, &dctr->n_visible, st);
     }
     launch_tile_totals(U32(oTileCount), tiles, kTilePartsSmall, U32(oCursor), U32(oTileTotals), st);
-    launch_tile_scan(U32(oTileTotals), tiles, ranges, dctr, st);
+    launch_tile_scan(U32(oTileTotals), tiles, ranges, dctr, 0xffffffffu, st);
     NA_CK(cudaGetLastError());
     NA_CK(cudaMemcpyAsync(&hc, dctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
     NA_CK(cudaStreamSynchronize(st));
     V = hc.n_visible;
     P = hc.n_pairs;
-    if (hc.error) {
+    if (hc.error & kErrTimeout) {
         NA_CK(cudaMemsetAsync(&dctr->error, 0, sizeof(uint32_t), st));
         return report(err, el, RECOGS_ETIMEOUT,
                       "a bounded device wait of an earlier call's sort gave up; that image "
@@ -252,12 +252,10 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
     if (V > 0 && (int)hc.max_tile <= kMaxSmemTile) {
         unsigned long long* keys = reinterpret_cast<unsigned long long*>(base + oTkeys0);
         launch_scatter(U32(oCount), reinterpret_cast<const uint2*>(base + oRect), U32(oZkey), n,
-                       dc.tiles_x, ranges, U32(oCursor), kTilePartsSmall, keys, st);
+                       dc.tiles_x, ranges, U32(oCursor), kTilePartsSmall, keys, dctr, st);
         launch_tile_order(ranges, tiles, U32(oOrder), st);
-        const uint32_t span = hc.zmax - ~hc.zmin_inv;
-        const int dbits = span == 0 ? 0 : 32 - __builtin_clz(span);
-        launch_tile_sort(ranges, U32(oOrder), hc.class_tiles, keys, U32(oTvals0), ~hc.zmin_inv,
-                         dbits, st);
+        launch_tile_sort(ranges, U32(oOrder), hc.class_tiles, tiles, keys, U32(oTvals0), dctr, 4,
+                         st);
     } else if (V > 0) {
         launch_compact(U32(oCount), U32(oZkey), n, U32(oBlockOffsets), dctr, U32(oDkeys0),
                        U32(oDvals0), st);
@@ -292,7 +290,7 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
         launch_tile_order(ranges, tiles, U32(oOrder), st);
     }
     NA_CK(cudaGetLastError());
-    launch_blend(ranges, U32(oOrder), ids, rec, dc, bgv, image_hwc_out, final_T_out, dctr, st);
+    launch_blend(ranges, U32(oOrder), ids, rec, dc, bgv, image_hwc_out, final_T_out, dctr, 256, st);
     NA_CK(cudaGetLastError());
 #undef NA_CK
     return RECOGS_OK;

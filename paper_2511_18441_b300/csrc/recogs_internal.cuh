@@ -60,10 +60,13 @@ struct DevCounters {
     unsigned long long pairs_read;
     uint32_t max_tile;   // pairs of the most crowded tile
     uint32_t class_tiles[kSortClasses];  // non-empty tiles per per-tile-sort class
-    uint32_t pad0;
-    uint32_t error;      // not cleared per frame: set by a bounded wait that gave up
+    uint32_t skip;       // 1: the pairs exceed the pair buffers; later stages skip the frame
+    uint32_t error;      // kErr* bits; not cleared per frame (the host reads and clears it)
     uint32_t pad1;
 };
+constexpr uint32_t kErrTimeout = 1u;   // a bounded look-back wait gave up
+constexpr uint32_t kErrCapacity = 2u;  // more pairs than the pair buffers hold
+constexpr uint32_t kErrCrowded = 4u;   // a tile above the per-tile sort's limit
 constexpr size_t kCountersClearBytes = 56;  // the fields before `error`
 static_assert(sizeof(DevCounters) == 64, "DevCounters layout");
 
@@ -199,16 +202,20 @@ int launch_emit(const uint32_t* sorted_ids, const uint32_t* counts_sorted, const
 int launch_tile_totals(const uint32_t* tile_count, int tiles, int parts, uint32_t* cursor,
                        uint32_t* totals, cudaStream_t st);
 int launch_tile_scan(const uint32_t* totals, int tiles, uint2* ranges, DevCounters* counters,
-                     cudaStream_t st);
+                     uint32_t capacity, cudaStream_t st);
 int launch_scatter(const uint32_t* count, const uint2* rect, const uint32_t* zkey, int n,
                    int tiles_x, const uint2* ranges, uint32_t* cursor, int parts,
-                   unsigned long long* keys, cudaStream_t st);
+                   unsigned long long* keys, const DevCounters* counters, cudaStream_t st);
+// class_tiles: host copy of the class sizes, or NULL to size the launches on the device
+// Classes 0 .. radix_classes-1 (the largest tiles) are sorted by radix, the rest
+// by the bitonic network.
 int launch_tile_sort(const uint2* ranges, const uint32_t* order, const uint32_t* class_tiles,
-                     const unsigned long long* keys, uint32_t* ids, uint32_t zmin, int depth_bits,
-                     cudaStream_t st);
+                     int tiles, const unsigned long long* keys, uint32_t* ids,
+                     const DevCounters* counters, int radix_classes, cudaStream_t st);
 int launch_tile_order(const uint2* ranges, int tiles, uint32_t* order, cudaStream_t st);
+// batch: Gaussians staged in shared memory per blend step, 128 or 256
 int launch_blend(const uint2* ranges, const uint32_t* order, const uint32_t* ids, const float4* rec,
                  const DevCamera& cam, const float bg[3], float* image, float* final_T,
-                 DevCounters* counters, cudaStream_t st);
+                 DevCounters* counters, int batch, cudaStream_t st);
 
 }  // namespace recogs

@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kOsThreads)
             const uint32_t f = v & ~kValueMask;
             if (f == 0u) {
                 if (++spins > kSpinLimit) {
-                    atomicOr(error, 1u);
+                    atomicOr(error, kErrTimeout);
                     break;
                 }
                 continue;

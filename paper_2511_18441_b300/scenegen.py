@@ -297,6 +297,37 @@ def paper_scale_workload(n=1_000_000, seed=1, width=1920, height=1080,
     return Workload(f"paper_{n}", scene, cam, edit)
 
 
+@dataclass
+class BatchWorkload:
+    name: str
+    scenes: list                         # list of Scene
+    views: list                          # list of (scene index, Camera, Edit)
+
+
+BATCH_RESOLUTIONS = ((1280, 720), (1920, 1080), (2560, 1440), (3840, 2160))
+
+
+def batched_workload(sizes=(500_000, 1_000_000, 2_000_000, 4_000_000), views_per_scene=16,
+                     resolutions=BATCH_RESOLUTIONS, seed=3) -> BatchWorkload:
+    """Several scenes of the paper-scale generator (different seeds), each
+    seen by `views_per_scene` cameras on a ring of radius 14 around the
+    origin with resolutions drawn uniformly from `resolutions`. Each scene has
+    its own edit: a pixel box covering the central quarter of its first ring
+    camera's image (the selection camera of all its views, so that every view
+    shows the same selected Gaussians recoloured) and its own tint."""
+    scenes, views = [], []
+    for k, n in enumerate(sizes):
+        scenes.append(make_scene(int(n), seed + 17 * k, 5.0, 40, (2.0, 5.0), 20, (2.0, 5.0)))
+        cams = ring_cameras(views_per_scene, 14.0, resolutions, seed + 31 * k)
+        c0 = cams[0]
+        region = pixel_box_region(c0.width // 4, c0.height // 4, c0.width // 2, c0.height // 2)
+        rng = np.random.default_rng(seed + 53 * k)
+        edit = Edit(region, tint_matrix(rng.uniform(0.2, 1.0, 3)), select_camera=c0)
+        for cam in cams:
+            views.append((k, cam, edit))
+    return BatchWorkload(f"batch_{len(sizes)}x{views_per_scene}", scenes, views)
+
+
 def to_half(sh: np.ndarray, kind: str) -> np.ndarray:
     """Round float32 SH to float16 ('f16') or bfloat16 ('bf16', round to
     nearest even); returns the 16-bit payload as uint16 for bf16 and float16

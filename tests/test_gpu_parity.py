@@ -315,7 +315,7 @@ def test_sort_paths_agree(ctx):
 
 
 def test_crowded_tile_takes_global_path(ctx):
-    """More than 16384 pairs in one tile: the per-tile shared-memory sort
+    """More than 8192 pairs in one tile: the per-tile shared-memory sort
     cannot hold the list, so the frame takes the global radix path."""
     rng = np.random.default_rng(5)
     n = 20_000
