@@ -41,7 +41,7 @@ WIDTH, HEIGHT = 1920, 1080
 PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
 
 
-def workload_config(sh_dtype):
+def workload_config(sh_dtype, readback=False):
     return {
         "workload": (f"recolor+render, {N_SPLATS / 1e6:g}M SH3 Gaussians ({sh_dtype} SH), "
                      f"{WIDTH}x{HEIGHT}, 12-gon selection covering 15%, 90 deg hue rotation"),
@@ -50,7 +50,16 @@ def workload_config(sh_dtype):
         "generator": "40 spheres + 20 planes in a 10^3 box, camera at distance 14, fovy 60",
         "l2": "inputs larger than L2 (708 MB scene vs 126 MB L2); no flush",
         "parallelism": "replicas (one independent frame stream per GPU)",
+        "frame": ("recogs_render, fused select+recolour edit, with the mid-frame read back"
+                  if readback else
+                  "recogs_render, fused select+recolour edit, no mid-frame read back "
+                  "(pair buffers preset from a first frame; overflow checked after the run)"),
     }
+
+
+def pair_capacity(n_pairs: int) -> int:
+    """Pair buffers for frames without the read back: 1/16 headroom."""
+    return n_pairs + n_pairs // 16 + 4096
 
 
 def make_workload():
@@ -332,10 +341,31 @@ def run_ours(args, rank, world, local):
         frame()
     torch.cuda.synchronize(dev)
     _, stats = ctx.render(ds, w.camera, w.edit, image_out=img, stats=True, stream=stream)
+    # frames without the mid-frame read back: pair buffers sized from this
+    # frame with 1/16 headroom; an overflow would be reported by check()
+    capacity = pair_capacity(stats["n_pairs"])
+    if not args.readback:
+        ctx.set_pair_capacity(capacity)
+        for _ in range(3):
+            frame()
+        ctx.check(stream)
+
+    # stage breakdown (every stage timed) outside the timed region; it names
+    # the dominant kernel, the only stage timed inside the timed region
+    k_breakdown = max(20, args.steps // 4)
+    ctx.set_timing(True)
+    ctx.stage_times(reset=True)
+    for _ in range(k_breakdown):
+        frame()
+    torch.cuda.synchronize(dev)
+    breakdown = {k: v for k, v in ctx.stage_times(reset=True).items()
+                 if v[1] > 0 and k not in ("h2d", "d2h")}
+    ctx.set_timing(False)
+    dom = max(breakdown, key=lambda k: breakdown[k][0])
 
     barrier(world)
     torch.cuda.synchronize(dev)
-    ctx.set_timing(True)
+    ctx.set_timing(True, stages=[dom])
     ctx.stage_times(reset=True)
     l0 = ctx.launch_count()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -351,16 +381,16 @@ def run_ours(args, rank, world, local):
     ms = e0.elapsed_time(e1)
     launches = ctx.launch_count() - l0
     stages = ctx.stage_times(reset=True)
-    ctx.set_timing(False)
+    ctx.set_timing(False, stages=None)
     clocks = sampler.stop()
+    ctx.check(stream)   # raises if any timed frame overflowed its buffers
     max_ms = max_over_ranks(ms, world, dev)
     value = aggregate_value(args.steps, world, max_ms)
 
-    # roofline of the dominant kernel (stage events are recorded on `stream`)
+    # roofline of the dominant kernel: its events (recorded on `stream`)
+    # bracket each of its launches inside the timed region
     peaks, peaks_src = load_peaks()
-    per_stage = {k: v for k, v in stages.items() if v[1] > 0 and k not in ("h2d", "d2h")}
-    dom = max(per_stage, key=lambda k: per_stage[k][0])
-    dom_ms = per_stage[dom][0] / max(per_stage[dom][1], 1)
+    dom_ms = stages[dom][0] / max(stages[dom][1], 1)
     sh_bytes = 4 if args.sh_dtype == "f32" else 2
     alg = algorithmic_bytes(dom, stats, N_SPLATS, sh_bytes)
     roof = None
@@ -369,15 +399,16 @@ def run_ours(args, rank, world, local):
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                 "peak_source": f"{peaks_src} copy bandwidth", "traffic": profiled_traffic(dom),
-                "algorithmic_bytes": alg, "ms_per_launch": dom_ms}
-    stage_ms = {k: round(v[0] / args.steps, 4) for k, v in per_stage.items()}
+                "algorithmic_bytes": alg, "ms_per_launch": dom_ms,
+                "timed": f"CUDA events around each {dom} launch of the {args.steps} timed frames"}
+    stage_ms = {k: round(v[0] / k_breakdown, 4) for k, v in breakdown.items()}
 
-    # other stages' HBM fractions for context
+    # other stages' HBM fractions for context (from the breakdown frames)
     other = {}
     for k in ("preprocess", "blend"):
-        if k in per_stage and k != dom:
+        if k in breakdown and k != dom:
             a = algorithmic_bytes(k, stats, N_SPLATS, sh_bytes)
-            t = per_stage[k][0] / max(per_stage[k][1], 1)
+            t = breakdown[k][0] / max(breakdown[k][1], 1)
             other[k] = {"achieved_gbs": a / (t / 1000.0) / 1e9,
                         "frac": a / (t / 1000.0) / 1e9 / peaks["hbm_gbs"], "ms_per_launch": t}
 
@@ -400,25 +431,40 @@ def run_ours(args, rank, world, local):
                "d2h_bytes_per_step": himg.numel() * 4, "steps": n_e2e,
                "api": "recogs_render_host (pinned host buffers)"}
 
-    # the same frame with 16-bit SH storage, for context
+    # context: 16-bit SH storage, the frame with the read back, and the frame
+    # replayed as a one-view CUDA graph (recogs_render_batch)
     variants = {}
-    if args.sh_dtype == "f32" and not args.no_variants:
-        for kind in ("bf16", "f16"):
-            dv = binding.DeviceScene.from_numpy(w.scene, dev, kind)
+    if not args.no_variants:
+        k = max(10, args.steps // 2)
+
+        def timed(fn):
             for _ in range(3):
-                ctx.render(dv, w.camera, w.edit, image_out=img, stream=stream)
+                fn()
             torch.cuda.synchronize(dev)
-            k = max(10, args.steps // 2)
             a0 = torch.cuda.Event(enable_timing=True)
             a1 = torch.cuda.Event(enable_timing=True)
             a0.record(stream)
             for _ in range(k):
-                ctx.render(dv, w.camera, w.edit, image_out=img, stream=stream)
+                fn()
             a1.record(stream)
             torch.cuda.synchronize(dev)
-            variants[kind] = {"frames_per_s": k / (a0.elapsed_time(a1) / 1000.0),
-                              "ms_per_step": a0.elapsed_time(a1) / k}
-            del dv
+            ctx.check(stream)
+            t = a0.elapsed_time(a1) / k
+            return {"frames_per_s": 1000.0 / t, "ms_per_step": t}
+
+        if args.sh_dtype == "f32":
+            for kind in ("bf16", "f16"):
+                dv = binding.DeviceScene.from_numpy(w.scene, dev, kind)
+                variants[kind] = timed(
+                    lambda: ctx.render(dv, w.camera, w.edit, image_out=img, stream=stream))
+                del dv
+        ctx.set_pair_capacity(0)
+        variants["with_readback"] = timed(frame)
+        b = ctx.batch([ds], [dict(scene=0, camera=w.camera, edit=w.edit, image_out=img)],
+                      graph=True)
+        b(stream=stream)
+        variants["graph_replay"] = timed(lambda: b(nowait=True, stream=stream))
+        variants["graph_replay"]["kernel_nodes"] = ctx.batch_info()["graph_launches"]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -431,10 +477,11 @@ def run_ours(args, rank, world, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.sh_dtype if args.sh_dtype != "f32" else "f32",
             "data": "synthetic (seeded generator; MipNeRF360 captures unavailable)",
-            "config": workload_config(args.sh_dtype),
+            "config": workload_config(args.sh_dtype, args.readback),
             "gaussians_per_s": value * N_SPLATS,
             "frame_stats": stats,
             "stage_ms_per_step": stage_ms,
+            "stage_ms_note": f"every stage timed by events over {k_breakdown} extra frames",
             "roofline": roof,
             "roofline_other": other,
             "cpu_baseline": cpu,
@@ -442,6 +489,97 @@ def run_ours(args, rank, world, local):
             "gpu_launches": launches,
             "clocks": clocks,
             "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# the batched workload: many scenes and views in one graph replay
+
+BATCH_SIZES = (500_000, 1_000_000, 2_000_000, 4_000_000)
+BATCH_VIEWS_PER_SCENE = 16
+
+
+def run_batch(args, rank, world, local):
+    """4 scenes (0.5M, 1M, 2M, 4M Gaussians, different seeds), 16 ring views
+    each at resolutions drawn from 720p/1080p/1440p/2160p, each scene with its
+    own selection box and tint; one step renders all 64 views through one
+    replay of the planned, autotuned batch graph (recogs_render_batch)."""
+    import torch
+    from paper_2511_18441_b300 import binding, build
+    from paper_2511_18441_b300 import scenegen as sg
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the library has no CPU path)")
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    bw = sg.batched_workload(sizes=BATCH_SIZES, views_per_scene=BATCH_VIEWS_PER_SCENE)
+    scenes = [binding.DeviceScene.from_numpy(sc, dev, args.sh_dtype) for sc in bw.scenes]
+    views = [dict(scene=si, camera=cam, edit=edit) for si, cam, edit in bw.views]
+    pixels = sum(cam.width * cam.height for _, cam, _ in bw.views)
+    splat_views = sum(bw.scenes[si].n for si, _, _ in bw.views)
+    ctx = binding.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    b = ctx.batch(scenes, views, graph=True, tune=True)
+    t0 = time.perf_counter()
+    b(stream=stream)                      # plans, tunes, captures
+    plan_s = time.perf_counter() - t0
+    info = ctx.batch_info()
+
+    def per_view_pass():
+        for v, img in zip(views, b.images):
+            ctx.render(scenes[v["scene"]], v["camera"], v["edit"], image_out=img, stream=stream)
+
+    def timed(fn, k):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        return e0.elapsed_time(e1)
+
+    sampler = ClockSampler(gpu_id_for_smi(local))
+    sampler.start()
+    steps = args.steps
+    sampler.mark_begin()
+    l0 = ctx.launch_count()
+    ms = timed(lambda: b(nowait=True, stream=stream), steps)
+    launches = ctx.launch_count() - l0
+    sampler.mark_end()
+    clocks = sampler.stop()
+    ctx.check(stream)
+    max_ms = max_over_ranks(ms, world, dev)
+    value = steps * len(views) * world / (max_ms / 1000.0)
+    seq_ms = timed(per_view_pass, max(2, steps // 4)) / max(2, steps // 4)
+    if rank == 0:
+        line = {
+            "metric": "views/s of the batched recolor+render workload (64 views, 4 scenes)",
+            "value": value, "unit": "views/s", "n_gpus": world, "steps": steps,
+            "warmup": max(3, args.warmup), "ms_per_step": max_ms / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.sh_dtype, "data": "synthetic (seeded generator)",
+            "config": {"workload": (f"{len(bw.scenes)} scenes of "
+                                    f"{'/'.join(f'{n / 1e6:g}M' for n in BATCH_SIZES)} Gaussians, "
+                                    f"{BATCH_VIEWS_PER_SCENE} ring views each, resolutions drawn "
+                                    "from 1280x720/1920x1080/2560x1440/3840x2160, per-scene box "
+                                    "selection and tint"),
+                       "views": len(views), "pixels_per_step": pixels,
+                       "gaussian_views_per_step": splat_views, "sh_dtype": args.sh_dtype,
+                       "l2": "inputs larger than L2; no flush"},
+            "megapixels_per_s": pixels * steps * world / (max_ms / 1000.0) / 1e6,
+            "plan": {**info, "plan_seconds": plan_s},
+            "per_view_renders": {"views_per_s": len(views) / (seq_ms / 1000.0),
+                                 "ms_per_step": seq_ms,
+                                 "api": "recogs_render per view, with the read back"},
+            "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -457,6 +595,10 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--readback", action="store_true",
+                    help="time frames with the mid-frame read back (default: pair capacity preset)")
+    ap.add_argument("--workload", choices=["frame", "batch"], default="frame",
+                    help="frame: the 3M/1080p headline; batch: 64 views of 4 scenes")
     ap.add_argument("--gaussians", type=int, default=None,
                     help="scene size for small profiling cases (default 3,000,000)")
     args = ap.parse_args(argv)
@@ -469,6 +611,8 @@ def main(argv=None):
     try:
         if args.impl == "reference":
             run_reference(args, rank, world)
+        elif args.workload == "batch":
+            run_batch(args, rank, world, local)
         else:
             run_ours(args, rank, world, local)
     finally:

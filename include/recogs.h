@@ -236,6 +236,11 @@ RECOGS_API recogs_status recogs_tile_lists(recogs_ctx* ctx, uint32_t* ranges_out
  * stream each stage runs on. */
 RECOGS_API recogs_status recogs_set_timing(recogs_ctx* ctx, int enable);
 
+/* Which stages the timing covers: bit i = stage i in the order of
+ * recogs_stage_times (default: all). Each timed stage costs two event
+ * records per frame on the stream. */
+RECOGS_API recogs_status recogs_set_timed_stages(recogs_ctx* ctx, uint32_t mask);
+
 /* Read accumulated stage timings (waits for recorded events). For up to
  * max_stages stages writes names[i] (static strings), total_ms[i] and
  * launches[i] (kernel launches of that stage); *n_stages = stages written.

@@ -92,6 +92,7 @@ SIGNATURES = {
                                         C.c_size_t, C.c_void_p]),
     "recogs_tile_lists": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "recogs_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "recogs_set_timed_stages": (C.c_int, [C.c_void_p, C.c_uint32]),
     "recogs_stage_times": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
                                      C.POINTER(C.c_char_p), C.POINTER(C.c_double),
                                      C.POINTER(C.c_int64), C.c_int]),
@@ -331,7 +332,15 @@ class Context:
                                               max(n_pairs, 1), _stream_ptr(stream)))
         return ranges, ids[:n_pairs]
 
-    def set_timing(self, enable: bool):
+    def set_timing(self, enable: bool, stages=None):
+        """Event timing of each stage (or only of the named stages)."""
+        mask = 0xFFFFFFFF
+        if stages is not None:
+            names = list(self.stage_times().keys())
+            mask = 0
+            for nm in stages:
+                mask |= 1 << names.index(nm)
+        self._check(self._L.recogs_set_timed_stages(self._h, mask))
         self._check(self._L.recogs_set_timing(self._h, 1 if enable else 0))
 
     def stage_times(self, reset=False):

@@ -3,11 +3,14 @@
 //
 // Paper: ReCoGS (arXiv 2511.18441). The per-frame pipeline renders Eq. 3
 // (Sec. 3.1) with the Sec. 3.3 edit fused into the per-Gaussian pass:
-//   preprocess (select, recolour, project, footprint, colour)
-//   -> block-sum scans (visible count, pair count; read back once)
-//   -> compaction of visible Gaussians -> radix sort by depth
-//   -> pair offsets in depth order -> pair expansion -> radix sort by tile
-//   -> tile ranges -> per-tile blend (HWC image, Sec. 4.2).
+//   preprocess (select, recolour, project, footprint, colour; pairs per tile)
+//   -> tile totals -> tile scan (ranges, tile order, pair total, sort classes;
+//      read back once unless a pair capacity is preset)
+//   -> scatter of (depth, index) keys into the tile ranges
+//   -> per-tile sort by (depth, index) -> per-tile blend (HWC image, Sec. 4.2).
+// A frame with a tile above the per-tile sort's limit takes the global path
+// instead: compaction of visible Gaussians -> radix sort by depth -> pair
+// offsets in depth order -> pair expansion -> stable radix sort by tile.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -25,12 +28,13 @@ namespace {
 
 enum Stage {
     ST_PREPROCESS, ST_SCAN, ST_COMPACT, ST_SORT_DEPTH, ST_PAIR_OFFSETS, ST_EMIT, ST_SORT_TILE,
-    ST_RANGES, ST_BLEND, ST_SELECT, ST_RECOLOR, ST_H2D, ST_D2H, ST_TILE_ORDER, ST_SCATTER,
-    ST_TILE_SORT, ST_COUNT
+    ST_BLEND, ST_SELECT, ST_RECOLOR, ST_H2D, ST_D2H, ST_SCATTER, ST_TILE_SORT, ST_COUNT
 };
+// "scan" = tile totals, tile ranges and tile order; "compact" .. "sort_tile"
+// = the global sort path
 const char* const kStageNames[ST_COUNT] = {
     "preprocess", "scan", "compact", "sort_depth", "pair_offsets", "emit", "sort_tile",
-    "ranges", "blend", "select", "recolor", "h2d", "d2h", "tile_order", "scatter", "tile_sort"};
+    "blend", "select", "recolor", "h2d", "d2h", "scatter", "tile_sort"};
 
 struct DevBuf {
     void* p = nullptr;
@@ -53,6 +57,9 @@ struct Scratch {
     DevBuf dkeys[2], dvals[2], sort_scratch, pair_sums, pair_offsets;
     DevBuf tkeys[2], tvals[2], ranges, order, tile_count, cursor, tile_totals, pair_keys;
     bool counters_ready = false;
+    bool tile_count_zero = false;   // every tile_count word is 0 (between frames)
+    bool has_class_hint = false;    // class_hint holds the last read-back frame's class sizes
+    uint32_t class_hint[kSortClasses] = {0, 0, 0, 0, 0, 0};
     void release() {
         DevBuf* bufs[] = {&rec, &count, &rect, &zkey, &block_sums, &block_offsets, &counters,
                           &dkeys[0], &dkeys[1], &dvals[0], &dvals[1], &sort_scratch, &pair_sums,
@@ -64,6 +71,7 @@ struct Scratch {
             b->cap = 0;
         }
         counters_ready = false;
+        tile_count_zero = false;
     }
 };
 
@@ -73,6 +81,7 @@ struct Schedule {
     int64_t pair_capacity = 0;  // > 0: no mid-frame read back, pair buffers of this size
     int radix_classes = 4;      // per-tile sort classes (largest first) sorted by radix
     int blend_batch = 256;      // Gaussians staged per blend batch (128 or 256)
+    const uint32_t* class_hint = nullptr;   // sort class sizes of an earlier frame (grid sizes)
 };
 
 // One lane of a batch: its own scratch and stream, so that the frames of
@@ -87,6 +96,7 @@ struct Lane {
 struct ViewPlan {
     int64_t pairs = 0;
     uint32_t max_tile = 0;
+    uint32_t class_tiles[kSortClasses] = {0, 0, 0, 0, 0, 0};   // tiles per sort class
     double ms = 0.0;     // measured time of its planning render
     int lane = -1;       // -1: rendered outside the graph (a tile above the per-tile limit)
 };
@@ -119,6 +129,7 @@ struct recogs_ctx {
     const uint2* last_ranges = nullptr;
     // timing and counts
     bool timing = false;
+    uint32_t timed_stages = ~0u;   // bit per Stage
     std::vector<cudaEvent_t> event_pool;
     std::vector<PendingTime> pending;
     double stage_ms[ST_COUNT] = {0};
@@ -208,8 +219,8 @@ cudaEvent_t get_event(recogs_ctx* ctx) {
     return e;
 }
 
-void stage_begin(recogs_ctx* ctx, cudaStream_t st) {
-    if (!ctx->timing || ctx->capturing) return;
+void stage_begin(recogs_ctx* ctx, int stage, cudaStream_t st) {
+    if (!ctx->timing || ctx->capturing || !((ctx->timed_stages >> stage) & 1u)) return;
     ctx->cur_start = get_event(ctx);
     cudaEventRecord(ctx->cur_start, st);
 }
@@ -365,7 +376,11 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
     CKS(ensure(ctx, sc.counters, sizeof(DevCounters)));
     CKS(ensure(ctx, sc.ranges, sizeof(uint2) * (size_t)tiles));
     CKS(ensure(ctx, sc.order, sizeof(uint32_t) * (size_t)tiles));
-    CKS(ensure(ctx, sc.tile_count, sizeof(uint32_t) * kTileParts * (size_t)tiles));
+    {
+        const void* before = sc.tile_count.p;
+        CKS(ensure(ctx, sc.tile_count, sizeof(uint32_t) * kTileParts * (size_t)tiles));
+        if (sc.tile_count.p != before) sc.tile_count_zero = false;
+    }
     CKS(ensure(ctx, sc.cursor, sizeof(uint32_t) * kTileParts * (size_t)tiles));
     CKS(ensure(ctx, sc.tile_totals, sizeof(uint32_t) * (size_t)tiles));
     DevCounters* dctr = P<DevCounters>(sc.counters);
@@ -374,7 +389,9 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
         sc.counters_ready = true;
     }
     CK(cudaMemsetAsync(dctr, 0, kCountersClearBytes, st));
-    CK(cudaMemsetAsync(sc.tile_count.p, 0, sizeof(uint32_t) * kTileParts * (size_t)tiles, st));
+    // the tile counts are left zero by the previous frame's tile_totals
+    if (!sc.tile_count_zero) CK(cudaMemsetAsync(sc.tile_count.p, 0, sc.tile_count.cap, st));
+    sc.tile_count_zero = false;
 
     // 1. per-Gaussian pass and per-tile pair counts
     uint32_t V = 0, Pn = 0, zmin = 0, zmax = 0, max_tile = 0;
@@ -394,21 +411,19 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
         po.tile_count = P<uint32_t>(sc.tile_count);
         po.parts = kTileParts;
         po.counters = dctr;
-        stage_begin(ctx, st);
+        stage_begin(ctx, ST_PREPROCESS, st);
         int l = launch_preprocess(s, dc, de, po, st);
         stage_end(ctx, ST_PREPROCESS, l, st);
         CK(cudaGetLastError());
     }
     // 2. visible count (and offsets for the global path), tile ranges, pair total
-    stage_begin(ctx, st);
-    int l = 0;
-    if (n > 0)
-        l += launch_scan_small(P<uint32_t>(sc.block_sums), P<uint32_t>(sc.block_offsets), nb, 1,
-                               &dctr->n_visible, st);
-    l += launch_tile_totals(P<uint32_t>(sc.tile_count), tiles, kTileParts,
-                            P<uint32_t>(sc.cursor), P<uint32_t>(sc.tile_totals), st);
+    stage_begin(ctx, ST_SCAN, st);
+    int l = launch_tile_totals(P<uint32_t>(sc.tile_count), tiles, kTileParts,
+                               P<uint32_t>(sc.cursor), P<uint32_t>(sc.tile_totals), st);
+    sc.tile_count_zero = true;
     const bool async = sched.pair_capacity > 0;
-    l += launch_tile_scan(P<uint32_t>(sc.tile_totals), tiles, P<uint2>(sc.ranges), dctr,
+    l += launch_tile_scan(P<uint32_t>(sc.tile_totals), tiles, P<uint2>(sc.ranges),
+                          P<uint32_t>(sc.order), dctr,
                           async ? (uint32_t)sched.pair_capacity : 0xffffffffu, st);
     stage_end(ctx, ST_SCAN, l, st);
     CK(cudaGetLastError());
@@ -434,9 +449,17 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
         }
         if (Pn >= (1u << 30))
             return fail(ctx, RECOGS_ECAPACITY, "%u (tile, Gaussian) pairs exceed 2^30", Pn);
+        // every pair belongs to a visible Gaussian; the blend reads the tile
+        // lists whenever there are pairs, so the two counts must agree
+        if ((Pn > 0) != (V > 0))
+            return fail(ctx, RECOGS_ECUDA, "inconsistent frame counters (%u visible, %u pairs)",
+                        V, Pn);
+        for (int c = 0; c < kSortClasses; ++c) sc.class_hint[c] = ctx->h_counters->class_tiles[c];
+        sc.has_class_hint = true;
         if (plan_out) {
             plan_out->pairs = Pn;
             plan_out->max_tile = max_tile;
+            for (int c = 0; c < kSortClasses; ++c) plan_out->class_tiles[c] = sc.class_hint[c];
         }
     } else {
         // no read back: buffers sized by the pair capacity, sizes read on the device
@@ -448,28 +471,28 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
     const uint32_t* ids = nullptr;
     const bool smem_path =
         async || sched.sort_path == 1 || (sched.sort_path == 0 && max_tile <= kMaxSmemTile);
-    if (V > 0 && smem_path && (int)max_tile <= kMaxSmemTile) {
+    if (Pn > 0 && smem_path && (int)max_tile <= kMaxSmemTile) {
         // 3a. scatter (depth, index) keys into the tile ranges, sort each tile in shared memory
         CKS(ensure(ctx, sc.pair_keys, sizeof(unsigned long long) * (size_t)Pn));
         CKS(ensure(ctx, sc.tvals[0], sizeof(uint32_t) * (size_t)Pn));
-        stage_begin(ctx, st);
+        stage_begin(ctx, ST_SCATTER, st);
         l = launch_scatter(P<uint32_t>(sc.count), P<uint2>(sc.rect), P<uint32_t>(sc.zkey), n,
                            dc.tiles_x, P<uint2>(sc.ranges), P<uint32_t>(sc.cursor), kTileParts,
                            P<unsigned long long>(sc.pair_keys), dctr, st);
         stage_end(ctx, ST_SCATTER, l, st);
-        stage_begin(ctx, st);
-        l = launch_tile_order(P<uint2>(sc.ranges), tiles, P<uint32_t>(sc.order), st);
-        stage_end(ctx, ST_TILE_ORDER, l, st);
-        stage_begin(ctx, st);
-        uint32_t classes[kSortClasses];
-        for (int c = 0; c < kSortClasses; ++c) classes[c] = ctx->h_counters->class_tiles[c];
-        l = launch_tile_sort(P<uint2>(sc.ranges), P<uint32_t>(sc.order),
-                             async ? nullptr : classes, tiles, P<unsigned long long>(sc.pair_keys),
-                             P<uint32_t>(sc.tvals[0]), dctr, sched.radix_classes, st);
+        stage_begin(ctx, ST_TILE_SORT, st);
+        // grid sizes: this frame's class sizes, else a hint from an earlier frame
+        const uint32_t* classes = !async                ? sc.class_hint
+                                  : sched.class_hint     ? sched.class_hint
+                                  : sc.has_class_hint    ? sc.class_hint
+                                                         : nullptr;
+        l = launch_tile_sort(P<uint2>(sc.ranges), P<uint32_t>(sc.order), classes, !async, tiles,
+                             P<unsigned long long>(sc.pair_keys), P<uint32_t>(sc.tvals[0]), dctr,
+                             sched.radix_classes, st);
         stage_end(ctx, ST_TILE_SORT, l, st);
         ids = P<uint32_t>(sc.tvals[0]);
         CK(cudaGetLastError());
-    } else if (V > 0) {
+    } else if (Pn > 0) {
         // 3b. global path: radix sort by depth, expand pairs in depth order,
         // stable radix sort by tile (any tile size)
         const int max_items = (int)(V > Pn ? V : Pn);
@@ -484,8 +507,10 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
         CKS(ensure(ctx, sc.pair_sums, sizeof(uint32_t) * (size_t)vb));
         CKS(ensure(ctx, sc.pair_offsets, sizeof(uint32_t) * (size_t)vb));
 
-        stage_begin(ctx, st);
-        l = launch_compact(P<uint32_t>(sc.count), P<uint32_t>(sc.zkey), n,
+        stage_begin(ctx, ST_COMPACT, st);
+        l = launch_scan_small(P<uint32_t>(sc.block_sums), P<uint32_t>(sc.block_offsets), nb, 1,
+                              nullptr, st);
+        l += launch_compact(P<uint32_t>(sc.count), P<uint32_t>(sc.zkey), n,
                            P<uint32_t>(sc.block_offsets), dctr, P<uint32_t>(sc.dkeys[0]),
                            P<uint32_t>(sc.dvals[0]), st);
         stage_end(ctx, ST_COMPACT, l, st);
@@ -499,13 +524,13 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
         sb.error = &dctr->error;
         const uint32_t span = zmax - zmin;
         const int dbits = span == 0 ? 0 : 32 - __builtin_clz(span);
-        stage_begin(ctx, st);
+        stage_begin(ctx, ST_SORT_DEPTH, st);
         l = 0;
         const int dcur = radix_sort_pairs(sb, (int)V, dbits, st, &l);
         stage_end(ctx, ST_SORT_DEPTH, l, st);
         const uint32_t* sorted = sb.vals[dcur];
 
-        stage_begin(ctx, st);
+        stage_begin(ctx, ST_PAIR_OFFSETS, st);
         // the depth sort's spare key buffer holds the counts in depth order
         uint32_t* counts_sorted = sb.keys[dcur ^ 1];
         l = launch_pair_block_sums(sorted, P<uint32_t>(sc.count), (int)V, counts_sorted,
@@ -514,7 +539,7 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
                                nullptr, st);
         stage_end(ctx, ST_PAIR_OFFSETS, l, st);
 
-        stage_begin(ctx, st);
+        stage_begin(ctx, ST_EMIT, st);
         l = launch_emit(sorted, counts_sorted, P<uint2>(sc.rect), (int)V,
                         P<uint32_t>(sc.pair_offsets), dc.tiles_x, P<uint32_t>(sc.tkeys[0]),
                         P<uint32_t>(sc.tvals[0]), st);
@@ -526,19 +551,12 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
         tb.vals[0] = P<uint32_t>(sc.tvals[0]);
         tb.vals[1] = P<uint32_t>(sc.tvals[1]);
         const int tbits = tiles <= 1 ? 0 : 32 - __builtin_clz((uint32_t)(tiles - 1));
-        stage_begin(ctx, st);
+        stage_begin(ctx, ST_SORT_TILE, st);
         l = 0;
         const int tcur = radix_sort_pairs(tb, (int)Pn, tbits, st, &l);
         stage_end(ctx, ST_SORT_TILE, l, st);
         ids = tb.vals[tcur];
-        stage_begin(ctx, st);
-        l = launch_tile_order(P<uint2>(sc.ranges), tiles, P<uint32_t>(sc.order), st);
-        stage_end(ctx, ST_TILE_ORDER, l, st);
         CK(cudaGetLastError());
-    } else {
-        stage_begin(ctx, st);
-        l = launch_tile_order(P<uint2>(sc.ranges), tiles, P<uint32_t>(sc.order), st);
-        stage_end(ctx, ST_TILE_ORDER, l, st);
     }
     if (!ids) {
         CKS(ensure(ctx, sc.tvals[0], 16));
@@ -547,7 +565,7 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
     if (n == 0) CKS(ensure(ctx, sc.rec, 16 * 3));
 
     // 4. blend
-    stage_begin(ctx, st);
+    stage_begin(ctx, ST_BLEND, st);
     l = launch_blend(P<uint2>(sc.ranges), P<uint32_t>(sc.order), ids, P<float4>(sc.rec), dc,
                      bgv, image, final_T, dctr, sched.blend_batch, st);
     stage_end(ctx, ST_BLEND, l, st);
@@ -680,6 +698,7 @@ recogs_status enqueue_lanes(recogs_ctx* ctx, const recogs_scene* scenes, const r
         for (int i = 0; i < n_views; ++i) {
             if (ctx->plan[i].lane != (int)li) continue;
             const recogs_view& v = views[i];
+            sched.class_hint = ctx->plan[i].class_tiles;
             CKS(render_device(ctx, l.sc, sched, scenes[v.scene], v.camera, v.edit, v.bg,
                               v.image_hwc_out, v.final_T_out, nullptr, l.stream));
         }
@@ -999,7 +1018,7 @@ recogs_status recogs_select(recogs_ctx* ctx, const recogs_scene* scene,
         return fail(ctx, RECOGS_EINVAL, "mask_out is NULL or misaligned");
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
-    stage_begin(ctx, st);
+    stage_begin(ctx, ST_SELECT, st);
     const int l = launch_select(*scene, dev_camera(*camera), dr, mask_out, near_boundary_out, st);
     stage_end(ctx, ST_SELECT, l, st);
     CK(cudaGetLastError());
@@ -1017,7 +1036,7 @@ recogs_status recogs_recolor(recogs_ctx* ctx, recogs_scene* scene, const uint32_
     cudaStream_t st = (cudaStream_t)stream;
     float fix[3];
     dc_fix_of(tint->color_matrix, fix);
-    stage_begin(ctx, st);
+    stage_begin(ctx, ST_RECOLOR, st);
     const int l = launch_recolor(*scene, mask, tint->color_matrix, fix, st);
     stage_end(ctx, ST_RECOLOR, l, st);
     CK(cudaGetLastError());
@@ -1078,7 +1097,7 @@ recogs_status recogs_render_host(recogs_ctx* ctx, const recogs_scene* hs,
     ds.quat = P<float>(ctx->hs_q);
     ds.opacity_logit = P<float>(ctx->hs_op);
     ds.sh = ctx->hs_sh.p;
-    stage_begin(ctx, st);
+    stage_begin(ctx, ST_H2D, st);
     if (n > 0) {
         CK(cudaMemcpyAsync((void*)ds.xyz, hs->xyz, 12 * n, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync((void*)ds.log_scale, hs->log_scale, 12 * n, cudaMemcpyHostToDevice, st));
@@ -1090,7 +1109,7 @@ recogs_status recogs_render_host(recogs_ctx* ctx, const recogs_scene* hs,
     stage_end(ctx, ST_H2D, 0, st);
     CKS(render_device(ctx, ctx->main, ctx->sched, ds, *camera, edit, bgv, P<float>(ctx->hs_img),
                       final_T_host ? P<float>(ctx->hs_T) : nullptr, stats, st));
-    stage_begin(ctx, st);
+    stage_begin(ctx, ST_D2H, st);
     CK(cudaMemcpyAsync(image_hwc_host, ctx->hs_img.p, 12 * npix, cudaMemcpyDeviceToHost, st));
     if (final_T_host)
         CK(cudaMemcpyAsync(final_T_host, ctx->hs_T.p, 4 * npix, cudaMemcpyDeviceToHost, st));
@@ -1115,6 +1134,12 @@ recogs_status recogs_tile_lists(recogs_ctx* ctx, uint32_t* ranges_out, uint32_t*
     if (ctx->last_pairs > 0)
         CK(cudaMemcpyAsync(ids_out, ctx->last_ids, sizeof(uint32_t) * (size_t)ctx->last_pairs,
                            cudaMemcpyDeviceToDevice, st));
+    return RECOGS_OK;
+}
+
+recogs_status recogs_set_timed_stages(recogs_ctx* ctx, uint32_t mask) {
+    if (!ctx) return RECOGS_EINVAL;
+    ctx->timed_stages = mask;
     return RECOGS_OK;
 }
 

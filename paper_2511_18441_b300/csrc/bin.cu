@@ -21,14 +21,19 @@ namespace recogs {
 
 // One warp per tile: lane l holds partition l (lanes beyond PARTS hold 0).
 template <int PARTS>
-__global__ void __launch_bounds__(256) tile_totals_kernel(const uint32_t* __restrict__ tile_count,
+__global__ void __launch_bounds__(256) tile_totals_kernel(uint32_t* __restrict__ tile_count,
                                                           int tiles, uint32_t* __restrict__ cursor,
                                                           uint32_t* __restrict__ totals) {
     static_assert(PARTS <= 32, "one partition per lane");
     const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (t >= tiles) return;
-    const uint32_t c = lane < PARTS ? tile_count[(size_t)t * PARTS + lane] : 0u;
+    uint32_t c = 0u;
+    if (lane < PARTS) {
+        // consume the count and leave it zero for the next frame
+        c = tile_count[(size_t)t * PARTS + lane];
+        tile_count[(size_t)t * PARTS + lane] = 0u;
+    }
     uint32_t inc = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -39,7 +44,7 @@ __global__ void __launch_bounds__(256) tile_totals_kernel(const uint32_t* __rest
     if (lane == 31) totals[t] = inc;
 }
 
-int launch_tile_totals(const uint32_t* tile_count, int tiles, int parts, uint32_t* cursor,
+int launch_tile_totals(uint32_t* tile_count, int tiles, int parts, uint32_t* cursor,
                        uint32_t* totals, cudaStream_t st) {
     if (parts == kTileParts)
         tile_totals_kernel<kTileParts><<<(tiles + 7) / 8, 256, 0, st>>>(tile_count, tiles, cursor,
@@ -64,13 +69,17 @@ __device__ __forceinline__ int sort_class(uint32_t c) {
 
 __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restrict__ totals,
                                                          int tiles, uint2* __restrict__ ranges,
+                                                         uint32_t* __restrict__ order,
                                                          DevCounters* __restrict__ ctr,
                                                          uint32_t capacity) {
     __shared__ uint32_t s_warp[33];
     __shared__ uint32_t s_max[32];
     __shared__ uint32_t s_cls[kSortClasses];
+    __shared__ uint32_t s_hist[kOrderBuckets];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    static_assert(kOrderBuckets == 1024, "one order bucket per thread");
     if (threadIdx.x < kSortClasses) s_cls[threadIdx.x] = 0;
+    s_hist[threadIdx.x] = 0;
     __syncthreads();
     unsigned long long carry = 0;
     uint32_t mx = 0;
@@ -79,6 +88,7 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restr
         const uint32_t c = t < tiles ? totals[t] : 0u;
         mx = max(mx, c);
         if (c) atomicAdd(&s_cls[sort_class(c)], 1u);
+        if (t < tiles) atomicAdd(&s_hist[order_bucket(c)], 1u);
         uint32_t inc = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -124,11 +134,38 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restr
             if (capacity != 0xffffffffu) ctr->skip = 1u;
         }
     }
+    // tile order: a counting sort of the tiles by order_bucket (the order
+    // inside a bucket is arbitrary, which changes no pixel)
+    const uint32_t x = s_hist[threadIdx.x];
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    __syncthreads();
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = s_warp[lane];
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        s_warp[lane] = wi - w;
+    }
+    __syncthreads();
+    s_hist[threadIdx.x] = s_warp[warp] + inc - x;
+    __syncthreads();
+    for (int t = threadIdx.x; t < tiles; t += 1024)
+        order[atomicAdd(&s_hist[order_bucket(totals[t])], 1u)] = (uint32_t)t;
 }
 
-int launch_tile_scan(const uint32_t* totals, int tiles, uint2* ranges, DevCounters* counters,
-                     uint32_t capacity, cudaStream_t st) {
-    tile_scan_kernel<<<1, 1024, 0, st>>>(totals, tiles, ranges, counters, capacity);
+int launch_tile_scan(const uint32_t* totals, int tiles, uint2* ranges, uint32_t* order,
+                     DevCounters* counters, uint32_t capacity, cudaStream_t st) {
+    tile_scan_kernel<<<1, 1024, 0, st>>>(totals, tiles, ranges, order, counters, capacity);
     return 1;
 }
 
@@ -582,16 +619,22 @@ static void sort_class_launch(uint32_t bound, const uint2* ranges, const uint32_
 }
 
 int launch_tile_sort(const uint2* ranges, const uint32_t* order, const uint32_t* class_tiles,
-                     int tiles, const unsigned long long* keys, uint32_t* ids,
+                     bool exact, int tiles, const unsigned long long* keys, uint32_t* ids,
                      const DevCounters* counters, int radix_classes, cudaStream_t st) {
     // Classes follow each other in the tile order from the largest CTA (1024
-    // threads) down. With host-known class sizes (class_tiles != NULL) empty
-    // classes are skipped; otherwise every class is launched with a persistent
-    // grid and reads its size on the device.
+    // threads) down. Every launch is a persistent grid that reads its class's
+    // size on the device; class_tiles only sizes the grids: exact host-known
+    // sizes (empty classes are skipped), a hint from an earlier frame (grids
+    // for 1.25x the hinted tiles, at least one block), or NULL (full grids).
     int launches = 0;
     for (int c = 0; c < kSortClasses; ++c) {
-        const uint32_t bound = class_tiles ? class_tiles[c] : (uint32_t)tiles;
-        if (bound == 0) continue;
+        uint32_t bound = (uint32_t)tiles;
+        if (class_tiles && exact) {
+            bound = class_tiles[c];
+            if (bound == 0) continue;
+        } else if (class_tiles) {
+            bound = class_tiles[c] + class_tiles[c] / 4 + 1;
+        }
         const bool radix = c < radix_classes;
         switch (c) {
             case 0:

@@ -2,7 +2,7 @@
 // Sec. 3.1) with HWC output (Sec. 4.2).
 //
 // One CTA of 256 threads per 16x16 tile, one thread per pixel; tiles are
-// launched heaviest first (tile_order_kernel). Each warp owns an 8x4-pixel
+// launched heaviest first (the tile order of the tile scan). Each warp owns an 8x4-pixel
 // sub-tile made of four 4x2-pixel groups of 8 lanes. Each batch of up to 256
 // (or 128) depth-sorted Gaussians is gathered by one thread per Gaussian (the next
 // batch is prefetched into registers while the current one is blended) and
@@ -190,61 +190,6 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
         if (final_T) final_T[p] = T;
     }
     if (threadIdx.x == 0 && ctr) atomicAdd(&ctr->pairs_read, (unsigned long long)(fetched - begin));
-}
-
-// Position bucket of a tile with c pairs in the tile order: descending pair
-// count in buckets of 8 pairs (b = min(c >> 3, 1022) goes to 1022 - b), empty
-// tiles last in a bucket of their own.
-__device__ __forceinline__ uint32_t order_bucket(uint32_t c) {
-    return c == 0u ? 1023u : 1022u - min(c >> 3, 1022u);
-}
-
-// Counting sort of the tiles by order_bucket (one block; the order inside a
-// bucket is arbitrary, which changes no pixel).
-__global__ void __launch_bounds__(1024) tile_order_kernel(const uint2* __restrict__ ranges,
-                                                          int tiles, uint32_t* __restrict__ order) {
-    __shared__ uint32_t s_hist[1024];
-    __shared__ uint32_t s_warp[32];
-    s_hist[threadIdx.x] = 0;
-    __syncthreads();
-    for (int t = threadIdx.x; t < tiles; t += 1024) {
-        const uint2 r = ranges[t];
-        atomicAdd(&s_hist[order_bucket(r.y - r.x)], 1u);
-    }
-    __syncthreads();
-    // exclusive scan of the 1024 bucket sizes, one per thread
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t x = s_hist[threadIdx.x];
-    uint32_t inc = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_warp[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t w = s_warp[lane];
-        uint32_t wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += y;
-        }
-        s_warp[lane] = wi - w;
-    }
-    __syncthreads();
-    s_hist[threadIdx.x] = s_warp[warp] + inc - x;
-    __syncthreads();
-    for (int t = threadIdx.x; t < tiles; t += 1024) {
-        const uint2 r = ranges[t];
-        order[atomicAdd(&s_hist[order_bucket(r.y - r.x)], 1u)] = (uint32_t)t;
-    }
-}
-
-int launch_tile_order(const uint2* ranges, int tiles, uint32_t* order, cudaStream_t st) {
-    tile_order_kernel<<<1, 1024, 0, st>>>(ranges, tiles, order);
-    return 1;
 }
 
 int launch_blend(const uint2* ranges, const uint32_t* order, const uint32_t* ids, const float4* rec,

@@ -231,7 +231,7 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
         launch_scan_small(po.block_sums, U32(oBlockOffsets), nb, 1, &dctr->n_visible, st);
     }
     launch_tile_totals(U32(oTileCount), tiles, kTilePartsSmall, U32(oCursor), U32(oTileTotals), st);
-    launch_tile_scan(U32(oTileTotals), tiles, ranges, dctr, 0xffffffffu, st);
+    launch_tile_scan(U32(oTileTotals), tiles, ranges, U32(oOrder), dctr, 0xffffffffu, st);
     NA_CK(cudaGetLastError());
     NA_CK(cudaMemcpyAsync(&hc, dctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
     NA_CK(cudaStreamSynchronize(st));
@@ -243,20 +243,22 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
                       "a bounded device wait of an earlier call's sort gave up; that image "
                       "is invalid");
     }
+    if ((P > 0) != (V > 0))
+        return report(err, el, RECOGS_ECUDA, "inconsistent frame counters (%u visible, %u pairs)",
+                      V, P);
     if ((size_t)P > kMaxP)
         return report(err, el, RECOGS_ECAPACITY,
                       "%u (tile, Gaussian) pairs exceed the no-alloc limit of %d; the image "
                       "was not written (use recogs_render)",
                       P, RECOGS_NOALLOC_MAX_PAIRS);
     const uint32_t* ids = U32(oTvals0);
-    if (V > 0 && (int)hc.max_tile <= kMaxSmemTile) {
+    if (P > 0 && (int)hc.max_tile <= kMaxSmemTile) {
         unsigned long long* keys = reinterpret_cast<unsigned long long*>(base + oTkeys0);
         launch_scatter(U32(oCount), reinterpret_cast<const uint2*>(base + oRect), U32(oZkey), n,
                        dc.tiles_x, ranges, U32(oCursor), kTilePartsSmall, keys, dctr, st);
-        launch_tile_order(ranges, tiles, U32(oOrder), st);
-        launch_tile_sort(ranges, U32(oOrder), hc.class_tiles, tiles, keys, U32(oTvals0), dctr, 4,
+        launch_tile_sort(ranges, U32(oOrder), hc.class_tiles, true, tiles, keys, U32(oTvals0), dctr, 4,
                          st);
-    } else if (V > 0) {
+    } else if (P > 0) {
         launch_compact(U32(oCount), U32(oZkey), n, U32(oBlockOffsets), dctr, U32(oDkeys0),
                        U32(oDvals0), st);
         SortBuffers sb;
@@ -285,9 +287,6 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
         const int tbits = tiles <= 1 ? 0 : 32 - __builtin_clz((uint32_t)(tiles - 1));
         const int tcur = radix_sort_pairs(tb, (int)P, tbits, st, &l);
         ids = tb.vals[tcur];
-        launch_tile_order(ranges, tiles, U32(oOrder), st);
-    } else {
-        launch_tile_order(ranges, tiles, U32(oOrder), st);
     }
     NA_CK(cudaGetLastError());
     launch_blend(ranges, U32(oOrder), ids, rec, dc, bgv, image_hwc_out, final_T_out, dctr, 256, st);

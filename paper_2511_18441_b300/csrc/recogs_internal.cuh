@@ -79,6 +79,15 @@ constexpr int kMaxSmemTile = 8192;
 constexpr int kTileParts = 16;
 constexpr int kTilePartsSmall = 32;
 
+// Position bucket of a tile with c pairs in the tile order (heaviest first,
+// the order of the per-tile sort classes and of the blend's CTAs):
+// descending pair count in buckets of 8 pairs (b = min(c >> 3, 1022) goes to
+// 1022 - b), empty tiles last in a bucket of their own.
+constexpr int kOrderBuckets = 1024;
+__device__ __forceinline__ uint32_t order_bucket(uint32_t c) {
+    return c == 0u ? 1023u : 1022u - min(c >> 3, 1022u);
+}
+
 // --------------------------------------------------------------------------
 // Exact-rounding helpers shared by the selection and recolour code so that
 // the fused and the stand-alone paths produce identical bits.
@@ -194,25 +203,29 @@ int launch_emit(const uint32_t* sorted_ids, const uint32_t* counts_sorted, const
                 const uint32_t* block_offsets, int tiles_x, uint32_t* tile_keys, uint32_t* vals,
                 cudaStream_t st);
 // Tile binning (bin.cu). tile_totals: per tile, the total and each
-// partition's exclusive offset (into cursor); tile_scan: ranges, the pair
-// total, the largest tile and the tile count of every sort class; scatter:
+// partition's exclusive offset (into cursor); tile_scan: ranges, the tile
+// order, the pair total, the largest tile and the tile count of every sort
+// class; scatter:
 // 64-bit (depth << 32 | index) keys into the ranges; tile_sort: per-tile sort
 // of the keys, writing the ordered Gaussian indices (class_tiles from the
 // host copy of the counters).
-int launch_tile_totals(const uint32_t* tile_count, int tiles, int parts, uint32_t* cursor,
+// tile_totals zeroes the counts it consumes, so tile_count is all zero
+// again after every frame.
+int launch_tile_totals(uint32_t* tile_count, int tiles, int parts, uint32_t* cursor,
                        uint32_t* totals, cudaStream_t st);
-int launch_tile_scan(const uint32_t* totals, int tiles, uint2* ranges, DevCounters* counters,
-                     uint32_t capacity, cudaStream_t st);
+// tile_scan also writes the tile order (tiles by order_bucket).
+int launch_tile_scan(const uint32_t* totals, int tiles, uint2* ranges, uint32_t* order,
+                     DevCounters* counters, uint32_t capacity, cudaStream_t st);
 int launch_scatter(const uint32_t* count, const uint2* rect, const uint32_t* zkey, int n,
                    int tiles_x, const uint2* ranges, uint32_t* cursor, int parts,
                    unsigned long long* keys, const DevCounters* counters, cudaStream_t st);
-// class_tiles: host copy of the class sizes, or NULL to size the launches on the device
-// Classes 0 .. radix_classes-1 (the largest tiles) are sorted by radix, the rest
-// by the bitonic network.
+// class_tiles: the class sizes (exact: this frame's; otherwise a hint from
+// an earlier frame) or NULL; they only size the persistent grids. Classes
+// 0 .. radix_classes-1 (the largest tiles) are sorted by radix, the rest by
+// the bitonic network.
 int launch_tile_sort(const uint2* ranges, const uint32_t* order, const uint32_t* class_tiles,
-                     int tiles, const unsigned long long* keys, uint32_t* ids,
+                     bool exact, int tiles, const unsigned long long* keys, uint32_t* ids,
                      const DevCounters* counters, int radix_classes, cudaStream_t st);
-int launch_tile_order(const uint2* ranges, int tiles, uint32_t* order, cudaStream_t st);
 // batch: Gaussians staged in shared memory per blend step, 128 or 256
 int launch_blend(const uint2* ranges, const uint32_t* order, const uint32_t* ids, const float4* rec,
                  const DevCamera& cam, const float bg[3], float* image, float* final_T,
