@@ -88,6 +88,12 @@ def lib():
         L.oracle_render_tiles.argtypes = [C.POINTER(Splats), i64p, i32p, C.c_int, C.c_int, C.c_int64,
                                           i32p, f64p, C.POINTER(Margins), f64p, f64p, u8p, i32p,
                                           C.c_int]
+        L.oracle_render_tiles_depth.argtypes = [C.POINTER(Splats), i64p, i32p, C.c_int, C.c_int,
+                                                C.c_int64, i32p, f64p, C.POINTER(Margins), f64p,
+                                                f64p, u8p, i32p, C.c_double, f64p, u8p, C.c_int]
+        L.oracle_color_grad_tiles.argtypes = [C.POINTER(Splats), i64p, i32p, C.c_int, C.c_int,
+                                              f64p, f64p]
+        L.oracle_sh_grad.argtypes = [C.c_int64, f32p, C.POINTER(Camera), f64p, f64p, f64p]
         _lib = L
     return _lib
 
@@ -291,9 +297,10 @@ def tile_lists(splats: SplatResult, order, tiles_x, tiles_y):
 
 
 def render_tiles(splats: SplatResult, offsets, ids, tiles=None, bg=(0.0, 0.0, 0.0), mg=None,
-                 threads=None):
+                 threads=None, tau=None):
     """Binned render of the listed tiles (all by default) into full-size HWC
-    arrays; pixels of other tiles are left at zero."""
+    arrays; pixels of other tiles are left at zero. With tau, also the median
+    depth (Sec. 3.2.2) and its decision flags."""
     cam = splats["camera"]
     W, H = cam.width, cam.height
     tx = (W + 15) // 16
@@ -312,10 +319,73 @@ def render_tiles(splats: SplatResult, offsets, ids, tiles=None, bg=(0.0, 0.0, 0.
     nc = np.zeros((H, W), np.int32)
     m = mg if mg is not None else splats["margins"]
     s = splats.struct()
-    lib().oracle_render_tiles(C.byref(s), _ptr(offsets, i64p), _ptr(ids, i32p), W, H, len(tiles),
-                              _ptr(tiles, i32p), _ptr(bgv, f64p), C.byref(m), _ptr(rgb, f64p),
-                              _ptr(T, f64p), _ptr(flag, u8p), _ptr(nc, i32p), _threads(threads))
-    return dict(rgb=rgb, T=T, flag=flag, ncontrib=nc)
+    if tau is None:
+        lib().oracle_render_tiles(C.byref(s), _ptr(offsets, i64p), _ptr(ids, i32p), W, H,
+                                  len(tiles), _ptr(tiles, i32p), _ptr(bgv, f64p), C.byref(m),
+                                  _ptr(rgb, f64p), _ptr(T, f64p), _ptr(flag, u8p), _ptr(nc, i32p),
+                                  _threads(threads))
+        return dict(rgb=rgb, T=T, flag=flag, ncontrib=nc)
+    depth = np.zeros((H, W))
+    dflag = np.zeros((H, W), np.uint8)
+    lib().oracle_render_tiles_depth(C.byref(s), _ptr(offsets, i64p), _ptr(ids, i32p), W, H,
+                                    len(tiles), _ptr(tiles, i32p), _ptr(bgv, f64p), C.byref(m),
+                                    _ptr(rgb, f64p), _ptr(T, f64p), _ptr(flag, u8p),
+                                    _ptr(nc, i32p), float(tau), _ptr(depth, f64p),
+                                    _ptr(dflag, u8p), _threads(threads))
+    return dict(rgb=rgb, T=T, flag=flag, ncontrib=nc, depth=depth, dflag=dflag)
+
+
+# ---------------------------------------------------------------------------
+# the SH-only refit (Sec. 3.3; Eq. 6 with lambda = 0, Eq. 7 restricted to the
+# SH coefficients)
+
+def l1_loss_grad(y, target):
+    """L1 loss mean |y - target| over the N = H*W*3 values and its gradient
+    sign(y - target) / N (Eq. 6 with the SSIM weight lambda = 0)."""
+    y = np.asarray(y, np.float64)
+    d = y - np.asarray(target, np.float64)
+    N = d.size
+    return float(np.abs(d).sum() / N), np.sign(d) / N
+
+
+def color_grad(splats: SplatResult, offsets, ids, dLdy) -> np.ndarray:
+    """dL/dc_i (shape [n, 3]) of the binned render for the image gradient
+    dLdy (HWC); splats that do not contribute get 0."""
+    cam = splats["camera"]
+    n = splats["n"]
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    ids = np.ascontiguousarray(ids, np.int32)
+    if len(ids) == 0:
+        ids = np.zeros(1, np.int32)
+    g = np.ascontiguousarray(dLdy, np.float64).reshape(-1)
+    out = np.zeros(3 * max(n, 1))
+    s = splats.struct()
+    lib().oracle_color_grad_tiles(C.byref(s), _ptr(offsets, i64p), _ptr(ids, i32p), cam.width,
+                                  cam.height, _ptr(g, f64p), _ptr(out, f64p))
+    return out[:3 * n].reshape(n, 3)
+
+
+def sh_grad(scene, splats: SplatResult, grad_rgb) -> np.ndarray:
+    """dL/dC (layout [16][3][n]) from the colour gradient (Eq. 2)."""
+    n = splats["n"]
+    xyz = np.ascontiguousarray(scene.xyz, np.float32)
+    g = np.ascontiguousarray(grad_rgb, np.float64).reshape(-1)
+    out = np.zeros((16, 3, n))
+    camc = camera_struct(splats["camera"])
+    lib().oracle_sh_grad(n, _ptr(xyz, f32p), C.byref(camc), _ptr(splats["rgb"], f64p),
+                         _ptr(g, f64p), _ptr(out, f64p))
+    return out
+
+
+def adam_step(C, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-15):
+    """One Adam step (Kingma and Ba, 2015) with bias correction at step t
+    (1-based); returns the new (C, m, v). The optimiser of the refit is not
+    named by the paper; Adam is the optimiser of the 3DGS rasteriser it uses."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mh = m / (1.0 - beta1 ** t)
+    vh = v / (1.0 - beta2 ** t)
+    return C - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
 def render_image(scene, cam, edit=None, bg=(0.0, 0.0, 0.0), mg=None, sh=None, threads=None):

@@ -519,9 +519,18 @@ int64_t oracle_depth_order(int64_t n, const oracle_splats* s, int64_t* order) {
  * T_i (1 - alpha_i) would drop below 1e-4; output C + T_final bg. The
  * exponent is at most 0 for a positive-definite conic, so no splat is
  * skipped for a positive exponent. */
+/* Median depth (Sec. 3.2.2): the depth of the pixel is the view depth t_z of
+ * the splat whose blending takes T from at least tau to below tau; 0 if T
+ * never drops below tau. tau is not given by the paper; callers pass it.
+ * depth_out may be NULL. dflag_out: 1 where T after that splat lies within
+ * its float32 uncertainty of tau, so the splat a float32 blend picks may
+ * differ. */
 static void blend_pixel(const oracle_splats* s, const int64_t* list, int64_t len, int use_shortcut,
                         double px, double py, const double bg[3], const oracle_margins* mg,
-                        double* rgb_out, double* T_out, uint8_t* flag_out, int32_t* nc_out) {
+                        double* rgb_out, double* T_out, uint8_t* flag_out, int32_t* nc_out,
+                        double tau, double* depth_out, uint8_t* dflag_out) {
+    double depth = 0.0;
+    uint8_t dflag = 0;
     double C[3] = {0.0, 0.0, 0.0};
     double T = 1.0;
     double eT = 0.0; /* relative uncertainty accumulated in T */
@@ -586,6 +595,12 @@ static void blend_pixel(const oracle_splats* s, const int64_t* list, int64_t len
         prev_alpha = alpha;
         prev_T = T;
         for (int ch = 0; ch < 3; ++ch) C[ch] += s->rgb[3 * i + ch] * alpha * T;
+        if (depth_out && T >= tau && testT < tau) {
+            depth = s->depth[i];
+            if (fabs(log(testT / tau)) <= eT_next) dflag = 1;
+        } else if (depth_out && T >= tau && fabs(log(testT / tau)) <= eT_next) {
+            dflag = 1;   /* stays above tau only within the uncertainty */
+        }
         T = testT;
         eT = eT_next;
         ++count;
@@ -594,6 +609,10 @@ static void blend_pixel(const oracle_splats* s, const int64_t* list, int64_t len
     *T_out = T;
     *flag_out = flag;
     *nc_out = count;
+    if (depth_out) {
+        *depth_out = depth;
+        *dflag_out = dflag;
+    }
 }
 
 typedef struct {
@@ -612,7 +631,7 @@ static void pix_range(void* vctx, int64_t b, int64_t e) {
     pix_ctx* P = (pix_ctx*)vctx;
     for (int64_t j = b; j < e; ++j)
         blend_pixel(P->s, P->order, P->n_order, 1, (double)P->px[j], (double)P->py[j], P->bg, P->mg,
-                    &P->rgb[3 * j], &P->T[j], &P->flag[j], &P->nc[j]);
+                    &P->rgb[3 * j], &P->T[j], &P->flag[j], &P->nc[j], 0.0, NULL, NULL);
 }
 
 void oracle_render_pixels(const oracle_splats* s, const int64_t* order, int64_t n_order,
@@ -664,6 +683,9 @@ typedef struct {
     double *rgb, *T;
     uint8_t* flag;
     int32_t* nc;
+    double tau;
+    double* depth;
+    uint8_t* dflag;
 } tile_ctx;
 
 static void tile_range_fn(void* vctx, int64_t b, int64_t e) {
@@ -678,17 +700,85 @@ static void tile_range_fn(void* vctx, int64_t b, int64_t e) {
             for (int x = tx * TILE; x < tx * TILE + TILE && x < P->width; ++x) {
                 int64_t pix = (int64_t)y * P->width + x;
                 blend_pixel(P->s, list, len, 0, (double)x, (double)y, P->bg, P->mg,
-                            &P->rgb[3 * pix], &P->T[pix], &P->flag[pix], &P->nc[pix]);
+                            &P->rgb[3 * pix], &P->T[pix], &P->flag[pix], &P->nc[pix], P->tau,
+                            P->depth ? &P->depth[pix] : NULL, P->depth ? &P->dflag[pix] : NULL);
             }
         free(list);
     }
+}
+
+void oracle_render_tiles_depth(const oracle_splats* s, const int64_t* offsets, const int32_t* ids,
+                               int width, int height, int64_t n_sel, const int32_t* tile_sel,
+                               const double bg[3], const oracle_margins* mg, double* rgb,
+                               double* T, uint8_t* flag, int32_t* ncontrib, double tau,
+                               double* depth, uint8_t* dflag, int threads) {
+    tile_ctx P = {s, offsets, ids, width, height, (width + TILE - 1) / TILE, tile_sel, bg, mg,
+                  rgb, T, flag, ncontrib, tau, depth, dflag};
+    parallel_for(n_sel, 1, threads, tile_range_fn, &P);
 }
 
 void oracle_render_tiles(const oracle_splats* s, const int64_t* offsets, const int32_t* ids,
                          int width, int height, int64_t n_sel, const int32_t* tile_sel,
                          const double bg[3], const oracle_margins* mg, double* rgb, double* T,
                          uint8_t* flag, int32_t* ncontrib, int threads) {
-    tile_ctx P = {s, offsets, ids, width, height, (width + TILE - 1) / TILE, tile_sel, bg, mg,
-                  rgb, T, flag, ncontrib};
-    parallel_for(n_sel, 1, threads, tile_range_fn, &P);
+    oracle_render_tiles_depth(s, offsets, ids, width, height, n_sel, tile_sel, bg, mg, rgb, T,
+                              flag, ncontrib, 0.0, NULL, NULL, threads);
+}
+
+/* ------------------------------------------------------------------------ */
+/* gradients of the SH-only refit (Sec. 3.3, Eq. 6-7)                       */
+
+/* Colour gradient of the binned render. Eq. 3 is linear in the splat
+ * colours: y_p = sum_i c_i alpha_i(p) T_i(p) + T_final(p) bg, so
+ * dL/dc_i = sum_p dL/dy_p alpha_i(p) T_i(p) over the pixels p where splat i
+ * contributes (same skip and termination rules as the render). dLdy: HWC
+ * [H*W*3]; grad_rgb: [3n], accumulated (the caller zeroes it). */
+void oracle_color_grad_tiles(const oracle_splats* s, const int64_t* offsets, const int32_t* ids,
+                             int width, int height, const double* dLdy, double* grad_rgb) {
+    const int tiles_x = (width + TILE - 1) / TILE, tiles_y = (height + TILE - 1) / TILE;
+    const double a_min = 1.0 / 255.0;
+    for (int ty = 0; ty < tiles_y; ++ty)
+        for (int tx = 0; tx < tiles_x; ++tx) {
+            const int64_t t = (int64_t)ty * tiles_x + tx;
+            for (int y = ty * TILE; y < ty * TILE + TILE && y < height; ++y)
+                for (int x = tx * TILE; x < tx * TILE + TILE && x < width; ++x) {
+                    const double* g = &dLdy[3 * ((int64_t)y * width + x)];
+                    double T = 1.0;
+                    for (int64_t k = offsets[t]; k < offsets[t + 1]; ++k) {
+                        const int64_t i = ids[k];
+                        if (!s->valid[i]) continue;
+                        double dx = x - s->u[i], dy = y - s->v[i];
+                        double A = s->conic[3 * i], B = s->conic[3 * i + 1];
+                        double Cc = s->conic[3 * i + 2];
+                        double p = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy;
+                        if (p > 0.0) p = 0.0;
+                        double alpha = s->opacity[i] * exp(p);
+                        if (alpha > 0.99) alpha = 0.99;
+                        if (alpha < a_min) continue;
+                        double testT = T * (1.0 - alpha);
+                        if (testT < 1e-4) break;
+                        for (int ch = 0; ch < 3; ++ch) grad_rgb[3 * i + ch] += g[ch] * alpha * T;
+                        T = testT;
+                    }
+                }
+        }
+}
+
+/* SH gradient from the colour gradient (Eq. 2 with the shown colour
+ * c = max(f + 0.5, 0), f = sum_k C_k Y_k(d), d = (mu - camera) / |mu - camera|):
+ * dL/dC_{k,ch} = Y_k(d) [c_ch > 0] dL/dc_ch. rgb: [3n] shown colours (the
+ * clamp is active where c = 0); grad_sh: [16][3][n]. */
+void oracle_sh_grad(int64_t n, const float* xyz, const oracle_camera* cam, const double* rgb,
+                    const double* grad_rgb, double* grad_sh) {
+    for (int64_t i = 0; i < n; ++i) {
+        double d[3] = {(double)xyz[i] - cam->cam_pos[0], (double)xyz[n + i] - cam->cam_pos[1],
+                       (double)xyz[2 * n + i] - cam->cam_pos[2]};
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double Y[16];
+        oracle_sh_basis(d[0] / r, d[1] / r, d[2] / r, Y);
+        for (int k = 0; k < 16; ++k)
+            for (int ch = 0; ch < 3; ++ch)
+                grad_sh[((int64_t)k * 3 + ch) * n + i] =
+                    rgb[3 * i + ch] > 0.0 ? Y[k] * grad_rgb[3 * i + ch] : 0.0;
+    }
 }

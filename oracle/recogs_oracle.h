@@ -135,6 +135,24 @@ void oracle_render_tiles(const oracle_splats* s, const int64_t* offsets, const i
                          const double bg[3], const oracle_margins* mg, double* rgb, double* T,
                          uint8_t* flag, int32_t* ncontrib, int threads);
 
+/* oracle_render_tiles plus the median depth of each pixel (Sec. 3.2.2): the
+ * view depth of the splat whose blending takes T from >= tau to < tau, 0 if
+ * none; dflag marks pixels where float32 may pick another splat. */
+void oracle_render_tiles_depth(const oracle_splats* s, const int64_t* offsets, const int32_t* ids,
+                               int width, int height, int64_t n_sel, const int32_t* tile_sel,
+                               const double bg[3], const oracle_margins* mg, double* rgb,
+                               double* T, uint8_t* flag, int32_t* ncontrib, double tau,
+                               double* depth, uint8_t* dflag, int threads);
+
+/* SH-only refit (Sec. 3.3, Eq. 6-7): the colour gradient dL/dc_i =
+ * sum_p dL/dy_p alpha_i(p) T_i(p) of the binned render (accumulated into
+ * grad_rgb[3n]), and the SH gradient dL/dC_{k,ch} = Y_k(d) [c_ch > 0] dL/dc_ch
+ * (grad_sh [16][3][n]). */
+void oracle_color_grad_tiles(const oracle_splats* s, const int64_t* offsets, const int32_t* ids,
+                             int width, int height, const double* dLdy, double* grad_rgb);
+void oracle_sh_grad(int64_t n, const float* xyz, const oracle_camera* cam, const double* rgb,
+                    const double* grad_rgb, double* grad_sh);
+
 #ifdef __cplusplus
 }
 #endif

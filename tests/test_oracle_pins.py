@@ -590,3 +590,145 @@ def test_tile_range_is_the_tiles_with_a_pixel_centre_in_the_box():
         if hit:
             assert tx0 <= hit[0] and tx1 >= hit[-1]
             assert tx1 - tx0 + 1 - len(hit) <= (1 if 2 * ex < 1 else 0)
+
+
+# ---------------------------------------------------------------------------
+# median depth (Sec. 3.2.2) and the SH-only refit (Sec. 3.3, Eq. 6-7)
+
+def stack_scene(opacities, depths, scale=3.0):
+    """Wide on-axis splats (near-constant alpha over a 16x16 view) at the
+    given world depths, rgb = 0.5 everywhere."""
+    n = len(opacities)
+    logit = [math.log(o / (1 - o)) for o in opacities]
+    return make_scene(np.stack([np.zeros(n), np.zeros(n), np.asarray(depths, np.float64)]),
+                      np.full((3, n), math.log(scale)), np.tile([[1.0], [0], [0], [0]], n),
+                      np.asarray(logit), np.zeros((16, 3, n)))
+
+
+@pytest.mark.parametrize("tau,expect", [(0.5, 1), (0.2, 2), (0.01, None)])
+def test_median_depth_is_the_splat_that_takes_T_below_tau(tau, expect):
+    """Opacities 0.3, 0.5, 0.9 front to back: T after each is about 0.7,
+    0.35, 0.035, so tau = 0.5 picks the second splat, tau = 0.2 the third,
+    and tau = 0.01 none (depth 0). The depth is the splat's view depth,
+    here the camera distance plus its world z."""
+    cam = sg.axis_camera(16, 16, 60.0, 2.0)
+    z = [0.0, 0.25, 0.5]
+    sc = stack_scene([0.3, 0.5, 0.9], z)
+    sp = oracle.preprocess(sc, cam)
+    order = oracle.depth_order(sp)
+    off, ids = oracle.tile_lists(sp, order, 1, 1)
+    out = oracle.render_tiles(sp, off, ids, tau=tau)
+    plain = oracle.render_tiles(sp, off, ids)
+    np.testing.assert_array_equal(out["rgb"], plain["rgb"])
+    d = out["depth"][8, 8]
+    if expect is None:
+        assert d == 0.0
+    else:
+        assert d == pytest.approx(2.0 + z[expect], abs=1e-12)
+        # and it is the first splat after which T < tau at that pixel
+        T = 1.0
+        for k in range(3):
+            A, B, Cc = sp["conic"][3 * k:3 * k + 3]
+            dx, dy = 8 - sp["u"][k], 8 - sp["v"][k]
+            a = min(0.99, sp["opacity"][k] * math.exp(-0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy))
+            if T >= tau > T * (1 - a):
+                assert k == expect
+                break
+            T *= 1 - a
+    assert not out["dflag"].any()
+
+
+def refit_scene():
+    w = sg.tiny_workload(n=400, width=48, height=40)
+    return w.scene, w.camera
+
+
+def l1_of(sp, off, ids, target):
+    img = oracle.render_tiles(sp, off, ids)["rgb"]
+    return oracle.l1_loss_grad(img, target)[0]
+
+
+def test_colour_gradient_matches_finite_differences():
+    """Eq. 3 is linear in the splat colours, so with the signs of y - target
+    held fixed the L1 loss is linear in each colour and a central difference
+    gives the gradient up to rounding."""
+    scene, cam = refit_scene()
+    sp = oracle.preprocess(scene, cam)
+    order = oracle.depth_order(sp)
+    off, ids = oracle.tile_lists(sp, order, 3, 3)
+    y = oracle.render_tiles(sp, off, ids)["rgb"]
+    rng = np.random.default_rng(0)
+    target = y + rng.choice([-1.0, 1.0], size=y.shape) * rng.uniform(0.05, 0.2, size=y.shape)
+    _, g = oracle.l1_loss_grad(y, target)
+    grad = oracle.color_grad(sp, off, ids, g)
+    contributing = np.nonzero(np.abs(grad).sum(1) > 1e-6)[0]
+    assert len(contributing) > 20
+    h = 1e-4
+    for i in rng.choice(contributing, 12, replace=False):
+        for ch in range(3):
+            base = sp["rgb"][3 * i + ch]
+            sp["rgb"][3 * i + ch] = base + h
+            lp = l1_of(sp, off, ids, target)
+            sp["rgb"][3 * i + ch] = base - h
+            lm = l1_of(sp, off, ids, target)
+            sp["rgb"][3 * i + ch] = base
+            assert grad[i, ch] == pytest.approx((lp - lm) / (2 * h), rel=1e-6, abs=1e-12)
+
+
+def test_sh_gradient_matches_finite_differences_through_the_whole_render():
+    """dL/dC of Eq. 2 chained with the colour gradient, against a central
+    difference of the full pipeline (preprocess + render) in one float32
+    SH coefficient; the colour is affine in C away from the clamp."""
+    scene, cam = refit_scene()
+    sp = oracle.preprocess(scene, cam)
+    order = oracle.depth_order(sp)
+    off, ids = oracle.tile_lists(sp, order, 3, 3)
+    y = oracle.render_tiles(sp, off, ids)["rgb"]
+    rng = np.random.default_rng(1)
+    target = y + rng.choice([-1.0, 1.0], size=y.shape) * rng.uniform(0.05, 0.2, size=y.shape)
+    _, g = oracle.l1_loss_grad(y, target)
+    gsh = oracle.sh_grad(scene, sp, oracle.color_grad(sp, off, ids, g))
+    cand = np.nonzero(np.abs(gsh[0]).sum(0) > 1e-6)[0]
+    assert len(cand) > 10
+
+    def loss(sh):
+        s2 = sg.Scene(scene.xyz, scene.log_scale, scene.quat, scene.opacity_logit, sh)
+        p2 = oracle.preprocess(s2, cam)
+        return l1_of(p2, off, ids, target)
+
+    for i in rng.choice(cand, 6, replace=False):
+        for k, ch in ((0, 0), (3, 1), (8, 2), (15, 0)):
+            shp = scene.sh.copy()
+            shm = scene.sh.copy()
+            shp[k, ch, i] = np.float32(shp[k, ch, i] + np.float32(2.0 ** -10))
+            shm[k, ch, i] = np.float32(shm[k, ch, i] - np.float32(2.0 ** -10))
+            dC = float(shp[k, ch, i]) - float(shm[k, ch, i])
+            fd = (loss(shp) - loss(shm)) / dC
+            assert gsh[k, ch, i] == pytest.approx(fd, rel=1e-5, abs=1e-10)
+
+
+def test_adam_first_step_moves_each_coefficient_by_lr_against_its_sign():
+    """From m = v = 0 the bias-corrected first Adam step is lr g / (|g| + eps):
+    lr sign(g) for |g| >> eps, and a zero gradient moves nothing."""
+    rng = np.random.default_rng(2)
+    C0 = rng.normal(size=(16, 3, 5))
+    g = rng.normal(size=C0.shape)
+    g[:, :, 0] = 0.0
+    C1, m, v = oracle.adam_step(C0, g, np.zeros_like(C0), np.zeros_like(C0), 1, 0.01)
+    np.testing.assert_allclose(C1, C0 - 0.01 * np.sign(g), rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(C1[:, :, 0], C0[:, :, 0])
+    np.testing.assert_allclose(m, 0.1 * g)
+    np.testing.assert_allclose(v, 0.001 * g * g)
+
+
+def test_refit_fixed_point_has_zero_loss_and_gradient():
+    """The target rendered from the scene itself is the refit's fixed point:
+    L1 = 0, sign(0) = 0, so every SH gradient and Adam update is zero."""
+    scene, cam = refit_scene()
+    sp = oracle.preprocess(scene, cam)
+    off, ids = oracle.tile_lists(sp, oracle.depth_order(sp), 3, 3)
+    y = oracle.render_tiles(sp, off, ids)["rgb"]
+    loss, g = oracle.l1_loss_grad(y, y)
+    assert loss == 0.0 and not g.any()
+    gsh = oracle.sh_grad(scene, sp, oracle.color_grad(sp, off, ids, g))
+    assert not gsh.any()
