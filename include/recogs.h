@@ -180,6 +180,65 @@ RECOGS_API recogs_status recogs_render_host(recogs_ctx* ctx, const recogs_scene*
                                  const float* bg, float* image_hwc_host, float* final_T_host,
                                  recogs_render_stats* stats, void* stream);
 
+/* recogs_render plus the "median" depth map of Sec. 3.2.2: depth_out
+ * (device, height*width float32) holds, per pixel, the view depth t_z of
+ * the Gaussian whose blending takes the transmittance from >= tau to < tau
+ * (front to back, Eq. 3), and 0 where T never falls below tau. The paper
+ * does not give tau; 0.5 makes it the median of the opacity-weighted depth
+ * distribution along the ray. tau in (0, 1]. */
+RECOGS_API recogs_status recogs_render_depth(recogs_ctx* ctx, const recogs_scene* scene,
+                                             const recogs_camera* camera, const recogs_edit* edit,
+                                             const float* bg, float* image_hwc_out,
+                                             float* final_T_out, float* depth_out, float tau,
+                                             recogs_render_stats* stats, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * SH-only refit (Sec. 3.3, Eq. 6-7)
+ *
+ * With the geometry frozen, the SH coefficients are fitted to an edited
+ * target view. Loss: L = mean |y - target| over the N = 3 * width * height
+ * values of the HWC render y (Eq. 6 with the SSIM weight lambda taken as 0:
+ * dL/dy = sign(y - target) / N). Eq. 7's rasteriser backward is needed
+ * only for dL/dC: Eq. 3 is linear in the colours, dL/dc_i = sum_p dL/dy_p
+ * alpha_i(p) T_i(p) over the pixels where Gaussian i contributes, and
+ * through Eq. 2 dL/dC_{k,ch} = Y_k(d) [c_ch > 0] dL/dc_ch with
+ * c = max(f + 0.5, 0). The scene is rendered without an edit. float32 SH
+ * only (RECOGS_EINVAL otherwise). All device buffers belong to the caller.
+ */
+
+/* Adam (Kingma and Ba, 2015): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * C -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
+typedef struct {
+    float lr;
+    float beta1;                /* e.g. 0.9 */
+    float beta2;                /* e.g. 0.999 */
+    float eps;                  /* e.g. 1e-15 */
+    int32_t step;               /* t >= 1 */
+    int32_t reserved;
+} recogs_adam;
+
+/* Forward render of `scene` from `camera` into image_hwc_out (device, may be
+ * NULL), then the gradients: grad_rgb_out (device [n][3], may be NULL) =
+ * dL/dc, grad_sh_out (device [16][3][n], may be NULL) = dL/dC; loss_out
+ * (host, may be NULL) = L, which makes the call wait for the stream. The
+ * colour gradient is summed with float atomics, so its last bits may vary
+ * from run to run. */
+RECOGS_API recogs_status recogs_refit_grad(recogs_ctx* ctx, const recogs_scene* scene,
+                                           const recogs_camera* camera, const float* bg,
+                                           const float* target_hwc, float* image_hwc_out,
+                                           float* grad_rgb_out, float* grad_sh_out,
+                                           double* loss_out, void* stream);
+
+/* One refit step: the gradient of recogs_refit_grad, then an Adam step of
+ * every SH coefficient of `scene` in place. adam_m, adam_v: device
+ * [16][3][n] float32 moments (zero before the first step), updated in place.
+ * loss_out (host, may be NULL) = L before the step. */
+RECOGS_API recogs_status recogs_refit_step(recogs_ctx* ctx, recogs_scene* scene,
+                                           const recogs_camera* camera, const float* bg,
+                                           const float* target_hwc, float* adam_m, float* adam_v,
+                                           const recogs_adam* adam, double* loss_out,
+                                           void* stream);
+
 /* ---------------------------------------------------------------------------
  * Rendering without allocation
  */

@@ -69,6 +69,11 @@ class CBatchInfo(C.Structure):
                 ("reserved", C.c_int32), ("graph_launches", C.c_int64), ("tuned_ms", C.c_double)]
 
 
+class CAdam(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("step", C.c_int32), ("reserved", C.c_int32)]
+
+
 BATCH_GRAPH, BATCH_TUNE, BATCH_NOWAIT = 1, 2, 4
 
 # Every entry point of include/recogs.h with its ctypes signature.
@@ -104,6 +109,16 @@ SIGNATURES = {
     "recogs_render_batch": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.c_int32,
                                       C.POINTER(CView), C.c_int32, C.c_uint32, C.c_void_p]),
     "recogs_batch_info": (C.c_int, [C.c_void_p, C.POINTER(CBatchInfo)]),
+    "recogs_render_depth": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.POINTER(CCamera),
+                                      C.POINTER(CEdit), C.POINTER(C.c_float), C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_float, C.POINTER(CStats),
+                                      C.c_void_p]),
+    "recogs_refit_grad": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.POINTER(CCamera),
+                                    C.POINTER(C.c_float), C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    "recogs_refit_step": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.POINTER(CCamera),
+                                    C.POINTER(C.c_float), C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.POINTER(CAdam), C.POINTER(C.c_double), C.c_void_p]),
 }
 
 _lib = None
@@ -321,6 +336,69 @@ class Context:
             return image_out, dict(n_visible=st.n_visible, n_pairs=st.n_pairs,
                                    n_pairs_read=st.n_pairs_read, n_tiles=st.n_tiles)
         return image_out
+
+    def render_depth(self, scene: DeviceScene, cam, edit=None, bg=None, tau=0.5, image_out=None,
+                     T_out=None, depth_out=None, stats=False, stream=None):
+        """Render plus the median depth map (Sec. 3.2.2); returns (image, depth)
+        or (image, depth, stats)."""
+        import torch
+        H, W = int(cam.height), int(cam.width)
+        dev = scene.xyz.device
+        if image_out is None:
+            image_out = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+        if depth_out is None:
+            depth_out = torch.empty((H, W), dtype=torch.float32, device=dev)
+        cs = scene.struct()
+        cc = camera_struct(cam)
+        e, keep = edit_struct(edit)
+        bgv = (C.c_float * 3)(*(np.asarray(bg if bg is not None else (0, 0, 0), np.float32)))
+        st = CStats()
+        self._check(self._L.recogs_render_depth(
+            self._h, C.byref(cs), C.byref(cc), C.byref(e) if e is not None else None, bgv,
+            image_out.data_ptr(), T_out.data_ptr() if T_out is not None else None,
+            depth_out.data_ptr(), float(tau), C.byref(st) if stats else None,
+            _stream_ptr(stream)))
+        if stats:
+            return image_out, depth_out, dict(n_visible=st.n_visible, n_pairs=st.n_pairs,
+                                              n_pairs_read=st.n_pairs_read, n_tiles=st.n_tiles)
+        return image_out, depth_out
+
+    def refit_grad(self, scene: DeviceScene, cam, target, bg=None, image_out=None, sh_grad=True,
+                   stream=None):
+        """Forward render and the L1 gradients of the SH-only refit (Sec. 3.3):
+        returns dict(image, grad_rgb [n, 3], grad_sh [16, 3, n] or None, loss)."""
+        import torch
+        H, W = int(cam.height), int(cam.width)
+        dev = scene.xyz.device
+        if image_out is None:
+            image_out = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+        n = scene.n
+        grad_rgb = torch.empty((max(n, 1), 3), dtype=torch.float32, device=dev)
+        grad_sh = torch.empty((16, 3, max(n, 1)), dtype=torch.float32, device=dev) if sh_grad else None
+        cs = scene.struct()
+        cc = camera_struct(cam)
+        bgv = (C.c_float * 3)(*(np.asarray(bg if bg is not None else (0, 0, 0), np.float32)))
+        loss = C.c_double()
+        self._check(self._L.recogs_refit_grad(
+            self._h, C.byref(cs), C.byref(cc), bgv, target.data_ptr(), image_out.data_ptr(),
+            grad_rgb.data_ptr(), grad_sh.data_ptr() if grad_sh is not None else None,
+            C.byref(loss), _stream_ptr(stream)))
+        return dict(image=image_out, grad_rgb=grad_rgb[:n],
+                    grad_sh=grad_sh[:, :, :n] if grad_sh is not None else None, loss=loss.value)
+
+    def refit_step(self, scene: DeviceScene, cam, target, m, v, step, lr, beta1=0.9,
+                   beta2=0.999, eps=1e-15, bg=None, want_loss=True, stream=None):
+        """One SH refit step (Adam on every coefficient, in place); returns the
+        L1 loss before the step (or None with want_loss=False)."""
+        cs = scene.struct()
+        cc = camera_struct(cam)
+        bgv = (C.c_float * 3)(*(np.asarray(bg if bg is not None else (0, 0, 0), np.float32)))
+        a = CAdam(float(lr), float(beta1), float(beta2), float(eps), int(step), 0)
+        loss = C.c_double()
+        self._check(self._L.recogs_refit_step(
+            self._h, C.byref(cs), C.byref(cc), bgv, target.data_ptr(), m.data_ptr(), v.data_ptr(),
+            C.byref(a), C.byref(loss) if want_loss else None, _stream_ptr(stream)))
+        return loss.value if want_loss else None
 
     # -- introspection --------------------------------------------------------
 

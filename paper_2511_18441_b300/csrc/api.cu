@@ -28,13 +28,13 @@ namespace {
 
 enum Stage {
     ST_PREPROCESS, ST_SCAN, ST_COMPACT, ST_SORT_DEPTH, ST_PAIR_OFFSETS, ST_EMIT, ST_SORT_TILE,
-    ST_BLEND, ST_SELECT, ST_RECOLOR, ST_H2D, ST_D2H, ST_SCATTER, ST_TILE_SORT, ST_COUNT
+    ST_BLEND, ST_SELECT, ST_RECOLOR, ST_H2D, ST_D2H, ST_SCATTER, ST_TILE_SORT, ST_REFIT, ST_COUNT
 };
 // "scan" = tile totals, tile ranges and tile order; "compact" .. "sort_tile"
 // = the global sort path
 const char* const kStageNames[ST_COUNT] = {
     "preprocess", "scan", "compact", "sort_depth", "pair_offsets", "emit", "sort_tile",
-    "blend", "select", "recolor", "h2d", "d2h", "scatter", "tile_sort"};
+    "blend", "select", "recolor", "h2d", "d2h", "scatter", "tile_sort", "refit"};
 
 struct DevBuf {
     void* p = nullptr;
@@ -121,6 +121,8 @@ struct recogs_ctx {
     int batch_tune_trials = 0;
     // host-memory render staging
     DevBuf hs_xyz, hs_ls, hs_q, hs_op, hs_sh, hs_img, hs_T;
+    // SH refit: forward image, colour gradient, loss
+    DevBuf rf_img, rf_grad, rf_loss;
     DevCounters* h_counters = nullptr;   // pinned
     // last render
     int64_t last_pairs = 0;
@@ -354,7 +356,7 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
                             const recogs_scene& s, const recogs_camera& cam,
                             const recogs_edit* edit, const float bgv[3], float* image,
                             float* final_T, recogs_render_stats* stats, cudaStream_t st,
-                            ViewPlan* plan_out = nullptr) {
+                            ViewPlan* plan_out = nullptr, const BlendExtra* extra = nullptr) {
     const int n = (int)s.n;
     const DevCamera dc = dev_camera(cam);
     const int tiles = dc.tiles_x * dc.tiles_y;
@@ -566,8 +568,13 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
 
     // 4. blend
     stage_begin(ctx, ST_BLEND, st);
+    BlendExtra ex;
+    if (extra) {
+        ex = *extra;
+        ex.zkey = P<uint32_t>(sc.zkey);
+    }
     l = launch_blend(P<uint2>(sc.ranges), P<uint32_t>(sc.order), ids, P<float4>(sc.rec), dc,
-                     bgv, image, final_T, dctr, sched.blend_batch, st);
+                     bgv, image, final_T, dctr, sched.blend_batch, extra ? &ex : nullptr, st);
     stage_end(ctx, ST_BLEND, l, st);
     CK(cudaGetLastError());
 
@@ -924,6 +931,90 @@ recogs_status plan_batch(recogs_ctx* ctx, const recogs_scene* scenes, int n_scen
     return RECOGS_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// SH-only refit (Sec. 3.3): forward render, colour gradient of the L1 loss
+// (Eq. 6 with the SSIM weight 0), SH gradient (Eq. 7 restricted to C) and an
+// optional Adam step.
+
+recogs_status refit(recogs_ctx* ctx, const recogs_scene& s, const recogs_camera& cam,
+                    const float bgv[3], const float* target, float* image_out,
+                    float* grad_rgb_out, float* grad_sh_out, float* m, float* v,
+                    const recogs_adam* adam, double* loss_out, cudaStream_t st) {
+    const int n = (int)s.n;
+    const size_t npix = (size_t)cam.width * cam.height;
+    float* image = image_out;
+    if (!image) {
+        CKS(ensure(ctx, ctx->rf_img, 12 * npix));
+        image = P<float>(ctx->rf_img);
+    }
+    float* grad_rgb = grad_rgb_out;
+    if (!grad_rgb) {
+        CKS(ensure(ctx, ctx->rf_grad, 12 * (size_t)(n > 0 ? n : 1)));
+        grad_rgb = P<float>(ctx->rf_grad);
+    }
+    CKS(ensure(ctx, ctx->rf_loss, sizeof(double)));
+    // 1. forward render of the unedited scene (with the read back)
+    Schedule sched = ctx->sched;
+    sched.pair_capacity = 0;
+    CKS(render_device(ctx, ctx->main, sched, s, cam, nullptr, bgv, image, nullptr, nullptr, st));
+    if (n > 0) CK(cudaMemsetAsync(grad_rgb, 0, 12 * (size_t)n, st));
+    CK(cudaMemsetAsync(ctx->rf_loss.p, 0, sizeof(double), st));
+    // 2. colour gradient over the same tile lists
+    const DevCamera dc = dev_camera(cam);
+    BlendExtra ex;
+    ex.target = target;
+    ex.inv_n = (float)(1.0 / (3.0 * (double)npix));
+    ex.grad_rgb = grad_rgb;
+    ex.loss = P<double>(ctx->rf_loss);
+    const uint32_t* ids = ctx->last_ids;
+    stage_begin(ctx, ST_BLEND, st);
+    int l = launch_blend(P<uint2>(ctx->main.ranges), P<uint32_t>(ctx->main.order), ids,
+                         P<float4>(ctx->main.rec), dc, bgv, image, nullptr, nullptr,
+                         sched.blend_batch, &ex, st);
+    stage_end(ctx, ST_BLEND, l, st);
+    // 3. SH gradient and the optional Adam step
+    RefitAdam ra = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (adam) {
+        ra.lr = adam->lr;
+        ra.beta1 = adam->beta1;
+        ra.beta2 = adam->beta2;
+        ra.eps = adam->eps;
+        ra.inv_bc1 = (float)(1.0 / (1.0 - std::pow((double)adam->beta1, (double)adam->step)));
+        ra.inv_bc2 = (float)(1.0 / (1.0 - std::pow((double)adam->beta2, (double)adam->step)));
+    }
+    stage_begin(ctx, ST_REFIT, st);
+    l = launch_sh_refit(n, s.xyz, cam.cam_pos, P<float4>(ctx->main.rec),
+                        P<uint32_t>(ctx->main.count), grad_rgb, (float*)s.sh, adam ? m : nullptr,
+                        adam ? v : nullptr, ra, grad_sh_out, st);
+    stage_end(ctx, ST_REFIT, l, st);
+    CK(cudaGetLastError());
+    if (loss_out) {
+        double sum = 0.0;
+        CK(cudaMemcpyAsync(&sum, ctx->rf_loss.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        *loss_out = sum / (3.0 * (double)npix);
+    }
+    return RECOGS_OK;
+}
+
+recogs_status check_refit_args(recogs_ctx* ctx, const recogs_scene* scene,
+                               const recogs_camera* camera, const float* bg, const float* target,
+                               float bgv[3]) {
+    CKS(check_scene(ctx, scene));
+    CKS(check_camera(ctx, camera, "camera"));
+    if (scene->sh_dtype != RECOGS_F32)
+        return fail(ctx, RECOGS_EINVAL, "the SH refit needs float32 SH coefficients");
+    if (!target || !aligned(target, 4)) return fail(ctx, RECOGS_EINVAL, "target is NULL or misaligned");
+    bgv[0] = bgv[1] = bgv[2] = 0.f;
+    if (bg)
+        for (int k = 0; k < 3; ++k) {
+            if (!finite(bg[k])) return fail(ctx, RECOGS_EINVAL, "bg not finite");
+            bgv[k] = bg[k];
+        }
+    return RECOGS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -985,7 +1076,7 @@ void recogs_ctx_destroy(recogs_ctx* ctx) {
     if (ctx->origin) cudaStreamDestroy(ctx->origin);
     if (ctx->fork) cudaEventDestroy(ctx->fork);
     DevBuf* bufs[] = {&ctx->hs_xyz, &ctx->hs_ls, &ctx->hs_q, &ctx->hs_op, &ctx->hs_sh,
-                      &ctx->hs_img, &ctx->hs_T};
+                      &ctx->hs_img, &ctx->hs_T, &ctx->rf_img, &ctx->rf_grad, &ctx->rf_loss};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
@@ -1280,6 +1371,69 @@ recogs_status recogs_batch_info(recogs_ctx* ctx, recogs_batch_info_t* info) {
         if (p.lane < 0) ++crowded;
     info->views_outside_lanes = crowded;
     return RECOGS_OK;
+}
+
+recogs_status recogs_render_depth(recogs_ctx* ctx, const recogs_scene* scene,
+                                  const recogs_camera* camera, const recogs_edit* edit,
+                                  const float* bg, float* image_hwc_out, float* final_T_out,
+                                  float* depth_out, float tau, recogs_render_stats* stats,
+                                  void* stream) {
+    if (!ctx) return RECOGS_EINVAL;
+    CKS(check_scene(ctx, scene));
+    CKS(check_camera(ctx, camera, "camera"));
+    if (!image_hwc_out || !aligned(image_hwc_out, 4))
+        return fail(ctx, RECOGS_EINVAL, "image_hwc_out is NULL or misaligned");
+    if (final_T_out && !aligned(final_T_out, 4))
+        return fail(ctx, RECOGS_EINVAL, "final_T_out is misaligned");
+    if (!depth_out || !aligned(depth_out, 4))
+        return fail(ctx, RECOGS_EINVAL, "depth_out is NULL or misaligned");
+    if (!(tau > 0.f) || !(tau <= 1.f)) return fail(ctx, RECOGS_EINVAL, "tau must be in (0, 1]");
+    float bgv[3] = {0.f, 0.f, 0.f};
+    if (bg)
+        for (int k = 0; k < 3; ++k) {
+            if (!finite(bg[k])) return fail(ctx, RECOGS_EINVAL, "bg not finite");
+            bgv[k] = bg[k];
+        }
+    DeviceGuard g(ctx->device);
+    BlendExtra ex;
+    ex.tau = tau;
+    ex.depth = depth_out;
+    return render_device(ctx, ctx->main, ctx->sched, *scene, *camera, edit, bgv, image_hwc_out,
+                         final_T_out, stats, (cudaStream_t)stream, nullptr, &ex);
+}
+
+recogs_status recogs_refit_grad(recogs_ctx* ctx, const recogs_scene* scene,
+                                const recogs_camera* camera, const float* bg,
+                                const float* target_hwc, float* image_hwc_out,
+                                float* grad_rgb_out, float* grad_sh_out, double* loss_out,
+                                void* stream) {
+    if (!ctx) return RECOGS_EINVAL;
+    float bgv[3];
+    CKS(check_refit_args(ctx, scene, camera, bg, target_hwc, bgv));
+    if ((image_hwc_out && !aligned(image_hwc_out, 4)) || (grad_rgb_out && !aligned(grad_rgb_out, 4)) ||
+        (grad_sh_out && !aligned(grad_sh_out, 4)))
+        return fail(ctx, RECOGS_EINVAL, "an output is misaligned");
+    DeviceGuard g(ctx->device);
+    return refit(ctx, *scene, *camera, bgv, target_hwc, image_hwc_out, grad_rgb_out, grad_sh_out,
+                 nullptr, nullptr, nullptr, loss_out, (cudaStream_t)stream);
+}
+
+recogs_status recogs_refit_step(recogs_ctx* ctx, recogs_scene* scene, const recogs_camera* camera,
+                                const float* bg, const float* target_hwc, float* adam_m,
+                                float* adam_v, const recogs_adam* adam, double* loss_out,
+                                void* stream) {
+    if (!ctx) return RECOGS_EINVAL;
+    float bgv[3];
+    CKS(check_refit_args(ctx, scene, camera, bg, target_hwc, bgv));
+    if (!adam) return fail(ctx, RECOGS_EINVAL, "adam is NULL");
+    if (scene->n > 0 && (!adam_m || !adam_v || !aligned(adam_m, 4) || !aligned(adam_v, 4)))
+        return fail(ctx, RECOGS_EINVAL, "adam_m / adam_v NULL or misaligned");
+    if (adam->step < 1 || !(adam->lr >= 0.f) || !(adam->beta1 >= 0.f && adam->beta1 < 1.f) ||
+        !(adam->beta2 >= 0.f && adam->beta2 < 1.f) || !(adam->eps >= 0.f))
+        return fail(ctx, RECOGS_EINVAL, "Adam parameters out of range");
+    DeviceGuard g(ctx->device);
+    return refit(ctx, *scene, *camera, bgv, target_hwc, nullptr, nullptr, nullptr, adam_m, adam_v,
+                 adam, loss_out, (cudaStream_t)stream);
 }
 
 }  // extern "C"

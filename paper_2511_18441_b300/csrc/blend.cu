@@ -54,19 +54,33 @@ __device__ __forceinline__ uint32_t group_mask(float u, float v, float ex, float
     return mask;
 }
 
+// What a blend launch computes besides the walk itself.
+enum BlendMode {
+    kBlendColour = 0,   // image (and final T)
+    kBlendDepth = 1,    // image, final T and the median depth (Sec. 3.2.2)
+    kBlendGrad = 2      // colour gradient of the L1 loss against a target (Sec. 3.3, Eq. 6-7)
+};
+
 // BATCH (128 or 256) Gaussians are staged per batch; threads below BATCH
-// gather them.
-template <int BATCH>
+// gather them. Every mode walks the same lists with the same arithmetic, so
+// the weights alpha_i T_i of the gradient are those of the image.
+template <int BATCH, int MODE>
 __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
     blend_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
                  const uint32_t* __restrict__ ids, const float4* __restrict__ rec, int width,
                  int height, int tiles_x, float bg0, float bg1, float bg2, float* __restrict__ image,
-                 float* __restrict__ final_T, DevCounters* __restrict__ ctr) {
+                 float* __restrict__ final_T, DevCounters* __restrict__ ctr, BlendExtra ex) {
     static_assert(BATCH == 128 || BATCH == 256, "blend batch");
     __shared__ float4 s_a[BATCH];     // (u, v, q0, q1), centre in this tile's frame
     __shared__ float4 s_b[BATCH];     // (q2, log2 sigma, r, g)
     __shared__ float s_c[BATCH];      // b
     __shared__ uint32_t s_m[BATCH];   // group mask
+    // depth mode: view depth of each staged Gaussian; gradient mode: its index
+    // and its colour gradient summed over this tile's pixels
+    __shared__ float s_z[MODE == kBlendDepth ? BATCH : 1];
+    __shared__ uint32_t s_id[MODE == kBlendGrad ? BATCH : 1];
+    __shared__ float s_g[MODE == kBlendGrad ? 3 * BATCH : 1];
+    __shared__ float s_loss[MODE == kBlendGrad ? kBlendThreads / 32 : 1];
 
     const int tile = (int)order[blockIdx.x];
     const int tx = tile % tiles_x, ty = tile / tiles_x;
@@ -79,6 +93,7 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
     const bool inside = px < width && py < height;
     const float fpx = (float)lx, fpy = (float)ly;
     const int mbit = 4 * warp + (grp & 1) + 2 * (grp >> 1);   // this lane's group bit
+    const size_t pix = (size_t)py * width + px;
 
     uint2 rg = ranges[tile];
     if (ctr && ctr->skip) rg = make_uint2(0u, 0u);  // pairs exceed the buffers: background only
@@ -88,19 +103,67 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
     bool done = !inside;
     uint32_t fetched = begin;
     const float a_min = 1.0f / 255.0f;
+    // median depth: the view depth of the Gaussian that takes T below tau
+    float dz = 0.f;
+    bool crossed = !(1.0f >= ex.tau);
+    // gradient: dL/dy of this pixel, sign(y - target) / N (Eq. 6, L1 term)
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f, l1 = 0.f;
+    if (MODE == kBlendGrad) {
+        if (inside) {
+            const float d0 = image[3 * pix + 0] - ex.target[3 * pix + 0];
+            const float d1 = image[3 * pix + 1] - ex.target[3 * pix + 1];
+            const float d2 = image[3 * pix + 2] - ex.target[3 * pix + 2];
+            g0 = d0 > 0.f ? ex.inv_n : d0 < 0.f ? -ex.inv_n : 0.f;
+            g1 = d1 > 0.f ? ex.inv_n : d1 < 0.f ? -ex.inv_n : 0.f;
+            g2 = d2 > 0.f ? ex.inv_n : d2 < 0.f ? -ex.inv_n : 0.f;
+            l1 = fabsf(d0) + fabsf(d1) + fabsf(d2);
+        }
+        for (int k = threadIdx.x; k < 3 * BATCH; k += kBlendThreads) s_g[k] = 0.f;
+    }
 
     // prefetch the first batch
     float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra;
+    uint32_t rid = 0;
     const bool gatherer = threadIdx.x < BATCH;
     if (gatherer && begin + threadIdx.x < end) {
-        const uint32_t id = __ldg(ids + begin + threadIdx.x);
-        ra = __ldg(rec + 3 * (size_t)id);
-        rb = __ldg(rec + 3 * (size_t)id + 1);
-        rc = __ldg(rec + 3 * (size_t)id + 2);
+        rid = __ldg(ids + begin + threadIdx.x);
+        ra = __ldg(rec + 3 * (size_t)rid);
+        rb = __ldg(rec + 3 * (size_t)rid + 1);
+        rc = __ldg(rec + 3 * (size_t)rid + 2);
     }
 
+    // gradient mode: add the previous batch's per-Gaussian sums to the global
+    // gradient (one atomic per Gaussian, tile and channel) and clear them
+    auto flush = [&](uint32_t prev_b) {
+        if (MODE != kBlendGrad) return;
+        const int k = threadIdx.x;
+        if (gatherer && prev_b + k < end) {
+            const uint32_t id = s_id[k];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float v = s_g[3 * k + c];
+                if (v != 0.f) atomicAdd(&ex.grad_rgb[3 * (size_t)id + c], v);
+                s_g[3 * k + c] = 0.f;
+            }
+        }
+    };
+
+    // sum of a value over the 8 lanes of this lane's group
+    auto group_sum = [&](float v) {
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        return v;
+    };
+
+    uint32_t prev_b = 0xffffffffu;
     for (uint32_t b = begin; b < end; b += BATCH) {
-        if (__syncthreads_count(done) == kBlendThreads) break;
+        const int n_done = __syncthreads_count(done);
+        if (prev_b != 0xffffffffu) flush(prev_b);
+        if (n_done == kBlendThreads) {
+            prev_b = 0xffffffffu;
+            break;
+        }
         if (gatherer && b + threadIdx.x < end) {
             // move the centre from its first tile's frame into this tile's frame
             const uint32_t o = __float_as_uint(rc.w);
@@ -110,16 +173,19 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
             s_b[threadIdx.x] = make_float4(rb.x, rb.y, rc.x, rc.y);
             s_c[threadIdx.x] = rc.z;
             s_m[threadIdx.x] = group_mask(u, v, rb.z, rb.w);
+            if (MODE == kBlendDepth) s_z[threadIdx.x] = __uint_as_float(__ldg(ex.zkey + rid));
+            if (MODE == kBlendGrad) s_id[threadIdx.x] = rid;
         }
         fetched = min(end, b + BATCH);
+        prev_b = b;
         __syncthreads();
         // prefetch the next batch while this one is blended
         const uint32_t jn = b + BATCH + threadIdx.x;
         if (gatherer && jn < end) {
-            const uint32_t id = __ldg(ids + jn);
-            ra = __ldg(rec + 3 * (size_t)id);
-            rb = __ldg(rec + 3 * (size_t)id + 1);
-            rc = __ldg(rec + 3 * (size_t)id + 2);
+            rid = __ldg(ids + jn);
+            ra = __ldg(rec + 3 * (size_t)rid);
+            rb = __ldg(rec + 3 * (size_t)rid + 1);
+            rc = __ldg(rec + 3 * (size_t)rid + 2);
         }
         const int cnt = (int)min((uint32_t)BATCH, end - b);
         if (__all_sync(0xffffffffu, done)) continue;
@@ -160,9 +226,23 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
                     const bool stop = take && nT < 1e-4f;
                     const bool add = take && !stop;
                     const float w = add ? al0 * T : 0.0f;
-                    cr = fmaf(b0.z, w, cr);
-                    cg = fmaf(b0.w, w, cg);
-                    cb = fmaf(s_c[s0], w, cb);
+                    if (MODE != kBlendGrad) {
+                        cr = fmaf(b0.z, w, cr);
+                        cg = fmaf(b0.w, w, cg);
+                        cb = fmaf(s_c[s0], w, cb);
+                    } else {
+                        const float v0 = group_sum(g0 * w), v1 = group_sum(g1 * w);
+                        const float v2 = group_sum(g2 * w);
+                        if ((lane & 7) == 0 && act0) {
+                            atomicAdd(&s_g[3 * s0 + 0], v0);
+                            atomicAdd(&s_g[3 * s0 + 1], v1);
+                            atomicAdd(&s_g[3 * s0 + 2], v2);
+                        }
+                    }
+                    if (MODE == kBlendDepth && add && !crossed && nT < ex.tau) {
+                        dz = s_z[s0];
+                        crossed = true;
+                    }
                     T = add ? nT : T;
                     done = done || stop;
                 }
@@ -172,9 +252,23 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
                     const bool stop = take && nT < 1e-4f;
                     const bool add = take && !stop;
                     const float w = add ? al1 * T : 0.0f;
-                    cr = fmaf(b1.z, w, cr);
-                    cg = fmaf(b1.w, w, cg);
-                    cb = fmaf(s_c[s1], w, cb);
+                    if (MODE != kBlendGrad) {
+                        cr = fmaf(b1.z, w, cr);
+                        cg = fmaf(b1.w, w, cg);
+                        cb = fmaf(s_c[s1], w, cb);
+                    } else {
+                        const float v0 = group_sum(g0 * w), v1 = group_sum(g1 * w);
+                        const float v2 = group_sum(g2 * w);
+                        if ((lane & 7) == 0 && act1) {
+                            atomicAdd(&s_g[3 * s1 + 0], v0);
+                            atomicAdd(&s_g[3 * s1 + 1], v1);
+                            atomicAdd(&s_g[3 * s1 + 2], v2);
+                        }
+                    }
+                    if (MODE == kBlendDepth && add && !crossed && nT < ex.tau) {
+                        dz = s_z[s1];
+                        crossed = true;
+                    }
                     T = add ? nT : T;
                     done = done || stop;
                 }
@@ -182,28 +276,62 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
             if (__all_sync(0xffffffffu, done)) break;
         }
     }
+    if (MODE == kBlendGrad) {
+        __syncthreads();
+        if (prev_b != 0xffffffffu) flush(prev_b);
+        // this tile's share of the L1 loss
+        float l = l1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+        if (lane == 0) s_loss[warp] = l;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+            for (int w = 0; w < kBlendThreads / 32; ++w) t += s_loss[w];
+            atomicAdd(ex.loss, (double)t);
+        }
+        return;
+    }
     if (inside) {
-        const size_t p = (size_t)py * width + px;
-        image[3 * p + 0] = cr + T * bg0;
-        image[3 * p + 1] = cg + T * bg1;
-        image[3 * p + 2] = cb + T * bg2;
-        if (final_T) final_T[p] = T;
+        image[3 * pix + 0] = cr + T * bg0;
+        image[3 * pix + 1] = cg + T * bg1;
+        image[3 * pix + 2] = cb + T * bg2;
+        if (final_T) final_T[pix] = T;
+        if (MODE == kBlendDepth) ex.depth[pix] = dz;
     }
     if (threadIdx.x == 0 && ctr) atomicAdd(&ctr->pairs_read, (unsigned long long)(fetched - begin));
 }
 
+template <int MODE>
+static void blend_launch(int batch, int tiles, const uint2* ranges, const uint32_t* order,
+                         const uint32_t* ids, const float4* rec, const DevCamera& cam,
+                         const float bg[3], float* image, float* final_T, DevCounters* counters,
+                         const BlendExtra& ex, cudaStream_t st) {
+    if (batch == 128)
+        blend_kernel<128, MODE><<<tiles, kBlendThreads, 0, st>>>(
+            ranges, order, ids, rec, cam.width, cam.height, cam.tiles_x, bg[0], bg[1], bg[2],
+            image, final_T, counters, ex);
+    else
+        blend_kernel<256, MODE><<<tiles, kBlendThreads, 0, st>>>(
+            ranges, order, ids, rec, cam.width, cam.height, cam.tiles_x, bg[0], bg[1], bg[2],
+            image, final_T, counters, ex);
+}
+
 int launch_blend(const uint2* ranges, const uint32_t* order, const uint32_t* ids, const float4* rec,
                  const DevCamera& cam, const float bg[3], float* image, float* final_T,
-                 DevCounters* counters, int batch, cudaStream_t st) {
+                 DevCounters* counters, int batch, const BlendExtra* extra, cudaStream_t st) {
     const int tiles = cam.tiles_x * cam.tiles_y;
-    if (batch == 128)
-        blend_kernel<128><<<tiles, kBlendThreads, 0, st>>>(ranges, order, ids, rec, cam.width,
-                                                           cam.height, cam.tiles_x, bg[0], bg[1],
-                                                           bg[2], image, final_T, counters);
+    BlendExtra ex;
+    if (extra) ex = *extra;
+    if (ex.grad_rgb)
+        blend_launch<kBlendGrad>(batch, tiles, ranges, order, ids, rec, cam, bg, image, final_T,
+                                 nullptr, ex, st);
+    else if (ex.depth)
+        blend_launch<kBlendDepth>(batch, tiles, ranges, order, ids, rec, cam, bg, image, final_T,
+                                  counters, ex, st);
     else
-        blend_kernel<256><<<tiles, kBlendThreads, 0, st>>>(ranges, order, ids, rec, cam.width,
-                                                           cam.height, cam.tiles_x, bg[0], bg[1],
-                                                           bg[2], image, final_T, counters);
+        blend_launch<kBlendColour>(batch, tiles, ranges, order, ids, rec, cam, bg, image, final_T,
+                                   counters, ex, st);
     return 1;
 }
 

@@ -289,7 +289,8 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
         ids = tb.vals[tcur];
     }
     NA_CK(cudaGetLastError());
-    launch_blend(ranges, U32(oOrder), ids, rec, dc, bgv, image_hwc_out, final_T_out, dctr, 256, st);
+    launch_blend(ranges, U32(oOrder), ids, rec, dc, bgv, image_hwc_out, final_T_out, dctr, 256, nullptr,
+                 st);
     NA_CK(cudaGetLastError());
 #undef NA_CK
     return RECOGS_OK;

@@ -226,9 +226,35 @@ int launch_scatter(const uint32_t* count, const uint2* rect, const uint32_t* zke
 int launch_tile_sort(const uint2* ranges, const uint32_t* order, const uint32_t* class_tiles,
                      bool exact, int tiles, const unsigned long long* keys, uint32_t* ids,
                      const DevCounters* counters, int radix_classes, cudaStream_t st);
+// Optional outputs of the blend. depth != NULL: the median depth of each
+// pixel (the view depth, from zkey, of the Gaussian whose blending takes T
+// below tau; 0 if none). grad_rgb != NULL: instead of the image, the colour
+// gradient dL/dc of L = mean |image - target| (image holds the forward
+// result), accumulated into grad_rgb [n][3] (zeroed by the caller), and
+// sum |image - target| added to *loss.
+struct BlendExtra {
+    const uint32_t* zkey = nullptr;
+    float tau = 0.5f;
+    float* depth = nullptr;
+    const float* target = nullptr;
+    float inv_n = 0.f;
+    float* grad_rgb = nullptr;
+    double* loss = nullptr;
+};
+
+// Adam parameters of the SH refit, with the bias corrections 1 / (1 - b^t).
+struct RefitAdam {
+    float lr, beta1, beta2, eps, inv_bc1, inv_bc2;
+};
+// SH gradient from the colour gradient and, with m and v, one Adam step of
+// the coefficients (refit.cu). grad_sh may be NULL; m == NULL: no step.
+int launch_sh_refit(int n, const float* xyz, const float cam_pos[3], const float4* rec,
+                    const uint32_t* count, const float* grad_rgb, float* sh, float* m, float* v,
+                    const RefitAdam& adam, float* grad_sh, cudaStream_t st);
+
 // batch: Gaussians staged in shared memory per blend step, 128 or 256
 int launch_blend(const uint2* ranges, const uint32_t* order, const uint32_t* ids, const float4* rec,
                  const DevCamera& cam, const float bg[3], float* image, float* final_T,
-                 DevCounters* counters, int batch, cudaStream_t st);
+                 DevCounters* counters, int batch, const BlendExtra* extra, cudaStream_t st);
 
 }  // namespace recogs
