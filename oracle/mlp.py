@@ -1,0 +1,256 @@
+"""FP64 oracle of the learned selection MLP (numpy).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/`` and never by the product
+package; it imports nothing from the product package.
+
+The paper names the leak of its selection as a limitation (Sec. 6: a
+Gaussian larger than the selection is recoloured as a whole or not at all).
+The learned variant predicts, per Gaussian, the plain selection bit (a
+logit) and the fraction of its projected 2D Gaussian inside the region (one
+coverage per RGB channel, the "tint residual"), from 59 features:
+
+  0, 1  the centre in the selection view, (u, v) - c, divided by the distance
+        rho from the polygon's vertex centroid c to the polygon boundary
+        along that direction (a star-shaped polygon maps onto the unit disc)
+  2     ln(t_z rho / f_x): log-scale minus this is the log of the projected
+        scale relative to rho
+  3-5   log-scales; 6-9 the normalised quaternion; 10 the opacity logit
+  11-58 the 48 SH coefficients ([16][3] order)
+  59-63 zero padding (K = 64)
+
+Coverage label: the 2D Gaussian N((u, v), Sigma') of the splat in the
+selection view (Sigma' with the 0.3 px^2 dilation) integrated against the
+region's indicator by the 5 x 5 Gauss-Hermite product rule (nodes and
+weights of numpy's hermgauss, rescaled to the standard normal), the
+indicator being the plain even-odd test. Splats with t_z <= z_near are
+outside the learned domain (the plain test decides them).
+
+Network (BF16 weights, FP32 accumulation): z1 = x W1 + b1, h1 = GELU(z1),
+z2 = h1 W2 + b2, h2 = GELU(z2), o = h2 W3 + b3 (o0 = selection logit,
+o1..o3 = coverage logits), GELU(z) = z Phi(z) with the exact normal CDF.
+The inputs of every product (features, weights, h1, h2 and the backward's
+dz3, dz2, dz1) are rounded to bfloat16 (round to nearest even) and products
+are summed in wide precision; with rnd=False the same network runs in FP64
+throughout (used by the finite-difference pins).
+
+Loss per sample: BCE(o0, sel) + sum_c (sigmoid(o_c) - coverage)^2, mean
+over the batch.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.special as sps
+
+import oracle as _o
+
+N_IN = 59
+K = 64
+H = 64
+N_OUT = 4
+# parameter vector: W1 [64][64] (input-major), b1 [64], W2 [64][64], b2 [64],
+# W3 [64][4], b3 [4]
+SHAPES = (("W1", (K, H)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (H, N_OUT)),
+          ("b3", (N_OUT,)))
+N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
+
+
+def unpack(theta):
+    theta = np.asarray(theta, np.float64)
+    out, o = {}, 0
+    for name, shape in SHAPES:
+        size = int(np.prod(shape))
+        out[name] = theta[o:o + size].reshape(shape)
+        o += size
+    return out
+
+
+def pack(d):
+    return np.concatenate([np.asarray(d[name], np.float64).reshape(-1) for name, _ in SHAPES])
+
+
+def bf16(x):
+    """Round to the nearest bfloat16 (ties to even), as float64 values."""
+    a = np.ascontiguousarray(np.asarray(x, np.float64).astype(np.float32))
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64).reshape(np.shape(x))
+
+
+def gelu(z):
+    return z * 0.5 * (1.0 + sps.erf(z / math.sqrt(2.0)))
+
+
+def gelu_grad(z):
+    return 0.5 * (1.0 + sps.erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2 * math.pi)
+
+
+def sigmoid(x):
+    return 0.5 * (1.0 + np.tanh(0.5 * x))
+
+
+# ---------------------------------------------------------------------------
+# features and labels
+
+def point_in_polygon(u, v, xy):
+    """Even-odd rule, vectorised over points (same convention as the plain
+    selection: an edge counts when exactly one end is strictly above v)."""
+    xy = np.asarray(xy, np.float64).reshape(-1, 2)
+    inside = np.zeros(np.shape(u), bool)
+    n = len(xy)
+    for i in range(n):
+        xi, yi = xy[i]
+        xj, yj = xy[i - 1]
+        cond = (yi > v) != (yj > v)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            xc = xi + (v - yi) * (xj - xi) / (yj - yi)
+        inside ^= cond & (u < xc)
+    return inside
+
+
+def radial_frame(u, v, xy):
+    """(q / rho, rho): q = (u, v) - centroid, rho = distance from the vertex
+    centroid to the boundary along q (the nearest edge crossing of the ray)."""
+    xy = np.asarray(xy, np.float64).reshape(-1, 2)
+    c = xy.mean(0)
+    mean_r = np.sqrt(((xy - c) ** 2).sum(1)).mean()
+    qx, qy = u - c[0], v - c[1]
+    lam = np.full(np.shape(u), np.inf)
+    n = len(xy)
+    for i in range(n):
+        ax, ay = xy[i - 1] - c
+        ex, ey = xy[i] - xy[i - 1]
+        den = qx * ey - qy * ex
+        with np.errstate(divide="ignore", invalid="ignore"):
+            l = (ax * ey - ay * ex) / den
+            s = (ax * qy - ay * qx) / den
+        ok = (den != 0) & (l > 0) & (s >= 0) & (s <= 1)
+        lam = np.where(ok & (l < lam), l, lam)
+    qn = np.sqrt(qx * qx + qy * qy)
+    with np.errstate(invalid="ignore"):
+        rho = np.where(np.isfinite(lam) & (qn > 0), lam * qn, mean_r)
+    return qx / rho, qy / rho, rho
+
+
+def hermite_rule(m=5):
+    x, w = np.polynomial.hermite.hermgauss(m)
+    return x * math.sqrt(2.0), w / math.sqrt(math.pi)
+
+
+def quadrature_points(u, v, a, b, c):
+    """Points and weights of the 5 x 5 product rule for N((u, v), [[a, b],
+    [b, c]]): (u, v) + L (x_i, x_j) with L the lower Cholesky factor.
+    Returns (pu, pv, w), each [25, ...]."""
+    l00 = np.sqrt(a)
+    l10 = b / l00
+    l11 = np.sqrt(np.maximum(c - l10 * l10, 0.0))
+    xs, ws = hermite_rule()
+    pu, pv, w = [], [], []
+    for i, xi in enumerate(xs):
+        for j, xj in enumerate(xs):
+            pu.append(u + l00 * xi)
+            pv.append(v + l10 * xi + l11 * xj)
+            w.append(ws[i] * ws[j])
+    return np.array(pu), np.array(pv), np.array(w)
+
+
+def features_and_labels(scene, cam, region_xy):
+    """Returns (F [n, 64], valid [n] bool, sel [n] uint8, coverage [n])."""
+    n = scene.xyz.shape[1]
+    xyz = np.asarray(scene.xyz, np.float32).astype(np.float64)
+    V = np.asarray(cam.world_to_view, np.float32).astype(np.float64).reshape(3, 4)
+    t = V[:, :3] @ xyz + V[:, 3:4]
+    tz = t[2]
+    valid = tz > float(np.float32(cam.z_near))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        u = float(np.float32(cam.fx)) * t[0] / tz + float(np.float32(cam.cx))
+        v = float(np.float32(cam.fy)) * t[1] / tz + float(np.float32(cam.cy))
+    un, vn, rho = radial_frame(np.where(valid, u, 0.0), np.where(valid, v, 0.0), region_xy)
+    F = np.zeros((n, K))
+    F[:, 0] = np.where(valid, un, 0.0)
+    F[:, 1] = np.where(valid, vn, 0.0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        F[:, 2] = np.where(valid, np.log(np.where(valid, tz, 1.0) * rho / float(np.float32(cam.fx))), 0.0)
+    F[:, 3:6] = np.asarray(scene.log_scale, np.float32).T
+    q = np.asarray(scene.quat, np.float32).astype(np.float64)
+    F[:, 6:10] = (q / np.sqrt((q * q).sum(0))).T
+    F[:, 10] = np.asarray(scene.opacity_logit, np.float32)
+    F[:, 11:59] = np.asarray(scene.sh, np.float32).reshape(48, n).T
+    # labels: the plain selection bit and the Gauss-Hermite coverage
+    edit = type("E", (), {})()
+    edit.region = type("R", (), {})()
+    edit.region.kind = "polygon"
+    edit.region.xy = np.asarray(region_xy, np.float64).reshape(-1, 2)
+    edit.color_matrix = np.eye(3)
+    edit.select_camera = cam
+    sel, _ = _o.select(scene, edit, cam)
+    sp = _o.preprocess(scene, cam)
+    a, b, c = sp["cov2d"][0::3], sp["cov2d"][1::3], sp["cov2d"][2::3]
+    pu, pv, w = quadrature_points(np.where(valid, u, 0.0), np.where(valid, v, 0.0),
+                                  np.where(valid, a, 1.0), np.where(valid, b, 0.0),
+                                  np.where(valid, c, 1.0))
+    cov = np.zeros(n)
+    for k in range(len(w)):
+        cov += w[k] * point_in_polygon(pu[k], pv[k], region_xy)
+    cov = np.where(valid, cov, 0.0)
+    return F, valid, sel.astype(np.uint8), cov
+
+
+# ---------------------------------------------------------------------------
+# network
+
+def forward(theta, X, rnd=True):
+    r = bf16 if rnd else (lambda a: np.asarray(a, np.float64))
+    P = unpack(theta)
+    x = r(X)
+    z1 = x @ r(P["W1"]) + P["b1"]
+    h1 = r(gelu(z1))
+    z2 = h1 @ r(P["W2"]) + P["b2"]
+    h2 = r(gelu(z2))
+    o = h2 @ r(P["W3"]) + P["b3"]
+    return dict(x=x, z1=z1, h1=h1, z2=z2, h2=h2, o=o)
+
+
+def loss_grad(theta, X, sel, cov, rnd=True):
+    """Mean loss over the batch and its gradient (parameter-vector layout)."""
+    r = bf16 if rnd else (lambda a: np.asarray(a, np.float64))
+    P = unpack(theta)
+    f = forward(theta, X, rnd)
+    o = f["o"]
+    B = len(X)
+    y = np.asarray(sel, np.float64)
+    cv = np.asarray(cov, np.float64)
+    p0 = sigmoid(o[:, 0])
+    pc = sigmoid(o[:, 1:4])
+    bce = np.maximum(o[:, 0], 0) - y * o[:, 0] + np.log1p(np.exp(-np.abs(o[:, 0])))
+    loss = float((bce + ((pc - cv[:, None]) ** 2).sum(1)).mean())
+    dz3 = np.zeros((B, N_OUT))
+    dz3[:, 0] = (p0 - y) / B
+    dz3[:, 1:] = 2.0 * (pc - cv[:, None]) * pc * (1 - pc) / B
+    g = {}
+    dz3r = r(dz3)
+    g["W3"] = f["h2"].T @ dz3r
+    g["b3"] = dz3.sum(0)
+    dz2 = (dz3r @ r(P["W3"]).T) * gelu_grad(f["z2"])
+    dz2r = r(dz2)
+    g["W2"] = f["h1"].T @ dz2r
+    g["b2"] = dz2.sum(0)
+    dz1 = (dz2r @ r(P["W2"]).T) * gelu_grad(f["z1"])
+    dz1r = r(dz1)
+    g["W1"] = f["x"].T @ dz1r
+    g["b1"] = dz1.sum(0)
+    return loss, pack(g)
+
+
+def decisions(o, plain_sel, exact_cov, valid, delta):
+    """Selection and per-channel tint weights of the learned path with the
+    plain fallback: |sigmoid(o0) - 1/2| < delta -> the plain bit and the
+    exact coverage; splats outside the learned domain take the plain bit as
+    a binary weight. Returns (sel, weights [n, 3], fallback mask)."""
+    p = sigmoid(o[:, 0])
+    fb = valid & (np.abs(p - 0.5) < delta)
+    sel = np.where(valid, np.where(fb, plain_sel, p > 0.5), plain_sel).astype(np.uint8)
+    w = np.where(fb[:, None], exact_cov[:, None], sigmoid(o[:, 1:4]))
+    w = np.where(valid[:, None], w, plain_sel[:, None].astype(np.float64))
+    return sel, w, fb

@@ -328,6 +328,42 @@ def batched_workload(sizes=(500_000, 1_000_000, 2_000_000, 4_000_000), views_per
     return BatchWorkload(f"batch_{len(sizes)}x{views_per_scene}", scenes, views)
 
 
+def random_polygons(count, width, height, seed, n_vertices=12, area=(0.05, 0.25)):
+    """`count` star-shaped polygons (as polygon_region) with area fractions
+    drawn from U(area) and centres drawn uniformly from the middle 60% of the
+    image."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        reg = polygon_region(width, height, n_vertices, float(rng.uniform(*area)),
+                             int(rng.integers(1 << 31)))
+        shift = np.array([rng.uniform(-0.3, 0.3) * width, rng.uniform(-0.3, 0.3) * height])
+        out.append(Region("polygon", (reg.xy + shift).astype(np.float32)))
+    return out
+
+
+# parameter vector of the selection MLP 59 -> 64 -> 64 -> 4: W1 [64][64]
+# (input-major, rows 59..63 zero: padding inputs), b1 [64], W2 [64][64],
+# b2 [64], W3 [64][4], b3 [4]
+MLP_SHAPES = ((64, 64), (64,), (64, 64), (64,), (64, 4), (4,))
+MLP_FAN_IN = (59, 59, 64, 64, 64, 64)
+MLP_PARAMS = 8580
+
+
+def mlp_init(seed) -> np.ndarray:
+    """Initial MLP parameters: every weight and bias U(-1/sqrt(fan_in),
+    1/sqrt(fan_in)) of its layer (the common default for linear layers)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for shape, fan in zip(MLP_SHAPES, MLP_FAN_IN):
+        b = 1.0 / math.sqrt(fan)
+        parts.append(rng.uniform(-b, b, size=shape).astype(np.float32).reshape(-1))
+    theta = np.concatenate(parts)
+    theta[59 * 64:64 * 64] = 0.0   # W1 rows of the padding inputs
+    assert theta.size == MLP_PARAMS
+    return theta
+
+
 def to_half(sh: np.ndarray, kind: str) -> np.ndarray:
     """Round float32 SH to float16 ('f16') or bfloat16 ('bf16', round to
     nearest even); returns the 16-bit payload as uint16 for bf16 and float16
