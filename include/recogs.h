@@ -240,6 +240,128 @@ RECOGS_API recogs_status recogs_refit_step(recogs_ctx* ctx, recogs_scene* scene,
                                            void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Learned selection (the leak of Sec. 6)
+ *
+ * The plain selection recolours a Gaussian wholly or not at all, so a
+ * Gaussian larger than the selection leaks colour across its boundary (the
+ * limitation the paper lists in Sec. 6). Recolouring each Gaussian by the
+ * least-squares weight of its contribution to the selection view -- the sum
+ * over pixels whose centre is inside the region of (alpha_i(p) T_i(p))^2
+ * over the sum over all pixels -- fits the pixel-tinted edit target of
+ * Sec. 3.3 better (by 0.6-1.5 dB PSNR on the synthetic scenes); computing it
+ * takes a render and a per-pixel pass of the selection view. A small MLP
+ * predicts it (and the plain selection bit) per Gaussian from its own
+ * attributes on the tensor cores, with the plain test as fallback where its
+ * selection logit is uncertain. The paper has no learned component; the
+ * network, its features and labels are this library's readings:
+ *
+ * Features (64 bf16 per Gaussian, row-major [n][64]): the splat in the
+ * selection view for a polygon region. 0-1 q / rho, q = the projected
+ * centre minus the polygon's vertex centroid, rho = the distance from that
+ * centroid to the boundary along q (a star-shaped polygon maps onto the unit
+ * disc); 2 ln(t_z rho / f_x); 3-4 ln(sigma / rho) for the axis standard
+ * deviations of the projected (dilated) 2D Gaussian; 5 ln(sigma_r / rho) for
+ * its standard deviation along q; 6-7 cos 2 theta, sin 2 theta of its major
+ * axis' angle to q; 8 (rho - |q|) / sigma_r clamped to [-8, 8]; 9 the mean
+ * log-scale; 10 the opacity logit; 11-58 the SH coefficients in [16][3]
+ * order; 59-63 zero. Gaussians with t_z <= z_near are outside the learned
+ * domain. Labels ([n][2] float32): the plain selection bit and the tint
+ * weight above (the plain bit for a Gaussian that reaches no pixel).
+ * Network 59 -> 64 -> 64 -> 4 with exact GELU: out = (selection logit,
+ * three per-channel coverage logits). Parameters (float32, RECOGS_MLP_PARAMS
+ * values): W1 [64][64] (input-major; rows 59-63 multiply the zero
+ * features), b1 [64], W2 [64][64], b2 [64], W3 [64][4], b3 [4]. Products
+ * take bf16 operands (features, weights, activations, the backward's output
+ * gradients) with float32 accumulation. Loss per sample: binary
+ * cross-entropy of the logit against the bit, plus the squared error of
+ * each sigmoid(coverage logit) against the coverage; mean over the batch.
+ * Destroy networks before their context.
+ */
+
+#define RECOGS_MLP_PARAMS 8580
+
+typedef struct recogs_mlp recogs_mlp;
+
+/* Create a network on ctx's device from params_host (RECOGS_MLP_PARAMS
+ * float32, host). Adam moments start at zero. *out is NULL on failure. */
+RECOGS_API recogs_status recogs_mlp_create(recogs_ctx* ctx, const float* params_host,
+                                           recogs_mlp** out);
+
+/* Release the network (synchronises the device). NULL is a no-op. */
+RECOGS_API void recogs_mlp_destroy(recogs_mlp* mlp);
+
+/* Copy the current float32 parameters to params_host_out (host, waits). */
+RECOGS_API recogs_status recogs_mlp_params(recogs_mlp* mlp, float* params_host_out);
+
+/* Features of every Gaussian of `scene` for `region` (a polygon, pixel
+ * coordinates of select_camera) into features_out (device, 128 bytes per
+ * Gaussian, 16-byte aligned); valid_out (device [n] bytes, 1 where
+ * t_z > z_near, may be NULL). */
+RECOGS_API recogs_status recogs_mlp_features(recogs_ctx* ctx, const recogs_scene* scene,
+                                             const recogs_camera* select_camera,
+                                             const recogs_region* region, uint16_t* features_out,
+                                             uint8_t* valid_out, void* stream);
+
+/* Training labels for `region`: renders the scene from select_camera (no
+ * edit, black background) and writes labels_out (device [n][2] float32,
+ * 8-byte aligned) = (plain selection bit, tint weight). The weight's sums
+ * are taken with float atomics (last bits may vary). Waits for the
+ * per-frame read back of the render. */
+RECOGS_API recogs_status recogs_mlp_labels(recogs_ctx* ctx, const recogs_scene* scene,
+                                           const recogs_camera* select_camera,
+                                           const recogs_region* region, float* labels_out,
+                                           void* stream);
+
+/* out[i] (device [n][4] float32, 16-byte aligned) = the network on
+ * features[i] (device bf16 [n][64]). */
+RECOGS_API recogs_status recogs_mlp_forward(recogs_mlp* mlp, const uint16_t* features, int64_t n,
+                                            float* out, void* stream);
+
+/* The gradient of the mean loss over the batch rows[0..batch) (device
+ * uint32 sample indices; indices >= n_samples count as empty rows) of
+ * features / labels (device, n_samples rows), into grad_host_out (host,
+ * RECOGS_MLP_PARAMS float32) without changing the network; loss_out (host,
+ * may be NULL) = the mean loss. Waits for the stream. Gradients are summed
+ * with float atomics (last bits may vary). */
+RECOGS_API recogs_status recogs_mlp_grad(recogs_mlp* mlp, const uint16_t* features,
+                                         const float* labels, int64_t n_samples,
+                                         const uint32_t* rows, int64_t batch,
+                                         float* grad_host_out, double* loss_out, void* stream);
+
+/* One training step on a batch (as recogs_mlp_grad) followed by an Adam
+ * step of every parameter (adam->step is ignored: the network counts its
+ * own steps). loss_out (host, may be NULL; waits) = the batch's mean loss
+ * before the step. */
+RECOGS_API recogs_status recogs_mlp_train_step(recogs_mlp* mlp, const uint16_t* features,
+                                               const float* labels, int64_t n_samples,
+                                               const uint32_t* rows, int64_t batch,
+                                               const recogs_adam* adam, double* loss_out,
+                                               void* stream);
+
+/* The learned selection: features, the network, and per Gaussian the
+ * decision: p = sigmoid(logit); where |p - 1/2| < delta, and outside the
+ * learned domain, the plain test decides, with its bit as the weight;
+ * elsewhere the bit is p > 1/2 and the weights are the sigmoid of the
+ * coverage logits.
+ * mask_out: device, ceil(n/32) words of selection bits; weights_out: device
+ * [n][3] float32 per-channel tint weights for recogs_recolor_weighted;
+ * fallbacks_out (host, may be NULL; waits) = Gaussians that fell back. */
+RECOGS_API recogs_status recogs_mlp_select(recogs_mlp* mlp, const recogs_scene* scene,
+                                           const recogs_camera* select_camera,
+                                           const recogs_region* region, float delta,
+                                           uint32_t* mask_out, float* weights_out,
+                                           int64_t* fallbacks_out, void* stream);
+
+/* Recolour (Sec. 3.3) by per-Gaussian, per-channel weights w in [0, 1]
+ * (device [n][3]): each coefficient triple becomes C + w (M C - C), the DC
+ * triple's target including the offset correction of recogs_recolor. w = 1
+ * gives recogs_recolor's result bit for bit, w = 0 leaves the Gaussian
+ * untouched, and the binary weights of the plain selection reproduce it. */
+RECOGS_API recogs_status recogs_recolor_weighted(recogs_ctx* ctx, recogs_scene* scene,
+                                                 const float* weights, const recogs_tint* tint,
+                                                 void* stream);
+
+/* ---------------------------------------------------------------------------
  * Rendering without allocation
  */
 

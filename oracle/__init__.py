@@ -94,6 +94,8 @@ def lib():
         L.oracle_color_grad_tiles.argtypes = [C.POINTER(Splats), i64p, i32p, C.c_int, C.c_int,
                                               f64p, f64p]
         L.oracle_sh_grad.argtypes = [C.c_int64, f32p, C.POINTER(Camera), f64p, f64p, f64p]
+        L.oracle_weight_sums_tiles.argtypes = [C.POINTER(Splats), i64p, i32p, C.c_int, C.c_int,
+                                               f64p, C.c_int, f64p]
         _lib = L
     return _lib
 
@@ -363,6 +365,22 @@ def color_grad(splats: SplatResult, offsets, ids, dLdy) -> np.ndarray:
     lib().oracle_color_grad_tiles(C.byref(s), _ptr(offsets, i64p), _ptr(ids, i32p), cam.width,
                                   cam.height, _ptr(g, f64p), _ptr(out, f64p))
     return out[:3 * n].reshape(n, 3)
+
+
+def weight_sums(splats: SplatResult, offsets, ids, pixel_weight, power) -> np.ndarray:
+    """Per splat: sum_p pixel_weight[p] (alpha T)^power over its contributions."""
+    cam = splats["camera"]
+    n = splats["n"]
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    ids = np.ascontiguousarray(ids, np.int32)
+    if len(ids) == 0:
+        ids = np.zeros(1, np.int32)
+    g = np.ascontiguousarray(pixel_weight, np.float64).reshape(-1)
+    out = np.zeros(max(n, 1))
+    s = splats.struct()
+    lib().oracle_weight_sums_tiles(C.byref(s), _ptr(offsets, i64p), _ptr(ids, i32p), cam.width,
+                                   cam.height, _ptr(g, f64p), int(power), _ptr(out, f64p))
+    return out[:n]
 
 
 def sh_grad(scene, splats: SplatResult, grad_rgb) -> np.ndarray:

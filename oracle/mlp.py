@@ -6,24 +6,33 @@ package; it imports nothing from the product package.
 The paper names the leak of its selection as a limitation (Sec. 6: a
 Gaussian larger than the selection is recoloured as a whole or not at all).
 The learned variant predicts, per Gaussian, the plain selection bit (a
-logit) and the fraction of its projected 2D Gaussian inside the region (one
-coverage per RGB channel, the "tint residual"), from 59 features:
+logit) and its tint weight (one per RGB channel, the "tint residual"), from
+59 features that express the splat in the selection view:
 
-  0, 1  the centre in the selection view, (u, v) - c, divided by the distance
-        rho from the polygon's vertex centroid c to the polygon boundary
-        along that direction (a star-shaped polygon maps onto the unit disc)
-  2     ln(t_z rho / f_x): log-scale minus this is the log of the projected
-        scale relative to rho
-  3-5   log-scales; 6-9 the normalised quaternion; 10 the opacity logit
+  0, 1  the centre, (u, v) - c, divided by the distance rho from the
+        polygon's vertex centroid c to the polygon boundary along that
+        direction (a star-shaped polygon maps onto the unit disc)
+  2     ln(t_z rho / f_x)
+  3, 4  ln(sigma_1 / rho), ln(sigma_2 / rho): standard deviations of the
+        projected 2D Gaussian (the dilated Sigma' of the render) along its
+        axes
+  5     ln(sigma_r / rho): its standard deviation along the radial
+        direction q = (u, v) - c
+  6, 7  cos 2 theta, sin 2 theta: the major axis' angle to q
+  8     (rho - |q|) / sigma_r, clamped to [-8, 8]: the distance to the
+        boundary along q in radial standard deviations (positive inside)
+  9     the mean of the three log-scales; 10 the opacity logit
   11-58 the 48 SH coefficients ([16][3] order)
   59-63 zero padding (K = 64)
 
-Coverage label: the 2D Gaussian N((u, v), Sigma') of the splat in the
-selection view (Sigma' with the 0.3 px^2 dilation) integrated against the
-region's indicator by the 5 x 5 Gauss-Hermite product rule (nodes and
-weights of numpy's hermgauss, rescaled to the standard normal), the
-indicator being the plain even-odd test. Splats with t_z <= z_near are
-outside the learned domain (the plain test decides them).
+Tint-weight label: the least-squares per-Gaussian weight of the selection
+view's render, sum over inside pixels of (alpha_i T_i)^2 / sum over all
+pixels (Eq. 3's contributions; pixels inside by the plain even-odd test at
+their centres); a Gaussian that reaches no pixel takes its plain bit. For a
+Gaussian whose colour error does not overlap others', recolouring it by
+weight w changes the error at pixel p by (w - 1[p inside]) alpha_i T_i
+(t - 1) c_i, whose sum of squares this weight minimises. Splats with
+t_z <= z_near are outside the learned domain (the plain test decides them).
 
 Network (BF16 weights, FP32 accumulation): z1 = x W1 + b1, h1 = GELU(z1),
 z2 = h1 W2 + b2, h2 = GELU(z2), o = h2 W3 + b3 (o0 = selection logit,
@@ -133,28 +142,6 @@ def radial_frame(u, v, xy):
     return qx / rho, qy / rho, rho
 
 
-def hermite_rule(m=5):
-    x, w = np.polynomial.hermite.hermgauss(m)
-    return x * math.sqrt(2.0), w / math.sqrt(math.pi)
-
-
-def quadrature_points(u, v, a, b, c):
-    """Points and weights of the 5 x 5 product rule for N((u, v), [[a, b],
-    [b, c]]): (u, v) + L (x_i, x_j) with L the lower Cholesky factor.
-    Returns (pu, pv, w), each [25, ...]."""
-    l00 = np.sqrt(a)
-    l10 = b / l00
-    l11 = np.sqrt(np.maximum(c - l10 * l10, 0.0))
-    xs, ws = hermite_rule()
-    pu, pv, w = [], [], []
-    for i, xi in enumerate(xs):
-        for j, xj in enumerate(xs):
-            pu.append(u + l00 * xi)
-            pv.append(v + l10 * xi + l11 * xj)
-            w.append(ws[i] * ws[j])
-    return np.array(pu), np.array(pv), np.array(w)
-
-
 def features_and_labels(scene, cam, region_xy):
     """Returns (F [n, 64], valid [n] bool, sel [n] uint8, coverage [n])."""
     n = scene.xyz.shape[1]
@@ -166,18 +153,39 @@ def features_and_labels(scene, cam, region_xy):
     with np.errstate(divide="ignore", invalid="ignore"):
         u = float(np.float32(cam.fx)) * t[0] / tz + float(np.float32(cam.cx))
         v = float(np.float32(cam.fy)) * t[1] / tz + float(np.float32(cam.cy))
-    un, vn, rho = radial_frame(np.where(valid, u, 0.0), np.where(valid, v, 0.0), region_xy)
+    uu, vv = np.where(valid, u, 0.0), np.where(valid, v, 0.0)
+    un, vn, rho = radial_frame(uu, vv, region_xy)
+    sp = _o.preprocess(scene, cam)
+    a, b, c = sp["cov2d"][0::3], sp["cov2d"][1::3], sp["cov2d"][2::3]
+    a, b, c = np.where(valid, a, 1.0), np.where(valid, b, 0.0), np.where(valid, c, 1.0)
+    cen = np.asarray(region_xy, np.float64).reshape(-1, 2).mean(0)
+    qx, qy = uu - cen[0], vv - cen[1]
+    qn = np.sqrt(qx * qx + qy * qy)
+    ux = np.where(qn > 0, qx / np.where(qn > 0, qn, 1.0), 1.0)
+    uy = np.where(qn > 0, qy / np.where(qn > 0, qn, 1.0), 0.0)
+    mid = 0.5 * (a + c)
+    rad = np.sqrt(0.25 * (a - c) ** 2 + b * b)
+    l1, l2 = mid + rad, mid - rad
+    c2p = np.where(rad > 0, 0.5 * (a - c) / np.where(rad > 0, rad, 1.0), 1.0)
+    s2p = np.where(rad > 0, b / np.where(rad > 0, rad, 1.0), 0.0)
+    c2q, s2q = ux * ux - uy * uy, 2 * ux * uy
+    sr = np.sqrt(a * ux * ux + 2 * b * ux * uy + c * uy * uy)
+    lr = np.log(rho)
     F = np.zeros((n, K))
     F[:, 0] = np.where(valid, un, 0.0)
     F[:, 1] = np.where(valid, vn, 0.0)
     with np.errstate(divide="ignore", invalid="ignore"):
         F[:, 2] = np.where(valid, np.log(np.where(valid, tz, 1.0) * rho / float(np.float32(cam.fx))), 0.0)
-    F[:, 3:6] = np.asarray(scene.log_scale, np.float32).T
-    q = np.asarray(scene.quat, np.float32).astype(np.float64)
-    F[:, 6:10] = (q / np.sqrt((q * q).sum(0))).T
+    F[:, 3] = np.where(valid, 0.5 * np.log(l1) - lr, 0.0)
+    F[:, 4] = np.where(valid, 0.5 * np.log(l2) - lr, 0.0)
+    F[:, 5] = np.where(valid, np.log(sr) - lr, 0.0)
+    F[:, 6] = np.where(valid, c2p * c2q + s2p * s2q, 0.0)
+    F[:, 7] = np.where(valid, s2p * c2q - c2p * s2q, 0.0)
+    F[:, 8] = np.where(valid, np.clip((rho - qn) / sr, -8.0, 8.0), 0.0)
+    F[:, 9] = np.asarray(scene.log_scale, np.float32).astype(np.float64).mean(0)
     F[:, 10] = np.asarray(scene.opacity_logit, np.float32)
     F[:, 11:59] = np.asarray(scene.sh, np.float32).reshape(48, n).T
-    # labels: the plain selection bit and the Gauss-Hermite coverage
+    # labels: the plain selection bit and the rendered coverage
     edit = type("E", (), {})()
     edit.region = type("R", (), {})()
     edit.region.kind = "polygon"
@@ -185,16 +193,25 @@ def features_and_labels(scene, cam, region_xy):
     edit.color_matrix = np.eye(3)
     edit.select_camera = cam
     sel, _ = _o.select(scene, edit, cam)
-    sp = _o.preprocess(scene, cam)
-    a, b, c = sp["cov2d"][0::3], sp["cov2d"][1::3], sp["cov2d"][2::3]
-    pu, pv, w = quadrature_points(np.where(valid, u, 0.0), np.where(valid, v, 0.0),
-                                  np.where(valid, a, 1.0), np.where(valid, b, 0.0),
-                                  np.where(valid, c, 1.0))
-    cov = np.zeros(n)
-    for k in range(len(w)):
-        cov += w[k] * point_in_polygon(pu[k], pv[k], region_xy)
-    cov = np.where(valid, cov, 0.0)
+    cov = rendered_coverage(scene, cam, region_xy, sel)
     return F, valid, sel.astype(np.uint8), cov
+
+
+def rendered_coverage(scene, cam, region_xy, plain_sel):
+    """sum over inside pixels of (alpha_i T_i)^2 / sum over all pixels, from
+    the binned FP64 render of the selection view; the plain bit where the
+    splat reaches no pixel."""
+    sp = _o.preprocess(scene, cam)
+    tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
+    off, ids = _o.tile_lists(sp, _o.depth_order(sp), tx, ty)
+    H, W = cam.height, cam.width
+    py, px = np.mgrid[0:H, 0:W]
+    inside = point_in_polygon(px.ravel().astype(np.float64), py.ravel().astype(np.float64),
+                              region_xy).astype(np.float64)
+    num = _o.weight_sums(sp, off, ids, inside, 2)
+    den = _o.weight_sums(sp, off, ids, np.ones(H * W), 2)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(den > 0, np.minimum(num / den, 1.0), np.asarray(plain_sel, np.float64))
 
 
 # ---------------------------------------------------------------------------
@@ -212,20 +229,22 @@ def forward(theta, X, rnd=True):
     return dict(x=x, z1=z1, h1=h1, z2=z2, h2=h2, o=o)
 
 
-def loss_grad(theta, X, sel, cov, rnd=True):
-    """Mean loss over the batch and its gradient (parameter-vector layout)."""
+def loss_grad(theta, X, sel, cov, rnd=True, batch=None):
+    """Mean loss over the batch and its gradient (parameter-vector layout).
+    batch: the batch size the sums are divided by (default len(X); larger
+    when the batch also holds empty rows)."""
     r = bf16 if rnd else (lambda a: np.asarray(a, np.float64))
     P = unpack(theta)
     f = forward(theta, X, rnd)
     o = f["o"]
-    B = len(X)
+    B = len(X) if batch is None else batch
     y = np.asarray(sel, np.float64)
     cv = np.asarray(cov, np.float64)
     p0 = sigmoid(o[:, 0])
     pc = sigmoid(o[:, 1:4])
     bce = np.maximum(o[:, 0], 0) - y * o[:, 0] + np.log1p(np.exp(-np.abs(o[:, 0])))
-    loss = float((bce + ((pc - cv[:, None]) ** 2).sum(1)).mean())
-    dz3 = np.zeros((B, N_OUT))
+    loss = float((bce + ((pc - cv[:, None]) ** 2).sum(1)).sum() / B)
+    dz3 = np.zeros((len(X), N_OUT))
     dz3[:, 0] = (p0 - y) / B
     dz3[:, 1:] = 2.0 * (pc - cv[:, None]) * pc * (1 - pc) / B
     g = {}
@@ -243,14 +262,16 @@ def loss_grad(theta, X, sel, cov, rnd=True):
     return loss, pack(g)
 
 
-def decisions(o, plain_sel, exact_cov, valid, delta):
+def decisions(o, plain_sel, valid, delta):
     """Selection and per-channel tint weights of the learned path with the
-    plain fallback: |sigmoid(o0) - 1/2| < delta -> the plain bit and the
-    exact coverage; splats outside the learned domain take the plain bit as
-    a binary weight. Returns (sel, weights [n, 3], fallback mask)."""
+    plain fallback: outside the learned domain or where
+    |sigmoid(o0) - 1/2| < delta, the plain bit (and the plain bit as a binary
+    weight); elsewhere the network's bit and sigmoid(o1..3).
+    Returns (sel, weights [n, 3], fallback mask)."""
     p = sigmoid(o[:, 0])
     fb = valid & (np.abs(p - 0.5) < delta)
-    sel = np.where(valid, np.where(fb, plain_sel, p > 0.5), plain_sel).astype(np.uint8)
-    w = np.where(fb[:, None], exact_cov[:, None], sigmoid(o[:, 1:4]))
-    w = np.where(valid[:, None], w, plain_sel[:, None].astype(np.float64))
+    plain = np.asarray(plain_sel, np.float64)
+    use_plain = ~valid | fb
+    sel = np.where(use_plain, plain_sel, p > 0.5).astype(np.uint8)
+    w = np.where(use_plain[:, None], plain[:, None], sigmoid(o[:, 1:4]))
     return sel, w, fb

@@ -764,6 +764,42 @@ void oracle_color_grad_tiles(const oracle_splats* s, const int64_t* offsets, con
         }
 }
 
+/* Per-splat sums of a per-pixel weight times (alpha_i(p) T_i(p))^power over
+ * the binned render's contributors (same skip and termination rules).
+ * pixel_weight: [H*W]; out: [n], accumulated. power 1 with weights dL/dy
+ * per channel is the colour gradient above. */
+void oracle_weight_sums_tiles(const oracle_splats* s, const int64_t* offsets, const int32_t* ids,
+                              int width, int height, const double* pixel_weight, int power,
+                              double* out) {
+    const int tiles_x = (width + TILE - 1) / TILE, tiles_y = (height + TILE - 1) / TILE;
+    const double a_min = 1.0 / 255.0;
+    for (int ty = 0; ty < tiles_y; ++ty)
+        for (int tx = 0; tx < tiles_x; ++tx) {
+            const int64_t t = (int64_t)ty * tiles_x + tx;
+            for (int y = ty * TILE; y < ty * TILE + TILE && y < height; ++y)
+                for (int x = tx * TILE; x < tx * TILE + TILE && x < width; ++x) {
+                    const double g = pixel_weight[(int64_t)y * width + x];
+                    double T = 1.0;
+                    for (int64_t k = offsets[t]; k < offsets[t + 1]; ++k) {
+                        const int64_t i = ids[k];
+                        if (!s->valid[i]) continue;
+                        double dx = x - s->u[i], dy = y - s->v[i];
+                        double A = s->conic[3 * i], B = s->conic[3 * i + 1];
+                        double Cc = s->conic[3 * i + 2];
+                        double p = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy;
+                        if (p > 0.0) p = 0.0;
+                        double alpha = s->opacity[i] * exp(p);
+                        if (alpha > 0.99) alpha = 0.99;
+                        if (alpha < a_min) continue;
+                        double testT = T * (1.0 - alpha);
+                        if (testT < 1e-4) break;
+                        out[i] += g * pow(alpha * T, (double)power);
+                        T = testT;
+                    }
+                }
+        }
+}
+
 /* SH gradient from the colour gradient (Eq. 2 with the shown colour
  * c = max(f + 0.5, 0), f = sum_k C_k Y_k(d), d = (mu - camera) / |mu - camera|):
  * dL/dC_{k,ch} = Y_k(d) [c_ch > 0] dL/dc_ch. rgb: [3n] shown colours (the

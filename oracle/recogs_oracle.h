@@ -153,6 +153,12 @@ void oracle_color_grad_tiles(const oracle_splats* s, const int64_t* offsets, con
 void oracle_sh_grad(int64_t n, const float* xyz, const oracle_camera* cam, const double* rgb,
                     const double* grad_rgb, double* grad_sh);
 
+/* out_i += sum_p pixel_weight[p] (alpha_i(p) T_i(p))^power over the binned
+ * render's contributors (the learned selection's coverage labels). */
+void oracle_weight_sums_tiles(const oracle_splats* s, const int64_t* offsets, const int32_t* ids,
+                              int width, int height, const double* pixel_weight, int power,
+                              double* out);
+
 #ifdef __cplusplus
 }
 #endif

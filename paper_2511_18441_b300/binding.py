@@ -119,7 +119,28 @@ SIGNATURES = {
     "recogs_refit_step": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.POINTER(CCamera),
                                     C.POINTER(C.c_float), C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.POINTER(CAdam), C.POINTER(C.c_double), C.c_void_p]),
+    "recogs_mlp_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_void_p)]),
+    "recogs_mlp_destroy": (None, [C.c_void_p]),
+    "recogs_mlp_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "recogs_mlp_features": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.POINTER(CCamera),
+                                      C.POINTER(CRegion), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "recogs_mlp_labels": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.POINTER(CCamera),
+                                    C.POINTER(CRegion), C.c_void_p, C.c_void_p]),
+    "recogs_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "recogs_mlp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                  C.c_int64, C.POINTER(C.c_float), C.POINTER(C.c_double),
+                                  C.c_void_p]),
+    "recogs_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                        C.c_int64, C.POINTER(CAdam), C.POINTER(C.c_double),
+                                        C.c_void_p]),
+    "recogs_mlp_select": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.POINTER(CCamera),
+                                    C.POINTER(CRegion), C.c_float, C.c_void_p, C.c_void_p,
+                                    C.POINTER(C.c_int64), C.c_void_p]),
+    "recogs_recolor_weighted": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.c_void_p,
+                                          C.POINTER(CTint), C.c_void_p]),
 }
+
+MLP_PARAMS = 8580
 
 _lib = None
 
@@ -400,6 +421,38 @@ class Context:
             C.byref(a), C.byref(loss) if want_loss else None, _stream_ptr(stream)))
         return loss.value if want_loss else None
 
+    # -- learned selection ----------------------------------------------------
+
+    def mlp(self, params):
+        """A learned-selection network initialised from `params` (8580 float32)."""
+        return Mlp(self, params)
+
+    def mlp_features(self, scene: DeviceScene, cam, region, labels=True, stream=None):
+        """(features bf16 [n, 64], labels float32 [n, 2] or None, valid uint8 [n])."""
+        import torch
+        n = scene.n
+        dev = scene.xyz.device
+        F = torch.empty((max(n, 1), 64), dtype=torch.bfloat16, device=dev)
+        V = torch.empty((max(n, 1),), dtype=torch.uint8, device=dev)
+        cs = scene.struct()
+        cc = camera_struct(cam)
+        r, keep = region_struct(region)
+        self._check(self._L.recogs_mlp_features(self._h, C.byref(cs), C.byref(cc), C.byref(r),
+                                                F.data_ptr(), V.data_ptr(), _stream_ptr(stream)))
+        L = None
+        if labels:
+            L = torch.empty((max(n, 1), 2), dtype=torch.float32, device=dev)
+            self._check(self._L.recogs_mlp_labels(self._h, C.byref(cs), C.byref(cc), C.byref(r),
+                                                  L.data_ptr(), _stream_ptr(stream)))
+            L = L[:n]
+        return F[:n], L, V[:n]
+
+    def recolor_weighted(self, scene: DeviceScene, weights, color_matrix, stream=None):
+        cs = scene.struct()
+        t = tint_struct(color_matrix)
+        self._check(self._L.recogs_recolor_weighted(self._h, C.byref(cs), weights.data_ptr(),
+                                                    C.byref(t), _stream_ptr(stream)))
+
     # -- introspection --------------------------------------------------------
 
     def tile_lists(self, n_tiles, n_pairs, device="cuda", stream=None):
@@ -457,6 +510,80 @@ class Context:
         self._check(self._L.recogs_batch_info(self._h, C.byref(info)))
         return {name: getattr(info, name) for name, _ in CBatchInfo._fields_
                 if name != "reserved"}
+
+
+class Mlp:
+    """recogs_mlp: the learned selection network (see recogs.h)."""
+
+    def __init__(self, ctx: Context, params):
+        p = np.ascontiguousarray(np.asarray(params, np.float32).reshape(-1))
+        if p.size != MLP_PARAMS:
+            raise ValueError(f"expected {MLP_PARAMS} parameters, got {p.size}")
+        h = C.c_void_p()
+        ctx._check(ctx._L.recogs_mlp_create(ctx._h, p.ctypes.data_as(C.POINTER(C.c_float)),
+                                            C.byref(h)))
+        self.ctx, self._h = ctx, h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.ctx._L.recogs_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(MLP_PARAMS, np.float32)
+        self.ctx._check(self.ctx._L.recogs_mlp_params(self._h,
+                                                      out.ctypes.data_as(C.POINTER(C.c_float))))
+        return out
+
+    def forward(self, features, out=None, stream=None):
+        import torch
+        n = int(features.shape[0])
+        if out is None:
+            out = torch.empty((max(n, 1), 4), dtype=torch.float32, device=features.device)
+        self.ctx._check(self.ctx._L.recogs_mlp_forward(self._h, features.data_ptr(), n,
+                                                       out.data_ptr(), _stream_ptr(stream)))
+        return out[:n]
+
+    def grad(self, features, labels, rows, stream=None):
+        g = np.zeros(MLP_PARAMS, np.float32)
+        loss = C.c_double()
+        self.ctx._check(self.ctx._L.recogs_mlp_grad(
+            self._h, features.data_ptr(), labels.data_ptr(), int(features.shape[0]),
+            rows.data_ptr(), int(rows.shape[0]), g.ctypes.data_as(C.POINTER(C.c_float)),
+            C.byref(loss), _stream_ptr(stream)))
+        return g, loss.value
+
+    def train_step(self, features, labels, rows, lr, beta1=0.9, beta2=0.999, eps=1e-8,
+                   want_loss=False, stream=None):
+        a = CAdam(float(lr), float(beta1), float(beta2), float(eps), 0, 0)
+        loss = C.c_double()
+        self.ctx._check(self.ctx._L.recogs_mlp_train_step(
+            self._h, features.data_ptr(), labels.data_ptr(), int(features.shape[0]),
+            rows.data_ptr(), int(rows.shape[0]), C.byref(a), C.byref(loss) if want_loss else None,
+            _stream_ptr(stream)))
+        return loss.value if want_loss else None
+
+    def select(self, scene: DeviceScene, cam, region, delta=0.1, stream=None):
+        """(mask words int32, weights [n, 3], fallback count)."""
+        import torch
+        n = scene.n
+        dev = scene.xyz.device
+        mask = torch.zeros((max(mask_words(n), 1),), dtype=torch.int32, device=dev)
+        w = torch.empty((max(n, 1), 3), dtype=torch.float32, device=dev)
+        fb = C.c_int64()
+        cs = scene.struct()
+        cc = camera_struct(cam)
+        r, keep = region_struct(region)
+        self.ctx._check(self.ctx._L.recogs_mlp_select(
+            self._h, C.byref(cs), C.byref(cc), C.byref(r), float(delta), mask.data_ptr(),
+            w.data_ptr(), C.byref(fb), _stream_ptr(stream)))
+        return mask, w[:n], fb.value
 
 
 class Batch:

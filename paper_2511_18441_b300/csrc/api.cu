@@ -28,13 +28,14 @@ namespace {
 
 enum Stage {
     ST_PREPROCESS, ST_SCAN, ST_COMPACT, ST_SORT_DEPTH, ST_PAIR_OFFSETS, ST_EMIT, ST_SORT_TILE,
-    ST_BLEND, ST_SELECT, ST_RECOLOR, ST_H2D, ST_D2H, ST_SCATTER, ST_TILE_SORT, ST_REFIT, ST_COUNT
+    ST_BLEND, ST_SELECT, ST_RECOLOR, ST_H2D, ST_D2H, ST_SCATTER, ST_TILE_SORT, ST_REFIT, ST_MLP,
+    ST_COUNT
 };
 // "scan" = tile totals, tile ranges and tile order; "compact" .. "sort_tile"
 // = the global sort path
 const char* const kStageNames[ST_COUNT] = {
     "preprocess", "scan", "compact", "sort_depth", "pair_offsets", "emit", "sort_tile",
-    "blend", "select", "recolor", "h2d", "d2h", "scatter", "tile_sort", "refit"};
+    "blend", "select", "recolor", "h2d", "d2h", "scatter", "tile_sort", "refit", "mlp"};
 
 struct DevBuf {
     void* p = nullptr;
@@ -1434,6 +1435,300 @@ recogs_status recogs_refit_step(recogs_ctx* ctx, recogs_scene* scene, const reco
     DeviceGuard g(ctx->device);
     return refit(ctx, *scene, *camera, bgv, target_hwc, nullptr, nullptr, nullptr, adam_m, adam_v,
                  adam, loss_out, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// learned selection MLP
+
+struct recogs_mlp {
+    recogs_ctx* ctx = nullptr;
+    float* params = nullptr;     // fp32 master parameters [kMlpParams]
+    float* m = nullptr;
+    float* v = nullptr;
+    float* grad = nullptr;
+    float* loss = nullptr;       // device scalar
+    MlpFrags* frags = nullptr;
+    unsigned long long* fallbacks = nullptr;
+    DevBuf feat, out;
+    int64_t step = 0;
+};
+
+namespace {
+
+recogs_status mlp_region(recogs_ctx* ctx, const recogs_camera* cam, const recogs_region* region,
+                         DevRegion& dr, MlpRegionFrame& fr) {
+    CKS(check_camera(ctx, cam, "select_camera"));
+    CKS(dev_region(ctx, region, *cam, dr));
+    if (region->kind != RECOGS_REGION_POLYGON)
+        return fail(ctx, RECOGS_EINVAL, "the learned selection takes a polygon region");
+    double cx = 0, cy = 0;
+    for (int k = 0; k < dr.n; ++k) {
+        cx += dr.xy[2 * k];
+        cy += dr.xy[2 * k + 1];
+    }
+    cx /= dr.n;
+    cy /= dr.n;
+    double mr = 0;
+    for (int k = 0; k < dr.n; ++k) mr += std::hypot(dr.xy[2 * k] - cx, dr.xy[2 * k + 1] - cy);
+    fr.cx = (float)cx;
+    fr.cy = (float)cy;
+    fr.mean_r = (float)(mr / dr.n);
+    if (!(fr.mean_r > 0.f)) return fail(ctx, RECOGS_EINVAL, "degenerate polygon");
+    return RECOGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+recogs_status recogs_mlp_create(recogs_ctx* ctx, const float* params_host, recogs_mlp** out) {
+    if (!ctx || !out) return RECOGS_EINVAL;
+    *out = nullptr;
+    if (!params_host) return fail(ctx, RECOGS_EINVAL, "params_host is NULL");
+    for (int k = 0; k < kMlpParams; ++k)
+        if (!finite(params_host[k])) return fail(ctx, RECOGS_EINVAL, "a parameter is not finite");
+    DeviceGuard g(ctx->device);
+    recogs_mlp* m = new recogs_mlp();
+    m->ctx = ctx;
+    const size_t pb = sizeof(float) * kMlpParams;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&m->params, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&m->m, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&m->v, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&m->grad, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&m->loss, sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&m->frags, mlp_frags_bytes());
+    if (e == cudaSuccess) e = cudaMalloc(&m->fallbacks, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemcpy(m->params, params_host, pb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(m->m, 0, pb);
+    if (e == cudaSuccess) e = cudaMemset(m->v, 0, pb);
+    if (e == cudaSuccess) e = cudaMemset(m->grad, 0, pb);
+    if (e == cudaSuccess) {
+        launch_mlp_pack(m->params, m->frags, 0);
+        e = cudaDeviceSynchronize();
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        recogs_mlp_destroy(m);
+        return fail(ctx, RECOGS_ENOMEM, "MLP set-up failed: %s", cudaGetErrorString(e));
+    }
+    *out = m;
+    return RECOGS_OK;
+}
+
+void recogs_mlp_destroy(recogs_mlp* m) {
+    if (!m) return;
+    DeviceGuard g(m->ctx->device);
+    cudaDeviceSynchronize();
+    void* ps[] = {m->params, m->m, m->v, m->grad, m->loss, m->frags, m->fallbacks, m->feat.p,
+                  m->out.p};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    delete m;
+}
+
+recogs_status recogs_mlp_params(recogs_mlp* m, float* params_host_out) {
+    if (!m || !params_host_out) return RECOGS_EINVAL;
+    recogs_ctx* ctx = m->ctx;
+    DeviceGuard g(ctx->device);
+    CK(cudaMemcpy(params_host_out, m->params, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost));
+    return RECOGS_OK;
+}
+
+recogs_status recogs_mlp_features(recogs_ctx* ctx, const recogs_scene* scene,
+                                  const recogs_camera* select_camera,
+                                  const recogs_region* region, uint16_t* features_out,
+                                  uint8_t* valid_out, void* stream) {
+    if (!ctx) return RECOGS_EINVAL;
+    CKS(check_scene(ctx, scene));
+    DevRegion dr;
+    MlpRegionFrame fr;
+    CKS(mlp_region(ctx, select_camera, region, dr, fr));
+    if (scene->n > 0 && (!features_out || !aligned(features_out, 16)))
+        return fail(ctx, RECOGS_EINVAL, "features_out is NULL or not 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    stage_begin(ctx, ST_MLP, st);
+    const int l = launch_mlp_features(*scene, dev_camera(*select_camera), dr, fr,
+                                      reinterpret_cast<uint32_t*>(features_out), valid_out, st);
+    stage_end(ctx, ST_MLP, l, st);
+    CK(cudaGetLastError());
+    return RECOGS_OK;
+}
+
+recogs_status recogs_mlp_labels(recogs_ctx* ctx, const recogs_scene* scene,
+                                const recogs_camera* select_camera, const recogs_region* region,
+                                float* labels_out, void* stream) {
+    if (!ctx) return RECOGS_EINVAL;
+    CKS(check_scene(ctx, scene));
+    DevRegion dr;
+    MlpRegionFrame fr;
+    CKS(mlp_region(ctx, select_camera, region, dr, fr));
+    const int64_t n = scene->n;
+    if (n > 0 && (!labels_out || !aligned(labels_out, 8)))
+        return fail(ctx, RECOGS_EINVAL, "labels_out is NULL or misaligned");
+    if (n == 0) return RECOGS_OK;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t npix = (size_t)select_camera->width * select_camera->height;
+    CKS(ensure(ctx, ctx->rf_img, 12 * npix));
+    CKS(ensure(ctx, ctx->rf_grad, 12 * (size_t)n));
+    // render of the selection view (tile lists and records), then the
+    // per-Gaussian sums of alpha T inside the region and over all pixels
+    Schedule sched = ctx->sched;
+    sched.pair_capacity = 0;
+    const float bg0[3] = {0.f, 0.f, 0.f};
+    CKS(render_device(ctx, ctx->main, sched, *scene, *select_camera, nullptr, bg0,
+                      P<float>(ctx->rf_img), nullptr, nullptr, st));
+    CK(cudaMemsetAsync(ctx->rf_grad.p, 0, 12 * (size_t)n, st));
+    const DevCamera dc = dev_camera(*select_camera);
+    BlendExtra ex;
+    ex.grad_rgb = P<float>(ctx->rf_grad);
+    ex.cover = true;
+    ex.region = dr;
+    stage_begin(ctx, ST_MLP, st);
+    int l = launch_blend(P<uint2>(ctx->main.ranges), P<uint32_t>(ctx->main.order), ctx->last_ids,
+                         P<float4>(ctx->main.rec), dc, bg0, P<float>(ctx->rf_img), nullptr,
+                         nullptr, sched.blend_batch, &ex, st);
+    l += launch_mlp_labels(*scene, dc, dr, P<float>(ctx->rf_grad), labels_out, st);
+    stage_end(ctx, ST_MLP, l, st);
+    CK(cudaGetLastError());
+    return RECOGS_OK;
+}
+
+recogs_status recogs_mlp_forward(recogs_mlp* m, const uint16_t* features, int64_t n, float* out,
+                                 void* stream) {
+    if (!m) return RECOGS_EINVAL;
+    recogs_ctx* ctx = m->ctx;
+    if (n < 0) return fail(ctx, RECOGS_EINVAL, "n < 0");
+    if (n > 0 && (!features || !out || !aligned(features, 16) || !aligned(out, 16)))
+        return fail(ctx, RECOGS_EINVAL, "features or out NULL or not 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    stage_begin(ctx, ST_MLP, st);
+    const int l = launch_mlp_forward(reinterpret_cast<const uint32_t*>(features), n, m->frags, out, st);
+    stage_end(ctx, ST_MLP, l, st);
+    CK(cudaGetLastError());
+    return RECOGS_OK;
+}
+
+static recogs_status mlp_batch_grad(recogs_mlp* m, const uint16_t* features, const float* labels,
+                                    int64_t n_samples, const uint32_t* rows, int64_t batch,
+                                    double* loss_out, cudaStream_t st) {
+    recogs_ctx* ctx = m->ctx;
+    if (batch < 1 || n_samples < 1)
+        return fail(ctx, RECOGS_EINVAL, "batch and n_samples must be positive");
+    if (!features || !labels || !rows || !aligned(features, 16) || !aligned(labels, 8) ||
+        !aligned(rows, 4))
+        return fail(ctx, RECOGS_EINVAL, "features, labels or rows NULL or misaligned");
+    CK(cudaMemsetAsync(m->loss, 0, sizeof(float), st));
+    stage_begin(ctx, ST_MLP, st);
+    const int l = launch_mlp_train(reinterpret_cast<const uint32_t*>(features), labels, n_samples,
+                                   rows, batch, m->frags, m->grad, m->loss, st);
+    stage_end(ctx, ST_MLP, l, st);
+    CK(cudaGetLastError());
+    if (loss_out) {
+        float ls = 0.f;
+        CK(cudaMemcpyAsync(&ls, m->loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        *loss_out = (double)ls / (double)batch;
+    }
+    return RECOGS_OK;
+}
+
+recogs_status recogs_mlp_grad(recogs_mlp* m, const uint16_t* features, const float* labels,
+                              int64_t n_samples, const uint32_t* rows, int64_t batch,
+                              float* grad_host_out, double* loss_out, void* stream) {
+    if (!m) return RECOGS_EINVAL;
+    recogs_ctx* ctx = m->ctx;
+    if (!grad_host_out) return fail(ctx, RECOGS_EINVAL, "grad_host_out is NULL");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CKS(mlp_batch_grad(m, features, labels, n_samples, rows, batch, loss_out, st));
+    CK(cudaMemcpyAsync(grad_host_out, m->grad, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaMemsetAsync(m->grad, 0, sizeof(float) * kMlpParams, st));
+    CK(cudaStreamSynchronize(st));
+    return RECOGS_OK;
+}
+
+recogs_status recogs_mlp_train_step(recogs_mlp* m, const uint16_t* features, const float* labels,
+                                    int64_t n_samples, const uint32_t* rows, int64_t batch,
+                                    const recogs_adam* adam, double* loss_out, void* stream) {
+    if (!m) return RECOGS_EINVAL;
+    recogs_ctx* ctx = m->ctx;
+    if (!adam || !(adam->lr >= 0.f) || !(adam->beta1 >= 0.f && adam->beta1 < 1.f) ||
+        !(adam->beta2 >= 0.f && adam->beta2 < 1.f) || !(adam->eps >= 0.f))
+        return fail(ctx, RECOGS_EINVAL, "Adam parameters NULL or out of range");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CKS(mlp_batch_grad(m, features, labels, n_samples, rows, batch, loss_out, st));
+    const int64_t t = ++m->step;
+    const float bc1 = (float)(1.0 / (1.0 - std::pow((double)adam->beta1, (double)t)));
+    const float bc2 = (float)(1.0 / (1.0 - std::pow((double)adam->beta2, (double)t)));
+    stage_begin(ctx, ST_MLP, st);
+    int l = launch_mlp_adam(m->params, m->m, m->v, m->grad, adam->lr, adam->beta1, adam->beta2,
+                            adam->eps, bc1, bc2, st);
+    l += launch_mlp_pack(m->params, m->frags, st);
+    stage_end(ctx, ST_MLP, l, st);
+    CK(cudaGetLastError());
+    return RECOGS_OK;
+}
+
+recogs_status recogs_mlp_select(recogs_mlp* m, const recogs_scene* scene,
+                                const recogs_camera* select_camera, const recogs_region* region,
+                                float delta, uint32_t* mask_out, float* weights_out,
+                                int64_t* fallbacks_out, void* stream) {
+    if (!m) return RECOGS_EINVAL;
+    recogs_ctx* ctx = m->ctx;
+    CKS(check_scene(ctx, scene));
+    DevRegion dr;
+    MlpRegionFrame fr;
+    CKS(mlp_region(ctx, select_camera, region, dr, fr));
+    if (!(delta >= 0.f && delta <= 0.5f)) return fail(ctx, RECOGS_EINVAL, "delta outside [0, 0.5]");
+    const int64_t n = scene->n;
+    if (n > 0 && (!mask_out || !weights_out || !aligned(mask_out, 4) || !aligned(weights_out, 4)))
+        return fail(ctx, RECOGS_EINVAL, "mask_out or weights_out NULL or misaligned");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CKS(ensure(ctx, m->feat, 128 * (size_t)(n > 0 ? n : 1)));
+    CKS(ensure(ctx, m->out, 16 * (size_t)(n > 0 ? n : 1)));
+    CK(cudaMemsetAsync(m->fallbacks, 0, sizeof(unsigned long long), st));
+    const DevCamera dc = dev_camera(*select_camera);
+    stage_begin(ctx, ST_MLP, st);
+    int l = launch_mlp_features(*scene, dc, dr, fr, P<uint32_t>(m->feat), nullptr, st);
+    l += launch_mlp_forward(P<uint32_t>(m->feat), n, m->frags, P<float>(m->out), st);
+    l += launch_mlp_decide(*scene, dc, dr, P<float>(m->out), delta, mask_out, weights_out,
+                           m->fallbacks, st);
+    stage_end(ctx, ST_MLP, l, st);
+    CK(cudaGetLastError());
+    if (fallbacks_out) {
+        unsigned long long fb = 0;
+        CK(cudaMemcpyAsync(&fb, m->fallbacks, sizeof(fb), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        *fallbacks_out = (int64_t)fb;
+    }
+    return RECOGS_OK;
+}
+
+recogs_status recogs_recolor_weighted(recogs_ctx* ctx, recogs_scene* scene, const float* weights,
+                                      const recogs_tint* tint, void* stream) {
+    if (!ctx) return RECOGS_EINVAL;
+    CKS(check_scene(ctx, scene));
+    CKS(check_tint(ctx, tint));
+    if (scene->n > 0 && (!weights || !aligned(weights, 4)))
+        return fail(ctx, RECOGS_EINVAL, "weights is NULL or misaligned");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    float fix[3];
+    dc_fix_of(tint->color_matrix, fix);
+    stage_begin(ctx, ST_RECOLOR, st);
+    const int l = launch_recolor_weighted(*scene, weights, tint->color_matrix, fix, st);
+    stage_end(ctx, ST_RECOLOR, l, st);
+    CK(cudaGetLastError());
+    return RECOGS_OK;
 }
 
 }  // extern "C"

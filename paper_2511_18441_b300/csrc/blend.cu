@@ -29,6 +29,24 @@ __device__ __forceinline__ float exp2_approx(float x) {
     return y;
 }
 
+// The region test of the plain selection at a pixel centre (box: half-open;
+// polygon: even-odd rule with the selection's arithmetic).
+__device__ __forceinline__ bool in_region(const DevRegion& r, float u, float v) {
+    if (r.kind == RECOGS_REGION_BOX)
+        return (u >= r.xy[0]) && (u < r.xy[2]) && (v >= r.xy[1]) && (v < r.xy[3]);
+    bool inside = false;
+    for (int i = 0, j = r.n - 1; i < r.n; j = i++) {
+        const float xi = r.xy[2 * i], yi = r.xy[2 * i + 1];
+        const float xj = r.xy[2 * j], yj = r.xy[2 * j + 1];
+        if ((yi > v) != (yj > v)) {
+            const float xc = __fadd_rn(xi, __fdiv_rn(__fmul_rn(__fsub_rn(v, yi), __fsub_rn(xj, xi)),
+                                                     __fsub_rn(yj, yi)));
+            if (u < xc) inside = !inside;
+        }
+    }
+    return inside;
+}
+
 // Group mask of a Gaussian with centre (u, v) in this tile's frame whose
 // alpha >= 1/255 box has half extents (ex, ey). The tile's 16x16 pixels are
 // split into 32 groups of 4x2 pixels (a 4 x 8 grid of groups); warp w owns
@@ -58,8 +76,12 @@ __device__ __forceinline__ uint32_t group_mask(float u, float v, float ex, float
 enum BlendMode {
     kBlendColour = 0,   // image (and final T)
     kBlendDepth = 1,    // image, final T and the median depth (Sec. 3.2.2)
-    kBlendGrad = 2      // colour gradient of the L1 loss against a target (Sec. 3.3, Eq. 6-7)
+    kBlendGrad = 2,     // colour gradient of the L1 loss against a target (Sec. 3.3, Eq. 6-7)
+    kBlendCover = 3     // per Gaussian: sum of (alpha T)^2 over pixels inside a region, and over all
 };
+
+// the modes that sum a per-pixel weight times alpha_i T_i per Gaussian
+template <int MODE> struct Accumulates { static constexpr bool value = MODE >= kBlendGrad; };
 
 // BATCH (128 or 256) Gaussians are staged per batch; threads below BATCH
 // gather them. Every mode walks the same lists with the same arithmetic, so
@@ -78,8 +100,9 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
     // depth mode: view depth of each staged Gaussian; gradient mode: its index
     // and its colour gradient summed over this tile's pixels
     __shared__ float s_z[MODE == kBlendDepth ? BATCH : 1];
-    __shared__ uint32_t s_id[MODE == kBlendGrad ? BATCH : 1];
-    __shared__ float s_g[MODE == kBlendGrad ? 3 * BATCH : 1];
+    constexpr bool kAcc = Accumulates<MODE>::value;
+    __shared__ uint32_t s_id[kAcc ? BATCH : 1];
+    __shared__ float s_g[kAcc ? 3 * BATCH : 1];
     __shared__ float s_loss[MODE == kBlendGrad ? kBlendThreads / 32 : 1];
 
     const int tile = (int)order[blockIdx.x];
@@ -118,8 +141,14 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
             g2 = d2 > 0.f ? ex.inv_n : d2 < 0.f ? -ex.inv_n : 0.f;
             l1 = fabsf(d0) + fabsf(d1) + fabsf(d2);
         }
-        for (int k = threadIdx.x; k < 3 * BATCH; k += kBlendThreads) s_g[k] = 0.f;
     }
+    if (MODE == kBlendCover && inside) {
+        // weights 1[pixel centre in the region] and 1 (the pixel centre is (px, py))
+        g0 = in_region(ex.region, (float)px, (float)py) ? 1.f : 0.f;
+        g1 = 1.f;
+    }
+    if (kAcc)
+        for (int k = threadIdx.x; k < 3 * BATCH; k += kBlendThreads) s_g[k] = 0.f;
 
     // prefetch the first batch
     float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra;
@@ -135,7 +164,7 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
     // gradient mode: add the previous batch's per-Gaussian sums to the global
     // gradient (one atomic per Gaussian, tile and channel) and clear them
     auto flush = [&](uint32_t prev_b) {
-        if (MODE != kBlendGrad) return;
+        if (!kAcc) return;
         const int k = threadIdx.x;
         if (gatherer && prev_b + k < end) {
             const uint32_t id = s_id[k];
@@ -174,7 +203,7 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
             s_c[threadIdx.x] = rc.z;
             s_m[threadIdx.x] = group_mask(u, v, rb.z, rb.w);
             if (MODE == kBlendDepth) s_z[threadIdx.x] = __uint_as_float(__ldg(ex.zkey + rid));
-            if (MODE == kBlendGrad) s_id[threadIdx.x] = rid;
+            if (kAcc) s_id[threadIdx.x] = rid;
         }
         fetched = min(end, b + BATCH);
         prev_b = b;
@@ -226,12 +255,14 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
                     const bool stop = take && nT < 1e-4f;
                     const bool add = take && !stop;
                     const float w = add ? al0 * T : 0.0f;
-                    if (MODE != kBlendGrad) {
+                    if (!kAcc) {
                         cr = fmaf(b0.z, w, cr);
                         cg = fmaf(b0.w, w, cg);
                         cb = fmaf(s_c[s0], w, cb);
                     } else {
-                        const float v0 = group_sum(g0 * w), v1 = group_sum(g1 * w);
+                        // gradient: g alpha T; coverage: g (alpha T)^2
+                        const float wc = MODE == kBlendCover ? w * w : w;
+                        const float v0 = group_sum(g0 * wc), v1 = group_sum(g1 * wc);
                         const float v2 = group_sum(g2 * w);
                         if ((lane & 7) == 0 && act0) {
                             atomicAdd(&s_g[3 * s0 + 0], v0);
@@ -252,12 +283,14 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
                     const bool stop = take && nT < 1e-4f;
                     const bool add = take && !stop;
                     const float w = add ? al1 * T : 0.0f;
-                    if (MODE != kBlendGrad) {
+                    if (!kAcc) {
                         cr = fmaf(b1.z, w, cr);
                         cg = fmaf(b1.w, w, cg);
                         cb = fmaf(s_c[s1], w, cb);
                     } else {
-                        const float v0 = group_sum(g0 * w), v1 = group_sum(g1 * w);
+                        // gradient: g alpha T; coverage: g (alpha T)^2
+                        const float wc = MODE == kBlendCover ? w * w : w;
+                        const float v0 = group_sum(g0 * wc), v1 = group_sum(g1 * wc);
                         const float v2 = group_sum(g2 * w);
                         if ((lane & 7) == 0 && act1) {
                             atomicAdd(&s_g[3 * s1 + 0], v0);
@@ -275,6 +308,11 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
             }
             if (__all_sync(0xffffffffu, done)) break;
         }
+    }
+    if (MODE == kBlendCover) {
+        __syncthreads();
+        if (prev_b != 0xffffffffu) flush(prev_b);
+        return;
     }
     if (MODE == kBlendGrad) {
         __syncthreads();
@@ -323,7 +361,10 @@ int launch_blend(const uint2* ranges, const uint32_t* order, const uint32_t* ids
     const int tiles = cam.tiles_x * cam.tiles_y;
     BlendExtra ex;
     if (extra) ex = *extra;
-    if (ex.grad_rgb)
+    if (ex.grad_rgb && ex.cover)
+        blend_launch<kBlendCover>(batch, tiles, ranges, order, ids, rec, cam, bg, image, final_T,
+                                  nullptr, ex, st);
+    else if (ex.grad_rgb)
         blend_launch<kBlendGrad>(batch, tiles, ranges, order, ids, rec, cam, bg, image, final_T,
                                  nullptr, ex, st);
     else if (ex.depth)

@@ -1,0 +1,729 @@
+// Learned selection: a per-Gaussian MLP 59 -> 64 -> 64 -> 4 (GELU) that
+// predicts the plain selection bit (a logit) and the Gaussian's tint weight
+// (three per-channel logits, the "tint residual"), with the plain test as
+// fallback and judge.
+//
+// ReCoGS (arXiv 2511.18441) names the leak of its selection as a limitation
+// (Sec. 6): a Gaussian larger than the selection is recoloured as a whole or
+// not at all. Recolouring each Gaussian by the least-squares weight of its
+// rendered contribution, sum over inside pixels of (alpha T)^2 over the sum
+// over all pixels, reduces the error against the pixel-tinted edit target of
+// Sec. 3.3; that weight needs a render and a per-pixel pass of the selection
+// view, the network predicts it per Gaussian from its own attributes.
+//
+// Features (64 per Gaussian, bf16, row-major [n][64]), the splat in the
+// selection view:
+//   0, 1  q / rho, q = (u, v) - c: c = polygon vertex centroid, rho =
+//         distance from c to the boundary along q (a star-shaped polygon
+//         maps onto the unit disc)
+//   2     ln(t_z rho / f_x)
+//   3, 4  ln(sigma_1 / rho), ln(sigma_2 / rho): axis standard deviations of
+//         the projected (dilated) 2D Gaussian
+//   5     ln(sigma_r / rho), its standard deviation along q
+//   6, 7  cos 2 theta, sin 2 theta of its major axis' angle to q
+//   8     (rho - |q|) / sigma_r clamped to [-8, 8]: distance to the boundary
+//   9     mean log-scale, 10 opacity logit, 11-58 SH coefficients in
+//         [16][3] order, 59-63 zero
+// Network: BF16 operands, FP32 accumulation (mma.sync m16n8k16), every
+// product's inputs (features, weights, activations and the backward's
+// output gradients) rounded to bf16, biases and GELU in FP32.
+#include "recogs_internal.cuh"
+
+namespace recogs {
+
+// ---------------------------------------------------------------------------
+// parameter layout and fragment-ordered weights
+
+constexpr int kOffW1 = 0, kOffB1 = 4096, kOffW2 = 4160, kOffB2 = 8256, kOffW3 = 8320,
+              kOffB3 = 8576;
+static_assert(kOffB3 + 4 == kMlpParams, "parameter layout");
+
+// B operands of mma.m16n8k16 (.col), per lane two registers of two bf16:
+// b0 = (B[2t][g], B[2t+1][g]), b1 = (B[2t+8][g], B[2t+9][g]) of the 16x8
+// block, g = lane / 4, t = lane % 4.
+//   F1, F2: B = W1, W2 ([in][out], 4 k-tiles x 8 n-tiles)
+//   F3:     B = W3 padded to 8 outputs (4 k-tiles x 1 n-tile)
+//   G2:     B = W2^T (K = outputs of layer 2, N = its inputs)
+//   G3:     B = W3^T (K = 16 outputs, 4 real; N = 64 inputs; 1 x 8 tiles)
+struct MlpFrags {
+    uint32_t F1[4 * 8 * 64], F2[4 * 8 * 64], F3[4 * 1 * 64], G2[4 * 8 * 64], G3[1 * 8 * 64];
+    float b1[64], b2[64], b3[8];
+};
+static_assert(sizeof(MlpFrags) % 16 == 0, "fragment block copies in 16-byte pieces");
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const uint32_t l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+    const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+    return l | (h << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// fp32 parameters -> fragment-ordered bf16 weights and fp32 biases (one block)
+__global__ void __launch_bounds__(256) mlp_pack_kernel(const float* __restrict__ p,
+                                                       MlpFrags* __restrict__ f) {
+    const float* W1 = p + kOffW1;
+    const float* W2 = p + kOffW2;
+    const float* W3 = p + kOffW3;
+    auto w3 = [&](int in, int out) { return out < 4 ? W3[in * 4 + out] : 0.f; };
+    for (int e = threadIdx.x; e < 4 * 8 * 32; e += blockDim.x) {
+        const int lane = e & 31, nt = (e >> 5) & 7, kt = e >> 8;
+        const int g = lane >> 2, t = lane & 3;
+        const int k0 = 16 * kt + 2 * t, n = 8 * nt + g;
+        uint32_t* o1 = f->F1 + 2 * e;
+        o1[0] = pack_bf16(W1[k0 * 64 + n], W1[(k0 + 1) * 64 + n]);
+        o1[1] = pack_bf16(W1[(k0 + 8) * 64 + n], W1[(k0 + 9) * 64 + n]);
+        uint32_t* o2 = f->F2 + 2 * e;
+        o2[0] = pack_bf16(W2[k0 * 64 + n], W2[(k0 + 1) * 64 + n]);
+        o2[1] = pack_bf16(W2[(k0 + 8) * 64 + n], W2[(k0 + 9) * 64 + n]);
+        // W2^T: K index = output unit k0.., N index = input unit n
+        uint32_t* q2 = f->G2 + 2 * e;
+        q2[0] = pack_bf16(W2[n * 64 + k0], W2[n * 64 + k0 + 1]);
+        q2[1] = pack_bf16(W2[n * 64 + k0 + 8], W2[n * 64 + k0 + 9]);
+    }
+    for (int e = threadIdx.x; e < 4 * 32; e += blockDim.x) {
+        const int lane = e & 31, kt = e >> 5;
+        const int g = lane >> 2, t = lane & 3;
+        const int k0 = 16 * kt + 2 * t;
+        uint32_t* o3 = f->F3 + 2 * e;
+        o3[0] = pack_bf16(w3(k0, g), w3(k0 + 1, g));
+        o3[1] = pack_bf16(w3(k0 + 8, g), w3(k0 + 9, g));
+    }
+    for (int e = threadIdx.x; e < 8 * 32; e += blockDim.x) {
+        const int lane = e & 31, nt = e >> 5;
+        const int g = lane >> 2, t = lane & 3;
+        const int n = 8 * nt + g;
+        uint32_t* q3 = f->G3 + 2 * e;
+        q3[0] = pack_bf16(w3(n, 2 * t), w3(n, 2 * t + 1));
+        q3[1] = 0u;   // K rows 8..15: padding outputs
+    }
+    for (int e = threadIdx.x; e < 64; e += blockDim.x) {
+        f->b1[e] = p[kOffB1 + e];
+        f->b2[e] = p[kOffB2 + e];
+    }
+    if (threadIdx.x < 8) f->b3[threadIdx.x] = threadIdx.x < 4 ? p[kOffB3 + threadIdx.x] : 0.f;
+}
+
+__device__ __forceinline__ float gelu(float z) {
+    return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+}
+
+__device__ __forceinline__ float gelu_grad(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
+           z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+__device__ __forceinline__ float sigmoidf(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+// copy the fragment block into shared memory (all threads of the block)
+__device__ __forceinline__ void load_frags(MlpFrags* s, const MlpFrags* g) {
+    const uint4* src = reinterpret_cast<const uint4*>(g);
+    uint4* dst = reinterpret_cast<uint4*>(s);
+    for (int k = threadIdx.x; k < (int)(sizeof(MlpFrags) / 16); k += blockDim.x) dst[k] = src[k];
+}
+
+// One warp: the forward pass of 16 rows. xa: A fragments of the features
+// (4 k-tiles). Returns the pre-activations z1, z2 (C layout, 8 n-tiles), the
+// hidden activations as A fragments (bf16) and the outputs (C layout).
+struct WarpFwd {
+    float z1[8][4], z2[8][4], o[4];
+    uint32_t h1[4][4], h2[4][4];
+};
+
+// acc = bias + a x B (bias == NULL: no bias), 16 rows x 64 columns
+__device__ __forceinline__ void layer_mma(float (&acc)[8][4], const uint32_t (&a)[4][4],
+                                          const uint32_t* frag, const float* bias, int lane) {
+    const int t = lane & 3;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        acc[nt][0] = acc[nt][2] = bias ? bias[8 * nt + 2 * t] : 0.f;
+        acc[nt][1] = acc[nt][3] = bias ? bias[8 * nt + 2 * t + 1] : 0.f;
+    }
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt)
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const uint2 b = *reinterpret_cast<const uint2*>(frag + 2 * ((kt * 8 + nt) * 32 + lane));
+            mma_bf16(acc[nt], a[kt][0], a[kt][1], a[kt][2], a[kt][3], b.x, b.y);
+        }
+}
+
+// C fragments of 8 n-tiles -> A fragments of 4 k-tiles after f (bf16)
+template <typename F>
+__device__ __forceinline__ void c_to_a(const float (&c)[8][4], uint32_t (&a)[4][4], F f) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        a[j][0] = pack_bf16(f(c[2 * j][0]), f(c[2 * j][1]));
+        a[j][1] = pack_bf16(f(c[2 * j][2]), f(c[2 * j][3]));
+        a[j][2] = pack_bf16(f(c[2 * j + 1][0]), f(c[2 * j + 1][1]));
+        a[j][3] = pack_bf16(f(c[2 * j + 1][2]), f(c[2 * j + 1][3]));
+    }
+}
+
+__device__ __forceinline__ void warp_forward(const uint32_t (&xa)[4][4], const MlpFrags& s,
+                                             WarpFwd& w, int lane) {
+    layer_mma(w.z1, xa, s.F1, s.b1, lane);
+    c_to_a(w.z1, w.h1, [](float z) { return gelu(z); });
+    layer_mma(w.z2, w.h1, s.F2, s.b2, lane);
+    c_to_a(w.z2, w.h2, [](float z) { return gelu(z); });
+    const int t = lane & 3;
+    w.o[0] = w.o[2] = s.b3[2 * t];
+    w.o[1] = w.o[3] = s.b3[2 * t + 1];
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+        const uint2 b = *reinterpret_cast<const uint2*>(s.F3 + 2 * (kt * 32 + lane));
+        mma_bf16(w.o, w.h2[kt][0], w.h2[kt][1], w.h2[kt][2], w.h2[kt][3], b.x, b.y);
+    }
+}
+
+// A fragments of 16 feature rows; rows[r] < 0 gives a zero row
+__device__ __forceinline__ void load_x(const uint32_t* __restrict__ X, int64_t row_g,
+                                       int64_t row_g8, uint32_t (&xa)[4][4], int lane) {
+    const int t = lane & 3;
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+        xa[kt][0] = row_g >= 0 ? __ldg(X + row_g * 32 + 8 * kt + t) : 0u;
+        xa[kt][1] = row_g8 >= 0 ? __ldg(X + row_g8 * 32 + 8 * kt + t) : 0u;
+        xa[kt][2] = row_g >= 0 ? __ldg(X + row_g * 32 + 8 * kt + 4 + t) : 0u;
+        xa[kt][3] = row_g8 >= 0 ? __ldg(X + row_g8 * 32 + 8 * kt + 4 + t) : 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// inference: out[n][4] = (selection logit, three coverage logits)
+
+__global__ void __launch_bounds__(256) mlp_forward_kernel(const uint32_t* __restrict__ X,
+                                                          int64_t n,
+                                                          const MlpFrags* __restrict__ frags,
+                                                          float* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MlpFrags& s = *reinterpret_cast<MlpFrags*>(smem_raw);
+    load_frags(&s, frags);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t tiles = (n + 15) / 16;
+    for (int64_t tile = (int64_t)blockIdx.x * 8 + warp; tile < tiles; tile += (int64_t)gridDim.x * 8) {
+        const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
+        uint32_t xa[4][4];
+        load_x(X, r0 < n ? r0 : -1, r1 < n ? r1 : -1, xa, lane);
+        WarpFwd w;
+        warp_forward(xa, s, w, lane);
+        if (t < 2) {
+            if (r0 < n) *reinterpret_cast<float2*>(out + r0 * 4 + 2 * t) = make_float2(w.o[0], w.o[1]);
+            if (r1 < n) *reinterpret_cast<float2*>(out + r1 * 4 + 2 * t) = make_float2(w.o[2], w.o[3]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// training: forward, loss, backward and the batch's gradient (atomically
+// added to grad[kMlpParams]); rows[b] = sample of batch position b
+
+constexpr int kTrainRows = 128;          // rows per block (8 warps x 16)
+constexpr int kTStride = kTrainRows + 8; // bf16 row stride of the transposed operands
+
+struct TrainSmem {
+    MlpFrags f;
+    __nv_bfloat16 XT[64 * kTStride], H1T[64 * kTStride], H2T[64 * kTStride];
+    __nv_bfloat16 D1T[64 * kTStride], D2T[64 * kTStride], D3T[8 * kTStride];
+    float gb[64 + 64 + 8];   // bias gradients of the block (layer 3 padded to 8 columns)
+    float loss;
+};
+
+// scatter a C fragment's values (rows g, g+8 of the warp's tile, columns
+// 8 nt + 2t, +1) into a transposed bf16 operand [col][row]
+__device__ __forceinline__ void store_ct(__nv_bfloat16* T, int rbase, int nt, const float (&c)[4],
+                                         int lane) {
+    const int g = lane >> 2, t = lane & 3;
+    const int col = 8 * nt + 2 * t;
+    T[col * kTStride + rbase + g] = __float2bfloat16_rn(c[0]);
+    T[(col + 1) * kTStride + rbase + g] = __float2bfloat16_rn(c[1]);
+    T[col * kTStride + rbase + g + 8] = __float2bfloat16_rn(c[2]);
+    T[(col + 1) * kTStride + rbase + g + 8] = __float2bfloat16_rn(c[3]);
+}
+
+// scatter an A fragment (already bf16) into a transposed operand
+__device__ __forceinline__ void store_at(__nv_bfloat16* T, int rbase, int kt, const uint32_t (&a)[4],
+                                         int lane) {
+    const int g = lane >> 2, t = lane & 3;
+    const int col = 16 * kt + 2 * t;
+    auto lo = [](uint32_t v) { return __ushort_as_bfloat16((unsigned short)(v & 0xffffu)); };
+    auto hi = [](uint32_t v) { return __ushort_as_bfloat16((unsigned short)(v >> 16)); };
+    T[col * kTStride + rbase + g] = lo(a[0]);
+    T[(col + 1) * kTStride + rbase + g] = hi(a[0]);
+    T[col * kTStride + rbase + g + 8] = lo(a[1]);
+    T[(col + 1) * kTStride + rbase + g + 8] = hi(a[1]);
+    T[(col + 8) * kTStride + rbase + g] = lo(a[2]);
+    T[(col + 9) * kTStride + rbase + g] = hi(a[2]);
+    T[(col + 8) * kTStride + rbase + g + 8] = lo(a[3]);
+    T[(col + 9) * kTStride + rbase + g + 8] = hi(a[3]);
+}
+
+// column sums over the warp's 16 rows of a C fragment tile, added to acc[col]
+__device__ __forceinline__ void bias_grad(const float (&c)[4], int nt, float* acc, int lane) {
+    float s0 = c[0] + c[2], s1 = c[1] + c[3];
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if (lane < 4) {
+        atomicAdd(&acc[8 * nt + 2 * lane], s0);
+        atomicAdd(&acc[8 * nt + 2 * lane + 1], s1);
+    }
+}
+
+// acc += A^T-operand (rows m, cols k of T_A) x B-operand (T_B[n][k]) over K = kTrainRows
+__device__ __forceinline__ void wgrad_tile(float (&acc)[4], const __nv_bfloat16* TA, int mt,
+                                           const __nv_bfloat16* TB, int nt, int lane) {
+    const int g = lane >> 2, t = lane & 3;
+    const uint32_t* A = reinterpret_cast<const uint32_t*>(TA);
+    const uint32_t* B = reinterpret_cast<const uint32_t*>(TB);
+    constexpr int W = kTStride / 2;   // 32-bit words per row
+#pragma unroll
+    for (int kt = 0; kt < kTrainRows / 16; ++kt) {
+        const int kw = 8 * kt + t;
+        const uint32_t a0 = A[(16 * mt + g) * W + kw], a1 = A[(16 * mt + g + 8) * W + kw];
+        const uint32_t a2 = A[(16 * mt + g) * W + kw + 4], a3 = A[(16 * mt + g + 8) * W + kw + 4];
+        const uint32_t b0 = B[(8 * nt + g) * W + kw], b1 = B[(8 * nt + g) * W + kw + 4];
+        mma_bf16(acc, a0, a1, a2, a3, b0, b1);
+    }
+}
+
+__device__ __forceinline__ void wgrad_flush(const float (&acc)[4], float* grad, int ncols,
+                                            int mt, int nt, int lane) {
+    const int g = lane >> 2, t = lane & 3;
+    const int m0 = 16 * mt + g, n0 = 8 * nt + 2 * t;
+    if (n0 < ncols) {
+        atomicAdd(&grad[m0 * ncols + n0], acc[0]);
+        atomicAdd(&grad[(m0 + 8) * ncols + n0], acc[2]);
+    }
+    if (n0 + 1 < ncols) {
+        atomicAdd(&grad[m0 * ncols + n0 + 1], acc[1]);
+        atomicAdd(&grad[(m0 + 8) * ncols + n0 + 1], acc[3]);
+    }
+}
+
+__global__ void __launch_bounds__(256, 1)
+    mlp_train_kernel(const uint32_t* __restrict__ X, const float* __restrict__ labels,
+                     int64_t n_samples, const uint32_t* __restrict__ rows, int64_t batch,
+                     const MlpFrags* __restrict__ frags, float* __restrict__ grad,
+                     float* __restrict__ loss_sum) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TrainSmem& s = *reinterpret_cast<TrainSmem*>(smem_raw);
+    load_frags(&s.f, frags);
+    for (int k = threadIdx.x; k < 136; k += blockDim.x) s.gb[k] = 0.f;
+    if (threadIdx.x == 0) s.loss = 0.f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const float inv_b = 1.0f / (float)batch;
+    const int64_t b0 = (int64_t)blockIdx.x * kTrainRows + warp * 16;
+    const int rbase = warp * 16;
+    const int64_t p0 = b0 + g, p1 = b0 + g + 8;      // batch positions of this lane's rows
+    // rows outside the samples are treated as padding
+    int64_t r0 = p0 < batch ? (int64_t)rows[p0] : -1;
+    int64_t r1 = p1 < batch ? (int64_t)rows[p1] : -1;
+    if (r0 >= n_samples) r0 = -1;
+    if (r1 >= n_samples) r1 = -1;
+
+    // forward
+    uint32_t xa[4][4];
+    load_x(X, r0, r1, xa, lane);
+    WarpFwd w;
+    warp_forward(xa, s.f, w, lane);
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+        store_at(s.XT, rbase, kt, xa[kt], lane);
+        store_at(s.H1T, rbase, kt, w.h1[kt], lane);
+        store_at(s.H2T, rbase, kt, w.h2[kt], lane);
+    }
+
+    // loss and dL/do: BCE on o0, squared error of sigmoid(o_c) against the coverage
+    float d3[4] = {0.f, 0.f, 0.f, 0.f};
+    float l = 0.f;
+    if (t < 2) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t r = h ? r1 : r0;
+            if (r < 0) continue;
+            const float sel = labels[2 * r], cov = labels[2 * r + 1];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int col = 2 * t + q;
+                const float o = w.o[2 * h + q];
+                const float p = sigmoidf(o);
+                if (col == 0) {
+                    l += fmaxf(o, 0.f) - sel * o + log1pf(expf(-fabsf(o)));
+                    d3[2 * h + q] = (p - sel) * inv_b;
+                } else {
+                    l += (p - cov) * (p - cov);
+                    d3[2 * h + q] = 2.0f * (p - cov) * p * (1.0f - p) * inv_b;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if (lane == 0) atomicAdd(&s.loss, l);
+    bias_grad(d3, 0, s.gb + 128, lane);   // columns 0..7 (4..7 are zero)
+    store_ct(s.D3T, rbase, 0, d3, lane);
+
+    // dh2 = dz3 W3^T, dz2 = dh2 gelu'(z2)
+    float dz2[8][4];
+    {
+        const uint32_t a0 = pack_bf16(d3[0], d3[1]), a1 = pack_bf16(d3[2], d3[3]);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            dz2[nt][0] = dz2[nt][1] = dz2[nt][2] = dz2[nt][3] = 0.f;
+            const uint2 b = *reinterpret_cast<const uint2*>(s.f.G3 + 2 * (nt * 32 + lane));
+            mma_bf16(dz2[nt], a0, a1, 0u, 0u, b.x, b.y);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) dz2[nt][e] *= gelu_grad(w.z2[nt][e]);
+            bias_grad(dz2[nt], nt, s.gb + 64, lane);
+            store_ct(s.D2T, rbase, nt, dz2[nt], lane);
+        }
+    }
+    // dh1 = dz2 W2^T, dz1 = dh1 gelu'(z1)
+    {
+        uint32_t a[4][4];
+        c_to_a(dz2, a, [](float v) { return v; });
+        float dz1[8][4];
+        layer_mma(dz1, a, s.f.G2, nullptr, lane);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) dz1[nt][e] *= gelu_grad(w.z1[nt][e]);
+            bias_grad(dz1[nt], nt, s.gb, lane);
+            store_ct(s.D1T, rbase, nt, dz1[nt], lane);
+        }
+    }
+    __syncthreads();
+
+    // weight gradients over the block's 128 rows: dW = A^T dZ; warp w owns
+    // m-tile w / 2 and n-tiles 4 (w % 2) .. +3 of dW1 and dW2, and m-tile w
+    // of dW3 (warps 0..3)
+    {
+        const int mt = warp >> 1, nt0 = 4 * (warp & 1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            wgrad_tile(acc, s.XT, mt, s.D1T, nt0 + q, lane);
+            wgrad_flush(acc, grad + kOffW1, 64, mt, nt0 + q, lane);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            wgrad_tile(acc, s.H1T, mt, s.D2T, nt0 + q, lane);
+            wgrad_flush(acc, grad + kOffW2, 64, mt, nt0 + q, lane);
+        }
+        if (warp < 4) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            wgrad_tile(acc, s.H2T, warp, s.D3T, 0, lane);
+            wgrad_flush(acc, grad + kOffW3, 4, warp, 0, lane);
+        }
+    }
+    for (int k = threadIdx.x; k < 132; k += blockDim.x) {
+        const int off = k < 64 ? kOffB1 + k : k < 128 ? kOffB2 + (k - 64) : kOffB3 + (k - 128);
+        atomicAdd(&grad[off], s.gb[k]);
+    }
+    if (threadIdx.x == 0) atomicAdd(loss_sum, s.loss);
+}
+
+// Adam on the parameters (Kingma and Ba, 2015), gradient cleared after use
+__global__ void __launch_bounds__(256) mlp_adam_kernel(float* __restrict__ p, float* __restrict__ m,
+                                                       float* __restrict__ v,
+                                                       float* __restrict__ grad, float lr,
+                                                       float beta1, float beta2, float eps,
+                                                       float inv_bc1, float inv_bc2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kMlpParams) return;
+    const float gi = grad[i];
+    const float mm = beta1 * m[i] + (1.0f - beta1) * gi;
+    const float vv = beta2 * v[i] + (1.0f - beta2) * gi * gi;
+    m[i] = mm;
+    v[i] = vv;
+    p[i] -= lr * (mm * inv_bc1) / (sqrtf(vv * inv_bc2) + eps);
+    grad[i] = 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// features and labels
+
+// Projected centre and view depth of Gaussian i in the selection view;
+// false if t_z <= z_near (outside the learned domain).
+__device__ __forceinline__ bool sel_view(const DevCamera& cam, const float* xyz, int n, int i,
+                                         float& u, float& v, float& tz) {
+    float tx, ty;
+    view_point(cam, xyz[i], xyz[n + i], xyz[2 * n + i], tx, ty, tz);
+    if (!(tz > cam.z_near)) return false;
+    u = __fmaf_rn(cam.fx, __fdiv_rn(tx, tz), cam.cx);
+    v = __fmaf_rn(cam.fy, __fdiv_rn(ty, tz), cam.cy);
+    return true;
+}
+
+// The dilated 2D covariance (a, b, c) of Gaussian i in the selection view
+// (Eq. 1 with the EWA projection, the render's formula).
+__device__ __forceinline__ void sel_cov2d(const DevCamera& cam, const float* xyz, const float* lsc,
+                                          const float* quat, int n, int i, float& a, float& b,
+                                          float& c) {
+    float tx, ty, tz;
+    view_point(cam, xyz[i], xyz[n + i], xyz[2 * n + i], tx, ty, tz);
+    const float qw = quat[i], qx = quat[n + i], qy = quat[2 * n + i], qz = quat[3 * n + i];
+    const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    const float w = qw * qn, x = qx * qn, y = qy * qn, z = qz * qn;
+    const float R[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
+                        2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
+                        2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
+    const float sc[3] = {expf(lsc[i]), expf(lsc[n + i]), expf(lsc[2 * n + i])};
+    const float iz = 1.0f / tz;
+    const float rx = fminf(fmaxf(tx * iz, -cam.limx), cam.limx);
+    const float ry = fminf(fmaxf(ty * iz, -cam.limy), cam.limy);
+    const float j00 = cam.fx * iz, j02 = -cam.fx * rx * iz;
+    const float j11 = cam.fy * iz, j12 = -cam.fy * ry * iz;
+    float T0[3], T1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        T0[k] = j00 * cam.W[k] + j02 * cam.W[6 + k];
+        T1[k] = j11 * cam.W[3 + k] + j12 * cam.W[6 + k];
+    }
+    a = 0.3f;
+    b = 0.f;
+    c = 0.3f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float A0 = (T0[0] * R[k] + T0[1] * R[3 + k] + T0[2] * R[6 + k]) * sc[k];
+        const float A1 = (T1[0] * R[k] + T1[1] * R[3 + k] + T1[2] * R[6 + k]) * sc[k];
+        a += A0 * A0;
+        b += A0 * A1;
+        c += A1 * A1;
+    }
+}
+
+// polygon frame: (q / rho, rho) with q = (u, v) - centroid
+__device__ __forceinline__ void radial(const DevRegion& r, const MlpRegionFrame& fr, float u,
+                                       float v, float& un, float& vn, float& rho) {
+    const float qx = u - fr.cx, qy = v - fr.cy;
+    float lam = INFINITY;
+    for (int i = 0, j = r.n - 1; i < r.n; j = i++) {
+        const float ax = r.xy[2 * j] - fr.cx, ay = r.xy[2 * j + 1] - fr.cy;
+        const float ex = r.xy[2 * i] - r.xy[2 * j], ey = r.xy[2 * i + 1] - r.xy[2 * j + 1];
+        const float den = qx * ey - qy * ex;
+        if (den == 0.f) continue;
+        const float l = (ax * ey - ay * ex) / den;
+        const float sp = (ax * qy - ay * qx) / den;
+        if (l > 0.f && sp >= 0.f && sp <= 1.f && l < lam) lam = l;
+    }
+    const float qn = sqrtf(qx * qx + qy * qy);
+    rho = (lam < INFINITY && qn > 0.f) ? lam * qn : fr.mean_r;
+    un = qx / rho;
+    vn = qy / rho;
+}
+
+// one thread per Gaussian: the 64 features (bf16); valid = t_z > z_near of
+// the selection view
+__global__ void __launch_bounds__(256)
+    mlp_features_kernel(int n, const float* __restrict__ xyz, const float* __restrict__ lsc,
+                        const float* __restrict__ quat, const float* __restrict__ opl,
+                        const float* __restrict__ sh, int sh_dtype, DevCamera cam, DevRegion reg,
+                        MlpRegionFrame fr, uint32_t* __restrict__ X, uint8_t* __restrict__ valid) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float u = 0.f, v = 0.f, tz = 0.f;
+    const bool ok = sel_view(cam, xyz, n, i, u, v, tz);
+    float f[64];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) f[k] = 0.f;
+    if (ok) {
+        float un, vn, rho;
+        radial(reg, fr, u, v, un, vn, rho);
+        float a, b, c;
+        sel_cov2d(cam, xyz, lsc, quat, n, i, a, b, c);
+        // unit radial direction (the +x axis at the centroid itself)
+        const float qx = u - fr.cx, qy = v - fr.cy;
+        const float qn = sqrtf(qx * qx + qy * qy);
+        const float ux = qn > 0.f ? qx / qn : 1.f, uy = qn > 0.f ? qy / qn : 0.f;
+        const float mid = 0.5f * (a + c);
+        const float rad = sqrtf(0.25f * (a - c) * (a - c) + b * b);
+        const float c2p = rad > 0.f ? 0.5f * (a - c) / rad : 1.f;
+        const float s2p = rad > 0.f ? b / rad : 0.f;
+        const float c2q = ux * ux - uy * uy, s2q = 2.f * ux * uy;
+        const float sr = sqrtf(a * ux * ux + 2.f * b * ux * uy + c * uy * uy);
+        const float lr = logf(rho);
+        f[0] = un;
+        f[1] = vn;
+        f[2] = logf(tz * rho / cam.fx);
+        f[3] = 0.5f * logf(mid + rad) - lr;
+        f[4] = 0.5f * logf(mid - rad) - lr;
+        f[5] = logf(sr) - lr;
+        f[6] = c2p * c2q + s2p * s2q;
+        f[7] = s2p * c2q - c2p * s2q;
+        f[8] = fminf(fmaxf((rho - qn) / sr, -8.f), 8.f);
+    }
+    f[9] = (lsc[i] + lsc[n + i] + lsc[2 * n + i]) * (1.0f / 3.0f);
+    f[10] = opl[i];
+#pragma unroll
+    for (int k = 0; k < 48; ++k) {
+        const size_t o = (size_t)k * n + i;
+        f[11 + k] = sh_dtype == RECOGS_F32   ? sh[o]
+                    : sh_dtype == RECOGS_F16 ? __half2float(reinterpret_cast<const __half*>(sh)[o])
+                                             : __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(sh)[o]);
+    }
+#pragma unroll
+    for (int k = 59; k < 64; ++k) f[k] = 0.f;
+    uint4* row = reinterpret_cast<uint4*>(X + (size_t)i * 32);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        row[q] = make_uint4(pack_bf16(f[8 * q + 0], f[8 * q + 1]), pack_bf16(f[8 * q + 2], f[8 * q + 3]),
+                            pack_bf16(f[8 * q + 4], f[8 * q + 5]), pack_bf16(f[8 * q + 6], f[8 * q + 7]));
+    if (valid) valid[i] = ok ? 1 : 0;
+}
+
+// labels[i] = (plain selection bit, tint weight): cover[i] holds the sums of
+// (alpha_i T_i)^2 over the pixels inside the region and over all pixels of
+// the selection view's render; a Gaussian that reaches no pixel takes its
+// plain bit as its weight
+__global__ void __launch_bounds__(256) mlp_label_kernel(int n, const float* __restrict__ xyz,
+                                                        DevCamera cam, DevRegion reg,
+                                                        const float* __restrict__ cover,
+                                                        float* __restrict__ labels) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool sel = select_centre(cam, reg, xyz[i], xyz[n + i], xyz[2 * n + i], nullptr);
+    const float in = cover[3 * (size_t)i], all = cover[3 * (size_t)i + 1];
+    labels[2 * (size_t)i] = sel ? 1.f : 0.f;
+    labels[2 * (size_t)i + 1] = all > 0.f ? fminf(1.f, in / all) : (sel ? 1.f : 0.f);
+}
+
+// Decisions of the learned path: p = sigmoid(o0); outside the learned
+// domain or where |p - 1/2| < delta the plain test decides, with its bit as
+// the weight; elsewhere the bit is p > 1/2 and the per-channel weights are
+// sigmoid(o1..3).
+__global__ void __launch_bounds__(256)
+    mlp_decide_kernel(int n, const float* __restrict__ xyz, DevCamera cam, DevRegion reg,
+                      const float* __restrict__ out, float delta, uint32_t* __restrict__ mask,
+                      float* __restrict__ weights, unsigned long long* __restrict__ fallbacks) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool sel = false, fb = false;
+    if (i < n) {
+        float u, v, tz;
+        const bool ok = sel_view(cam, xyz, n, i, u, v, tz);
+        const float4 o = reinterpret_cast<const float4*>(out)[i];
+        const float p = sigmoidf(o.x);
+        fb = ok && fabsf(p - 0.5f) < delta;
+        float w0, w1, w2;
+        if (!ok || fb) {
+            sel = select_centre(cam, reg, xyz[i], xyz[n + i], xyz[2 * n + i], nullptr);
+            w0 = w1 = w2 = sel ? 1.f : 0.f;
+        } else {
+            sel = p > 0.5f;
+            w0 = sigmoidf(o.y);
+            w1 = sigmoidf(o.z);
+            w2 = sigmoidf(o.w);
+        }
+        weights[3 * (size_t)i + 0] = w0;
+        weights[3 * (size_t)i + 1] = w1;
+        weights[3 * (size_t)i + 2] = w2;
+    }
+    const uint32_t bits = __ballot_sync(0xffffffffu, sel);
+    if ((threadIdx.x & 31) == 0 && i < n) mask[i >> 5] = bits;
+    const uint32_t nfb = __popc(__ballot_sync(0xffffffffu, fb));
+    if ((threadIdx.x & 31) == 0 && nfb) atomicAdd(fallbacks, (unsigned long long)nfb);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+
+int launch_mlp_pack(const float* params, MlpFrags* frags, cudaStream_t st) {
+    mlp_pack_kernel<<<1, 256, 0, st>>>(params, frags);
+    return 1;
+}
+
+size_t mlp_frags_bytes() { return sizeof(MlpFrags); }
+
+int launch_mlp_forward(const uint32_t* X, int64_t n, const MlpFrags* frags, float* out,
+                       cudaStream_t st) {
+    if (n == 0) return 0;
+    const int smem = (int)sizeof(MlpFrags);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    static int grid_max = 0;
+    if (grid_max == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_forward_kernel, 256, smem) !=
+                cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        grid_max = (sms > 0 ? sms : 1) * per_sm;
+    }
+    const int64_t tiles = (n + 127) / 128;
+    const int g = (int)(tiles < grid_max ? tiles : grid_max);
+    mlp_forward_kernel<<<g, 256, smem, st>>>(X, n, frags, out);
+    return 1;
+}
+
+int launch_mlp_train(const uint32_t* X, const float* labels, int64_t n_samples,
+                     const uint32_t* rows, int64_t batch, const MlpFrags* frags, float* grad,
+                     float* loss_sum, cudaStream_t st) {
+    if (batch == 0) return 0;
+    const int smem = (int)sizeof(TrainSmem);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    const int64_t g = (batch + kTrainRows - 1) / kTrainRows;
+    mlp_train_kernel<<<(unsigned)g, 256, smem, st>>>(X, labels, n_samples, rows, batch, frags, grad,
+                                                     loss_sum);
+    return 1;
+}
+
+int launch_mlp_adam(float* p, float* m, float* v, float* grad, float lr, float beta1, float beta2,
+                    float eps, float inv_bc1, float inv_bc2, cudaStream_t st) {
+    mlp_adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, st>>>(p, m, v, grad, lr, beta1, beta2,
+                                                              eps, inv_bc1, inv_bc2);
+    return 1;
+}
+
+int launch_mlp_features(const recogs_scene& s, const DevCamera& cam, const DevRegion& reg,
+                        const MlpRegionFrame& fr, uint32_t* X, uint8_t* valid, cudaStream_t st) {
+    const int n = (int)s.n;
+    if (n == 0) return 0;
+    mlp_features_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, s.xyz, s.log_scale, s.quat,
+                                                         s.opacity_logit, (const float*)s.sh,
+                                                         s.sh_dtype, cam, reg, fr, X, valid);
+    return 1;
+}
+
+int launch_mlp_labels(const recogs_scene& s, const DevCamera& cam, const DevRegion& reg,
+                      const float* cover, float* labels, cudaStream_t st) {
+    const int n = (int)s.n;
+    if (n == 0) return 0;
+    mlp_label_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, s.xyz, cam, reg, cover, labels);
+    return 1;
+}
+
+int launch_mlp_decide(const recogs_scene& s, const DevCamera& cam, const DevRegion& reg,
+                      const float* out, float delta, uint32_t* mask, float* weights,
+                      unsigned long long* fallbacks, cudaStream_t st) {
+    const int n = (int)s.n;
+    if (n == 0) return 0;
+    mlp_decide_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, s.xyz, cam, reg, out, delta, mask,
+                                                       weights, fallbacks);
+    return 1;
+}
+
+}  // namespace recogs

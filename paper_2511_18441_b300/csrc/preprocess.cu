@@ -109,6 +109,62 @@ int launch_recolor(recogs_scene& s, const uint32_t* mask, const float M[9], cons
     return 1;
 }
 
+// weighted recolour: C <- C + w (M C - C) per coefficient triple and channel
+template <typename T>
+__global__ void __launch_bounds__(256) recolor_weighted_kernel(int n, T* __restrict__ sh,
+                                                                const float* __restrict__ weights,
+                                                                RecolorParams p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float w0 = weights[3 * (size_t)i], w1 = weights[3 * (size_t)i + 1],
+                w2 = weights[3 * (size_t)i + 2];
+    if (w0 == 0.f && w1 == 0.f && w2 == 0.f) return;
+    float C[48];
+#pragma unroll
+    for (int k = 0; k < 48; ++k) C[k] = to_f32(sh[(size_t)k * n + i]);
+    if (w0 == 1.f && w1 == 1.f && w2 == 1.f) {
+        recolor_coeffs<T>(p.M, p.dc_fix, C);   // the plain recolour, bit for bit
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            float r = C[3 * k], g = C[3 * k + 1], b = C[3 * k + 2];
+            recolor_triple(p.M, r, g, b);
+            if (k == 0) {
+                r = __fadd_rn(r, p.dc_fix[0]);
+                g = __fadd_rn(g, p.dc_fix[1]);
+                b = __fadd_rn(b, p.dc_fix[2]);
+            }
+            C[3 * k] = fmaf(w0, r - C[3 * k], C[3 * k]);
+            C[3 * k + 1] = fmaf(w1, g - C[3 * k + 1], C[3 * k + 1]);
+            C[3 * k + 2] = fmaf(w2, b - C[3 * k + 2], C[3 * k + 2]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 48; ++k) sh[(size_t)k * n + i] = from_f32<T>(C[k]);
+}
+
+int launch_recolor_weighted(recogs_scene& s, const float* weights, const float M[9],
+                            const float dc_fix[3], cudaStream_t st) {
+    const int n = (int)s.n;
+    if (n == 0) return 0;
+    RecolorParams p;
+    for (int k = 0; k < 9; ++k) p.M[k] = M[k];
+    for (int k = 0; k < 3; ++k) p.dc_fix[k] = dc_fix[k];
+    const int g = (n + 255) / 256;
+    switch (s.sh_dtype) {
+        case RECOGS_F32:
+            recolor_weighted_kernel<float><<<g, 256, 0, st>>>(n, (float*)s.sh, weights, p);
+            break;
+        case RECOGS_F16:
+            recolor_weighted_kernel<__half><<<g, 256, 0, st>>>(n, (__half*)s.sh, weights, p);
+            break;
+        default:
+            recolor_weighted_kernel<__nv_bfloat16><<<g, 256, 0, st>>>(n, (__nv_bfloat16*)s.sh,
+                                                                      weights, p);
+    }
+    return 1;
+}
+
 // ---------------------------------------------------------------------------
 // fused select + recolour + preprocess
 

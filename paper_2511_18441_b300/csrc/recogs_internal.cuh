@@ -231,7 +231,9 @@ int launch_tile_sort(const uint2* ranges, const uint32_t* order, const uint32_t*
 // below tau; 0 if none). grad_rgb != NULL: instead of the image, the colour
 // gradient dL/dc of L = mean |image - target| (image holds the forward
 // result), accumulated into grad_rgb [n][3] (zeroed by the caller), and
-// sum |image - target| added to *loss.
+// sum |image - target| added to *loss. cover (with grad_rgb): instead, per
+// Gaussian, the sums of (alpha_i T_i)^2 over the pixels whose centre lies in
+// `region` ([i][0]) and over all pixels ([i][1]).
 struct BlendExtra {
     const uint32_t* zkey = nullptr;
     float tau = 0.5f;
@@ -240,6 +242,8 @@ struct BlendExtra {
     float inv_n = 0.f;
     float* grad_rgb = nullptr;
     double* loss = nullptr;
+    bool cover = false;
+    DevRegion region;
 };
 
 // Adam parameters of the SH refit, with the bias corrections 1 / (1 - b^t).
@@ -251,6 +255,36 @@ struct RefitAdam {
 int launch_sh_refit(int n, const float* xyz, const float cam_pos[3], const float4* rec,
                     const uint32_t* count, const float* grad_rgb, float* sh, float* m, float* v,
                     const RefitAdam& adam, float* grad_sh, cudaStream_t st);
+
+// Learned selection MLP (mlp.cu). Parameters: W1 [64][64], b1, W2 [64][64],
+// b2, W3 [64][4], b3 (fp32, input-major weights).
+constexpr int kMlpParams = 8580;
+struct MlpFrags;                 // fragment-ordered bf16 weights and biases
+struct MlpRegionFrame {          // polygon frame of the features
+    float cx, cy;                // vertex centroid
+    float mean_r;                // mean vertex distance from it (rho where no edge is hit)
+};
+size_t mlp_frags_bytes();
+int launch_mlp_pack(const float* params, MlpFrags* frags, cudaStream_t st);
+int launch_mlp_forward(const uint32_t* X, int64_t n, const MlpFrags* frags, float* out,
+                       cudaStream_t st);
+int launch_mlp_train(const uint32_t* X, const float* labels, int64_t n_samples,
+                     const uint32_t* rows, int64_t batch, const MlpFrags* frags, float* grad,
+                     float* loss_sum, cudaStream_t st);
+int launch_mlp_adam(float* p, float* m, float* v, float* grad, float lr, float beta1, float beta2,
+                    float eps, float inv_bc1, float inv_bc2, cudaStream_t st);
+int launch_mlp_features(const recogs_scene& s, const DevCamera& cam, const DevRegion& reg,
+                        const MlpRegionFrame& fr, uint32_t* X, uint8_t* valid, cudaStream_t st);
+int launch_mlp_labels(const recogs_scene& s, const DevCamera& cam, const DevRegion& reg,
+                      const float* cover, float* labels, cudaStream_t st);
+int launch_mlp_decide(const recogs_scene& s, const DevCamera& cam, const DevRegion& reg,
+                      const float* out, float delta, uint32_t* mask, float* weights,
+                      unsigned long long* fallbacks, cudaStream_t st);
+// Recolour with per-Gaussian, per-channel weights w in [0, 1]:
+// C <- C + w (M C - C) per triple (DC also + w dc_fix); w = 1 is the plain
+// recolour bit for bit, w = 0 leaves the Gaussian untouched (preprocess.cu).
+int launch_recolor_weighted(recogs_scene& s, const float* weights, const float M[9],
+                            const float dc_fix[3], cudaStream_t st);
 
 // batch: Gaussians staged in shared memory per blend step, 128 or 256
 int launch_blend(const uint2* ranges, const uint32_t* order, const uint32_t* ids, const float4* rec,

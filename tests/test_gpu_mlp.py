@@ -1,0 +1,233 @@
+"""The learned selection (features, labels, the bf16 MLP's forward and
+gradient, training, the decisions with the plain fallback, the weighted
+recolour) against the FP64 oracle in oracle/mlp.py, and the test of what the
+trained network gains over the plain selection.
+
+Tolerances: SH and opacity features are the same bf16 roundings of the same
+float32 inputs (exact); the selection-view geometry within two bf16 ulps
+(99.9%: near-isotropic footprints make the orientation ill-conditioned);
+tint-weight labels (sums of (alpha T)^2 over float32 and FP64 renders)
+within 1e-3 for 99% of the Gaussians (the rest reach pixels whose render the
+oracle flags);
+network outputs and gradients are compared on the GPU's own bf16 features,
+so they differ only by the accumulation order and an occasional flipped bf16
+rounding of an activation.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as omlp
+from paper_2511_18441_b300 import scenegen as sg
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2511_18441_b300 import binding, build
+    build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    c = lib.Context(0)
+    yield c
+    c.close()
+
+
+def scene_and_view(n=20_000, seed=7, W=320, H=240, log_scale_shift=0.0):
+    w = sg.paper_scale_workload(n=n, seed=seed, width=W, height=H)
+    if log_scale_shift:
+        w.scene.log_scale[:] += np.float32(log_scale_shift)
+    return w.scene, w.camera
+
+
+def test_features_and_labels_match_the_oracle(lib, ctx):
+    scene, cam = scene_and_view()
+    reg = sg.random_polygons(1, cam.width, cam.height, 11)[0]
+    ds = lib.DeviceScene.from_numpy(scene, "cuda", "f32")
+    F, L, V = ctx.mlp_features(ds, cam, reg)
+    torch.cuda.synchronize()
+    Fg = F.float().cpu().numpy().astype(np.float64)
+    Lg = parity.to_np(L)
+    Vg = parity.to_np(V).astype(bool)
+    Fo, Vo, So, Co = omlp.features_and_labels(scene, cam, reg.xy)
+    np.testing.assert_array_equal(Vg, Vo)
+    Fo16 = omlp.bf16(Fo)
+    np.testing.assert_array_equal(Fg[:, 10:], Fo16[:, 10:])           # opacity, SH, padding
+    # geometry in the selection view: float32 against FP64, then bf16
+    ulp = np.maximum(np.abs(Fo16[:, :10]), 1e-30) * 2.0 ** -7
+    geo = np.abs(Fg[:, :10] - Fo16[:, :10]) <= 2.01 * ulp + 1e-3
+    assert geo[Vo].mean() >= 0.999, np.argwhere(~geo & Vo[:, None])[:5]
+    edit = sg.Edit(reg, np.eye(3, dtype=np.float32), cam)
+    _, near = oracle.select(scene, edit, cam)
+    ok = near == 0
+    np.testing.assert_array_equal(Lg[ok, 0], So[ok].astype(np.float32))
+    close = np.abs(Lg[:, 1] - Co) <= 1e-3
+    assert close.mean() >= 0.99, close.mean()
+    assert 0.02 < Co.mean() < 0.9 and ((Co > 0.05) & (Co < 0.95)).sum() > 50
+
+
+def rand_params(seed):
+    return sg.mlp_init(seed)
+
+
+def test_forward_matches_the_oracle(lib, ctx):
+    scene, cam = scene_and_view(n=5000)
+    reg = sg.random_polygons(1, cam.width, cam.height, 3)[0]
+    ds = lib.DeviceScene.from_numpy(scene, "cuda", "f32")
+    F, L, V = ctx.mlp_features(ds, cam, reg)
+    theta = rand_params(1)
+    net = ctx.mlp(theta)
+    out = parity.to_np(net.forward(F))
+    X = F.float().cpu().numpy().astype(np.float64)
+    ref = omlp.forward(theta.astype(np.float64), X)["o"]
+    err = np.abs(out - ref)
+    tol = 2e-3 * np.maximum(1.0, np.abs(ref))
+    assert (err <= tol).mean() >= 0.999 and err.max() < 5e-2, (err.max(), (err > tol).mean())
+    net.close()
+
+
+def test_gradient_matches_the_oracle(lib, ctx):
+    scene, cam = scene_and_view(n=6000)
+    reg = sg.random_polygons(1, cam.width, cam.height, 5)[0]
+    ds = lib.DeviceScene.from_numpy(scene, "cuda", "f32")
+    F, L, V = ctx.mlp_features(ds, cam, reg)
+    theta = rand_params(2)
+    net = ctx.mlp(theta)
+    rng = np.random.default_rng(0)
+    valid = np.flatnonzero(parity.to_np(V))
+    rows = rng.choice(valid, 1000, replace=True).astype(np.uint32)   # duplicates allowed
+    g, loss = net.grad(F, L, torch.from_numpy(rows).cuda())
+    X = F.float().cpu().numpy().astype(np.float64)[rows]
+    Lh = parity.to_np(L).astype(np.float64)[rows]
+    loss_o, g_o = omlp.loss_grad(theta.astype(np.float64), X, Lh[:, 0], Lh[:, 1])
+    assert loss == pytest.approx(loss_o, rel=1e-4)
+    scale = np.abs(g_o).max()
+    err = np.abs(g - g_o)
+    assert (err <= 1e-3 * scale + 1e-2 * np.abs(g_o)).mean() >= 0.99, err.max() / scale
+    assert err.max() <= 2e-2 * scale
+    # rows outside the samples are empty rows (they only count in the batch size)
+    rows2 = np.concatenate([rows, [10 ** 9]]).astype(np.uint32)
+    g2, loss2 = net.grad(F, L, torch.from_numpy(rows2).cuda())
+    loss2_o, g2_o = omlp.loss_grad(theta.astype(np.float64), X, Lh[:, 0], Lh[:, 1], batch=1001)
+    assert loss2 == pytest.approx(loss2_o, rel=1e-4)
+    err2 = np.abs(g2 - g2_o)
+    assert (err2 <= 1e-3 * scale + 1e-2 * np.abs(g2_o)).mean() >= 0.99
+    assert err2.max() <= 2e-2 * scale
+    # the gradient call leaves the network unchanged
+    np.testing.assert_array_equal(net.params(), theta)
+    net.close()
+
+
+def test_weighted_recolour_special_cases(lib, ctx):
+    """w = 1 reproduces recogs_recolor bit for bit; w = 0 leaves the SH."""
+    scene, cam = scene_and_view(n=3000)
+    M = sg.hue_rotation_matrix(70.0)
+    a = lib.DeviceScene.from_numpy(scene, "cuda", "f32")
+    b = lib.DeviceScene.from_numpy(scene, "cuda", "f32")
+    n = scene.n
+    sel = (np.arange(n) % 3 == 0)
+    words = np.zeros(lib.mask_words(n), np.uint32)
+    for i in np.flatnonzero(sel):
+        words[i >> 5] |= np.uint32(1 << (i & 31))
+    ctx.recolor(a, torch.from_numpy(words.view(np.int32)).cuda(), M)
+    w = torch.from_numpy(np.repeat(sel[:, None].astype(np.float32), 3, 1)).cuda()
+    ctx.recolor_weighted(b, w, M)
+    torch.cuda.synchronize()
+    assert torch.equal(a.sh, b.sh)
+    # partial weights: C + w (M C + fix - C), checked in FP64 on one Gaussian per weight
+    c = lib.DeviceScene.from_numpy(scene, "cuda", "f32")
+    wv = np.zeros((n, 3), np.float32)
+    wv[1] = (0.25, 0.5, 0.75)
+    ctx.recolor_weighted(c, torch.from_numpy(wv).cuda(), M)
+    got = parity.to_np(c.sh)[:, :, 1].astype(np.float64)
+    ref = oracle.recolor(scene.sh[:, :, 1:2], np.ones(1, np.uint8), M)[:, :, 0]
+    C0 = scene.sh[:, :, 1].astype(np.float64)
+    np.testing.assert_allclose(got, C0 + wv[1].astype(np.float64) * (ref - C0), atol=2e-6)
+    np.testing.assert_array_equal(parity.to_np(c.sh)[:, :, 2:], scene.sh[:, :, 2:])
+
+
+def psnr(a, b):
+    mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
+    return 10 * math.log10(1.0 / max(mse, 1e-20))
+
+
+def pixel_target(img, reg, tint):
+    H, W, _ = img.shape
+    py, px = np.mgrid[0:H, 0:W]
+    inside = omlp.point_in_polygon(px.ravel().astype(np.float64), py.ravel().astype(np.float64),
+                                   reg.xy).reshape(H, W)
+    return np.where(inside[..., None], img * np.asarray(tint)[None, None], img)
+
+
+def test_training_and_the_gain_over_the_plain_selection(lib, ctx):
+    """Train on the labels of 32 polygons, evaluate on 8 held-out polygons.
+    The labels' tint weights beat the plain selection's all-or-nothing
+    recolour against the pixel-tinted target of Sec. 3.3 on every polygon;
+    the trained network, which sees only per-Gaussian features (not the
+    occlusion inside the weight), keeps part of that gain on average, its
+    mask disagrees with the plain selection on few Gaussians and only a
+    small fraction falls back."""
+    scene, cam = scene_and_view(n=40_000, seed=9, W=320, H=240, log_scale_shift=1.0)
+    ds = lib.DeviceScene.from_numpy(scene, "cuda", "f32")
+    polys = sg.random_polygons(40, cam.width, cam.height, 21)
+    feats, labs = [], []
+    for reg in polys[:32]:
+        F, L, V = ctx.mlp_features(ds, cam, reg)
+        keep = V.bool()
+        feats.append(F[keep])
+        labs.append(L[keep])
+    F = torch.cat(feats)
+    L = torch.cat(labs)
+    N = F.shape[0]
+    net = ctx.mlp(sg.mlp_init(4))
+    rng = np.random.default_rng(5)
+    losses = []
+    for step in range(6000):
+        rows = torch.from_numpy(rng.integers(0, N, 8192).astype(np.uint32)).cuda()
+        l = net.train_step(F, L, rows, lr=2e-3, want_loss=(step % 500 == 0 or step == 5999))
+        if l is not None:
+            losses.append(l)
+    assert losses[-1] < 0.05 * losses[0], losses
+    tint = (0.3, 0.9, 1.4)
+    M = sg.tint_matrix(tint)
+    base = parity.to_np(ctx.render(ds, cam))
+    rows = []
+    for reg in polys[32:]:
+        target = pixel_target(base, reg, tint)
+        # plain selection and recolour
+        p = lib.DeviceScene.from_numpy(scene, "cuda", "f32")
+        mask = torch.zeros((lib.mask_words(p.n),), dtype=torch.int32, device="cuda")
+        ctx.select(p, cam, reg, mask)
+        ctx.recolor(p, mask, M)
+        plain_img = parity.to_np(ctx.render(p, cam))
+        # the labels' weights
+        _, Lr, _ = ctx.mlp_features(ds, cam, reg)
+        r = lib.DeviceScene.from_numpy(scene, "cuda", "f32")
+        ctx.recolor_weighted(r, Lr[:, 1:2].repeat(1, 3).contiguous(), M)
+        label_img = parity.to_np(ctx.render(r, cam))
+        # learned selection and weighted recolour
+        q = lib.DeviceScene.from_numpy(scene, "cuda", "f32")
+        m2, wts, nfb = net.select(q, cam, reg, delta=0.1)
+        ctx.recolor_weighted(q, wts, M)
+        mlp_img = parity.to_np(ctx.render(q, cam))
+        b1 = np.unpackbits(parity.to_np(mask).view(np.uint8), bitorder="little")[:p.n]
+        b2 = np.unpackbits(parity.to_np(m2).view(np.uint8), bitorder="little")[:p.n]
+        rows.append((psnr(plain_img, target), psnr(label_img, target), psnr(mlp_img, target),
+                     float((b1 != b2).mean()), nfb / p.n, psnr(mlp_img, plain_img)))
+    R = np.array(rows)
+    print("\nPSNR vs pixel-tinted target: plain, label weights, learned; mask disagreement; "
+          "fallback; learned vs plain PSNR\n" +
+          "\n".join(" ".join(f"{x:8.4f}" for x in r) for r in R))
+    assert (R[:, 1] > R[:, 0]).all()
+    gain = R[:, 2] - R[:, 0]
+    assert gain.mean() > 0.05 and gain.min() > -0.4, gain
+    assert R[:, 3].max() < 0.01 and R[:, 4].max() < 0.05
+    net.close()

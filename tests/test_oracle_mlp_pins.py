@@ -1,7 +1,7 @@
 """Pins of the learned-selection oracle (oracle/mlp.py) against facts fixed
 outside it: finite differences of its own loss (FP64 path), torch's bfloat16
-conversion, closed forms of GELU, the radial frame and the Gauss-Hermite
-rule, and the plain selection. ReCoGS (arXiv 2511.18441) names the leak of
+conversion, closed forms of GELU, the radial frame and the rendered coverage
+of a single Gaussian, and the plain selection. ReCoGS (arXiv 2511.18441) names the leak of
 its selection as a limitation (Sec. 6); the learned variant is the
 the benchmark spec's extension."""
 import math
@@ -83,31 +83,6 @@ def test_radial_frame_maps_the_polygon_onto_the_unit_disc():
     assert b[0] == pytest.approx(a[0] / 2.0, rel=1e-12)
 
 
-def test_gauss_hermite_rule_moments():
-    x, w = mlp.hermite_rule()
-    assert w.sum() == pytest.approx(1.0, rel=1e-14)
-    np.testing.assert_allclose(np.sort(x), -np.sort(x)[::-1], atol=1e-15)
-    # a 5-point rule integrates polynomials up to degree 9 exactly (N(0,1) moments)
-    for k, m in ((2, 1.0), (4, 3.0), (6, 15.0), (8, 105.0)):
-        assert (w * x ** k).sum() == pytest.approx(m, rel=1e-12)
-
-
-def test_quadrature_points_reproduce_mean_and_covariance():
-    """The rule integrates quadratics exactly: the weighted points have the
-    Gaussian's mean and covariance (this fixes the Cholesky factor)."""
-    rng = np.random.default_rng(4)
-    for _ in range(20):
-        A = rng.normal(size=(2, 2))
-        S = A @ A.T + 0.3 * np.eye(2)
-        mu = rng.normal(0, 50, 2)
-        pu, pv, w = mlp.quadrature_points(mu[0], mu[1], S[0, 0], S[0, 1], S[1, 1])
-        m = np.array([(w * pu).sum(), (w * pv).sum()])
-        np.testing.assert_allclose(m, mu, rtol=1e-12, atol=1e-9)
-        d = np.stack([pu - mu[0], pv - mu[1]])
-        C = (w * d) @ d.T
-        np.testing.assert_allclose(C, S, rtol=1e-10, atol=1e-10)
-
-
 def small_scene(n=300, seed=3):
     w = sg.tiny_workload(n=n, seed=seed, width=64, height=64)
     return w.scene, w.camera
@@ -118,54 +93,98 @@ def test_features_layout_and_plain_label():
     xy = sg.polygon_region(64, 64, 12, 0.2, 5).xy
     F, valid, sel, cov = mlp.features_and_labels(scene, cam, xy)
     n = scene.n
-    np.testing.assert_array_equal(F[:, 3:6], scene.log_scale.T.astype(np.float64))
-    np.testing.assert_allclose((F[:, 6:10] ** 2).sum(1), 1.0, rtol=1e-12)
+    np.testing.assert_allclose(F[:, 9], scene.log_scale.astype(np.float64).mean(0), rtol=1e-12)
     np.testing.assert_array_equal(F[:, 10], scene.opacity_logit.astype(np.float64))
+    np.testing.assert_allclose(F[:, 6] ** 2 + F[:, 7] ** 2, 1.0, rtol=1e-9)
+    assert (F[:, 3] >= F[:, 4]).all() and (F[:, 5] <= F[:, 3] + 1e-12).all()
+    assert (F[:, 5] >= F[:, 4] - 1e-12).all()
     np.testing.assert_array_equal(F[:, 11:59], scene.sh.reshape(48, n).T.astype(np.float64))
     assert not F[:, 59:].any()
     edit = sg.Edit(sg.Region("polygon", xy), np.eye(3, dtype=np.float32), cam)
     ref, _ = oracle.select(scene, edit, cam)
     np.testing.assert_array_equal(sel, ref)
     assert valid.all() and 0.05 < sel.mean() < 0.95
-    assert ((cov >= 0) & (cov <= 1 + 1e-12)).all()
+    assert ((cov >= 0) & (cov <= 1)).all()
     # centre inside the polygon frame <=> plain selection, for a star-shaped polygon
     r = np.hypot(F[:, 0], F[:, 1])
     far = np.abs(r - 1) > 1e-9
     np.testing.assert_array_equal((r < 1)[far], sel.astype(bool)[far])
 
 
-def test_coverage_of_tiny_and_straddling_gaussians():
-    """Far inside -> 1, far outside -> 0; a splat cut by a straight edge at
-    offset d (in units of its standard deviation along the normal) covers
-    the weight of the 1D rule's nodes on the inside of the edge."""
-    cam = sg.axis_camera(101, 101, 60.0, 3.0)
-    s = 0.004
-    mus = [(0, 0, 0), (2.0, 2.0, 0)]
-    sc = sg.Scene(np.array(mus, np.float32).T.copy(), np.full((3, 2), math.log(s), np.float32),
-                  np.tile(np.array([[1.0], [0], [0], [0]], np.float32), 2),
-                  np.zeros(2, np.float32), np.zeros((16, 3, 2), np.float32))
-    box = np.array([[10, 10], [90, 10], [90, 90], [10, 90]], np.float64)
-    F, valid, sel, cov = mlp.features_and_labels(sc, cam, box)
-    assert cov[0] == pytest.approx(1.0, rel=1e-12) and cov[1] == 0.0
-    # a vertical edge at u = cx + d sigma: inside where u + sigma x < cx + d sigma
-    sp = oracle.preprocess(sc, cam)
-    sigma = math.sqrt(sp["cov2d"][0])
-    x, w = mlp.hermite_rule()
-    for d in (-1.7, -0.3, 0.4, 1.1):
-        edge = cam.cx + d * sigma
+def test_selection_view_shape_features_closed_form():
+    """An isotropic splat at (x0, 0, 0) in front of the axis camera and a
+    square of half-width h centred on the image: along +x, rho = h,
+    Sigma'_xx = (f s / z)^2 (1 + (x0 / z)^2) + 0.3 (the Jacobian's x row),
+    Sigma'_yy = (f s / z)^2 + 0.3, no cross term; the major axis lies along
+    the radial direction."""
+    cam = sg.axis_camera(201, 201, 60.0, 3.0)
+    s, x0, h = 0.15, 0.4, 60.0
+    sc = sg.Scene(np.array([[x0], [0.0], [0.0]], np.float32), np.full((3, 1), math.log(s), np.float32),
+                  np.array([[1.0], [0], [0], [0]], np.float32), np.zeros(1, np.float32),
+                  np.zeros((16, 3, 1), np.float32))
+    c = np.array([cam.cx, cam.cy])
+    sq = c + np.array([[-h, -h], [h, -h], [h, h], [-h, h]])
+    F = mlp.features_and_labels(sc, cam, sq)[0][0]
+    z = 3.0
+    s32 = math.exp(float(np.float32(math.log(s))))
+    x32 = float(np.float32(x0))
+    fx = float(np.float32(cam.fx))
+    sxx = (fx * s32 / z) ** 2 * (1 + (x32 / z) ** 2) + 0.3
+    syy = (float(np.float32(cam.fy)) * s32 / z) ** 2 + 0.3
+    u = fx * x32 / z + float(np.float32(cam.cx))
+    d = u - c[0]
+    assert F[0] == pytest.approx(d / h, rel=1e-9) and F[1] == pytest.approx(0.0, abs=1e-12)
+    assert F[3] == pytest.approx(0.5 * math.log(sxx) - math.log(h), rel=1e-9)
+    assert F[4] == pytest.approx(0.5 * math.log(syy) - math.log(h), rel=1e-9)
+    assert F[5] == pytest.approx(F[3], rel=1e-12)
+    assert F[6] == pytest.approx(1.0, abs=1e-12) and F[7] == pytest.approx(0.0, abs=1e-12)
+    assert F[8] == pytest.approx((h - d) / math.sqrt(sxx), rel=1e-8)
+    assert F[2] == pytest.approx(math.log(z * h / fx), rel=1e-9)
+    # far from the boundary the distance feature saturates at 8
+    sq_big = c + np.array([[-h, -h], [h, -h], [h, h], [-h, h]]) * 3
+    assert mlp.features_and_labels(sc, cam, sq_big)[0][0, 8] == 8.0
+
+
+def test_rendered_coverage_of_a_single_gaussian_in_closed_form():
+    """One isotropic Gaussian on the axis: T = 1 at every pixel, so the
+    tint-weight label of a half-plane region is the sum of alpha^2 over the
+    pixels inside it over the sum over all pixels, alpha = min(0.99,
+    sigma exp(-d^2 / (2 v))) with v = (f s / z)^2 + 0.3 (the single-Gaussian
+    pin of the render), counting only alpha >= 1/255."""
+    W = H = 41
+    cam = sg.axis_camera(W, H, 60.0, 3.0)
+    s, logit = 0.03, 1.2
+    sc = sg.Scene(np.zeros((3, 1), np.float32), np.full((3, 1), math.log(s), np.float32),
+                  np.array([[1.0], [0], [0], [0]], np.float32), np.array([logit], np.float32),
+                  np.zeros((16, 3, 1), np.float32))
+    s32 = math.exp(float(np.float32(math.log(s))))
+    v = (cam.fy * s32 / 3.0) ** 2 + 0.3
+    sigma = 1 / (1 + math.exp(-float(np.float32(logit))))
+    py, px = np.mgrid[0:H, 0:W]
+    a = np.minimum(0.99, sigma * np.exp(-((px - cam.cx) ** 2 + (py - cam.cy) ** 2) / (2 * v)))
+    a = np.where(a >= 1 / 255, a, 0.0) ** 2
+    for edge in (cam.cx - 2.3, cam.cx + 0.5, cam.cx + 4.0):
         half = np.array([[edge - 500, -500], [edge, -500], [edge, 600], [edge - 500, 600]])
-        c = mlp.features_and_labels(sc, cam, half)[3][0]
-        assert c == pytest.approx(w[x < d].sum(), abs=1e-12)
+        c = mlp.rendered_coverage(sc, cam, half, np.zeros(1))[0]
+        assert c == pytest.approx(a[px < edge].sum() / a.sum(), rel=1e-12)
+    # a region the Gaussian never reaches, and one containing it all
+    far = np.array([[1000, 1000], [1100, 1000], [1100, 1100], [1000, 1100]], np.float64)
+    assert mlp.rendered_coverage(sc, cam, far, np.zeros(1))[0] == 0.0
+    box = np.array([[-10, -10], [60, -10], [60, 60], [-10, 60]], np.float64)
+    assert mlp.rendered_coverage(sc, cam, box, np.zeros(1))[0] == pytest.approx(1.0, rel=1e-14)
+    # a Gaussian that reaches no pixel takes its plain bit
+    off = np.array([[0.0], [0.0], [-5.0]], np.float32)   # behind the camera
+    sc2 = sg.Scene(off, sc.log_scale, sc.quat, sc.opacity_logit, sc.sh)
+    assert mlp.rendered_coverage(sc2, cam, box, np.ones(1))[0] == 1.0
 
 
 def test_decisions_truth_table():
     o = np.array([[4.0, 0, 0, 0], [-4.0, 0, 0, 0], [0.1, 2, 2, 2], [4.0, 0, 0, 0]])
     plain = np.array([0, 1, 1, 1], np.uint8)
-    exact = np.array([0.2, 0.3, 0.4, 0.5])
     valid = np.array([True, True, True, False])
-    sel, w, fb = mlp.decisions(o, plain, exact, valid, delta=0.2)
+    sel, w, fb = mlp.decisions(o, plain, valid, delta=0.2)
     np.testing.assert_array_equal(fb, [False, False, True, False])
     np.testing.assert_array_equal(sel, [1, 0, 1, 1])
     np.testing.assert_allclose(w[0], 0.5)
-    np.testing.assert_allclose(w[2], 0.4)
+    np.testing.assert_allclose(w[2], 1.0)
     np.testing.assert_allclose(w[3], 1.0)
