@@ -585,6 +585,160 @@ def run_batch(args, rank, world, local):
     ctx.close()
 
 
+# ---------------------------------------------------------------------------
+# the learned selection workload
+
+MLP_SPLATS = 6_000_000
+MLP_TRAIN_POLYGONS = 32
+MLP_EVAL_POLYGONS = 8
+
+
+def run_mlp(args, rank, world, local):
+    """6M Gaussians at 1920x1080: labels of 32 random polygons train the
+    59-64-64-4 selection MLP on the GPU; 8 held-out polygons compare the
+    learned selection (features + network + fallback decisions) with the
+    plain selection: mask disagreement, PSNR of the learned render against
+    the plain one and against the pixel-tinted target, fallback rate, and
+    the timings (learned selection, plain selection, labels, the network's
+    forward pass with its tensor-core rate)."""
+    import torch
+    from paper_2511_18441_b300 import binding, build
+    from paper_2511_18441_b300 import scenegen as sg
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the library has no CPU path)")
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.gaussians or MLP_SPLATS
+    w = sg.paper_scale_workload(n=n, seed=SEED, width=WIDTH, height=HEIGHT)
+    cam = w.camera
+    ds = binding.DeviceScene.from_numpy(w.scene, dev, "f32")
+    ctx = binding.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    polys = sg.random_polygons(MLP_TRAIN_POLYGONS + MLP_EVAL_POLYGONS, WIDTH, HEIGHT, 17)
+    rng = np.random.default_rng(SEED)
+
+    def event_ms(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    # training set: features and labels of the training polygons, 1M
+    # random Gaussians of each (inside the learned domain)
+    feats, labs = [], []
+    per_poly = min(1_000_000, n)
+    for reg in polys[:MLP_TRAIN_POLYGONS]:
+        F, L, V = ctx.mlp_features(ds, cam, reg, stream=stream)
+        idx = torch.nonzero(V.bool()).squeeze(1)
+        pick = idx[torch.from_numpy(rng.integers(0, idx.numel(), per_poly)).to(dev)]
+        feats.append(F[pick])
+        labs.append(L[pick])
+        del F, L, V
+    F = torch.cat(feats)
+    L = torch.cat(labs)
+    del feats, labs
+    N = F.shape[0]
+    net = ctx.mlp(sg.mlp_init(SEED))
+    steps, B = args.mlp_steps, 16384
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    first = last = None
+    for k in range(steps):
+        rows = torch.from_numpy(rng.integers(0, N, B).astype(np.uint32)).to(dev)
+        l = net.train_step(F, L, rows, lr=2e-3, want_loss=(k == 0 or k == steps - 1),
+                           stream=stream)
+        if k == 0:
+            first = l
+        if k == steps - 1:
+            last = l
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    flop_fwd = 2 * (64 * 64 + 64 * 64 + 64 * 8)       # per sample, padded shapes
+    # evaluation on held-out polygons
+    tint = (0.3, 0.9, 1.4)
+    M = sg.tint_matrix(tint)
+    base = ctx.render(ds, cam, stream=stream).cpu().numpy()
+    py, px = np.mgrid[0:HEIGHT, 0:WIDTH]
+    evals = []
+    for reg in polys[MLP_TRAIN_POLYGONS:]:
+        xy = np.asarray(reg.xy, np.float64)
+        inside = np.zeros(HEIGHT * WIDTH, bool)
+        u, v = px.ravel().astype(np.float64), py.ravel().astype(np.float64)
+        for i in range(len(xy)):
+            (xi, yi), (xj, yj) = xy[i], xy[i - 1]
+            cond = (yi > v) != (yj > v)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                xc = xi + (v - yi) * (xj - xi) / (yj - yi)
+            inside ^= cond & (u < xc)
+        target = np.where(inside.reshape(HEIGHT, WIDTH)[..., None], base * np.asarray(tint), base)
+        p = binding.DeviceScene.from_numpy(w.scene, dev, "f32")
+        mask = torch.zeros((binding.mask_words(n),), dtype=torch.int32, device=dev)
+        ctx.select(p, cam, reg, mask, stream=stream)
+        ctx.recolor(p, mask, M, stream=stream)
+        plain_img = ctx.render(p, cam, stream=stream).cpu().numpy()
+        del p
+        q = binding.DeviceScene.from_numpy(w.scene, dev, "f32")
+        m2, wts, nfb = net.select(q, cam, reg, delta=0.1, stream=stream)
+        ctx.recolor_weighted(q, wts, M, stream=stream)
+        mlp_img = ctx.render(q, cam, stream=stream).cpu().numpy()
+        del q
+        b1 = np.unpackbits(mask.cpu().numpy().view(np.uint8), bitorder="little")[:n]
+        b2 = np.unpackbits(m2.cpu().numpy().view(np.uint8), bitorder="little")[:n]
+
+        def psnr(a, b):
+            mse = float(np.mean((a.astype(np.float64) - b) ** 2))
+            return 10 * math.log10(1.0 / max(mse, 1e-20))
+        evals.append(dict(disagreement=float((b1 != b2).mean()), fallback=nfb / n,
+                          psnr_vs_plain=psnr(mlp_img, plain_img),
+                          psnr_plain_vs_target=psnr(plain_img, target),
+                          psnr_learned_vs_target=psnr(mlp_img, target)))
+    reg = polys[MLP_TRAIN_POLYGONS]
+    mask = torch.zeros((binding.mask_words(n),), dtype=torch.int32, device=dev)
+    Fe = torch.empty((n, 64), dtype=torch.bfloat16, device=dev)
+    out = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    t_learned = event_ms(lambda: net.select(ds, cam, reg, delta=0.1, stream=stream))
+    t_plain = event_ms(lambda: ctx.select(ds, cam, reg, mask, stream=stream))
+    t_labels = event_ms(lambda: ctx.mlp_features(ds, cam, reg, stream=stream), reps=2)
+    Fe = ctx.mlp_features(ds, cam, reg, labels=False, stream=stream)[0]
+    t_fwd = event_ms(lambda: net.forward(Fe, out=out, stream=stream))
+    peaks, src = load_peaks()
+    tflops = n * flop_fwd / (t_fwd / 1000.0) / 1e12
+    E = {k: float(np.mean([e[k] for e in evals])) for k in evals[0]}
+    if rank == 0:
+        line = {
+            "metric": "learned selection Gaussians/s at 6M, 1080p (features + MLP + fallback)",
+            "value": n / (t_learned / 1000.0), "unit": "Gaussians/s", "n_gpus": world,
+            "steps": MLP_EVAL_POLYGONS, "warmup": 2, "ms_per_step": t_learned,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic (seeded generator)",
+            "config": {"workload": (f"{n / 1e6:g}M Gaussians, {WIDTH}x{HEIGHT}, MLP 59-64-64-4 "
+                                    f"GELU trained on {MLP_TRAIN_POLYGONS} random 12-gons, "
+                                    f"evaluated on {MLP_EVAL_POLYGONS} held-out ones, tint "
+                                    f"{tint}"),
+                       "train_samples": N, "train_steps": steps, "batch": B},
+            "quality_mean_over_heldout": E, "quality_per_polygon": evals,
+            "training": {"seconds": train_s, "samples_per_s": steps * B / train_s,
+                         "loss_first": first, "loss_last": last},
+            "timings_ms": {"learned_selection": t_learned, "plain_selection": t_plain,
+                           "labels_render_and_cover": t_labels, "mlp_forward": t_fwd},
+            "roofline": {"kernel": "mlp_forward_kernel (mma.sync bf16)", "bound": "tensor",
+                         "achieved": tflops, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                         "frac": tflops / peaks["bf16_tflops"],
+                         "peak_source": f"{src} cuBLAS bf16 burst", "traffic": None},
+        }
+        print(json.dumps(line), flush=True)
+    net.close()
+    ctx.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -597,8 +751,11 @@ def main(argv=None):
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--readback", action="store_true",
                     help="time frames with the mid-frame read back (default: pair capacity preset)")
-    ap.add_argument("--workload", choices=["frame", "batch"], default="frame",
-                    help="frame: the 3M/1080p headline; batch: 64 views of 4 scenes")
+    ap.add_argument("--workload", choices=["frame", "batch", "mlp"], default="frame",
+                    help="frame: the 3M/1080p headline; batch: 64 views of 4 scenes; "
+                         "mlp: the learned selection at 6M Gaussians")
+    ap.add_argument("--mlp-steps", type=int, default=4000,
+                    help="training steps of the mlp workload (batch 16384)")
     ap.add_argument("--gaussians", type=int, default=None,
                     help="scene size for small profiling cases (default 3,000,000)")
     args = ap.parse_args(argv)
@@ -613,6 +770,8 @@ def main(argv=None):
             run_reference(args, rank, world)
         elif args.workload == "batch":
             run_batch(args, rank, world, local)
+        elif args.workload == "mlp":
+            run_mlp(args, rank, world, local)
         else:
             run_ours(args, rank, world, local)
     finally:
