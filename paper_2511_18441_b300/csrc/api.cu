@@ -123,7 +123,7 @@ struct recogs_ctx {
     // host-memory render staging
     DevBuf hs_xyz, hs_ls, hs_q, hs_op, hs_sh, hs_img, hs_T;
     // SH refit: forward image, colour gradient, loss
-    DevBuf rf_img, rf_grad, rf_loss;
+    DevBuf rf_img, rf_grad, rf_loss, rf_region;
     DevCounters* h_counters = nullptr;   // pinned
     // last render
     int64_t last_pairs = 0;
@@ -1077,7 +1077,8 @@ void recogs_ctx_destroy(recogs_ctx* ctx) {
     if (ctx->origin) cudaStreamDestroy(ctx->origin);
     if (ctx->fork) cudaEventDestroy(ctx->fork);
     DevBuf* bufs[] = {&ctx->hs_xyz, &ctx->hs_ls, &ctx->hs_q, &ctx->hs_op, &ctx->hs_sh,
-                      &ctx->hs_img, &ctx->hs_T, &ctx->rf_img, &ctx->rf_grad, &ctx->rf_loss};
+                      &ctx->hs_img, &ctx->hs_T, &ctx->rf_img, &ctx->rf_grad, &ctx->rf_loss,
+                      &ctx->rf_region};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
@@ -1584,10 +1585,12 @@ recogs_status recogs_mlp_labels(recogs_ctx* ctx, const recogs_scene* scene,
                       P<float>(ctx->rf_img), nullptr, nullptr, st));
     CK(cudaMemsetAsync(ctx->rf_grad.p, 0, 12 * (size_t)n, st));
     const DevCamera dc = dev_camera(*select_camera);
+    CKS(ensure(ctx, ctx->rf_region, sizeof(DevRegion)));
+    CK(cudaMemcpyAsync(ctx->rf_region.p, &dr, sizeof(DevRegion), cudaMemcpyHostToDevice, st));
     BlendExtra ex;
     ex.grad_rgb = P<float>(ctx->rf_grad);
     ex.cover = true;
-    ex.region = dr;
+    ex.region = P<DevRegion>(ctx->rf_region);
     stage_begin(ctx, ST_MLP, st);
     int l = launch_blend(P<uint2>(ctx->main.ranges), P<uint32_t>(ctx->main.order), ctx->last_ids,
                          P<float4>(ctx->main.rec), dc, bg0, P<float>(ctx->rf_img), nullptr,

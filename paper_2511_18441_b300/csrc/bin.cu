@@ -404,8 +404,9 @@ __global__ void __launch_bounds__(THREADS)
 // ---------------------------------------------------------------------------
 // per-tile LSD radix sort in shared memory (tiles of 512 .. 8192 pairs)
 //
-// Sorts a tile's pairs by the 32-bit depth key relative to the frame's
-// smallest depth, 8 bits per pass, carrying the Gaussian index. Each pass is
+// Sorts a tile's pairs by the 32-bit depth key relative to the tile's
+// smallest key, 8 bits per pass over the bits the tile's key span needs,
+// carrying the Gaussian index. Each pass is
 // a stable split: warp w owns positions 256w .. 256w+255 of the current
 // sequence (8 rounds of 32), ranks its items with warp match and per-warp
 // digit counters, and all items move to their digit's run in shared memory.
@@ -420,8 +421,7 @@ __global__ void __launch_bounds__(THREADS)
 template <int THREADS>
 __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges, int tile,
                                                const unsigned long long* __restrict__ keys,
-                                               uint32_t* __restrict__ ids, uint32_t zmin,
-                                               int passes) {
+                                               uint32_t* __restrict__ ids) {
     constexpr int W = THREADS / 32;
     constexpr int ITEMS = 8;
     constexpr int MAXN = THREADS * ITEMS;
@@ -430,7 +430,7 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
     uint32_t* s_val = s_key + MAXN;              // MAXN
     uint32_t* s_wcnt = s_val + MAXN;             // W * 256
     __shared__ uint32_t s_dstart[256];
-    __shared__ uint32_t s_part[W + 1];
+    __shared__ uint32_t s_zmin[W], s_zmax[W];
 
     const uint2 r = ranges[tile];
     const int n = (int)(r.y - r.x);
@@ -438,19 +438,44 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
 
+    // positions of round i of this warp start at warp * 256 + i * 32; rounds
+    // past the tile's end are skipped by the whole warp
     uint32_t key[ITEMS], val[ITEMS];
+    uint32_t kmin = 0xffffffffu, kmax = 0u;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const int p = warp * 256 + i * 32 + lane;
         if (p < n) {
             const unsigned long long k = keys[r.x + p];
-            key[i] = (uint32_t)(k >> 32) - zmin;
+            key[i] = (uint32_t)(k >> 32);
             val[i] = (uint32_t)k;
+            kmin = min(kmin, key[i]);
+            kmax = max(kmax, key[i]);
         } else {
             key[i] = 0xffffffffu;
             val[i] = 0u;
         }
     }
+    // the tile's own depth-key range: keys relative to its minimum, and
+    // only as many 8-bit passes as its span needs
+    kmin = __reduce_min_sync(0xffffffffu, kmin);
+    kmax = __reduce_max_sync(0xffffffffu, kmax);
+    if (lane == 0) {
+        s_zmin[warp] = kmin;
+        s_zmax[warp] = kmax;
+    }
+    __syncthreads();
+    uint32_t zmin = 0xffffffffu, zmax = 0u;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        zmin = min(zmin, s_zmin[w]);
+        zmax = max(zmax, s_zmax[w]);
+    }
+    const uint32_t span = n > 0 ? zmax - zmin : 0u;
+    const int passes = span == 0u ? 0 : (32 - __clz((int)span) + 7) / 8;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i)
+        if (warp * 256 + i * 32 + lane < n) key[i] -= zmin;
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
         for (int d = threadIdx.x; d < W * 256; d += THREADS) s_wcnt[d] = 0;
@@ -458,6 +483,8 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
         uint32_t rank[ITEMS];
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
+            rank[i] = 0u;
+            if (warp * 256 + i * 32 >= n) continue;   // warp-uniform: round past the end
             const int p = warp * 256 + i * 32 + lane;
             const bool ok = p < n;
             const uint32_t dg = ok ? ((key[i] >> shift) & 0xffu) : 256u;
@@ -552,7 +579,6 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
     }
     __syncthreads();
     for (int p = threadIdx.x; p < n; p += THREADS) ids[r.x + p] = s_val[p];
-    (void)s_part;
 }
 
 template <int THREADS>
@@ -565,11 +591,8 @@ __global__ void __launch_bounds__(THREADS, (RECOGS_RADIX_WARPS_PER_SM * 32 / THR
     if (ctr->skip) return;
     uint32_t count, first;
     class_span(ctr, cls, count, first);
-    const uint32_t zmin = ~ctr->zmin_inv;
-    const uint32_t span = ctr->zmax - zmin;
-    const int passes = span == 0u ? 0 : (32 - __clz((int)span) + 7) / 8;
     for (uint32_t item = blockIdx.x; item < count; item += gridDim.x) {
-        tile_radix_one<THREADS>(ranges, (int)order[first + item], keys, ids, zmin, passes);
+        tile_radix_one<THREADS>(ranges, (int)order[first + item], keys, ids);
         __syncthreads();
     }
 }

@@ -93,8 +93,10 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
                  int height, int tiles_x, float bg0, float bg1, float bg2, float* __restrict__ image,
                  float* __restrict__ final_T, DevCounters* __restrict__ ctr, BlendExtra ex) {
     static_assert(BATCH == 128 || BATCH == 256, "blend batch");
-    __shared__ float4 s_a[BATCH];     // (u, v, q0, q1), centre in this tile's frame
-    __shared__ float4 s_b[BATCH];     // (q2, log2 sigma, r, g)
+    // exponent polynomial A x^2 + B x y + C y^2 + D x + E y + F in the
+    // tile-centred pixel coordinates
+    __shared__ float4 s_a[BATCH];     // (A, B, C, D)
+    __shared__ float4 s_b[BATCH];     // (E, F, r, g)
     __shared__ float s_c[BATCH];      // b
     __shared__ uint32_t s_m[BATCH];   // group mask
     // depth mode: view depth of each staged Gaussian; gradient mode: its index
@@ -114,7 +116,10 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
     const int ly = (warp >> 1) * 4 + (grp >> 1) * 2 + ((lane >> 2) & 1);
     const int px = tx * kTile + lx, py = ty * kTile + ly;
     const bool inside = px < width && py < height;
-    const float fpx = (float)lx, fpy = (float)ly;
+    // pixel coordinates relative to the tile centre (exact halves), and the
+    // monomials of the exponent polynomial
+    const float fpx = (float)lx - 7.5f, fpy = (float)ly - 7.5f;
+    const float fxx = fpx * fpx, fxy = fpx * fpy, fyy = fpy * fpy;
     const int mbit = 4 * warp + (grp & 1) + 2 * (grp >> 1);   // this lane's group bit
     const size_t pix = (size_t)py * width + px;
 
@@ -144,7 +149,7 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
     }
     if (MODE == kBlendCover && inside) {
         // weights 1[pixel centre in the region] and 1 (the pixel centre is (px, py))
-        g0 = in_region(ex.region, (float)px, (float)py) ? 1.f : 0.f;
+        g0 = in_region(*ex.region, (float)px, (float)py) ? 1.f : 0.f;
         g1 = 1.f;
     }
     if (kAcc)
@@ -198,8 +203,15 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
             const uint32_t o = __float_as_uint(rc.w);
             const float u = ra.x + (float)(kTile * ((int)(o & 0xffffu) - tx));
             const float v = ra.y + (float)(kTile * ((int)(o >> 16) - ty));
-            s_a[threadIdx.x] = make_float4(u, v, ra.z, ra.w);
-            s_b[threadIdx.x] = make_float4(rb.x, rb.y, rc.x, rc.y);
+            // the exponent q0 du^2 + q1 du dv + q2 dv^2 + log2 sigma (du = x - u,
+            // dv = y - v) as a polynomial in the centred pixel coordinates
+            const float uc = u - 7.5f, vc = v - 7.5f;
+            const float q0 = ra.z, q1 = ra.w, q2 = rb.x;
+            const float D = -fmaf(2.0f * q0, uc, q1 * vc);
+            const float E = -fmaf(2.0f * q2, vc, q1 * uc);
+            const float F = fmaf(uc, fmaf(q0, uc, q1 * vc), fmaf(q2 * vc, vc, rb.y));
+            s_a[threadIdx.x] = make_float4(q0, q1, q2, D);
+            s_b[threadIdx.x] = make_float4(E, F, rc.x, rc.y);
             s_c[threadIdx.x] = rc.z;
             s_m[threadIdx.x] = group_mask(u, v, rb.z, rb.w);
             if (MODE == kBlendDepth) s_z[threadIdx.x] = __uint_as_float(__ldg(ex.zkey + rid));
@@ -242,19 +254,20 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
                 m &= m - 1;
                 const float4 a0 = s_a[s0], b0 = s_b[s0];
                 const float4 a1 = s_a[s1], b1 = s_b[s1];
-                float dx = fpx - a0.x, dy = fpy - a0.y;
-                const float p0 = fmaf(dx, fmaf(a0.z, dx, a0.w * dy), b0.x * dy * dy);
-                dx = fpx - a1.x;
-                dy = fpy - a1.y;
-                const float p1 = fmaf(dx, fmaf(a1.z, dx, a1.w * dy), b1.x * dy * dy);
-                const float al0 = fminf(0.99f, exp2_approx(fminf(p0, 0.0f) + b0.y));
-                const float al1 = fminf(0.99f, exp2_approx(fminf(p1, 0.0f) + b1.y));
+                // exponent <= 0 up to rounding (a positive-definite conic): no clamp
+                const float p0 = fmaf(a0.x, fxx, fmaf(a0.y, fxy, fmaf(a0.z, fyy,
+                                 fmaf(a0.w, fpx, fmaf(b0.x, fpy, b0.y)))));
+                const float p1 = fmaf(a1.x, fxx, fmaf(a1.y, fxy, fmaf(a1.z, fyy,
+                                 fmaf(a1.w, fpx, fmaf(b1.x, fpy, b1.y)))));
+                const float al0 = fminf(0.99f, exp2_approx(p0));
+                const float al1 = fminf(0.99f, exp2_approx(p1));
                 {
-                    const float nT = T * (1.0f - al0);
+                    const float wt = al0 * T;
+                    const float nT = T - wt;
                     const bool take = act0 && !done && al0 >= a_min;
                     const bool stop = take && nT < 1e-4f;
                     const bool add = take && !stop;
-                    const float w = add ? al0 * T : 0.0f;
+                    const float w = add ? wt : 0.0f;
                     if (!kAcc) {
                         cr = fmaf(b0.z, w, cr);
                         cg = fmaf(b0.w, w, cg);
@@ -278,11 +291,12 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
                     done = done || stop;
                 }
                 {
-                    const float nT = T * (1.0f - al1);
+                    const float wt = al1 * T;
+                    const float nT = T - wt;
                     const bool take = act1 && !done && al1 >= a_min;
                     const bool stop = take && nT < 1e-4f;
                     const bool add = take && !stop;
-                    const float w = add ? al1 * T : 0.0f;
+                    const float w = add ? wt : 0.0f;
                     if (!kAcc) {
                         cr = fmaf(b1.z, w, cr);
                         cg = fmaf(b1.w, w, cg);

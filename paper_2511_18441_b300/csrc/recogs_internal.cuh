@@ -243,7 +243,7 @@ struct BlendExtra {
     float* grad_rgb = nullptr;
     double* loss = nullptr;
     bool cover = false;
-    DevRegion region;
+    const DevRegion* region = nullptr;   // device memory
 };
 
 // Adam parameters of the SH refit, with the bias corrections 1 / (1 - b^t).
