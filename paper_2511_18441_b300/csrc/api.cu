@@ -57,6 +57,9 @@ struct Scratch {
     DevBuf rec, count, rect, zkey, block_sums, block_offsets, counters;
     DevBuf dkeys[2], dvals[2], sort_scratch, pair_sums, pair_offsets;
     DevBuf tkeys[2], tvals[2], ranges, order, tile_count, cursor, tile_totals, pair_keys;
+    DevBuf sort_work;               // per-class tile counters of the per-tile sort
+    cudaStream_t aux[2] = {nullptr, nullptr};   // concurrent sort classes
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
     bool counters_ready = false;
     bool tile_count_zero = false;   // every tile_count word is 0 (between frames)
     bool has_class_hint = false;    // class_hint holds the last read-back frame's class sizes
@@ -65,12 +68,20 @@ struct Scratch {
         DevBuf* bufs[] = {&rec, &count, &rect, &zkey, &block_sums, &block_offsets, &counters,
                           &dkeys[0], &dkeys[1], &dvals[0], &dvals[1], &sort_scratch, &pair_sums,
                           &pair_offsets, &tkeys[0], &tkeys[1], &tvals[0], &tvals[1], &ranges,
-                          &order, &tile_count, &cursor, &tile_totals, &pair_keys};
+                          &order, &tile_count, &cursor, &tile_totals, &pair_keys, &sort_work};
         for (DevBuf* b : bufs) {
             if (b->p) cudaFree(b->p);
             b->p = nullptr;
             b->cap = 0;
         }
+        for (int k = 0; k < 2; ++k) {
+            if (aux[k]) cudaStreamDestroy(aux[k]);
+            if (ev_join[k]) cudaEventDestroy(ev_join[k]);
+            aux[k] = nullptr;
+            ev_join[k] = nullptr;
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        ev_fork = nullptr;
         counters_ready = false;
         tile_count_zero = false;
     }
@@ -425,8 +436,9 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
                                P<uint32_t>(sc.cursor), P<uint32_t>(sc.tile_totals), st);
     sc.tile_count_zero = true;
     const bool async = sched.pair_capacity > 0;
+    CKS(ensure(ctx, sc.sort_work, sizeof(uint32_t) * kSortClasses));
     l += launch_tile_scan(P<uint32_t>(sc.tile_totals), tiles, P<uint2>(sc.ranges),
-                          P<uint32_t>(sc.order), dctr,
+                          P<uint32_t>(sc.order), dctr, P<uint32_t>(sc.sort_work),
                           async ? (uint32_t)sched.pair_capacity : 0xffffffffu, st);
     stage_end(ctx, ST_SCAN, l, st);
     CK(cudaGetLastError());
@@ -489,9 +501,24 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
                                   : sched.class_hint     ? sched.class_hint
                                   : sc.has_class_hint    ? sc.class_hint
                                                          : nullptr;
+        // the classes run on three streams forked from st and joined back
+        if (!sc.ev_fork) {
+            CK(cudaEventCreateWithFlags(&sc.ev_fork, cudaEventDisableTiming));
+            for (int k = 0; k < 2; ++k) {
+                CK(cudaStreamCreateWithFlags(&sc.aux[k], cudaStreamNonBlocking));
+                CK(cudaEventCreateWithFlags(&sc.ev_join[k], cudaEventDisableTiming));
+            }
+        }
+        CK(cudaEventRecord(sc.ev_fork, st));
+        for (int k = 0; k < 2; ++k) CK(cudaStreamWaitEvent(sc.aux[k], sc.ev_fork, 0));
+        const cudaStream_t streams[3] = {st, sc.aux[0], sc.aux[1]};
         l = launch_tile_sort(P<uint2>(sc.ranges), P<uint32_t>(sc.order), classes, !async, tiles,
                              P<unsigned long long>(sc.pair_keys), P<uint32_t>(sc.tvals[0]), dctr,
-                             sched.radix_classes, st);
+                             P<uint32_t>(sc.sort_work), sched.radix_classes, streams);
+        for (int k = 0; k < 2; ++k) {
+            CK(cudaEventRecord(sc.ev_join[k], sc.aux[k]));
+            CK(cudaStreamWaitEvent(st, sc.ev_join[k], 0));
+        }
         stage_end(ctx, ST_TILE_SORT, l, st);
         ids = P<uint32_t>(sc.tvals[0]);
         CK(cudaGetLastError());

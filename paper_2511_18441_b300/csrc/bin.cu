@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restr
                                                          int tiles, uint2* __restrict__ ranges,
                                                          uint32_t* __restrict__ order,
                                                          DevCounters* __restrict__ ctr,
+                                                         uint32_t* __restrict__ work,
                                                          uint32_t capacity) {
     __shared__ uint32_t s_warp[33];
     __shared__ uint32_t s_max[32];
@@ -78,7 +79,10 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restr
     __shared__ uint32_t s_hist[kOrderBuckets];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     static_assert(kOrderBuckets == 1024, "one order bucket per thread");
-    if (threadIdx.x < kSortClasses) s_cls[threadIdx.x] = 0;
+    if (threadIdx.x < kSortClasses) {
+        s_cls[threadIdx.x] = 0;
+        if (work) work[threadIdx.x] = 0u;   // the sort classes' tile counters
+    }
     s_hist[threadIdx.x] = 0;
     __syncthreads();
     unsigned long long carry = 0;
@@ -164,8 +168,8 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restr
 }
 
 int launch_tile_scan(const uint32_t* totals, int tiles, uint2* ranges, uint32_t* order,
-                     DevCounters* counters, uint32_t capacity, cudaStream_t st) {
-    tile_scan_kernel<<<1, 1024, 0, st>>>(totals, tiles, ranges, order, counters, capacity);
+                     DevCounters* counters, uint32_t* work, uint32_t capacity, cudaStream_t st) {
+    tile_scan_kernel<<<1, 1024, 0, st>>>(totals, tiles, ranges, order, counters, work, capacity);
     return 1;
 }
 
@@ -308,6 +312,22 @@ __device__ __forceinline__ void class_span(const DevCounters* ctr, int cls, uint
     count = ctr->class_tiles[cls];
 }
 
+// Next tile of a sort class for this block: with `work` (a per-class
+// counter zeroed by the tile scan) blocks take tiles as they become free,
+// otherwise block b takes items b, b + grid, ...; UINT32_MAX when done.
+__device__ __forceinline__ uint32_t next_item(uint32_t* work, int cls, uint32_t& k,
+                                              uint32_t count, uint32_t* s_item) {
+    if (work) {
+        if (threadIdx.x == 0) *s_item = atomicAdd(&work[cls], 1u);
+        __syncthreads();
+        const uint32_t item = *s_item;
+        __syncthreads();
+        return item < count ? item : 0xffffffffu;
+    }
+    const uint32_t item = blockIdx.x + (k++) * gridDim.x;
+    return item < count ? item : 0xffffffffu;
+}
+
 template <int THREADS>
 __device__ __forceinline__ void tile_sort_one(const uint2* __restrict__ ranges, int tile,
                                               const unsigned long long* __restrict__ keys,
@@ -390,11 +410,12 @@ template <int THREADS>
 __global__ void __launch_bounds__(THREADS)
     tile_sort_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
                      const unsigned long long* __restrict__ keys, uint32_t* __restrict__ ids,
-                     const DevCounters* __restrict__ ctr, int cls) {
+                     const DevCounters* __restrict__ ctr, uint32_t* __restrict__ work, int cls) {
+    __shared__ uint32_t s_item;
     if (ctr->skip) return;
-    uint32_t count, first;
+    uint32_t count, first, k = 0;
     class_span(ctr, cls, count, first);
-    for (uint32_t item = blockIdx.x; item < count; item += gridDim.x) {
+    for (uint32_t item; (item = next_item(work, cls, k, count, &s_item)) != 0xffffffffu;) {
         tile_sort_one<THREADS>(ranges, (int)order[first + item], keys, ids);
         __syncthreads();
     }
@@ -587,11 +608,12 @@ __global__ void __launch_bounds__(THREADS, (RECOGS_RADIX_WARPS_PER_SM * 32 / THR
                                                : 1)
     tile_radix_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
                       const unsigned long long* __restrict__ keys, uint32_t* __restrict__ ids,
-                      const DevCounters* __restrict__ ctr, int cls) {
+                      const DevCounters* __restrict__ ctr, uint32_t* __restrict__ work, int cls) {
+    __shared__ uint32_t s_item;
     if (ctr->skip) return;
-    uint32_t count, first;
+    uint32_t count, first, k = 0;
     class_span(ctr, cls, count, first);
-    for (uint32_t item = blockIdx.x; item < count; item += gridDim.x) {
+    for (uint32_t item; (item = next_item(work, cls, k, count, &s_item)) != 0xffffffffu;) {
         tile_radix_one<THREADS>(ranges, (int)order[first + item], keys, ids);
         __syncthreads();
     }
@@ -619,36 +641,40 @@ static int persistent_grid(K kernel, int threads, size_t smem, uint32_t bound) {
 template <int THREADS>
 static void radix_class_launch(uint32_t bound, const uint2* ranges, const uint32_t* order,
                                const unsigned long long* keys, uint32_t* ids,
-                               const DevCounters* ctr, int cls, cudaStream_t st) {
+                               const DevCounters* ctr, uint32_t* work, int cls, cudaStream_t st) {
     const size_t smem = sizeof(uint32_t) * (2 * 8 * THREADS + (THREADS / 32) * 256);
     // dynamic plus static shared memory above the 48 KiB default needs the opt-in
     if (smem + 2048 > 48 * 1024)
         cudaFuncSetAttribute(tile_radix_kernel<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     const int g = persistent_grid(tile_radix_kernel<THREADS>, THREADS, smem, bound);
-    tile_radix_kernel<THREADS><<<g, THREADS, smem, st>>>(ranges, order, keys, ids, ctr, cls);
+    tile_radix_kernel<THREADS><<<g, THREADS, smem, st>>>(ranges, order, keys, ids, ctr, work, cls);
 }
 
 template <int THREADS>
 static void sort_class_launch(uint32_t bound, const uint2* ranges, const uint32_t* order,
                               const unsigned long long* keys, uint32_t* ids,
-                              const DevCounters* ctr, int cls, cudaStream_t st) {
+                              const DevCounters* ctr, uint32_t* work, int cls, cudaStream_t st) {
     const size_t smem = THREADS > 32 ? sizeof(unsigned long long) * 8 * THREADS : 0;
     if (smem + 2048 > 48 * 1024)
         cudaFuncSetAttribute(tile_sort_kernel<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     const int g = persistent_grid(tile_sort_kernel<THREADS>, THREADS, smem, bound);
-    tile_sort_kernel<THREADS><<<g, THREADS, smem, st>>>(ranges, order, keys, ids, ctr, cls);
+    tile_sort_kernel<THREADS><<<g, THREADS, smem, st>>>(ranges, order, keys, ids, ctr, work, cls);
 }
 
 int launch_tile_sort(const uint2* ranges, const uint32_t* order, const uint32_t* class_tiles,
                      bool exact, int tiles, const unsigned long long* keys, uint32_t* ids,
-                     const DevCounters* counters, int radix_classes, cudaStream_t st) {
+                     const DevCounters* counters, uint32_t* work, int radix_classes,
+                     const cudaStream_t streams[3]) {
     // Classes follow each other in the tile order from the largest CTA (1024
     // threads) down. Every launch is a persistent grid that reads its class's
     // size on the device; class_tiles only sizes the grids: exact host-known
     // sizes (empty classes are skipped), a hint from an earlier frame (grids
     // for 1.25x the hinted tiles, at least one block), or NULL (full grids).
+    // streams: class 0 (few, slow tiles) runs on streams[1], the small
+    // classes 4-5 on streams[2], classes 1-3 on streams[0], so that their
+    // tails overlap; with `work` blocks take tiles dynamically.
     int launches = 0;
     for (int c = 0; c < kSortClasses; ++c) {
         uint32_t bound = (uint32_t)tiles;
@@ -659,29 +685,30 @@ int launch_tile_sort(const uint2* ranges, const uint32_t* order, const uint32_t*
             bound = class_tiles[c] + class_tiles[c] / 4 + 1;
         }
         const bool radix = c < radix_classes;
+        const cudaStream_t st = c == 0 ? streams[1] : c >= 4 ? streams[2] : streams[0];
         switch (c) {
             case 0:
-                if (radix) radix_class_launch<1024>(bound, ranges, order, keys, ids, counters, c, st);
-                else sort_class_launch<1024>(bound, ranges, order, keys, ids, counters, c, st);
+                if (radix) radix_class_launch<1024>(bound, ranges, order, keys, ids, counters, work, c, st);
+                else sort_class_launch<1024>(bound, ranges, order, keys, ids, counters, work, c, st);
                 break;
             case 1:
-                if (radix) radix_class_launch<512>(bound, ranges, order, keys, ids, counters, c, st);
-                else sort_class_launch<512>(bound, ranges, order, keys, ids, counters, c, st);
+                if (radix) radix_class_launch<512>(bound, ranges, order, keys, ids, counters, work, c, st);
+                else sort_class_launch<512>(bound, ranges, order, keys, ids, counters, work, c, st);
                 break;
             case 2:
-                if (radix) radix_class_launch<256>(bound, ranges, order, keys, ids, counters, c, st);
-                else sort_class_launch<256>(bound, ranges, order, keys, ids, counters, c, st);
+                if (radix) radix_class_launch<256>(bound, ranges, order, keys, ids, counters, work, c, st);
+                else sort_class_launch<256>(bound, ranges, order, keys, ids, counters, work, c, st);
                 break;
             case 3:
-                if (radix) radix_class_launch<128>(bound, ranges, order, keys, ids, counters, c, st);
-                else sort_class_launch<128>(bound, ranges, order, keys, ids, counters, c, st);
+                if (radix) radix_class_launch<128>(bound, ranges, order, keys, ids, counters, work, c, st);
+                else sort_class_launch<128>(bound, ranges, order, keys, ids, counters, work, c, st);
                 break;
             case 4:
-                if (radix) radix_class_launch<64>(bound, ranges, order, keys, ids, counters, c, st);
-                else sort_class_launch<64>(bound, ranges, order, keys, ids, counters, c, st);
+                if (radix) radix_class_launch<64>(bound, ranges, order, keys, ids, counters, work, c, st);
+                else sort_class_launch<64>(bound, ranges, order, keys, ids, counters, work, c, st);
                 break;
             default:
-                sort_class_launch<32>(bound, ranges, order, keys, ids, counters, c, st);
+                sort_class_launch<32>(bound, ranges, order, keys, ids, counters, work, c, st);
                 break;
         }
         ++launches;

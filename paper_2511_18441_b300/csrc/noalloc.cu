@@ -231,7 +231,7 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
         launch_scan_small(po.block_sums, U32(oBlockOffsets), nb, 1, &dctr->n_visible, st);
     }
     launch_tile_totals(U32(oTileCount), tiles, kTilePartsSmall, U32(oCursor), U32(oTileTotals), st);
-    launch_tile_scan(U32(oTileTotals), tiles, ranges, U32(oOrder), dctr, 0xffffffffu, st);
+    launch_tile_scan(U32(oTileTotals), tiles, ranges, U32(oOrder), dctr, nullptr, 0xffffffffu, st);
     NA_CK(cudaGetLastError());
     NA_CK(cudaMemcpyAsync(&hc, dctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
     NA_CK(cudaStreamSynchronize(st));
@@ -256,8 +256,9 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
         unsigned long long* keys = reinterpret_cast<unsigned long long*>(base + oTkeys0);
         launch_scatter(U32(oCount), reinterpret_cast<const uint2*>(base + oRect), U32(oZkey), n,
                        dc.tiles_x, ranges, U32(oCursor), kTilePartsSmall, keys, dctr, st);
-        launch_tile_sort(ranges, U32(oOrder), hc.class_tiles, true, tiles, keys, U32(oTvals0), dctr, 4,
-                         st);
+        const cudaStream_t streams[3] = {st, st, st};
+        launch_tile_sort(ranges, U32(oOrder), hc.class_tiles, true, tiles, keys, U32(oTvals0), dctr,
+                         nullptr, 4, streams);
     } else if (P > 0) {
         launch_compact(U32(oCount), U32(oZkey), n, U32(oBlockOffsets), dctr, U32(oDkeys0),
                        U32(oDvals0), st);

@@ -214,8 +214,10 @@ int launch_emit(const uint32_t* sorted_ids, const uint32_t* counts_sorted, const
 int launch_tile_totals(uint32_t* tile_count, int tiles, int parts, uint32_t* cursor,
                        uint32_t* totals, cudaStream_t st);
 // tile_scan also writes the tile order (tiles by order_bucket).
+// tile_scan also zeroes the sort classes' work counters (work: kSortClasses
+// words, may be NULL).
 int launch_tile_scan(const uint32_t* totals, int tiles, uint2* ranges, uint32_t* order,
-                     DevCounters* counters, uint32_t capacity, cudaStream_t st);
+                     DevCounters* counters, uint32_t* work, uint32_t capacity, cudaStream_t st);
 int launch_scatter(const uint32_t* count, const uint2* rect, const uint32_t* zkey, int n,
                    int tiles_x, const uint2* ranges, uint32_t* cursor, int parts,
                    unsigned long long* keys, const DevCounters* counters, cudaStream_t st);
@@ -223,9 +225,12 @@ int launch_scatter(const uint32_t* count, const uint2* rect, const uint32_t* zke
 // an earlier frame) or NULL; they only size the persistent grids. Classes
 // 0 .. radix_classes-1 (the largest tiles) are sorted by radix, the rest by
 // the bitonic network.
+// work: per-class tile counters (dynamic tile assignment) or NULL (static);
+// streams[0..2]: see the definition (all three may be the same stream).
 int launch_tile_sort(const uint2* ranges, const uint32_t* order, const uint32_t* class_tiles,
                      bool exact, int tiles, const unsigned long long* keys, uint32_t* ids,
-                     const DevCounters* counters, int radix_classes, cudaStream_t st);
+                     const DevCounters* counters, uint32_t* work, int radix_classes,
+                     const cudaStream_t streams[3]);
 // Optional outputs of the blend. depth != NULL: the median depth of each
 // pixel (the view depth, from zkey, of the Gaussian whose blending takes T
 // below tau; 0 if none). grad_rgb != NULL: instead of the image, the colour
