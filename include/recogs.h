@@ -441,15 +441,19 @@ RECOGS_API int64_t recogs_launch_count(const recogs_ctx* ctx);
  * Both give identical lists. */
 RECOGS_API recogs_status recogs_set_sort_path(recogs_ctx* ctx, int path);
 
-/* Schedule knobs of recogs_render (the batch autotuner searches the same
- * ones; every setting gives the same image bit for bit):
+/* Schedule knobs of recogs_render (the batch autotuner searches them too;
+ * every setting gives the same image bit for bit):
  * radix_classes (0..5) = how many of the per-tile sort's size classes, from
  * the largest tiles (up to 8192 pairs) down, are sorted by the shared-memory
  * radix sort rather than the register bitonic network (default 4);
  * blend_batch (128 or 256) = depth-sorted Gaussians staged in shared memory
- * per step of the blend (default 256). */
+ * per step of the blend (default 256); overlap (0 or 1) = blend each size
+ * class's tiles on the class's stream as soon as they are sorted (stage
+ * timing then reports one "sort_blend" stage) rather than one blend of all
+ * tiles, heaviest first, after every sort (default 0: measured faster at
+ * 3M Gaussians, 1080p). */
 RECOGS_API recogs_status recogs_set_schedule(recogs_ctx* ctx, int32_t radix_classes,
-                                             int32_t blend_batch);
+                                             int32_t blend_batch, int32_t overlap);
 
 /* ---------------------------------------------------------------------------
  * Frames without a read back, batches of views, CUDA graphs
@@ -497,7 +501,8 @@ typedef struct {
  * stream; views run concurrently across lanes) and, with RECOGS_BATCH_GRAPH,
  * captures all lanes as one CUDA graph. With RECOGS_BATCH_TUNE the planning
  * also times candidate schedules (lane count 1/2/4, the per-tile sort's radix
- * classes, the blend batch) and keeps the fastest. Planning waits for the
+ * classes, the blend batch, blending each sort class as it is sorted) and
+ * keeps the fastest. Planning waits for the
  * device. Later calls with the same description replay the plan (one graph
  * launch) without any read back; the scenes' and regions' contents may
  * change between calls, their sizes and pointers may not.
@@ -518,7 +523,7 @@ typedef struct {
     int32_t blend_batch;
     int32_t tune_trials;        /* schedules timed by the autotuner */
     int32_t views_outside_lanes;
-    int32_t reserved;
+    int32_t overlap;            /* 1 if the plan blends each sort class as it is sorted */
     int64_t graph_launches;     /* kernel launches in one replay of the graph */
     double tuned_ms;            /* best batch time the autotuner measured (0 if not tuned) */
 } recogs_batch_info_t;

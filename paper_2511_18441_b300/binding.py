@@ -66,7 +66,7 @@ class CBatchInfo(C.Structure):
     _fields_ = [("planned", C.c_int32), ("graph", C.c_int32), ("lanes", C.c_int32),
                 ("radix_classes", C.c_int32), ("blend_batch", C.c_int32),
                 ("tune_trials", C.c_int32), ("views_outside_lanes", C.c_int32),
-                ("reserved", C.c_int32), ("graph_launches", C.c_int64), ("tuned_ms", C.c_double)]
+                ("overlap", C.c_int32), ("graph_launches", C.c_int64), ("tuned_ms", C.c_double)]
 
 
 class CAdam(C.Structure):
@@ -103,7 +103,7 @@ SIGNATURES = {
                                      C.POINTER(C.c_int64), C.c_int]),
     "recogs_launch_count": (C.c_int64, [C.c_void_p]),
     "recogs_set_sort_path": (C.c_int, [C.c_void_p, C.c_int]),
-    "recogs_set_schedule": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "recogs_set_schedule": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
     "recogs_set_pair_capacity": (C.c_int, [C.c_void_p, C.c_int64]),
     "recogs_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "recogs_render_batch": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.c_int32,
@@ -490,8 +490,9 @@ class Context:
         """0 automatic, 1 per-tile shared-memory sort, 2 global radix path."""
         self._check(self._L.recogs_set_sort_path(self._h, int(path)))
 
-    def set_schedule(self, radix_classes: int = 4, blend_batch: int = 256):
-        self._check(self._L.recogs_set_schedule(self._h, int(radix_classes), int(blend_batch)))
+    def set_schedule(self, radix_classes: int = 4, blend_batch: int = 256, overlap: bool = False):
+        self._check(self._L.recogs_set_schedule(self._h, int(radix_classes), int(blend_batch),
+                                                1 if overlap else 0))
 
     def set_pair_capacity(self, pairs: int):
         """> 0: frames without the mid-frame read back (see recogs.h)."""
@@ -508,8 +509,7 @@ class Context:
     def batch_info(self) -> dict:
         info = CBatchInfo()
         self._check(self._L.recogs_batch_info(self._h, C.byref(info)))
-        return {name: getattr(info, name) for name, _ in CBatchInfo._fields_
-                if name != "reserved"}
+        return {name: getattr(info, name) for name, _ in CBatchInfo._fields_}
 
 
 class Mlp:

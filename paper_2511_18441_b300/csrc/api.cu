@@ -29,13 +29,14 @@ namespace {
 enum Stage {
     ST_PREPROCESS, ST_SCAN, ST_COMPACT, ST_SORT_DEPTH, ST_PAIR_OFFSETS, ST_EMIT, ST_SORT_TILE,
     ST_BLEND, ST_SELECT, ST_RECOLOR, ST_H2D, ST_D2H, ST_SCATTER, ST_TILE_SORT, ST_REFIT, ST_MLP,
-    ST_COUNT
+    ST_SORT_BLEND, ST_COUNT
 };
 // "scan" = tile totals, tile ranges and tile order; "compact" .. "sort_tile"
 // = the global sort path
 const char* const kStageNames[ST_COUNT] = {
     "preprocess", "scan", "compact", "sort_depth", "pair_offsets", "emit", "sort_tile",
-    "blend", "select", "recolor", "h2d", "d2h", "scatter", "tile_sort", "refit", "mlp"};
+    "blend", "select", "recolor", "h2d", "d2h", "scatter", "tile_sort", "refit", "mlp",
+    "sort_blend"};
 
 struct DevBuf {
     void* p = nullptr;
@@ -58,8 +59,8 @@ struct Scratch {
     DevBuf dkeys[2], dvals[2], sort_scratch, pair_sums, pair_offsets;
     DevBuf tkeys[2], tvals[2], ranges, order, tile_count, cursor, tile_totals, pair_keys;
     DevBuf sort_work;               // per-class tile counters of the per-tile sort
-    cudaStream_t aux[2] = {nullptr, nullptr};   // concurrent sort classes
-    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+    cudaStream_t aux[kSortClasses] = {};        // one stream per sort class
+    cudaEvent_t ev_fork = nullptr, ev_join[kSortClasses] = {};
     bool counters_ready = false;
     bool tile_count_zero = false;   // every tile_count word is 0 (between frames)
     bool has_class_hint = false;    // class_hint holds the last read-back frame's class sizes
@@ -74,7 +75,7 @@ struct Scratch {
             b->p = nullptr;
             b->cap = 0;
         }
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < kSortClasses; ++k) {
             if (aux[k]) cudaStreamDestroy(aux[k]);
             if (ev_join[k]) cudaEventDestroy(ev_join[k]);
             aux[k] = nullptr;
@@ -93,6 +94,7 @@ struct Schedule {
     int64_t pair_capacity = 0;  // > 0: no mid-frame read back, pair buffers of this size
     int radix_classes = 4;      // per-tile sort classes (largest first) sorted by radix
     int blend_batch = 256;      // Gaussians staged per blend batch (128 or 256)
+    bool overlap = false;       // blend each sort class's tiles right after its sort
     const uint32_t* class_hint = nullptr;   // sort class sizes of an earlier frame (grid sizes)
 };
 
@@ -484,6 +486,7 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
     }
 
     const uint32_t* ids = nullptr;
+    bool overlapped = false;
     const bool smem_path =
         async || sched.sort_path == 1 || (sched.sort_path == 0 && max_tile <= kMaxSmemTile);
     if (Pn > 0 && smem_path && (int)max_tile <= kMaxSmemTile) {
@@ -495,31 +498,53 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
                            dc.tiles_x, P<uint2>(sc.ranges), P<uint32_t>(sc.cursor), kTileParts,
                            P<unsigned long long>(sc.pair_keys), dctr, st);
         stage_end(ctx, ST_SCATTER, l, st);
-        stage_begin(ctx, ST_TILE_SORT, st);
         // grid sizes: this frame's class sizes, else a hint from an earlier frame
         const uint32_t* classes = !async                ? sc.class_hint
                                   : sched.class_hint     ? sched.class_hint
                                   : sc.has_class_hint    ? sc.class_hint
                                                          : nullptr;
-        // the classes run on three streams forked from st and joined back
+        // every class on its own stream forked from st and joined back
         if (!sc.ev_fork) {
             CK(cudaEventCreateWithFlags(&sc.ev_fork, cudaEventDisableTiming));
-            for (int k = 0; k < 2; ++k) {
+            for (int k = 0; k < kSortClasses; ++k) {
                 CK(cudaStreamCreateWithFlags(&sc.aux[k], cudaStreamNonBlocking));
                 CK(cudaEventCreateWithFlags(&sc.ev_join[k], cudaEventDisableTiming));
             }
         }
+        overlapped = sched.overlap && !extra;
+        stage_begin(ctx, overlapped ? ST_SORT_BLEND : ST_TILE_SORT, st);
         CK(cudaEventRecord(sc.ev_fork, st));
-        for (int k = 0; k < 2; ++k) CK(cudaStreamWaitEvent(sc.aux[k], sc.ev_fork, 0));
-        const cudaStream_t streams[3] = {st, sc.aux[0], sc.aux[1]};
-        l = launch_tile_sort(P<uint2>(sc.ranges), P<uint32_t>(sc.order), classes, !async, tiles,
-                             P<unsigned long long>(sc.pair_keys), P<uint32_t>(sc.tvals[0]), dctr,
-                             P<uint32_t>(sc.sort_work), sched.radix_classes, streams);
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < kSortClasses; ++k) CK(cudaStreamWaitEvent(sc.aux[k], sc.ev_fork, 0));
+        l = 0;
+        uint32_t bound_sum = 0;
+        for (int c = 0; c < kSortClasses; ++c) {
+            const uint32_t bound = sort_class_bound(classes, !async, c, tiles);
+            bound_sum += bound;
+            l += launch_tile_sort_class(c, bound, P<uint2>(sc.ranges), P<uint32_t>(sc.order),
+                                        P<unsigned long long>(sc.pair_keys),
+                                        P<uint32_t>(sc.tvals[0]), dctr, P<uint32_t>(sc.sort_work),
+                                        sched.radix_classes, sc.aux[c]);
+            // overlapped: each class's tiles are blended as soon as they are sorted
+            if (overlapped)
+                l += launch_blend_class(P<uint2>(sc.ranges), P<uint32_t>(sc.order),
+                                        P<uint32_t>(sc.tvals[0]), P<float4>(sc.rec), dc, bgv,
+                                        image, final_T, dctr, sched.blend_batch, c,
+                                        (int)min(bound, (uint32_t)tiles), sc.aux[c]);
+        }
+        if (overlapped) {
+            // the empty tiles (background only) after the classes
+            const uint32_t empty = !async && classes ? (uint32_t)tiles - bound_sum
+                                                     : (uint32_t)tiles;
+            l += launch_blend_class(P<uint2>(sc.ranges), P<uint32_t>(sc.order),
+                                    P<uint32_t>(sc.tvals[0]), P<float4>(sc.rec), dc, bgv, image,
+                                    final_T, dctr, sched.blend_batch, kSortClasses,
+                                    (int)min(empty, 1184u), st);
+        }
+        for (int k = 0; k < kSortClasses; ++k) {
             CK(cudaEventRecord(sc.ev_join[k], sc.aux[k]));
             CK(cudaStreamWaitEvent(st, sc.ev_join[k], 0));
         }
-        stage_end(ctx, ST_TILE_SORT, l, st);
+        stage_end(ctx, overlapped ? ST_SORT_BLEND : ST_TILE_SORT, l, st);
         ids = P<uint32_t>(sc.tvals[0]);
         CK(cudaGetLastError());
     } else if (Pn > 0) {
@@ -594,16 +619,18 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
     }
     if (n == 0) CKS(ensure(ctx, sc.rec, 16 * 3));
 
-    // 4. blend
-    stage_begin(ctx, ST_BLEND, st);
-    BlendExtra ex;
-    if (extra) {
-        ex = *extra;
-        ex.zkey = P<uint32_t>(sc.zkey);
+    // 4. blend (unless it ran per class with the sorts)
+    if (!overlapped) {
+        stage_begin(ctx, ST_BLEND, st);
+        BlendExtra ex;
+        if (extra) {
+            ex = *extra;
+            ex.zkey = P<uint32_t>(sc.zkey);
+        }
+        l = launch_blend(P<uint2>(sc.ranges), P<uint32_t>(sc.order), ids, P<float4>(sc.rec), dc,
+                         bgv, image, final_T, dctr, sched.blend_batch, extra ? &ex : nullptr, st);
+        stage_end(ctx, ST_BLEND, l, st);
     }
-    l = launch_blend(P<uint2>(sc.ranges), P<uint32_t>(sc.order), ids, P<float4>(sc.rec), dc,
-                     bgv, image, final_T, dctr, sched.blend_batch, extra ? &ex : nullptr, st);
-    stage_end(ctx, ST_BLEND, l, st);
     CK(cudaGetLastError());
 
     ctx->last_pairs = Pn;
@@ -945,6 +972,12 @@ recogs_status plan_batch(recogs_ctx* ctx, const recogs_scene* scenes, int n_scen
             sc.blend_batch = 128;
             CKS(trial(best_lanes, sc, &better));
             if (better) best.blend_batch = 128;
+        }
+        {
+            Schedule sc = best;
+            sc.overlap = true;
+            CKS(trial(best_lanes, sc, &better));
+            if (better) best.overlap = true;
         }
         ctx->batch_sched = best;
         ctx->batch_lanes = best_lanes;
@@ -1308,8 +1341,10 @@ recogs_status recogs_set_pair_capacity(recogs_ctx* ctx, int64_t pairs) {
     return RECOGS_OK;
 }
 
-recogs_status recogs_set_schedule(recogs_ctx* ctx, int32_t radix_classes, int32_t blend_batch) {
+recogs_status recogs_set_schedule(recogs_ctx* ctx, int32_t radix_classes, int32_t blend_batch,
+                                  int32_t overlap) {
     if (!ctx) return RECOGS_EINVAL;
+    ctx->sched.overlap = overlap != 0;
     if (radix_classes < 0 || radix_classes > 5)
         return fail(ctx, RECOGS_EINVAL, "radix_classes must be 0..5, got %d", radix_classes);
     if (blend_batch != 128 && blend_batch != 256)
@@ -1392,6 +1427,7 @@ recogs_status recogs_batch_info(recogs_ctx* ctx, recogs_batch_info_t* info) {
     info->lanes = (int32_t)ctx->lanes.size();
     info->radix_classes = ctx->batch_sched.radix_classes;
     info->blend_batch = ctx->batch_sched.blend_batch;
+    info->overlap = ctx->batch_sched.overlap ? 1 : 0;
     info->tune_trials = ctx->batch_tune_trials;
     info->graph_launches = ctx->batch_graph_launches;
     info->tuned_ms = ctx->batch_tuned_ms;

@@ -663,6 +663,46 @@ static void sort_class_launch(uint32_t bound, const uint2* ranges, const uint32_
     tile_sort_kernel<THREADS><<<g, THREADS, smem, st>>>(ranges, order, keys, ids, ctr, work, cls);
 }
 
+int launch_tile_sort_class(int c, uint32_t bound, const uint2* ranges, const uint32_t* order,
+                           const unsigned long long* keys, uint32_t* ids,
+                           const DevCounters* counters, uint32_t* work, int radix_classes,
+                           cudaStream_t st) {
+    if (bound == 0) return 0;
+    const bool radix = c < radix_classes;
+    switch (c) {
+        case 0:
+            if (radix) radix_class_launch<1024>(bound, ranges, order, keys, ids, counters, work, c, st);
+            else sort_class_launch<1024>(bound, ranges, order, keys, ids, counters, work, c, st);
+            break;
+        case 1:
+            if (radix) radix_class_launch<512>(bound, ranges, order, keys, ids, counters, work, c, st);
+            else sort_class_launch<512>(bound, ranges, order, keys, ids, counters, work, c, st);
+            break;
+        case 2:
+            if (radix) radix_class_launch<256>(bound, ranges, order, keys, ids, counters, work, c, st);
+            else sort_class_launch<256>(bound, ranges, order, keys, ids, counters, work, c, st);
+            break;
+        case 3:
+            if (radix) radix_class_launch<128>(bound, ranges, order, keys, ids, counters, work, c, st);
+            else sort_class_launch<128>(bound, ranges, order, keys, ids, counters, work, c, st);
+            break;
+        case 4:
+            if (radix) radix_class_launch<64>(bound, ranges, order, keys, ids, counters, work, c, st);
+            else sort_class_launch<64>(bound, ranges, order, keys, ids, counters, work, c, st);
+            break;
+        default:
+            sort_class_launch<32>(bound, ranges, order, keys, ids, counters, work, c, st);
+            break;
+    }
+    return 1;
+}
+
+uint32_t sort_class_bound(const uint32_t* class_tiles, bool exact, int c, int tiles) {
+    if (class_tiles && exact) return class_tiles[c];
+    if (class_tiles) return class_tiles[c] + class_tiles[c] / 4 + 1;
+    return (uint32_t)tiles;
+}
+
 int launch_tile_sort(const uint2* ranges, const uint32_t* order, const uint32_t* class_tiles,
                      bool exact, int tiles, const unsigned long long* keys, uint32_t* ids,
                      const DevCounters* counters, uint32_t* work, int radix_classes,
@@ -677,41 +717,9 @@ int launch_tile_sort(const uint2* ranges, const uint32_t* order, const uint32_t*
     // tails overlap; with `work` blocks take tiles dynamically.
     int launches = 0;
     for (int c = 0; c < kSortClasses; ++c) {
-        uint32_t bound = (uint32_t)tiles;
-        if (class_tiles && exact) {
-            bound = class_tiles[c];
-            if (bound == 0) continue;
-        } else if (class_tiles) {
-            bound = class_tiles[c] + class_tiles[c] / 4 + 1;
-        }
-        const bool radix = c < radix_classes;
         const cudaStream_t st = c == 0 ? streams[1] : c >= 4 ? streams[2] : streams[0];
-        switch (c) {
-            case 0:
-                if (radix) radix_class_launch<1024>(bound, ranges, order, keys, ids, counters, work, c, st);
-                else sort_class_launch<1024>(bound, ranges, order, keys, ids, counters, work, c, st);
-                break;
-            case 1:
-                if (radix) radix_class_launch<512>(bound, ranges, order, keys, ids, counters, work, c, st);
-                else sort_class_launch<512>(bound, ranges, order, keys, ids, counters, work, c, st);
-                break;
-            case 2:
-                if (radix) radix_class_launch<256>(bound, ranges, order, keys, ids, counters, work, c, st);
-                else sort_class_launch<256>(bound, ranges, order, keys, ids, counters, work, c, st);
-                break;
-            case 3:
-                if (radix) radix_class_launch<128>(bound, ranges, order, keys, ids, counters, work, c, st);
-                else sort_class_launch<128>(bound, ranges, order, keys, ids, counters, work, c, st);
-                break;
-            case 4:
-                if (radix) radix_class_launch<64>(bound, ranges, order, keys, ids, counters, work, c, st);
-                else sort_class_launch<64>(bound, ranges, order, keys, ids, counters, work, c, st);
-                break;
-            default:
-                sort_class_launch<32>(bound, ranges, order, keys, ids, counters, work, c, st);
-                break;
-        }
-        ++launches;
+        launches += launch_tile_sort_class(c, sort_class_bound(class_tiles, exact, c, tiles), ranges,
+                                           order, keys, ids, counters, work, radix_classes, st);
     }
     return launches;
 }

@@ -87,11 +87,12 @@ template <int MODE> struct Accumulates { static constexpr bool value = MODE >= k
 // gather them. Every mode walks the same lists with the same arithmetic, so
 // the weights alpha_i T_i of the gradient are those of the image.
 template <int BATCH, int MODE>
-__global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
-    blend_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
-                 const uint32_t* __restrict__ ids, const float4* __restrict__ rec, int width,
-                 int height, int tiles_x, float bg0, float bg1, float bg2, float* __restrict__ image,
-                 float* __restrict__ final_T, DevCounters* __restrict__ ctr, BlendExtra ex) {
+__device__ __forceinline__ void blend_tile(const int tile, const uint2* __restrict__ ranges,
+                                           const uint32_t* __restrict__ ids,
+                                           const float4* __restrict__ rec, int width, int height,
+                                           int tiles_x, float bg0, float bg1, float bg2,
+                                           float* __restrict__ image, float* __restrict__ final_T,
+                                           DevCounters* __restrict__ ctr, const BlendExtra& ex) {
     static_assert(BATCH == 128 || BATCH == 256, "blend batch");
     // exponent polynomial A x^2 + B x y + C y^2 + D x + E y + F in the
     // tile-centred pixel coordinates
@@ -107,7 +108,6 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
     __shared__ float s_g[kAcc ? 3 * BATCH : 1];
     __shared__ float s_loss[MODE == kBlendGrad ? kBlendThreads / 32 : 1];
 
-    const int tile = (int)order[blockIdx.x];
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = lane >> 3;                // 4x2-pixel group inside the warp's 8x4 sub-tile
@@ -354,11 +354,45 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
     if (threadIdx.x == 0 && ctr) atomicAdd(&ctr->pairs_read, (unsigned long long)(fetched - begin));
 }
 
+// One CTA per tile of the tile order.
+template <int BATCH, int MODE>
+__global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
+    blend_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+                 const uint32_t* __restrict__ ids, const float4* __restrict__ rec, int width,
+                 int height, int tiles_x, float bg0, float bg1, float bg2,
+                 float* __restrict__ image, float* __restrict__ final_T,
+                 DevCounters* __restrict__ ctr, BlendExtra ex) {
+    blend_tile<BATCH, MODE>((int)order[blockIdx.x], ranges, ids, rec, width, height, tiles_x, bg0,
+                            bg1, bg2, image, final_T, ctr, ex);
+}
+
+// The tiles of per-tile sort class cls (a contiguous run of the tile order),
+// or with cls == kSortClasses the empty tiles after them; the CTAs loop over
+// the run, so any grid covers it (colour mode).
+template <int BATCH>
+__global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
+    blend_class_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+                       const uint32_t* __restrict__ ids, const float4* __restrict__ rec,
+                       int width, int height, int tiles_x, int tiles, float bg0, float bg1,
+                       float bg2, float* __restrict__ image, float* __restrict__ final_T,
+                       DevCounters* __restrict__ ctr, int cls) {
+    uint32_t first = 0;
+    for (int c = 0; c < cls; ++c) first += ctr->class_tiles[c];
+    const uint32_t count = cls < kSortClasses ? ctr->class_tiles[cls] : (uint32_t)tiles - first;
+    const BlendExtra ex;
+    for (uint32_t item = blockIdx.x; item < count; item += gridDim.x) {
+        blend_tile<BATCH, kBlendColour>((int)order[first + item], ranges, ids, rec, width, height,
+                                        tiles_x, bg0, bg1, bg2, image, final_T, ctr, ex);
+        __syncthreads();
+    }
+}
+
 template <int MODE>
-static void blend_launch(int batch, int tiles, const uint2* ranges, const uint32_t* order,
+static void blend_launch(int batch, const uint2* ranges, const uint32_t* order,
                          const uint32_t* ids, const float4* rec, const DevCamera& cam,
                          const float bg[3], float* image, float* final_T, DevCounters* counters,
                          const BlendExtra& ex, cudaStream_t st) {
+    const int tiles = cam.tiles_x * cam.tiles_y;
     if (batch == 128)
         blend_kernel<128, MODE><<<tiles, kBlendThreads, 0, st>>>(
             ranges, order, ids, rec, cam.width, cam.height, cam.tiles_x, bg[0], bg[1], bg[2],
@@ -369,23 +403,39 @@ static void blend_launch(int batch, int tiles, const uint2* ranges, const uint32
             image, final_T, counters, ex);
 }
 
+int launch_blend_class(const uint2* ranges, const uint32_t* order, const uint32_t* ids,
+                       const float4* rec, const DevCamera& cam, const float bg[3], float* image,
+                       float* final_T, DevCounters* counters, int batch, int cls, int grid,
+                       cudaStream_t st) {
+    if (grid <= 0) return 0;
+    const int tiles = cam.tiles_x * cam.tiles_y;
+    if (batch == 128)
+        blend_class_kernel<128><<<grid, kBlendThreads, 0, st>>>(
+            ranges, order, ids, rec, cam.width, cam.height, cam.tiles_x, tiles, bg[0], bg[1],
+            bg[2], image, final_T, counters, cls);
+    else
+        blend_class_kernel<256><<<grid, kBlendThreads, 0, st>>>(
+            ranges, order, ids, rec, cam.width, cam.height, cam.tiles_x, tiles, bg[0], bg[1],
+            bg[2], image, final_T, counters, cls);
+    return 1;
+}
+
 int launch_blend(const uint2* ranges, const uint32_t* order, const uint32_t* ids, const float4* rec,
                  const DevCamera& cam, const float bg[3], float* image, float* final_T,
                  DevCounters* counters, int batch, const BlendExtra* extra, cudaStream_t st) {
-    const int tiles = cam.tiles_x * cam.tiles_y;
     BlendExtra ex;
     if (extra) ex = *extra;
     if (ex.grad_rgb && ex.cover)
-        blend_launch<kBlendCover>(batch, tiles, ranges, order, ids, rec, cam, bg, image, final_T,
-                                  nullptr, ex, st);
+        blend_launch<kBlendCover>(batch, ranges, order, ids, rec, cam, bg, image, final_T, nullptr,
+                                  ex, st);
     else if (ex.grad_rgb)
-        blend_launch<kBlendGrad>(batch, tiles, ranges, order, ids, rec, cam, bg, image, final_T,
-                                 nullptr, ex, st);
+        blend_launch<kBlendGrad>(batch, ranges, order, ids, rec, cam, bg, image, final_T, nullptr,
+                                 ex, st);
     else if (ex.depth)
-        blend_launch<kBlendDepth>(batch, tiles, ranges, order, ids, rec, cam, bg, image, final_T,
+        blend_launch<kBlendDepth>(batch, ranges, order, ids, rec, cam, bg, image, final_T,
                                   counters, ex, st);
     else
-        blend_launch<kBlendColour>(batch, tiles, ranges, order, ids, rec, cam, bg, image, final_T,
+        blend_launch<kBlendColour>(batch, ranges, order, ids, rec, cam, bg, image, final_T,
                                    counters, ex, st);
     return 1;
 }

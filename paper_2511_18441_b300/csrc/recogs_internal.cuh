@@ -225,6 +225,13 @@ int launch_scatter(const uint32_t* count, const uint2* rect, const uint32_t* zke
 // an earlier frame) or NULL; they only size the persistent grids. Classes
 // 0 .. radix_classes-1 (the largest tiles) are sorted by radix, the rest by
 // the bitonic network.
+// One class c of the per-tile sort with a grid for `bound` tiles (0: none).
+int launch_tile_sort_class(int c, uint32_t bound, const uint2* ranges, const uint32_t* order,
+                           const unsigned long long* keys, uint32_t* ids,
+                           const DevCounters* counters, uint32_t* work, int radix_classes,
+                           cudaStream_t st);
+// Grid bound of class c: the exact size, 1.25x a hinted size + 1, or `tiles`.
+uint32_t sort_class_bound(const uint32_t* class_tiles, bool exact, int c, int tiles);
 // work: per-class tile counters (dynamic tile assignment) or NULL (static);
 // streams[0..2]: see the definition (all three may be the same stream).
 int launch_tile_sort(const uint2* ranges, const uint32_t* order, const uint32_t* class_tiles,
@@ -291,6 +298,13 @@ int launch_mlp_decide(const recogs_scene& s, const DevCamera& cam, const DevRegi
 int launch_recolor_weighted(recogs_scene& s, const float* weights, const float M[9],
                             const float dc_fix[3], cudaStream_t st);
 
+// The blend of one per-tile sort class's tiles (cls < kSortClasses) or of
+// the empty tiles after them (cls == kSortClasses), colour mode, `grid` CTAs
+// looping over the run (any grid covers it).
+int launch_blend_class(const uint2* ranges, const uint32_t* order, const uint32_t* ids,
+                       const float4* rec, const DevCamera& cam, const float bg[3], float* image,
+                       float* final_T, DevCounters* counters, int batch, int cls, int grid,
+                       cudaStream_t st);
 // batch: Gaussians staged in shared memory per blend step, 128 or 256
 int launch_blend(const uint2* ranges, const uint32_t* order, const uint32_t* ids, const float4* rec,
                  const DevCamera& cam, const float bg[3], float* image, float* final_T,

@@ -98,13 +98,14 @@ def test_crowded_tile_without_read_back_is_reported(lib, ctx):
 
 @pytest.mark.parametrize("radix_classes", [0, 2, 5])
 @pytest.mark.parametrize("blend_batch", [128, 256])
-def test_schedules_give_identical_frames(lib, ctx, radix_classes, blend_batch):
+@pytest.mark.parametrize("overlap", [False, True])
+def test_schedules_give_identical_frames(lib, ctx, radix_classes, blend_batch, overlap):
     w = sg.paper_scale_workload(n=300_000, width=960, height=540)
     ds = dscene(lib, w.scene)
     img0, T0, st = render(ctx, ds, w.camera, w.edit, stats=True)
     r0, g0 = ctx.tile_lists(st["n_tiles"], st["n_pairs"])
     r0, g0 = parity.to_np(r0), parity.to_np(g0)
-    ctx.set_schedule(radix_classes, blend_batch)
+    ctx.set_schedule(radix_classes, blend_batch, overlap)
     img1, T1, st1 = render(ctx, ds, w.camera, w.edit, stats=True)
     r1, g1 = ctx.tile_lists(st1["n_tiles"], st1["n_pairs"])
     assert np.array_equal(r0, parity.to_np(r1)) and np.array_equal(g0, parity.to_np(g1))
