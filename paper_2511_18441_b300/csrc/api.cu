@@ -324,6 +324,7 @@ recogs_status dev_region(recogs_ctx* ctx, const recogs_region* r, const recogs_c
             d.xy[k] = r->xy[k];
         }
         d.n = r->n_vertices;
+        region_slopes(d);
     } else {
         return fail(ctx, RECOGS_EINVAL, "unknown region kind %d", r->kind);
     }

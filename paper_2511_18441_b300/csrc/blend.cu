@@ -30,21 +30,11 @@ __device__ __forceinline__ float exp2_approx(float x) {
 }
 
 // The region test of the plain selection at a pixel centre (box: half-open;
-// polygon: even-odd rule with the selection's arithmetic).
+// polygon: the selection's even-odd rule).
 __device__ __forceinline__ bool in_region(const DevRegion& r, float u, float v) {
     if (r.kind == RECOGS_REGION_BOX)
         return (u >= r.xy[0]) && (u < r.xy[2]) && (v >= r.xy[1]) && (v < r.xy[3]);
-    bool inside = false;
-    for (int i = 0, j = r.n - 1; i < r.n; j = i++) {
-        const float xi = r.xy[2 * i], yi = r.xy[2 * i + 1];
-        const float xj = r.xy[2 * j], yj = r.xy[2 * j + 1];
-        if ((yi > v) != (yj > v)) {
-            const float xc = __fadd_rn(xi, __fdiv_rn(__fmul_rn(__fsub_rn(v, yi), __fsub_rn(xj, xi)),
-                                                     __fsub_rn(yj, yi)));
-            if (u < xc) inside = !inside;
-        }
-    }
-    return inside;
+    return in_polygon(r, u, v);
 }
 
 // Group mask of a Gaussian with centre (u, v) in this tile's frame whose

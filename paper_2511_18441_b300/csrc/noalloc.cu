@@ -179,6 +179,7 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
                 return report(err, el, RECOGS_EINVAL, "polygon invalid");
             for (int k = 0; k < 2 * r.n_vertices; ++k) de.region.xy[k] = r.xy[k];
             de.region.n = r.n_vertices;
+            region_slopes(de.region);
         } else {
             return report(err, el, RECOGS_EINVAL, "unknown region kind %d", r.kind);
         }

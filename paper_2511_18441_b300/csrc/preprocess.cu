@@ -228,11 +228,13 @@ __device__ __forceinline__ float dot3c(float w0, float w1, float w2, float x, fl
     return p;
 }
 
-// (xh + xl) / (zh + zl) as hi + lo
-__device__ __forceinline__ float div2(float xh, float xl, float zh, float zl, float& lo) {
-    const float q = __fdiv_rn(xh, zh);
+// (xh + xl) / (zh + zl) as hi + lo, given rz ~ 1 / zh: the quotient's
+// residual xh - q zh is exact under FMA, so hi + lo carries the quotient to
+// ~2^-44 relative whatever the last bit of q.
+__device__ __forceinline__ float div2(float xh, float xl, float zh, float zl, float rz, float& lo) {
+    const float q = __fmul_rn(xh, rz);
     const float r = __fmaf_rn(-q, zh, xh);
-    lo = __fdiv_rn(__fsub_rn(__fadd_rn(r, xl), __fmul_rn(q, zl)), zh);
+    lo = __fmul_rn(__fsub_rn(__fadd_rn(r, xl), __fmul_rn(q, zl)), rz);
     return q;
 }
 
@@ -276,9 +278,9 @@ __device__ __forceinline__ uint32_t prep_one(int i, float mx, float my, float mz
     float A = 0.f, B = 0.f, Cc = 0.f, sa = 0.f, sc = 0.f;
     float qxh = 0.f, qxl = 0.f, qyh = 0.f, qyl = 0.f, u = 0.f, v = 0.f;
     if (valid) {
-        const float iz = 1.0f / tz;
-        qxh = div2(tx, txl, tz, tzl, qxl);
-        qyh = div2(ty, tyl, tz, tzl, qyl);
+        const float iz = rcp_approx(tz);
+        qxh = div2(tx, txl, tz, tzl, iz, qxl);
+        qyh = div2(ty, tyl, tz, tzl, iz, qyl);
         u = __fadd_rn(__fmaf_rn(cam.fx, qxh, cam.cx), __fmul_rn(cam.fx, qxl));
         v = __fadd_rn(__fmaf_rn(cam.fy, qyh, cam.cy), __fmul_rn(cam.fy, qyl));
         // Eq. 1 with the EWA projection: Sigma' = (J W R S)(J W R S)^T + 0.3 I.
@@ -312,7 +314,7 @@ __device__ __forceinline__ uint32_t prep_one(int i, float mx, float my, float mz
         const float det = a * c2 - b * b;
         valid = det > 0.f;
         if (valid) {
-            const float idet = 1.0f / det;
+            const float idet = rcp_approx(det);
             A = c2 * idet;
             B = -b * idet;
             Cc = a * idet;
@@ -346,19 +348,25 @@ __device__ __forceinline__ uint32_t prep_one(int i, float mx, float my, float mz
     float Y[16];
     sh_basis(dx, dy, dz, Y);
     float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-    if (sel) {
+    // one branch per warp: a warp with any selected lane recolours in every
+    // lane and keeps the unselected lanes' coefficients as read
+    if (__any_sync(__activemask(), sel)) {
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             float c0 = sh(3 * k), c1 = sh(3 * k + 1), c2 = sh(3 * k + 2);
-            recolor_triple(edit.M, c0, c1, c2);
+            float r0 = c0, r1 = c1, r2 = c2;
+            recolor_triple(edit.M, r0, r1, r2);
             if (k == 0) {
-                c0 = __fadd_rn(c0, edit.dc_fix[0]);
-                c1 = __fadd_rn(c1, edit.dc_fix[1]);
-                c2 = __fadd_rn(c2, edit.dc_fix[2]);
+                r0 = __fadd_rn(r0, edit.dc_fix[0]);
+                r1 = __fadd_rn(r1, edit.dc_fix[1]);
+                r2 = __fadd_rn(r2, edit.dc_fix[2]);
             }
-            f0 = fmaf(Y[k], to_f32(from_f32<T>(c0)), f0);
-            f1 = fmaf(Y[k], to_f32(from_f32<T>(c1)), f1);
-            f2 = fmaf(Y[k], to_f32(from_f32<T>(c2)), f2);
+            c0 = sel ? to_f32(from_f32<T>(r0)) : c0;
+            c1 = sel ? to_f32(from_f32<T>(r1)) : c1;
+            c2 = sel ? to_f32(from_f32<T>(r2)) : c2;
+            f0 = fmaf(Y[k], c0, f0);
+            f1 = fmaf(Y[k], c1, f1);
+            f2 = fmaf(Y[k], c2, f2);
         }
     } else {
 #pragma unroll
@@ -401,16 +409,18 @@ __device__ __forceinline__ void prep_chunk_end(int chunk, int n_chunks, uint32_t
     const unsigned full = 0xffffffffu;
     if (out.tile_count) {
         const uint32_t rounds = __reduce_max_sync(full, cnt);
+        // this lane's k-th tile, walked row by row through its rectangle
+        uint32_t row = (uint32_t)ry0 * (uint32_t)cam.tiles_x + (uint32_t)rx0, col = 0;
         for (uint32_t k = 0; k < rounds; ++k) {
-            uint32_t t = 0xffffffffu;
-            if (k < cnt) {
-                const uint32_t dy = k / (uint32_t)rw;
-                t = (uint32_t)(ry0 + (int)dy) * (uint32_t)cam.tiles_x + (uint32_t)rx0 + (k - dy * rw);
-            }
+            const uint32_t t = k < cnt ? row + col : 0xffffffffu;
             const uint32_t peers = __match_any_sync(full, t);
             if (t != 0xffffffffu && (threadIdx.x & 31) == __ffs(peers) - 1)
                 atomicAdd(&out.tile_count[(size_t)t * out.parts + (chunk & (out.parts - 1))],
                           (uint32_t)__popc(peers));
+            if (++col == (uint32_t)rw) {
+                col = 0;
+                row += (uint32_t)cam.tiles_x;
+            }
         }
     }
     // chunk totals of visible Gaussians and pairs; depth range of visible
@@ -448,13 +458,21 @@ __device__ __forceinline__ void prep_chunk_end(int chunk, int n_chunks, uint32_t
     }
 }
 
-// One block per chunk, every attribute loaded straight into registers (all
-// 48 SH coefficients up front, so that their loads are in flight together).
-// Resident blocks per SM the registers are held to: two for float32 SH
-// (the 48 coefficients held in registers need them), three for 16-bit SH
-// (measured: 0.227 ms against 0.280 ms with two at 3M Gaussians).
-template <typename T> struct PrepMinBlocks { static constexpr int value = 3; };
-template <> struct PrepMinBlocks<float> { static constexpr int value = 2; };
+// One block per chunk. The SH coefficients are read where Eq. 2 needs them,
+// after the projection and the culling tests (a culled Gaussian reads none),
+// so they are not held in registers across the geometry; the kernel runs at
+// 48-64 registers and four resident blocks (32 warps) per SM, whose
+// geometry work overlaps the other warps' SH reads. Measured at 3M Gaussians
+// against loading all 48 coefficients up front (124 registers, 2 blocks):
+// 0.172 against 0.206 ms (float32 SH), 0.180 against 0.216 ms (BF16).
+#ifndef RECOGS_PREP_MIN_BLOCKS_F32
+#define RECOGS_PREP_MIN_BLOCKS_F32 4
+#endif
+#ifndef RECOGS_PREP_MIN_BLOCKS_16
+#define RECOGS_PREP_MIN_BLOCKS_16 4
+#endif
+template <typename T> struct PrepMinBlocks { static constexpr int value = RECOGS_PREP_MIN_BLOCKS_16; };
+template <> struct PrepMinBlocks<float> { static constexpr int value = RECOGS_PREP_MIN_BLOCKS_F32; };
 
 template <typename T>
 __global__ void __launch_bounds__(kPrepThreads, PrepMinBlocks<T>::value)
@@ -472,14 +490,13 @@ __global__ void __launch_bounds__(kPrepThreads, PrepMinBlocks<T>::value)
     float4 r3[3];
     r3[0] = r3[1] = r3[2] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i < n) {
-        float C[48];
-#pragma unroll
-        for (int k = 0; k < 48; ++k) C[k] = to_f32(sh[(size_t)k * n + i]);
+        const T* shi = sh + i;
         cnt = prep_one<T>(i, __ldg(xyz + i), __ldg(xyz + n + i), __ldg(xyz + 2 * n + i),
                           __ldg(lsc + i), __ldg(lsc + n + i), __ldg(lsc + 2 * n + i),
                           __ldg(quat + i), __ldg(quat + n + i), __ldg(quat + 2 * n + i),
                           __ldg(quat + 3 * n + i), __ldg(opl + i),
-                          [&](int r) { return C[r]; }, cam, edit, out, r3, zbits, rx0, ry0, rw);
+                          [&](int r) { return to_f32(shi[(size_t)r * n]); }, cam, edit, out, r3,
+                          zbits, rx0, ry0, rw);
         out.count[i] = cnt;
         out.zkey[i] = zbits;
     }

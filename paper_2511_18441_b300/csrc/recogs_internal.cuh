@@ -38,7 +38,23 @@ struct DevRegion {
     int n;               // polygon vertices
     float eps;           // near-boundary width in px
     float xy[2 * RECOGS_MAX_POLYGON];
+    // polygon edge i runs from vertex i to vertex i - 1 (mod n); slope[i] =
+    // dx / dy of that edge (0 for a horizontal edge, which never crosses)
+    float slope[RECOGS_MAX_POLYGON];
 };
+
+// Fills DevRegion::slope from the vertices (host side). The differences are
+// rounded to float first, as the kernels would form them, and the quotient
+// is rounded once.
+inline void region_slopes(DevRegion& d) {
+    if (d.kind != RECOGS_REGION_POLYGON) return;
+    for (int i = 0; i < d.n; ++i) {
+        const int j = i == 0 ? d.n - 1 : i - 1;
+        const float dx = d.xy[2 * j] - d.xy[2 * i];
+        const float dy = d.xy[2 * j + 1] - d.xy[2 * i + 1];
+        d.slope[i] = dy != 0.0f ? (float)((double)dx / (double)dy) : 0.0f;
+    }
+}
 
 struct DevEdit {
     int enabled;
@@ -99,6 +115,29 @@ __device__ __forceinline__ void view_point(const DevCamera& c, float x, float y,
     tz = __fadd_rn(__fmaf_rn(c.W[8], z, __fmaf_rn(c.W[7], y, __fmul_rn(c.W[6], x))), c.t[2]);
 }
 
+// Approximate reciprocal (PTX rcp.approx: relative error within 2^-23).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Even-odd rule at (u, v) (Sec. 3.2.1 stand-in): edge i counts when one end
+// is above the line v and the other is not, and the crossing
+// x = x_i + (v - y_i) slope_i lies to the right of u. Branch-free per edge.
+__device__ __forceinline__ bool in_polygon(const DevRegion& r, float u, float v) {
+    bool inside = false;
+    bool above_j = r.xy[2 * (r.n - 1) + 1] > v;
+    for (int i = 0; i < r.n; ++i) {
+        const float xi = r.xy[2 * i], yi = r.xy[2 * i + 1];
+        const bool above_i = yi > v;
+        const float xc = __fmaf_rn(__fsub_rn(v, yi), r.slope[i], xi);
+        inside ^= (above_i != above_j) && (u < xc);
+        above_j = above_i;
+    }
+    return inside;
+}
+
 // Selection of one centre (Sec. 3.2.1 stand-in): in front of the camera and
 // inside the region. near_out: within eps px of the boundary, or depth ~ 0.
 __device__ __forceinline__ bool select_centre(const DevCamera& c, const DevRegion& r, float x,
@@ -109,26 +148,20 @@ __device__ __forceinline__ bool select_centre(const DevCamera& c, const DevRegio
     bool near_b = fabsf(tz) <= 1e-6f * zs;
     bool in = false;
     if (tz > 0.0f) {
-        float u = __fmaf_rn(c.fx, __fdiv_rn(tx, tz), c.cx);
-        float v = __fmaf_rn(c.fy, __fdiv_rn(ty, tz), c.cy);
+        const float iz = rcp_approx(tz);
+        float u = __fmaf_rn(c.fx, __fmul_rn(tx, iz), c.cx);
+        float v = __fmaf_rn(c.fy, __fmul_rn(ty, iz), c.cy);
         if (r.kind == RECOGS_REGION_BOX) {
             in = (u >= r.xy[0]) && (u < r.xy[2]) && (v >= r.xy[1]) && (v < r.xy[3]);
             if (near_out)
                 near_b = near_b || fabsf(u - r.xy[0]) <= r.eps || fabsf(u - r.xy[2]) <= r.eps ||
                          fabsf(v - r.xy[1]) <= r.eps || fabsf(v - r.xy[3]) <= r.eps;
         } else if (r.kind == RECOGS_REGION_POLYGON) {
-            // even-odd rule: an edge counts when one end is above the line v and
-            // the other is not, and the crossing lies to the right of u
-            bool inside = false;
-            for (int i = 0, j = r.n - 1; i < r.n; j = i++) {
-                float xi = r.xy[2 * i], yi = r.xy[2 * i + 1];
-                float xj = r.xy[2 * j], yj = r.xy[2 * j + 1];
-                if ((yi > v) != (yj > v)) {
-                    float xc = __fadd_rn(xi, __fdiv_rn(__fmul_rn(__fsub_rn(v, yi), __fsub_rn(xj, xi)),
-                                                       __fsub_rn(yj, yi)));
-                    if (u < xc) inside = !inside;
-                }
-                if (near_out) {
+            in = in_polygon(r, u, v);
+            if (near_out) {
+                for (int i = 0, j = r.n - 1; i < r.n; j = i++) {
+                    const float xi = r.xy[2 * i], yi = r.xy[2 * i + 1];
+                    const float xj = r.xy[2 * j], yj = r.xy[2 * j + 1];
                     float ex = xi - xj, ey = yi - yj;
                     float l2 = ex * ex + ey * ey;
                     float s = l2 > 0.f ? ((u - xj) * ex + (v - yj) * ey) / l2 : 0.f;
@@ -137,7 +170,6 @@ __device__ __forceinline__ bool select_centre(const DevCamera& c, const DevRegio
                     near_b = near_b || (dx * dx + dy * dy <= r.eps * r.eps);
                 }
             }
-            in = inside;
         }
     }
     if (near_out) *near_out = near_b;
