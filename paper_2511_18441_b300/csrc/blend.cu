@@ -76,6 +76,12 @@ template <int MODE> struct Accumulates { static constexpr bool value = MODE >= k
 // BATCH (128 or 256) Gaussians are staged per batch; threads below BATCH
 // gather them. Every mode walks the same lists with the same arithmetic, so
 // the weights alpha_i T_i of the gradient are those of the image.
+//
+// Hit lists: after staging, each warp writes, for each of its four pixel
+// groups, the batch's Gaussians whose box meets the group, in depth order, as
+// byte offsets into the staged arrays (u16), padded with the offset of a
+// sentinel entry whose alpha is 0. The four groups then walk their lists in
+// lockstep for as many steps as the longest list of the batch.
 template <int BATCH, int MODE>
 __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restrict__ ranges,
                                            const uint32_t* __restrict__ ids,
@@ -85,18 +91,17 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
                                            DevCounters* __restrict__ ctr, const BlendExtra& ex) {
     static_assert(BATCH == 128 || BATCH == 256, "blend batch");
     // exponent polynomial A x^2 + B x y + C y^2 + D x + E y + F in the
-    // tile-centred pixel coordinates
-    __shared__ float4 s_a[BATCH];     // (A, B, C, D)
-    __shared__ float4 s_b[BATCH];     // (E, F, r, g)
-    __shared__ float s_c[BATCH];      // b
-    __shared__ uint32_t s_m[BATCH];   // group mask
-    // depth mode: view depth of each staged Gaussian; gradient mode: its index
-    // and its colour gradient summed over this tile's pixels
-    __shared__ float s_z[MODE == kBlendDepth ? BATCH : 1];
+    // tile-centred pixel coordinates; entry BATCH is the sentinel
+    __shared__ float4 s_a[BATCH + 1];     // (A, B, C, D)
+    __shared__ float4 s_b[BATCH + 1];     // (E, F, r, g)
+    __shared__ float4 s_c[BATCH + 1];     // (b, view depth, Gaussian index bits, 0)
+    __shared__ uint32_t s_m[BATCH];       // group mask (0 past the batch's end)
+    __shared__ __align__(16) uint16_t s_list[32 * BATCH];   // per group: BATCH byte offsets
+    // gradient mode: each staged Gaussian's colour gradient summed over this tile's pixels
     constexpr bool kAcc = Accumulates<MODE>::value;
-    __shared__ uint32_t s_id[kAcc ? BATCH : 1];
     __shared__ float s_g[kAcc ? 3 * BATCH : 1];
     __shared__ float s_loss[MODE == kBlendGrad ? kBlendThreads / 32 : 1];
+    constexpr uint32_t kSent = 16u * BATCH;   // byte offset of the sentinel
 
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -110,8 +115,8 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
     // monomials of the exponent polynomial
     const float fpx = (float)lx - 7.5f, fpy = (float)ly - 7.5f;
     const float fxx = fpx * fpx, fxy = fpx * fpy, fyy = fpy * fpy;
-    const int mbit = 4 * warp + (grp & 1) + 2 * (grp >> 1);   // this lane's group bit
     const size_t pix = (size_t)py * width + px;
+    uint16_t* const my_list = s_list + (4 * warp + grp) * BATCH;
 
     uint2 rg = ranges[tile];
     if (ctr && ctr->skip) rg = make_uint2(0u, 0u);  // pairs exceed the buffers: background only
@@ -144,6 +149,12 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
     }
     if (kAcc)
         for (int k = threadIdx.x; k < 3 * BATCH; k += kBlendThreads) s_g[k] = 0.f;
+    if (threadIdx.x == 0) {
+        // alpha = 2^-inf = 0: never taken
+        s_a[BATCH] = make_float4(0.f, 0.f, 0.f, 0.f);
+        s_b[BATCH] = make_float4(0.f, -INFINITY, 0.f, 0.f);
+        s_c[BATCH] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 
     // prefetch the first batch
     float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra;
@@ -162,7 +173,7 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
         if (!kAcc) return;
         const int k = threadIdx.x;
         if (gatherer && prev_b + k < end) {
-            const uint32_t id = s_id[k];
+            const uint32_t id = __float_as_uint(s_c[k].z);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const float v = s_g[3 * k + c];
@@ -180,6 +191,44 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
         return v;
     };
 
+    // one staged Gaussian at byte offset o against this lane's pixel
+    auto blend_one = [&](uint32_t o) {
+        const float4 a = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(s_a) + o);
+        const float4 b = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(s_b) + o);
+        const float4 c = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(s_c) + o);
+        // exponent <= 0 up to rounding (a positive-definite conic): no clamp
+        const float p = fmaf(a.x, fxx, fmaf(a.y, fxy, fmaf(a.z, fyy, fmaf(a.w, fpx, fmaf(b.x, fpy, b.y)))));
+        const float al = fminf(0.99f, exp2_approx(p));
+        const float wt = al * T;
+        const float nT = T - wt;
+        const bool take = !done && al >= a_min;
+        const bool stop = take && nT < 1e-4f;
+        const bool add = take && !stop;
+        const float w = add ? wt : 0.0f;
+        if (!kAcc) {
+            cr = fmaf(b.z, w, cr);
+            cg = fmaf(b.w, w, cg);
+            cb = fmaf(c.x, w, cb);
+        } else {
+            // gradient: g alpha T; coverage: g (alpha T)^2
+            const float wc = MODE == kBlendCover ? w * w : w;
+            const float v0 = group_sum(g0 * wc), v1 = group_sum(g1 * wc);
+            const float v2 = group_sum(g2 * w);
+            if ((lane & 7) == 0 && o != kSent) {
+                const uint32_t sl = o >> 4;
+                atomicAdd(&s_g[3 * sl + 0], v0);
+                atomicAdd(&s_g[3 * sl + 1], v1);
+                atomicAdd(&s_g[3 * sl + 2], v2);
+            }
+        }
+        if (MODE == kBlendDepth && add && !crossed && nT < ex.tau) {
+            dz = c.y;
+            crossed = true;
+        }
+        T = add ? nT : T;
+        done = done || stop;
+    };
+
     uint32_t prev_b = 0xffffffffu;
     for (uint32_t b = begin; b < end; b += BATCH) {
         const int n_done = __syncthreads_count(done);
@@ -188,24 +237,28 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
             prev_b = 0xffffffffu;
             break;
         }
-        if (gatherer && b + threadIdx.x < end) {
-            // move the centre from its first tile's frame into this tile's frame
-            const uint32_t o = __float_as_uint(rc.w);
-            const float u = ra.x + (float)(kTile * ((int)(o & 0xffffu) - tx));
-            const float v = ra.y + (float)(kTile * ((int)(o >> 16) - ty));
-            // the exponent q0 du^2 + q1 du dv + q2 dv^2 + log2 sigma (du = x - u,
-            // dv = y - v) as a polynomial in the centred pixel coordinates
-            const float uc = u - 7.5f, vc = v - 7.5f;
-            const float q0 = ra.z, q1 = ra.w, q2 = rb.x;
-            const float D = -fmaf(2.0f * q0, uc, q1 * vc);
-            const float E = -fmaf(2.0f * q2, vc, q1 * uc);
-            const float F = fmaf(uc, fmaf(q0, uc, q1 * vc), fmaf(q2 * vc, vc, rb.y));
-            s_a[threadIdx.x] = make_float4(q0, q1, q2, D);
-            s_b[threadIdx.x] = make_float4(E, F, rc.x, rc.y);
-            s_c[threadIdx.x] = rc.z;
-            s_m[threadIdx.x] = group_mask(u, v, rb.z, rb.w);
-            if (MODE == kBlendDepth) s_z[threadIdx.x] = __uint_as_float(__ldg(ex.zkey + rid));
-            if (kAcc) s_id[threadIdx.x] = rid;
+        if (gatherer) {
+            uint32_t gm = 0u;
+            if (b + threadIdx.x < end) {
+                // move the centre from its first tile's frame into this tile's frame
+                const uint32_t o = __float_as_uint(rc.w);
+                const float u = ra.x + (float)(kTile * ((int)(o & 0xffffu) - tx));
+                const float v = ra.y + (float)(kTile * ((int)(o >> 16) - ty));
+                // the exponent q0 du^2 + q1 du dv + q2 dv^2 + log2 sigma (du = x - u,
+                // dv = y - v) as a polynomial in the centred pixel coordinates
+                const float uc = u - 7.5f, vc = v - 7.5f;
+                const float q0 = ra.z, q1 = ra.w, q2 = rb.x;
+                const float D = -fmaf(2.0f * q0, uc, q1 * vc);
+                const float E = -fmaf(2.0f * q2, vc, q1 * uc);
+                const float F = fmaf(uc, fmaf(q0, uc, q1 * vc), fmaf(q2 * vc, vc, rb.y));
+                s_a[threadIdx.x] = make_float4(q0, q1, q2, D);
+                s_b[threadIdx.x] = make_float4(E, F, rc.x, rc.y);
+                s_c[threadIdx.x] = make_float4(rc.z,
+                                               MODE == kBlendDepth ? __uint_as_float(__ldg(ex.zkey + rid)) : 0.f,
+                                               __uint_as_float(rid), 0.f);
+                gm = group_mask(u, v, rb.z, rb.w);
+            }
+            s_m[threadIdx.x] = gm;
         }
         fetched = min(end, b + BATCH);
         prev_b = b;
@@ -218,98 +271,42 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
             rb = __ldg(rec + 3 * (size_t)rid + 1);
             rc = __ldg(rec + 3 * (size_t)rid + 2);
         }
-        const int cnt = (int)min((uint32_t)BATCH, end - b);
         if (__all_sync(0xffffffffu, done)) continue;
+        const int cnt = (int)min((uint32_t)BATCH, end - b);
+        // this warp's four lists: sentinel everywhere, then the hits in order
+        {
+            uint4* w4 = reinterpret_cast<uint4*>(s_list + 4 * warp * BATCH);
+            const uint4 sent4 = make_uint4(kSent | kSent << 16, kSent | kSent << 16,
+                                           kSent | kSent << 16, kSent | kSent << 16);
+#pragma unroll
+            for (int k = lane; k < BATCH / 2; k += 32) w4[k] = sent4;
+        }
+        __syncwarp();
+        int n_mine = 0;
+        const int q = lane & 7;   // this lane writes bits 4q .. 4q+3 of its group's mask
 #pragma unroll 1
-        for (int g = 0; g * 32 < cnt; ++g) {
-            // candidates g*32 .. g*32+31: one ballot per group of this warp
-            const int sl = g * 32 + lane;
-            const uint32_t gm = sl < cnt ? (s_m[sl] >> (4 * warp)) : 0u;
+        for (int c0 = 0; c0 < cnt; c0 += 32) {
+            const uint32_t gm = s_m[c0 + lane] >> (4 * warp);
             const uint32_t m0 = __ballot_sync(0xffffffffu, gm & 1u);
             const uint32_t m1 = __ballot_sync(0xffffffffu, gm & 2u);
             const uint32_t m2 = __ballot_sync(0xffffffffu, gm & 4u);
             const uint32_t m3 = __ballot_sync(0xffffffffu, gm & 8u);
-            const int gb = mbit - 4 * warp;
-            uint32_t m = gb == 0 ? m0 : gb == 1 ? m1 : gb == 2 ? m2 : m3;
-            // the four groups walk their own lists in lockstep; lanes whose list
-            // is exhausted (or whose pixel has stopped) carry weight 0
-            const int iters = (int)__reduce_max_sync(0xffffffffu, (uint32_t)__popc(m));
+            const uint32_t m = grp == 0 ? m0 : grp == 1 ? m1 : grp == 2 ? m2 : m3;
+            const uint32_t part = (m >> (4 * q)) & 0xfu;
+            int pos = n_mine + __popc(m & ((1u << (4 * q)) - 1u));
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (part & (1u << t)) my_list[pos++] = (uint16_t)(16 * (c0 + 4 * q + t));
+            n_mine += __popc(m);
+        }
+        __syncwarp();
+        const int iters = (int)__reduce_max_sync(0xffffffffu, (uint32_t)n_mine);
+        const uint32_t* my2 = reinterpret_cast<const uint32_t*>(my_list);
 #pragma unroll 1
-            for (int k = 0; k < iters; k += 2) {
-                const bool act0 = m != 0u;
-                const int s0 = g * 32 + (act0 ? __ffs(m) - 1 : 0);
-                m &= m - 1;
-                const bool act1 = m != 0u;
-                const int s1 = g * 32 + (act1 ? __ffs(m) - 1 : 0);
-                m &= m - 1;
-                const float4 a0 = s_a[s0], b0 = s_b[s0];
-                const float4 a1 = s_a[s1], b1 = s_b[s1];
-                // exponent <= 0 up to rounding (a positive-definite conic): no clamp
-                const float p0 = fmaf(a0.x, fxx, fmaf(a0.y, fxy, fmaf(a0.z, fyy,
-                                 fmaf(a0.w, fpx, fmaf(b0.x, fpy, b0.y)))));
-                const float p1 = fmaf(a1.x, fxx, fmaf(a1.y, fxy, fmaf(a1.z, fyy,
-                                 fmaf(a1.w, fpx, fmaf(b1.x, fpy, b1.y)))));
-                const float al0 = fminf(0.99f, exp2_approx(p0));
-                const float al1 = fminf(0.99f, exp2_approx(p1));
-                {
-                    const float wt = al0 * T;
-                    const float nT = T - wt;
-                    const bool take = act0 && !done && al0 >= a_min;
-                    const bool stop = take && nT < 1e-4f;
-                    const bool add = take && !stop;
-                    const float w = add ? wt : 0.0f;
-                    if (!kAcc) {
-                        cr = fmaf(b0.z, w, cr);
-                        cg = fmaf(b0.w, w, cg);
-                        cb = fmaf(s_c[s0], w, cb);
-                    } else {
-                        // gradient: g alpha T; coverage: g (alpha T)^2
-                        const float wc = MODE == kBlendCover ? w * w : w;
-                        const float v0 = group_sum(g0 * wc), v1 = group_sum(g1 * wc);
-                        const float v2 = group_sum(g2 * w);
-                        if ((lane & 7) == 0 && act0) {
-                            atomicAdd(&s_g[3 * s0 + 0], v0);
-                            atomicAdd(&s_g[3 * s0 + 1], v1);
-                            atomicAdd(&s_g[3 * s0 + 2], v2);
-                        }
-                    }
-                    if (MODE == kBlendDepth && add && !crossed && nT < ex.tau) {
-                        dz = s_z[s0];
-                        crossed = true;
-                    }
-                    T = add ? nT : T;
-                    done = done || stop;
-                }
-                {
-                    const float wt = al1 * T;
-                    const float nT = T - wt;
-                    const bool take = act1 && !done && al1 >= a_min;
-                    const bool stop = take && nT < 1e-4f;
-                    const bool add = take && !stop;
-                    const float w = add ? wt : 0.0f;
-                    if (!kAcc) {
-                        cr = fmaf(b1.z, w, cr);
-                        cg = fmaf(b1.w, w, cg);
-                        cb = fmaf(s_c[s1], w, cb);
-                    } else {
-                        // gradient: g alpha T; coverage: g (alpha T)^2
-                        const float wc = MODE == kBlendCover ? w * w : w;
-                        const float v0 = group_sum(g0 * wc), v1 = group_sum(g1 * wc);
-                        const float v2 = group_sum(g2 * w);
-                        if ((lane & 7) == 0 && act1) {
-                            atomicAdd(&s_g[3 * s1 + 0], v0);
-                            atomicAdd(&s_g[3 * s1 + 1], v1);
-                            atomicAdd(&s_g[3 * s1 + 2], v2);
-                        }
-                    }
-                    if (MODE == kBlendDepth && add && !crossed && nT < ex.tau) {
-                        dz = s_z[s1];
-                        crossed = true;
-                    }
-                    T = add ? nT : T;
-                    done = done || stop;
-                }
-            }
+        for (int k = 0; k < iters; k += 2) {
+            const uint32_t pr = my2[k >> 1];
+            blend_one(pr & 0xffffu);
+            blend_one(pr >> 16);
             if (__all_sync(0xffffffffu, done)) break;
         }
     }
