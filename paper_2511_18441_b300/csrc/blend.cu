@@ -2,22 +2,22 @@
 // Sec. 3.1) with HWC output (Sec. 4.2).
 //
 // One CTA of 256 threads per 16x16 tile, one thread per pixel; tiles are
-// launched heaviest first (the tile order of the tile scan). Each warp owns an 8x4-pixel
-// sub-tile made of four 4x2-pixel groups of 8 lanes. Each batch of up to 256
-// (or 128) depth-sorted Gaussians is gathered by one thread per Gaussian (the next
-// batch is prefetched into registers while the current one is blended) and
-// staged in shared memory with a 32-bit mask of the groups its alpha >= 1/255
-// box meets. The four groups of a warp then walk their own hit lists in
-// depth order in lockstep (same instructions, a different Gaussian per
-// group), so a warp iterates as often as its busiest group, not as often as
-// the union of its groups' lists. Pixels stop at the transmittance cut-off, a
-// warp stops when all its pixels have, and the CTA stops fetching when every
-// pixel has.
+// launched heaviest first (the tile order of the tile scan). Each warp owns an
+// 8x4-pixel sub-tile made of four 4x2-pixel groups of 8 lanes. Each batch of
+// up to 256 (or 128) depth-sorted Gaussians is gathered by one thread per
+// Gaussian (the next batch is prefetched into registers while the current one
+// is blended) and staged in shared memory with a 32-bit mask of the groups its
+// alpha >= 1/255 box meets. Each warp then lists, per group, the staged
+// Gaussians that meet it, and the four groups walk their own lists in depth
+// order in lockstep (same instructions, a different Gaussian per group), so a
+// warp iterates as often as its busiest group, not as often as the union of
+// its groups' lists. Pixels stop at the transmittance cut-off, a warp stops
+// when all its pixels have, and the CTA stops fetching when every pixel has.
 #include "recogs_internal.cuh"
 
 // Resident CTAs per SM the register allocation is held to (a tuning knob).
 #ifndef RECOGS_BLEND_MIN_BLOCKS
-#define RECOGS_BLEND_MIN_BLOCKS 6
+#define RECOGS_BLEND_MIN_BLOCKS 4
 #endif
 
 namespace recogs {
@@ -55,11 +55,15 @@ __device__ __forceinline__ uint32_t group_mask(float u, float v, float ex, float
     const float r1 = fminf(floorf((v + ey) * 0.5f), 7.0f);
     if (!(c0 <= c1) || !(r0 <= r1)) return 0u;
     const int ic0 = (int)c0, ic1 = (int)c1, ir0 = (int)r0, ir1 = (int)r1;
-    uint32_t mask = 0u;
-    for (int r = ir0; r <= ir1; ++r)
-        for (int c = ic0; c <= ic1; ++c)
-            mask |= 1u << (4 * ((c >> 1) + 2 * (r >> 1)) + (c & 1) + 2 * (r & 1));
-    return mask;
+    // bit of group (c, r) = cpos(c) + rpos(r), cpos(c) = 4 (c >> 1) + (c & 1),
+    // rpos(r) = 8 (r >> 1) + 2 (r & 1): all such sums are distinct, so the
+    // product of the column bits X and the row bits Y sets exactly the bits of
+    // the rectangle (no carries)
+    const int cp0 = ic0 + 2 * (ic0 >> 1), cp1 = ic1 + 2 * (ic1 >> 1);
+    const int rp0 = 2 * ir0 + 4 * (ir0 >> 1), rp1 = 2 * ir1 + 4 * (ir1 >> 1);
+    const uint32_t X = 0x33u & (0xffffffffu << cp0) & ((2u << cp1) - 1u);
+    const uint32_t Y = 0x05050505u & (0xffffffffu << rp0) & ((2u << rp1) - 1u);
+    return X * Y;
 }
 
 // What a blend launch computes besides the walk itself.
@@ -301,12 +305,15 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
         }
         __syncwarp();
         const int iters = (int)__reduce_max_sync(0xffffffffu, (uint32_t)n_mine);
-        const uint32_t* my2 = reinterpret_cast<const uint32_t*>(my_list);
+        // four hits per step (one 8-byte read of four offsets), then the warp's exit test
+        const uint2* my4 = reinterpret_cast<const uint2*>(my_list);
 #pragma unroll 1
-        for (int k = 0; k < iters; k += 2) {
-            const uint32_t pr = my2[k >> 1];
-            blend_one(pr & 0xffffu);
-            blend_one(pr >> 16);
+        for (int k = 0; k < iters; k += 4) {
+            const uint2 pr = my4[k >> 2];
+            blend_one(pr.x & 0xffffu);
+            blend_one(pr.x >> 16);
+            blend_one(pr.y & 0xffffu);
+            blend_one(pr.y >> 16);
             if (__all_sync(0xffffffffu, done)) break;
         }
     }
