@@ -5,9 +5,9 @@
 // kTileParts counter partitions). An exclusive scan over tiles gives each
 // tile's range in the pair array. Every visible Gaussian then writes the
 // 64-bit key (depth bits << 32 | index) of each of its pairs into its tiles'
-// ranges through per-tile cursors (block-aggregated atomics: arbitrary order
-// inside a range), and one CTA per tile sorts its range with a bitonic
-// network held in registers. The result is
+// ranges through per-tile cursors (warp-aggregated atomics: arbitrary order
+// inside a range), and one CTA per tile sorts its range (shared-memory radix
+// sort, or a bitonic network in registers for small tiles). The result is
 // every tile's list in (float32 depth, index) order -- the order a stable LSD
 // radix sort of (tile, depth) keys of index-ordered pairs produces -- without
 // sorting all pairs globally. Tiles with more pairs than shared memory holds
@@ -176,19 +176,15 @@ int launch_tile_scan(const uint32_t* totals, int tiles, uint2* ranges, uint32_t*
 // ---------------------------------------------------------------------------
 // pair scatter: per visible Gaussian, one key per covered tile
 //
-// Consecutive Gaussians lie on the same surfaces and share tiles, so the
-// pairs of a block are first counted per tile in a shared-memory hash table
-// (one shared atomic per pair, which also gives the pair its rank among the
-// block's pairs of that tile); then one global atomic per distinct tile of
-// the block reserves the block's slots inside that tile's range, on the
-// counter partition of the block (the per-Gaussian pass counted the same
-// pairs on the same partition). Pairs that do not fit the table (or beyond a
-// Gaussian's first kScatterLocal tiles) take one global atomic each.
+// Round k of a warp takes every lane's k-th tile; the lanes of the warp on
+// the same tile reserve their slots with one atomic by the lowest of them (on
+// the counter partition of the Gaussian's block, where the per-Gaussian pass
+// counted the same pairs), each taking its rank among them. Two rounds per
+// step, so that two reservations are in flight together. (A block-level
+// shared-memory hash of the block's tiles with one atomic per distinct tile
+// was measured slower: 0.110 against 0.096 ms at 3M Gaussians.)
 
 constexpr int kScatterThreads = 256;
-constexpr int kHashSlots = 2048;
-constexpr int kScatterLocal = 8;
-constexpr uint32_t kEmptySlot = 0xffffffffu;
 static_assert(kScatterThreads == kPrepThreads, "scatter blocks mirror the per-Gaussian blocks");
 
 __global__ void __launch_bounds__(kScatterThreads)
@@ -196,76 +192,47 @@ __global__ void __launch_bounds__(kScatterThreads)
                    const uint32_t* __restrict__ zkey, int n, int tiles_x,
                    const uint2* __restrict__ ranges, uint32_t* __restrict__ cursor, int parts,
                    unsigned long long* __restrict__ keys, const DevCounters* __restrict__ ctr) {
-    __shared__ uint32_t s_tile[kHashSlots];
-    __shared__ uint32_t s_cnt[kHashSlots];
     if (*reinterpret_cast<const volatile uint32_t*>(&ctr->skip)) return;  // pairs exceed the buffers
-    for (int k = threadIdx.x; k < kHashSlots; k += kScatterThreads) {
-        s_tile[k] = kEmptySlot;
-        s_cnt[k] = 0;
-    }
-    __syncthreads();
+    const unsigned full = 0xffffffffu;
     const uint32_t part = blockIdx.x & (uint32_t)(parts - 1);
     const int i = blockIdx.x * kScatterThreads + threadIdx.x;
-    uint32_t c = 0, x0 = 0, y0 = 0, w = 1;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t c = 0, row = 0, w = 1;
     unsigned long long key = 0;
     if (i < n) {
         c = count[i];
         if (c) {
             const uint2 r = rect[i];
-            x0 = r.x & 0xffffu;
-            y0 = r.y & 0xffffu;
+            const uint32_t x0 = r.x & 0xffffu, y0 = r.y & 0xffffu;
             w = (r.x >> 16) - x0 + 1;
+            row = y0 * (uint32_t)tiles_x + x0;
             key = ((unsigned long long)zkey[i] << 32) | (uint32_t)i;
         }
     }
-    // phase 1: count per tile in the block's table; remember (slot, rank)
-    uint32_t slot[kScatterLocal], rank[kScatterLocal];
-    const uint32_t nloc = min(c, (uint32_t)kScatterLocal);
-#pragma unroll
-    for (int k = 0; k < kScatterLocal; ++k) {
-        slot[k] = kEmptySlot;
-        rank[k] = 0;
-        if ((uint32_t)k < nloc) {
-            const uint32_t dy = (uint32_t)k / w;
-            const uint32_t t = (y0 + dy) * (uint32_t)tiles_x + x0 + ((uint32_t)k - dy * w);
-            uint32_t h = (t * 2654435761u) >> 21;   // 11-bit multiplicative hash
-            for (int probe = 0; probe < 32; ++probe) {
-                const uint32_t prev = atomicCAS(&s_tile[h], kEmptySlot, t);
-                if (prev == kEmptySlot || prev == t) {
-                    slot[k] = h;
-                    rank[k] = atomicAdd(&s_cnt[h], 1u);
-                    break;
-                }
-                h = (h + 1) & (kHashSlots - 1);
-            }
+    const uint32_t rounds = __reduce_max_sync(full, c);
+    uint32_t col = 0;
+    auto next_tile = [&](uint32_t k) {
+        const uint32_t t = k < c ? row + col : 0xffffffffu;
+        if (++col == w) {
+            col = 0;
+            row += (uint32_t)tiles_x;
         }
-    }
-    __syncthreads();
-    // phase 2: reserve each distinct tile's slots in its range
-    for (int k = threadIdx.x; k < kHashSlots; k += kScatterThreads) {
-        const uint32_t t = s_tile[k];
-        if (t != kEmptySlot)
-            s_cnt[k] = ranges[t].x + atomicAdd(&cursor[(size_t)t * parts + part], s_cnt[k]);
-    }
-    __syncthreads();
-    // phase 3: write the keys
-#pragma unroll
-    for (int k = 0; k < kScatterLocal; ++k) {
-        if ((uint32_t)k >= nloc) break;
-        uint32_t pos;
-        if (slot[k] != kEmptySlot) {
-            pos = s_cnt[slot[k]] + rank[k];
-        } else {
-            const uint32_t dy = (uint32_t)k / w;
-            const uint32_t t = (y0 + dy) * (uint32_t)tiles_x + x0 + ((uint32_t)k - dy * w);
-            pos = ranges[t].x + atomicAdd(&cursor[(size_t)t * parts + part], 1u);
-        }
-        keys[pos] = key;
-    }
-    for (uint32_t k = kScatterLocal; k < c; ++k) {
-        const uint32_t dy = k / w;
-        const uint32_t t = (y0 + dy) * (uint32_t)tiles_x + x0 + (k - dy * w);
-        keys[ranges[t].x + atomicAdd(&cursor[(size_t)t * parts + part], 1u)] = key;
+        return t;
+    };
+    for (uint32_t k = 0; k < rounds; k += 2) {
+        const uint32_t t0 = next_tile(k), t1 = next_tile(k + 1);
+        const uint32_t p0 = __match_any_sync(full, t0), p1 = __match_any_sync(full, t1);
+        const int l0 = __ffs(p0) - 1, l1 = __ffs(p1) - 1;
+        uint32_t b0 = 0, b1 = 0;
+        if (t0 != 0xffffffffu && lane == l0)
+            b0 = ranges[t0].x + atomicAdd(&cursor[(size_t)t0 * parts + part], (uint32_t)__popc(p0));
+        if (t1 != 0xffffffffu && lane == l1)
+            b1 = ranges[t1].x + atomicAdd(&cursor[(size_t)t1 * parts + part], (uint32_t)__popc(p1));
+        b0 = __shfl_sync(full, b0, l0);
+        b1 = __shfl_sync(full, b1, l1);
+        if (t0 != 0xffffffffu) keys[b0 + __popc(p0 & lt)] = key;
+        if (t1 != 0xffffffffu) keys[b1 + __popc(p1 & lt)] = key;
     }
 }
 
