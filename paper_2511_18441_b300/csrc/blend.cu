@@ -126,8 +126,12 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
     if (ctr && ctr->skip) rg = make_uint2(0u, 0u);  // pairs exceed the buffers: background only
     const uint32_t begin = rg.x, end = rg.y;
 
-    float T = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f;
+    // colour mode keeps "stopped" in the sign of T (T < 0: stopped at |T|,
+    // or outside the image); the other modes keep a flag
+    constexpr bool kSignT = MODE == kBlendColour;
+    float T = (kSignT && !inside) ? -1.0f : 1.0f, cr = 0.f, cg = 0.f, cb = 0.f;
     bool done = !inside;
+    auto stopped = [&]() { return kSignT ? T < 0.0f : done; };
     uint32_t fetched = begin;
     const float a_min = 1.0f / 255.0f;
     // median depth: the view depth of the Gaussian that takes T below tau
@@ -203,6 +207,21 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
         // exponent <= 0 up to rounding (a positive-definite conic): no clamp
         const float p = fmaf(a.x, fxx, fmaf(a.y, fxy, fmaf(a.z, fyy, fmaf(a.w, fpx, fmaf(b.x, fpy, b.y)))));
         const float al = fminf(0.99f, exp2_approx(p));
+        if (kSignT) {
+            // alpha below 1/255 (and the sentinel) weighs 0 and leaves T as it
+            // is, so a running pixel (T >= 1e-4) cannot stop on it; a stopped
+            // pixel (T < 0) stops again, adding nothing
+            const float a2 = al >= a_min ? al : 0.0f;
+            const float wt = a2 * T;
+            const float nT = T - wt;
+            const bool stop = nT < 1e-4f;
+            const float w = stop ? 0.0f : wt;
+            cr = fmaf(b.z, w, cr);
+            cg = fmaf(b.w, w, cg);
+            cb = fmaf(c.x, w, cb);
+            T = stop ? -fabsf(T) : nT;
+            return;
+        }
         const float wt = al * T;
         const float nT = T - wt;
         const bool take = !done && al >= a_min;
@@ -235,7 +254,7 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
 
     uint32_t prev_b = 0xffffffffu;
     for (uint32_t b = begin; b < end; b += BATCH) {
-        const int n_done = __syncthreads_count(done);
+        const int n_done = __syncthreads_count(stopped());
         if (prev_b != 0xffffffffu) flush(prev_b);
         if (n_done == kBlendThreads) {
             prev_b = 0xffffffffu;
@@ -275,7 +294,7 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
             rb = __ldg(rec + 3 * (size_t)rid + 1);
             rc = __ldg(rec + 3 * (size_t)rid + 2);
         }
-        if (__all_sync(0xffffffffu, done)) continue;
+        if (__all_sync(0xffffffffu, stopped())) continue;
         const int cnt = (int)min((uint32_t)BATCH, end - b);
         // this warp's four lists: sentinel everywhere, then the hits in order
         {
@@ -314,7 +333,7 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
             blend_one(pr.x >> 16);
             blend_one(pr.y & 0xffffu);
             blend_one(pr.y >> 16);
-            if (__all_sync(0xffffffffu, done)) break;
+            if (__all_sync(0xffffffffu, stopped())) break;
         }
     }
     if (MODE == kBlendCover) {
@@ -339,6 +358,7 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
         return;
     }
     if (inside) {
+        if (kSignT) T = fabsf(T);
         image[3 * pix + 0] = cr + T * bg0;
         image[3 * pix + 1] = cg + T * bg1;
         image[3 * pix + 2] = cb + T * bg2;
