@@ -496,7 +496,8 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
         CKS(ensure(ctx, sc.tvals[0], sizeof(uint32_t) * (size_t)Pn));
         stage_begin(ctx, ST_SCATTER, st);
         l = launch_scatter(P<uint32_t>(sc.count), P<uint2>(sc.rect), P<uint32_t>(sc.zkey), n,
-                           dc.tiles_x, P<uint2>(sc.ranges), P<uint32_t>(sc.cursor), kTileParts,
+                           dc.tiles_x, tiles, P<uint2>(sc.ranges), P<uint32_t>(sc.cursor),
+                           kTileParts,
                            P<unsigned long long>(sc.pair_keys), dctr, st);
         stage_end(ctx, ST_SCATTER, l, st);
         // grid sizes: this frame's class sizes, else a hint from an earlier frame

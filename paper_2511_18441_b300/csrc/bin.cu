@@ -19,39 +19,34 @@ namespace recogs {
 // ---------------------------------------------------------------------------
 // per-tile totals over the counter partitions
 
-// One warp per tile: lane l holds partition l (lanes beyond PARTS hold 0).
+// One thread per tile: the counts are partition-major ([part][tile]), so the
+// threads of a warp read consecutive words of each partition's row.
 template <int PARTS>
 __global__ void __launch_bounds__(256) tile_totals_kernel(uint32_t* __restrict__ tile_count,
                                                           int tiles, uint32_t* __restrict__ cursor,
                                                           uint32_t* __restrict__ totals) {
-    static_assert(PARTS <= 32, "one partition per lane");
-    const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * 256 + threadIdx.x;
     if (t >= tiles) return;
-    uint32_t c = 0u;
-    if (lane < PARTS) {
-        // consume the count and leave it zero for the next frame
-        c = tile_count[(size_t)t * PARTS + lane];
-        tile_count[(size_t)t * PARTS + lane] = 0u;
-    }
-    uint32_t inc = c;
+    uint32_t c[PARTS];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
+    for (int p = 0; p < PARTS; ++p) c[p] = tile_count[(size_t)p * tiles + t];
+    uint32_t run = 0;
+#pragma unroll
+    for (int p = 0; p < PARTS; ++p) {
+        // consume the count and leave it zero for the next frame
+        tile_count[(size_t)p * tiles + t] = 0u;
+        cursor[(size_t)p * tiles + t] = run;
+        run += c[p];
     }
-    if (lane < PARTS) cursor[(size_t)t * PARTS + lane] = inc - c;
-    if (lane == 31) totals[t] = inc;
+    totals[t] = run;
 }
 
 int launch_tile_totals(uint32_t* tile_count, int tiles, int parts, uint32_t* cursor,
                        uint32_t* totals, cudaStream_t st) {
-    if (parts == kTileParts)
-        tile_totals_kernel<kTileParts><<<(tiles + 7) / 8, 256, 0, st>>>(tile_count, tiles, cursor,
+    static_assert(kTileParts == kTilePartsSmall, "one partition count");
+    (void)parts;   // always kTileParts
+    tile_totals_kernel<kTileParts><<<(tiles + 255) / 256, 256, 0, st>>>(tile_count, tiles, cursor,
                                                                         totals);
-    else
-        tile_totals_kernel<kTilePartsSmall><<<(tiles + 7) / 8, 256, 0, st>>>(tile_count, tiles,
-                                                                             cursor, totals);
     return 1;
 }
 
@@ -187,61 +182,80 @@ int launch_tile_scan(const uint32_t* totals, int tiles, uint2* ranges, uint32_t*
 constexpr int kScatterThreads = 256;
 static_assert(kScatterThreads == kPrepThreads, "scatter blocks mirror the per-Gaussian blocks");
 
+// G Gaussians per thread (chunks G b .. G b + G - 1 of the per-Gaussian
+// pass; the counter partition is each Gaussian's own chunk), so that the
+// loads and reservations of G Gaussians are in flight together.
+template <int G>
 __global__ void __launch_bounds__(kScatterThreads)
     scatter_kernel(const uint32_t* __restrict__ count, const uint2* __restrict__ rect,
-                   const uint32_t* __restrict__ zkey, int n, int tiles_x,
+                   const uint32_t* __restrict__ zkey, int n, int tiles_x, int tiles,
                    const uint2* __restrict__ ranges, uint32_t* __restrict__ cursor, int parts,
                    unsigned long long* __restrict__ keys, const DevCounters* __restrict__ ctr) {
     if (*reinterpret_cast<const volatile uint32_t*>(&ctr->skip)) return;  // pairs exceed the buffers
     const unsigned full = 0xffffffffu;
-    const uint32_t part = blockIdx.x & (uint32_t)(parts - 1);
-    const int i = blockIdx.x * kScatterThreads + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
-    uint32_t c = 0, row = 0, w = 1;
-    unsigned long long key = 0;
-    if (i < n) {
-        c = count[i];
-        if (c) {
+    uint32_t c[G], row[G], w[G], col[G], part[G];
+    unsigned long long key[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const int chunk = G * blockIdx.x + g;
+        const int i = chunk * kScatterThreads + threadIdx.x;
+        part[g] = (uint32_t)chunk & (uint32_t)(parts - 1);
+        c[g] = i < n ? count[i] : 0u;
+        row[g] = 0;
+        w[g] = 1;
+        col[g] = 0;
+        key[g] = 0;
+        if (c[g]) {
             const uint2 r = rect[i];
             const uint32_t x0 = r.x & 0xffffu, y0 = r.y & 0xffffu;
-            w = (r.x >> 16) - x0 + 1;
-            row = y0 * (uint32_t)tiles_x + x0;
-            key = ((unsigned long long)zkey[i] << 32) | (uint32_t)i;
+            w[g] = (r.x >> 16) - x0 + 1;
+            row[g] = y0 * (uint32_t)tiles_x + x0;
+            key[g] = ((unsigned long long)zkey[i] << 32) | (uint32_t)i;
         }
     }
-    const uint32_t rounds = __reduce_max_sync(full, c);
-    uint32_t col = 0;
-    auto next_tile = [&](uint32_t k) {
-        const uint32_t t = k < c ? row + col : 0xffffffffu;
-        if (++col == w) {
-            col = 0;
-            row += (uint32_t)tiles_x;
+    uint32_t cmax = c[0];
+#pragma unroll
+    for (int g = 1; g < G; ++g) cmax = max(cmax, c[g]);
+    const uint32_t rounds = __reduce_max_sync(full, cmax);
+    for (uint32_t k = 0; k < rounds; ++k) {
+        uint32_t t[G], p[G], b[G];
+        int l[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            t[g] = k < c[g] ? row[g] + col[g] : 0xffffffffu;
+            if (++col[g] == w[g]) {
+                col[g] = 0;
+                row[g] += (uint32_t)tiles_x;
+            }
+            p[g] = __match_any_sync(full, t[g]);
+            l[g] = __ffs(p[g]) - 1;
+            b[g] = 0;
+            if (t[g] != 0xffffffffu && lane == l[g])
+                b[g] = ranges[t[g]].x +
+                       atomicAdd(&cursor[(size_t)part[g] * tiles + t[g]], (uint32_t)__popc(p[g]));
         }
-        return t;
-    };
-    for (uint32_t k = 0; k < rounds; k += 2) {
-        const uint32_t t0 = next_tile(k), t1 = next_tile(k + 1);
-        const uint32_t p0 = __match_any_sync(full, t0), p1 = __match_any_sync(full, t1);
-        const int l0 = __ffs(p0) - 1, l1 = __ffs(p1) - 1;
-        uint32_t b0 = 0, b1 = 0;
-        if (t0 != 0xffffffffu && lane == l0)
-            b0 = ranges[t0].x + atomicAdd(&cursor[(size_t)t0 * parts + part], (uint32_t)__popc(p0));
-        if (t1 != 0xffffffffu && lane == l1)
-            b1 = ranges[t1].x + atomicAdd(&cursor[(size_t)t1 * parts + part], (uint32_t)__popc(p1));
-        b0 = __shfl_sync(full, b0, l0);
-        b1 = __shfl_sync(full, b1, l1);
-        if (t0 != 0xffffffffu) keys[b0 + __popc(p0 & lt)] = key;
-        if (t1 != 0xffffffffu) keys[b1 + __popc(p1 & lt)] = key;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            b[g] = __shfl_sync(full, b[g], l[g]);
+            if (t[g] != 0xffffffffu) keys[b[g] + __popc(p[g] & lt)] = key[g];
+        }
     }
 }
 
+#ifndef RECOGS_SCATTER_G
+#define RECOGS_SCATTER_G 2
+#endif
+
 int launch_scatter(const uint32_t* count, const uint2* rect, const uint32_t* zkey, int n,
-                   int tiles_x, const uint2* ranges, uint32_t* cursor, int parts,
+                   int tiles_x, int tiles, const uint2* ranges, uint32_t* cursor, int parts,
                    unsigned long long* keys, const DevCounters* counters, cudaStream_t st) {
     if (n == 0) return 0;
-    scatter_kernel<<<(n + kScatterThreads - 1) / kScatterThreads, kScatterThreads, 0, st>>>(
-        count, rect, zkey, n, tiles_x, ranges, cursor, parts, keys, counters);
+    constexpr int G = RECOGS_SCATTER_G;
+    const int chunks = (n + kScatterThreads - 1) / kScatterThreads;
+    scatter_kernel<G><<<(chunks + G - 1) / G, kScatterThreads, 0, st>>>(
+        count, rect, zkey, n, tiles_x, tiles, ranges, cursor, parts, keys, counters);
     return 1;
 }
 

@@ -256,7 +256,7 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
     if (P > 0 && (int)hc.max_tile <= kMaxSmemTile) {
         unsigned long long* keys = reinterpret_cast<unsigned long long*>(base + oTkeys0);
         launch_scatter(U32(oCount), reinterpret_cast<const uint2*>(base + oRect), U32(oZkey), n,
-                       dc.tiles_x, ranges, U32(oCursor), kTilePartsSmall, keys, dctr, st);
+                       dc.tiles_x, tiles, ranges, U32(oCursor), kTilePartsSmall, keys, dctr, st);
         const cudaStream_t streams[3] = {st, st, st};
         launch_tile_sort(ranges, U32(oOrder), hc.class_tiles, true, tiles, keys, U32(oTvals0), dctr,
                          nullptr, 4, streams);

@@ -415,7 +415,7 @@ __device__ __forceinline__ void prep_chunk_end(int chunk, int n_chunks, uint32_t
             const uint32_t t = k < cnt ? row + col : 0xffffffffu;
             const uint32_t peers = __match_any_sync(full, t);
             if (t != 0xffffffffu && (threadIdx.x & 31) == __ffs(peers) - 1)
-                atomicAdd(&out.tile_count[(size_t)t * out.parts + (chunk & (out.parts - 1))],
+                atomicAdd(&out.tile_count[(size_t)(chunk & (out.parts - 1)) * (cam.tiles_x * cam.tiles_y) + t],
                           (uint32_t)__popc(peers));
             if (++col == (uint32_t)rw) {
                 col = 0;

@@ -90,9 +90,12 @@ static_assert(sizeof(DevCounters) == 64, "DevCounters layout");
 // threads); a frame with a larger tile takes the global radix path.
 constexpr int kMaxSmemTile = 8192;
 // Per-tile pair counters are split into partitions (by block index) so that
-// concurrent blocks rarely update the same counter: kTileParts for the
-// context path, kTilePartsSmall where scratch must stay small.
-constexpr int kTileParts = 16;
+// concurrent blocks rarely update the same counter; the counters are stored
+// partition-major, so the partitions of a tile sit in different L2 slices
+// (measured at 3M Gaussians, scatter: 0.094 ms tile-major with 16
+// partitions, 0.079 partition-major with 16, 0.073 with 32, 0.076 with 64).
+// kTileParts for the context path, kTilePartsSmall for the allocation-free one.
+constexpr int kTileParts = 32;
 constexpr int kTilePartsSmall = 32;
 
 // Position bucket of a tile with c pairs in the tile order (heaviest first,
@@ -196,7 +199,8 @@ struct PrepOut {
     uint2* rect;          // [n] (tx0 | tx1 << 16, ty0 | ty1 << 16)
     uint32_t* zkey;       // [n] float bits of the view depth
     uint32_t* block_sums; // [2 * blocks]: visible count, pair count
-    uint32_t* tile_count; // [tiles][parts] pairs per tile and partition (zeroed first)
+    uint32_t* tile_count; // [parts][tiles] pairs per tile and partition (zeroed first); the
+                          // partitions of one tile lie on different cache lines (L2 slices)
     int parts;            // kTileParts or kTilePartsSmall
     DevCounters* counters;
 };
@@ -251,7 +255,7 @@ int launch_tile_totals(uint32_t* tile_count, int tiles, int parts, uint32_t* cur
 int launch_tile_scan(const uint32_t* totals, int tiles, uint2* ranges, uint32_t* order,
                      DevCounters* counters, uint32_t* work, uint32_t capacity, cudaStream_t st);
 int launch_scatter(const uint32_t* count, const uint2* rect, const uint32_t* zkey, int n,
-                   int tiles_x, const uint2* ranges, uint32_t* cursor, int parts,
+                   int tiles_x, int tiles, const uint2* ranges, uint32_t* cursor, int parts,
                    unsigned long long* keys, const DevCounters* counters, cudaStream_t st);
 // class_tiles: the class sizes (exact: this frame's; otherwise a hint from
 // an earlier frame) or NULL; they only size the persistent grids. Classes
