@@ -399,8 +399,7 @@ __device__ __forceinline__ uint32_t prep_one(int i, float mx, float my, float mz
 
 // Per-chunk epilogue (a chunk = kPrepThreads consecutive Gaussians, one per
 // thread): pairs per tile and partition, and the chunk's visible and pair
-// totals. Round k of the tile count adds every lane's k-th tile with one
-// atomic per distinct tile of the warp. s_*: per-warp shared scratch.
+// totals. s_*: per-warp shared scratch.
 __device__ __forceinline__ void prep_chunk_end(int chunk, int n_chunks, uint32_t cnt,
                                                uint32_t zbits, int rx0, int ry0, int rw,
                                                const DevCamera& cam, const PrepOut& out,
@@ -408,15 +407,13 @@ __device__ __forceinline__ void prep_chunk_end(int chunk, int n_chunks, uint32_t
                                                uint32_t* s_zmax) {
     const unsigned full = 0xffffffffu;
     if (out.tile_count) {
-        const uint32_t rounds = __reduce_max_sync(full, cnt);
-        // this lane's k-th tile, walked row by row through its rectangle
+        // one atomic per pair (measured faster than aggregating the lanes of a
+        // warp on the same tile with a warp match: 0.162 against 0.169 ms at
+        // 3M Gaussians); this lane's tiles row by row through its rectangle
+        uint32_t* tc = out.tile_count + (size_t)(chunk & (out.parts - 1)) * (cam.tiles_x * cam.tiles_y);
         uint32_t row = (uint32_t)ry0 * (uint32_t)cam.tiles_x + (uint32_t)rx0, col = 0;
-        for (uint32_t k = 0; k < rounds; ++k) {
-            const uint32_t t = k < cnt ? row + col : 0xffffffffu;
-            const uint32_t peers = __match_any_sync(full, t);
-            if (t != 0xffffffffu && (threadIdx.x & 31) == __ffs(peers) - 1)
-                atomicAdd(&out.tile_count[(size_t)(chunk & (out.parts - 1)) * (cam.tiles_x * cam.tiles_y) + t],
-                          (uint32_t)__popc(peers));
+        for (uint32_t k = 0; k < cnt; ++k) {
+            atomicAdd(tc + row + col, 1u);
             if (++col == (uint32_t)rw) {
                 col = 0;
                 row += (uint32_t)cam.tiles_x;
