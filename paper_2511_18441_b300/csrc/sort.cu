@@ -10,7 +10,7 @@
 // bytes moved: 32-bit depth keys over V Gaussians plus ~13 tile bits over
 // P pairs instead of ~45 bits over P pairs.
 //
-// Radix pass = stable tile-local ranking with warp match + decoupled
+// Radix pass = stable tile-local ranking with bit ballots + decoupled
 // look-back for the tile's global digit offsets + digit-ordered scatter (see
 // the radix sort section for the bounded waits).
 #include "recogs_internal.cuh"
@@ -194,7 +194,13 @@ __global__ void __launch_bounds__(kOsThreads)
         const int li = warp * PER_WARP + k * 32 + lane;
         const bool ok = li < nblk;
         const uint32_t dg = ok ? ((key[k] >> shift) & 0xffu) : (uint32_t)kRadix;
-        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        // lanes with the same digit: the intersection of the digit's bit ballots
+        uint32_t peers = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+        for (int bit = 0; bit < kRadixBits; ++bit) {
+            const uint32_t bb = __ballot_sync(0xffffffffu, (dg >> bit) & 1u);
+            peers &= ((dg >> bit) & 1u) ? bb : ~bb;
+        }
         const uint32_t before = ok ? s_wcnt[warp][dg] : 0u;
         __syncwarp();
         if (ok && (peers & lt) == 0) s_wcnt[warp][dg] = before + __popc(peers);
