@@ -100,7 +100,11 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
     __shared__ float4 s_b[BATCH + 1];     // (E, F, r, g)
     __shared__ float4 s_c[BATCH + 1];     // (b, view depth, Gaussian index bits, 0)
     __shared__ uint32_t s_m[BATCH];       // group mask (0 past the batch's end)
-    __shared__ __align__(16) uint16_t s_list[32 * BATCH];   // per group: BATCH byte offsets
+    // per group: BATCH byte offsets; the lists are LSTRIDE apart, 16 bytes more
+    // than BATCH entries, so that the four groups of a warp reading position
+    // k of their lists hit different banks
+    constexpr int LSTRIDE = BATCH + 8;
+    __shared__ __align__(16) uint16_t s_list[32 * LSTRIDE];
     // gradient mode: each staged Gaussian's colour gradient summed over this tile's pixels
     constexpr bool kAcc = Accumulates<MODE>::value;
     __shared__ float s_g[kAcc ? 3 * BATCH : 1];
@@ -120,7 +124,7 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
     const float fpx = (float)lx - 7.5f, fpy = (float)ly - 7.5f;
     const float fxx = fpx * fpx, fxy = fpx * fpy, fyy = fpy * fpy;
     const size_t pix = (size_t)py * width + px;
-    uint16_t* const my_list = s_list + (4 * warp + grp) * BATCH;
+    uint16_t* const my_list = s_list + (4 * warp + grp) * LSTRIDE;
 
     uint2 rg = ranges[tile];
     if (ctr && ctr->skip) rg = make_uint2(0u, 0u);  // pairs exceed the buffers: background only
@@ -298,11 +302,11 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
         const int cnt = (int)min((uint32_t)BATCH, end - b);
         // this warp's four lists: sentinel everywhere, then the hits in order
         {
-            uint4* w4 = reinterpret_cast<uint4*>(s_list + 4 * warp * BATCH);
+            uint4* w4 = reinterpret_cast<uint4*>(s_list + 4 * warp * LSTRIDE);
             const uint4 sent4 = make_uint4(kSent | kSent << 16, kSent | kSent << 16,
                                            kSent | kSent << 16, kSent | kSent << 16);
 #pragma unroll
-            for (int k = lane; k < BATCH / 2; k += 32) w4[k] = sent4;
+            for (int k = lane; k < LSTRIDE / 2; k += 32) w4[k] = sent4;
         }
         __syncwarp();
         int n_mine = 0;
