@@ -80,39 +80,59 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restr
     }
     s_hist[threadIdx.x] = 0;
     __syncthreads();
-    unsigned long long carry = 0;
-    uint32_t mx = 0;
-    for (int base = 0; base < tiles; base += 1024) {
-        const int t = base + threadIdx.x;
-        const uint32_t c = t < tiles ? totals[t] : 0u;
+    // thread i takes the contiguous tiles [seg i, seg (i + 1)): their sum, one
+    // block-wide exclusive scan of the sums (64-bit, so that the capacity test
+    // below sees the true total), then the ranges
+    __shared__ unsigned long long s_wsum[33];
+    const int seg = (tiles + 1023) / 1024;
+    const int t0 = min(tiles, (int)threadIdx.x * seg), t1 = min(tiles, t0 + seg);
+    uint32_t mx = 0, cls_n[kSortClasses] = {0, 0, 0, 0, 0, 0};
+    unsigned long long sum = 0;
+    for (int t = t0; t < t1; ++t) {
+        const uint32_t c = totals[t];
         mx = max(mx, c);
-        if (c) atomicAdd(&s_cls[sort_class(c)], 1u);
-        if (t < tiles) atomicAdd(&s_hist[order_bucket(c)], 1u);
-        uint32_t inc = c;
+        sum += c;
+        if (c) {
+            const int k = sort_class(c);
+#pragma unroll
+            for (int q = 0; q < kSortClasses; ++q) cls_n[q] += k == q ? 1u : 0u;
+        }
+        atomicAdd(&s_hist[order_bucket(c)], 1u);
+    }
+    // tiles per sort class: one shared atomic per warp and class
+#pragma unroll
+    for (int q = 0; q < kSortClasses; ++q) {
+        const uint32_t w = __reduce_add_sync(0xffffffffu, cls_n[q]);
+        if (lane == 0 && w) atomicAdd(&s_cls[q], w);
+    }
+    unsigned long long inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned long long w = s_wsum[lane];
+        unsigned long long wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
         }
-        if (lane == 31) s_warp[warp] = inc;
-        __syncthreads();
-        if (warp == 0) {
-            const uint32_t w = s_warp[lane];
-            uint32_t wi = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
-                if (lane >= o) wi += y;
-            }
-            s_warp[lane] = wi - w;
-            if (lane == 31) s_warp[32] = wi;
-        }
-        __syncthreads();
-        const uint32_t start = (uint32_t)carry + s_warp[warp] + inc - c;
-        if (t < tiles) ranges[t] = make_uint2(start, start + c);
-        carry += s_warp[32];
-        __syncthreads();
+        s_wsum[lane] = wi - w;
+        if (lane == 31) s_wsum[32] = wi;
     }
+    __syncthreads();
+    // positions are 32-bit: a frame past 2^32 pairs fails the capacity test
+    uint32_t start = (uint32_t)(s_wsum[warp] + inc - sum);
+    for (int t = t0; t < t1; ++t) {
+        const uint32_t c = totals[t];
+        ranges[t] = make_uint2(start, start + c);
+        start += c;
+    }
+    const unsigned long long carry = s_wsum[32];
     mx = __reduce_max_sync(0xffffffffu, mx);
     if (lane == 0) s_max[warp] = mx;
     __syncthreads();
@@ -136,14 +156,14 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restr
     // tile order: a counting sort of the tiles by order_bucket (the order
     // inside a bucket is arbitrary, which changes no pixel)
     const uint32_t x = s_hist[threadIdx.x];
-    uint32_t inc = x;
+    uint32_t hinc = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
+        const uint32_t y = __shfl_up_sync(0xffffffffu, hinc, o);
+        if (lane >= o) hinc += y;
     }
     __syncthreads();
-    if (lane == 31) s_warp[warp] = inc;
+    if (lane == 31) s_warp[warp] = hinc;
     __syncthreads();
     if (warp == 0) {
         const uint32_t w = s_warp[lane];
@@ -156,7 +176,7 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restr
         s_warp[lane] = wi - w;
     }
     __syncthreads();
-    s_hist[threadIdx.x] = s_warp[warp] + inc - x;
+    s_hist[threadIdx.x] = s_warp[warp] + hinc - x;
     __syncthreads();
     for (int t = threadIdx.x; t < tiles; t += 1024)
         order[atomicAdd(&s_hist[order_bucket(totals[t])], 1u)] = (uint32_t)t;
