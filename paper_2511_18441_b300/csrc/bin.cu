@@ -482,8 +482,10 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
         if (warp * PW + i * 32 + lane < n) key[i] -= zmin;
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
-        for (int d = threadIdx.x; d < W * 256; d += THREADS) s_wcnt[d] = 0;
-        __syncthreads();
+        // each warp clears its own counters (no other warp touches them until
+        // the block barrier after the ranking)
+        for (int d = lane; d < 256; d += 32) s_wcnt[warp * 256 + d] = 0;
+        __syncwarp();
         uint32_t rank[ITEMS];
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {

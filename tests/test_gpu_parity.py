@@ -300,8 +300,11 @@ def test_stage_timing_and_launch_count(ctx):
 # ---------------------------------------------------------------------------
 # the two ways of ordering each tile's list give identical results
 
-def test_sort_paths_agree(ctx):
-    w = sg.paper_scale_workload(n=300_000, width=960, height=540)
+@pytest.mark.parametrize("W,H", [(960, 540), (2560, 1440)])
+def test_sort_paths_agree(ctx, W, H):
+    """Per-tile and global ordering agree bit for bit, also past 8192 tiles
+    (2560x1440: 14,400 tiles, 15 per thread of the tile scan)."""
+    w = sg.paper_scale_workload(n=300_000, width=W, height=H)
     ds = dscene(w.scene)
     out = {}
     for path in (1, 2):
