@@ -5,7 +5,7 @@
 // kTileParts counter partitions). An exclusive scan over tiles gives each
 // tile's range in the pair array. Every visible Gaussian then writes the
 // 64-bit key (depth bits << 32 | index) of each of its pairs into its tiles'
-// ranges through per-tile cursors (warp-aggregated atomics: arbitrary order
+// ranges through per-tile cursors (one atomic per pair: arbitrary order
 // inside a range), and one CTA per tile sorts its range (shared-memory radix
 // sort, or a bitonic network in registers for small tiles). The result is
 // every tile's list in (float32 depth, index) order -- the order a stable LSD
