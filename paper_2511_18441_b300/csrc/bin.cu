@@ -25,6 +25,8 @@ template <int PARTS>
 __global__ void __launch_bounds__(256) tile_totals_kernel(uint32_t* __restrict__ tile_count,
                                                           int tiles, uint32_t* __restrict__ cursor,
                                                           uint32_t* __restrict__ totals) {
+    grid_dependents_launch();   // the tile scan (one CTA) may be scheduled now
+    grid_dependency_wait();     // the per-Gaussian pass's counts
     const int t = blockIdx.x * 256 + threadIdx.x;
     if (t >= tiles) return;
     uint32_t c[PARTS];
@@ -45,8 +47,8 @@ int launch_tile_totals(uint32_t* tile_count, int tiles, int parts, uint32_t* cur
                        uint32_t* totals, cudaStream_t st) {
     static_assert(kTileParts == kTilePartsSmall, "one partition count");
     (void)parts;   // always kTileParts
-    tile_totals_kernel<kTileParts><<<(tiles + 255) / 256, 256, 0, st>>>(tile_count, tiles, cursor,
-                                                                        totals);
+    launch_pdl(tile_totals_kernel<kTileParts>, dim3((tiles + 255) / 256), dim3(256), 0, st,
+               tile_count, tiles, cursor, totals);
     return 1;
 }
 
@@ -72,6 +74,8 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restr
     __shared__ uint32_t s_max[32];
     __shared__ uint32_t s_cls[kSortClasses];
     __shared__ uint32_t s_hist[kOrderBuckets];
+    grid_dependents_launch();   // the scatter may be scheduled now
+    grid_dependency_wait();     // the tile totals
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     static_assert(kOrderBuckets == 1024, "one order bucket per thread");
     if (threadIdx.x < kSortClasses) {
@@ -184,7 +188,8 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restr
 
 int launch_tile_scan(const uint32_t* totals, int tiles, uint2* ranges, uint32_t* order,
                      DevCounters* counters, uint32_t* work, uint32_t capacity, cudaStream_t st) {
-    tile_scan_kernel<<<1, 1024, 0, st>>>(totals, tiles, ranges, order, counters, work, capacity);
+    launch_pdl(tile_scan_kernel, dim3(1), dim3(1024), 0, st, totals, tiles, ranges, order,
+               counters, work, capacity);
     return 1;
 }
 
@@ -208,6 +213,7 @@ __global__ void __launch_bounds__(kScatterThreads)
                    const uint32_t* __restrict__ zkey, int n, int tiles_x, int tiles,
                    const uint2* __restrict__ ranges, uint32_t* __restrict__ cursor, int parts,
                    unsigned long long* __restrict__ keys, const DevCounters* __restrict__ ctr) {
+    grid_dependency_wait();     // the tile scan's ranges and flags
     if (*reinterpret_cast<const volatile uint32_t*>(&ctr->skip)) return;  // pairs exceed the buffers
     constexpr int G = kScatterG;
     uint32_t c[G], row[G], w[G], col[G];
@@ -255,8 +261,8 @@ int launch_scatter(const uint32_t* count, const uint2* rect, const uint32_t* zke
                    unsigned long long* keys, const DevCounters* counters, cudaStream_t st) {
     if (n == 0) return 0;
     const int chunks = (n + kScatterThreads - 1) / kScatterThreads;
-    scatter_kernel<<<(chunks + kScatterG - 1) / kScatterG, kScatterThreads, 0, st>>>(
-        count, rect, zkey, n, tiles_x, tiles, ranges, cursor, parts, keys, counters);
+    launch_pdl(scatter_kernel, dim3((chunks + kScatterG - 1) / kScatterG), dim3(kScatterThreads), 0,
+               st, count, rect, zkey, n, tiles_x, tiles, ranges, cursor, parts, keys, counters);
     return 1;
 }
 

@@ -108,6 +108,37 @@ __device__ __forceinline__ uint32_t order_bucket(uint32_t c) {
 }
 
 // --------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel launched with launch_pdl may be
+// scheduled while the previous kernel on its stream is still running; it calls
+// grid_dependency_wait() before it reads anything that kernel writes (the
+// wait returns once that kernel has completed and its writes are visible).
+
+__device__ __forceinline__ void grid_dependency_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Let the next kernel on the stream (launched with launch_pdl) be scheduled now.
+__device__ __forceinline__ void grid_dependents_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// --------------------------------------------------------------------------
 // Exact-rounding helpers shared by the selection and recolour code so that
 // the fused and the stand-alone paths produce identical bits.
 
