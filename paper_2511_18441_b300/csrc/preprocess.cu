@@ -459,7 +459,8 @@ __device__ __forceinline__ void prep_chunk_end(int chunk, int n_chunks, uint32_t
 // after the projection and the culling tests (a culled Gaussian reads none),
 // so they are not held in registers across the geometry; the kernel runs at
 // 48-64 registers and four resident blocks (32 warps) per SM, whose
-// geometry work overlaps the other warps' SH reads. Measured at 3M Gaussians
+// geometry work overlaps the other warps' SH reads; a bulk L2 prefetch of the
+// chunk's SH rows at the start shortens those reads (0.163 -> 0.160 ms). Measured at 3M Gaussians
 // against loading all 48 coefficients up front (124 registers, 2 blocks):
 // 0.172 against 0.206 ms (float32 SH), 0.180 against 0.216 ms (BF16).
 #ifndef RECOGS_PREP_MIN_BLOCKS_F32
@@ -482,6 +483,18 @@ __global__ void __launch_bounds__(kPrepThreads, PrepMinBlocks<T>::value)
     __shared__ float4 s_rec[3 * kPrepThreads];   // the block's records, staged per warp
     const int chunk = blockIdx.x;
     const int i = chunk * kPrepThreads + threadIdx.x;
+    // the chunk's 48 SH rows (one contiguous run per row) start on their way
+    // into L2 now, while the geometry is computed: one bulk prefetch per row,
+    // clipped inward to 16-byte boundaries (a prefetch is only a hint)
+    if (threadIdx.x < 48) {
+        const uintptr_t row = (uintptr_t)sh + (uintptr_t)threadIdx.x * (uintptr_t)n * sizeof(T);
+        const uintptr_t a = (row + (uintptr_t)chunk * kPrepThreads * sizeof(T) + 15) & ~(uintptr_t)15;
+        const uintptr_t e = row + (uintptr_t)min(n, (chunk + 1) * kPrepThreads) * sizeof(T);
+        const uintptr_t b = e & ~(uintptr_t)15;
+        if (b > a)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(b - a))
+                         : "memory");
+    }
     uint32_t cnt = 0, zbits = 0;
     int rx0 = 0, ry0 = 0, rw = 1;
     float4 r3[3];
