@@ -435,8 +435,8 @@ RECOGS_API int64_t recogs_launch_count(const recogs_ctx* ctx);
 
 /* How recogs_render orders each tile's list by (depth, index) (the order of
  * Eq. 3): 0 = automatic (per-tile shared-memory sort when the most crowded
- * tile has at most 8192 pairs, else the global path), 1 = per-tile sort
- * (falls back to the global path above 8192 pairs), 2 = global path (radix
+ * tile has at most 16384 pairs, else the global path), 1 = per-tile sort
+ * (falls back to the global path above 16384 pairs), 2 = global path (radix
  * sort by depth, pair expansion in depth order, stable radix sort by tile).
  * Both give identical lists. */
 RECOGS_API recogs_status recogs_set_sort_path(recogs_ctx* ctx, int path);
@@ -444,8 +444,10 @@ RECOGS_API recogs_status recogs_set_sort_path(recogs_ctx* ctx, int path);
 /* Schedule knobs of recogs_render (the batch autotuner searches them too;
  * every setting gives the same image bit for bit):
  * radix_classes (0..5) = how many of the per-tile sort's size classes, from
- * the largest tiles (up to 8192 pairs) down, are sorted by the shared-memory
- * radix sort rather than the register bitonic network (default 4);
+ * the largest tiles (4096 to 16384 pairs) down, are sorted by the
+ * shared-memory radix sort rather than the register bitonic network (default
+ * 4; the largest class always takes the radix sort, which alone holds tiles
+ * above 8192 pairs);
  * blend_batch (128 or 256) = depth-sorted Gaussians staged in shared memory
  * per step of the blend (default 256); overlap (0 or 1) = blend each size
  * class's tiles on the class's stream as soon as they are sorted (stage
@@ -464,7 +466,7 @@ RECOGS_API recogs_status recogs_set_schedule(recogs_ctx* ctx, int32_t radix_clas
  * captured into a CUDA graph once its scratch has grown, e.g. after one
  * call of the same size). The pair buffers then hold `pairs` (tile, Gaussian)
  * pairs and the per-tile sort is always used. A frame with more pairs, or
- * with a tile above 8192 pairs, is not rendered: its image is the background
+ * with a tile above 16384 pairs, is not rendered: its image is the background
  * only (T = 1) and an error is recorded on the device, reported by the next
  * recogs_check (or by recogs_render when stats are requested).
  * pairs = 0 restores the read back (the default). At most 2^28 - 1. */
@@ -509,7 +511,7 @@ typedef struct {
  * Without RECOGS_BATCH_NOWAIT the call waits for the batch and, if a view
  * outgrew its lane's pair buffers, plans again (rendering every view again).
  * With it, the call returns at once and recogs_check reports overflows (the
- * affected images hold the background only). Views with a tile above 8192
+ * affected images hold the background only). Views with a tile above 16384
  * pairs are rendered with the read back after the lanes. */
 RECOGS_API recogs_status recogs_render_batch(recogs_ctx* ctx, const recogs_scene* scenes,
                                              int32_t n_scenes, const recogs_view* views,

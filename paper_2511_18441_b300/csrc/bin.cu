@@ -618,6 +618,34 @@ __global__ void __launch_bounds__(THREADS, (RECOGS_RADIX_WARPS_PER_SM * 32 / THR
     }
 }
 
+// The largest class (tiles of 4096 pairs and up): tiles of up to 8192 pairs
+// take the 8-key-per-thread sort, larger ones (up to kMaxSmemTile = 16384)
+// the 16-key one (same CTA of 1024 threads, shared memory sized for 16).
+__global__ void __launch_bounds__(1024, 1)
+    tile_radix_big_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+                          const unsigned long long* __restrict__ keys, uint32_t* __restrict__ ids,
+                          const DevCounters* __restrict__ ctr, uint32_t* __restrict__ work, int cls) {
+    __shared__ uint32_t s_item;
+    if (ctr->skip) return;
+    uint32_t count, first, k = 0;
+    class_span(ctr, cls, count, first);
+    for (uint32_t item; (item = next_item(work, cls, k, count, &s_item)) != 0xffffffffu;) {
+        const int tile = (int)order[first + item];
+        const uint2 r = ranges[tile];
+        if (r.y - r.x <= 8u * 1024u)
+            tile_radix_one<1024, 8>(ranges, tile, keys, ids);
+        else
+            tile_radix_one<1024, 16>(ranges, tile, keys, ids);
+        __syncthreads();
+    }
+}
+
+static_assert(kMaxSmemTile == 16 * 1024, "the largest sort class holds 16 keys per thread");
+
+static void radix_big_launch(uint32_t bound, const uint2* ranges, const uint32_t* order,
+                             const unsigned long long* keys, uint32_t* ids, const DevCounters* ctr,
+                             uint32_t* work, int cls, cudaStream_t st);
+
 // Persistent grid for a sort class: as many CTAs as fit on the GPU at once
 // (at most `bound`), each looping over the class's tiles.
 template <typename K>
@@ -659,6 +687,20 @@ static void radix_class_launch(uint32_t bound, const uint2* ranges, const uint32
                                                                  work, cls);
 }
 
+static void radix_big_launch(uint32_t bound, const uint2* ranges, const uint32_t* order,
+                             const unsigned long long* keys, uint32_t* ids, const DevCounters* ctr,
+                             uint32_t* work, int cls, cudaStream_t st) {
+    const size_t smem = sizeof(uint32_t) * (2 * 16 * 1024 + 32 * 256);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(tile_radix_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attr = true;
+    }
+    const int g = persistent_grid(tile_radix_big_kernel, 1024, smem, bound);
+    tile_radix_big_kernel<<<g, 1024, smem, st>>>(ranges, order, keys, ids, ctr, work, cls);
+}
+
 template <int THREADS>
 static void sort_class_launch(uint32_t bound, const uint2* ranges, const uint32_t* order,
                               const unsigned long long* keys, uint32_t* ids,
@@ -679,8 +721,9 @@ int launch_tile_sort_class(int c, uint32_t bound, const uint2* ranges, const uin
     const bool radix = c < radix_classes;
     switch (c) {
         case 0:
-            if (radix) radix_class_launch<1024>(bound, ranges, order, keys, ids, counters, work, c, st);
-            else sort_class_launch<1024>(bound, ranges, order, keys, ids, counters, work, c, st);
+            // always the radix sort: it alone holds tiles above 8192 pairs
+            (void)radix;
+            radix_big_launch(bound, ranges, order, keys, ids, counters, work, c, st);
             break;
         case 1:
             if (radix) radix_class_launch<512>(bound, ranges, order, keys, ids, counters, work, c, st);

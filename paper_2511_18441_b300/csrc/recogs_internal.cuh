@@ -86,9 +86,9 @@ constexpr uint32_t kErrCrowded = 4u;   // a tile above the per-tile sort's limit
 constexpr size_t kCountersClearBytes = 56;  // the fields before `error`
 static_assert(sizeof(DevCounters) == 64, "DevCounters layout");
 
-// Largest tile list sorted by the per-tile sort (8192 keys for a CTA of 1024
-// threads); a frame with a larger tile takes the global radix path.
-constexpr int kMaxSmemTile = 8192;
+// Largest tile list sorted by the per-tile sort (16384 keys: 16 per thread of
+// a CTA of 1024 threads); a frame with a larger tile takes the global radix path.
+constexpr int kMaxSmemTile = 16384;
 // Per-tile pair counters are split into partitions (by block index) so that
 // concurrent blocks rarely update the same counter; the counters are stored
 // partition-major, so the partitions of a tile sit in different L2 slices

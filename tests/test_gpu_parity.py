@@ -318,8 +318,44 @@ def test_sort_paths_agree(ctx, W, H):
         assert np.array_equal(a, b)
 
 
+def test_dense_tile_per_tile_path(ctx):
+    """Between 8192 and 16384 pairs in a tile: the largest sort class (16
+    keys per thread) sorts it in shared memory; identical to the global path
+    and to the oracle, also without the read back."""
+    rng = np.random.default_rng(6)
+    n = 11_000
+    xyz = np.stack([rng.normal(0, 0.004, n), rng.normal(0, 0.004, n), rng.uniform(-0.3, 0.3, n)])
+    sc = sg.Scene(xyz.astype(np.float32), np.full((3, n), -5.5, np.float32),
+                  rng.normal(size=(4, n)).astype(np.float32),
+                  rng.normal(-2.0, 1.0, n).astype(np.float32),
+                  rng.normal(0, 0.3, (16, 3, n)).astype(np.float32))
+    cam = sg.axis_camera(64, 64, 60.0, 2.5)
+    ds = dscene(sc)
+    out = {}
+    for path in (1, 2):
+        ctx.set_sort_path(path)
+        img, T, st = render(ctx, ds, cam, None, stats=True)
+        ranges, gids = ctx.tile_lists(st["n_tiles"], st["n_pairs"])
+        torch.cuda.synchronize()
+        out[path] = (img, T, parity.to_np(ranges), parity.to_np(gids))
+    ctx.set_sort_path(0)
+    r = out[1][2]
+    assert 8192 < (r[:, 1] - r[:, 0]).max() <= 16384
+    for a, b in zip(out[1], out[2]):
+        assert np.array_equal(a, b)
+    ref, sp, order, off, ids = oracle.render_image(sc, cam, None)
+    parity.check_image(out[1][0], out[1][1], ref)
+    parity.check_tile_lists(r, out[1][3], sp, off, ids)
+    # without the read back the frame stays on the per-tile path
+    ctx.set_pair_capacity(int(r[-1, 1]) + 1024)
+    img2, T2 = render(ctx, ds, cam, None)
+    ctx.check()
+    ctx.set_pair_capacity(0)
+    assert np.array_equal(img2, out[1][0]) and np.array_equal(T2, out[1][1])
+
+
 def test_crowded_tile_takes_global_path(ctx):
-    """More than 8192 pairs in one tile: the per-tile shared-memory sort
+    """More than 16384 pairs in one tile: the per-tile shared-memory sort
     cannot hold the list, so the frame takes the global radix path."""
     rng = np.random.default_rng(5)
     n = 20_000
