@@ -509,7 +509,11 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
         if (!sc.ev_fork) {
             CK(cudaEventCreateWithFlags(&sc.ev_fork, cudaEventDisableTiming));
             for (int k = 0; k < kSortClasses; ++k) {
-                CK(cudaStreamCreateWithFlags(&sc.aux[k], cudaStreamNonBlocking));
+                // the two largest classes hold the longest sorts: their CTAs
+                // are scheduled first when the classes compete for the SMs
+                int lo = 0, hi = 0;
+                CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+                CK(cudaStreamCreateWithPriority(&sc.aux[k], cudaStreamNonBlocking, k < 2 ? hi : lo));
                 CK(cudaEventCreateWithFlags(&sc.ev_join[k], cudaEventDisableTiming));
             }
         }
