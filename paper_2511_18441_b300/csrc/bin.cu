@@ -486,8 +486,10 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i)
         if (warp * PW + i * 32 + lane < n) key[i] -= zmin;
-    for (int pass = 0; pass < passes; ++pass) {
-        const int shift = 8 * pass;
+    // one stable 8-bit pass: items ordered by digit (BY_VAL ? val - vbase :
+    // key) >> shift, kept in registers at positions warp * PW + i * 32 + lane
+    // and copied to s_key / s_val
+    auto radix_pass = [&](int shift, bool by_val, uint32_t vbase) {
         // each warp clears its own counters (no other warp touches them until
         // the block barrier after the ranking)
         for (int d = lane; d < 256; d += 32) s_wcnt[warp * 256 + d] = 0;
@@ -499,7 +501,8 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
             if (warp * PW + i * 32 >= n) continue;   // warp-uniform: round past the end
             const int p = warp * PW + i * 32 + lane;
             const bool ok = p < n;
-            const uint32_t dg = ok ? ((key[i] >> shift) & 0xffu) : 256u;
+            const uint32_t src = by_val ? val[i] - vbase : key[i];
+            const uint32_t dg = ok ? ((src >> shift) & 0xffu) : 256u;
             // lanes with the same digit: the intersection of the digit's bit
             // ballots (measured faster than a warp match: tile sort 0.136
             // against 0.158 ms at 3M Gaussians)
@@ -553,7 +556,8 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
         for (int i = 0; i < ITEMS; ++i) {
             const int p = warp * PW + i * 32 + lane;
             if (p < n) {
-                const uint32_t dg = (key[i] >> shift) & 0xffu;
+                const uint32_t src = by_val ? val[i] - vbase : key[i];
+                const uint32_t dg = (src >> shift) & 0xffu;
                 const uint32_t q = s_dstart[dg] + s_wcnt[warp * 256 + dg] + rank[i];
                 s_key[q] = key[i];
                 s_val[q] = val[i];
@@ -568,7 +572,8 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
                 val[i] = s_val[p];
             }
         }
-    }
+    };
+    for (int pass = 0; pass < passes; ++pass) radix_pass(8 * pass, false, 0u);
     if (passes == 0) {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
@@ -580,8 +585,42 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
         }
     }
     __syncthreads();
-    // equal depth keys: order each run by index (insertion sort by the run's first position)
-    for (int p = threadIdx.x; p < n; p += THREADS) {
+    // a run of more than 32 equal depth keys (e.g. many Gaussians at exactly
+    // one depth): the insertion sort below would take quadratic time, so sort
+    // by index first and by depth again (both stable: (depth, index) order)
+    bool long_run = false;
+    for (int p = threadIdx.x; p + 32 < n; p += THREADS) long_run |= s_key[p] == s_key[p + 32];
+    const bool full_order = __syncthreads_or(long_run);
+    if (full_order) {
+        uint32_t vlo = 0xffffffffu, vhi = 0u;
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i)
+            if (warp * PW + i * 32 + lane < n) {
+                vlo = min(vlo, val[i]);
+                vhi = max(vhi, val[i]);
+            }
+        vlo = __reduce_min_sync(0xffffffffu, vlo);
+        vhi = __reduce_max_sync(0xffffffffu, vhi);
+        if (lane == 0) {
+            s_zmin[warp] = vlo;
+            s_zmax[warp] = vhi;
+        }
+        __syncthreads();
+        uint32_t vmin = 0xffffffffu, vmax = 0u;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            vmin = min(vmin, s_zmin[w]);
+            vmax = max(vmax, s_zmax[w]);
+        }
+        const uint32_t vspan = vmax - vmin;
+        const int vpasses = vspan == 0u ? 0 : (32 - __clz((int)vspan) + 7) / 8;
+        for (int pass = 0; pass < vpasses; ++pass) radix_pass(8 * pass, true, vmin);
+        for (int pass = 0; pass < passes; ++pass) radix_pass(8 * pass, false, 0u);
+        // (s_key / s_val hold the final order; no run is left unordered)
+    }
+    // equal depth keys: order each run (at most 32 long here) by index
+    // (insertion sort by the run's first position)
+    for (int p = threadIdx.x; p < n && !full_order; p += THREADS) {
         const bool starts = (p == 0 || s_key[p - 1] != s_key[p]) && p + 1 < n && s_key[p + 1] == s_key[p];
         if (starts) {
             int e = p + 1;

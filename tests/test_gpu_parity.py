@@ -354,6 +354,39 @@ def test_dense_tile_per_tile_path(ctx):
     assert np.array_equal(img2, out[1][0]) and np.array_equal(T2, out[1][1])
 
 
+def test_equal_depth_run_in_a_tile(ctx):
+    """Thousands of Gaussians at exactly one depth in one tile: the per-tile
+    radix sort orders the run by index (sorting by index, then by depth)
+    instead of an insertion sort, and agrees bit for bit with the global
+    path, which orders ties by index too."""
+    rng = np.random.default_rng(7)
+    n = 6_000
+    xyz = np.stack([rng.normal(0, 0.004, n), rng.normal(0, 0.004, n), np.zeros(n)])
+    sc = sg.Scene(xyz.astype(np.float32), np.full((3, n), -5.5, np.float32),
+                  rng.normal(size=(4, n)).astype(np.float32),
+                  rng.normal(-2.0, 1.0, n).astype(np.float32),
+                  rng.normal(0, 0.3, (16, 3, n)).astype(np.float32))
+    cam = sg.axis_camera(64, 64, 60.0, 2.5)
+    ds = dscene(sc)
+    out = {}
+    for path in (1, 2):
+        ctx.set_sort_path(path)
+        img, T, st = render(ctx, ds, cam, None, stats=True)
+        ranges, gids = ctx.tile_lists(st["n_tiles"], st["n_pairs"])
+        torch.cuda.synchronize()
+        out[path] = (img, T, parity.to_np(ranges), parity.to_np(gids))
+    ctx.set_sort_path(0)
+    r = out[1][2]
+    assert (r[:, 1] - r[:, 0]).max() > 1000
+    for a, b in zip(out[1], out[2]):
+        assert np.array_equal(a, b)
+    # every tile list in index order (one depth)
+    g = out[1][3]
+    for t in range(len(r)):
+        lst = g[r[t, 0]:r[t, 1]]
+        assert np.all(np.diff(lst.astype(np.int64)) > 0)
+
+
 def test_crowded_tile_takes_global_path(ctx):
     """More than 16384 pairs in one tile: the per-tile shared-memory sort
     cannot hold the list, so the frame takes the global radix path."""
