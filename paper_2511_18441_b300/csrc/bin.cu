@@ -213,9 +213,12 @@ __global__ void __launch_bounds__(kScatterThreads)
                    const uint32_t* __restrict__ zkey, int n, int tiles_x, int tiles,
                    const uint2* __restrict__ ranges, uint32_t* __restrict__ cursor, int parts,
                    unsigned long long* __restrict__ keys, const DevCounters* __restrict__ ctr) {
+    __shared__ uint32_t s_nbig, s_big[kScatterG * kScatterThreads];
     grid_dependency_wait();     // the tile scan's ranges and flags
     if (*reinterpret_cast<const volatile uint32_t*>(&ctr->skip)) return;  // pairs exceed the buffers
     constexpr int G = kScatterG;
+    if (threadIdx.x == 0) s_nbig = 0;
+    __syncthreads();
     uint32_t c[G], row[G], w[G], col[G];
     uint32_t* cur[G];
     unsigned long long key[G];
@@ -229,6 +232,11 @@ __global__ void __launch_bounds__(kScatterThreads)
         w[g] = 1;
         col[g] = 0;
         key[g] = 0;
+        if (c[g] > kBigPairs) {
+            // many tiles: the block scatters this Gaussian's pairs together below
+            s_big[atomicAdd(&s_nbig, 1u)] = (uint32_t)i;
+            c[g] = 0;
+        }
         if (c[g]) {
             const uint2 r = rect[i];
             const uint32_t x0 = r.x & 0xffffu, y0 = r.y & 0xffffu;
@@ -252,6 +260,22 @@ __global__ void __launch_bounds__(kScatterThreads)
                     row[g] += (uint32_t)tiles_x;
                 }
             }
+        }
+    }
+    // the block's Gaussians with many tiles, each by all threads of the block
+    __syncthreads();
+    const uint32_t nbig = s_nbig;
+    for (uint32_t b = 0; b < nbig; ++b) {
+        const uint32_t i = s_big[b];
+        const uint32_t cb = count[i];
+        const uint2 r = rect[i];
+        const uint32_t x0 = r.x & 0xffffu, y0 = r.y & 0xffffu, wb = (r.x >> 16) - x0 + 1;
+        const unsigned long long kb = ((unsigned long long)zkey[i] << 32) | i;
+        uint32_t* cb_cur = cursor + (size_t)((i / kScatterThreads) & (uint32_t)(parts - 1)) * tiles;
+        for (uint32_t k = threadIdx.x; k < cb; k += kScatterThreads) {
+            const uint32_t dy = k / wb;
+            const uint32_t t = (y0 + dy) * (uint32_t)tiles_x + x0 + (k - dy * wb);
+            keys[ranges[t].x + atomicAdd(cb_cur + t, 1u)] = kb;
         }
     }
 }

@@ -400,19 +400,39 @@ __device__ __forceinline__ uint32_t prep_one(int i, float mx, float my, float mz
 // Per-chunk epilogue (a chunk = kPrepThreads consecutive Gaussians, one per
 // thread): pairs per tile and partition, and the chunk's visible and pair
 // totals. s_*: per-warp shared scratch.
+// A Gaussian of the chunk covering more than kBigPairs tiles, counted by the
+// whole block after the chunk's barrier (per warp: up to 32 entries).
+struct PrepBig {
+    uint32_t row0[kPrepThreads], rw[kPrepThreads], cnt[kPrepThreads];
+    uint32_t n[kPrepThreads / 32];
+};
+
 __device__ __forceinline__ void prep_chunk_end(int chunk, int n_chunks, uint32_t cnt,
                                                uint32_t zbits, int rx0, int ry0, int rw,
                                                const DevCamera& cam, const PrepOut& out,
                                                uint32_t* s_v, uint32_t* s_p, uint32_t* s_zmin,
-                                               uint32_t* s_zmax) {
+                                               uint32_t* s_zmax, PrepBig& s_big) {
     const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* tc = nullptr;
+    bool has_big = false;
     if (out.tile_count) {
         // one atomic per pair (measured faster than aggregating the lanes of a
         // warp on the same tile with a warp match: 0.162 against 0.169 ms at
         // 3M Gaussians); this lane's tiles row by row through its rectangle
-        uint32_t* tc = out.tile_count + (size_t)(chunk & (out.parts - 1)) * (cam.tiles_x * cam.tiles_y);
+        tc = out.tile_count + (size_t)(chunk & (out.parts - 1)) * (cam.tiles_x * cam.tiles_y);
         uint32_t row = (uint32_t)ry0 * (uint32_t)cam.tiles_x + (uint32_t)rx0, col = 0;
-        for (uint32_t k = 0; k < cnt; ++k) {
+        const bool big = cnt > kBigPairs;
+        has_big = big;
+        const uint32_t bm = __ballot_sync(full, big);
+        if (big) {
+            const int q = warp * 32 + __popc(bm & ((1u << lane) - 1u));
+            s_big.row0[q] = row;
+            s_big.rw[q] = (uint32_t)rw;
+            s_big.cnt[q] = cnt;
+        }
+        if (lane == 0) s_big.n[warp] = __popc(bm);
+        for (uint32_t k = 0; k < (big ? 0u : cnt); ++k) {
             atomicAdd(tc + row + col, 1u);
             if (++col == (uint32_t)rw) {
                 col = 0;
@@ -428,14 +448,28 @@ __device__ __forceinline__ void prep_chunk_end(int chunk, int n_chunks, uint32_t
     const uint32_t wp = __reduce_add_sync(full, cnt);
     const uint32_t wzmin = __reduce_min_sync(full, cnt > 0 ? zbits : 0xffffffffu);
     const uint32_t wzmax = __reduce_max_sync(full, cnt > 0 ? zbits : 0u);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
         s_v[warp] = wv;
         s_p[warp] = wp;
         s_zmin[warp] = wzmin;
         s_zmax[warp] = wzmax;
     }
-    __syncthreads();
+    // (the barrier also tells whether any Gaussian of the chunk has many tiles)
+    const bool any_big = __syncthreads_or(has_big);
+    // the chunk's Gaussians with many tiles, each counted by the whole block
+    if (any_big) {
+        for (int w = 0; w < kPrepThreads / 32; ++w) {
+            const uint32_t nb = s_big.n[w];
+            for (uint32_t b = 0; b < nb; ++b) {
+                const uint32_t row0 = s_big.row0[w * 32 + b], bw = s_big.rw[w * 32 + b];
+                const uint32_t bc = s_big.cnt[w * 32 + b];
+                for (uint32_t k = threadIdx.x; k < bc; k += kPrepThreads) {
+                    const uint32_t dy = k / bw;
+                    atomicAdd(tc + row0 + dy * (uint32_t)cam.tiles_x + (k - dy * bw), 1u);
+                }
+            }
+        }
+    }
     if (threadIdx.x == 0) {
         uint32_t tv = 0, tp = 0, zmin = 0xffffffffu, zmax = 0u;
 #pragma unroll
@@ -481,6 +515,7 @@ __global__ void __launch_bounds__(kPrepThreads, PrepMinBlocks<T>::value)
     __shared__ uint32_t s_v[kPrepThreads / 32], s_p[kPrepThreads / 32];
     __shared__ uint32_t s_zmin[kPrepThreads / 32], s_zmax[kPrepThreads / 32];
     __shared__ float4 s_rec[3 * kPrepThreads];   // the block's records, staged per warp
+    __shared__ PrepBig s_big;
     const int chunk = blockIdx.x;
     const int i = chunk * kPrepThreads + threadIdx.x;
     // the chunk's 48 SH rows (one contiguous run per row) start on their way
@@ -525,7 +560,8 @@ __global__ void __launch_bounds__(kPrepThreads, PrepMinBlocks<T>::value)
         for (int k = 0; k < 3; ++k)
             if (base + 32 * k + lane < lim) out.rec[base + 32 * k + lane] = sw[32 * k + lane];
     }
-    prep_chunk_end(chunk, n_chunks, cnt, zbits, rx0, ry0, rw, cam, out, s_v, s_p, s_zmin, s_zmax);
+    prep_chunk_end(chunk, n_chunks, cnt, zbits, rx0, ry0, rw, cam, out, s_v, s_p, s_zmin, s_zmax,
+                   s_big);
 }
 
 template <typename T>

@@ -96,6 +96,10 @@ constexpr int kMaxSmemTile = 16384;
 // partitions, 0.079 partition-major with 16, 0.073 with 32, 0.076 with 64).
 // kTileParts for the context path, kTilePartsSmall for the allocation-free one.
 constexpr int kTileParts = 32;
+// A Gaussian covering more tiles than this has its pairs counted and scattered
+// by all threads of its block together instead of by its own thread alone
+// (one thread looping over hundreds of tiles would hold up the kernel).
+constexpr uint32_t kBigPairs = 64;
 constexpr int kTilePartsSmall = 32;
 
 // Position bucket of a tile with c pairs in the tile order (heaviest first,

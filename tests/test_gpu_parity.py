@@ -387,6 +387,34 @@ def test_equal_depth_run_in_a_tile(ctx):
         assert np.all(np.diff(lst.astype(np.int64)) > 0)
 
 
+def test_large_gaussians_counted_and_scattered_by_the_block(ctx):
+    """Gaussians covering hundreds of tiles (their pairs are counted and
+    scattered by the whole block): identical to the global path and to the
+    oracle."""
+    w = sg.paper_scale_workload(n=60_000, width=640, height=360)
+    sc = w.scene
+    big = np.arange(0, sc.n, 997)
+    sc.log_scale[:, big] = np.float32(0.3)          # a few Gaussians of metre scale
+    sc.opacity_logit[big] = np.float32(-3.0)       # faint, so the rest stays visible
+    ds = dscene(sc)
+    out = {}
+    for path in (1, 2):
+        ctx.set_sort_path(path)
+        img, T, st = render(ctx, ds, w.camera, w.edit, stats=True)
+        ranges, gids = ctx.tile_lists(st["n_tiles"], st["n_pairs"])
+        torch.cuda.synchronize()
+        out[path] = (img, T, parity.to_np(ranges), parity.to_np(gids))
+    ctx.set_sort_path(0)
+    for a, b in zip(out[1], out[2]):
+        assert np.array_equal(a, b)
+    ref, sp, order, off, ids = oracle.render_image(sc, w.camera, w.edit)
+    rect = sp["rect"].reshape(-1, 4)
+    ntiles = (rect[:, 1] - rect[:, 0] + 1) * (rect[:, 3] - rect[:, 2] + 1)
+    assert (ntiles[big] > 64).sum() >= 20
+    parity.check_image(out[1][0], out[1][1], ref)
+    parity.check_tile_lists(out[1][2], out[1][3], sp, off, ids)
+
+
 def test_crowded_tile_takes_global_path(ctx):
     """More than 16384 pairs in one tile: the per-tile shared-memory sort
     cannot hold the list, so the frame takes the global radix path."""
