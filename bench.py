@@ -209,7 +209,8 @@ def kernel_source_sha(kernel_file):
 def profiled_traffic(stage):
     """DRAM bytes per launch from a committed ncu summary, or None if absent
     or taken on a different version of the kernel's source."""
-    files = {"blend": "blend.cu", "preprocess": "preprocess.cu"}
+    files = {"blend": "blend.cu", "preprocess": "preprocess.cu", "refit": "refit.cu",
+             "blend_grad": "blend.cu"}
     if stage not in files:
         return None
     path = os.path.join(ROOT, "profiles", f"traffic_{stage}_3m_1080p.txt")
@@ -586,6 +587,242 @@ def run_batch(args, rank, world, local):
 
 
 # ---------------------------------------------------------------------------
+# the refit tail: median depth (Sec. 3.2.2) and the SH-only refit (Sec. 3.3)
+
+REFIT_LR = 0.005
+
+
+def refit_algorithmic_bytes(stage, stats, n, n_vis):
+    """Minimum bytes of one launch of the refit's own kernels."""
+    W, H = WIDTH, HEIGHT
+    if stage == "refit":
+        # per Gaussian: 4 B count, SH, m and v (48 float32 each) read and
+        # written; per visible Gaussian: 12 B position, 16 B colour record,
+        # 12 B colour gradient
+        return n * (4 + 6 * 48 * 4) + n_vis * (12 + 16 + 12)
+    if stage == "blend_grad":
+        # per consumed pair 40 B; image and target 24 B/pixel; 8 B range per
+        # tile; the colour gradient of every visible Gaussian written once
+        return stats["n_pairs_read"] * 40 + 24 * W * H + 8 * stats["n_tiles"] + 12 * n_vis
+    return None
+
+
+def oracle_refit_step(w, lr, threads):
+    """One FP64 oracle refit step of the whole workload on the host cores:
+    per-Gaussian pass, depth order, tile lists, full render, L1 gradient,
+    colour gradient, SH gradient and an Adam step. Returns seconds."""
+    import oracle
+    t0 = time.perf_counter()
+    sp = oracle.preprocess(w.scene, w.camera, None, threads=threads)
+    order = oracle.depth_order(sp)
+    tx, ty = (WIDTH + 15) // 16, (HEIGHT + 15) // 16
+    off, ids = oracle.tile_lists(sp, order, tx, ty)
+    y = oracle.render_tiles(sp, off, ids, threads=threads)
+    target = np.clip(y["rgb"][:, :, ::-1], 0.0, None)   # any fixed target: channels swapped
+    _, g = oracle.l1_loss_grad(y["rgb"], target)
+    grgb = oracle.color_grad(sp, off, ids, g)
+    gsh = oracle.sh_grad(w.scene, sp, grgb)
+    C = np.asarray(w.scene.sh, np.float64)
+    oracle.adam_step(C, gsh, np.zeros_like(gsh), np.zeros_like(gsh), 1, lr)
+    return time.perf_counter() - t0
+
+
+def run_refit(args, rank, world, local):
+    """The refit tail at the headline workload (3M SH3 Gaussians, 1920x1080,
+    polygon selection and hue rotation). (1) The median-depth render
+    (Sec. 3.2.2) against the plain render, frames/s. (2) SH-only refit steps
+    (Sec. 3.3) towards the edited render of the same view: forward render, L1
+    colour gradient, SH gradient and Adam on every coefficient; steps/s, stage
+    times, the dominant kernel's roofline, the loss before and after, and one
+    FP64 oracle step on the host cores."""
+    import torch
+    from paper_2511_18441_b300 import binding, build
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the library has no CPU path)")
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = make_workload()
+    cam = w.camera
+    n = N_SPLATS
+    ds = binding.DeviceScene.from_numpy(w.scene, dev, "f32")
+    ctx = binding.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    img = torch.empty((HEIGHT, WIDTH, 3), dtype=torch.float32, device=dev)
+    depth = torch.empty((HEIGHT, WIDTH), dtype=torch.float32, device=dev)
+    warm = max(3, args.warmup)
+
+    def timed(fn, k):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        return max_over_ranks(e0.elapsed_time(e1), world, dev) / k
+
+    def stage_breakdown(fn, k):
+        ctx.set_timing(True)
+        ctx.stage_times(reset=True)
+        for _ in range(k):
+            fn()
+        torch.cuda.synchronize(dev)
+        b = {s: v for s, v in ctx.stage_times(reset=True).items()
+             if v[1] > 0 and s not in ("h2d", "d2h")}
+        ctx.set_timing(False)
+        return b
+
+    # (1) median depth: frames without the read back, like the headline frame
+    _, stats_e = ctx.render(ds, cam, w.edit, image_out=img, stats=True, stream=stream)
+    ctx.set_pair_capacity(pair_capacity(stats_e["n_pairs"]))
+    k_depth = max(20, args.steps // 2)
+    plain_ms = timed(lambda: ctx.render(ds, cam, w.edit, image_out=img, stream=stream), k_depth)
+    depth_ms = timed(lambda: ctx.render_depth(ds, cam, w.edit, tau=0.5, image_out=img,
+                                              depth_out=depth, stream=stream), k_depth)
+    ctx.check(stream)
+    bd_plain = stage_breakdown(lambda: ctx.render(ds, cam, w.edit, image_out=img,
+                                                  stream=stream), 20)
+    bd_depth = stage_breakdown(lambda: ctx.render_depth(ds, cam, w.edit, tau=0.5, image_out=img,
+                                                        depth_out=depth, stream=stream), 20)
+    covered = float((depth > 0).float().mean())
+    ctx.set_pair_capacity(0)
+
+    # (2) the refit: the target is the edited render; the fitted scene starts
+    # from the unedited SH coefficients
+    target = ctx.render(ds, cam, w.edit, stream=stream).clone()
+    fit = binding.DeviceScene.from_numpy(w.scene, dev, "f32")
+    m = torch.zeros((16, 3, n), dtype=torch.float32, device=dev)
+    v = torch.zeros_like(m)
+    step = [0]
+
+    def refit_step(want_loss=False):
+        step[0] += 1
+        return ctx.refit_step(fit, cam, target, m, v, step=step[0], lr=REFIT_LR,
+                              want_loss=want_loss, stream=stream)
+
+    loss_first = refit_step(want_loss=True)
+    for _ in range(warm):
+        refit_step()
+    k_breakdown = max(10, args.steps // 4)
+    breakdown = stage_breakdown(refit_step, k_breakdown)
+    dom = max(breakdown, key=lambda s: breakdown[s][0])
+
+    sampler = ClockSampler(gpu_id_for_smi(local))
+    sampler.start()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    ctx.set_timing(True, stages=[dom])
+    ctx.stage_times(reset=True)
+    l0 = ctx.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sampler.mark_begin()
+    e0.record(stream)
+    for _ in range(args.steps):
+        refit_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    sampler.mark_end()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    launches = ctx.launch_count() - l0
+    stages = ctx.stage_times(reset=True)
+    ctx.set_timing(False, stages=None)
+    clocks = sampler.stop()
+    max_ms = max_over_ranks(ms, world, dev)
+    loss_last = refit_step(want_loss=True)
+    fitted = ctx.render(fit, cam, stream=stream)
+    mse = float(((fitted - target) ** 2).mean())
+    start_img = ctx.render(ds, cam, stream=stream)
+    mse0 = float(((start_img - target) ** 2).mean())
+    psnr = lambda e: 10.0 * math.log10(1.0 / e) if e > 0 else float("inf")
+    _, stats_r = ctx.render(fit, cam, image_out=img, stats=True, stream=stream)
+    n_vis = stats_r["n_visible"]
+
+    peaks, peaks_src = load_peaks()
+
+    def roof_of(stage, ms_launch):
+        alg = refit_algorithmic_bytes(stage, stats_r, n, n_vis)
+        if alg is None:
+            alg = algorithmic_bytes(stage, stats_r, n, 4)
+        if alg is None:
+            return None
+        a = alg / (ms_launch / 1000.0) / 1e9
+        return {"kernel": stage, "bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": a / peaks["hbm_gbs"],
+                "peak_source": f"{peaks_src} copy bandwidth", "algorithmic_bytes": alg,
+                "ms_per_launch": ms_launch}
+
+    dom_ms = stages[dom][0] / max(stages[dom][1], 1)
+    roof = roof_of(dom, dom_ms)
+    if roof is not None:
+        roof["traffic"] = profiled_traffic(dom)
+        roof["timed"] = f"CUDA events around each {dom} launch of the {args.steps} timed steps"
+    other = {}
+    for s_ in ("refit", "blend_grad", "blend", "preprocess"):
+        if s_ in breakdown and s_ != dom:
+            r = roof_of(s_, breakdown[s_][0] / max(breakdown[s_][1], 1))
+            if r is not None:
+                other[s_] = {"achieved_gbs": r["achieved"], "frac": r["frac"],
+                             "ms_per_launch": r["ms_per_launch"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        sec = oracle_refit_step(w, REFIT_LR, cores)
+        cpu = {"value": 1.0 / sec, "unit": "steps/s", "cores": cores, "kind": "oracle",
+               "sample": (f"one whole FP64 oracle refit step of the workload ({n} Gaussians, "
+                          f"{WIDTH}x{HEIGHT}: render on {cores} threads, colour gradient on one "
+                          f"thread, SH gradient, numpy Adam): {sec:.1f} s")}
+
+    if rank == 0:
+        line = {
+            "metric": ("SH refit steps/s at 1080p, 3M SH3 splats (render, L1 colour and SH "
+                       "gradients, Adam)"),
+            "value": args.steps * world / (max_ms / 1000.0), "unit": "steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": warm,
+            "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator)",
+            "config": {"workload": (f"SH-only refit of {n / 1e6:g}M SH3 Gaussians at "
+                                    f"{WIDTH}x{HEIGHT} towards the render of the 12-gon + "
+                                    f"90 deg hue edit, Adam lr {REFIT_LR}; median depth "
+                                    "(tau 0.5) of the edited frame"),
+                       "n_gaussians": n, "width": WIDTH, "height": HEIGHT, "seed": SEED,
+                       "l2": (f"inputs larger than L2 (SH, m and v {3 * 192 * n / 1e9:.2f} GB); "
+                              "no flush"),
+                       "step": ("recogs_refit_step: render with the mid-frame read back, "
+                                "gradient blend, SH gradient + Adam; no loss read back")},
+            "frame_stats": stats_r,
+            "stage_ms_per_step": {s_: round(v_[0] / k_breakdown, 4) for s_, v_ in breakdown.items()},
+            "stage_ms_note": f"every stage timed by events over {k_breakdown} extra steps",
+            "roofline": roof,
+            "roofline_other": other,
+            "quality": {"loss_step1": loss_first, "loss_after": loss_last,
+                        "steps_taken": step[0], "psnr_start_vs_target": psnr(mse0),
+                        "psnr_fitted_vs_target": psnr(mse)},
+            "median_depth": {
+                "frames_per_s": 1000.0 / depth_ms, "ms_per_frame": depth_ms,
+                "plain_frames_per_s": 1000.0 / plain_ms, "plain_ms_per_frame": plain_ms,
+                "overhead_ms": depth_ms - plain_ms, "pixels_with_depth": covered,
+                "blend_ms": bd_depth.get("blend", (0, 1))[0] / 20,
+                "plain_blend_ms": bd_plain.get("blend", (0, 1))[0] / 20,
+                "api": "recogs_render_depth (tau 0.5) vs recogs_render, pair capacity preset"},
+            "cpu_baseline": cpu,
+            "e2e": None,
+            "e2e_note": "the refit entry points take device buffers only",
+            "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
 # the learned selection workload
 
 MLP_SPLATS = 6_000_000
@@ -751,9 +988,10 @@ def main(argv=None):
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--readback", action="store_true",
                     help="time frames with the mid-frame read back (default: pair capacity preset)")
-    ap.add_argument("--workload", choices=["frame", "batch", "mlp"], default="frame",
+    ap.add_argument("--workload", choices=["frame", "batch", "mlp", "refit"], default="frame",
                     help="frame: the 3M/1080p headline; batch: 64 views of 4 scenes; "
-                         "mlp: the learned selection at 6M Gaussians")
+                         "mlp: the learned selection at 6M Gaussians; refit: median depth "
+                         "and SH-only refit steps at 3M/1080p")
     ap.add_argument("--mlp-steps", type=int, default=4000,
                     help="training steps of the mlp workload (batch 16384)")
     ap.add_argument("--gaussians", type=int, default=None,
@@ -772,6 +1010,8 @@ def main(argv=None):
             run_batch(args, rank, world, local)
         elif args.workload == "mlp":
             run_mlp(args, rank, world, local)
+        elif args.workload == "refit":
+            run_refit(args, rank, world, local)
         else:
             run_ours(args, rank, world, local)
     finally:

@@ -29,14 +29,14 @@ namespace {
 enum Stage {
     ST_PREPROCESS, ST_SCAN, ST_COMPACT, ST_SORT_DEPTH, ST_PAIR_OFFSETS, ST_EMIT, ST_SORT_TILE,
     ST_BLEND, ST_SELECT, ST_RECOLOR, ST_H2D, ST_D2H, ST_SCATTER, ST_TILE_SORT, ST_REFIT, ST_MLP,
-    ST_SORT_BLEND, ST_COUNT
+    ST_SORT_BLEND, ST_BLEND_GRAD, ST_COUNT
 };
 // "scan" = tile totals, tile ranges and tile order; "compact" .. "sort_tile"
-// = the global sort path
+// = the global sort path; "blend_grad" = the refit's gradient blend
 const char* const kStageNames[ST_COUNT] = {
     "preprocess", "scan", "compact", "sort_depth", "pair_offsets", "emit", "sort_tile",
     "blend", "select", "recolor", "h2d", "d2h", "scatter", "tile_sort", "refit", "mlp",
-    "sort_blend"};
+    "sort_blend", "blend_grad"};
 
 struct DevBuf {
     void* p = nullptr;
@@ -1035,11 +1035,11 @@ recogs_status refit(recogs_ctx* ctx, const recogs_scene& s, const recogs_camera&
     ex.grad_rgb = grad_rgb;
     ex.loss = P<double>(ctx->rf_loss);
     const uint32_t* ids = ctx->last_ids;
-    stage_begin(ctx, ST_BLEND, st);
+    stage_begin(ctx, ST_BLEND_GRAD, st);
     int l = launch_blend(P<uint2>(ctx->main.ranges), P<uint32_t>(ctx->main.order), ids,
                          P<float4>(ctx->main.rec), dc, bgv, image, nullptr, nullptr,
                          sched.blend_batch, &ex, st);
-    stage_end(ctx, ST_BLEND, l, st);
+    stage_end(ctx, ST_BLEND_GRAD, l, st);
     // 3. SH gradient and the optional Adam step
     RefitAdam ra = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (adam) {

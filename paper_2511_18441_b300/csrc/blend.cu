@@ -154,6 +154,27 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
             l1 = fabsf(d0) + fabsf(d1) + fabsf(d2);
         }
     }
+    // gradient mode: the group sums of g_c w (c = 0, 1, 2) of a hit are a
+    // reduce-scatter over the group's 8 lanes. Lane bit 0 (b) picks the
+    // channel pair it keeps, P0 = (0, 1) or P1 = (2, none), and sends the
+    // other pair to lane ^ 1; bit 1 (c) picks the member of the pair it keeps
+    // and sends the other to lane ^ 2; lane ^ 4 completes the sum. The sums
+    // are linear in w, so the per-lane channel order is fixed here once:
+    // kp = the kept pair and sp = the sent pair, each with the member kept at
+    // the second step first. Lane ends with channel 2b + c (3: padding).
+    float kp0 = 0.f, kp1 = 0.f, sp0 = 0.f, sp1 = 0.f;
+    const int red_ch = 2 * (lane & 1) + ((lane >> 1) & 1);
+    const bool red_lane = (lane & 4) == 0 && red_ch < 3;
+    if (MODE == kBlendGrad) {
+        const bool rc = (lane >> 1) & 1;
+        const float p0a = rc ? g1 : g0, p0b = rc ? g0 : g1;
+        const float p1a = rc ? 0.f : g2, p1b = rc ? g2 : 0.f;
+        const bool rb = lane & 1;
+        kp0 = rb ? p1a : p0a;
+        kp1 = rb ? p1b : p0b;
+        sp0 = rb ? p0a : p1a;
+        sp1 = rb ? p0b : p1b;
+    }
     if (MODE == kBlendCover && inside) {
         // weights 1[pixel centre in the region] and 1 (the pixel centre is (px, py))
         g0 = in_region(*ex.region, (float)px, (float)py) ? 1.f : 0.f;
@@ -236,9 +257,18 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
             cr = fmaf(b.z, w, cr);
             cg = fmaf(b.w, w, cg);
             cb = fmaf(c.x, w, cb);
+        } else if (MODE == kBlendGrad) {
+            // gradient: g alpha T, reduce-scattered over the group (above)
+            const float r0 = __shfl_xor_sync(0xffffffffu, sp0 * w, 1);
+            const float r1 = __shfl_xor_sync(0xffffffffu, sp1 * w, 1);
+            const float u0 = fmaf(kp0, w, r0);
+            const float u1 = fmaf(kp1, w, r1);
+            float x = u0 + __shfl_xor_sync(0xffffffffu, u1, 2);
+            x += __shfl_xor_sync(0xffffffffu, x, 4);
+            if (red_lane && o != kSent) atomicAdd(&s_g[3 * (o >> 4) + red_ch], x);
         } else {
-            // gradient: g alpha T; coverage: g (alpha T)^2
-            const float wc = MODE == kBlendCover ? w * w : w;
+            // coverage: g (alpha T)^2
+            const float wc = w * w;
             const float v0 = group_sum(g0 * wc), v1 = group_sum(g1 * wc);
             const float v2 = group_sum(g2 * w);
             if ((lane & 7) == 0 && o != kSent) {

@@ -115,8 +115,11 @@ def close_enough(gpu, ref, rel=1e-3, floor=1e-4, outliers=0.01):
     return frac
 
 
-def test_refit_gradients_match_the_oracle(ctx):
-    w = sg.tiny_workload(n=6000, width=128, height=96)
+# n % 4 == 0 takes the row-tiled SH kernel (2048 Gaussians per block: three
+# blocks, a ragged last one), other n the one-Gaussian-per-thread kernel
+@pytest.mark.parametrize("n", [6000, 6003])
+def test_refit_gradients_match_the_oracle(ctx, n):
+    w = sg.tiny_workload(n=n, width=128, height=96)
     ds = dscene(w.scene)
     y_or = oracle.render_image(w.scene, w.camera)[0]
     target = target_away_from(y_or["rgb"], 3).astype(np.float32)
@@ -131,8 +134,9 @@ def test_refit_gradients_match_the_oracle(ctx):
     assert np.abs(grgb).max() > 0
 
 
-def test_refit_step_is_the_oracle_adam_step(ctx):
-    w = sg.tiny_workload(n=4000, width=96, height=96)
+@pytest.mark.parametrize("n", [4000, 4001])
+def test_refit_step_is_the_oracle_adam_step(ctx, n):
+    w = sg.tiny_workload(n=n, width=96, height=96)
     ds = dscene(w.scene)
     y_or = oracle.render_image(w.scene, w.camera)[0]
     target = target_away_from(y_or["rgb"], 4).astype(np.float32)
@@ -153,6 +157,39 @@ def test_refit_step_is_the_oracle_adam_step(ctx):
     # no gradient, no move
     assert np.array_equal(C1[gsh == 0], C0[gsh == 0])
     close_enough(parity.to_np(m), m_or)
+
+
+@pytest.mark.parametrize("n", [4000, 4001])
+def test_refit_second_step_is_the_oracle_adam_step(ctx, n):
+    """Step 2 from the GPU's own state after step 1: the oracle gradient at
+    the stepped coefficients and the oracle Adam update with the bias
+    corrections of t = 2."""
+    import dataclasses
+    w = sg.tiny_workload(n=n, width=96, height=96)
+    ds = dscene(w.scene)
+    y_or = oracle.render_image(w.scene, w.camera)[0]
+    target = target_away_from(y_or["rgb"], 5).astype(np.float32)
+    tg = torch.from_numpy(target).cuda()
+    m = torch.zeros((16, 3, ds.n), device="cuda")
+    v = torch.zeros_like(m)
+    ctx.refit_step(ds, w.camera, tg, m, v, step=1, lr=0.002)
+    torch.cuda.synchronize()
+    C1 = parity.to_np(ds.sh).astype(np.float64)
+    m1 = parity.to_np(m).astype(np.float64)
+    v1 = parity.to_np(v).astype(np.float64)
+    loss = ctx.refit_step(ds, w.camera, tg, m, v, step=2, lr=0.002)
+    torch.cuda.synchronize()
+    s1 = dataclasses.replace(w.scene, sh=C1.astype(np.float32))
+    _, loss_or, _, gsh = oracle_refit(s1, w.camera, target.astype(np.float64))
+    assert loss == pytest.approx(loss_or, rel=1e-5)
+    C2_or, m2_or, v2_or = oracle.adam_step(C1, gsh, m1, v1, 2, 0.002)
+    C2 = parity.to_np(ds.sh).astype(np.float64)
+    # where the gradient is clear of the float atomics' rounding
+    clear = np.abs(gsh) > 1e-3 * np.abs(gsh).max()
+    assert clear.sum() > 1000
+    np.testing.assert_allclose(C2[clear], C2_or[clear], atol=2e-5)
+    close_enough(parity.to_np(m), m2_or)
+    close_enough(parity.to_np(v), v2_or, rel=3e-3)
 
 
 def test_refit_fixed_point_on_the_gpu(ctx):
