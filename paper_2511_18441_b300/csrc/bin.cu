@@ -713,13 +713,7 @@ static void radix_big_launch(uint32_t bound, const uint2* ranges, const uint32_t
 // (at most `bound`), each looping over the class's tiles.
 template <typename K>
 static int persistent_grid(K kernel, int threads, size_t smem, uint32_t bound) {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
+    const int sms = device_sms();
     int per_sm = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
         per_sm < 1)
@@ -742,9 +736,8 @@ static void radix_class_launch(uint32_t bound, const uint2* ranges, const uint32
     constexpr int THREADS = 8 * CAP / ITEMS;
     const size_t smem = sizeof(uint32_t) * (2 * ITEMS * THREADS + (THREADS / 32) * 256);
     // dynamic plus static shared memory above the 48 KiB default needs the opt-in
-    if (smem + 2048 > 48 * 1024)
-        cudaFuncSetAttribute(tile_radix_kernel<THREADS, ITEMS>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static std::atomic<uint64_t> opted{0};
+    if (smem + 2048 > 48 * 1024) smem_opt_in(tile_radix_kernel<THREADS, ITEMS>, (int)smem, opted);
     const int g = persistent_grid(tile_radix_kernel<THREADS, ITEMS>, THREADS, smem, bound);
     tile_radix_kernel<THREADS, ITEMS><<<g, THREADS, smem, st>>>(ranges, order, keys, ids, ctr,
                                                                  work, cls);
@@ -754,12 +747,8 @@ static void radix_big_launch(uint32_t bound, const uint2* ranges, const uint32_t
                              const unsigned long long* keys, uint32_t* ids, const DevCounters* ctr,
                              uint32_t* work, int cls, cudaStream_t st) {
     const size_t smem = sizeof(uint32_t) * (2 * 16 * 1024 + 32 * 256);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(tile_radix_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        attr = true;
-    }
+    static std::atomic<uint64_t> opted{0};
+    smem_opt_in(tile_radix_big_kernel, (int)smem, opted);
     const int g = persistent_grid(tile_radix_big_kernel, 1024, smem, bound);
     tile_radix_big_kernel<<<g, 1024, smem, st>>>(ranges, order, keys, ids, ctr, work, cls);
 }
@@ -769,9 +758,8 @@ static void sort_class_launch(uint32_t bound, const uint2* ranges, const uint32_
                               const unsigned long long* keys, uint32_t* ids,
                               const DevCounters* ctr, uint32_t* work, int cls, cudaStream_t st) {
     const size_t smem = THREADS > 32 ? sizeof(unsigned long long) * 8 * THREADS : 0;
-    if (smem + 2048 > 48 * 1024)
-        cudaFuncSetAttribute(tile_sort_kernel<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+    static std::atomic<uint64_t> opted{0};
+    if (smem + 2048 > 48 * 1024) smem_opt_in(tile_sort_kernel<THREADS>, (int)smem, opted);
     const int g = persistent_grid(tile_sort_kernel<THREADS>, THREADS, smem, bound);
     tile_sort_kernel<THREADS><<<g, THREADS, smem, st>>>(ranges, order, keys, ids, ctr, work, cls);
 }

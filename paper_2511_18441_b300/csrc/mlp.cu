@@ -653,22 +653,14 @@ int launch_mlp_forward(const uint32_t* X, int64_t n, const MlpFrags* frags, floa
                        cudaStream_t st) {
     if (n == 0) return 0;
     const int smem = (int)sizeof(MlpFrags);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
-    }
-    static int grid_max = 0;
-    if (grid_max == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_forward_kernel, 256, smem) !=
-                cudaSuccess ||
-            per_sm < 1)
-            per_sm = 1;
-        grid_max = (sms > 0 ? sms : 1) * per_sm;
-    }
+    static std::atomic<uint64_t> opted{0};
+    smem_opt_in(mlp_forward_kernel, smem, opted);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_forward_kernel, 256, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const int grid_max = device_sms() * per_sm;
     const int64_t tiles = (n + 127) / 128;
     const int g = (int)(tiles < grid_max ? tiles : grid_max);
     mlp_forward_kernel<<<g, 256, smem, st>>>(X, n, frags, out);
@@ -680,11 +672,8 @@ int launch_mlp_train(const uint32_t* X, const float* labels, int64_t n_samples,
                      float* loss_sum, cudaStream_t st) {
     if (batch == 0) return 0;
     const int smem = (int)sizeof(TrainSmem);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
-    }
+    static std::atomic<uint64_t> opted{0};
+    smem_opt_in(mlp_train_kernel, smem, opted);
     const int64_t g = (batch + kTrainRows - 1) / kTrainRows;
     mlp_train_kernel<<<(unsigned)g, 256, smem, st>>>(X, labels, n_samples, rows, batch, frags, grad,
                                                      loss_sum);

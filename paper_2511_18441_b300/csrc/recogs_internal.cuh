@@ -8,6 +8,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/recogs.h"
 
 namespace recogs {
@@ -124,6 +126,40 @@ __device__ __forceinline__ void grid_dependency_wait() {
 // Let the next kernel on the stream (launched with launch_pdl) be scheduled now.
 __device__ __forceinline__ void grid_dependents_launch() {
     asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
+// --------------------------------------------------------------------------
+// Per-device launch set-up. cudaFuncSetAttribute and the SM count are per
+// device, and one process may drive several devices (a context each), so the
+// one-time work is remembered per device ordinal (bit d of a mask; devices
+// from 64 on redo it every launch). Concurrent first calls may both do it;
+// the attribute call is idempotent.
+
+// Opt a kernel in to `bytes` of dynamic shared memory on the current device.
+template <typename K>
+inline void smem_opt_in(K kernel, int bytes, std::atomic<uint64_t>& done) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (bit) done.fetch_or(bit, std::memory_order_release);
+}
+
+// Streaming multiprocessors of the current device (at least 1).
+inline int device_sms() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 1;
+    if (dev >= 0 && dev < 64) cache[dev].store(sms, std::memory_order_relaxed);
+    return sms;
 }
 
 template <typename... KArgs, typename... Args>

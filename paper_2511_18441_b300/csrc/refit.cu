@@ -213,16 +213,8 @@ void refit_launch(int n, const float* xyz, float3 cp, const float4* rec, const u
                        aligned16(grad_sh);
     if (tiled) {
         constexpr int smem = 6 * kRefitTile * 4;
-        static int resident = 0;   // blocks per SM (the attribute set once)
-        if (!resident) {
-            cudaFuncSetAttribute(sh_refit_tile_kernel<ADAM, GRAD>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            int nb = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &nb, sh_refit_tile_kernel<ADAM, GRAD>, kRefitTileThreads, smem) != cudaSuccess)
-                nb = 0;
-            resident = nb > 0 ? nb : 1;
-        }
+        static std::atomic<uint64_t> opted{0};
+        smem_opt_in(sh_refit_tile_kernel<ADAM, GRAD>, smem, opted);
         const int n4 = n / 4;
         const int per_block = kRefitTile / 4;   // one tile per block
         const int blocks = (n4 + per_block - 1) / per_block;
