@@ -506,7 +506,10 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
         zmax = max(zmax, s_zmax[w]);
     }
     const uint32_t span = n > 0 ? zmax - zmin : 0u;
-    const int passes = span == 0u ? 0 : (32 - __clz((int)span) + 7) / 8;
+    // the radix passes order the top 16 bits of the span; keys that agree
+    // there (runs, a few keys long: their depths differ by less than 2^-16 of
+    // the tile's depth range) are ordered by the full key and the index below
+    const int bits = span == 0u ? 0 : 32 - __clz((int)span);
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i)
         if (warp * PW + i * 32 + lane < n) key[i] -= zmin;
@@ -597,8 +600,10 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
             }
         }
     };
-    for (int pass = 0; pass < passes; ++pass) radix_pass(8 * pass, false, 0u);
-    if (passes == 0) {
+    for (int shift = bits > 16 ? bits - 16 : 0; shift < bits; shift += 8)
+        radix_pass(shift, false, 0u);
+    const int low = bits > 16 ? bits - 16 : 0;   // bits below the sorted top 16
+    if (bits == 0) {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const int p = warp * PW + i * 32 + lane;
@@ -609,11 +614,13 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
         }
     }
     __syncthreads();
-    // a run of more than 32 equal depth keys (e.g. many Gaussians at exactly
-    // one depth): the insertion sort below would take quadratic time, so sort
-    // by index first and by depth again (both stable: (depth, index) order)
+    // a run of more than 32 keys equal in their top bits (e.g. many Gaussians
+    // at exactly one depth): the insertion sort below would take quadratic
+    // time, so sort by index first and by the whole depth key again (both
+    // stable: (depth, index) order)
     bool long_run = false;
-    for (int p = threadIdx.x; p + 32 < n; p += THREADS) long_run |= s_key[p] == s_key[p + 32];
+    for (int p = threadIdx.x; p + 32 < n; p += THREADS)
+        long_run |= (s_key[p] >> low) == (s_key[p + 32] >> low);
     const bool full_order = __syncthreads_or(long_run);
     if (full_order) {
         uint32_t vlo = 0xffffffffu, vhi = 0u;
@@ -639,24 +646,28 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
         const uint32_t vspan = vmax - vmin;
         const int vpasses = vspan == 0u ? 0 : (32 - __clz((int)vspan) + 7) / 8;
         for (int pass = 0; pass < vpasses; ++pass) radix_pass(8 * pass, true, vmin);
-        for (int pass = 0; pass < passes; ++pass) radix_pass(8 * pass, false, 0u);
+        for (int pass = 0; pass < (bits + 7) / 8; ++pass) radix_pass(8 * pass, false, 0u);
         // (s_key / s_val hold the final order; no run is left unordered)
     }
-    // equal depth keys: order each run (at most 32 long here) by index
-    // (insertion sort by the run's first position)
+    // keys equal in their top bits: order each run (at most 32 long here) by
+    // key and index (insertion sort by the run's first position)
     for (int p = threadIdx.x; p < n && !full_order; p += THREADS) {
-        const bool starts = (p == 0 || s_key[p - 1] != s_key[p]) && p + 1 < n && s_key[p + 1] == s_key[p];
+        const uint32_t hk = s_key[p] >> low;
+        const bool starts = (p == 0 || (s_key[p - 1] >> low) != hk) && p + 1 < n &&
+                            (s_key[p + 1] >> low) == hk;
         if (starts) {
             int e = p + 1;
-            while (e + 1 < n && s_key[e + 1] == s_key[p]) ++e;
+            while (e + 1 < n && (s_key[e + 1] >> low) == hk) ++e;
             for (int a = p + 1; a <= e; ++a) {
-                const uint32_t x = s_val[a];
+                const uint32_t xk = s_key[a], xv = s_val[a];
                 int b = a - 1;
-                while (b >= p && s_val[b] > x) {
+                while (b >= p && (s_key[b] > xk || (s_key[b] == xk && s_val[b] > xv))) {
+                    s_key[b + 1] = s_key[b];
                     s_val[b + 1] = s_val[b];
                     --b;
                 }
-                s_val[b + 1] = x;
+                s_key[b + 1] = xk;
+                s_val[b + 1] = xv;
             }
         }
     }
@@ -683,7 +694,20 @@ __global__ void __launch_bounds__(THREADS, (RECOGS_RADIX_WARPS_PER_SM * 32 / THR
 
 // The largest class (tiles of 4096 pairs and up): tiles of up to 8192 pairs
 // take the 8-key-per-thread sort, larger ones (up to kMaxSmemTile = 16384)
-// the 16-key one (same CTA of 1024 threads, shared memory sized for 16).
+// the 16-key one (same CTA of 1024 threads, shared memory sized for 16). Each
+// is a call of its own, so that the 16-key sort's registers do not crowd the
+// 8-key one.
+__device__ __noinline__ void tile_radix_big8(const uint2* __restrict__ ranges, int tile,
+                                             const unsigned long long* __restrict__ keys,
+                                             uint32_t* __restrict__ ids) {
+    tile_radix_one<1024, 8>(ranges, tile, keys, ids);
+}
+__device__ __noinline__ void tile_radix_big16(const uint2* __restrict__ ranges, int tile,
+                                              const unsigned long long* __restrict__ keys,
+                                              uint32_t* __restrict__ ids) {
+    tile_radix_one<1024, 16>(ranges, tile, keys, ids);
+}
+
 __global__ void __launch_bounds__(1024, 1)
     tile_radix_big_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
                           const unsigned long long* __restrict__ keys, uint32_t* __restrict__ ids,
@@ -696,9 +720,9 @@ __global__ void __launch_bounds__(1024, 1)
         const int tile = (int)order[first + item];
         const uint2 r = ranges[tile];
         if (r.y - r.x <= 8u * 1024u)
-            tile_radix_one<1024, 8>(ranges, tile, keys, ids);
+            tile_radix_big8(ranges, tile, keys, ids);
         else
-            tile_radix_one<1024, 16>(ranges, tile, keys, ids);
+            tile_radix_big16(ranges, tile, keys, ids);
         __syncthreads();
     }
 }

@@ -387,6 +387,40 @@ def test_equal_depth_run_in_a_tile(ctx):
         assert np.all(np.diff(lst.astype(np.int64)) > 0)
 
 
+def test_close_depths_in_a_tile(ctx):
+    """Depth keys that differ only below the top 16 bits of their tile's key
+    span: the per-tile radix sort orders the top bits, then each run of keys
+    equal there by key and index (a short cluster of close depths), or the
+    whole tile by index and key (a cluster longer than 32); both agree bit for
+    bit with the global path's full sort."""
+    rng = np.random.default_rng(11)
+    n_wide, n_a, n_b = 3000, 20, 120
+    z = np.concatenate([rng.uniform(-1.0, 0.8, n_wide),
+                        0.3 + 1e-6 * rng.permutation(n_a),
+                        -0.4 + 2e-7 * rng.permutation(n_b)])
+    z = z[rng.permutation(len(z))]
+    n = len(z)
+    xyz = np.stack([rng.normal(0, 0.004, n), rng.normal(0, 0.004, n), z])
+    sc = sg.Scene(xyz.astype(np.float32), np.full((3, n), -5.5, np.float32),
+                  rng.normal(size=(4, n)).astype(np.float32),
+                  rng.normal(-2.0, 1.0, n).astype(np.float32),
+                  rng.normal(0, 0.3, (16, 3, n)).astype(np.float32))
+    cam = sg.axis_camera(64, 64, 60.0, 2.5)
+    ds = dscene(sc)
+    out = {}
+    for path in (1, 2):
+        ctx.set_sort_path(path)
+        img, T, st = render(ctx, ds, cam, None, stats=True)
+        ranges, gids = ctx.tile_lists(st["n_tiles"], st["n_pairs"])
+        torch.cuda.synchronize()
+        out[path] = (img, T, parity.to_np(ranges), parity.to_np(gids))
+    ctx.set_sort_path(0)
+    r = out[1][2]
+    assert (r[:, 1] - r[:, 0]).max() > 2000
+    for a, b in zip(out[1], out[2]):
+        assert np.array_equal(a, b)
+
+
 def test_large_gaussians_counted_and_scattered_by_the_block(ctx):
     """Gaussians covering hundreds of tiles (their pairs are counted and
     scattered by the whole block): identical to the global path and to the
