@@ -92,7 +92,7 @@ struct Scratch {
 struct Schedule {
     int sort_path = 0;          // 0 auto, 1 per-tile shared-memory sort, 2 global radix sort
     int64_t pair_capacity = 0;  // > 0: no mid-frame read back, pair buffers of this size
-    int radix_classes = 4;      // per-tile sort classes (largest first) sorted by radix
+    int radix_classes = 5;      // per-tile sort classes (largest first) sorted by radix
     int blend_batch = 256;      // Gaussians staged per blend batch (128 or 256)
     bool overlap = false;       // blend each sort class's tiles right after its sort
     const uint32_t* class_hint = nullptr;   // sort class sizes of an earlier frame (grid sizes)
@@ -966,7 +966,7 @@ recogs_status plan_batch(recogs_ctx* ctx, const recogs_scene* scenes, int n_scen
             CKS(trial(lanes, best, &better));
             if (better) best_lanes = lanes;
         }
-        const int radix_opts[2] = {3, 5};
+        const int radix_opts[2] = {4, 6};
         for (int rc : radix_opts) {
             Schedule sc = best;
             sc.radix_classes = rc;
@@ -1351,8 +1351,9 @@ recogs_status recogs_set_schedule(recogs_ctx* ctx, int32_t radix_classes, int32_
                                   int32_t overlap) {
     if (!ctx) return RECOGS_EINVAL;
     ctx->sched.overlap = overlap != 0;
-    if (radix_classes < 0 || radix_classes > 5)
-        return fail(ctx, RECOGS_EINVAL, "radix_classes must be 0..5, got %d", radix_classes);
+    if (radix_classes < 0 || radix_classes > kSortClasses)
+        return fail(ctx, RECOGS_EINVAL, "radix_classes must be 0..%d, got %d", kSortClasses,
+                    radix_classes);
     if (blend_batch != 128 && blend_batch != 256)
         return fail(ctx, RECOGS_EINVAL, "blend_batch must be 128 or 256, got %d", blend_batch);
     ctx->sched.radix_classes = radix_classes;

@@ -358,7 +358,10 @@ __device__ __forceinline__ void tile_sort_one(const uint2* __restrict__ ranges, 
         v[e] = idx < n ? keys[r.x + idx] : ~0ull;
     }
     bool in_smem = false;
-    for (int k = 2; k <= NPAD; k <<= 1) {
+    // the network need only span the next power of two >= n: every element
+    // above it is padding (~0), in blocks the smaller stages never mix with
+    const int P = n <= 2 ? 2 : 1 << (32 - __clz(n - 1));
+    for (int k = 2; k <= P; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
             if (j >= 32 * E) {
                 // partner in another warp: shared memory
@@ -438,14 +441,15 @@ __global__ void __launch_bounds__(THREADS)
 // per-tile LSD radix sort in shared memory (tiles of 512 .. 8192 pairs)
 //
 // Sorts a tile's pairs by the 32-bit depth key relative to the tile's
-// smallest key, 8 bits per pass over the bits the tile's key span needs,
+// smallest key, 8 bits per pass over the top 16 bits of the tile's key span,
 // carrying the Gaussian index. Each pass is
 // a stable split: warp w owns positions 32 ITEMS w .. 32 ITEMS (w + 1) - 1 of
 // the current sequence (ITEMS rounds of 32), ranks its items with the digit's
 // bit ballots and per-warp digit counters, and all items move to their
 // digit's run in shared memory.
-// Pairs with equal depth keys are put in index order afterwards (runs of
-// equal keys are rare and short), so the result is (depth, index) order.
+// Pairs whose keys agree in those top bits are put in (key, index) order
+// afterwards (such runs are rare and short), so the result is (depth, index)
+// order.
 
 // Resident CTAs per SM the register allocation of the per-tile radix sort is held to.
 #ifndef RECOGS_RADIX_WARPS_PER_SM
@@ -817,7 +821,8 @@ int launch_tile_sort_class(int c, uint32_t bound, const uint2* ranges, const uin
             else sort_class_launch<64>(bound, ranges, order, keys, ids, counters, work, c, st);
             break;
         default:
-            sort_class_launch<32>(bound, ranges, order, keys, ids, counters, work, c, st);
+            if (radix) radix_class_launch<32>(bound, ranges, order, keys, ids, counters, work, c, st);
+            else sort_class_launch<32>(bound, ranges, order, keys, ids, counters, work, c, st);
             break;
     }
     return 1;
