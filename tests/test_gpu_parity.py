@@ -146,6 +146,17 @@ def test_render_background_and_T(ctx, bg):
     parity.check_image(img, T, ref)
 
 
+def test_two_axis_gaussians_worked_example(ctx):
+    """The stored closed-form example (two on-axis Gaussians over a
+    background, Eq. 1-3) through the CUDA render."""
+    from tests import golden_fixtures
+    scene, cam, bg, rgb, T_ref = golden_fixtures.two_axis_gaussians()
+    ds = dscene(scene)
+    img, T = render(ctx, ds, cam, None, bg=bg)
+    assert np.abs(img - rgb).max() <= parity.IMAGE_TOL
+    assert np.abs(T - T_ref).max() <= parity.IMAGE_TOL
+
+
 def test_fused_equals_select_recolor_render(ctx):
     """The fused edit equals select + in-place recolour + plain render bit
     for bit (same selection decisions, same recoloured coefficients)."""

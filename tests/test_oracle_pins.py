@@ -176,6 +176,18 @@ def test_single_isotropic_gaussian_closed_form():
     np.testing.assert_allclose(out["T"], np.where(keep, 1 - alpha, 1.0), atol=1e-13)
 
 
+def test_two_axis_gaussians_worked_example():
+    """The stored closed-form example (tests/golden/two_axis_gaussians_16x16.txt:
+    two on-axis Gaussians composited front to back over a background, Eq. 1-3)
+    against the binned oracle render of the same scene."""
+    from tests import golden_fixtures
+    scene, cam, bg, rgb, T = golden_fixtures.two_axis_gaussians()
+    img = oracle.render_image(scene, cam, None, bg=bg)[0]
+    np.testing.assert_allclose(img["rgb"], rgb, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(img["T"], T, rtol=0, atol=1e-12)
+    assert not img["flag"].any()
+
+
 def test_off_axis_covariance_matches_analytic_jacobian():
     """Isotropic splat at view position (x0, 0, z): Sigma' = s^2 J J^T + 0.3 I
     with J = [[f/z, 0, -f x0/z^2], [0, f/z, 0]]."""
