@@ -130,12 +130,10 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
     if (ctr && ctr->skip) rg = make_uint2(0u, 0u);  // pairs exceed the buffers: background only
     const uint32_t begin = rg.x, end = rg.y;
 
-    // colour mode keeps "stopped" in the sign of T (T < 0: stopped at |T|,
-    // or outside the image); the other modes keep a flag
-    constexpr bool kSignT = MODE == kBlendColour;
-    float T = (kSignT && !inside) ? -1.0f : 1.0f, cr = 0.f, cg = 0.f, cb = 0.f;
-    bool done = !inside;
-    auto stopped = [&]() { return kSignT ? T < 0.0f : done; };
+    // "stopped" is kept in the sign of T (T < 0: stopped at |T|, or outside
+    // the image)
+    float T = inside ? 1.0f : -1.0f, cr = 0.f, cg = 0.f, cb = 0.f;
+    auto stopped = [&]() { return T < 0.0f; };
     uint32_t fetched = begin;
     const float a_min = 1.0f / 255.0f;
     // median depth: the view depth of the Gaussian that takes T below tau
@@ -232,27 +230,14 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
         // exponent <= 0 up to rounding (a positive-definite conic): no clamp
         const float p = fmaf(a.x, fxx, fmaf(a.y, fxy, fmaf(a.z, fyy, fmaf(a.w, fpx, fmaf(b.x, fpy, b.y)))));
         const float al = fminf(0.99f, exp2_approx(p));
-        if (kSignT) {
-            // alpha below 1/255 (and the sentinel) weighs 0 and leaves T as it
-            // is, so a running pixel (T >= 1e-4) cannot stop on it; a stopped
-            // pixel (T < 0) stops again, adding nothing
-            const float a2 = al >= a_min ? al : 0.0f;
-            const float wt = a2 * T;
-            const float nT = T - wt;
-            const bool stop = nT < 1e-4f;
-            const float w = stop ? 0.0f : wt;
-            cr = fmaf(b.z, w, cr);
-            cg = fmaf(b.w, w, cg);
-            cb = fmaf(c.x, w, cb);
-            T = stop ? -fabsf(T) : nT;
-            return;
-        }
-        const float wt = al * T;
+        // alpha below 1/255 (and the sentinel) weighs 0 and leaves T as it
+        // is, so a running pixel (T >= 1e-4) cannot stop on it; a stopped
+        // pixel (T < 0) stops again, adding nothing
+        const float a2 = al >= a_min ? al : 0.0f;
+        const float wt = a2 * T;
         const float nT = T - wt;
-        const bool take = !done && al >= a_min;
-        const bool stop = take && nT < 1e-4f;
-        const bool add = take && !stop;
-        const float w = add ? wt : 0.0f;
+        const bool stop = nT < 1e-4f;
+        const float w = stop ? 0.0f : wt;
         if (!kAcc) {
             cr = fmaf(b.z, w, cr);
             cg = fmaf(b.w, w, cg);
@@ -278,12 +263,11 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
                 atomicAdd(&s_g[3 * sl + 2], v2);
             }
         }
-        if (MODE == kBlendDepth && add && !crossed && nT < ex.tau) {
+        if (MODE == kBlendDepth && !stop && !crossed && nT < ex.tau) {
             dz = c.y;
             crossed = true;
         }
-        T = add ? nT : T;
-        done = done || stop;
+        T = stop ? -fabsf(T) : nT;
     };
 
     uint32_t prev_b = 0xffffffffu;
@@ -392,7 +376,7 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
         return;
     }
     if (inside) {
-        if (kSignT) T = fabsf(T);
+        T = fabsf(T);
         image[3 * pix + 0] = cr + T * bg0;
         image[3 * pix + 1] = cg + T * bg1;
         image[3 * pix + 2] = cb + T * bg2;
