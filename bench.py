@@ -414,9 +414,8 @@ def run_ours(args, rank, world, local):
                         "frac": a / (t / 1000.0) / 1e9 / peaks["hbm_gbs"], "ms_per_launch": t}
 
     # end to end through the public API: pinned host scene in, host image out
-    e2e = None
-    if not args.no_e2e:
-        hs = binding.DeviceScene.from_numpy(w.scene, "cpu", args.sh_dtype, pin=True)
+    def e2e_run(sh_dtype):
+        hs = binding.DeviceScene.from_numpy(w.scene, "cpu", sh_dtype, pin=True)
         himg = torch.empty((HEIGHT, WIDTH, 3), dtype=torch.float32).pin_memory()
         n_e2e = max(3, min(args.steps, 20))
         ctx.render_host(hs, w.camera, w.edit, image_out=himg, stream=stream)
@@ -428,9 +427,18 @@ def run_ours(args, rank, world, local):
         el = max_over_ranks(el, world, dev)
         h2d = sum(t.numel() * t.element_size() for t in (hs.xyz, hs.log_scale, hs.quat,
                                                           hs.opacity_logit, hs.sh))
-        e2e = {"value": n_e2e * world / el, "unit": "frames/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": himg.numel() * 4, "steps": n_e2e,
-               "api": "recogs_render_host (pinned host buffers)"}
+        return {"value": n_e2e * world / el, "unit": "frames/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": himg.numel() * 4, "steps": n_e2e,
+                "api": "recogs_render_host (pinned host buffers)"}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_run(args.sh_dtype)
+        if args.sh_dtype == "f32" and not args.no_variants:
+            # the same through the host with 16-bit SH storage: the
+            # upload, which bounds this number, shrinks from 236 to 140 B per
+            # Gaussian
+            e2e["variants"] = {"bf16": e2e_run("bf16")}
 
     # context: 16-bit SH storage, the frame with the read back, and the frame
     # replayed as a one-view CUDA graph (recogs_render_batch)
