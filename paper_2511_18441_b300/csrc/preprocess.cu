@@ -497,6 +497,13 @@ __device__ __forceinline__ void prep_chunk_end(int chunk, int n_chunks, uint32_t
 // chunk's SH rows at the start shortens those reads (0.163 -> 0.160 ms). Measured at 3M Gaussians
 // against loading all 48 coefficients up front (124 registers, 2 blocks):
 // 0.172 against 0.206 ms (float32 SH), 0.180 against 0.216 ms (BF16).
+// Blocks ahead whose geometry rows a block prefetches into L2 (0: none).
+// Measured at 3M Gaussians: 148 ahead 0.156 ms, 222 0.156, 296 0.158, 592
+// 0.159, 1184 0.174, none 0.159; prefetching the SH rows of a later block
+// instead of the block's own was slower (0.167-0.190 ms).
+#ifndef RECOGS_PREP_AHEAD
+#define RECOGS_PREP_AHEAD 148
+#endif
 #ifndef RECOGS_PREP_MIN_BLOCKS_F32
 #define RECOGS_PREP_MIN_BLOCKS_F32 4
 #endif
@@ -530,6 +537,24 @@ __global__ void __launch_bounds__(kPrepThreads, PrepMinBlocks<T>::value)
             asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(b - a))
                          : "memory");
     }
+#if RECOGS_PREP_AHEAD > 0
+    // the geometry rows of the chunk RECOGS_PREP_AHEAD blocks ahead (a block
+    // that starts a short while later) go into L2 now
+    if (threadIdx.x >= 64 && threadIdx.x < 64 + 11 && chunk + RECOGS_PREP_AHEAD < n_chunks) {
+        const int r = threadIdx.x - 64;
+        const float* base = r < 3 ? xyz + (size_t)r * n
+                          : r < 6 ? lsc + (size_t)(r - 3) * n
+                          : r < 10 ? quat + (size_t)(r - 6) * n : opl;
+        const int c2 = chunk + RECOGS_PREP_AHEAD;
+        const uintptr_t row = (uintptr_t)base;
+        const uintptr_t a = (row + (uintptr_t)c2 * kPrepThreads * 4 + 15) & ~(uintptr_t)15;
+        const uintptr_t e = row + (uintptr_t)min(n, (c2 + 1) * kPrepThreads) * 4;
+        const uintptr_t b = e & ~(uintptr_t)15;
+        if (b > a)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(b - a))
+                         : "memory");
+    }
+#endif
     uint32_t cnt = 0, zbits = 0;
     int rx0 = 0, ry0 = 0, rw = 1;
     float4 r3[3];
