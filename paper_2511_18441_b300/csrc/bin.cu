@@ -520,7 +520,7 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
     // one stable 8-bit pass: items ordered by digit (BY_VAL ? val - vbase :
     // key) >> shift, kept in registers at positions warp * PW + i * 32 + lane
     // and copied to s_key / s_val
-    auto radix_pass = [&](int shift, bool by_val, uint32_t vbase) {
+    auto radix_pass = [&](int shift, bool by_val, uint32_t vbase, bool reload) {
         // each warp clears its own counters (no other warp touches them until
         // the block barrier after the ranking)
         for (int d = lane; d < 256; d += 32) s_wcnt[warp * 256 + d] = 0;
@@ -595,6 +595,7 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
             }
         }
         __syncthreads();
+        if (!reload) return;   // the items stay in s_key / s_val only
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const int p = warp * PW + i * 32 + lane;
@@ -604,8 +605,10 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
             }
         }
     };
+    // after the last pass the registers keep the items in the previous order
+    // (the full sort below does not depend on it)
     for (int shift = bits > 16 ? bits - 16 : 0; shift < bits; shift += 8)
-        radix_pass(shift, false, 0u);
+        radix_pass(shift, false, 0u, shift + 8 < bits);
     const int low = bits > 16 ? bits - 16 : 0;   // bits below the sorted top 16
     if (bits == 0) {
 #pragma unroll
@@ -649,8 +652,8 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
         }
         const uint32_t vspan = vmax - vmin;
         const int vpasses = vspan == 0u ? 0 : (32 - __clz((int)vspan) + 7) / 8;
-        for (int pass = 0; pass < vpasses; ++pass) radix_pass(8 * pass, true, vmin);
-        for (int pass = 0; pass < (bits + 7) / 8; ++pass) radix_pass(8 * pass, false, 0u);
+        for (int pass = 0; pass < vpasses; ++pass) radix_pass(8 * pass, true, vmin, true);
+        for (int pass = 0; pass < (bits + 7) / 8; ++pass) radix_pass(8 * pass, false, 0u, true);
         // (s_key / s_val hold the final order; no run is left unordered)
     }
     // keys equal in their top bits: order each run (at most 32 long here) by
