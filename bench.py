@@ -699,10 +699,11 @@ def run_refit(args, rank, world, local):
     bd_depth = stage_breakdown(lambda: ctx.render_depth(ds, cam, w.edit, tau=0.5, image_out=img,
                                                         depth_out=depth, stream=stream), 20)
     covered = float((depth > 0).float().mean())
-    ctx.set_pair_capacity(0)
 
     # (2) the refit: the target is the edited render; the fitted scene starts
-    # from the unedited SH coefficients
+    # from the unedited SH coefficients; the pair capacity stays preset (the
+    # geometry, hence the pairs, are those of the depth frames), so a step has
+    # no mid-frame read back
     target = ctx.render(ds, cam, w.edit, stream=stream).clone()
     fit = binding.DeviceScene.from_numpy(w.scene, dev, "f32")
     m = torch.zeros((16, 3, n), dtype=torch.float32, device=dev)
@@ -743,6 +744,7 @@ def run_refit(args, rank, world, local):
     stages = ctx.stage_times(reset=True)
     ctx.set_timing(False, stages=None)
     clocks = sampler.stop()
+    ctx.check(stream)   # raises if any timed step overflowed its pair buffers
     max_ms = max_over_ranks(ms, world, dev)
     loss_last = refit_step(want_loss=True)
     fitted = ctx.render(fit, cam, stream=stream)
@@ -804,8 +806,9 @@ def run_refit(args, rank, world, local):
                        "n_gaussians": n, "width": WIDTH, "height": HEIGHT, "seed": SEED,
                        "l2": (f"inputs larger than L2 (SH, m and v {3 * 192 * n / 1e9:.2f} GB); "
                               "no flush"),
-                       "step": ("recogs_refit_step: render with the mid-frame read back, "
-                                "gradient blend, SH gradient + Adam; no loss read back")},
+                       "step": ("recogs_refit_step: render (pair capacity preset, no mid-frame "
+                                "read back), gradient blend, SH gradient + Adam; no loss read "
+                                "back")},
             "frame_stats": stats_r,
             "stage_ms_per_step": {s_: round(v_[0] / k_breakdown, 4) for s_, v_ in breakdown.items()},
             "stage_ms_note": f"every stage timed by events over {k_breakdown} extra steps",

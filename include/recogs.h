@@ -461,14 +461,16 @@ RECOGS_API recogs_status recogs_set_schedule(recogs_ctx* ctx, int32_t radix_clas
  * Frames without a read back, batches of views, CUDA graphs
  */
 
-/* pairs > 0: recogs_render no longer reads the visible and pair counts back
- * in the middle of a frame (no stream synchronisation; the call can be
- * captured into a CUDA graph once its scratch has grown, e.g. after one
- * call of the same size). The pair buffers then hold `pairs` (tile, Gaussian)
+/* pairs > 0: recogs_render (and the forward render of recogs_render_depth,
+ * recogs_refit_grad and recogs_refit_step) no longer reads the visible and
+ * pair counts back in the middle of a frame (no stream synchronisation; the
+ * call can be captured into a CUDA graph once its scratch has grown, e.g.
+ * after one call of the same size). The pair buffers then hold `pairs` (tile, Gaussian)
  * pairs and the per-tile sort is always used. A frame with more pairs, or
  * with a tile above 16384 pairs, is not rendered: its image is the background
- * only (T = 1) and an error is recorded on the device, reported by the next
- * recogs_check (or by recogs_render when stats are requested).
+ * only (T = 1; a refit then sees no contribution and takes its Adam step
+ * with zero gradients) and an error is recorded on the device, reported by
+ * the next recogs_check (or by recogs_render when stats are requested).
  * pairs = 0 restores the read back (the default). At most 2^28 - 1. */
 RECOGS_API recogs_status recogs_set_pair_capacity(recogs_ctx* ctx, int64_t pairs);
 

@@ -1021,9 +1021,9 @@ recogs_status refit(recogs_ctx* ctx, const recogs_scene& s, const recogs_camera&
         grad_rgb = P<float>(ctx->rf_grad);
     }
     CKS(ensure(ctx, ctx->rf_loss, sizeof(double)));
-    // 1. forward render of the unedited scene (with the read back)
-    Schedule sched = ctx->sched;
-    sched.pair_capacity = 0;
+    // 1. forward render of the unedited scene (with the read back unless a
+    // pair capacity is set)
+    const Schedule sched = ctx->sched;
     CKS(render_device(ctx, ctx->main, sched, s, cam, nullptr, bgv, image, nullptr, nullptr, st));
     if (n > 0) CK(cudaMemsetAsync(grad_rgb, 0, 12 * (size_t)n, st));
     CK(cudaMemsetAsync(ctx->rf_loss.p, 0, sizeof(double), st));

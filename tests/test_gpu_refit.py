@@ -192,6 +192,37 @@ def test_refit_second_step_is_the_oracle_adam_step(ctx, n):
     close_enough(parity.to_np(v), v2_or, rel=3e-3)
 
 
+def test_refit_without_the_read_back(ctx):
+    """With a pair capacity set the refit's forward render skips the mid-frame
+    read back; the gradients and the step are those of the default path (up
+    to the order of the float atomics)."""
+    w = sg.tiny_workload(n=6000, width=128, height=96)
+    ds = dscene(w.scene)
+    y_or = oracle.render_image(w.scene, w.camera)[0]
+    tg = torch.from_numpy(target_away_from(y_or["rgb"], 6).astype(np.float32)).cuda()
+    ref = ctx.refit_grad(ds, w.camera, tg)
+    torch.cuda.synchronize()
+    _, st = ctx.render(ds, w.camera, stats=True)
+    ctx.set_pair_capacity(st["n_pairs"] + 1024)
+    try:
+        out = ctx.refit_grad(ds, w.camera, tg)
+        torch.cuda.synchronize()
+        ctx.check()
+        assert out["loss"] == pytest.approx(ref["loss"], rel=1e-6)
+        assert torch.equal(out["image"], ref["image"])
+        close_enough(parity.to_np(out["grad_rgb"]), parity.to_np(ref["grad_rgb"]).astype(np.float64),
+                     rel=1e-5, floor=1e-6, outliers=0.0)
+        m = torch.zeros((16, 3, ds.n), device="cuda")
+        v = torch.zeros_like(m)
+        C0 = ds.sh.clone()
+        ctx.refit_step(ds, w.camera, tg, m, v, step=1, lr=0.01, want_loss=False)
+        torch.cuda.synchronize()
+        ctx.check()
+        assert not torch.equal(ds.sh, C0)
+    finally:
+        ctx.set_pair_capacity(0)
+
+
 def test_refit_fixed_point_on_the_gpu(ctx):
     """Target = the render itself: zero loss, zero gradients, the SH do not move."""
     w = sg.tiny_workload(n=5000)
