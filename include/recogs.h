@@ -207,7 +207,9 @@ RECOGS_API recogs_status recogs_render_depth(recogs_ctx* ctx, const recogs_scene
  */
 
 /* Adam (Kingma and Ba, 2015): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
- * C -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
+ * C -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), the square root
+ * and the division to a few ulp. recogs_refit_step needs eps > 0 (a
+ * coefficient that never had a gradient would otherwise divide 0 by 0). */
 typedef struct {
     float lr;
     float beta1;                /* e.g. 0.9 */

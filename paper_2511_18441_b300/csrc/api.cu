@@ -1501,7 +1501,7 @@ recogs_status recogs_refit_step(recogs_ctx* ctx, recogs_scene* scene, const reco
     if (scene->n > 0 && (!adam_m || !adam_v || !aligned(adam_m, 4) || !aligned(adam_v, 4)))
         return fail(ctx, RECOGS_EINVAL, "adam_m / adam_v NULL or misaligned");
     if (adam->step < 1 || !(adam->lr >= 0.f) || !(adam->beta1 >= 0.f && adam->beta1 < 1.f) ||
-        !(adam->beta2 >= 0.f && adam->beta2 < 1.f) || !(adam->eps >= 0.f))
+        !(adam->beta2 >= 0.f && adam->beta2 < 1.f) || !(adam->eps > 0.f))
         return fail(ctx, RECOGS_EINVAL, "Adam parameters out of range");
     DeviceGuard g(ctx->device);
     return refit(ctx, *scene, *camera, bgv, target_hwc, nullptr, nullptr, nullptr, adam_m, adam_v,

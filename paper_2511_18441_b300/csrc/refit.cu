@@ -40,7 +40,12 @@ __device__ __forceinline__ void refit_adam(const RefitAdam& a, float g, float& C
                                            float& v) {
     m = a.beta1 * m + (1.0f - a.beta1) * g;
     v = a.beta2 * v + (1.0f - a.beta2) * g * g;
-    C = C - a.lr * (m * a.inv_bc1) / (sqrtf(v * a.inv_bc2) + a.eps);
+    // approximate square root and reciprocal (a few ulp; the IEEE-rounded
+    // forms cost the streaming kernel 13% of its time): sqrt.approx(0) = 0,
+    // and eps > 0 keeps the reciprocal finite
+    float s;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(v * a.inv_bc2));
+    C = C - a.lr * (m * a.inv_bc1) * rcp_approx(s + a.eps);
 }
 
 // Per Gaussian: dL/dC_{k,ch} = Y_k(d) [c_ch > 0] dL/dc_ch (the shown colour
