@@ -43,3 +43,44 @@ def test_two_rank_max_and_aggregate():
 def test_aggregate_single():
     import bench
     assert bench.aggregate_value(10, 1, 1000.0) == pytest.approx(10.0)
+
+
+def test_algorithmic_bytes_per_unit():
+    """The per-unit byte counts of the roofline figures (design table):
+    preprocess 44 + 48 s + 44 per Gaussian, blend 40 per consumed pair + 12
+    per pixel + 8 per tile, SH refit 4 + 1152 per Gaussian + 40 per visible
+    one, gradient blend 40 per pair + 24 per pixel + 8 per tile + 12 per
+    visible Gaussian."""
+    import bench
+    W, H = bench.WIDTH, bench.HEIGHT
+    st = {"n_pairs_read": 1000, "n_tiles": 10}
+    assert bench.algorithmic_bytes("preprocess", st, 100, 4) == 100 * (44 + 192 + 44)
+    assert bench.algorithmic_bytes("preprocess", st, 100, 2) == 100 * (44 + 96 + 44)
+    assert bench.algorithmic_bytes("blend", st, 100, 4) == 1000 * 40 + 12 * W * H + 80
+    assert bench.algorithmic_bytes("scatter", st, 100, 4) is None
+    assert bench.refit_algorithmic_bytes("refit", st, 100, 60) == 100 * 1156 + 60 * 40
+    assert (bench.refit_algorithmic_bytes("blend_grad", st, 100, 60)
+            == 1000 * 40 + 24 * W * H + 80 + 60 * 12)
+
+
+def test_profiled_traffic_only_for_the_profiled_source(tmp_path, monkeypatch):
+    """A committed traffic figure is used only while its kernel source is the
+    one it was taken on."""
+    import bench
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    sha = bench.kernel_source_sha("blend.cu")
+    (prof / "traffic_blend_3m_1080p.txt").write_text(
+        f"# note\nsource_sha256_16: {sha}\ndram_bytes_per_launch: 123\n")
+    (prof / "traffic_refit_3m_1080p.txt").write_text(
+        "source_sha256_16: 0000000000000000\ndram_bytes_per_launch: 456\n")
+    real_join = os.path.join
+
+    def join(*parts):
+        if len(parts) >= 2 and parts[0] == bench.ROOT and parts[1] == "profiles":
+            return real_join(str(tmp_path), *parts[1:])
+        return real_join(*parts)
+    monkeypatch.setattr(bench.os.path, "join", join)
+    assert bench.profiled_traffic("blend") == 123.0
+    assert bench.profiled_traffic("refit") is None        # another source
+    assert bench.profiled_traffic("scatter") is None      # never profiled
