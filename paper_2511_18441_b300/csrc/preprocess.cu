@@ -47,25 +47,43 @@ __device__ __forceinline__ void recolor_coeffs(const float* M, const float* dc_f
 // ---------------------------------------------------------------------------
 // select
 
+// Four chunks of 256 Gaussians per block, their positions loaded before the
+// first test so that twelve loads per thread are in flight.
+constexpr int kSelectChunks = 4;
+
 __global__ void __launch_bounds__(256) select_kernel(int n, const float* __restrict__ xyz,
                                                       DevCamera cam, DevRegion reg,
                                                       uint32_t* __restrict__ mask,
                                                       uint8_t* __restrict__ near_out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool sel = false, nb = false;
-    if (i < n)
-        sel = select_centre(cam, reg, __ldg(xyz + i), __ldg(xyz + n + i), __ldg(xyz + 2 * n + i),
-                            near_out ? &nb : nullptr);
-    const uint32_t bits = __ballot_sync(0xffffffffu, sel);
-    if ((threadIdx.x & 31) == 0 && i < n) mask[i >> 5] = bits;
-    if (near_out && i < n) near_out[i] = nb ? 1 : 0;
+    float px[kSelectChunks], py[kSelectChunks], pz[kSelectChunks];
+#pragma unroll
+    for (int c = 0; c < kSelectChunks; ++c) {
+        const int i = (blockIdx.x * kSelectChunks + c) * 256 + threadIdx.x;
+        px[c] = py[c] = pz[c] = 0.f;
+        if (i < n) {
+            px[c] = __ldg(xyz + i);
+            py[c] = __ldg(xyz + n + i);
+            pz[c] = __ldg(xyz + 2 * (size_t)n + i);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < kSelectChunks; ++c) {
+        const int i = (blockIdx.x * kSelectChunks + c) * 256 + threadIdx.x;
+        bool sel = false, nb = false;
+        if (i < n) sel = select_centre(cam, reg, px[c], py[c], pz[c], near_out ? &nb : nullptr);
+        const uint32_t bits = __ballot_sync(0xffffffffu, sel);
+        if ((threadIdx.x & 31) == 0 && i < n) mask[i >> 5] = bits;
+        if (near_out && i < n) near_out[i] = nb ? 1 : 0;
+    }
 }
 
 int launch_select(const recogs_scene& s, const DevCamera& cam, const DevRegion& reg,
                   uint32_t* mask, uint8_t* near_out, cudaStream_t st) {
     const int n = (int)s.n;
     if (n == 0) return 0;
-    select_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, s.xyz, cam, reg, mask, near_out);
+    const int per_block = kSelectChunks * 256;
+    select_kernel<<<(n + per_block - 1) / per_block, 256, 0, st>>>(n, s.xyz, cam, reg, mask,
+                                                                  near_out);
     return 1;
 }
 
