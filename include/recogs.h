@@ -415,6 +415,14 @@ RECOGS_API recogs_status recogs_render_noalloc(const recogs_scene* scene,
 RECOGS_API recogs_status recogs_tile_lists(recogs_ctx* ctx, uint32_t* ranges_out, uint32_t* ids_out,
                                 int64_t capacity, void* stream);
 
+/* Copy the depth keys of the last recogs_render on ctx: keys_out (device,
+ * capacity uint32), per Gaussian the bits of its float32 sort key, the
+ * float32 nearest its view depth t_z (the front-to-back order of Eq. 3, Sec.
+ * 3.1), or 0 for a culled Gaussian. Each tile's list is in (key, index)
+ * order. Fails with RECOGS_ECAPACITY if capacity < the scene's n. */
+RECOGS_API recogs_status recogs_depth_keys(recogs_ctx* ctx, uint32_t* keys_out, int64_t capacity,
+                                           void* stream);
+
 /* Enable (1) or disable (0) CUDA-event timing of each pipeline stage on the
  * stream each stage runs on. */
 RECOGS_API recogs_status recogs_set_timing(recogs_ctx* ctx, int enable);

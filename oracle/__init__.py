@@ -61,7 +61,7 @@ class Splats(C.Structure):
     _fields_ = [("u", f64p), ("v", f64p), ("depth", f64p), ("cov2d", f64p), ("conic", f64p),
                 ("opacity", f64p), ("rgb", f64p), ("extent", f64p), ("rect", i32p),
                 ("valid", u8p), ("visible", u8p), ("selected", u8p), ("sel_flag", u8p),
-                ("fp_flag", u8p)]
+                ("fp_flag", u8p), ("alt_rgb", f64p)]
 
 
 def lib():
@@ -94,6 +94,9 @@ def lib():
         L.oracle_color_grad_tiles.argtypes = [C.POINTER(Splats), i64p, i32p, C.c_int, C.c_int,
                                               f64p, f64p]
         L.oracle_sh_grad.argtypes = [C.c_int64, f32p, C.POINTER(Camera), f64p, f64p, f64p]
+        L.oracle_pixel_outcomes.argtypes = [C.POINTER(Splats), i64p, i32p, C.c_int, C.c_int, i64p,
+                                            C.c_int64, C.c_int64, i32p, i32p, f64p,
+                                            C.POINTER(Margins), C.c_int64, f64p, i64p, C.c_int]
         L.oracle_weight_sums_tiles.argtypes = [C.POINTER(Splats), i64p, i32p, C.c_int, C.c_int,
                                                f64p, C.c_int, f64p]
         _lib = L
@@ -142,7 +145,7 @@ def edit_struct(edit, cam):
 
 
 def margins(cam, eps_pos=None, eps_rel=1e-5, eps_k=1e-6, eps_pix=2e-5, eps_cov=1e-5,
-            eps_exp=4e-6, eps_depth=1e-6, impact=5e-5) -> Margins:
+            eps_exp=4e-6, eps_depth=1e-12, impact=5e-5) -> Margins:
     """Decision margins: how far float32 arithmetic may move each quantity.
 
     eps_pos (selection and tile-range decisions) defaults to 1e-6 * max(W, H)
@@ -150,9 +153,11 @@ def margins(cam, eps_pos=None, eps_rel=1e-5, eps_k=1e-6, eps_pix=2e-5, eps_cov=1
     pixel-level margins bound a float32 implementation that keeps the
     pixel-to-centre offset to ~1e-6 px, covariance entries to ~1e-6 of their
     scale and the exponent to a few ulp; each default is 2.5-10x that bound.
-    eps_depth: two contributors whose depths differ by less (relative) may
-    share a float32 depth key, so their order, and the pixel's colour, is
-    not unique; such pixels are flagged.
+    eps_depth: a depth within this distance (relative) of the midpoint
+    between two float32 values may get either as its float32 key (a float32
+    implementation carries the depth to ~1e-13 before rounding it). Two
+    contributors whose keys may be equal may be blended in either order, so
+    the pixel's colour is not unique there; such pixels are flagged.
     """
     m = Margins()
     m.eps_pos = float(1e-6 * max(cam.width, cam.height) if eps_pos is None else eps_pos)
@@ -225,7 +230,7 @@ class SplatResult(dict):
         for name, t in (("u", f64p), ("v", f64p), ("depth", f64p), ("cov2d", f64p),
                         ("conic", f64p), ("opacity", f64p), ("rgb", f64p), ("extent", f64p),
                         ("rect", i32p), ("valid", u8p), ("visible", u8p), ("selected", u8p),
-                        ("sel_flag", u8p), ("fp_flag", u8p)):
+                        ("sel_flag", u8p), ("fp_flag", u8p), ("alt_rgb", f64p)):
             setattr(s, name, _ptr(self[name], t))
         return s
 
@@ -242,7 +247,7 @@ def preprocess(scene, cam, edit=None, mg=None, sh=None, threads=None) -> SplatRe
         conic=np.zeros(3 * n), opacity=np.zeros(n), rgb=np.zeros(3 * n), extent=np.zeros(2 * n),
         rect=np.zeros(4 * n, np.int32), valid=np.zeros(n, np.uint8), visible=np.zeros(n, np.uint8),
         selected=np.zeros(n, np.uint8), sel_flag=np.zeros(n, np.uint8),
-        fp_flag=np.zeros(n, np.uint8))
+        fp_flag=np.zeros(n, np.uint8), alt_rgb=np.zeros(3 * n))
     camc = camera_struct(cam)
     e, keep = edit_struct(edit, cam)
     m = mg if mg is not None else margins(cam)
@@ -296,6 +301,52 @@ def tile_lists(splats: SplatResult, order, tiles_x, tiles_y):
     lib().oracle_tile_lists(C.byref(s), _ptr(order, i64p), len(order), tiles_x, tiles_y,
                             _ptr(offsets, i64p), _ptr(ids, i32p))
     return offsets, ids[:P]
+
+
+def depth_keys(splats: SplatResult):
+    """Float32 depth keys: the float32 nearest each FP64 view depth, and a
+    mask of the depths within eps_depth (relative) of a float32 rounding
+    midpoint, whose key float32 arithmetic may round either way. A float32
+    sort by (key, index) is the (depth, index) order of Eq. 3 except inside
+    runs of equal keys."""
+    d = np.asarray(splats["depth"], np.float64)
+    eps = splats["margins"].eps_depth
+    k = d.astype(np.float32)
+    other = np.where(k.astype(np.float64) <= d, np.nextafter(k, np.float32(np.inf)),
+                     np.nextafter(k, np.float32(-np.inf)))
+    mid = 0.5 * (k.astype(np.float64) + other.astype(np.float64))
+    amb = np.abs(d - mid) <= eps * np.abs(d)
+    return k, amb
+
+
+def pixel_outcomes(splats: SplatResult, offsets, ids, px, py, bg=(0.0, 0.0, 0.0), mg=None,
+                   max_out=256, threads=None):
+    """Every outcome (r, g, b, T) of the binned render at pixels (px[j],
+    py[j]) that the doubtful decisions allow (the oracle's flags): returns
+    (outcomes [npix, max_out, 4], counts [npix]; -1 where there are more
+    than max_out)."""
+    cam = splats["camera"]
+    px = np.ascontiguousarray(px, np.int32)
+    py = np.ascontiguousarray(py, np.int32)
+    npix = len(px)
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    ids = np.ascontiguousarray(ids, np.int32)
+    if len(ids) == 0:
+        ids = np.zeros(1, np.int32)
+    extra = np.ascontiguousarray(np.flatnonzero(splats["fp_flag"] > 0), np.int64)
+    n_extra = len(extra)
+    if n_extra == 0:
+        extra = np.zeros(1, np.int64)
+    bgv = np.ascontiguousarray(bg, np.float64)
+    out = np.zeros((max(npix, 1), max_out, 4))
+    cnt = np.zeros(max(npix, 1), np.int64)
+    m = mg if mg is not None else splats["margins"]
+    s = splats.struct()
+    lib().oracle_pixel_outcomes(C.byref(s), _ptr(offsets, i64p), _ptr(ids, i32p), cam.width,
+                                cam.height, _ptr(extra, i64p), n_extra, npix, _ptr(px, i32p),
+                                _ptr(py, i32p), _ptr(bgv, f64p), C.byref(m), int(max_out),
+                                _ptr(out, f64p), _ptr(cnt, i64p), _threads(threads))
+    return out[:npix], cnt[:npix]
 
 
 def render_tiles(splats: SplatResult, offsets, ids, tiles=None, bg=(0.0, 0.0, 0.0), mg=None,

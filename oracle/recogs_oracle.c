@@ -315,9 +315,10 @@ static void prep_range(void* vctx, int64_t begin, int64_t end) {
         uint8_t fp = 0;
 
         /* selection and recolour of the SH coefficients (Sec. 3.3) */
-        double C[16][3];
+        double C[16][3], Calt[16][3];
         for (int k = 0; k < 16; ++k)
             for (int ch = 0; ch < 3; ++ch) C[k][ch] = P->sh[(int64_t)(k * 3 + ch) * n + i];
+        memcpy(Calt, C, sizeof(C));
         uint8_t sel = 0, sflag = 0;
         if (P->edit && P->edit->kind != ORACLE_REGION_NONE) {
             double eps_sel = 1e-6 * (P->edit->select_cam.width > P->edit->select_cam.height
@@ -325,7 +326,11 @@ static void prep_range(void* vctx, int64_t begin, int64_t end) {
                                          : P->edit->select_cam.height);
             if (mg->eps_pos > 0) eps_sel = eps_sel > mg->eps_pos ? eps_sel : mg->eps_pos;
             select_one(P->edit, mu, eps_sel, &sel, &sflag);
+            /* Calt: the coefficients under the other selection decision,
+             * which a float32 test may take for a centre this near the
+             * region's boundary */
             if (sel) recolor_one(P->edit->M, P->Y0, C);
+            else if (sflag) recolor_one(P->edit->M, P->Y0, Calt);
         }
         o->selected[i] = sel;
         o->sel_flag[i] = sflag;
@@ -451,6 +456,16 @@ static void prep_range(void* vctx, int64_t begin, int64_t end) {
             f += 0.5;
             o->rgb[3 * i + ch] = f > 0.0 ? f : 0.0;
         }
+        if (o->alt_rgb) {
+            /* the shown colour under the other selection decision (the same
+             * as rgb where the decision is not in doubt) */
+            for (int ch = 0; ch < 3; ++ch) {
+                double f = 0.0;
+                for (int k = 0; k < 16; ++k) f += (sflag ? Calt[k][ch] : C[k][ch]) * Y[k];
+                f += 0.5;
+                o->alt_rgb[3 * i + ch] = f > 0.0 ? f : 0.0;
+            }
+        }
     }
 }
 
@@ -507,6 +522,37 @@ int64_t oracle_depth_order(int64_t n, const oracle_splats* s, int64_t* order) {
     for (int64_t k = 0; k < m; ++k) order[k] = keys[k].idx;
     free(keys);
     return m;
+}
+
+/* ------------------------------------------------------------------------ */
+/* float32 depth keys                                                        */
+
+/* The front-to-back order of Eq. 3 is by view depth, ties by index. A
+ * float32 implementation sorts by the float32 nearest each depth, ties by
+ * index; where two depths round to the same float32 that is an equally valid
+ * front-to-back order, and it is the only place where the two orders differ.
+ * key_bounds: the float32 values the key of depth d may take: the nearest,
+ * or both neighbours when d lies within eps (relative) of the midpoint
+ * between them (float32 arithmetic that carries the depth to ~1e-13 may then
+ * round either way). */
+static void key_bounds(double d, double eps, float* lo, float* hi) {
+    float f = (float)d;
+    float g = (double)f <= d ? nextafterf(f, INFINITY) : nextafterf(f, -INFINITY);
+    double mid = 0.5 * ((double)f + (double)g);
+    if (fabs(d - mid) <= eps * fabs(d)) {
+        *lo = f < g ? f : g;
+        *hi = f < g ? g : f;
+    } else {
+        *lo = *hi = f;
+    }
+}
+
+/* 1 if the float32 keys of depths a and b may be equal */
+static int keys_may_tie(double a, double b, double eps) {
+    float alo, ahi, blo, bhi;
+    key_bounds(a, eps, &alo, &ahi);
+    key_bounds(b, eps, &blo, &bhi);
+    return alo <= bhi && blo <= ahi;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -584,7 +630,7 @@ static void blend_pixel(const oracle_splats* s, const int64_t* list, int64_t len
         double eT_next = eT + alpha * ea / (1.0 - alpha) + 2.4e-7;
         if (fabs(log(testT / 1e-4)) <= eT_next) flag |= 2;
         if (testT < 1e-4) break;
-        if (prev >= 0 && fabs(s->depth[i] - s->depth[prev]) <= mg->eps_depth * fabs(s->depth[i])) {
+        if (prev >= 0 && keys_may_tie(s->depth[prev], s->depth[i], mg->eps_depth)) {
             /* swapping the two changes the colour by a_p a_i T_p (c_i - c_p) */
             double dc = 0.0;
             for (int ch = 0; ch < 3; ++ch)
@@ -723,6 +769,243 @@ void oracle_render_tiles(const oracle_splats* s, const int64_t* offsets, const i
                          uint8_t* flag, int32_t* ncontrib, int threads) {
     oracle_render_tiles_depth(s, offsets, ids, width, height, n_sel, tile_sel, bg, mg, rgb, T,
                               flag, ncontrib, 0.0, NULL, NULL, threads);
+}
+
+/* ------------------------------------------------------------------------ */
+/* every outcome of a pixel whose decisions float32 may take the other way   */
+
+/* One splat that may contribute to the pixel being enumerated. */
+typedef struct {
+    int64_t idx;
+    double alpha;   /* min(0.99, sigma G), FP64 */
+    double ea;      /* uncertainty of alpha (relative; 0 where clamped at 0.99) */
+    int take;       /* alpha vs 1/255: 1 taken, 2 either way */
+    int ncol;       /* 2 when the selection decision is in doubt (colour rgb or alt_rgb) */
+} outcome_entry;
+
+typedef struct {
+    const oracle_splats* s;
+    const outcome_entry* e;
+    const int64_t* run_end;   /* per position: end of the run of possibly equal keys from it */
+    int64_t len;
+    const double* bg;
+    int64_t max_out, n_out;
+    int overflow;
+    double* out;              /* max_out x (r, g, b, T) */
+} outcome_walk;
+
+static void outcome_emit(outcome_walk* O, const double C[3], double T) {
+    if (O->n_out >= O->max_out) {
+        O->overflow = 1;
+        return;
+    }
+    double* o = O->out + 4 * O->n_out++;
+    for (int ch = 0; ch < 3; ++ch) o[ch] = C[ch] + T * O->bg[ch];
+    o[3] = T;
+}
+
+static int next_permutation(int* a, int m) {
+    int i = m - 2;
+    while (i >= 0 && a[i] >= a[i + 1]) --i;
+    if (i < 0) return 0;
+    int j = m - 1;
+    while (a[j] <= a[i]) --j;
+    int t = a[i]; a[i] = a[j]; a[j] = t;
+    for (int l = i + 1, r = m - 1; l < r; ++l, --r) {
+        t = a[l]; a[l] = a[r]; a[r] = t;
+    }
+    return 1;
+}
+
+/* The walk of Eq. 3 from position pos of seq (indices into O->e) with
+ * transmittance T, colour C and T's accumulated relative uncertainty eT,
+ * branching at each decision that is in doubt. Positions below permuted_to
+ * already hold one order of their run. */
+static void outcome_walk_from(outcome_walk* O, int64_t* seq, int64_t pos, int64_t permuted_to,
+                              double T, const double C[3], double eT) {
+    if (O->overflow) return;
+    if (pos == O->len) {
+        outcome_emit(O, C, T);
+        return;
+    }
+    const int64_t end = O->run_end[pos];
+    if (pos >= permuted_to && end - pos > 1) {
+        /* a run of splats whose float32 keys may be equal: every order of it
+         * (runs of more than 4: the FP64 order and the index order) */
+        const int m = (int)(end - pos);
+        int64_t* seq2 = (int64_t*)malloc(sizeof(int64_t) * (size_t)O->len);
+        memcpy(seq2, seq, sizeof(int64_t) * (size_t)O->len);
+        if (m <= 4) {
+            int perm[4] = {0, 1, 2, 3};
+            do {
+                for (int k = 0; k < m; ++k) seq2[pos + k] = seq[pos + perm[k]];
+                outcome_walk_from(O, seq2, pos, end, T, C, eT);
+            } while (!O->overflow && next_permutation(perm, m));
+        } else {
+            outcome_walk_from(O, seq, pos, end, T, C, eT);
+            /* index order: insertion sort of the run by splat index */
+            for (int a = 1; a < m; ++a) {
+                int64_t v = seq2[pos + a];
+                int b = a - 1;
+                while (b >= 0 && O->e[seq2[pos + b]].idx > O->e[v].idx) {
+                    seq2[pos + b + 1] = seq2[pos + b];
+                    --b;
+                }
+                seq2[pos + b + 1] = v;
+            }
+            outcome_walk_from(O, seq2, pos, end, T, C, eT);
+        }
+        free(seq2);
+        return;
+    }
+    const outcome_entry* e = &O->e[seq[pos]];
+    if (e->take == 2) outcome_walk_from(O, seq, pos + 1, permuted_to, T, C, eT);  /* skipped */
+    const double testT = T * (1.0 - e->alpha);
+    const double eT_next = eT + e->alpha * e->ea / (1.0 - e->alpha) + 2.4e-7;
+    const int near_stop = fabs(log(testT / 1e-4)) <= eT_next;
+    if (testT < 1e-4 || near_stop) outcome_emit(O, C, T);   /* stops before this splat */
+    if (testT >= 1e-4 || near_stop) {
+        for (int k = 0; k < e->ncol; ++k) {
+            const double* col = k == 0 ? &O->s->rgb[3 * e->idx] : &O->s->alt_rgb[3 * e->idx];
+            double C2[3];
+            for (int ch = 0; ch < 3; ++ch) C2[ch] = C[ch] + col[ch] * e->alpha * T;
+            outcome_walk_from(O, seq, pos + 1, permuted_to, testT, C2, eT_next);
+        }
+    }
+}
+
+static int cmp_depth_idx(const oracle_splats* s, int64_t a, int64_t b) {
+    if (s->depth[a] < s->depth[b]) return -1;
+    if (s->depth[a] > s->depth[b]) return 1;
+    return (a > b) - (a < b);
+}
+
+typedef struct {
+    const oracle_splats* s;
+    const int64_t* offsets;
+    const int32_t* ids;
+    int width, height, tiles_x;
+    const int64_t* extra;
+    int64_t n_extra;
+    const int32_t *px, *py;
+    const double* bg;
+    const oracle_margins* mg;
+    int64_t max_out;
+    double* out;
+    int64_t* n_out;
+} outcomes_ctx;
+
+static void outcomes_range(void* vctx, int64_t b, int64_t e_) {
+    outcomes_ctx* P = (outcomes_ctx*)vctx;
+    const oracle_splats* s = P->s;
+    const oracle_margins* mg = P->mg;
+    const double a_min = 1.0 / 255.0;
+    for (int64_t j = b; j < e_; ++j) {
+        const int x = P->px[j], y = P->py[j];
+        const int tx = x / TILE, ty = y / TILE;
+        const int64_t t = (int64_t)ty * P->tiles_x + tx;
+        const int64_t beg = P->offsets[t], len = P->offsets[t + 1] - beg;
+        /* candidates: the tile's list, plus splats whose tile range or
+         * visibility is in doubt and that a float32 footprint may put in this
+         * tile (one tile beyond the FP64 range, or any tile when the
+         * visibility is in doubt) */
+        int64_t cap = len + P->n_extra + 1;
+        int64_t* cand = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap);
+        uint8_t* listed = (uint8_t*)malloc((size_t)cap);
+        int64_t nc = 0;
+        for (int64_t k = 0; k < len; ++k) {
+            listed[nc] = 1;
+            cand[nc++] = P->ids[beg + k];
+        }
+        for (int64_t k = 0; k < P->n_extra; ++k) {
+            const int64_t i = P->extra[k];
+            int near = 0;
+            if (s->fp_flag[i] & 2) {
+                near = s->conic[3 * i] != 0.0 && s->depth[i] > 0.0;
+            } else if (s->visible[i]) {
+                const int32_t* r = &s->rect[4 * i];
+                near = tx >= r[0] - 1 && tx <= r[1] + 1 && ty >= r[2] - 1 && ty <= r[3] + 1;
+            }
+            if (!near) continue;
+            int dup = 0;
+            for (int64_t q = 0; q < len && !dup; ++q) dup = P->ids[beg + q] == i;
+            if (dup) continue;
+            listed[nc] = 0;
+            cand[nc++] = i;
+        }
+        /* insertion of the extra candidates into (depth, index) order */
+        for (int64_t a = len; a < nc; ++a) {
+            int64_t v = cand[a];
+            uint8_t lv = listed[a];
+            int64_t q = a - 1;
+            while (q >= 0 && cmp_depth_idx(s, cand[q], v) > 0) {
+                cand[q + 1] = cand[q];
+                listed[q + 1] = listed[q];
+                --q;
+            }
+            cand[q + 1] = v;
+            listed[q + 1] = lv;
+        }
+        /* the splats that may contribute, with the decisions in doubt */
+        outcome_entry* ent = (outcome_entry*)malloc(sizeof(outcome_entry) * (size_t)(nc + 1));
+        int64_t ne = 0;
+        for (int64_t k = 0; k < nc; ++k) {
+            const int64_t i = cand[k];
+            const double dx = (double)x - s->u[i], dy = (double)y - s->v[i];
+            const double sigma = s->opacity[i];
+            const double kk = 2.0 * log(255.0 * sigma);
+            const double A = s->conic[3 * i], B = s->conic[3 * i + 1], Cc = s->conic[3 * i + 2];
+            double p = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy;
+            if (p > 0.0) p = 0.0;
+            double alpha = sigma * exp(p);
+            if (alpha > 0.99) alpha = 0.99;
+            const double gx = A * dx + B * dy, gy = B * dx + Cc * dy;
+            const double a = s->cov2d[3 * i], c = s->cov2d[3 * i + 2];
+            const double sg = sqrt(a) * fabs(gx) + sqrt(c) * fabs(gy);
+            const double ep = mg->eps_pix * (fabs(gx) + fabs(gy)) + 0.5 * mg->eps_cov * sg * sg +
+                              mg->eps_exp * (fabs(p) + 1.0);
+            const int near = fabs(p + 0.5 * kk) <= ep;
+            int take;
+            if (near) take = 2;
+            else if (alpha >= a_min) take = 1;
+            else continue;
+            if (!listed[k] || !s->valid[i]) take = 2;
+            ent[ne].idx = i;
+            ent[ne].alpha = alpha;
+            ent[ne].ea = alpha < 0.99 ? ep : 0.0;
+            ent[ne].take = take;
+            ent[ne].ncol = s->sel_flag[i] && s->alt_rgb ? 2 : 1;
+            ++ne;
+        }
+        /* runs of possibly equal float32 keys among them */
+        int64_t* run_end = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ne + 1));
+        for (int64_t k = ne - 1; k >= 0; --k)
+            run_end[k] = (k + 1 < ne && keys_may_tie(s->depth[ent[k].idx], s->depth[ent[k + 1].idx],
+                                                     mg->eps_depth))
+                             ? run_end[k + 1]
+                             : k + 1;
+        int64_t* seq = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ne + 1));
+        for (int64_t k = 0; k < ne; ++k) seq[k] = k;
+        outcome_walk O = {s, ent, run_end, ne, P->bg, P->max_out, 0, 0, P->out + 4 * P->max_out * j};
+        const double C0[3] = {0.0, 0.0, 0.0};
+        outcome_walk_from(&O, seq, 0, 0, 1.0, C0, 0.0);
+        P->n_out[j] = O.overflow ? -1 : O.n_out;
+        free(seq);
+        free(run_end);
+        free(ent);
+        free(listed);
+        free(cand);
+    }
+}
+
+void oracle_pixel_outcomes(const oracle_splats* s, const int64_t* offsets, const int32_t* ids,
+                           int width, int height, const int64_t* extra, int64_t n_extra,
+                           int64_t npix, const int32_t* px, const int32_t* py, const double bg[3],
+                           const oracle_margins* mg, int64_t max_out, double* out, int64_t* n_out,
+                           int threads) {
+    outcomes_ctx P = {s, offsets, ids, width, height, (width + TILE - 1) / TILE, extra, n_extra,
+                      px, py, bg, mg, max_out, out, n_out};
+    parallel_for(npix, 4, threads, outcomes_range, &P);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -58,7 +58,8 @@ typedef struct {
     double eps_pix;          /* px: uncertainty of the pixel-to-centre offset inside alpha */
     double eps_cov;          /* uncertainty of 2D covariance entries relative to sqrt(a_ii a_jj) */
     double eps_exp;          /* relative uncertainty of the exponent and of alpha */
-    double eps_depth;        /* relative depth difference below which a float32 key may tie */
+    double eps_depth;        /* relative distance of a depth to a float32 rounding midpoint
+                                below which its float32 key may round either way */
     double impact;           /* a pixel decision is flagged only if it can move a channel by more */
 } oracle_margins;
 
@@ -78,6 +79,8 @@ typedef struct {
     uint8_t* selected;       /* selected by the edit (0 without an edit) */
     uint8_t* sel_flag;       /* selection decision within the margins of its boundary */
     uint8_t* fp_flag;        /* bit0: tile range near a boundary; bit1: validity/visibility near threshold */
+    double* alt_rgb;         /* 3n: colour under the other selection decision where sel_flag is
+                                set, else rgb; may be NULL */
 } oracle_splats;
 
 /* Real SH basis of degree 3 at unit direction (x, y, z), 16 values ordered
@@ -143,6 +146,22 @@ void oracle_render_tiles_depth(const oracle_splats* s, const int64_t* offsets, c
                                const double bg[3], const oracle_margins* mg, double* rgb,
                                double* T, uint8_t* flag, int32_t* ncontrib, double tau,
                                double* depth, uint8_t* dflag, int threads);
+
+/* Every outcome (r, g, b, T) that the binned render of pixel (px[j], py[j])
+ * may take when float32 arithmetic takes its doubtful decisions the other way
+ * (Eq. 3 with the readings of blend_pixel): alpha within its margin of 1/255
+ * (splat skipped or taken), T (1 - alpha) within its margin of 1e-4 (stop or
+ * go on), a selection decision near the region's boundary (either colour),
+ * splats whose float32 depth keys may be equal (every order of such a run of
+ * up to 4 splats; the FP64 and the index order of a longer one), and splats
+ * of `extra` (those with an ambiguous tile range or visibility, in any order)
+ * that a float32 footprint may list for the pixel's tile. out: npix x max_out
+ * x 4; n_out[j]: the number of outcomes, -1 if there are more than max_out. */
+void oracle_pixel_outcomes(const oracle_splats* s, const int64_t* offsets, const int32_t* ids,
+                           int width, int height, const int64_t* extra, int64_t n_extra,
+                           int64_t npix, const int32_t* px, const int32_t* py, const double bg[3],
+                           const oracle_margins* mg, int64_t max_out, double* out, int64_t* n_out,
+                           int threads);
 
 /* SH-only refit (Sec. 3.3, Eq. 6-7): the colour gradient dL/dc_i =
  * sum_p dL/dy_p alpha_i(p) T_i(p) of the binned render (accumulated into

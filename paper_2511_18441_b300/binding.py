@@ -96,6 +96,7 @@ SIGNATURES = {
                                         C.POINTER(C.c_float), C.c_void_p, C.c_void_p, C.c_char_p,
                                         C.c_size_t, C.c_void_p]),
     "recogs_tile_lists": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "recogs_depth_keys": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "recogs_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "recogs_set_timed_stages": (C.c_int, [C.c_void_p, C.c_uint32]),
     "recogs_stage_times": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
@@ -462,6 +463,14 @@ class Context:
         self._check(self._L.recogs_tile_lists(self._h, ranges.data_ptr(), ids.data_ptr(),
                                               max(n_pairs, 1), _stream_ptr(stream)))
         return ranges, ids[:n_pairs]
+
+    def depth_keys(self, n, device="cuda", stream=None):
+        """Float32 depth keys of the last render (as float32; 0 for culled)."""
+        import torch
+        keys = torch.empty((max(n, 1),), dtype=torch.int32, device=device)
+        self._check(self._L.recogs_depth_keys(self._h, keys.data_ptr(), max(n, 1),
+                                              _stream_ptr(stream)))
+        return keys[:n].view(torch.float32)
 
     def set_timing(self, enable: bool, stages=None):
         """Event timing of each stage (or only of the named stages)."""

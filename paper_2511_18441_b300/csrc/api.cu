@@ -143,6 +143,8 @@ struct recogs_ctx {
     int last_tiles = 0;
     const uint32_t* last_ids = nullptr;
     const uint2* last_ranges = nullptr;
+    int64_t last_n = 0;
+    const uint32_t* last_zkey = nullptr;
     // timing and counts
     bool timing = false;
     uint32_t timed_stages = ~0u;   // bit per Stage
@@ -643,6 +645,8 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
     ctx->last_tiles = tiles;
     ctx->last_ids = ids;
     ctx->last_ranges = P<uint2>(sc.ranges);
+    ctx->last_n = n;
+    ctx->last_zkey = n > 0 ? P<uint32_t>(sc.zkey) : nullptr;
 
     if (stats) {
         CK(cudaMemcpyAsync(ctx->h_counters, dctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
@@ -1293,6 +1297,21 @@ recogs_status recogs_tile_lists(recogs_ctx* ctx, uint32_t* ranges_out, uint32_t*
     if (ctx->last_pairs > 0)
         CK(cudaMemcpyAsync(ids_out, ctx->last_ids, sizeof(uint32_t) * (size_t)ctx->last_pairs,
                            cudaMemcpyDeviceToDevice, st));
+    return RECOGS_OK;
+}
+
+recogs_status recogs_depth_keys(recogs_ctx* ctx, uint32_t* keys_out, int64_t capacity,
+                                void* stream) {
+    if (!ctx) return RECOGS_EINVAL;
+    if (!ctx->last_ranges) return fail(ctx, RECOGS_EINVAL, "no render on this context yet");
+    if (capacity < ctx->last_n)
+        return fail(ctx, RECOGS_ECAPACITY, "capacity %lld < %lld Gaussians", (long long)capacity,
+                    (long long)ctx->last_n);
+    if (ctx->last_n == 0) return RECOGS_OK;
+    if (!keys_out) return fail(ctx, RECOGS_EINVAL, "keys_out is NULL");
+    DeviceGuard g(ctx->device);
+    CK(cudaMemcpyAsync(keys_out, ctx->last_zkey, sizeof(uint32_t) * (size_t)ctx->last_n,
+                       cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
     return RECOGS_OK;
 }
 

@@ -352,7 +352,12 @@ __device__ __forceinline__ uint32_t prep_one(int i, float mx, float my, float mz
     tile_span(v, ey, cam.tiles_y, ty0, ty1);
     if (!(tx0 <= tx1 && ty0 <= ty1)) return 0;
     cnt = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
-    zbits = __float_as_uint(tz);
+    // depth key: tz + tzl carries the view depth to ~2^-44 relative, so its
+    // rounded sum is the float32 nearest the exact depth (correct rounding
+    // unless the depth lies within ~1e-13 relative of a rounding midpoint):
+    // two Gaussians swap places against the exact depth order only when
+    // their keys are equal, and equal keys are ordered by index
+    zbits = __float_as_uint(__fadd_rn(tz, tzl));
     rx0 = tx0;
     ry0 = ty0;
     rw = tx1 - tx0 + 1;

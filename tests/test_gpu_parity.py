@@ -117,7 +117,7 @@ def test_render_tiny_full_image(ctx):
     ds = dscene(w.scene)
     img, T, st = render(ctx, ds, w.camera, w.edit, stats=True)
     ref, sp, order, off, ids = oracle.render_image(w.scene, w.camera, w.edit)
-    info = parity.check_image(img, T, ref)
+    info = parity.check_image(img, T, ref, sp, off, ids)
     print(f"\ntiny: {info}")
     assert st["n_visible"] == int(sp["visible"].sum()) or \
         abs(st["n_visible"] - int(sp["visible"].sum())) <= int((sp["fp_flag"] > 0).sum())
@@ -129,11 +129,13 @@ def test_tile_lists_tiny(ctx):
     ds = dscene(w.scene)
     img, T, st = render(ctx, ds, w.camera, w.edit, stats=True)
     ranges, gids = ctx.tile_lists(st["n_tiles"], st["n_pairs"])
+    keys = ctx.depth_keys(w.scene.n)
     torch.cuda.synchronize()
     sp = oracle.preprocess(w.scene, w.camera, w.edit)
     order = oracle.depth_order(sp)
     off, ids = oracle.tile_lists(sp, order, 16, 16)
-    n = parity.check_tile_lists(parity.to_np(ranges), parity.to_np(gids), sp, off, ids)
+    n = parity.check_tile_lists(parity.to_np(ranges), parity.to_np(gids), parity.to_np(keys),
+                                sp, off, ids)
     assert n > 10000
 
 
@@ -142,8 +144,8 @@ def test_render_background_and_T(ctx, bg):
     w = sg.tiny_workload(n=3000)
     ds = dscene(w.scene)
     img, T = render(ctx, ds, w.camera, None, bg=bg)
-    ref, *_ = oracle.render_image(w.scene, w.camera, None, bg=bg)
-    parity.check_image(img, T, ref)
+    ref, sp, _, off, ids = oracle.render_image(w.scene, w.camera, None, bg=bg)
+    parity.check_image(img, T, ref, sp, off, ids, bg=bg)
 
 
 def test_two_axis_gaussians_worked_example(ctx):
@@ -187,8 +189,8 @@ def test_render_ragged_sizes(ctx, W, H, n):
     edit = sg.Edit(sg.pixel_box_region(W // 4, H // 4, max(1, W // 2), max(1, H // 2)),
                    sg.tint_matrix((0.5, 1.0, 0.25)))
     img, T = render(ctx, ds, cam, edit, bg=(0.1, 0.1, 0.1))
-    ref, *_ = oracle.render_image(sc, cam, edit, bg=(0.1, 0.1, 0.1))
-    parity.check_image(img, T, ref)
+    ref, sp, _, off, ids = oracle.render_image(sc, cam, edit, bg=(0.1, 0.1, 0.1))
+    parity.check_image(img, T, ref, sp, off, ids, bg=(0.1, 0.1, 0.1))
 
 
 def test_render_everything_culled(ctx):
@@ -221,8 +223,8 @@ def test_select_camera_differs_from_render_camera(ctx):
     e = sg.Edit(w.edit.region, w.edit.color_matrix, select_camera=scam)
     ds = dscene(w.scene)
     img, T = render(ctx, ds, w.camera, e)
-    ref, *_ = oracle.render_image(w.scene, w.camera, e)
-    parity.check_image(img, T, ref)
+    ref, sp, _, off, ids = oracle.render_image(w.scene, w.camera, e)
+    parity.check_image(img, T, ref, sp, off, ids)
 
 
 @pytest.mark.parametrize("kind", ["f16", "bf16"])
@@ -234,8 +236,8 @@ def test_render_half_precision_sh_no_edit(ctx, kind):
     ds = dscene(w.scene, kind)
     img, T = render(ctx, ds, w.camera, None)
     shq = sg.from_half(sg.to_half(w.scene.sh, kind), kind)
-    ref, *_ = oracle.render_image(w.scene, w.camera, None, sh=shq)
-    parity.check_image(img, T, ref)
+    ref, sp, _, off, ids = oracle.render_image(w.scene, w.camera, None, sh=shq)
+    parity.check_image(img, T, ref, sp, off, ids)
 
 
 @pytest.mark.parametrize("kind", ["f16", "bf16"])
@@ -273,10 +275,12 @@ def test_render_paper_scale_full_frame(ctx, n, seed):
     ds = dscene(w.scene)
     img, T, st = render(ctx, ds, cam, w.edit, stats=True)
     ranges, gids = ctx.tile_lists(st["n_tiles"], st["n_pairs"])
+    keys = ctx.depth_keys(w.scene.n)
     torch.cuda.synchronize()
     ref, sp, order, off, ids = oracle.render_image(w.scene, cam, w.edit)
-    info = parity.check_image(img, T, ref)
-    nl = parity.check_tile_lists(parity.to_np(ranges), parity.to_np(gids), sp, off, ids)
+    info = parity.check_image(img, T, ref, sp, off, ids)
+    nl = parity.check_tile_lists(parity.to_np(ranges), parity.to_np(gids), parity.to_np(keys),
+                                 sp, off, ids)
     nflag = int((sp["fp_flag"] > 0).sum())
     assert abs(st["n_pairs"] - len(ids)) <= 64 * nflag + 16
     assert nl > 0.99 * len(ids)
@@ -322,8 +326,9 @@ def test_sort_paths_agree(ctx, W, H):
         ctx.set_sort_path(path)
         img, T, st = render(ctx, ds, w.camera, w.edit, stats=True)
         ranges, gids = ctx.tile_lists(st["n_tiles"], st["n_pairs"])
+        keys = ctx.depth_keys(ds.n)
         torch.cuda.synchronize()
-        out[path] = (img, T, parity.to_np(ranges), parity.to_np(gids))
+        out[path] = (img, T, parity.to_np(ranges), parity.to_np(gids), parity.to_np(keys))
     ctx.set_sort_path(0)
     for a, b in zip(out[1], out[2]):
         assert np.array_equal(a, b)
@@ -347,16 +352,17 @@ def test_dense_tile_per_tile_path(ctx):
         ctx.set_sort_path(path)
         img, T, st = render(ctx, ds, cam, None, stats=True)
         ranges, gids = ctx.tile_lists(st["n_tiles"], st["n_pairs"])
+        keys = ctx.depth_keys(ds.n)
         torch.cuda.synchronize()
-        out[path] = (img, T, parity.to_np(ranges), parity.to_np(gids))
+        out[path] = (img, T, parity.to_np(ranges), parity.to_np(gids), parity.to_np(keys))
     ctx.set_sort_path(0)
     r = out[1][2]
     assert 8192 < (r[:, 1] - r[:, 0]).max() <= 16384
     for a, b in zip(out[1], out[2]):
         assert np.array_equal(a, b)
     ref, sp, order, off, ids = oracle.render_image(sc, cam, None)
-    parity.check_image(out[1][0], out[1][1], ref)
-    parity.check_tile_lists(r, out[1][3], sp, off, ids)
+    parity.check_image(out[1][0], out[1][1], ref, sp, off, ids)
+    parity.check_tile_lists(r, out[1][3], out[1][4], sp, off, ids)
     # without the read back the frame stays on the per-tile path
     ctx.set_pair_capacity(int(r[-1, 1]) + 1024)
     img2, T2 = render(ctx, ds, cam, None)
@@ -384,8 +390,9 @@ def test_equal_depth_run_in_a_tile(ctx):
         ctx.set_sort_path(path)
         img, T, st = render(ctx, ds, cam, None, stats=True)
         ranges, gids = ctx.tile_lists(st["n_tiles"], st["n_pairs"])
+        keys = ctx.depth_keys(ds.n)
         torch.cuda.synchronize()
-        out[path] = (img, T, parity.to_np(ranges), parity.to_np(gids))
+        out[path] = (img, T, parity.to_np(ranges), parity.to_np(gids), parity.to_np(keys))
     ctx.set_sort_path(0)
     r = out[1][2]
     assert (r[:, 1] - r[:, 0]).max() > 1000
@@ -423,8 +430,9 @@ def test_close_depths_in_a_tile(ctx):
         ctx.set_sort_path(path)
         img, T, st = render(ctx, ds, cam, None, stats=True)
         ranges, gids = ctx.tile_lists(st["n_tiles"], st["n_pairs"])
+        keys = ctx.depth_keys(ds.n)
         torch.cuda.synchronize()
-        out[path] = (img, T, parity.to_np(ranges), parity.to_np(gids))
+        out[path] = (img, T, parity.to_np(ranges), parity.to_np(gids), parity.to_np(keys))
     ctx.set_sort_path(0)
     r = out[1][2]
     assert (r[:, 1] - r[:, 0]).max() > 2000
@@ -447,8 +455,9 @@ def test_large_gaussians_counted_and_scattered_by_the_block(ctx):
         ctx.set_sort_path(path)
         img, T, st = render(ctx, ds, w.camera, w.edit, stats=True)
         ranges, gids = ctx.tile_lists(st["n_tiles"], st["n_pairs"])
+        keys = ctx.depth_keys(ds.n)
         torch.cuda.synchronize()
-        out[path] = (img, T, parity.to_np(ranges), parity.to_np(gids))
+        out[path] = (img, T, parity.to_np(ranges), parity.to_np(gids), parity.to_np(keys))
     ctx.set_sort_path(0)
     for a, b in zip(out[1], out[2]):
         assert np.array_equal(a, b)
@@ -456,8 +465,8 @@ def test_large_gaussians_counted_and_scattered_by_the_block(ctx):
     rect = sp["rect"].reshape(-1, 4)
     ntiles = (rect[:, 1] - rect[:, 0] + 1) * (rect[:, 3] - rect[:, 2] + 1)
     assert (ntiles[big] > 64).sum() >= 20
-    parity.check_image(out[1][0], out[1][1], ref)
-    parity.check_tile_lists(out[1][2], out[1][3], sp, off, ids)
+    parity.check_image(out[1][0], out[1][1], ref, sp, off, ids)
+    parity.check_tile_lists(out[1][2], out[1][3], out[1][4], sp, off, ids)
 
 
 def test_crowded_tile_takes_global_path(ctx):
@@ -474,9 +483,10 @@ def test_crowded_tile_takes_global_path(ctx):
     ds = dscene(sc)
     img, T, st = render(ctx, ds, cam, None, stats=True)
     ranges, gids = ctx.tile_lists(st["n_tiles"], st["n_pairs"])
+    keys = ctx.depth_keys(n)
     torch.cuda.synchronize()
     r = parity.to_np(ranges)
     assert (r[:, 1] - r[:, 0]).max() > 16384
     ref, sp, order, off, ids = oracle.render_image(sc, cam, None)
-    parity.check_image(img, T, ref)
-    parity.check_tile_lists(r, parity.to_np(gids), sp, off, ids)
+    parity.check_image(img, T, ref, sp, off, ids)
+    parity.check_tile_lists(r, parity.to_np(gids), parity.to_np(keys), sp, off, ids)

@@ -103,6 +103,7 @@ def oracle_refit(scene, cam, target):
     y = oracle.render_tiles(sp, off, ids)
     loss, g = oracle.l1_loss_grad(y["rgb"], target)
     grgb = oracle.color_grad(sp, off, ids, g)
+    y["frame"] = (sp, off, ids)
     return y, loss, grgb, oracle.sh_grad(scene, sp, grgb)
 
 
@@ -127,7 +128,7 @@ def test_refit_gradients_match_the_oracle(ctx, n):
     out = ctx.refit_grad(ds, w.camera, tg)
     torch.cuda.synchronize()
     y, loss, grgb, gsh = oracle_refit(w.scene, w.camera, target.astype(np.float64))
-    parity.check_image(parity.to_np(out["image"]), y["T"], y)
+    parity.check_image(parity.to_np(out["image"]), y["T"], y, *y["frame"])
     assert out["loss"] == pytest.approx(loss, rel=1e-5)
     close_enough(parity.to_np(out["grad_rgb"]), grgb)
     close_enough(parity.to_np(out["grad_sh"]), gsh)
