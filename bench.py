@@ -123,12 +123,12 @@ class ClockSampler:
         self.t0 = self.t1 = None
 
     def start(self):
+        # no -i: inside a container the visible GPU may carry another index
+        # than CUDA_VISIBLE_DEVICES names; rows are filtered in stop()
         cmd = ["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}", "--format=csv,noheader,nounits",
                "-lms", "100"]
-        if self.gpu_id is not None:
-            cmd += ["-i", str(self.gpu_id)]
         try:
-            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
                                          text=True)
         except OSError:
             self.proc = None
@@ -162,7 +162,18 @@ class ClockSampler:
                 continue
             rows.append((ts, parts))
         if not rows:
-            return None
+            err = ""
+            try:
+                err = (self.proc.stderr.read() or "").strip()
+            except (OSError, ValueError):
+                pass
+            first = self.lines[0][1] if self.lines else ""
+            return {"unavailable": (err or first or "nvidia-smi printed nothing")[:300],
+                    "lines_read": len(self.lines)}
+        gpus = sorted({r[0] for _, r in rows})
+        if len(gpus) > 1:
+            want = str(self.gpu_id) if str(self.gpu_id) in gpus else gpus[0]
+            rows = [(ts, r) for ts, r in rows if r[0] == want]
         inside = [r for ts, r in rows if self.t0 is not None and self.t0 - 0.15 <= ts <= self.t1 + 0.15]
         use = inside or [r for _, r in rows]
 
@@ -235,81 +246,91 @@ def algorithmic_bytes(stage, stats, n, sh_bytes):
     design notes x units per launch)."""
     W, H = WIDTH, HEIGHT
     tiles = stats["n_tiles"]
+    n_vis = stats["n_visible"]
+    pairs = stats["n_pairs"]
     if stage == "blend":
         # per consumed pair: 4 B index + 36 B record; image 12 B/pixel; 8 B range per tile
         return stats["n_pairs_read"] * 40 + 12 * W * H + 8 * tiles
     if stage == "preprocess":
-        # per Gaussian: 44 B geometry + 48 SH coefficients read, 44 B record written
-        return n * (44 + 48 * sh_bytes + 44)
+        # per Gaussian: 44 B geometry read, 4 B tile count written; per
+        # visible Gaussian: 48 SH coefficients read, 40 B of its 2D record
+        # written (mean 8, conic 12, opacity 4, colour 12, depth 4)
+        return n * (44 + 4) + n_vis * (48 * sh_bytes + 40)
+    if stage == "scatter":
+        # per visible Gaussian 16 B read (count, rectangle, depth key); per
+        # pair one 8-byte key written
+        return n_vis * 16 + pairs * 8
+    if stage == "tile_sort":
+        # per pair: the 8-byte key read, the 4-byte index written
+        return pairs * 12
     return None
+
+
+FRAME_STAGES = ("preprocess", "scatter", "tile_sort", "blend")
+
+
+def frame_algorithmic_bytes(stats, n, sh_bytes):
+    """The frame's minimum traffic: the sum over the stages that move the
+    per-Gaussian and per-pair data."""
+    return sum(algorithmic_bytes(k, stats, n, sh_bytes) for k in FRAME_STAGES)
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle timing (the reference arm and the cpu_baseline leg)
 
-def oracle_frame_sample(w, tile_stride, threads=None):
-    """One FP64 oracle frame on a bounded sample: the full per-Gaussian pass,
-    depth order and tile lists, then every tile_stride-th tile blended. Returns
-    (estimated seconds per full frame, seconds spent)."""
+def oracle_frame(w, threads=None):
+    """One whole FP64 oracle frame of the workload: the per-Gaussian pass
+    (selection, recolour, projection, colour), depth order, tile lists and
+    every tile blended. Returns (seconds, image dict)."""
     import oracle
     t0 = time.perf_counter()
-    sp = oracle.preprocess(w.scene, w.camera, w.edit, threads=threads)
-    order = oracle.depth_order(sp)
-    tx, ty = (WIDTH + 15) // 16, (HEIGHT + 15) // 16
-    off, ids = oracle.tile_lists(sp, order, tx, ty)
-    t1 = time.perf_counter()
-    tiles = np.arange(0, tx * ty, tile_stride, dtype=np.int32)
-    oracle.render_tiles(sp, off, ids, tiles, threads=threads)
-    t2 = time.perf_counter()
-    frame = (t1 - t0) + (t2 - t1) * (tx * ty) / len(tiles)
-    return frame, t2 - t0
+    img, *_ = oracle.render_image(w.scene, w.camera, w.edit, threads=threads)
+    return time.perf_counter() - t0, img
 
 
 def cpu_baseline(w, budget_s=20.0):
+    """Whole oracle frames on all host cores until about budget_s / 2 of
+    wall time is spent (at least one). Returns (the cpu_baseline entry, the
+    last frame's image)."""
     cores = os.cpu_count() or 1
-    frames = []
-    spent = 0.0
-    stride = 4
-    while spent < budget_s * 0.5 or not frames:
-        f, s = oracle_frame_sample(w, stride, threads=cores)
-        frames.append(f)
-        spent += s
-        if spent > budget_s:
-            break
-    est = statistics.median(frames)
-    return {"value": 1.0 / est, "unit": "frames/s", "cores": cores, "kind": "oracle",
-            "sample": (f"{len(frames)} oracle frame(s): full per-Gaussian pass, depth order and "
-                       f"tile lists over all {N_SPLATS} Gaussians, every {stride}th of "
-                       f"{((WIDTH + 15) // 16) * ((HEIGHT + 15) // 16)} tiles blended, scaled "
-                       f"to a full frame; {spent:.1f} s of CPU wall time")}
+    times = []
+    img = None
+    while not times or sum(times) < budget_s * 0.5:
+        t, img = oracle_frame(w, threads=cores)
+        times.append(t)
+    spent = sum(times)
+    return ({"value": len(times) / spent, "unit": "frames/s", "cores": cores, "kind": "oracle",
+             "sample": (f"{len(times)} whole FP64 oracle frame(s) of the workload ({N_SPLATS} "
+                        f"Gaussians, all {((WIDTH + 15) // 16) * ((HEIGHT + 15) // 16)} tiles "
+                        f"blended) on {cores} threads: {spent:.1f} s of wall time")}, img)
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle, each step one whole frame of the
+    workload on all host cores (rank 0 only)."""
     if rank != 0:
         return
     w = make_workload()
     cores = os.cpu_count() or 1
-    stride = 16
     for _ in range(args.warmup):
-        oracle_frame_sample(w, stride, threads=cores)
-    frames = []
+        oracle_frame(w, threads=cores)
+    times = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        f, _ = oracle_frame_sample(w, stride, threads=cores)
-        frames.append(f)
+        times.append(oracle_frame(w, threads=cores)[0])
     spent = time.perf_counter() - t0
-    total = sum(frames)
-    value = args.steps / total
+    value = args.steps / spent
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
+        "ms_per_step": 1000.0 * spent / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config("f32"),
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
-                         "sample": (f"per step: full per-Gaussian pass, depth order and tile "
-                                    f"lists over all {N_SPLATS} Gaussians, every {stride}th tile "
-                                    f"blended, scaled to a full frame ({spent:.1f} s total)")},
+                         "sample": (f"each step one whole FP64 oracle frame of the workload "
+                                    f"({N_SPLATS} Gaussians, every tile blended) on {cores} "
+                                    f"threads; {args.steps} steps in {spent:.1f} s, slowest "
+                                    f"{max(times):.2f} s")},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -406,12 +427,23 @@ def run_ours(args, rank, world, local):
 
     # other stages' HBM fractions for context (from the breakdown frames)
     other = {}
-    for k in ("preprocess", "blend"):
+    for k in FRAME_STAGES:
         if k in breakdown and k != dom:
+            # bytes of the stage per frame over its time per frame (the tile
+            # sort is one launch per size class)
             a = algorithmic_bytes(k, stats, N_SPLATS, sh_bytes)
-            t = breakdown[k][0] / max(breakdown[k][1], 1)
+            t = breakdown[k][0] / k_breakdown
             other[k] = {"achieved_gbs": a / (t / 1000.0) / 1e9,
-                        "frac": a / (t / 1000.0) / 1e9 / peaks["hbm_gbs"], "ms_per_launch": t}
+                        "frac": a / (t / 1000.0) / 1e9 / peaks["hbm_gbs"], "ms_per_frame": t,
+                        "launches_per_frame": breakdown[k][1] / k_breakdown,
+                        "algorithmic_bytes": a}
+    # the whole frame: the stages' algorithmic bytes over the timed frame time
+    fb = frame_algorithmic_bytes(stats, N_SPLATS, sh_bytes)
+    frame_ms = max_ms / args.steps
+    whole = {"achieved_gbs": fb / (frame_ms / 1000.0) / 1e9,
+             "frac": fb / (frame_ms / 1000.0) / 1e9 / peaks["hbm_gbs"],
+             "algorithmic_bytes": fb, "ms_per_frame": frame_ms,
+             "stages": list(FRAME_STAGES), "peak_source": f"{peaks_src} copy bandwidth"}
 
     # end to end through the public API: pinned host scene in, host image out
     def e2e_run(sh_dtype):
@@ -443,6 +475,7 @@ def run_ours(args, rank, world, local):
     # context: 16-bit SH storage, the frame with the read back, and the frame
     # replayed as a one-view CUDA graph (recogs_render_batch)
     variants = {}
+    variant_images = {}
     if not args.no_variants:
         k = max(10, args.steps // 2)
 
@@ -466,6 +499,8 @@ def run_ours(args, rank, world, local):
                 dv = binding.DeviceScene.from_numpy(w.scene, dev, kind)
                 variants[kind] = timed(
                     lambda: ctx.render(dv, w.camera, w.edit, image_out=img, stream=stream))
+                torch.cuda.synchronize(dev)
+                variant_images[kind] = img.cpu().numpy()
                 del dv
         ctx.set_pair_capacity(0)
         variants["with_readback"] = timed(frame)
@@ -476,8 +511,25 @@ def run_ours(args, rank, world, local):
         variants["graph_replay"]["kernel_nodes"] = ctx.batch_info()["graph_launches"]
 
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w)
+        ctx.render(ds, w.camera, w.edit, image_out=img, stream=stream)
+        torch.cuda.synchronize(dev)
+        ours = img.cpu().numpy()
+        cpu, ref_img = cpu_baseline(w)
+        # the error of each measured form against the FP64 oracle frame
+        for kind, im in [("f32", ours)] + sorted(variant_images.items()):
+            d = im.astype(np.float64) - ref_img["rgb"]
+            mse = float(np.mean(d ** 2))
+            e = {"max_abs_error": float(np.abs(d).max()),
+                 "psnr_db": 10.0 * math.log10(1.0 / mse) if mse > 0 else float("inf"),
+                 "vs": "FP64 oracle frame of the float32 scene"}
+            if kind == "f32":
+                e["pixels_over_2e-4"] = int((np.abs(d).max(-1) > 2e-4).sum())
+                e["oracle_flagged_pixels"] = int((ref_img["flag"] > 0).sum())
+                accuracy = e
+            else:
+                variants[kind]["error"] = e
 
     if rank == 0:
         line = {
@@ -493,6 +545,8 @@ def run_ours(args, rank, world, local):
             "stage_ms_note": f"every stage timed by events over {k_breakdown} extra frames",
             "roofline": roof,
             "roofline_other": other,
+            "roofline_frame": whole,
+            "accuracy": accuracy,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -990,7 +1044,7 @@ def run_mlp(args, rank, world, local):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--sh-dtype", choices=["f32", "f16", "bf16"], default="f32")

@@ -208,8 +208,10 @@ RECOGS_API recogs_status recogs_render_depth(recogs_ctx* ctx, const recogs_scene
 
 /* Adam (Kingma and Ba, 2015): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
  * C -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), the square root
- * and the division to a few ulp. recogs_refit_step needs eps > 0 (a
- * coefficient that never had a gradient would otherwise divide 0 by 0). */
+ * and the division to a few ulp. recogs_refit_step needs eps >= FLT_MIN, a
+ * normal float (a coefficient that never had a gradient would otherwise
+ * divide 0 by 0, and the approximate reciprocal flushes a subnormal sum to
+ * 0). */
 typedef struct {
     float lr;
     float beta1;                /* e.g. 0.9 */
@@ -383,7 +385,7 @@ RECOGS_API recogs_status recogs_recolor_weighted(recogs_ctx* ctx, recogs_scene* 
  * file-scope device array of about 13 MiB inside librecogs.so, which every
  * GPU that loads the library holds until the process exits. The first call
  * on each device looks up that array's device address (cudaGetSymbolAddress,
- * with that device current); make that first call before any stream capture.
+ * with that device current).
  *
  * Limits: at most RECOGS_NOALLOC_MAX_GAUSSIANS Gaussians, at most
  * RECOGS_NOALLOC_MAX_TILES 16x16 tiles (e.g. 1024x1024 px) and at most
@@ -391,13 +393,17 @@ RECOGS_API recogs_status recogs_recolor_weighted(recogs_ctx* ctx, recogs_scene* 
  * RECOGS_ECAPACITY with a message and render nothing (a pair overflow is only
  * known after the per-Gaussian pass; the image is then left unwritten).
  *
- * Arguments and results are those of recogs_render (device scene, device
- * image_hwc_out and optional final_T_out, host bg and edit); error_out
- * (host, may be NULL) receives a message of at most error_len bytes. The
- * call reads two counts back to the host (a stream synchronisation).
- * All calls share the one array: calls that overlap on the GPU (other
- * streams, other host threads) race and must be serialised by the caller.
- * Each call clears the parts that must start at zero. */
+ * Arguments, their checks and results are those of recogs_render (device
+ * scene, device image_hwc_out and optional final_T_out, host bg and edit;
+ * NULL, non-finite or misaligned arguments give RECOGS_EINVAL); error_out
+ * (host, may be NULL) receives a message of at most error_len bytes. Every
+ * call reads the frame's counts back to the host mid-frame, so it
+ * synchronises its stream each time and cannot be captured into a CUDA
+ * graph. A frame with a tile above 16384 pairs is sorted by the global radix
+ * path, whose bounded device waits report RECOGS_ETIMEOUT (invalid image)
+ * from the same call. All calls share the one array: calls that overlap on
+ * the GPU (other streams, other host threads) race and must be serialised by
+ * the caller. Each call clears the parts that must start at zero. */
 RECOGS_API recogs_status recogs_render_noalloc(const recogs_scene* scene,
                                                const recogs_camera* camera,
                                                const recogs_edit* edit, const float* bg,

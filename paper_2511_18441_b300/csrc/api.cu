@@ -12,6 +12,7 @@
 // instead: compaction of visible Gaussians -> radix sort by depth -> pair
 // offsets in depth order -> pair expansion -> stable radix sort by tile.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -271,101 +272,35 @@ void collect_times(recogs_ctx* ctx) {
 
 bool finite(float x) { return std::isfinite(x); }
 
-recogs_status check_camera(recogs_ctx* ctx, const recogs_camera* c, const char* what) {
-    if (!c) return fail(ctx, RECOGS_EINVAL, "%s is NULL", what);
-    if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384)
-        return fail(ctx, RECOGS_EINVAL, "%s size %dx%d outside 1..16384", what, c->width,
-                    c->height);
-    if (!(c->fx > 0.f) || !(c->fy > 0.f) || !finite(c->fx) || !finite(c->fy) || !finite(c->cx) ||
-        !finite(c->cy) || !(c->z_near >= 0.f) || !finite(c->z_near))
-        return fail(ctx, RECOGS_EINVAL, "%s intrinsics or z_near invalid", what);
-    for (int k = 0; k < 12; ++k)
-        if (!finite(c->world_to_view[k])) return fail(ctx, RECOGS_EINVAL, "%s pose not finite", what);
-    for (int k = 0; k < 3; ++k)
-        if (!finite(c->cam_pos[k])) return fail(ctx, RECOGS_EINVAL, "%s position not finite", what);
-    return RECOGS_OK;
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// The shared checks of args.cu, with the message kept as the context's last error.
+template <typename F>
+recogs_status checked(recogs_ctx* ctx, F f) {
+    char buf[512];
+    buf[0] = '\0';
+    const recogs_status s = f(ErrSink{buf, sizeof(buf)});
+    if (s != RECOGS_OK && ctx) ctx->err = buf;
+    return s;
 }
 
-DevCamera dev_camera(const recogs_camera& c) {
-    DevCamera d;
-    d.width = c.width;
-    d.height = c.height;
-    d.tiles_x = (c.width + kTile - 1) / kTile;
-    d.tiles_y = (c.height + kTile - 1) / kTile;
-    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
-    for (int r = 0; r < 3; ++r) {
-        for (int k = 0; k < 3; ++k) d.W[r * 3 + k] = c.world_to_view[r * 4 + k];
-        d.t[r] = c.world_to_view[r * 4 + 3];
-        d.pos[r] = c.cam_pos[r];
-    }
-    d.z_near = c.z_near;
-    d.limx = (float)(1.3 * c.width / (2.0 * c.fx));
-    d.limy = (float)(1.3 * c.height / (2.0 * c.fy));
-    return d;
+recogs_status check_camera(recogs_ctx* ctx, const recogs_camera* c, const char* what) {
+    return checked(ctx, [&](ErrSink e) { return check_camera_args(c, what, e); });
 }
+
+DevCamera dev_camera(const recogs_camera& c) { return camera_to_dev(c); }
 
 recogs_status dev_region(recogs_ctx* ctx, const recogs_region* r, const recogs_camera& cam,
                          DevRegion& d) {
-    memset(&d, 0, sizeof(d));
-    if (!r) return fail(ctx, RECOGS_EINVAL, "region is NULL");
-    if (!r->xy) return fail(ctx, RECOGS_EINVAL, "region.xy is NULL");
-    d.kind = r->kind;
-    d.eps = 1e-6f * (float)(cam.width > cam.height ? cam.width : cam.height);
-    if (r->kind == RECOGS_REGION_BOX) {
-        for (int k = 0; k < 4; ++k) {
-            if (!finite(r->xy[k])) return fail(ctx, RECOGS_EINVAL, "box corner not finite");
-            d.xy[k] = r->xy[k];
-        }
-        d.n = 2;
-    } else if (r->kind == RECOGS_REGION_POLYGON) {
-        if (r->n_vertices < 3 || r->n_vertices > RECOGS_MAX_POLYGON)
-            return fail(ctx, RECOGS_EINVAL, "polygon needs 3..%d vertices, got %d",
-                        RECOGS_MAX_POLYGON, r->n_vertices);
-        for (int k = 0; k < 2 * r->n_vertices; ++k) {
-            if (!finite(r->xy[k])) return fail(ctx, RECOGS_EINVAL, "polygon vertex not finite");
-            d.xy[k] = r->xy[k];
-        }
-        d.n = r->n_vertices;
-        region_slopes(d);
-    } else {
-        return fail(ctx, RECOGS_EINVAL, "unknown region kind %d", r->kind);
-    }
-    return RECOGS_OK;
-}
-
-void dc_fix_of(const float M[9], float out[3]) {
-    // (row sum - 1) * 0.5 / Y_0 with Y_0 = 1 / (2 sqrt(pi)): (row sum - 1) sqrt(pi)
-    const double sqrt_pi = 1.7724538509055159;
-    for (int c = 0; c < 3; ++c) {
-        const double row = (double)M[3 * c] + (double)M[3 * c + 1] + (double)M[3 * c + 2];
-        out[c] = (float)((row - 1.0) * sqrt_pi);
-    }
+    return checked(ctx, [&](ErrSink e) { return region_to_dev(r, cam, d, e); });
 }
 
 recogs_status check_tint(recogs_ctx* ctx, const recogs_tint* t) {
-    if (!t) return fail(ctx, RECOGS_EINVAL, "tint is NULL");
-    for (int k = 0; k < 9; ++k)
-        if (!finite(t->color_matrix[k])) return fail(ctx, RECOGS_EINVAL, "colour matrix not finite");
-    return RECOGS_OK;
+    return checked(ctx, [&](ErrSink e) { return check_tint_args(t, e); });
 }
 
-bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
-
-size_t sh_elem_size(int dt) { return dt == RECOGS_F32 ? 4 : 2; }
-
 recogs_status check_scene(recogs_ctx* ctx, const recogs_scene* s) {
-    if (!s) return fail(ctx, RECOGS_EINVAL, "scene is NULL");
-    if (s->n < 0 || s->n >= (int64_t)1 << 31)
-        return fail(ctx, RECOGS_EINVAL, "scene.n = %lld outside 0..2^31-1", (long long)s->n);
-    if (s->sh_dtype != RECOGS_F32 && s->sh_dtype != RECOGS_F16 && s->sh_dtype != RECOGS_BF16)
-        return fail(ctx, RECOGS_EINVAL, "unknown sh_dtype %d", s->sh_dtype);
-    if (s->n == 0) return RECOGS_OK;
-    if (!s->xyz || !s->log_scale || !s->quat || !s->opacity_logit || !s->sh)
-        return fail(ctx, RECOGS_EINVAL, "a scene array is NULL");
-    if (!aligned(s->xyz, 4) || !aligned(s->log_scale, 4) || !aligned(s->quat, 4) ||
-        !aligned(s->opacity_logit, 4) || !aligned(s->sh, sh_elem_size(s->sh_dtype)))
-        return fail(ctx, RECOGS_EINVAL, "a scene array is misaligned");
-    return RECOGS_OK;
+    return checked(ctx, [&](ErrSink e) { return check_scene_args(s, e); });
 }
 
 // The frame pipeline on device-resident inputs.
@@ -379,17 +314,7 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
     const int tiles = dc.tiles_x * dc.tiles_y;
 
     DevEdit de;
-    memset(&de, 0, sizeof(de));
-    if (edit) {
-        const recogs_camera* sc = edit->select_camera ? edit->select_camera : &cam;
-        if (edit->select_camera) CKS(check_camera(ctx, sc, "edit.select_camera"));
-        CKS(check_tint(ctx, &edit->tint));
-        CKS(dev_region(ctx, &edit->region, *sc, de.region));
-        de.enabled = 1;
-        de.cam = dev_camera(*sc);
-        for (int k = 0; k < 9; ++k) de.M[k] = edit->tint.color_matrix[k];
-        dc_fix_of(de.M, de.dc_fix);
-    }
+    CKS(checked(ctx, [&](ErrSink e) { return edit_to_dev(edit, cam, de, e); }));
 
     const int nb = (n + kPrepThreads - 1) / kPrepThreads;
     CKS(ensure(ctx, sc.counters, sizeof(DevCounters)));
@@ -1520,8 +1445,9 @@ recogs_status recogs_refit_step(recogs_ctx* ctx, recogs_scene* scene, const reco
     if (scene->n > 0 && (!adam_m || !adam_v || !aligned(adam_m, 4) || !aligned(adam_v, 4)))
         return fail(ctx, RECOGS_EINVAL, "adam_m / adam_v NULL or misaligned");
     if (adam->step < 1 || !(adam->lr >= 0.f) || !(adam->beta1 >= 0.f && adam->beta1 < 1.f) ||
-        !(adam->beta2 >= 0.f && adam->beta2 < 1.f) || !(adam->eps > 0.f))
-        return fail(ctx, RECOGS_EINVAL, "Adam parameters out of range");
+        !(adam->beta2 >= 0.f && adam->beta2 < 1.f) || !(adam->eps >= FLT_MIN) ||
+        !std::isfinite(adam->eps))
+        return fail(ctx, RECOGS_EINVAL, "Adam parameters out of range (eps must be a normal float)");
     DeviceGuard g(ctx->device);
     return refit(ctx, *scene, *camera, bgv, target_hwc, nullptr, nullptr, nullptr, adam_m, adam_v,
                  adam, loss_out, (cudaStream_t)stream);

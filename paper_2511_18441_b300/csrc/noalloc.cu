@@ -96,37 +96,7 @@ recogs_status scratch_address(unsigned char** out, char* err, size_t len) {
     return RECOGS_OK;
 }
 
-bool finite3(const float* v, int k) {
-    for (int i = 0; i < k; ++i)
-        if (!std::isfinite(v[i])) return false;
-    return true;
-}
-
-bool camera_ok(const recogs_camera* c) {
-    return c && c->width >= 1 && c->height >= 1 && c->width <= 16384 && c->height <= 16384 &&
-           c->fx > 0.f && c->fy > 0.f && std::isfinite(c->fx) && std::isfinite(c->fy) &&
-           std::isfinite(c->cx) && std::isfinite(c->cy) && c->z_near >= 0.f &&
-           std::isfinite(c->z_near) &&
-           finite3(c->world_to_view, 12) && finite3(c->cam_pos, 3);
-}
-
-DevCamera to_dev(const recogs_camera& c) {
-    DevCamera d;
-    d.width = c.width;
-    d.height = c.height;
-    d.tiles_x = (c.width + kTile - 1) / kTile;
-    d.tiles_y = (c.height + kTile - 1) / kTile;
-    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
-    for (int r = 0; r < 3; ++r) {
-        for (int k = 0; k < 3; ++k) d.W[r * 3 + k] = c.world_to_view[r * 4 + k];
-        d.t[r] = c.world_to_view[r * 4 + 3];
-        d.pos[r] = c.cam_pos[r];
-    }
-    d.z_near = c.z_near;
-    d.limx = (float)(1.3 * c.width / (2.0 * c.fx));
-    d.limy = (float)(1.3 * c.height / (2.0 * c.fy));
-    return d;
-}
+bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }
 
 }  // namespace
 
@@ -137,14 +107,15 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
     char* err = error_out;
     const size_t el = error_len;
     if (err && el) err[0] = '\0';
-    if (!scene || !camera_ok(camera) || !image_hwc_out)
-        return report(err, el, RECOGS_EINVAL, "scene, camera or image_hwc_out invalid");
-    if (scene->n < 0 || (scene->sh_dtype != RECOGS_F32 && scene->sh_dtype != RECOGS_F16 &&
-                         scene->sh_dtype != RECOGS_BF16))
-        return report(err, el, RECOGS_EINVAL, "scene.n or scene.sh_dtype invalid");
-    if (scene->n > 0 && (!scene->xyz || !scene->log_scale || !scene->quat ||
-                         !scene->opacity_logit || !scene->sh))
-        return report(err, el, RECOGS_EINVAL, "a scene array is NULL");
+    // the same argument checks as recogs_render (args.cu)
+    const ErrSink sink{err, el};
+    recogs_status s = check_scene_args(scene, sink);
+    if (s != RECOGS_OK) return s;
+    if ((s = check_camera_args(camera, "camera", sink)) != RECOGS_OK) return s;
+    if (!image_hwc_out || !aligned4(image_hwc_out))
+        return report(err, el, RECOGS_EINVAL, "image_hwc_out is NULL or misaligned");
+    if (final_T_out && !aligned4(final_T_out))
+        return report(err, el, RECOGS_EINVAL, "final_T_out is misaligned");
     const int tiles = ((camera->width + kTile - 1) / kTile) * ((camera->height + kTile - 1) / kTile);
     if ((size_t)scene->n > kMaxN)
         return report(err, el, RECOGS_ECAPACITY,
@@ -156,48 +127,20 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
                       camera->width, camera->height, RECOGS_NOALLOC_MAX_TILES);
     float bgv[3] = {0.f, 0.f, 0.f};
     if (bg) {
-        if (!finite3(bg, 3)) return report(err, el, RECOGS_EINVAL, "bg not finite");
-        for (int k = 0; k < 3; ++k) bgv[k] = bg[k];
+        for (int k = 0; k < 3; ++k) {
+            if (!std::isfinite(bg[k])) return report(err, el, RECOGS_EINVAL, "bg not finite");
+            bgv[k] = bg[k];
+        }
     }
     DevEdit de;
-    memset(&de, 0, sizeof(de));
-    if (edit) {
-        const recogs_camera* sc = edit->select_camera ? edit->select_camera : camera;
-        if (!camera_ok(sc)) return report(err, el, RECOGS_EINVAL, "edit.select_camera invalid");
-        if (!finite3(edit->tint.color_matrix, 9))
-            return report(err, el, RECOGS_EINVAL, "colour matrix not finite");
-        const recogs_region& r = edit->region;
-        if (!r.xy) return report(err, el, RECOGS_EINVAL, "region.xy is NULL");
-        de.region.kind = r.kind;
-        de.region.eps = 1e-6f * (float)(sc->width > sc->height ? sc->width : sc->height);
-        if (r.kind == RECOGS_REGION_BOX) {
-            if (!finite3(r.xy, 4)) return report(err, el, RECOGS_EINVAL, "box not finite");
-            for (int k = 0; k < 4; ++k) de.region.xy[k] = r.xy[k];
-            de.region.n = 2;
-        } else if (r.kind == RECOGS_REGION_POLYGON) {
-            if (r.n_vertices < 3 || r.n_vertices > RECOGS_MAX_POLYGON || !finite3(r.xy, 2 * r.n_vertices))
-                return report(err, el, RECOGS_EINVAL, "polygon invalid");
-            for (int k = 0; k < 2 * r.n_vertices; ++k) de.region.xy[k] = r.xy[k];
-            de.region.n = r.n_vertices;
-            region_slopes(de.region);
-        } else {
-            return report(err, el, RECOGS_EINVAL, "unknown region kind %d", r.kind);
-        }
-        de.enabled = 1;
-        de.cam = to_dev(*sc);
-        for (int k = 0; k < 9; ++k) de.M[k] = edit->tint.color_matrix[k];
-        for (int c = 0; c < 3; ++c) {
-            const double row = (double)de.M[3 * c] + de.M[3 * c + 1] + de.M[3 * c + 2];
-            de.dc_fix[c] = (float)((row - 1.0) * 1.7724538509055159);  // (row - 1) 0.5 / Y_0
-        }
-    }
+    if ((s = edit_to_dev(edit, *camera, de, sink)) != RECOGS_OK) return s;
 
     unsigned char* base = nullptr;
-    recogs_status s = scratch_address(&base, err, el);
+    s = scratch_address(&base, err, el);
     if (s != RECOGS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const int n = (int)scene->n;
-    const DevCamera dc = to_dev(*camera);
+    const DevCamera dc = camera_to_dev(*camera);
     auto U32 = [&](size_t o) { return reinterpret_cast<uint32_t*>(base + o); };
     DevCounters* dctr = reinterpret_cast<DevCounters*>(base + oCounters);
     uint2* ranges = reinterpret_cast<uint2*>(base + oRanges);
@@ -210,8 +153,10 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
             return report(err, el, RECOGS_ECUDA, "%s: %s", #expr, cudaGetErrorString(_e)); \
     } while (0)
 
-    // the array keeps the previous call's contents: zero what must start at zero
-    NA_CK(cudaMemsetAsync(dctr, 0, kCountersClearBytes, st));
+    // the array keeps the previous call's contents: zero what must start at
+    // zero (the frame counters and the error word: every error this call
+    // reports is its own)
+    NA_CK(cudaMemsetAsync(dctr, 0, sizeof(DevCounters), st));
     NA_CK(cudaMemsetAsync(U32(oTileCount), 0, sizeof(uint32_t) * kTilePartsSmall * (size_t)tiles, st));
 
     uint32_t V = 0, P = 0;
@@ -238,12 +183,6 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
     NA_CK(cudaStreamSynchronize(st));
     V = hc.n_visible;
     P = hc.n_pairs;
-    if (hc.error & kErrTimeout) {
-        NA_CK(cudaMemsetAsync(&dctr->error, 0, sizeof(uint32_t), st));
-        return report(err, el, RECOGS_ETIMEOUT,
-                      "a bounded device wait of an earlier call's sort gave up; that image "
-                      "is invalid");
-    }
     if ((P > 0) != (V > 0))
         return report(err, el, RECOGS_ECUDA, "inconsistent frame counters (%u visible, %u pairs)",
                       V, P);
@@ -294,6 +233,16 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
     launch_blend(ranges, U32(oOrder), ids, rec, dc, bgv, image_hwc_out, final_T_out, dctr, 256, nullptr,
                  st);
     NA_CK(cudaGetLastError());
+    // a sort of the global path whose bounded wait gave up left the error
+    // word set (and an invalid image): report it from this call
+    if (P > 0 && (int)hc.max_tile > kMaxSmemTile) {
+        uint32_t e = 0;
+        NA_CK(cudaMemcpyAsync(&e, &dctr->error, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        NA_CK(cudaStreamSynchronize(st));
+        if (e & kErrTimeout)
+            return report(err, el, RECOGS_ETIMEOUT,
+                          "a bounded device wait of the sort gave up; the image is invalid");
+    }
 #undef NA_CK
     return RECOGS_OK;
 }

@@ -66,6 +66,27 @@ struct DevEdit {
     float dc_fix[3];     // (row sum of M - 1) * 0.5 / Y_0, the DC offset correction
 };
 
+// Argument checks and conversions of the C ABI (args.cu), shared by every
+// entry point. Messages go to an ErrSink (buf may be NULL).
+struct ErrSink {
+    char* buf;
+    size_t len;
+};
+recogs_status arg_fail(ErrSink e, recogs_status s, const char* fmt, ...);
+size_t sh_elem_size(int sh_dtype);
+recogs_status check_scene_args(const recogs_scene* s, ErrSink e);
+recogs_status check_camera_args(const recogs_camera* c, const char* what, ErrSink e);
+recogs_status check_tint_args(const recogs_tint* t, ErrSink e);
+DevCamera camera_to_dev(const recogs_camera& c);
+recogs_status region_to_dev(const recogs_region* r, const recogs_camera& cam, DevRegion& d,
+                            ErrSink e);
+// (row sum of M - 1) * 0.5 / Y_0: the DC correction of the recolour
+void dc_fix_of(const float M[9], float out[3]);
+// The edit as the kernels see it (disabled when edit is NULL): selection
+// camera (cam when the edit names none), region, colour matrix, DC correction.
+recogs_status edit_to_dev(const recogs_edit* edit, const recogs_camera& cam, DevEdit& de,
+                          ErrSink e);
+
 // Size classes of the per-tile sort (CTAs of 1024, 512, 256, 128, 64, 32 threads).
 constexpr int kSortClasses = 6;
 

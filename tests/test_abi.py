@@ -66,3 +66,31 @@ def test_null_arguments_rejected_without_touching_a_device(lib):
     assert lib.recogs_select(None, None, None, None, None, None, None) == binding.EINVAL
     assert lib.recogs_render(None, None, None, None, None, None, None, None, None) == binding.EINVAL
     assert lib.recogs_launch_count(None) == 0
+
+
+def test_noalloc_checks_arguments_before_any_device_work(lib):
+    """The allocation-free render applies recogs_render's argument checks
+    before it touches a device: a misaligned scene array or output, or a
+    missing image, is refused with RECOGS_EINVAL and a message (run here
+    without a GPU, so nothing past the checks can have run)."""
+    from paper_2511_18441_b300 import scenegen as sg
+    cam = binding.camera_struct(sg.axis_camera(64, 64, 60.0, 2.5))
+    base = 1 << 20
+    cases = [("xyz", base + 2, binding.F32, base, b"misaligned"),
+             ("quat", base + 1, binding.F32, base, b"misaligned"),
+             ("sh", base + 1, binding.BF16, base, b"misaligned"),
+             ("sh", base + 2, binding.F32, base, b"misaligned"),
+             (None, 0, binding.F32, base + 2, b"image_hwc_out"),
+             (None, 0, binding.F32, 0, b"image_hwc_out")]
+    for field, addr, dtype, image, words in cases:
+        cs = binding.CScene()
+        cs.n = 100
+        cs.xyz = cs.log_scale = cs.quat = cs.opacity_logit = cs.sh = base
+        cs.sh_dtype = dtype
+        if field:
+            setattr(cs, field, addr)
+        msg = C.create_string_buffer(256)
+        s = lib.recogs_render_noalloc(C.byref(cs), C.byref(cam), None, None, image or None, None,
+                                      msg, 256, None)
+        assert s == binding.EINVAL, (field, addr, s)
+        assert words in msg.value, msg.value

@@ -47,17 +47,22 @@ def test_aggregate_single():
 
 def test_algorithmic_bytes_per_unit():
     """The per-unit byte counts of the roofline figures (design table):
-    preprocess 44 + 48 s + 44 per Gaussian, blend 40 per consumed pair + 12
-    per pixel + 8 per tile, SH refit 4 + 1152 per Gaussian + 40 per visible
-    one, gradient blend 40 per pair + 24 per pixel + 8 per tile + 12 per
-    visible Gaussian."""
+    preprocess 48 per Gaussian + 48 s + 40 per visible one, scatter 16 per
+    visible Gaussian + 8 per pair, tile sort 12 per pair, blend 40 per
+    consumed pair + 12 per pixel + 8 per tile, the frame the sum of those
+    four, SH refit 4 + 1152 per Gaussian + 40 per visible one, gradient blend
+    40 per pair + 24 per pixel + 8 per tile + 12 per visible Gaussian."""
     import bench
     W, H = bench.WIDTH, bench.HEIGHT
-    st = {"n_pairs_read": 1000, "n_tiles": 10}
-    assert bench.algorithmic_bytes("preprocess", st, 100, 4) == 100 * (44 + 192 + 44)
-    assert bench.algorithmic_bytes("preprocess", st, 100, 2) == 100 * (44 + 96 + 44)
+    st = {"n_pairs_read": 1000, "n_tiles": 10, "n_visible": 90, "n_pairs": 1200}
+    assert bench.algorithmic_bytes("preprocess", st, 100, 4) == 100 * 48 + 90 * (192 + 40)
+    assert bench.algorithmic_bytes("preprocess", st, 100, 2) == 100 * 48 + 90 * (96 + 40)
     assert bench.algorithmic_bytes("blend", st, 100, 4) == 1000 * 40 + 12 * W * H + 80
-    assert bench.algorithmic_bytes("scatter", st, 100, 4) is None
+    assert bench.algorithmic_bytes("scatter", st, 100, 4) == 90 * 16 + 1200 * 8
+    assert bench.algorithmic_bytes("tile_sort", st, 100, 4) == 1200 * 12
+    assert bench.algorithmic_bytes("scan", st, 100, 4) is None
+    assert bench.frame_algorithmic_bytes(st, 100, 4) == (
+        100 * 48 + 90 * 232 + 90 * 16 + 1200 * 8 + 1200 * 12 + 1000 * 40 + 12 * W * H + 80)
     assert bench.refit_algorithmic_bytes("refit", st, 100, 60) == 100 * 1156 + 60 * 40
     assert (bench.refit_algorithmic_bytes("blend_grad", st, 100, 60)
             == 1000 * 40 + 24 * W * H + 80 + 60 * 12)

@@ -222,3 +222,38 @@ def test_batch_rejects_bad_views(lib, ctx):
     with pytest.raises(lib.RecogsError) as e:
         ctx.batch(scenes, views)()
     assert e.value.status == lib.EINVAL
+
+
+def test_batched_workload_views_match_the_oracle(lib, ctx):
+    """The batched workload as the benchmark launches it (4 scenes of 0.5, 1,
+    2 and 4M Gaussians, 16 ring views each at resolutions from 1280x720 to
+    3840x2160, a box selection and tint per scene; planned, tuned and
+    replayed as one captured graph): a 3840x2160 and a 1280x720 view of the
+    4M scene against the FP64 oracle, every pixel."""
+    import oracle
+    bw = sg.batched_workload()
+    scenes = [dscene(lib, s) for s in bw.scenes]
+    views = [dict(scene=si, camera=cam, edit=edit,
+                  T_out=torch.empty((cam.height, cam.width), device="cuda"))
+             for si, cam, edit in bw.views]
+    b = ctx.batch(scenes, views, graph=True, tune=True)
+    b()                                   # plans, tunes, captures
+    for img in b.images:
+        img.fill_(-1.0)
+    b()                                   # one replay of the captured graph
+    ctx.check()
+    torch.cuda.synchronize()
+    big = len(bw.scenes) - 1
+    assert bw.scenes[big].n == 4_000_000
+    picked = {}
+    for k, (si, cam, edit) in enumerate(bw.views):
+        if si == big and (cam.width, cam.height) in ((3840, 2160), (1280, 720)):
+            picked.setdefault((cam.width, cam.height), k)
+    assert len(picked) == 2, "the 4M scene's ring has no 2160p or no 720p view"
+    for (W, H), k in sorted(picked.items()):
+        si, cam, edit = bw.views[k]
+        img, T = parity.to_np(b.images[k]), parity.to_np(b.T[k])
+        ref, sp, _, off, ids = oracle.render_image(bw.scenes[si], cam, edit)
+        info = parity.check_image(img, T, ref, sp, off, ids)
+        assert int(sp["selected"].sum()) > 1000
+        print(f"\n4M scene, view {k} ({W}x{H}): {info}")

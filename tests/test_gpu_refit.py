@@ -35,10 +35,14 @@ def dscene(scene, kind="f32"):
 
 
 def check_depth(gpu_depth, ref):
+    """The GPU's median depth is the float32 nearest the oracle's FP64 depth
+    of the same Gaussian (its correctly rounded depth key): within half a
+    float32 spacing, both at a rounding midpoint."""
     use = (ref["flag"] == 0) & (ref["dflag"] == 0)
     d_or = ref["depth"]
-    err = np.abs(gpu_depth - d_or)
-    bad = use & (err > parity.DEPTH_REL * np.abs(d_or) + 1e-12)
+    err = np.abs(gpu_depth.astype(np.float64) - d_or)
+    half_ulp = 0.5 * np.spacing(np.abs(d_or).astype(np.float32)).astype(np.float64)
+    bad = use & (err > half_ulp * (1 + 1e-9))
     assert not bad.any(), (f"{int(bad.sum())} depth pixels differ, e.g. "
                            f"gpu {gpu_depth[bad][:5]} oracle {d_or[bad][:5]}")
     assert use.mean() > 0.95

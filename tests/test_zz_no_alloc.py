@@ -6,9 +6,13 @@ device memory, code that cannot keep a library context). This entry point
 uses a fixed device array inside the library instead. These tests call it
 through the C ABI and compare it with recogs_render on two calls in a row
 (with different scenes, so that nothing from the first call leaks into the
-second), and check that inputs beyond its limits are refused. The file is
-named so that pytest collects it last.
+second), on both sort paths (per tile, and the global radix sort a tile of
+more than 16384 pairs takes), and check that inputs beyond its limits and
+misaligned arrays are refused. The file is named so that pytest collects it
+last.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -89,3 +93,56 @@ def test_pair_overflow_is_refused_and_leaves_the_image(lib):
     out, T = noalloc_render(lib, ds, a.camera, a.edit, (0, 0, 0))
     assert np.abs(out - ref_img).max() <= TOL and np.abs(T - ref_T).max() <= TOL
     ctx.close()
+
+
+def crowded_scene(seed, n=20_000):
+    """n small Gaussians around the optical axis: one tile of a 64x64 view
+    holds more than 16384 of them."""
+    rng = np.random.default_rng(seed)
+    xyz = np.stack([rng.normal(0, 0.004, n), rng.normal(0, 0.004, n), rng.uniform(-0.3, 0.3, n)])
+    return sg.Scene(xyz.astype(np.float32), np.full((3, n), -5.5, np.float32),
+                    rng.normal(size=(4, n)).astype(np.float32),
+                    rng.normal(-2.0, 1.0, n).astype(np.float32),
+                    rng.normal(0, 0.3, (16, 3, n)).astype(np.float32))
+
+
+def test_crowded_tile_takes_the_global_sort_path(lib):
+    """A tile of more than 16384 pairs sends the frame through the global
+    radix path (compaction, depth sort, pair expansion, tile sort), whose
+    buffers are carved from the same array: two calls in a row (different
+    scenes) against recogs_render and against the FP64 oracle."""
+    import oracle
+    from tests import parity
+    ctx = lib.Context(0)
+    cam = sg.axis_camera(64, 64, 60.0, 2.5)
+    for seed, bg in ((5, (0.0, 0.0, 0.0)), (9, (0.3, 0.2, 0.1))):
+        sc = crowded_scene(seed)
+        ds = lib.DeviceScene.from_numpy(sc, "cuda", "f32")
+        T0 = torch.empty((cam.height, cam.width), device="cuda")
+        _, st = ctx.render(ds, cam, None, bg=bg, T_out=T0, stats=True)
+        ranges, _ = ctx.tile_lists(st["n_tiles"], st["n_pairs"])
+        r = ranges.cpu().numpy()
+        assert (r[:, 1] - r[:, 0]).max() > 16384
+        assert st["n_pairs"] <= lib.NOALLOC_MAX_PAIRS
+        ref_img, ref_T = reference_render(lib, ctx, ds, cam, None, bg)
+        img, T = noalloc_render(lib, ds, cam, None, bg)
+        assert np.abs(img - ref_img).max() <= TOL
+        assert np.abs(T - ref_T).max() <= TOL
+        ref, sp, _, off, ids = oracle.render_image(sc, cam, None, bg=bg)
+        parity.check_image(img, T, ref, sp, off, ids, bg=bg)
+    ctx.close()
+
+
+def test_misaligned_scene_array_is_refused(lib):
+    """A scene array off its element alignment is refused with
+    RECOGS_EINVAL on the host, before any kernel could read it."""
+    w = sg.tiny_workload(n=1000)
+    ds = lib.DeviceScene.from_numpy(w.scene, "cuda", "f32")
+    cs = ds.struct()
+    cs.xyz = cs.xyz + 2
+    cc = lib.camera_struct(w.camera)
+    img = torch.empty((w.camera.height, w.camera.width, 3), device="cuda")
+    msg = C.create_string_buffer(256)
+    s = lib.load().recogs_render_noalloc(C.byref(cs), C.byref(cc), None, None, img.data_ptr(),
+                                         None, msg, 256, None)
+    assert s == lib.EINVAL and b"misaligned" in msg.value
