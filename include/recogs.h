@@ -429,6 +429,22 @@ RECOGS_API recogs_status recogs_tile_lists(recogs_ctx* ctx, uint32_t* ranges_out
 RECOGS_API recogs_status recogs_depth_keys(recogs_ctx* ctx, uint32_t* keys_out, int64_t capacity,
                                            void* stream);
 
+/* Fault injection for tests of the failure paths (the paper has none; no
+ * fault reaches the GPU: every injected failure is taken on the host or by a
+ * bounded device wait). spec: NULL or "" clears; otherwise comma-separated
+ * items
+ *   "alloc:N"  the N-th device allocation of ctx from now fails once; the
+ *              call that needed it returns RECOGS_ENOMEM and leaves ctx usable;
+ *   "wait:N"   every look-back wait of the global radix sort (the path of a
+ *              frame with a tile above 16384 pairs) polls a word nothing
+ *              writes and gives up after N polls (1 <= N <= 2^20): the frame
+ *              is rejected (background image, T = 1) and RECOGS_ETIMEOUT is
+ *              reported at the next read of the frame's counters
+ *              (recogs_check, or stats); until cleared.
+ * The environment variable RECOGS_FAULT, read by recogs_ctx_create, sets the
+ * same. A malformed spec gives RECOGS_EINVAL and changes nothing. */
+RECOGS_API recogs_status recogs_set_fault(recogs_ctx* ctx, const char* spec);
+
 /* Enable (1) or disable (0) CUDA-event timing of each pipeline stage on the
  * stream each stage runs on. */
 RECOGS_API recogs_status recogs_set_timing(recogs_ctx* ctx, int enable);

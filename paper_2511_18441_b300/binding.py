@@ -97,6 +97,7 @@ SIGNATURES = {
                                         C.c_size_t, C.c_void_p]),
     "recogs_tile_lists": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "recogs_depth_keys": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "recogs_set_fault": (C.c_int, [C.c_void_p, C.c_char_p]),
     "recogs_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "recogs_set_timed_stages": (C.c_int, [C.c_void_p, C.c_uint32]),
     "recogs_stage_times": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
@@ -471,6 +472,10 @@ class Context:
         self._check(self._L.recogs_depth_keys(self._h, keys.data_ptr(), max(n, 1),
                                               _stream_ptr(stream)))
         return keys[:n].view(torch.float32)
+
+    def set_fault(self, spec: str = ""):
+        """Fault injection: "alloc:N", "wait:N" (comma-separated) or "" to clear."""
+        self._check(self._L.recogs_set_fault(self._h, spec.encode()))
 
     def set_timing(self, enable: bool, stages=None):
         """Event timing of each stage (or only of the named stages)."""

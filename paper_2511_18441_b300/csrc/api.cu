@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -146,6 +147,9 @@ struct recogs_ctx {
     const uint2* last_ranges = nullptr;
     int64_t last_n = 0;
     const uint32_t* last_zkey = nullptr;
+    // fault injection (recogs_set_fault, or RECOGS_FAULT at creation)
+    int fault_wait_polls = 0;       // > 0: look-back waits poll a word nothing sets
+    int64_t fault_alloc_in = 0;     // > 0: the fault_alloc_in-th device allocation from now fails
     // timing and counts
     bool timing = false;
     uint32_t timed_stages = ~0u;   // bit per Stage
@@ -214,6 +218,8 @@ recogs_status ensure(recogs_ctx* ctx, DevBuf& b, size_t bytes) {
     }
     size_t want = bytes + bytes / 4;
     want = (want + 255) & ~(size_t)255;
+    if (ctx->fault_alloc_in > 0 && --ctx->fault_alloc_in == 0)
+        return fail(ctx, RECOGS_ENOMEM, "injected failure of a %zu-byte device allocation", want);
     cudaError_t e = cudaMalloc(&b.p, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -315,6 +321,14 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
 
     DevEdit de;
     CKS(checked(ctx, [&](ErrSink e) { return edit_to_dev(edit, cam, de, e); }));
+
+    // until this frame completes, there is no last render to inspect (a
+    // failure below may free buffers the previous frame's lists live in)
+    ctx->last_ranges = nullptr;
+    ctx->last_ids = nullptr;
+    ctx->last_zkey = nullptr;
+    ctx->last_pairs = 0;
+    ctx->last_n = 0;
 
     const int nb = (n + kPrepThreads - 1) / kPrepThreads;
     CKS(ensure(ctx, sc.counters, sizeof(DevCounters)));
@@ -509,7 +523,8 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
         sb.vals[0] = P<uint32_t>(sc.dvals[0]);
         sb.vals[1] = P<uint32_t>(sc.dvals[1]);
         sb.scratch = P<uint32_t>(sc.sort_scratch);
-        sb.error = &dctr->error;
+        sb.ctr = dctr;
+        sb.wait_polls = ctx->fault_wait_polls;
         const uint32_t span = zmax - zmin;
         const int dbits = span == 0 ? 0 : 32 - __builtin_clz(span);
         stage_begin(ctx, ST_SORT_DEPTH, st);
@@ -522,7 +537,7 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
         // the depth sort's spare key buffer holds the counts in depth order
         uint32_t* counts_sorted = sb.keys[dcur ^ 1];
         l = launch_pair_block_sums(sorted, P<uint32_t>(sc.count), (int)V, counts_sorted,
-                                   P<uint32_t>(sc.pair_sums), st);
+                                   P<uint32_t>(sc.pair_sums), dctr, st);
         l += launch_scan_small(P<uint32_t>(sc.pair_sums), P<uint32_t>(sc.pair_offsets), vb, 1,
                                nullptr, st);
         stage_end(ctx, ST_PAIR_OFFSETS, l, st);
@@ -530,7 +545,7 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
         stage_begin(ctx, ST_EMIT, st);
         l = launch_emit(sorted, counts_sorted, P<uint2>(sc.rect), (int)V,
                         P<uint32_t>(sc.pair_offsets), dc.tiles_x, P<uint32_t>(sc.tkeys[0]),
-                        P<uint32_t>(sc.tvals[0]), st);
+                        P<uint32_t>(sc.tvals[0]), dctr, st);
         stage_end(ctx, ST_EMIT, l, st);
 
         SortBuffers tb = sb;
@@ -580,12 +595,17 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
             V = ctx->h_counters->n_visible;
             Pn = ctx->h_counters->n_pairs;
             ctx->last_pairs = Pn;
-            const uint32_t err = ctx->h_counters->error;
-            if (err) {
-                CK(cudaMemsetAsync(&dctr->error, 0, sizeof(uint32_t), st));
-                return fail(ctx, (err & kErrTimeout) ? RECOGS_ETIMEOUT : RECOGS_ECAPACITY,
-                            "this frame overflowed the pair capacity or a tile's sort limit");
-            }
+        }
+        // with the read back a crowded tile only chose the global path
+        const uint32_t err = ctx->h_counters->error & (async ? ~0u : ~kErrCrowded);
+        if (err) {
+            CK(cudaMemsetAsync(&dctr->error, 0, sizeof(uint32_t), st));
+            if (err & kErrTimeout)
+                return fail(ctx, RECOGS_ETIMEOUT,
+                            "a bounded device wait of this frame's sort gave up; the frame was "
+                            "rejected (background image)");
+            return fail(ctx, RECOGS_ECAPACITY,
+                        "this frame overflowed the pair capacity or a tile's sort limit");
         }
         stats->n_visible = V;
         stats->n_pairs = Pn;
@@ -965,9 +985,10 @@ recogs_status refit(recogs_ctx* ctx, const recogs_scene& s, const recogs_camera&
     ex.loss = P<double>(ctx->rf_loss);
     const uint32_t* ids = ctx->last_ids;
     stage_begin(ctx, ST_BLEND_GRAD, st);
+    // the forward frame's counters: a skipped frame contributes no gradient
     int l = launch_blend(P<uint2>(ctx->main.ranges), P<uint32_t>(ctx->main.order), ids,
-                         P<float4>(ctx->main.rec), dc, bgv, image, nullptr, nullptr,
-                         sched.blend_batch, &ex, st);
+                         P<float4>(ctx->main.rec), dc, bgv, image, nullptr,
+                         P<DevCounters>(ctx->main.counters), sched.blend_batch, &ex, st);
     stage_end(ctx, ST_BLEND_GRAD, l, st);
     // 3. SH gradient and the optional Adam step
     RefitAdam ra = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -1028,6 +1049,56 @@ const char* recogs_status_string(recogs_status s) {
     return "RECOGS_UNKNOWN";
 }
 
+namespace {
+
+// A fault specification: empty (none) or comma-separated items "alloc:N"
+// (the N-th device allocation of the context from now fails, once) and
+// "wait:N" (every look-back wait of the global sort polls a word nothing
+// writes and gives up after N polls, until cleared). False if malformed.
+bool parse_fault(const char* spec, int& wait_polls, int64_t& alloc_in) {
+    wait_polls = 0;
+    alloc_in = 0;
+    if (!spec) return true;
+    const std::string s(spec);
+    size_t pos = 0;
+    while (pos <= s.size()) {
+        size_t end = s.find(',', pos);
+        if (end == std::string::npos) end = s.size();
+        const std::string item = s.substr(pos, end - pos);
+        pos = end + 1;
+        if (item.empty()) continue;
+        const size_t c = item.find(':');
+        if (c == std::string::npos) return false;
+        const std::string key = item.substr(0, c);
+        const char* v = item.c_str() + c + 1;
+        char* e = nullptr;
+        const long long x = strtoll(v, &e, 10);
+        if (!*v || *e || x < 1) return false;
+        if (key == "alloc") {
+            alloc_in = x;
+        } else if (key == "wait") {
+            if (x > (1 << 20)) return false;
+            wait_polls = (int)x;
+        } else {
+            return false;
+        }
+    }
+    return true;
+}
+
+}  // namespace
+
+recogs_status recogs_set_fault(recogs_ctx* ctx, const char* spec) {
+    if (!ctx) return RECOGS_EINVAL;
+    int w = 0;
+    int64_t a = 0;
+    if (!parse_fault(spec, w, a))
+        return fail(ctx, RECOGS_EINVAL, "bad fault specification '%s' (alloc:N, wait:N)", spec);
+    ctx->fault_wait_polls = w;
+    ctx->fault_alloc_in = a;
+    return RECOGS_OK;
+}
+
 recogs_status recogs_ctx_create(recogs_ctx** out, int device) {
     if (!out) return RECOGS_EINVAL;
     *out = nullptr;
@@ -1053,6 +1124,10 @@ recogs_status recogs_ctx_create(recogs_ctx** out, int device) {
                                                std::to_string(prop.major) + std::to_string(prop.minor));
     recogs_ctx* c = new recogs_ctx();
     c->device = device;
+    if (!parse_fault(getenv("RECOGS_FAULT"), c->fault_wait_polls, c->fault_alloc_in)) {
+        delete c;
+        return create_fail(RECOGS_EINVAL, "RECOGS_FAULT is not a fault specification");
+    }
     DeviceGuard g(device);
     if (cudaMallocHost(&c->h_counters, sizeof(DevCounters)) != cudaSuccess) {
         cudaGetLastError();
@@ -1609,7 +1684,7 @@ recogs_status recogs_mlp_labels(recogs_ctx* ctx, const recogs_scene* scene,
     stage_begin(ctx, ST_MLP, st);
     int l = launch_blend(P<uint2>(ctx->main.ranges), P<uint32_t>(ctx->main.order), ctx->last_ids,
                          P<float4>(ctx->main.rec), dc, bg0, P<float>(ctx->rf_img), nullptr,
-                         nullptr, sched.blend_batch, &ex, st);
+                         P<DevCounters>(ctx->main.counters), sched.blend_batch, &ex, st);
     l += launch_mlp_labels(*scene, dc, dr, P<float>(ctx->rf_grad), labels_out, st);
     stage_end(ctx, ST_MLP, l, st);
     CK(cudaGetLastError());

@@ -457,11 +457,13 @@ int launch_blend(const uint2* ranges, const uint32_t* order, const uint32_t* ids
                  DevCounters* counters, int batch, const BlendExtra* extra, cudaStream_t st) {
     BlendExtra ex;
     if (extra) ex = *extra;
+    // every mode honours the frame's skip flag (a frame whose pairs overflowed
+    // or whose sort gave up has no valid lists)
     if (ex.grad_rgb && ex.cover)
-        blend_launch<kBlendCover>(batch, ranges, order, ids, rec, cam, bg, image, final_T, nullptr,
+        blend_launch<kBlendCover>(batch, ranges, order, ids, rec, cam, bg, image, final_T, counters,
                                   ex, st);
     else if (ex.grad_rgb)
-        blend_launch<kBlendGrad>(batch, ranges, order, ids, rec, cam, bg, image, final_T, nullptr,
+        blend_launch<kBlendGrad>(batch, ranges, order, ids, rec, cam, bg, image, final_T, counters,
                                  ex, st);
     else if (ex.depth)
         blend_launch<kBlendDepth>(batch, ranges, order, ids, rec, cam, bg, image, final_T,

@@ -208,7 +208,7 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
         sb.vals[0] = U32(oDvals0);
         sb.vals[1] = U32(oDvals1);
         sb.scratch = U32(oSortScratch);
-        sb.error = &dctr->error;
+        sb.ctr = dctr;
         const uint32_t span = hc.zmax - ~hc.zmin_inv;
         const int dbits = span == 0 ? 0 : 32 - __builtin_clz(span);
         int l = 0;
@@ -216,10 +216,11 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
         const uint32_t* sorted = sb.vals[dcur];
         const int vb = ((int)V + kEmitBlock - 1) / kEmitBlock;
         uint32_t* counts_sorted = sb.keys[dcur ^ 1];
-        launch_pair_block_sums(sorted, U32(oCount), (int)V, counts_sorted, U32(oPairSums), st);
+        launch_pair_block_sums(sorted, U32(oCount), (int)V, counts_sorted, U32(oPairSums), dctr,
+                               st);
         launch_scan_small(U32(oPairSums), U32(oPairOffsets), vb, 1, nullptr, st);
         launch_emit(sorted, counts_sorted, reinterpret_cast<const uint2*>(base + oRect), (int)V,
-                    U32(oPairOffsets), dc.tiles_x, U32(oTkeys0), U32(oTvals0), st);
+                    U32(oPairOffsets), dc.tiles_x, U32(oTkeys0), U32(oTvals0), dctr, st);
         SortBuffers tb = sb;
         tb.keys[0] = U32(oTkeys0);
         tb.keys[1] = U32(oTkeys1);

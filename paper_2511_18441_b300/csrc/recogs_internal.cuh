@@ -314,7 +314,9 @@ int launch_compact(const uint32_t* count, const uint32_t* zkey, int n, const uin
 struct SortBuffers {
     uint32_t *keys[2], *vals[2];
     uint32_t* scratch;     // sort_scratch_words(max items) words, cleared by each sort
-    uint32_t* error;       // set non-zero if a look-back wait gave up
+    DevCounters* ctr;      // a look-back wait that gives up sets kErrTimeout in error and skip
+    int wait_polls = 0;    // > 0 (fault injection): every wait polls a word nothing sets and
+                           // gives up after this many polls
 };
 // Scratch words a sort of up to max_items pairs needs.
 size_t sort_scratch_words(int max_items);
@@ -326,10 +328,11 @@ int radix_sort_pairs(SortBuffers& b, int n, int bits, cudaStream_t st, int* laun
 // counts_sorted[j] = tile count of sorted Gaussian j, sums[b] = block totals;
 // after an exclusive scan of sums into block_offsets, emit writes the pairs.
 int launch_pair_block_sums(const uint32_t* sorted_ids, const uint32_t* count, int v,
-                           uint32_t* counts_sorted, uint32_t* sums, cudaStream_t st);
+                           uint32_t* counts_sorted, uint32_t* sums, const DevCounters* counters,
+                           cudaStream_t st);
 int launch_emit(const uint32_t* sorted_ids, const uint32_t* counts_sorted, const uint2* rect, int v,
                 const uint32_t* block_offsets, int tiles_x, uint32_t* tile_keys, uint32_t* vals,
-                cudaStream_t st);
+                const DevCounters* counters, cudaStream_t st);
 // Tile binning (bin.cu). tile_totals: per tile, the total and each
 // partition's exclusive offset (into cursor); tile_scan: ranges, the tile
 // order, the pair total, the largest tile and the tile count of every sort

@@ -115,9 +115,13 @@ int launch_compact(const uint32_t* count, const uint32_t* zkey, int n, const uin
 // back over its predecessors' published words until it meets a P. Tiles are
 // numbered in the order their CTAs start (an atomic counter), so every
 // predecessor a CTA waits on is already running and publishes its count
-// without waiting itself. Each wait is bounded: after kSpinLimit polls the
-// CTA records an error for the host and carries on (the host reports
-// RECOGS_ETIMEOUT); no wait can hang the GPU.
+// without waiting itself. Each wait is bounded: after spin_limit polls
+// (kSpinLimit unless a test injects a short limit) the CTA records an error
+// for the host (RECOGS_ETIMEOUT) and marks the frame skipped; every later
+// kernel of the frame then does nothing (a pass that starts on a skipped
+// frame publishes its look-back words at once, so nothing waits on it, and
+// writes nothing), and the blend writes the background: a wait that gives up
+// can only produce a rejected frame, never a hang or a stray access.
 
 constexpr int kOsThreads = 256;
 constexpr int kOsItems = 8;
@@ -158,7 +162,8 @@ __global__ void __launch_bounds__(kOsThreads)
     os_pass(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
             uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int n, int shift,
             const uint32_t* __restrict__ hist, uint32_t* __restrict__ status,
-            uint32_t* __restrict__ tile_counter, uint32_t* __restrict__ error) {
+            uint32_t* __restrict__ tile_counter, DevCounters* __restrict__ ctr,
+            uint32_t spin_limit, const uint32_t* __restrict__ never_set) {
     constexpr int W = kOsThreads / 32;
     constexpr int PER_WARP = kOsTile / W;         // 256 consecutive pairs per warp
     __shared__ uint32_t s_keys[kOsTile];
@@ -167,15 +172,23 @@ __global__ void __launch_bounds__(kOsThreads)
     __shared__ uint32_t s_bstart[kRadix];         // block-local start of each digit
     __shared__ uint32_t s_gbase[kRadix];          // global start of each digit for this tile
     __shared__ uint32_t s_warp[33];
-    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_tile, s_dead;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int d = threadIdx.x;                    // kOsThreads == kRadix: one digit per thread
-    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
+    if (threadIdx.x == 0) {
+        s_tile = atomicAdd(tile_counter, 1u);
+        s_dead = ld_relaxed(&ctr->skip);
+    }
 #pragma unroll
     for (int w = 0; w < W; ++w) s_wcnt[w][d] = 0;
     __syncthreads();
     const uint32_t t = s_tile;
+    if (s_dead) {
+        // the frame is skipped: publish at once so that no later tile waits
+        st_relaxed(status + (size_t)t * kRadix + d, kFlagP);
+        return;
+    }
     const int base = (int)t * kOsTile;
     const int nblk = min(kOsTile, n - base);
 
@@ -225,11 +238,14 @@ __global__ void __launch_bounds__(kOsThreads)
         int j = (int)t - 1;
         uint32_t spins = 0;
         while (true) {
-            const uint32_t v = ld_relaxed(status + (size_t)j * kRadix + d);
+            // never_set (fault injection): a word nothing writes, so the wait
+            // runs out
+            const uint32_t v = ld_relaxed(never_set ? never_set : status + (size_t)j * kRadix + d);
             const uint32_t f = v & ~kValueMask;
             if (f == 0u) {
-                if (++spins > kSpinLimit) {
-                    atomicOr(error, kErrTimeout);
+                if (++spins > spin_limit) {
+                    atomicOr(&ctr->error, kErrTimeout);
+                    st_relaxed(&ctr->skip, 1u);
                     break;
                 }
                 continue;
@@ -281,12 +297,16 @@ int radix_sort_pairs(SortBuffers& b, int n, int bits, cudaStream_t st, int* laun
     cudaMemsetAsync(b.scratch, 0, words * sizeof(uint32_t), st);
     const int hb = min((n + kOsThreads - 1) / kOsThreads, 148 * 4);
     os_histogram<<<hb, kOsThreads, 0, st>>>(b.keys[0], n, passes, hist);
+    // the last counter word is zeroed above and never written: the word an
+    // injected wait polls
+    const uint32_t* never_set = b.wait_polls > 0 ? counters + (kCounterWords - 1) : nullptr;
+    const uint32_t limit = b.wait_polls > 0 ? (uint32_t)b.wait_polls : kSpinLimit;
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
         os_pass<<<tiles, kOsThreads, 0, st>>>(b.keys[cur], b.vals[cur], b.keys[cur ^ 1],
                                               b.vals[cur ^ 1], n, kRadixBits * p, hist + p * kRadix,
                                               status + (size_t)p * tiles * kRadix, counters + p,
-                                              b.error);
+                                              b.ctr, limit, never_set);
         cur ^= 1;
     }
     *launches += 1 + passes;
@@ -299,10 +319,14 @@ int radix_sort_pairs(SortBuffers& b, int n, int bits, cudaStream_t st, int* laun
 // counts_sorted[j] = tile count of the j-th Gaussian in depth order; per-block totals.
 __global__ void __launch_bounds__(kEmitBlock)
     pair_block_sums(const uint32_t* __restrict__ ids, const uint32_t* __restrict__ count, int v,
-                    uint32_t* __restrict__ counts_sorted, uint32_t* __restrict__ sums) {
+                    uint32_t* __restrict__ counts_sorted, uint32_t* __restrict__ sums,
+                    const DevCounters* __restrict__ ctr) {
     __shared__ uint32_t s_warp[33];
     const int j = blockIdx.x * kEmitBlock + threadIdx.x;
-    const uint32_t c = j < v ? __ldg(count + __ldg(ids + j)) : 0u;
+    // a skipped frame (its depth sort gave up) expands no pairs: its sorted
+    // indices are not to be trusted
+    const bool live = ld_relaxed(&ctr->skip) == 0u;
+    const uint32_t c = (live && j < v) ? __ldg(count + __ldg(ids + j)) : 0u;
     if (j < v) counts_sorted[j] = c;
     uint32_t tot;
     block_exclusive_scan<kEmitBlock>(c, s_warp, &tot);
@@ -310,21 +334,24 @@ __global__ void __launch_bounds__(kEmitBlock)
 }
 
 int launch_pair_block_sums(const uint32_t* sorted_ids, const uint32_t* count, int v,
-                           uint32_t* counts_sorted, uint32_t* sums, cudaStream_t st) {
+                           uint32_t* counts_sorted, uint32_t* sums, const DevCounters* counters,
+                           cudaStream_t st) {
     pair_block_sums<<<(v + kEmitBlock - 1) / kEmitBlock, kEmitBlock, 0, st>>>(
-        sorted_ids, count, v, counts_sorted, sums);
+        sorted_ids, count, v, counts_sorted, sums, counters);
     return 1;
 }
 
 __global__ void __launch_bounds__(kEmitBlock)
     emit_kernel(const uint32_t* __restrict__ ids, const uint32_t* __restrict__ counts_sorted,
                 const uint2* __restrict__ rect, int v, const uint32_t* __restrict__ block_offsets,
-                int tiles_x, uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ vals) {
+                int tiles_x, uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ vals,
+                const DevCounters* __restrict__ ctr) {
     __shared__ uint32_t s_warp[33];
     const int j = blockIdx.x * kEmitBlock + threadIdx.x;
-    const uint32_t c = j < v ? counts_sorted[j] : 0u;
+    const bool live = ld_relaxed(&ctr->skip) == 0u;
+    const uint32_t c = (live && j < v) ? counts_sorted[j] : 0u;
     uint32_t o = block_offsets[blockIdx.x] + block_exclusive_scan<kEmitBlock>(c, s_warp, nullptr);
-    if (j >= v) return;
+    if (!live || j >= v) return;
     const uint32_t id = __ldg(ids + j);
     const uint2 r = __ldg(rect + id);
     const uint32_t x0 = r.x & 0xffffu, x1 = r.x >> 16, y0 = r.y & 0xffffu, y1 = r.y >> 16;
@@ -338,9 +365,9 @@ __global__ void __launch_bounds__(kEmitBlock)
 
 int launch_emit(const uint32_t* sorted_ids, const uint32_t* counts_sorted, const uint2* rect, int v,
                 const uint32_t* block_offsets, int tiles_x, uint32_t* tile_keys, uint32_t* vals,
-                cudaStream_t st) {
+                const DevCounters* counters, cudaStream_t st) {
     emit_kernel<<<(v + kEmitBlock - 1) / kEmitBlock, kEmitBlock, 0, st>>>(
-        sorted_ids, counts_sorted, rect, v, block_offsets, tiles_x, tile_keys, vals);
+        sorted_ids, counts_sorted, rect, v, block_offsets, tiles_x, tile_keys, vals, counters);
     return 1;
 }
 
