@@ -112,33 +112,59 @@ def aggregate_value(steps: int, world: int, max_ms: float) -> float:
 # clocks during the timed region
 
 class ClockSampler:
-    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
-              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
-              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+    """SM clock, power and clock-event reasons of the bench's GPU, sampled by
+    NVML every 50 ms on a thread while the bench runs (read-only queries)."""
 
-    def __init__(self, gpu_id):
-        self.gpu_id = gpu_id
-        self.proc = None
-        self.lines = []
+    # NVML clock-event reason bits
+    REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+               "hw_thermal_slowdown": 0x40}
+
+    def __init__(self, device):
+        self.device = device
+        self.samples = []
         self.t0 = self.t1 = None
+        self.error = None
+        self._stop = threading.Event()
+        self.th = None
+
+    def _handle(self, nv):
+        import torch
+        props = torch.cuda.get_device_properties(self.device)
+        bus = getattr(props, "pci_bus_id", None)
+        dom = getattr(props, "pci_domain_id", None)
+        dev = getattr(props, "pci_device_id", None)
+        if bus is not None and dom is not None and dev is not None:
+            try:
+                return nv.nvmlDeviceGetHandleByPciBusId(f"{dom:08x}:{bus:02x}:{dev:02x}.0")
+            except nv.NVMLError:
+                pass
+        if nv.nvmlDeviceGetCount() == 1:
+            return nv.nvmlDeviceGetHandleByIndex(0)
+        return nv.nvmlDeviceGetHandleByIndex(int(self.device))
 
     def start(self):
-        # no -i: inside a container the visible GPU may carry another index
-        # than CUDA_VISIBLE_DEVICES names; rows are filtered in stop()
-        cmd = ["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}", "--format=csv,noheader,nounits",
-               "-lms", "100"]
         try:
-            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
-                                         text=True)
-        except OSError:
-            self.proc = None
+            import pynvml as nv
+            nv.nvmlInit()
+            h = self._handle(nv)
+            self.max_mhz = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+        except Exception as e:   # no NVML: report why instead of clocks
+            self.error = f"{type(e).__name__}: {e}"
             return
-        self.th = threading.Thread(target=self._read, daemon=True)
-        self.th.start()
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append((time.time(), line.strip()))
+        def run():
+            while not self._stop.is_set():
+                try:
+                    self.samples.append((time.time(), nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM),
+                                         nv.nvmlDeviceGetPowerUsage(h) / 1000.0,
+                                         nv.nvmlDeviceGetCurrentClocksEventReasons(h)))
+                except Exception as e:
+                    self.error = f"{type(e).__name__}: {e}"
+                    return
+                self._stop.wait(0.05)
+
+        self.th = threading.Thread(target=run, daemon=True)
+        self.th.start()
 
     def mark_begin(self):
         self.t0 = time.time()
@@ -147,57 +173,20 @@ class ClockSampler:
         self.t1 = time.time()
 
     def stop(self):
-        if self.proc is None:
-            return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        self.th.join(timeout=5)
-        rows = []
-        for ts, line in self.lines:
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) != len(self.FIELDS):
-                continue
-            rows.append((ts, parts))
-        if not rows:
-            err = ""
-            try:
-                err = (self.proc.stderr.read() or "").strip()
-            except (OSError, ValueError):
-                pass
-            first = self.lines[0][1] if self.lines else ""
-            return {"unavailable": (err or first or "nvidia-smi printed nothing")[:300],
-                    "lines_read": len(self.lines)}
-        gpus = sorted({r[0] for _, r in rows})
-        if len(gpus) > 1:
-            want = str(self.gpu_id) if str(self.gpu_id) in gpus else gpus[0]
-            rows = [(ts, r) for ts, r in rows if r[0] == want]
-        inside = [r for ts, r in rows if self.t0 is not None and self.t0 - 0.15 <= ts <= self.t1 + 0.15]
-        use = inside or [r for _, r in rows]
-
-        def num(x):
-            try:
-                return float(x)
-            except ValueError:
-                return float("nan")
-
-        sm = [num(r[1]) for r in use]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in use for k in range(4) if r[5 + k].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(num(r[2]) for r in use),
-                "reasons": reasons, "samples": len(use),
-                "power_w_max": max(num(r[3]) for r in use)}
-
-
-def gpu_id_for_smi(local_rank):
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-    if vis:
-        ids = [v.strip() for v in vis.split(",") if v.strip()]
-        if local_rank < len(ids):
-            return ids[local_rank]
-    return local_rank
+        self._stop.set()
+        if self.th is not None:
+            self.th.join(timeout=5)
+        if not self.samples:
+            return {"unavailable": self.error or "no NVML samples"}
+        # samples within 0.2 s of the timed region (the region itself may be
+        # shorter than the sampling period), else all of them
+        near = [s for s in self.samples
+                if self.t0 is not None and self.t0 - 0.2 <= s[0] <= self.t1 + 0.2]
+        use = near or self.samples
+        reasons = sorted({k for s in use for k, bit in self.REASONS.items() if s[3] & bit})
+        return {"sm_mhz": statistics.median(s[1] for s in use), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(use), "power_w_max": max(s[2] for s in use),
+                "source": "NVML, 50 ms period, samples within 0.2 s of the timed region"}
 
 
 # ---------------------------------------------------------------------------
@@ -357,7 +346,7 @@ def run_ours(args, rank, world, local):
     def frame():
         ctx.render(ds, w.camera, w.edit, image_out=img, stream=stream)
 
-    sampler = ClockSampler(gpu_id_for_smi(local))
+    sampler = ClockSampler(local)
     sampler.start()
     for _ in range(args.warmup):
         frame()
@@ -609,7 +598,7 @@ def run_batch(args, rank, world, local):
         barrier(world)
         return e0.elapsed_time(e1)
 
-    sampler = ClockSampler(gpu_id_for_smi(local))
+    sampler = ClockSampler(local)
     sampler.start()
     steps = args.steps
     sampler.mark_begin()
@@ -776,7 +765,7 @@ def run_refit(args, rank, world, local):
     breakdown = stage_breakdown(refit_step, k_breakdown)
     dom = max(breakdown, key=lambda s: breakdown[s][0])
 
-    sampler = ClockSampler(gpu_id_for_smi(local))
+    sampler = ClockSampler(local)
     sampler.start()
     torch.cuda.synchronize(dev)
     barrier(world)

@@ -150,6 +150,51 @@ __device__ __forceinline__ void grid_dependents_launch() {
 }
 
 // --------------------------------------------------------------------------
+// Shared-memory mbarriers (PTX mbarrier.*): a producer/consumer hand-off
+// inside a CTA without block-wide barriers. Every wait is bounded: each poll
+// may suspend the thread for at most kMbarPollNs (the suspend-time hint) and
+// after kMbarSpinLimit unsuccessful polls (~70 ms) the wait returns false
+// (the caller records an error and abandons its work), so no wait can hang
+// the GPU. A legitimate wait lasts microseconds.
+
+constexpr uint32_t kMbarSpinLimit = 1u << 16;
+constexpr uint32_t kMbarPollNs = 1024;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+// Arrive (release: this thread's earlier shared-memory accesses are ordered
+// before the phase completes).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+
+// Wait (acquire) until the phase of the given parity has completed; false if
+// the bounded wait gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_addr(bar);
+    for (uint32_t i = 0; i < kMbarSpinLimit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity), "r"(kMbarPollNs)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// --------------------------------------------------------------------------
 // Per-device launch set-up. cudaFuncSetAttribute and the SM count are per
 // device, and one process may drive several devices (a context each), so the
 // one-time work is remembered per device ordinal (bit d of a mask; devices

@@ -78,7 +78,9 @@ def test_a_timed_out_refit_frame_contributes_no_gradient(lib):
     assert e.value.status == lib.ETIMEOUT
     ctx.set_fault("")
     again = ctx.refit_grad(ds, w.camera, target)
-    assert np.array_equal(parity.to_np(again["grad_rgb"]), g0)
+    # the gradient is summed with float atomics: equal up to summation order
+    np.testing.assert_allclose(parity.to_np(again["grad_rgb"]), g0, rtol=1e-4,
+                               atol=1e-6 * np.abs(g0).max())
     ctx.close()
 
 
