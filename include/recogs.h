@@ -346,10 +346,15 @@ RECOGS_API recogs_status recogs_mlp_train_step(recogs_mlp* mlp, const uint16_t* 
  * decision: p = sigmoid(logit); where |p - 1/2| < delta, and outside the
  * learned domain, the plain test decides, with its bit as the weight;
  * elsewhere the bit is p > 1/2 and the weights are the sigmoid of the
- * coverage logits.
+ * coverage logits. One kernel computes all three per tile of 128 Gaussians
+ * (the network's products on the tcgen05 tensor cores); the features never
+ * reach device memory.
  * mask_out: device, ceil(n/32) words of selection bits; weights_out: device
  * [n][3] float32 per-channel tint weights for recogs_recolor_weighted;
- * fallbacks_out (host, may be NULL; waits) = Gaussians that fell back. */
+ * fallbacks_out (host, may be NULL; waits) = Gaussians that fell back. With
+ * fallbacks_out, a bounded wait for the tensor cores that gave up (in this
+ * call or an earlier one without fallbacks_out) is reported as
+ * RECOGS_ETIMEOUT. */
 RECOGS_API recogs_status recogs_mlp_select(recogs_mlp* mlp, const recogs_scene* scene,
                                            const recogs_camera* select_camera,
                                            const recogs_region* region, float delta,

@@ -229,6 +229,47 @@ def forward(theta, X, rnd=True):
     return dict(x=x, z1=z1, h1=h1, z2=z2, h2=h2, o=o)
 
 
+# A float32 implementation that rounds at the same points (bf16 features,
+# weights and activations) differs from forward() only through (1) the
+# accumulation of each product in float32, in any order (the error of a sum
+# of m terms is at most gamma_m times the sum of their magnitudes, gamma_m =
+# m u / (1 - m u); u = 2^-22 allows for additions that truncate), (2) its
+# GELU approximation (GELU_ERR absolute plus a few float32 roundings) and (3)
+# the bf16 rounding of each activation, which can go to the other neighbour
+# when the value's uncertainty interval contains a rounding midpoint.
+ACC_U = 2.0 ** -22
+GELU_ERR = 4.1e-7
+GELU_SLOPE = 1.13        # max |GELU'(z)| = 1.1289...
+
+
+def _gamma(m):
+    return m * ACC_U / (1.0 - m * ACC_U)
+
+
+def _bf16_spread(v, d):
+    """Largest distance between bf16(v) and the bf16 rounding of any value
+    within d of v (0 where no rounding midpoint lies within d)."""
+    h = bf16(v)
+    d = d + 2.0 ** -24 * np.abs(v)       # the float32 step before the bf16 rounding
+    return np.maximum(np.abs(bf16(v - d) - h), np.abs(bf16(v + d) - h))
+
+
+def forward_bound(theta, X):
+    """Per output element, a bound on |o - forward(theta, X)["o"]| for any
+    float32 implementation that rounds at forward's points (see above).
+    Returns (forward dict, bound [n, 4])."""
+    P = unpack(theta)
+    f = forward(theta, X)
+    W1, W2, W3 = bf16(P["W1"]), bf16(P["W2"]), bf16(P["W3"])
+    g = _gamma(K + 1)
+    e1 = g * (np.abs(f["x"]) @ np.abs(W1) + np.abs(P["b1"]))
+    dh1 = _bf16_spread(gelu(f["z1"]), GELU_SLOPE * e1 + GELU_ERR + 4 * 2.0 ** -24 * np.abs(f["z1"]))
+    e2 = dh1 @ np.abs(W2) + g * ((np.abs(f["h1"]) + dh1) @ np.abs(W2) + np.abs(P["b2"]))
+    dh2 = _bf16_spread(gelu(f["z2"]), GELU_SLOPE * e2 + GELU_ERR + 4 * 2.0 ** -24 * np.abs(f["z2"]))
+    e3 = dh2 @ np.abs(W3) + g * ((np.abs(f["h2"]) + dh2) @ np.abs(W3) + np.abs(P["b3"]))
+    return f, e3
+
+
 def loss_grad(theta, X, sel, cov, rnd=True, batch=None):
     """Mean loss over the batch and its gradient (parameter-vector layout).
     batch: the batch size the sums are divided by (default len(X); larger

@@ -1541,8 +1541,7 @@ struct recogs_mlp {
     float* grad = nullptr;
     float* loss = nullptr;       // device scalar
     MlpFrags* frags = nullptr;
-    unsigned long long* fallbacks = nullptr;
-    DevBuf feat, out;
+    unsigned long long* fallbacks = nullptr;   // [0] fallback count, [1] fused kernel's error word
     int64_t step = 0;
 };
 
@@ -1591,7 +1590,9 @@ recogs_status recogs_mlp_create(recogs_ctx* ctx, const float* params_host, recog
     if (e == cudaSuccess) e = cudaMalloc(&m->grad, pb);
     if (e == cudaSuccess) e = cudaMalloc(&m->loss, sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&m->frags, mlp_frags_bytes());
-    if (e == cudaSuccess) e = cudaMalloc(&m->fallbacks, sizeof(unsigned long long));
+    // fallbacks[0]: the count; fallbacks[1]: the fused kernel's error word
+    if (e == cudaSuccess) e = cudaMalloc(&m->fallbacks, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(m->fallbacks, 0, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemcpy(m->params, params_host, pb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(m->m, 0, pb);
     if (e == cudaSuccess) e = cudaMemset(m->v, 0, pb);
@@ -1613,8 +1614,7 @@ void recogs_mlp_destroy(recogs_mlp* m) {
     if (!m) return;
     DeviceGuard g(m->ctx->device);
     cudaDeviceSynchronize();
-    void* ps[] = {m->params, m->m, m->v, m->grad, m->loss, m->frags, m->fallbacks, m->feat.p,
-                  m->out.p};
+    void* ps[] = {m->params, m->m, m->v, m->grad, m->loss, m->frags, m->fallbacks};
     for (void* p : ps)
         if (p) cudaFree(p);
     delete m;
@@ -1786,22 +1786,26 @@ recogs_status recogs_mlp_select(recogs_mlp* m, const recogs_scene* scene,
         return fail(ctx, RECOGS_EINVAL, "mask_out or weights_out NULL or misaligned");
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
-    CKS(ensure(ctx, m->feat, 128 * (size_t)(n > 0 ? n : 1)));
-    CKS(ensure(ctx, m->out, 16 * (size_t)(n > 0 ? n : 1)));
+    // the count of this call (the error word is cleared where it is reported)
     CK(cudaMemsetAsync(m->fallbacks, 0, sizeof(unsigned long long), st));
     const DevCamera dc = dev_camera(*select_camera);
     stage_begin(ctx, ST_MLP, st);
-    int l = launch_mlp_features(*scene, dc, dr, fr, P<uint32_t>(m->feat), nullptr, st);
-    l += launch_mlp_forward(P<uint32_t>(m->feat), n, m->frags, P<float>(m->out), st);
-    l += launch_mlp_decide(*scene, dc, dr, P<float>(m->out), delta, mask_out, weights_out,
-                           m->fallbacks, st);
+    // features, network (tcgen05) and decisions in one kernel
+    int l = launch_mlp_select_fused(*scene, dc, dr, fr, m->frags, delta, mask_out, weights_out,
+                                    m->fallbacks, reinterpret_cast<uint32_t*>(m->fallbacks + 1),
+                                    st);
     stage_end(ctx, ST_MLP, l, st);
     CK(cudaGetLastError());
     if (fallbacks_out) {
-        unsigned long long fb = 0;
-        CK(cudaMemcpyAsync(&fb, m->fallbacks, sizeof(fb), cudaMemcpyDeviceToHost, st));
+        unsigned long long fb[2] = {0, 0};
+        CK(cudaMemcpyAsync(fb, m->fallbacks, sizeof(fb), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        *fallbacks_out = (int64_t)fb;
+        *fallbacks_out = (int64_t)fb[0];
+        if (fb[1]) {
+            CK(cudaMemsetAsync(m->fallbacks + 1, 0, sizeof(unsigned long long), st));
+            return fail(ctx, RECOGS_ETIMEOUT,
+                        "a bounded wait for the tensor cores gave up; the selection is invalid");
+        }
     }
     return RECOGS_OK;
 }

@@ -481,8 +481,11 @@ __device__ __forceinline__ bool sel_view(const DevCamera& cam, const float* xyz,
     float tx, ty;
     view_point(cam, xyz[i], xyz[n + i], xyz[2 * n + i], tx, ty, tz);
     if (!(tz > cam.z_near)) return false;
-    u = __fmaf_rn(cam.fx, __fdiv_rn(tx, tz), cam.cx);
-    v = __fmaf_rn(cam.fy, __fdiv_rn(ty, tz), cam.cy);
+    // the features are rounded to bf16 (2^-9 relative): an approximate
+    // reciprocal (2^-23) is far inside that
+    const float iz = rcp_approx(tz);
+    u = __fmaf_rn(cam.fx, tx * iz, cam.cx);
+    v = __fmaf_rn(cam.fy, ty * iz, cam.cy);
     return true;
 }
 
@@ -499,8 +502,8 @@ __device__ __forceinline__ void sel_cov2d(const DevCamera& cam, const float* xyz
     const float R[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
                         2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
                         2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
-    const float sc[3] = {expf(lsc[i]), expf(lsc[n + i]), expf(lsc[2 * n + i])};
-    const float iz = 1.0f / tz;
+    const float sc[3] = {__expf(lsc[i]), __expf(lsc[n + i]), __expf(lsc[2 * n + i])};
+    const float iz = rcp_approx(tz);
     const float rx = fminf(fmaxf(tx * iz, -cam.limx), cam.limx);
     const float ry = fminf(fmaxf(ty * iz, -cam.limy), cam.limy);
     const float j00 = cam.fx * iz, j02 = -cam.fx * rx * iz;
@@ -534,14 +537,76 @@ __device__ __forceinline__ void radial(const DevRegion& r, const MlpRegionFrame&
         const float ex = r.xy[2 * i] - r.xy[2 * j], ey = r.xy[2 * i + 1] - r.xy[2 * j + 1];
         const float den = qx * ey - qy * ex;
         if (den == 0.f) continue;
-        const float l = (ax * ey - ay * ex) / den;
-        const float sp = (ax * qy - ay * qx) / den;
+        const float id = rcp_approx(den);
+        const float l = (ax * ey - ay * ex) * id;
+        const float sp = (ax * qy - ay * qx) * id;
         if (l > 0.f && sp >= 0.f && sp <= 1.f && l < lam) lam = l;
     }
     const float qn = sqrtf(qx * qx + qy * qy);
     rho = (lam < INFINITY && qn > 0.f) ? lam * qn : fr.mean_r;
-    un = qx / rho;
-    vn = qy / rho;
+    const float ir = rcp_approx(rho);
+    un = qx * ir;
+    vn = qy * ir;
+}
+
+// The 64 features of Gaussian i (float32, before the bf16 rounding); returns
+// false when t_z <= z_near in the selection view (outside the learned
+// domain, geometry features 0). Shared by the feature kernel (training) and
+// the fused selection kernel (inference), so both see the same values.
+__device__ __forceinline__ bool mlp_feature_row(int n, int i, const float* __restrict__ xyz,
+                                                const float* __restrict__ lsc,
+                                                const float* __restrict__ quat,
+                                                const float* __restrict__ opl,
+                                                const float* __restrict__ sh, int sh_dtype,
+                                                const DevCamera& cam, const DevRegion& reg,
+                                                const MlpRegionFrame& fr, float (&f)[64]) {
+    // the 48 SH coefficients first: their loads are in flight while the
+    // geometry below is computed
+#pragma unroll
+    for (int k = 0; k < 48; ++k) {
+        const size_t o = (size_t)k * n + i;
+        f[11 + k] = sh_dtype == RECOGS_F32   ? __ldg(sh + o)
+                    : sh_dtype == RECOGS_F16 ? __half2float(reinterpret_cast<const __half*>(sh)[o])
+                                             : __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(sh)[o]);
+    }
+    float u = 0.f, v = 0.f, tz = 0.f;
+    const bool ok = sel_view(cam, xyz, n, i, u, v, tz);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) f[k] = 0.f;
+    if (ok) {
+        float un, vn, rho;
+        radial(reg, fr, u, v, un, vn, rho);
+        float a, b, c;
+        sel_cov2d(cam, xyz, lsc, quat, n, i, a, b, c);
+        // unit radial direction (the +x axis at the centroid itself)
+        const float qx = u - fr.cx, qy = v - fr.cy;
+        const float qn = sqrtf(qx * qx + qy * qy);
+        const float iq = qn > 0.f ? rcp_approx(qn) : 0.f;
+        const float ux = qn > 0.f ? qx * iq : 1.f, uy = qn > 0.f ? qy * iq : 0.f;
+        const float mid = 0.5f * (a + c);
+        const float rad = sqrtf(0.25f * (a - c) * (a - c) + b * b);
+        const float irad = rad > 0.f ? rcp_approx(rad) : 0.f;
+        const float c2p = rad > 0.f ? 0.5f * (a - c) * irad : 1.f;
+        const float s2p = rad > 0.f ? b * irad : 0.f;
+        const float c2q = ux * ux - uy * uy, s2q = 2.f * ux * uy;
+        const float sr = sqrtf(a * ux * ux + 2.f * b * ux * uy + c * uy * uy);
+        // logarithms to ~1e-6 absolute (MUFU lg2), far inside the bf16 rounding
+        const float lr = __logf(rho);
+        f[0] = un;
+        f[1] = vn;
+        f[2] = __logf(tz * rho * rcp_approx(cam.fx));
+        f[3] = 0.5f * __logf(mid + rad) - lr;
+        f[4] = 0.5f * __logf(mid - rad) - lr;
+        f[5] = __logf(sr) - lr;
+        f[6] = c2p * c2q + s2p * s2q;
+        f[7] = s2p * c2q - c2p * s2q;
+        f[8] = fminf(fmaxf((rho - qn) * rcp_approx(sr), -8.f), 8.f);
+    }
+    f[9] = (lsc[i] + lsc[n + i] + lsc[2 * n + i]) * (1.0f / 3.0f);
+    f[10] = opl[i];
+#pragma unroll
+    for (int k = 59; k < 64; ++k) f[k] = 0.f;
+    return ok;
 }
 
 // one thread per Gaussian: the 64 features (bf16); valid = t_z > z_near of
@@ -553,48 +618,8 @@ __global__ void __launch_bounds__(256)
                         MlpRegionFrame fr, uint32_t* __restrict__ X, uint8_t* __restrict__ valid) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float u = 0.f, v = 0.f, tz = 0.f;
-    const bool ok = sel_view(cam, xyz, n, i, u, v, tz);
     float f[64];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) f[k] = 0.f;
-    if (ok) {
-        float un, vn, rho;
-        radial(reg, fr, u, v, un, vn, rho);
-        float a, b, c;
-        sel_cov2d(cam, xyz, lsc, quat, n, i, a, b, c);
-        // unit radial direction (the +x axis at the centroid itself)
-        const float qx = u - fr.cx, qy = v - fr.cy;
-        const float qn = sqrtf(qx * qx + qy * qy);
-        const float ux = qn > 0.f ? qx / qn : 1.f, uy = qn > 0.f ? qy / qn : 0.f;
-        const float mid = 0.5f * (a + c);
-        const float rad = sqrtf(0.25f * (a - c) * (a - c) + b * b);
-        const float c2p = rad > 0.f ? 0.5f * (a - c) / rad : 1.f;
-        const float s2p = rad > 0.f ? b / rad : 0.f;
-        const float c2q = ux * ux - uy * uy, s2q = 2.f * ux * uy;
-        const float sr = sqrtf(a * ux * ux + 2.f * b * ux * uy + c * uy * uy);
-        const float lr = logf(rho);
-        f[0] = un;
-        f[1] = vn;
-        f[2] = logf(tz * rho / cam.fx);
-        f[3] = 0.5f * logf(mid + rad) - lr;
-        f[4] = 0.5f * logf(mid - rad) - lr;
-        f[5] = logf(sr) - lr;
-        f[6] = c2p * c2q + s2p * s2q;
-        f[7] = s2p * c2q - c2p * s2q;
-        f[8] = fminf(fmaxf((rho - qn) / sr, -8.f), 8.f);
-    }
-    f[9] = (lsc[i] + lsc[n + i] + lsc[2 * n + i]) * (1.0f / 3.0f);
-    f[10] = opl[i];
-#pragma unroll
-    for (int k = 0; k < 48; ++k) {
-        const size_t o = (size_t)k * n + i;
-        f[11 + k] = sh_dtype == RECOGS_F32   ? sh[o]
-                    : sh_dtype == RECOGS_F16 ? __half2float(reinterpret_cast<const __half*>(sh)[o])
-                                             : __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(sh)[o]);
-    }
-#pragma unroll
-    for (int k = 59; k < 64; ++k) f[k] = 0.f;
+    const bool ok = mlp_feature_row(n, i, xyz, lsc, quat, opl, sh, sh_dtype, cam, reg, fr, f);
     uint4* row = reinterpret_cast<uint4*>(X + (size_t)i * 32);
 #pragma unroll
     for (int q = 0; q < 8; ++q)
@@ -619,10 +644,29 @@ __global__ void __launch_bounds__(256) mlp_label_kernel(int n, const float* __re
     labels[2 * (size_t)i + 1] = all > 0.f ? fminf(1.f, in / all) : (sel ? 1.f : 0.f);
 }
 
-// Decisions of the learned path: p = sigmoid(o0); outside the learned
-// domain or where |p - 1/2| < delta the plain test decides, with its bit as
-// the weight; elsewhere the bit is p > 1/2 and the per-channel weights are
-// sigmoid(o1..3).
+// Decisions of the learned path for one Gaussian with outputs o: p =
+// sigmoid(o0); outside the learned domain (ok false) or where |p - 1/2| <
+// delta the plain test decides, with its bit as the weight; elsewhere the
+// bit is p > 1/2 and the per-channel weights are sigmoid(o1..3). fb: the
+// plain test decided inside the learned domain.
+__device__ __forceinline__ bool mlp_decide_row(bool ok, float4 o, float delta, const DevCamera& cam,
+                                               const DevRegion& reg, float x, float y, float z,
+                                               bool& fb, float (&w)[3]) {
+    const float p = sigmoidf(o.x);
+    fb = ok && fabsf(p - 0.5f) < delta;
+    bool sel;
+    if (!ok || fb) {
+        sel = select_centre(cam, reg, x, y, z, nullptr);
+        w[0] = w[1] = w[2] = sel ? 1.f : 0.f;
+    } else {
+        sel = p > 0.5f;
+        w[0] = sigmoidf(o.y);
+        w[1] = sigmoidf(o.z);
+        w[2] = sigmoidf(o.w);
+    }
+    return sel;
+}
+
 __global__ void __launch_bounds__(256)
     mlp_decide_kernel(int n, const float* __restrict__ xyz, DevCamera cam, DevRegion reg,
                       const float* __restrict__ out, float delta, uint32_t* __restrict__ mask,
@@ -633,21 +677,11 @@ __global__ void __launch_bounds__(256)
         float u, v, tz;
         const bool ok = sel_view(cam, xyz, n, i, u, v, tz);
         const float4 o = reinterpret_cast<const float4*>(out)[i];
-        const float p = sigmoidf(o.x);
-        fb = ok && fabsf(p - 0.5f) < delta;
-        float w0, w1, w2;
-        if (!ok || fb) {
-            sel = select_centre(cam, reg, xyz[i], xyz[n + i], xyz[2 * n + i], nullptr);
-            w0 = w1 = w2 = sel ? 1.f : 0.f;
-        } else {
-            sel = p > 0.5f;
-            w0 = sigmoidf(o.y);
-            w1 = sigmoidf(o.z);
-            w2 = sigmoidf(o.w);
-        }
-        weights[3 * (size_t)i + 0] = w0;
-        weights[3 * (size_t)i + 1] = w1;
-        weights[3 * (size_t)i + 2] = w2;
+        float w[3];
+        sel = mlp_decide_row(ok, o, delta, cam, reg, xyz[i], xyz[n + i], xyz[2 * n + i], fb, w);
+        weights[3 * (size_t)i + 0] = w[0];
+        weights[3 * (size_t)i + 1] = w[1];
+        weights[3 * (size_t)i + 2] = w[2];
     }
     const uint32_t bits = __ballot_sync(0xffffffffu, sel);
     if ((threadIdx.x & 31) == 0 && i < n) mask[i >> 5] = bits;
@@ -656,14 +690,381 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------------------
+// Fused learned selection on the 5th-generation tensor cores (tcgen05)
+//
+// One CTA of 256 threads, persistent over pairs of tiles of 128 Gaussians;
+// thread t owns row t % 128 of tile t / 128 of the pair. Per tile:
+//   features (its thread) -> X (shared memory, bf16, tensor-core operand layout)
+//   layer 1: D = X W1 (tcgen05.mma, M = 128, N = 64, fp32 accumulator in TMEM)
+//   D (tcgen05.ld) + b1 -> GELU -> bf16 -> X (layer 1 has read X)
+//   layer 2: D = X W2 -> + b2 -> GELU -> bf16 -> X
+//   layer 3: D = X W3 (N = 16, 4 used) -> + b3 -> decisions -> mask, weights
+// so the features never leave the SM. Each tile has one 16 KB operand buffer
+// and 64 TMEM columns reused by its three layers; one thread issues a
+// layer's MMAs for both tiles and commits them to an mbarrier every thread
+// waits on (bounded: a wait that gives up records an error and the CTA frees
+// its tensor memory and returns). The rounding points are those of the
+// mma.sync path: bf16 features, weights and activations, fp32 accumulation,
+// biases and GELU in fp32.
+
+constexpr int kSelRows = 128;               // rows per tile (the MMA's M)
+constexpr int kSelTiles = 2;                // tiles per CTA in flight
+constexpr int kSelThreads = kSelRows * kSelTiles;
+
+// Operand layout (K-major, no swizzle): element (r, k) of an R x 64 bf16
+// operand at byte (k / 8) (R / 8) 128 + (r / 8) 128 + (r % 8) 16 + (k % 8) 2,
+// i.e. 8 x 8 core matrices of 128 contiguous bytes, consecutive 8-row groups
+// 128 B apart (the stride byte offset) and consecutive 8-column groups
+// R * 16 B apart (the leading byte offset).
+__host__ __device__ constexpr uint32_t umma_off(int r, int k, int R) {
+    return (uint32_t)((k >> 3) * (R >> 3) * 128 + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Weights as tcgen05 B operands (bf16 bits, umma_off layout with R = N) and
+// fp32 biases; stored right after the MlpFrags block.
+struct MlpUmma {
+    uint16_t W1[64 * 64];   // N = 64 outputs x K = 64 inputs
+    uint16_t W2[64 * 64];
+    uint16_t W3[16 * 64];   // N = 16: the 4 outputs and 12 zero rows
+    float b1[64], b2[64], b3[16];
+};
+static_assert(sizeof(MlpUmma) % 16 == 0, "copied in 16-byte pieces");
+
+__host__ __device__ inline const MlpUmma* umma_weights(const MlpFrags* f) {
+    return reinterpret_cast<const MlpUmma*>(f + 1);
+}
+
+__global__ void __launch_bounds__(256) mlp_pack_umma_kernel(const float* __restrict__ p,
+                                                            MlpUmma* __restrict__ u) {
+    const float* W1 = p + kOffW1;
+    const float* W2 = p + kOffW2;
+    const float* W3 = p + kOffW3;
+    auto bf = [](float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); };
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+        const int nn = e >> 6, k = e & 63;    // output nn, input k
+        u->W1[umma_off(nn, k, 64) / 2] = bf(W1[k * 64 + nn]);
+        u->W2[umma_off(nn, k, 64) / 2] = bf(W2[k * 64 + nn]);
+    }
+    for (int e = threadIdx.x; e < 16 * 64; e += blockDim.x) {
+        const int nn = e >> 6, k = e & 63;
+        u->W3[umma_off(nn, k, 16) / 2] = nn < 4 ? bf(W3[k * 4 + nn]) : (uint16_t)0;
+    }
+    for (int e = threadIdx.x; e < 64; e += blockDim.x) {
+        u->b1[e] = p[kOffB1 + e];
+        u->b2[e] = p[kOffB2 + e];
+    }
+    if (threadIdx.x < 16) u->b3[threadIdx.x] = threadIdx.x < 4 ? p[kOffB3 + threadIdx.x] : 0.f;
+}
+
+// Shared-memory matrix descriptor of tcgen05 (K-major, no swizzle): start
+// address, leading byte offset (between 8-column groups) and stride byte
+// offset (between 8-row groups), each in 16-byte units; bits 46-47 hold the
+// descriptor version 1, swizzle bits 61-63 stay 0.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of tcgen05.mma .kind::f16: fp32 accumulator (bits
+// 4-5 = 1), bf16 A and B (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 =
+// 0), N / 8 in bits 17-22, M / 16 in bits 24-28.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// the MMAs issued so far by this thread arrive on the mbarrier once complete
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// shared-memory writes of this thread become visible to the tensor cores
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 32 consecutive fp32 columns of this thread's TMEM lane (row)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// two fp32 lanes per instruction (PTX .f32x2)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(*reinterpret_cast<unsigned long long*>(&d))
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)),
+          "l"(*reinterpret_cast<unsigned long long*>(&b)),
+          "l"(*reinterpret_cast<unsigned long long*>(&c)));
+    return d;
+}
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+    float2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;"
+        : "=l"(*reinterpret_cast<unsigned long long*>(&d))
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)),
+          "l"(*reinterpret_cast<unsigned long long*>(&b)));
+    return d;
+}
+
+// gelu() of two values, the same operations in pairs
+__device__ __forceinline__ float2 gelu2(float2 z) {
+    const float2 a = make_float2(fabsf(z.x), fabsf(z.y));
+    const float2 d = ffma2(make_float2(0.2316419f, 0.2316419f), a, make_float2(1.0f, 1.0f));
+    const float2 t = make_float2(rcp_approx(d.x), rcp_approx(d.y));
+    float2 p = ffma2(t, make_float2(0.5307027f, 0.5307027f), make_float2(-0.72657603f, -0.72657603f));
+    p = ffma2(t, p, make_float2(0.7107069f, 0.7107069f));
+    p = ffma2(t, p, make_float2(-0.14224836f, -0.14224836f));
+    p = ffma2(t, p, make_float2(0.1274148f, 0.1274148f));
+    const float2 m = fmul2(fmul2(make_float2(-0.7213475f, -0.7213475f), a), a);
+    float2 e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(m.x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(m.y));
+    const float2 q = fmul2(e, fmul2(p, t));     // 1 - Phi(|z|)
+    const float2 s = ffma2(q, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
+    return fmul2(z, make_float2(z.x >= 0.0f ? s.x : q.x, z.y >= 0.0f ? s.y : q.y));
+}
+
+// D (32 x 2 columns from TMEM, this thread's row) + bias -> GELU -> bf16 row
+// of the next layer's A operand
+__device__ __forceinline__ void sel_hidden(uint32_t tcol, const float* __restrict__ bias,
+                                           unsigned char* dst, int row) {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        uint32_t r[32];
+        tmem_ld32(tcol + 32 * half, r);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int k = 32 * half + 8 * c + 2 * j;
+                const float2 z = make_float2(__uint_as_float(r[8 * c + 2 * j]) + bias[k],
+                                             __uint_as_float(r[8 * c + 2 * j + 1]) + bias[k + 1]);
+                const float2 g = gelu2(z);
+                const __nv_bfloat162 h = __floats2bfloat162_rn(g.x, g.y);
+                pk[j] = *reinterpret_cast<const uint32_t*>(&h);
+            }
+            *reinterpret_cast<uint4*>(dst + umma_off(row, 32 * half + 8 * c, kSelRows)) =
+                make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+    }
+}
+
+struct SelSmem {
+    MlpUmma w;
+    alignas(128) unsigned char X[kSelTiles][kSelRows * 64 * 2];   // each tile's A operand
+    alignas(8) uint64_t bar;
+    uint32_t taddr;
+};
+
+#ifndef RECOGS_SEL_MIN_BLOCKS
+#define RECOGS_SEL_MIN_BLOCKS 3
+#endif
+__global__ void __launch_bounds__(kSelThreads, RECOGS_SEL_MIN_BLOCKS)
+    mlp_select_tc_kernel(int n, const float* __restrict__ xyz, const float* __restrict__ lsc,
+                         const float* __restrict__ quat, const float* __restrict__ opl,
+                         const float* __restrict__ sh, int sh_dtype, DevCamera cam, DevRegion reg,
+                         MlpRegionFrame fr, const MlpUmma* __restrict__ wg, float delta,
+                         uint32_t* __restrict__ mask, float* __restrict__ weights,
+                         unsigned long long* __restrict__ fallbacks, uint32_t* __restrict__ error) {
+    extern __shared__ __align__(128) unsigned char sel_smem[];
+    SelSmem& sm = *reinterpret_cast<SelSmem*>(sel_smem);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int tl = t / kSelRows, row = t % kSelRows;   // this thread's tile of the pair and row
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(wg);
+        uint4* dst = reinterpret_cast<uint4*>(&sm.w);
+        for (int k = t; k < (int)(sizeof(MlpUmma) / 16); k += kSelThreads) dst[k] = src[k];
+    }
+    if (warp == 0) {
+        // 128 TMEM columns: tile 0 in 0..63, tile 1 in 64..127
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+                         smem_addr(&sm.taddr))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) mbar_init(&sm.bar, 1);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.taddr;
+    // this thread's TMEM lane (warp w reads lanes 32 (w % 4) ..) and its tile's columns
+    const uint32_t my_tmem = tmem + ((uint32_t)((warp & 3) * 32) << 16) + 64u * (uint32_t)tl;
+    unsigned char* const myX = sm.X[tl];
+    const uint32_t sX0 = smem_addr(sm.X[0]);
+    constexpr uint32_t kXBytes = kSelRows * 64 * 2;
+    const uint32_t sW1 = smem_addr(sm.w.W1), sW2 = smem_addr(sm.w.W2), sW3 = smem_addr(sm.w.W3);
+    constexpr uint32_t kLboA = (kSelRows / 8) * 128, kLboB = 8 * 128, kLboB3 = 2 * 128;
+    constexpr uint32_t idesc64 = umma_idesc_bf16(kSelRows, 64), idesc16 = umma_idesc_bf16(kSelRows, 16);
+    uint32_t phase = 0;
+    // one thread: both tiles' four K = 16 MMAs of a layer, then the commit
+    auto issue = [&](uint32_t sW, uint32_t lboB, uint32_t idesc) {
+        if (t != 0) return;
+        tc_fence_after();
+#pragma unroll
+        for (int q = 0; q < kSelTiles; ++q)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                umma_bf16(tmem + 64u * q, umma_desc(sX0 + q * kXBytes + 2 * kk * kLboA, kLboA, 128),
+                          umma_desc(sW + 2 * kk * lboB, lboB, 128), idesc, kk > 0);
+        umma_commit(&sm.bar);
+    };
+    // operand writes visible to the tensor cores, earlier TMEM reads done, then the MMAs
+    auto handoff = [&](uint32_t sW, uint32_t lboB, uint32_t idesc) {
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        issue(sW, lboB, idesc);
+    };
+    // every thread waits for the layer's MMAs; false (all threads) if the bounded wait gave up
+    auto layer_done = [&]() {
+        const bool ok = mbar_wait(&sm.bar, phase);
+        phase ^= 1u;
+        const bool all = __syncthreads_and(ok);
+        tc_fence_after();
+        return all;
+    };
+    const int tiles = (n + kSelRows - 1) / kSelRows;
+    const int pairs = (tiles + kSelTiles - 1) / kSelTiles;
+    bool alive = true;
+    for (int pr = blockIdx.x; alive && pr < pairs; pr += gridDim.x) {
+        const int i = (pr * kSelTiles + tl) * kSelRows + row;
+        float f[64];
+        bool ok = false;
+        if (i < n) {
+            ok = mlp_feature_row(n, i, xyz, lsc, quat, opl, sh, sh_dtype, cam, reg, fr, f);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 64; ++k) f[k] = 0.f;
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            *reinterpret_cast<uint4*>(myX + umma_off(row, 8 * c, kSelRows)) =
+                make_uint4(pack_bf16(f[8 * c + 0], f[8 * c + 1]), pack_bf16(f[8 * c + 2], f[8 * c + 3]),
+                           pack_bf16(f[8 * c + 4], f[8 * c + 5]), pack_bf16(f[8 * c + 6], f[8 * c + 7]));
+        handoff(sW1, kLboB, idesc64);                       // layer 1
+        if (!(alive = layer_done())) break;
+        sel_hidden(my_tmem, sm.w.b1, myX, row);
+        tc_fence_before();
+        handoff(sW2, kLboB, idesc64);                       // layer 2
+        if (!(alive = layer_done())) break;
+        sel_hidden(my_tmem, sm.w.b2, myX, row);
+        tc_fence_before();
+        handoff(sW3, kLboB3, idesc16);                      // layer 3
+        if (!(alive = layer_done())) break;
+        uint32_t o[4];
+        tmem_ld4(my_tmem, o);
+        tmem_wait_ld();
+        tc_fence_before();   // these reads precede the next pair's layer 1 (after its barrier)
+        bool sel = false, fb = false;
+        if (i < n) {
+            const float4 out = make_float4(__uint_as_float(o[0]) + sm.w.b3[0],
+                                           __uint_as_float(o[1]) + sm.w.b3[1],
+                                           __uint_as_float(o[2]) + sm.w.b3[2],
+                                           __uint_as_float(o[3]) + sm.w.b3[3]);
+            float wv[3];
+            sel = mlp_decide_row(ok, out, delta, cam, reg, xyz[i], xyz[n + i], xyz[2 * n + i], fb, wv);
+            weights[3 * (size_t)i + 0] = wv[0];
+            weights[3 * (size_t)i + 1] = wv[1];
+            weights[3 * (size_t)i + 2] = wv[2];
+        }
+        const uint32_t bits = __ballot_sync(0xffffffffu, sel);
+        const int i0 = i - lane;
+        if (lane == 0 && i0 < n) mask[i0 >> 5] = bits;
+        const uint32_t nfb = __popc(__ballot_sync(0xffffffffu, fb));
+        if (lane == 0 && nfb) atomicAdd(fallbacks, (unsigned long long)nfb);
+    }
+    if (!alive && t == 0) atomicOr(error, 1u);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 
 int launch_mlp_pack(const float* params, MlpFrags* frags, cudaStream_t st) {
     mlp_pack_kernel<<<1, 256, 0, st>>>(params, frags);
-    return 1;
+    mlp_pack_umma_kernel<<<1, 256, 0, st>>>(params, reinterpret_cast<MlpUmma*>(frags + 1));
+    return 2;
 }
 
-size_t mlp_frags_bytes() { return sizeof(MlpFrags); }
+// the mma.sync fragments followed by the tcgen05 operand images
+size_t mlp_frags_bytes() { return sizeof(MlpFrags) + sizeof(MlpUmma); }
+
+int launch_mlp_select_fused(const recogs_scene& s, const DevCamera& cam, const DevRegion& reg,
+                            const MlpRegionFrame& fr, const MlpFrags* frags, float delta,
+                            uint32_t* mask, float* weights, unsigned long long* fallbacks,
+                            uint32_t* error, cudaStream_t st) {
+    const int n = (int)s.n;
+    if (n == 0) return 0;
+    const int smem = (int)sizeof(SelSmem);
+    static std::atomic<uint64_t> opted{0};
+    smem_opt_in(mlp_select_tc_kernel, smem, opted);
+    // the largest shared-memory share of the SM (the default split leaves
+    // room for one CTA only)
+    static std::atomic<uint64_t> carved{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (!bit || !(carved.load(std::memory_order_acquire) & bit)) {
+        cudaFuncSetAttribute(mlp_select_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        if (bit) carved.fetch_or(bit, std::memory_order_release);
+    }
+    // the occupancy the kernel is compiled for (its launch bound; at most 4
+    // CTAs: four 128-column tensor-memory allocations fill the SM's 512); the
+    // persistent loop covers any grid
+    const int per_sm = RECOGS_SEL_MIN_BLOCKS < 4 ? RECOGS_SEL_MIN_BLOCKS : 4;
+    const int pairs = (n + kSelThreads - 1) / kSelThreads;
+    const int g = pairs < device_sms() * per_sm ? pairs : device_sms() * per_sm;
+    mlp_select_tc_kernel<<<g, kSelThreads, smem, st>>>(n, s.xyz, s.log_scale, s.quat, s.opacity_logit,
+                                                    (const float*)s.sh, s.sh_dtype, cam, reg, fr,
+                                                    umma_weights(frags), delta, mask, weights,
+                                                    fallbacks, error);
+    return 1;
+}
 
 int launch_mlp_forward(const uint32_t* X, int64_t n, const MlpFrags* frags, float* out,
                        cudaStream_t st) {

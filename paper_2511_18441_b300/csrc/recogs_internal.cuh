@@ -150,15 +150,13 @@ __device__ __forceinline__ void grid_dependents_launch() {
 }
 
 // --------------------------------------------------------------------------
-// Shared-memory mbarriers (PTX mbarrier.*): a producer/consumer hand-off
-// inside a CTA without block-wide barriers. Every wait is bounded: each poll
-// may suspend the thread for at most kMbarPollNs (the suspend-time hint) and
-// after kMbarSpinLimit unsuccessful polls (~70 ms) the wait returns false
-// (the caller records an error and abandons its work), so no wait can hang
-// the GPU. A legitimate wait lasts microseconds.
+// Shared-memory mbarriers (PTX mbarrier.*), e.g. for the completion of
+// tensor-core work. Every wait is bounded: it polls without blocking
+// (test_wait, a short sleep between later polls) and after kMbarSpinLimit
+// polls (~0.1 s) returns false (the caller records an error and abandons its
+// work), so no wait can hang the GPU. A legitimate wait lasts microseconds.
 
-constexpr uint32_t kMbarSpinLimit = 1u << 16;
-constexpr uint32_t kMbarPollNs = 1024;
+constexpr uint32_t kMbarSpinLimit = 1u << 20;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -184,12 +182,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     for (uint32_t i = 0; i < kMbarSpinLimit; ++i) {
         uint32_t ok;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(ok)
-            : "r"(a), "r"(parity), "r"(kMbarPollNs)
+            : "r"(a), "r"(parity)
             : "memory");
         if (ok) return true;
+        if (i >= 16) __nanosleep(64);
     }
     return false;
 }
@@ -468,6 +467,13 @@ int launch_mlp_labels(const recogs_scene& s, const DevCamera& cam, const DevRegi
 int launch_mlp_decide(const recogs_scene& s, const DevCamera& cam, const DevRegion& reg,
                       const float* out, float delta, uint32_t* mask, float* weights,
                       unsigned long long* fallbacks, cudaStream_t st);
+// Features, the network on the tcgen05 tensor cores and the decisions in one
+// kernel (the result of features + forward + decide); error (device word) is
+// set non-zero if a bounded wait for the tensor cores gave up.
+int launch_mlp_select_fused(const recogs_scene& s, const DevCamera& cam, const DevRegion& reg,
+                            const MlpRegionFrame& fr, const MlpFrags* frags, float delta,
+                            uint32_t* mask, float* weights, unsigned long long* fallbacks,
+                            uint32_t* error, cudaStream_t st);
 // Recolour with per-Gaussian, per-channel weights w in [0, 1]:
 // C <- C + w (M C - C) per triple (DC also + w dc_fix); w = 1 is the plain
 // recolour bit for bit, w = 0 leaves the Gaussian untouched (preprocess.cu).

@@ -188,3 +188,57 @@ def test_decisions_truth_table():
     np.testing.assert_allclose(w[0], 0.5)
     np.testing.assert_allclose(w[2], 1.0)
     np.testing.assert_allclose(w[3], 1.0)
+
+
+def _f32_forward(theta, X, order):
+    """A float32 implementation rounding at the oracle's points: bf16
+    operands, float32 sums over the inputs in the given order, the
+    Abramowitz-Stegun 26.2.17 GELU in float32."""
+    P = mlp.unpack(theta)
+    f32 = np.float32
+
+    def layer(x, W, b):
+        x = x.astype(f32)
+        W = W.astype(f32)
+        acc = np.broadcast_to(b.astype(f32), (x.shape[0], W.shape[1])).copy()
+        for k in order[:W.shape[0]]:
+            acc = (acc + x[:, k:k + 1] * W[k:k + 1, :]).astype(f32)
+        return acc
+
+    def gelu32(z):
+        a = np.abs(z).astype(f32)
+        t = (f32(1) / (f32(0.2316419) * a + f32(1))).astype(f32)
+        p = t * f32(0.5307027) + f32(-0.72657603)
+        p = t * p + f32(0.7107069)
+        p = t * p + f32(-0.14224836)
+        p = t * p + f32(0.1274148)
+        e = np.exp2((f32(-0.7213475) * a) * a).astype(f32)
+        q = (e * (p * t)).astype(f32)
+        return (z * np.where(z >= 0, f32(1) - q, q)).astype(f32)
+
+    x = mlp.bf16(X)
+    h1 = mlp.bf16(gelu32(layer(x, mlp.bf16(P["W1"]), P["b1"])).astype(np.float64))
+    h2 = mlp.bf16(gelu32(layer(h1, mlp.bf16(P["W2"]), P["b2"])).astype(np.float64))
+    return layer(h2, mlp.bf16(P["W3"]), P["b3"]).astype(np.float64)
+
+
+def test_forward_bound_covers_a_float32_implementation():
+    """Every output of a float32 implementation (reverse summation order,
+    the A&S GELU) lies within forward_bound of the FP64 oracle; a bound
+    without the activations' rounding flips does not, so the flip term is
+    exercised."""
+    rng = np.random.default_rng(3)
+    n = 3000
+    X = rng.normal(0, 1.0, (n, 64))
+    X[:, 59:] = 0.0
+    for seed, scale in ((1, 1.0), (2, 3.0)):
+        theta = sg.mlp_init(seed).astype(np.float64) * scale
+        f, bound = mlp.forward_bound(theta, X)
+        o32 = _f32_forward(theta, X, order=list(range(63, -1, -1)))
+        err = np.abs(o32 - f["o"])
+        assert np.all(err <= bound), (err / bound).max()
+        # without the flip term the bound is the accumulation alone
+        P = mlp.unpack(theta)
+        g = mlp._gamma(65)
+        acc_only = g * ((np.abs(f["h2"])) @ np.abs(mlp.bf16(P["W3"])) + np.abs(P["b3"]))
+        assert np.any(err > acc_only)
