@@ -111,9 +111,66 @@ def aggregate_value(steps: int, world: int, max_ms: float) -> float:
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 
+class _Nvml:
+    """The few read-only NVML queries the clock sampler needs, through the
+    driver's libnvidia-ml (no Python package required)."""
+
+    CLOCK_SM = 1
+
+    def __init__(self):
+        import ctypes as C
+        self.C = C
+        self.lib = C.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+
+    def handle(self, device):
+        C = self.C
+        import torch
+        h = C.c_void_p()
+        props = torch.cuda.get_device_properties(device)
+        bus = getattr(props, "pci_bus_id", None)
+        dom = getattr(props, "pci_domain_id", None)
+        dev = getattr(props, "pci_device_id", None)
+        if bus is not None and dom is not None and dev is not None:
+            pci = f"{dom:08x}:{bus:02x}:{dev:02x}.0".encode()
+            if self.lib.nvmlDeviceGetHandleByPciBusId_v2(C.c_char_p(pci), C.byref(h)) == 0:
+                return h
+        count = C.c_uint()
+        self.lib.nvmlDeviceGetCount_v2(C.byref(count))
+        idx = 0 if count.value == 1 else int(device)
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(idx), C.byref(h)) != 0:
+            raise RuntimeError("no NVML handle for the device")
+        return h
+
+    def _u(self, fn, *args):
+        v = self.C.c_uint()
+        if fn(*args, self.C.byref(v)) != 0:
+            raise RuntimeError(fn.__name__)
+        return v.value
+
+    def sm_mhz(self, h):
+        return self._u(self.lib.nvmlDeviceGetClockInfo, h, self.C.c_int(self.CLOCK_SM))
+
+    def sm_max_mhz(self, h):
+        return self._u(self.lib.nvmlDeviceGetMaxClockInfo, h, self.C.c_int(self.CLOCK_SM))
+
+    def power_w(self, h):
+        return self._u(self.lib.nvmlDeviceGetPowerUsage, h) / 1000.0
+
+    def reasons(self, h):
+        v = self.C.c_ulonglong()
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        if fn(h, self.C.byref(v)) != 0:
+            raise RuntimeError("clock event reasons")
+        return v.value
+
+
 class ClockSampler:
-    """SM clock, power and clock-event reasons of the bench's GPU, sampled by
-    NVML every 50 ms on a thread while the bench runs (read-only queries)."""
+    """SM clock, power and clock-event reasons of the bench's GPU, sampled
+    through NVML every 50 ms on a thread while the bench runs (read-only
+    queries)."""
 
     # NVML clock-event reason bits
     REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
@@ -127,27 +184,11 @@ class ClockSampler:
         self._stop = threading.Event()
         self.th = None
 
-    def _handle(self, nv):
-        import torch
-        props = torch.cuda.get_device_properties(self.device)
-        bus = getattr(props, "pci_bus_id", None)
-        dom = getattr(props, "pci_domain_id", None)
-        dev = getattr(props, "pci_device_id", None)
-        if bus is not None and dom is not None and dev is not None:
-            try:
-                return nv.nvmlDeviceGetHandleByPciBusId(f"{dom:08x}:{bus:02x}:{dev:02x}.0")
-            except nv.NVMLError:
-                pass
-        if nv.nvmlDeviceGetCount() == 1:
-            return nv.nvmlDeviceGetHandleByIndex(0)
-        return nv.nvmlDeviceGetHandleByIndex(int(self.device))
-
     def start(self):
         try:
-            import pynvml as nv
-            nv.nvmlInit()
-            h = self._handle(nv)
-            self.max_mhz = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+            nv = _Nvml()
+            h = nv.handle(self.device)
+            self.max_mhz = nv.sm_max_mhz(h)
         except Exception as e:   # no NVML: report why instead of clocks
             self.error = f"{type(e).__name__}: {e}"
             return
@@ -155,9 +196,7 @@ class ClockSampler:
         def run():
             while not self._stop.is_set():
                 try:
-                    self.samples.append((time.time(), nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM),
-                                         nv.nvmlDeviceGetPowerUsage(h) / 1000.0,
-                                         nv.nvmlDeviceGetCurrentClocksEventReasons(h)))
+                    self.samples.append((time.time(), nv.sm_mhz(h), nv.power_w(h), nv.reasons(h)))
                 except Exception as e:
                     self.error = f"{type(e).__name__}: {e}"
                     return
@@ -1002,6 +1041,8 @@ def run_mlp(args, rank, world, local):
     t_fwd = event_ms(lambda: net.forward(Fe, out=out, stream=stream))
     peaks, src = load_peaks()
     tflops = n * flop_fwd / (t_fwd / 1000.0) / 1e12
+    flop_sel = 2 * (64 * 64 + 64 * 64 + 64 * 16)      # per row, the tcgen05 shapes
+    sel_tflops = n * flop_sel / (t_learned / 1000.0) / 1e12
     E = {k: float(np.mean([e[k] for e in evals])) for k in evals[0]}
     if rank == 0:
         line = {
@@ -1020,10 +1061,194 @@ def run_mlp(args, rank, world, local):
                          "loss_first": first, "loss_last": last},
             "timings_ms": {"learned_selection": t_learned, "plain_selection": t_plain,
                            "labels_render_and_cover": t_labels, "mlp_forward": t_fwd},
-            "roofline": {"kernel": "mlp_forward_kernel (mma.sync bf16)", "bound": "tensor",
-                         "achieved": tflops, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                         "frac": tflops / peaks["bf16_tflops"],
-                         "peak_source": f"{src} cuBLAS bf16 burst", "traffic": None},
+            "roofline": {"kernel": ("mlp_select_tc_kernel (features + tcgen05 network + "
+                                    "decisions in one kernel)"),
+                         "bound": "tensor", "achieved": sel_tflops, "peak": peaks["bf16_tflops"],
+                         "unit": "TFLOP/s", "frac": sel_tflops / peaks["bf16_tflops"],
+                         "peak_source": f"{src} cuBLAS bf16 burst", "traffic": None,
+                         "note": ("the tensor pipe is far from busy: the kernel is bound by "
+                                  "CUDA-core issue (128 GELUs and the features per row)")},
+            "forward_only_mma_sync": {"kernel": "mlp_forward_kernel (mma.sync bf16, features "
+                                                "read from HBM)",
+                                      "achieved_tflops": tflops, "ms": t_fwd},
+        }
+        print(json.dumps(line), flush=True)
+    net.close()
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# the combined form: BF16 SH + learned selection + batched graph launch
+
+COMBINED_TRAIN_POLYGONS = 16
+
+
+def psnr_db(a, b):
+    mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
+    return 10.0 * math.log10(1.0 / mse) if mse > 0 else float("inf")
+
+
+def run_combined(args, rank, world, local):
+    """The batched workload (4 scenes of 0.5/1/2/4M Gaussians, 16 ring views
+    each at 720p-2160p, a box selection and tint per scene) in two forms in
+    the same run. Plain FP32: float32 SH, every view through recogs_render
+    with the fused plain edit. Combined: BF16 SH; per scene the learned
+    selection (its box as a 4-vertex polygon, plain fallback) and the
+    weighted recolour of the unedited coefficients, then all 64 views in one
+    replay of the planned, tuned batch graph. Both in views/s; each form's
+    PSNR on sampled views against the FP64 oracle of the plain edit."""
+    import torch
+    import oracle
+    from paper_2511_18441_b300 import binding, build
+    from paper_2511_18441_b300 import scenegen as sg
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the library has no CPU path)")
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    bw = sg.batched_workload(sizes=BATCH_SIZES, views_per_scene=BATCH_VIEWS_PER_SCENE)
+    ctx = binding.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    nv = len(bw.views)
+    first = {si: k for k, (si, _, _) in reversed(list(enumerate(bw.views)))}
+
+    # the plain FP32 form
+    f32 = [binding.DeviceScene.from_numpy(sc, dev, "f32") for sc in bw.scenes]
+    img_p = [torch.empty((cam.height, cam.width, 3), device=dev) for _, cam, _ in bw.views]
+
+    def plain_step():
+        for (si, cam, edit), img in zip(bw.views, img_p):
+            ctx.render(f32[si], cam, edit, image_out=img, stream=stream)
+
+    # the selection network: labels of random polygons in the 1M scene's first view
+    tsi = 1
+    tcam = bw.views[first[tsi]][1]
+    net = ctx.mlp(sg.mlp_init(SEED))
+    feats, labs = [], []
+    for reg in sg.random_polygons(COMBINED_TRAIN_POLYGONS, tcam.width, tcam.height, 23):
+        F, L, V = ctx.mlp_features(f32[tsi], tcam, reg, stream=stream)
+        keep = V.bool()
+        feats.append(F[keep])
+        labs.append(L[keep])
+    F = torch.cat(feats)
+    L = torch.cat(labs)
+    del feats, labs
+    rng = np.random.default_rng(SEED)
+    t0 = time.perf_counter()
+    for k in range(args.mlp_steps):
+        rows = torch.from_numpy(rng.integers(0, F.shape[0], 16384).astype(np.uint32)).to(dev)
+        net.train_step(F, L, rows, lr=2e-3, stream=stream)
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    del F, L
+
+    # the combined form
+    orig = [binding.DeviceScene.from_numpy(sc, dev, "bf16") for sc in bw.scenes]
+    work = [binding.DeviceScene.from_numpy(sc, dev, "bf16") for sc in bw.scenes]
+    edits = []
+    for si in range(len(bw.scenes)):
+        e = bw.views[first[si]][2]
+        n = bw.scenes[si].n
+        edits.append(dict(cam=e.select_camera, poly=sg.box_as_polygon(e.region), M=e.color_matrix,
+                          mask=torch.zeros((binding.mask_words(n),), dtype=torch.int32, device=dev),
+                          w=torch.empty((n, 3), dtype=torch.float32, device=dev)))
+    img_c = [torch.empty((cam.height, cam.width, 3), device=dev) for _, cam, _ in bw.views]
+    views_c = [dict(scene=si, camera=cam, edit=None, image_out=img)
+               for (si, cam, _), img in zip(bw.views, img_c)]
+
+    def edit_all():
+        for si, e in enumerate(edits):
+            work[si].sh.copy_(orig[si].sh)             # the unedited coefficients
+            net.select(work[si], e["cam"], e["poly"], delta=0.1, mask_out=e["mask"],
+                       weights_out=e["w"], count_fallbacks=False, stream=stream)
+            ctx.recolor_weighted(work[si], e["w"], e["M"], stream=stream)
+
+    edit_all()
+    b = ctx.batch(work, views_c, graph=True, tune=True)
+    b(stream=stream)                                   # plans, tunes, captures
+
+    def combined_step():
+        edit_all()
+        b(nowait=True, stream=stream)
+
+    def timed(fn, k):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        return max_over_ranks(e0.elapsed_time(e1), world, dev) / k
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    sampler.mark_begin()
+    l0 = ctx.launch_count()
+    comb_ms = timed(combined_step, args.steps)
+    launches = (ctx.launch_count() - l0) // (args.steps + max(3, args.warmup))
+    sampler.mark_end()
+    clocks = sampler.stop()
+    ctx.check(stream)
+    plain_ms = timed(plain_step, max(3, args.steps // 2))
+    edit_ms = timed(edit_all, max(3, args.steps // 2))
+
+    # quality: sampled views of the 1M scene against the FP64 oracle of the plain edit
+    combined_step()
+    plain_step()
+    torch.cuda.synchronize(dev)
+    quality = []
+    fallbacks = []
+    for si, e in enumerate(edits):
+        _, _, nfb = net.select(work[si], e["cam"], e["poly"], delta=0.1, stream=stream)
+        fallbacks.append(nfb / bw.scenes[si].n)
+    edit_all()
+    b(stream=stream)
+    torch.cuda.synchronize(dev)
+    picked = {}
+    for k, (si, cam, edit) in enumerate(bw.views):
+        if si == tsi and (cam.width, cam.height) in ((1280, 720), (1920, 1080)):
+            picked.setdefault((cam.width, cam.height), k)
+    for (W, H), k in sorted(picked.items()):
+        si, cam, edit = bw.views[k]
+        ref, *_ = oracle.render_image(bw.scenes[si], cam, edit)
+        quality.append({"view": k, "size": f"{W}x{H}",
+                        "psnr_combined_db": psnr_db(img_c[k].cpu().numpy(), ref["rgb"]),
+                        "psnr_plain_f32_db": psnr_db(img_p[k].cpu().numpy(), ref["rgb"])})
+    if rank == 0:
+        line = {
+            "metric": ("views/s of the batched recolor+render workload: BF16 SH + learned "
+                       "selection + one graph replay, against the plain FP32 form"),
+            "value": nv * world / (comb_ms / 1000.0), "unit": "views/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": comb_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic (seeded generator)",
+            "config": {"workload": (f"{len(bw.scenes)} scenes of "
+                                    f"{'/'.join(f'{n / 1e6:g}M' for n in BATCH_SIZES)} Gaussians, "
+                                    f"{BATCH_VIEWS_PER_SCENE} ring views each (1280x720 to "
+                                    "3840x2160), per-scene box selection (as a 4-gon) and tint"),
+                       "step": ("per scene: restore the unedited BF16 SH, learned selection "
+                                "(features + tcgen05 network + decisions, plain fallback at "
+                                "|p - 1/2| < 0.1), weighted recolour; then one replay of the "
+                                "64-view batch graph"),
+                       "network": (f"59-64-64-4 GELU trained on the GPU for {args.mlp_steps} "
+                                   f"steps on labels of {COMBINED_TRAIN_POLYGONS} random "
+                                   "polygons of the 1M scene's first view"),
+                       "l2": "inputs larger than L2; no flush"},
+            "plain_f32_form": {"views_per_s": nv * world / (plain_ms / 1000.0),
+                               "ms_per_step": plain_ms,
+                               "api": "recogs_render per view with the fused plain edit"},
+            "speedup_vs_plain_f32": plain_ms / comb_ms,
+            "edit_ms_per_step": edit_ms,
+            "quality_vs_fp64_oracle_of_the_plain_edit": quality,
+            "fallback_fraction_per_scene": fallbacks,
+            "training_seconds": train_s,
+            "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     net.close()
@@ -1042,10 +1267,12 @@ def main(argv=None):
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--readback", action="store_true",
                     help="time frames with the mid-frame read back (default: pair capacity preset)")
-    ap.add_argument("--workload", choices=["frame", "batch", "mlp", "refit"], default="frame",
+    ap.add_argument("--workload", choices=["frame", "batch", "mlp", "refit", "combined"],
+                    default="frame",
                     help="frame: the 3M/1080p headline; batch: 64 views of 4 scenes; "
                          "mlp: the learned selection at 6M Gaussians; refit: median depth "
-                         "and SH-only refit steps at 3M/1080p")
+                         "and SH-only refit steps at 3M/1080p; combined: BF16 + learned "
+                         "selection + batched graph against the plain FP32 form")
     ap.add_argument("--mlp-steps", type=int, default=4000,
                     help="training steps of the mlp workload (batch 16384)")
     ap.add_argument("--gaussians", type=int, default=None,
@@ -1066,6 +1293,8 @@ def main(argv=None):
             run_mlp(args, rank, world, local)
         elif args.workload == "refit":
             run_refit(args, rank, world, local)
+        elif args.workload == "combined":
+            run_combined(args, rank, world, local)
         else:
             run_ours(args, rank, world, local)
     finally:

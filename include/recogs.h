@@ -403,8 +403,7 @@ RECOGS_API recogs_status recogs_recolor_weighted(recogs_ctx* ctx, recogs_scene* 
  * NULL, non-finite or misaligned arguments give RECOGS_EINVAL); error_out
  * (host, may be NULL) receives a message of at most error_len bytes. Every
  * call reads the frame's counts back to the host mid-frame, so it
- * synchronises its stream each time and cannot be captured into a CUDA
- * graph. A frame with a tile above 16384 pairs is sorted by the global radix
+ * synchronises its stream each time. A frame with a tile above 16384 pairs is sorted by the global radix
  * path, whose bounded device waits report RECOGS_ETIMEOUT (invalid image)
  * from the same call. All calls share the one array: calls that overlap on
  * the GPU (other streams, other host threads) race and must be serialised by

@@ -583,21 +583,25 @@ class Mlp:
             _stream_ptr(stream)))
         return loss.value if want_loss else None
 
-    def select(self, scene: DeviceScene, cam, region, delta=0.1, stream=None):
-        """(mask words int32, weights [n, 3], fallback count)."""
+    def select(self, scene: DeviceScene, cam, region, delta=0.1, mask_out=None, weights_out=None,
+               count_fallbacks=True, stream=None):
+        """(mask words int32, weights [n, 3], fallback count or None when
+        count_fallbacks is False: then the call does not wait)."""
         import torch
         n = scene.n
         dev = scene.xyz.device
-        mask = torch.zeros((max(mask_words(n), 1),), dtype=torch.int32, device=dev)
-        w = torch.empty((max(n, 1), 3), dtype=torch.float32, device=dev)
+        mask = mask_out if mask_out is not None else torch.zeros(
+            (max(mask_words(n), 1),), dtype=torch.int32, device=dev)
+        w = weights_out if weights_out is not None else torch.empty(
+            (max(n, 1), 3), dtype=torch.float32, device=dev)
         fb = C.c_int64()
         cs = scene.struct()
         cc = camera_struct(cam)
         r, keep = region_struct(region)
         self.ctx._check(self.ctx._L.recogs_mlp_select(
             self._h, C.byref(cs), C.byref(cc), C.byref(r), float(delta), mask.data_ptr(),
-            w.data_ptr(), C.byref(fb), _stream_ptr(stream)))
-        return mask, w[:n], fb.value
+            w.data_ptr(), C.byref(fb) if count_fallbacks else None, _stream_ptr(stream)))
+        return mask, w[:n], (fb.value if count_fallbacks else None)
 
 
 class Batch:

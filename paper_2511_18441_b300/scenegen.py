@@ -234,6 +234,12 @@ def pixel_box_region(x0, y0, size_x, size_y) -> Region:
     return box_region(x0 - 0.5, y0 - 0.5, x0 + size_x - 0.5, y0 + size_y - 0.5)
 
 
+def box_as_polygon(region: Region) -> Region:
+    """A box region as the 4-vertex polygon with the same corners."""
+    (u0, v0), (u1, v1) = np.asarray(region.xy, np.float32)
+    return Region("polygon", np.array([[u0, v0], [u1, v0], [u1, v1], [u0, v1]], np.float32))
+
+
 def shoelace_area(xy) -> float:
     x, y = np.asarray(xy, np.float64).T
     return 0.5 * abs(float(np.dot(x, np.roll(y, -1)) - np.dot(y, np.roll(x, -1))))
