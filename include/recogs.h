@@ -297,6 +297,23 @@ RECOGS_API void recogs_mlp_destroy(recogs_mlp* mlp);
 /* Copy the current float32 parameters to params_host_out (host, waits). */
 RECOGS_API recogs_status recogs_mlp_params(recogs_mlp* mlp, float* params_host_out);
 
+/* Training state, for checkpoint and resume: the float32 parameters, Adam's
+ * first and second moments (RECOGS_MLP_PARAMS float32 each, host) and the
+ * number of Adam steps taken. get: synchronises the device, then copies
+ * each array whose pointer is not NULL. set: checks every value first
+ * (parameters and moments finite, second moments >= 0, step >= 0; else
+ * RECOGS_EINVAL and nothing changes), then synchronises the device and
+ * replaces the state. Training is deterministic (the same batches give the
+ * same bits), so a network restored from a state taken after k steps and
+ * trained on the remaining batches ends with the bits of an uninterrupted
+ * run. */
+RECOGS_API recogs_status recogs_mlp_get_state(recogs_mlp* mlp, float* params_out,
+                                              float* adam_m_out, float* adam_v_out,
+                                              int64_t* step_out);
+RECOGS_API recogs_status recogs_mlp_set_state(recogs_mlp* mlp, const float* params,
+                                              const float* adam_m, const float* adam_v,
+                                              int64_t step);
+
 /* Features of every Gaussian of `scene` for `region` (a polygon, pixel
  * coordinates of select_camera) into features_out (device, 128 bytes per
  * Gaussian, 16-byte aligned); valid_out (device [n] bytes, 1 where
@@ -325,8 +342,9 @@ RECOGS_API recogs_status recogs_mlp_forward(recogs_mlp* mlp, const uint16_t* fea
  * uint32 sample indices; indices >= n_samples count as empty rows) of
  * features / labels (device, n_samples rows), into grad_host_out (host,
  * RECOGS_MLP_PARAMS float32) without changing the network; loss_out (host,
- * may be NULL) = the mean loss. Waits for the stream. Gradients are summed
- * with float atomics (last bits may vary). */
+ * may be NULL) = the mean loss. Waits for the stream. Deterministic: each
+ * block sums its rows in a fixed order and the block sums are added in
+ * block order (no float atomics), so the same batch gives the same bits. */
 RECOGS_API recogs_status recogs_mlp_grad(recogs_mlp* mlp, const uint16_t* features,
                                          const float* labels, int64_t n_samples,
                                          const uint32_t* rows, int64_t batch,

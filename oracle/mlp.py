@@ -254,10 +254,10 @@ def _bf16_spread(v, d):
     return np.maximum(np.abs(bf16(v - d) - h), np.abs(bf16(v + d) - h))
 
 
-def forward_bound(theta, X):
-    """Per output element, a bound on |o - forward(theta, X)["o"]| for any
-    float32 implementation that rounds at forward's points (see above).
-    Returns (forward dict, bound [n, 4])."""
+def _forward_errors(theta, X):
+    """forward() and, per element, bounds on the float32 implementation's
+    departure from it: e1, e2, e3 for z1, z2, o; dh1, dh2 for the bf16
+    activations h1, h2."""
     P = unpack(theta)
     f = forward(theta, X)
     W1, W2, W3 = bf16(P["W1"]), bf16(P["W2"]), bf16(P["W3"])
@@ -267,7 +267,15 @@ def forward_bound(theta, X):
     e2 = dh1 @ np.abs(W2) + g * ((np.abs(f["h1"]) + dh1) @ np.abs(W2) + np.abs(P["b2"]))
     dh2 = _bf16_spread(gelu(f["z2"]), GELU_SLOPE * e2 + GELU_ERR + 4 * 2.0 ** -24 * np.abs(f["z2"]))
     e3 = dh2 @ np.abs(W3) + g * ((np.abs(f["h2"]) + dh2) @ np.abs(W3) + np.abs(P["b3"]))
-    return f, e3
+    return f, dict(e1=e1, dh1=dh1, e2=e2, dh2=dh2, e3=e3)
+
+
+def forward_bound(theta, X):
+    """Per output element, a bound on |o - forward(theta, X)["o"]| for any
+    float32 implementation that rounds at forward's points (see above).
+    Returns (forward dict, bound [n, 4])."""
+    f, e = _forward_errors(theta, X)
+    return f, e["e3"]
 
 
 def loss_grad(theta, X, sel, cov, rnd=True, batch=None):
@@ -301,6 +309,75 @@ def loss_grad(theta, X, sel, cov, rnd=True, batch=None):
     g["W1"] = f["x"].T @ dz1r
     g["b1"] = dz1.sum(0)
     return loss, pack(g)
+
+
+# The backward of a float32 implementation that rounds at loss_grad's points
+# departs from it through the forward's departures (above), float32 sigmoid
+# and GELU' (SIG_ERR, GGRAD_ERR absolute: a few roundings of values below 1
+# and 1.13), their slopes (|sigmoid'| <= 1/4, |d/dp 2 (p - c) p (1 - p)| <=
+# 5/2 for p, c in [0, 1], |GELU''| <= 2 phi(0) < GELU_CURV), the float32
+# sums over the rows (any order and grouping: at most ACC_DEPTH additions
+# per term beyond the rows themselves, e.g. a block's 128 rows, its 8 warps
+# and the blocks) and the bf16 rounding of dz3, dz2, dz1, which can go to
+# the other neighbour like an activation's. A sum over the rows whose
+# grouping puts at most `depth` additions between any row's term and the
+# result (len(X) for plain sums in any order; e.g. 128 + blocks for sums of
+# blocks of 128 rows) errs by at most gamma_depth times the sum of the
+# magnitudes.
+SIG_ERR = 2.0 ** -20
+GGRAD_ERR = 2.0 ** -20
+GELU_CURV = 0.8
+
+
+def grad_bound(theta, X, sel, cov, batch=None, depth=None):
+    """loss_grad(theta, X, sel, cov, batch=batch) and, per parameter, a bound
+    on the float32 implementation's departure from its gradient; depth: the
+    most additions on any row's path in the implementation's row sums
+    (default len(X) + 8: any order).
+    Returns (loss, grad, bound), grad and bound in the parameter layout."""
+    P = unpack(theta)
+    f, e = _forward_errors(theta, X)
+    loss, grad = loss_grad(theta, X, sel, cov, batch=batch)
+    B = len(X) if batch is None else batch
+    W2r, W3r = bf16(P["W2"]), bf16(P["W3"])
+    o = f["o"]
+    y = np.asarray(sel, np.float64)
+    cv = np.asarray(cov, np.float64)
+    p = sigmoid(o)
+    dp = 0.25 * e["e3"] + SIG_ERR
+    dz3 = np.empty_like(o)
+    dz3[:, 0] = (p[:, 0] - y) / B
+    dz3[:, 1:] = 2.0 * (p[:, 1:] - cv[:, None]) * p[:, 1:] * (1 - p[:, 1:]) / B
+    d3 = (np.concatenate([dp[:, :1], 2.5 * dp[:, 1:]], 1) + 2.0 ** -21) / B
+    gr = _gamma(len(X) + 8 if depth is None else depth)
+
+    def wgrad(A, dA, D, s):
+        # |A^T D - A'^T D'| for |A - A'| <= dA, |D - D'| <= s, float32 sums
+        aA, aD = np.abs(A), np.abs(D)
+        return aA.T @ s + dA.T @ aD + dA.T @ s + gr * ((aA + dA).T @ (aD + s))
+
+    def delta(Dr, s, Wr, z, ez):
+        # dz = (Dr Wr^T) GELU'(z) with Dr within s, z within ez, float32 sums of H terms
+        a = Dr @ Wr.T
+        da = s @ np.abs(Wr).T + _gamma(Wr.shape[1] + 1) * ((np.abs(Dr) + s) @ np.abs(Wr).T)
+        gg = gelu_grad(z)
+        dgg = GELU_CURV * ez + GGRAD_ERR
+        dz = a * gg
+        return dz, da * (np.abs(gg) + dgg) + np.abs(a) * dgg + 2.0 ** -22 * np.abs(dz)
+
+    b = {}
+    s3 = _bf16_spread(dz3, d3)
+    b["W3"] = wgrad(f["h2"], e["dh2"], bf16(dz3), s3)
+    b["b3"] = d3.sum(0) + gr * np.abs(dz3).sum(0)
+    dz2, d2 = delta(bf16(dz3), s3, W3r, f["z2"], e["e2"])
+    s2 = _bf16_spread(dz2, d2)
+    b["W2"] = wgrad(f["h1"], e["dh1"], bf16(dz2), s2)
+    b["b2"] = d2.sum(0) + gr * np.abs(dz2).sum(0)
+    dz1, d1 = delta(bf16(dz2), s2, W2r, f["z1"], e["e1"])
+    s1 = _bf16_spread(dz1, d1)
+    b["W1"] = wgrad(f["x"], np.zeros_like(f["x"]), bf16(dz1), s1)
+    b["b1"] = d1.sum(0) + gr * np.abs(dz1).sum(0)
+    return loss, grad, pack(b)
 
 
 def decisions(o, plain_sel, valid, delta):

@@ -124,6 +124,10 @@ SIGNATURES = {
     "recogs_mlp_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_void_p)]),
     "recogs_mlp_destroy": (None, [C.c_void_p]),
     "recogs_mlp_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "recogs_mlp_get_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                       C.POINTER(C.c_float), C.POINTER(C.c_int64)]),
+    "recogs_mlp_set_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                       C.POINTER(C.c_float), C.c_int64]),
     "recogs_mlp_features": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.POINTER(CCamera),
                                       C.POINTER(CRegion), C.c_void_p, C.c_void_p, C.c_void_p]),
     "recogs_mlp_labels": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.POINTER(CCamera),
@@ -554,6 +558,41 @@ class Mlp:
         self.ctx._check(self.ctx._L.recogs_mlp_params(self._h,
                                                       out.ctypes.data_as(C.POINTER(C.c_float))))
         return out
+
+    def state(self) -> dict:
+        """Training state: params, Adam moments m and v (float32) and step."""
+        fp = C.POINTER(C.c_float)
+        arrs = {k: np.zeros(MLP_PARAMS, np.float32) for k in ("params", "m", "v")}
+        step = C.c_int64()
+        self.ctx._check(self.ctx._L.recogs_mlp_get_state(
+            self._h, arrs["params"].ctypes.data_as(fp), arrs["m"].ctypes.data_as(fp),
+            arrs["v"].ctypes.data_as(fp), C.byref(step)))
+        return dict(arrs, step=int(step.value))
+
+    def set_state(self, state: dict):
+        fp = C.POINTER(C.c_float)
+        a = [np.ascontiguousarray(np.asarray(state[k], np.float32).reshape(-1))
+             for k in ("params", "m", "v")]
+        if any(x.size != MLP_PARAMS for x in a):
+            raise ValueError(f"each state array holds {MLP_PARAMS} values")
+        self.ctx._check(self.ctx._L.recogs_mlp_set_state(
+            self._h, a[0].ctypes.data_as(fp), a[1].ctypes.data_as(fp), a[2].ctypes.data_as(fp),
+            int(state["step"])))
+
+    def save(self, path):
+        """Checkpoint the training state to an .npz file."""
+        st = self.state()
+        np.savez(path, params=st["params"], m=st["m"], v=st["v"], step=np.int64(st["step"]))
+
+    @classmethod
+    def load(cls, ctx: "Context", path) -> "Mlp":
+        """A network on ctx with the training state saved by save()."""
+        with np.load(path) as z:
+            st = {k: z[k] for k in ("params", "m", "v")}
+            st["step"] = int(z["step"])
+        net = cls(ctx, st["params"])
+        net.set_state(st)
+        return net
 
     def forward(self, features, out=None, stream=None):
         import torch

@@ -1542,7 +1542,9 @@ struct recogs_mlp {
     float* loss = nullptr;       // device scalar
     MlpFrags* frags = nullptr;
     unsigned long long* fallbacks = nullptr;   // [0] fallback count, [1] fused kernel's error word
-    int64_t step = 0;
+    float* partials = nullptr;   // training: per-block gradient partials
+    size_t partials_bytes = 0;
+    int64_t step = 0;            // Adam steps taken
 };
 
 namespace {
@@ -1614,7 +1616,7 @@ void recogs_mlp_destroy(recogs_mlp* m) {
     if (!m) return;
     DeviceGuard g(m->ctx->device);
     cudaDeviceSynchronize();
-    void* ps[] = {m->params, m->m, m->v, m->grad, m->loss, m->frags, m->fallbacks};
+    void* ps[] = {m->params, m->m, m->v, m->grad, m->loss, m->frags, m->fallbacks, m->partials};
     for (void* p : ps)
         if (p) cudaFree(p);
     delete m;
@@ -1625,6 +1627,46 @@ recogs_status recogs_mlp_params(recogs_mlp* m, float* params_host_out) {
     recogs_ctx* ctx = m->ctx;
     DeviceGuard g(ctx->device);
     CK(cudaMemcpy(params_host_out, m->params, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost));
+    return RECOGS_OK;
+}
+
+recogs_status recogs_mlp_get_state(recogs_mlp* m, float* params_out, float* adam_m_out,
+                                   float* adam_v_out, int64_t* step_out) {
+    if (!m) return RECOGS_EINVAL;
+    recogs_ctx* ctx = m->ctx;
+    DeviceGuard g(ctx->device);
+    // the device copies are ordered after all work on the legacy stream;
+    // finish work on other streams first
+    CK(cudaDeviceSynchronize());
+    const size_t pb = sizeof(float) * kMlpParams;
+    if (params_out) CK(cudaMemcpy(params_out, m->params, pb, cudaMemcpyDeviceToHost));
+    if (adam_m_out) CK(cudaMemcpy(adam_m_out, m->m, pb, cudaMemcpyDeviceToHost));
+    if (adam_v_out) CK(cudaMemcpy(adam_v_out, m->v, pb, cudaMemcpyDeviceToHost));
+    if (step_out) *step_out = m->step;
+    return RECOGS_OK;
+}
+
+recogs_status recogs_mlp_set_state(recogs_mlp* m, const float* params, const float* adam_m,
+                                   const float* adam_v, int64_t step) {
+    if (!m) return RECOGS_EINVAL;
+    recogs_ctx* ctx = m->ctx;
+    if (!params || !adam_m || !adam_v) return fail(ctx, RECOGS_EINVAL, "a state array is NULL");
+    if (step < 0) return fail(ctx, RECOGS_EINVAL, "step < 0");
+    for (int k = 0; k < kMlpParams; ++k) {
+        if (!finite(params[k]) || !finite(adam_m[k]))
+            return fail(ctx, RECOGS_EINVAL, "a parameter or first moment is not finite");
+        if (!finite(adam_v[k]) || adam_v[k] < 0.f)
+            return fail(ctx, RECOGS_EINVAL, "a second moment is negative or not finite");
+    }
+    DeviceGuard g(ctx->device);
+    CK(cudaDeviceSynchronize());
+    const size_t pb = sizeof(float) * kMlpParams;
+    CK(cudaMemcpy(m->params, params, pb, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->m, adam_m, pb, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->v, adam_v, pb, cudaMemcpyHostToDevice));
+    launch_mlp_pack(m->params, m->frags, 0);
+    CK(cudaDeviceSynchronize());
+    m->step = step;
     return RECOGS_OK;
 }
 
@@ -1716,10 +1758,24 @@ static recogs_status mlp_batch_grad(recogs_mlp* m, const uint16_t* features, con
     if (!features || !labels || !rows || !aligned(features, 16) || !aligned(labels, 8) ||
         !aligned(rows, 4))
         return fail(ctx, RECOGS_EINVAL, "features, labels or rows NULL or misaligned");
-    CK(cudaMemsetAsync(m->loss, 0, sizeof(float), st));
+    const size_t need = mlp_partials_bytes(batch);
+    if (need > m->partials_bytes) {
+        if (m->partials) {
+            CK(cudaStreamSynchronize(st));
+            CK(cudaFree(m->partials));
+            m->partials = nullptr;
+            m->partials_bytes = 0;
+        }
+        if (cudaMalloc(&m->partials, need) != cudaSuccess) {
+            cudaGetLastError();
+            m->partials = nullptr;
+            return fail(ctx, RECOGS_ENOMEM, "MLP gradient partials (%zu bytes)", need);
+        }
+        m->partials_bytes = need;
+    }
     stage_begin(ctx, ST_MLP, st);
     const int l = launch_mlp_train(reinterpret_cast<const uint32_t*>(features), labels, n_samples,
-                                   rows, batch, m->frags, m->grad, m->loss, st);
+                                   rows, batch, m->frags, m->partials, m->grad, m->loss, st);
     stage_end(ctx, ST_MLP, l, st);
     CK(cudaGetLastError());
     if (loss_out) {
@@ -1742,7 +1798,6 @@ recogs_status recogs_mlp_grad(recogs_mlp* m, const uint16_t* features, const flo
     CKS(mlp_batch_grad(m, features, labels, n_samples, rows, batch, loss_out, st));
     CK(cudaMemcpyAsync(grad_host_out, m->grad, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost,
                        st));
-    CK(cudaMemsetAsync(m->grad, 0, sizeof(float) * kMlpParams, st));
     CK(cudaStreamSynchronize(st));
     return RECOGS_OK;
 }

@@ -240,18 +240,22 @@ __global__ void __launch_bounds__(256) mlp_forward_kernel(const uint32_t* __rest
 }
 
 // ---------------------------------------------------------------------------
-// training: forward, loss, backward and the batch's gradient (atomically
-// added to grad[kMlpParams]); rows[b] = sample of batch position b
+// training: forward, loss, backward and the batch's gradient; rows[b] =
+// sample of batch position b. The gradient is deterministic: every block
+// sums its chunks of 128 rows in a fixed order into its own partial (no
+// float atomics), and a second kernel adds the partials in block order, so
+// the same batch gives the same bits on every call (checkpoint and resume
+// reproduce an uninterrupted run exactly).
 
-constexpr int kTrainRows = 128;          // rows per block (8 warps x 16)
+constexpr int kTrainRows = 128;          // rows per chunk (8 warps x 16)
 constexpr int kTStride = kTrainRows + 8; // bf16 row stride of the transposed operands
 
 struct TrainSmem {
     MlpFrags f;
     __nv_bfloat16 XT[64 * kTStride], H1T[64 * kTStride], H2T[64 * kTStride];
     __nv_bfloat16 D1T[64 * kTStride], D2T[64 * kTStride], D3T[8 * kTStride];
-    float gb[64 + 64 + 8];   // bias gradients of the block (layer 3 padded to 8 columns)
-    float loss;
+    float gbw[8][64 + 64 + 8];   // bias gradients per warp (layer 3 padded to 8 columns)
+    float lossw[8];              // loss per warp
 };
 
 // scatter a C fragment's values (rows g, g+8 of the warp's tile, columns
@@ -283,7 +287,8 @@ __device__ __forceinline__ void store_at(__nv_bfloat16* T, int rbase, int kt, co
     T[(col + 9) * kTStride + rbase + g + 8] = hi(a[3]);
 }
 
-// column sums over the warp's 16 rows of a C fragment tile, added to acc[col]
+// column sums over the warp's 16 rows of a C fragment tile, added to the
+// warp's own acc[col] (each column of a warp has one writer)
 __device__ __forceinline__ void bias_grad(const float (&c)[4], int nt, float* acc, int lane) {
     float s0 = c[0] + c[2], s1 = c[1] + c[3];
 #pragma unroll
@@ -292,8 +297,8 @@ __device__ __forceinline__ void bias_grad(const float (&c)[4], int nt, float* ac
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
     }
     if (lane < 4) {
-        atomicAdd(&acc[8 * nt + 2 * lane], s0);
-        atomicAdd(&acc[8 * nt + 2 * lane + 1], s1);
+        acc[8 * nt + 2 * lane] += s0;
+        acc[8 * nt + 2 * lane + 1] += s1;
     }
 }
 
@@ -314,150 +319,186 @@ __device__ __forceinline__ void wgrad_tile(float (&acc)[4], const __nv_bfloat16*
     }
 }
 
-__device__ __forceinline__ void wgrad_flush(const float (&acc)[4], float* grad, int ncols,
-                                            int mt, int nt, int lane) {
+// store a weight-gradient tile into the block's partial (one writer per element)
+__device__ __forceinline__ void wgrad_flush(const float (&acc)[4], float* part, int ncols, int mt,
+                                            int nt, int lane) {
     const int g = lane >> 2, t = lane & 3;
     const int m0 = 16 * mt + g, n0 = 8 * nt + 2 * t;
     if (n0 < ncols) {
-        atomicAdd(&grad[m0 * ncols + n0], acc[0]);
-        atomicAdd(&grad[(m0 + 8) * ncols + n0], acc[2]);
+        part[m0 * ncols + n0] = acc[0];
+        part[(m0 + 8) * ncols + n0] = acc[2];
     }
     if (n0 + 1 < ncols) {
-        atomicAdd(&grad[m0 * ncols + n0 + 1], acc[1]);
-        atomicAdd(&grad[(m0 + 8) * ncols + n0 + 1], acc[3]);
+        part[m0 * ncols + n0 + 1] = acc[1];
+        part[(m0 + 8) * ncols + n0 + 1] = acc[3];
     }
 }
+
+// a block's partial: the kMlpParams gradient sums and the loss, padded to 16 bytes
+constexpr int kPartStride = (kMlpParams + 1 + 3) / 4 * 4;
+constexpr int kMaxTrainBlocks = 512;   // partials kept (larger batches loop in each block)
 
 __global__ void __launch_bounds__(256, 1)
     mlp_train_kernel(const uint32_t* __restrict__ X, const float* __restrict__ labels,
                      int64_t n_samples, const uint32_t* __restrict__ rows, int64_t batch,
-                     const MlpFrags* __restrict__ frags, float* __restrict__ grad,
-                     float* __restrict__ loss_sum) {
+                     const MlpFrags* __restrict__ frags, float* __restrict__ partials) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TrainSmem& s = *reinterpret_cast<TrainSmem*>(smem_raw);
     load_frags(&s.f, frags);
-    for (int k = threadIdx.x; k < 136; k += blockDim.x) s.gb[k] = 0.f;
-    if (threadIdx.x == 0) s.loss = 0.f;
+    for (int k = threadIdx.x; k < 8 * 136; k += blockDim.x) (&s.gbw[0][0])[k] = 0.f;
+    if (threadIdx.x < 8) s.lossw[threadIdx.x] = 0.f;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
     const float inv_b = 1.0f / (float)batch;
-    const int64_t b0 = (int64_t)blockIdx.x * kTrainRows + warp * 16;
     const int rbase = warp * 16;
-    const int64_t p0 = b0 + g, p1 = b0 + g + 8;      // batch positions of this lane's rows
-    // rows outside the samples are treated as padding
-    int64_t r0 = p0 < batch ? (int64_t)rows[p0] : -1;
-    int64_t r1 = p1 < batch ? (int64_t)rows[p1] : -1;
-    if (r0 >= n_samples) r0 = -1;
-    if (r1 >= n_samples) r1 = -1;
-
-    // forward
-    uint32_t xa[4][4];
-    load_x(X, r0, r1, xa, lane);
-    WarpFwd w;
-    warp_forward(xa, s.f, w, lane);
+    float* gbw = s.gbw[warp];
+    // weight-gradient tiles of this warp, summed over the block's chunks:
+    // warp w owns m-tile w / 2 and n-tiles 4 (w % 2) .. +3 of dW1 and dW2,
+    // and m-tile w of dW3 (warps 0..3)
+    const int mt = warp >> 1, nt0 = 4 * (warp & 1);
+    float aw1[4][4], aw2[4][4], aw3[4];
 #pragma unroll
-    for (int kt = 0; kt < 4; ++kt) {
-        store_at(s.XT, rbase, kt, xa[kt], lane);
-        store_at(s.H1T, rbase, kt, w.h1[kt], lane);
-        store_at(s.H2T, rbase, kt, w.h2[kt], lane);
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) aw1[q][e] = aw2[q][e] = 0.f;
+        aw3[q] = 0.f;
     }
+    const int64_t n_chunks = (batch + kTrainRows - 1) / kTrainRows;
 
-    // loss and dL/do: BCE on o0, squared error of sigmoid(o_c) against the coverage
-    float d3[4] = {0.f, 0.f, 0.f, 0.f};
-    float l = 0.f;
-    if (t < 2) {
+    for (int64_t chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
+        const int64_t b0 = chunk * kTrainRows + warp * 16;
+        const int64_t p0 = b0 + g, p1 = b0 + g + 8;      // batch positions of this lane's rows
+        // rows outside the samples are treated as padding
+        int64_t r0 = p0 < batch ? (int64_t)rows[p0] : -1;
+        int64_t r1 = p1 < batch ? (int64_t)rows[p1] : -1;
+        if (r0 >= n_samples) r0 = -1;
+        if (r1 >= n_samples) r1 = -1;
+
+        // forward
+        uint32_t xa[4][4];
+        load_x(X, r0, r1, xa, lane);
+        WarpFwd w;
+        warp_forward(xa, s.f, w, lane);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t r = h ? r1 : r0;
-            if (r < 0) continue;
-            const float sel = labels[2 * r], cov = labels[2 * r + 1];
+        for (int kt = 0; kt < 4; ++kt) {
+            store_at(s.XT, rbase, kt, xa[kt], lane);
+            store_at(s.H1T, rbase, kt, w.h1[kt], lane);
+            store_at(s.H2T, rbase, kt, w.h2[kt], lane);
+        }
+
+        // loss and dL/do: BCE on o0, squared error of sigmoid(o_c) against the coverage
+        float d3[4] = {0.f, 0.f, 0.f, 0.f};
+        float l = 0.f;
+        if (t < 2) {
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int col = 2 * t + q;
-                const float o = w.o[2 * h + q];
-                const float p = sigmoidf(o);
-                if (col == 0) {
-                    l += fmaxf(o, 0.f) - sel * o + log1pf(expf(-fabsf(o)));
-                    d3[2 * h + q] = (p - sel) * inv_b;
-                } else {
-                    l += (p - cov) * (p - cov);
-                    d3[2 * h + q] = 2.0f * (p - cov) * p * (1.0f - p) * inv_b;
+            for (int h = 0; h < 2; ++h) {
+                const int64_t r = h ? r1 : r0;
+                if (r < 0) continue;
+                const float sel = labels[2 * r], cov = labels[2 * r + 1];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int col = 2 * t + q;
+                    const float o = w.o[2 * h + q];
+                    const float p = sigmoidf(o);
+                    if (col == 0) {
+                        l += fmaxf(o, 0.f) - sel * o + log1pf(expf(-fabsf(o)));
+                        d3[2 * h + q] = (p - sel) * inv_b;
+                    } else {
+                        l += (p - cov) * (p - cov);
+                        d3[2 * h + q] = 2.0f * (p - cov) * p * (1.0f - p) * inv_b;
+                    }
                 }
             }
         }
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-    if (lane == 0) atomicAdd(&s.loss, l);
-    bias_grad(d3, 0, s.gb + 128, lane);   // columns 0..7 (4..7 are zero)
-    store_ct(s.D3T, rbase, 0, d3, lane);
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+        if (lane == 0) s.lossw[warp] += l;
+        bias_grad(d3, 0, gbw + 128, lane);   // columns 0..7 (4..7 are zero)
+        store_ct(s.D3T, rbase, 0, d3, lane);
 
-    // dh2 = dz3 W3^T, dz2 = dh2 gelu'(z2)
-    float dz2[8][4];
-    {
-        const uint32_t a0 = pack_bf16(d3[0], d3[1]), a1 = pack_bf16(d3[2], d3[3]);
+        // dh2 = dz3 W3^T, dz2 = dh2 gelu'(z2)
+        float dz2[8][4];
+        {
+            const uint32_t a0 = pack_bf16(d3[0], d3[1]), a1 = pack_bf16(d3[2], d3[3]);
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            dz2[nt][0] = dz2[nt][1] = dz2[nt][2] = dz2[nt][3] = 0.f;
-            const uint2 b = *reinterpret_cast<const uint2*>(s.f.G3 + 2 * (nt * 32 + lane));
-            mma_bf16(dz2[nt], a0, a1, 0u, 0u, b.x, b.y);
+            for (int nt = 0; nt < 8; ++nt) {
+                dz2[nt][0] = dz2[nt][1] = dz2[nt][2] = dz2[nt][3] = 0.f;
+                const uint2 b = *reinterpret_cast<const uint2*>(s.f.G3 + 2 * (nt * 32 + lane));
+                mma_bf16(dz2[nt], a0, a1, 0u, 0u, b.x, b.y);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) dz2[nt][e] *= gelu_grad(w.z2[nt][e]);
-            bias_grad(dz2[nt], nt, s.gb + 64, lane);
-            store_ct(s.D2T, rbase, nt, dz2[nt], lane);
+                for (int e = 0; e < 4; ++e) dz2[nt][e] *= gelu_grad(w.z2[nt][e]);
+                bias_grad(dz2[nt], nt, gbw + 64, lane);
+                store_ct(s.D2T, rbase, nt, dz2[nt], lane);
+            }
         }
-    }
-    // dh1 = dz2 W2^T, dz1 = dh1 gelu'(z1)
-    {
-        uint32_t a[4][4];
-        c_to_a(dz2, a, [](float v) { return v; });
-        float dz1[8][4];
-        layer_mma(dz1, a, s.f.G2, nullptr, lane);
+        // dh1 = dz2 W2^T, dz1 = dh1 gelu'(z1)
+        {
+            uint32_t a[4][4];
+            c_to_a(dz2, a, [](float v) { return v; });
+            float dz1[8][4];
+            layer_mma(dz1, a, s.f.G2, nullptr, lane);
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
+            for (int nt = 0; nt < 8; ++nt) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) dz1[nt][e] *= gelu_grad(w.z1[nt][e]);
-            bias_grad(dz1[nt], nt, s.gb, lane);
-            store_ct(s.D1T, rbase, nt, dz1[nt], lane);
+                for (int e = 0; e < 4; ++e) dz1[nt][e] *= gelu_grad(w.z1[nt][e]);
+                bias_grad(dz1[nt], nt, gbw, lane);
+                store_ct(s.D1T, rbase, nt, dz1[nt], lane);
+            }
         }
-    }
-    __syncthreads();
+        __syncthreads();
 
-    // weight gradients over the block's 128 rows: dW = A^T dZ; warp w owns
-    // m-tile w / 2 and n-tiles 4 (w % 2) .. +3 of dW1 and dW2, and m-tile w
-    // of dW3 (warps 0..3)
-    {
-        const int mt = warp >> 1, nt0 = 4 * (warp & 1);
+        // weight gradients over the chunk's 128 rows: dW += A^T dZ
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            wgrad_tile(acc, s.XT, mt, s.D1T, nt0 + q, lane);
-            wgrad_flush(acc, grad + kOffW1, 64, mt, nt0 + q, lane);
-        }
+        for (int q = 0; q < 4; ++q) wgrad_tile(aw1[q], s.XT, mt, s.D1T, nt0 + q, lane);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            wgrad_tile(acc, s.H1T, mt, s.D2T, nt0 + q, lane);
-            wgrad_flush(acc, grad + kOffW2, 64, mt, nt0 + q, lane);
-        }
-        if (warp < 4) {
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            wgrad_tile(acc, s.H2T, warp, s.D3T, 0, lane);
-            wgrad_flush(acc, grad + kOffW3, 4, warp, 0, lane);
-        }
+        for (int q = 0; q < 4; ++q) wgrad_tile(aw2[q], s.H1T, mt, s.D2T, nt0 + q, lane);
+        if (warp < 4) wgrad_tile(aw3, s.H2T, warp, s.D3T, 0, lane);
+        __syncthreads();   // the next chunk rewrites the operands
     }
+
+    float* part = partials + (size_t)blockIdx.x * kPartStride;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        wgrad_flush(aw1[q], part + kOffW1, 64, mt, nt0 + q, lane);
+        wgrad_flush(aw2[q], part + kOffW2, 64, mt, nt0 + q, lane);
+    }
+    if (warp < 4) wgrad_flush(aw3, part + kOffW3, 4, warp, 0, lane);
+    // biases and loss: the warps' sums added in warp order
     for (int k = threadIdx.x; k < 132; k += blockDim.x) {
         const int off = k < 64 ? kOffB1 + k : k < 128 ? kOffB2 + (k - 64) : kOffB3 + (k - 128);
-        atomicAdd(&grad[off], s.gb[k]);
+        float sum = 0.f;
+#pragma unroll
+        for (int ww = 0; ww < 8; ++ww) sum += s.gbw[ww][k];
+        part[off] = sum;
     }
-    if (threadIdx.x == 0) atomicAdd(loss_sum, s.loss);
+    if (threadIdx.x == 0) {
+        float sum = 0.f;
+#pragma unroll
+        for (int ww = 0; ww < 8; ++ww) sum += s.lossw[ww];
+        part[kMlpParams] = sum;
+    }
 }
 
-// Adam on the parameters (Kingma and Ba, 2015), gradient cleared after use
+// the batch's gradient and loss: the blocks' partials added in block order
+__global__ void __launch_bounds__(256) mlp_reduce_kernel(const float* __restrict__ partials,
+                                                         int nb, float* __restrict__ grad,
+                                                         float* __restrict__ loss) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > kMlpParams) return;
+    float sum = 0.f;
+#pragma unroll 8
+    for (int b = 0; b < nb; ++b) sum += partials[(size_t)b * kPartStride + i];
+    if (i < kMlpParams)
+        grad[i] = sum;
+    else
+        *loss = sum;
+}
+
+// Adam on the parameters (Kingma and Ba, 2015)
 __global__ void __launch_bounds__(256) mlp_adam_kernel(float* __restrict__ p, float* __restrict__ m,
                                                        float* __restrict__ v,
-                                                       float* __restrict__ grad, float lr,
+                                                       const float* __restrict__ grad, float lr,
                                                        float beta1, float beta2, float eps,
                                                        float inv_bc1, float inv_bc2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -468,7 +509,6 @@ __global__ void __launch_bounds__(256) mlp_adam_kernel(float* __restrict__ p, fl
     m[i] = mm;
     v[i] = vv;
     p[i] -= lr * (mm * inv_bc1) / (sqrtf(vv * inv_bc2) + eps);
-    grad[i] = 0.f;
 }
 
 // ---------------------------------------------------------------------------
@@ -1012,7 +1052,12 @@ __global__ void __launch_bounds__(kSelThreads, RECOGS_SEL_MIN_BLOCKS)
         const uint32_t nfb = __popc(__ballot_sync(0xffffffffu, fb));
         if (lane == 0 && nfb) atomicAdd(fallbacks, (unsigned long long)nfb);
     }
-    if (!alive && t == 0) atomicOr(error, 1u);
+    if (!alive) {
+        if (t == 0) atomicOr(error, 1u);
+        // the MMAs of the abandoned wait may still be in flight: wait for
+        // their commit once more (bounded) before the TMEM is freed
+        mbar_wait(&sm.bar, phase ^ 1u);
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -1084,21 +1129,31 @@ int launch_mlp_forward(const uint32_t* X, int64_t n, const MlpFrags* frags, floa
     return 1;
 }
 
+int64_t mlp_train_blocks(int64_t batch) {
+    const int64_t chunks = (batch + kTrainRows - 1) / kTrainRows;
+    return chunks < kMaxTrainBlocks ? chunks : kMaxTrainBlocks;
+}
+
+size_t mlp_partials_bytes(int64_t batch) {
+    return sizeof(float) * (size_t)kPartStride * (size_t)mlp_train_blocks(batch);
+}
+
 int launch_mlp_train(const uint32_t* X, const float* labels, int64_t n_samples,
-                     const uint32_t* rows, int64_t batch, const MlpFrags* frags, float* grad,
-                     float* loss_sum, cudaStream_t st) {
+                     const uint32_t* rows, int64_t batch, const MlpFrags* frags, float* partials,
+                     float* grad, float* loss_sum, cudaStream_t st) {
     if (batch == 0) return 0;
     const int smem = (int)sizeof(TrainSmem);
     static std::atomic<uint64_t> opted{0};
     smem_opt_in(mlp_train_kernel, smem, opted);
-    const int64_t g = (batch + kTrainRows - 1) / kTrainRows;
-    mlp_train_kernel<<<(unsigned)g, 256, smem, st>>>(X, labels, n_samples, rows, batch, frags, grad,
-                                                     loss_sum);
-    return 1;
+    const int nb = (int)mlp_train_blocks(batch);
+    mlp_train_kernel<<<(unsigned)nb, 256, smem, st>>>(X, labels, n_samples, rows, batch, frags,
+                                                      partials);
+    mlp_reduce_kernel<<<(kMlpParams + 1 + 255) / 256, 256, 0, st>>>(partials, nb, grad, loss_sum);
+    return 2;
 }
 
-int launch_mlp_adam(float* p, float* m, float* v, float* grad, float lr, float beta1, float beta2,
-                    float eps, float inv_bc1, float inv_bc2, cudaStream_t st) {
+int launch_mlp_adam(float* p, float* m, float* v, const float* grad, float lr, float beta1,
+                    float beta2, float eps, float inv_bc1, float inv_bc2, cudaStream_t st) {
     mlp_adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, st>>>(p, m, v, grad, lr, beta1, beta2,
                                                               eps, inv_bc1, inv_bc2);
     return 1;

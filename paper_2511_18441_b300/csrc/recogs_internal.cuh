@@ -455,11 +455,14 @@ size_t mlp_frags_bytes();
 int launch_mlp_pack(const float* params, MlpFrags* frags, cudaStream_t st);
 int launch_mlp_forward(const uint32_t* X, int64_t n, const MlpFrags* frags, float* out,
                        cudaStream_t st);
+// Training: per-block partial sums (mlp_partials_bytes of scratch), added in
+// block order into grad[kMlpParams] and *loss_sum (overwritten, not accumulated).
+size_t mlp_partials_bytes(int64_t batch);
 int launch_mlp_train(const uint32_t* X, const float* labels, int64_t n_samples,
-                     const uint32_t* rows, int64_t batch, const MlpFrags* frags, float* grad,
-                     float* loss_sum, cudaStream_t st);
-int launch_mlp_adam(float* p, float* m, float* v, float* grad, float lr, float beta1, float beta2,
-                    float eps, float inv_bc1, float inv_bc2, cudaStream_t st);
+                     const uint32_t* rows, int64_t batch, const MlpFrags* frags, float* partials,
+                     float* grad, float* loss_sum, cudaStream_t st);
+int launch_mlp_adam(float* p, float* m, float* v, const float* grad, float lr, float beta1,
+                    float beta2, float eps, float inv_bc1, float inv_bc2, cudaStream_t st);
 int launch_mlp_features(const recogs_scene& s, const DevCamera& cam, const DevRegion& reg,
                         const MlpRegionFrame& fr, uint32_t* X, uint8_t* valid, cudaStream_t st);
 int launch_mlp_labels(const recogs_scene& s, const DevCamera& cam, const DevRegion& reg,

@@ -10,8 +10,9 @@ tint-weight labels (sums of (alpha T)^2 over float32 and FP64 renders)
 within 1e-3 for 99% of the Gaussians (the rest reach pixels whose render the
 oracle flags);
 network outputs and gradients are compared on the GPU's own bf16 features,
-so they differ only by the accumulation order and an occasional flipped bf16
-rounding of an activation.
+element by element within the bounds oracle/mlp.py derives for a float32
+implementation (accumulation order, GELU and sigmoid in float32, bf16
+roundings that go the other way).
 """
 import math
 
@@ -140,7 +141,21 @@ def test_fused_selection_against_the_oracle(lib, ctx):
     net.close()
 
 
-def test_gradient_matches_the_oracle(lib, ctx):
+def gpu_sum_depth(batch):
+    """The most additions on a row's path through the training kernel's
+    sums: 128 rows of a chunk (tensor-core k-steps, or 16 rows by shuffles
+    plus 8 warps for the biases), the chunks of a block, the blocks."""
+    chunks = -(-batch // 128)
+    blocks = min(chunks, 512)
+    return 128 + 8 + 4 + -(-chunks // blocks) + blocks
+
+
+@pytest.mark.parametrize("batch", [1000, 70_000])
+def test_gradient_matches_the_oracle(lib, ctx, batch):
+    """Every gradient element within oracle.mlp.grad_bound of the FP64
+    gradient (the float32 departures the bound derives, on the GPU's own
+    bf16 features), twice with the same bits; 70,000 rows run more chunks
+    than the kernel has blocks."""
     scene, cam = scene_and_view(n=6000)
     reg = sg.random_polygons(1, cam.width, cam.height, 5)[0]
     ds = lib.DeviceScene.from_numpy(scene, "cuda", "f32")
@@ -149,26 +164,125 @@ def test_gradient_matches_the_oracle(lib, ctx):
     net = ctx.mlp(theta)
     rng = np.random.default_rng(0)
     valid = np.flatnonzero(parity.to_np(V))
-    rows = rng.choice(valid, 1000, replace=True).astype(np.uint32)   # duplicates allowed
-    g, loss = net.grad(F, L, torch.from_numpy(rows).cuda())
+    rows = rng.choice(valid, batch, replace=True).astype(np.uint32)   # duplicates allowed
+    rows_d = torch.from_numpy(rows).cuda()
+    g, loss = net.grad(F, L, rows_d)
+    g_again, _ = net.grad(F, L, rows_d)
+    np.testing.assert_array_equal(g, g_again)          # deterministic sums
     X = F.float().cpu().numpy().astype(np.float64)[rows]
     Lh = parity.to_np(L).astype(np.float64)[rows]
-    loss_o, g_o = omlp.loss_grad(theta.astype(np.float64), X, Lh[:, 0], Lh[:, 1])
+    loss_o, g_o, bound = omlp.grad_bound(theta.astype(np.float64), X, Lh[:, 0], Lh[:, 1],
+                                         depth=gpu_sum_depth(batch))
     assert loss == pytest.approx(loss_o, rel=1e-4)
-    scale = np.abs(g_o).max()
     err = np.abs(g - g_o)
-    assert (err <= 1e-3 * scale + 1e-2 * np.abs(g_o)).mean() >= 0.99, err.max() / scale
-    assert err.max() <= 2e-2 * scale
+    assert np.all(err <= bound), (err / np.maximum(bound, 1e-30)).max()
     # rows outside the samples are empty rows (they only count in the batch size)
     rows2 = np.concatenate([rows, [10 ** 9]]).astype(np.uint32)
     g2, loss2 = net.grad(F, L, torch.from_numpy(rows2).cuda())
-    loss2_o, g2_o = omlp.loss_grad(theta.astype(np.float64), X, Lh[:, 0], Lh[:, 1], batch=1001)
+    loss2_o, g2_o, bound2 = omlp.grad_bound(theta.astype(np.float64), X, Lh[:, 0], Lh[:, 1],
+                                            batch=batch + 1, depth=gpu_sum_depth(batch + 1))
     assert loss2 == pytest.approx(loss2_o, rel=1e-4)
-    err2 = np.abs(g2 - g2_o)
-    assert (err2 <= 1e-3 * scale + 1e-2 * np.abs(g2_o)).mean() >= 0.99
-    assert err2.max() <= 2e-2 * scale
+    assert np.all(np.abs(g2 - g2_o) <= bound2)
     # the gradient call leaves the network unchanged
     np.testing.assert_array_equal(net.params(), theta)
+    net.close()
+
+
+def test_training_resumes_from_a_checkpoint_bit_for_bit(lib, ctx, tmp_path):
+    """12 Adam steps straight, against 5 steps, a checkpoint file, a new
+    context restoring it and the remaining 7 steps: the same parameters,
+    moments and step count, bit for bit (training is deterministic)."""
+    scene, cam = scene_and_view(n=20_000)
+    reg = sg.random_polygons(1, cam.width, cam.height, 3)[0]
+    ds = lib.DeviceScene.from_numpy(scene, "cuda", "f32")
+    F, L, V = ctx.mlp_features(ds, cam, reg)
+    valid = np.flatnonzero(parity.to_np(V))
+    rng = np.random.default_rng(5)
+    batches = [torch.from_numpy(rng.choice(valid, 4096).astype(np.uint32)).cuda()
+               for _ in range(12)]
+    theta = rand_params(3)
+
+    def run(net, bs):
+        for r in bs:
+            net.train_step(F, L, r, lr=2e-3)
+
+    straight = ctx.mlp(theta)
+    run(straight, batches)
+    want = straight.state()
+    assert want["step"] == 12 and not np.array_equal(want["params"], theta)
+    again = ctx.mlp(theta)
+    run(again, batches)
+    got = again.state()
+    for k in ("params", "m", "v"):
+        np.testing.assert_array_equal(got[k], want[k])
+    first = ctx.mlp(theta)
+    run(first, batches[:5])
+    first.save(tmp_path / "mlp.npz")
+    first.close()
+    ctx2 = lib.Context(0)
+    resumed = lib.Mlp.load(ctx2, tmp_path / "mlp.npz")
+    assert resumed.state()["step"] == 5
+    run(resumed, batches[5:])
+    got = resumed.state()
+    assert got["step"] == 12
+    for k in ("params", "m", "v"):
+        np.testing.assert_array_equal(got[k], want[k])
+    resumed.close()
+    ctx2.close()
+    straight.close()
+    again.close()
+
+
+def test_a_training_step_is_adam_on_the_batch_gradient(lib, ctx):
+    """Two train steps against oracle.adam_step (FP64) applied to the GPU's
+    own gradients of the same batches (the same bits, since the sums are
+    deterministic): parameters within a few float32 roundings of the
+    update and of the value, moments within float32 roundings."""
+    scene, cam = scene_and_view(n=6000)
+    reg = sg.random_polygons(1, cam.width, cam.height, 9)[0]
+    ds = lib.DeviceScene.from_numpy(scene, "cuda", "f32")
+    F, L, V = ctx.mlp_features(ds, cam, reg)
+    valid = np.flatnonzero(parity.to_np(V))
+    rng = np.random.default_rng(8)
+    theta = rand_params(6)
+    net = ctx.mlp(theta)
+    p = theta.astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    # the hyper-parameters as the float32 values the call passes
+    lr, b1, b2, eps = (float(np.float32(x)) for x in (3e-3, 0.9, 0.999, 1e-8))
+    for t in (1, 2):
+        rows = torch.from_numpy(rng.choice(valid, 2048).astype(np.uint32)).cuda()
+        g, _ = net.grad(F, L, rows)
+        net.train_step(F, L, rows, lr=lr, beta1=b1, beta2=b2, eps=eps)
+        p_prev = p
+        p, m, v = oracle.adam_step(p, g.astype(np.float64), m, v, t, lr, beta1=b1, beta2=b2,
+                                   eps=eps)
+        st = net.state()
+        assert st["step"] == t
+        tol = 2.0 ** -20 * (lr + np.abs(p_prev)) + 2.0 ** -22 * np.abs(p)
+        assert np.all(np.abs(st["params"] - p) <= tol)
+        assert np.all(np.abs(st["m"] - m) <= 2.0 ** -21 * (np.abs(m) + np.abs(g)))
+        assert np.all(np.abs(st["v"] - v) <= 2.0 ** -21 * (np.abs(v) + g.astype(np.float64) ** 2))
+        p, m, v = (st[k].astype(np.float64) for k in ("params", "m", "v"))
+    net.close()
+
+
+def test_set_state_checks_every_value_first(lib, ctx):
+    net = ctx.mlp(rand_params(1))
+    st = net.state()
+    for key, val in (("params", np.nan), ("m", np.inf), ("v", -1.0), ("v", np.nan)):
+        bad = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in st.items()}
+        bad[key][17] = val
+        with pytest.raises(lib.RecogsError) as e:
+            net.set_state(bad)
+        assert e.value.status == lib.EINVAL
+    with pytest.raises(lib.RecogsError) as e:
+        net.set_state(dict(st, step=-1))
+    assert e.value.status == lib.EINVAL
+    after = net.state()
+    for k in ("params", "m", "v"):
+        np.testing.assert_array_equal(after[k], st[k])
     net.close()
 
 

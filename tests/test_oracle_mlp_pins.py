@@ -190,10 +190,10 @@ def test_decisions_truth_table():
     np.testing.assert_allclose(w[3], 1.0)
 
 
-def _f32_forward(theta, X, order):
+def _f32_forward(theta, X, order, full=False):
     """A float32 implementation rounding at the oracle's points: bf16
     operands, float32 sums over the inputs in the given order, the
-    Abramowitz-Stegun 26.2.17 GELU in float32."""
+    Abramowitz-Stegun 26.2.17 GELU in float32 (full: every intermediate)."""
     P = mlp.unpack(theta)
     f32 = np.float32
 
@@ -217,9 +217,14 @@ def _f32_forward(theta, X, order):
         return (z * np.where(z >= 0, f32(1) - q, q)).astype(f32)
 
     x = mlp.bf16(X)
-    h1 = mlp.bf16(gelu32(layer(x, mlp.bf16(P["W1"]), P["b1"])).astype(np.float64))
-    h2 = mlp.bf16(gelu32(layer(h1, mlp.bf16(P["W2"]), P["b2"])).astype(np.float64))
-    return layer(h2, mlp.bf16(P["W3"]), P["b3"]).astype(np.float64)
+    z1 = layer(x, mlp.bf16(P["W1"]), P["b1"])
+    h1 = mlp.bf16(gelu32(z1).astype(np.float64))
+    z2 = layer(h1, mlp.bf16(P["W2"]), P["b2"])
+    h2 = mlp.bf16(gelu32(z2).astype(np.float64))
+    o = layer(h2, mlp.bf16(P["W3"]), P["b3"])
+    if full:
+        return dict(x=x, z1=z1, h1=h1, z2=z2, h2=h2, o=o)
+    return o.astype(np.float64)
 
 
 def test_forward_bound_covers_a_float32_implementation():
@@ -242,3 +247,87 @@ def test_forward_bound_covers_a_float32_implementation():
         g = mlp._gamma(65)
         acc_only = g * ((np.abs(f["h2"])) @ np.abs(mlp.bf16(P["W3"])) + np.abs(P["b3"]))
         assert np.any(err > acc_only)
+
+
+def _f32_grad(theta, X, sel, cov, B, block=128):
+    """The backward of a float32 implementation rounding at loss_grad's
+    points: _f32_forward, float32 sigmoid and GELU' (erf), bf16 dz3, dz2,
+    dz1, products over the hidden units summed in reverse order, and the
+    rows summed in float32 block by block (rows in order within a block of
+    128, then the blocks in order)."""
+    import scipy.special as sps
+    f32 = np.float32
+    P = mlp.unpack(theta)
+    fw = _f32_forward(theta, X, order=list(range(63, -1, -1)), full=True)
+    o = fw["o"].astype(f32)
+    p = (f32(1) / (f32(1) + np.exp(-o))).astype(f32)
+    inv_b = f32(1.0 / B)
+    s_ = np.asarray(sel, f32)
+    c_ = np.asarray(cov, f32)[:, None]
+    d3 = np.zeros_like(o)
+    d3[:, 0] = (p[:, 0] - s_) * inv_b
+    d3[:, 1:] = ((f32(2) * (p[:, 1:] - c_)) * p[:, 1:] * (f32(1) - p[:, 1:])) * inv_b
+
+    def ggrad(z):
+        z = z.astype(f32)
+        e = sps.erf(z * f32(0.70710677)).astype(f32)
+        return (f32(0.5) * (f32(1) + e) + z * np.exp(f32(-0.5) * z * z) * f32(0.3989423)).astype(f32)
+
+    def back(D, W):          # D W^T, float32, the hidden units summed in reverse order
+        D = D.astype(f32)
+        W = W.astype(f32)
+        acc = np.zeros((D.shape[0], W.shape[0]), f32)
+        for k in range(W.shape[1] - 1, -1, -1):
+            acc = (acc + D[:, k:k + 1] * W[:, k][None, :]).astype(f32)
+        return acc
+
+    def rowsum(A, Dm):       # A^T Dm, float32, by blocks of rows
+        A = A.astype(f32)
+        Dm = Dm.astype(f32)
+        total = np.zeros((A.shape[1], Dm.shape[1]), f32)
+        for b0 in range(0, len(A), block):
+            acc = np.zeros_like(total)
+            for r in range(b0, min(b0 + block, len(A))):
+                acc = (acc + A[r][:, None] * Dm[r][None, :]).astype(f32)
+            total = (total + acc).astype(f32)
+        return total
+
+    def colsum(Dm):
+        return rowsum(np.ones((len(Dm), 1)), Dm)[0]
+
+    d3r = mlp.bf16(d3.astype(np.float64))
+    dz2 = back(d3r, mlp.bf16(P["W3"])) * ggrad(fw["z2"])
+    dz2r = mlp.bf16(dz2.astype(np.float64))
+    dz1 = back(dz2r, mlp.bf16(P["W2"])) * ggrad(fw["z1"])
+    dz1r = mlp.bf16(dz1.astype(np.float64))
+    g = dict(W3=rowsum(fw["h2"], d3r), b3=colsum(d3), W2=rowsum(fw["h1"], dz2r), b2=colsum(dz2),
+             W1=rowsum(fw["x"], dz1r), b1=colsum(dz1))
+    return mlp.pack(g)
+
+
+@pytest.mark.parametrize("scale", [1.0, 3.0])
+def test_grad_bound_covers_a_float32_implementation(scale, monkeypatch):
+    """Every gradient element of a float32 backward (other summation orders,
+    float32 sigmoid and GELU') lies within grad_bound of the FP64 oracle and
+    the bound is far below the gradient's scale; with the bf16 flips taken
+    out of the bound (no spread beyond the value's own rounding) the same
+    float32 backward falls outside it, so those terms are exercised."""
+    rng = np.random.default_rng(11)
+    n = 2000
+    X = rng.normal(0, 1.0, (n, 64))
+    X[:, 59:] = 0.0
+    sel = (rng.random(n) < 0.4).astype(np.float64)
+    cov = rng.random(n)
+    theta = sg.mlp_init(4).astype(np.float64) * scale
+    depth = 128 + (n + 127) // 128 + 2      # _f32_grad's blocks of 128 rows
+    for B in (n, n + 7):
+        g32 = _f32_grad(theta, X, sel, cov, B)
+        for d in (None, depth):
+            loss, g, bound = mlp.grad_bound(theta, X, sel, cov, batch=B, depth=d)
+            err = np.abs(g32 - g)
+            assert np.all(err <= bound), (err / bound).max()
+        # most of the bound is the chance of bf16 flips, far below the gradient
+        assert np.median(bound) <= 0.05 * np.abs(g).max()
+    monkeypatch.setattr(mlp, "_bf16_spread", lambda v, d: np.zeros_like(np.asarray(v, float)))
+    _, g, no_flips = mlp.grad_bound(theta, X, sel, cov, batch=n, depth=depth)
+    assert np.any(np.abs(_f32_grad(theta, X, sel, cov, n) - g) > no_flips)
