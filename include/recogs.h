@@ -50,7 +50,8 @@ typedef enum {
     RECOGS_ECUDA = 3,     /* a CUDA runtime call failed (message has the CUDA error) */
     RECOGS_ECAPACITY = 4, /* a size exceeds a fixed limit (pairs >= 2^31, image too large) */
     RECOGS_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
-    RECOGS_EDEVICE = 6    /* no usable CUDA device, or not an sm_103 device */
+    RECOGS_EDEVICE = 6,   /* no usable CUDA device, or not an sm_103 device */
+    RECOGS_EBOUNDS = 7    /* debug build only: an index check failed; the access was skipped */
 } recogs_status;
 
 typedef enum { RECOGS_F32 = 0, RECOGS_F16 = 1, RECOGS_BF16 = 2 } recogs_dtype;
@@ -471,6 +472,15 @@ RECOGS_API recogs_status recogs_set_fault(recogs_ctx* ctx, const char* spec);
  * stream each stage runs on. */
 RECOGS_API recogs_status recogs_set_timing(recogs_ctx* ctx, int enable);
 
+/* Enable (1) or disable (0) an NVTX range per pipeline stage on the calling
+ * host thread (named as recogs_stage_times names the stages: "preprocess",
+ * "scan", "scatter", "tile_sort", "blend", ...), for timeline profilers.
+ * The ranges mark the host-side launch of each stage. Off by default; the
+ * environment variable RECOGS_NVTX (any value but "0"), read by
+ * recogs_ctx_create, turns it on. Costs nothing measurable when no
+ * profiler is attached. */
+RECOGS_API recogs_status recogs_set_tracing(recogs_ctx* ctx, int enable);
+
 /* Which stages the timing covers: bit i = stage i in the order of
  * recogs_stage_times (default: all). Each timed stage costs two event
  * records per frame on the stream. */
@@ -531,7 +541,12 @@ RECOGS_API recogs_status recogs_set_pair_capacity(recogs_ctx* ctx, int64_t pairs
 /* Wait for `stream` and for the context's batch lanes, then report and clear
  * the errors recorded on the device by frames without a read back:
  * RECOGS_ECAPACITY (pairs above the capacity, or a tile above the per-tile
- * limit), RECOGS_ETIMEOUT (a bounded device wait gave up). */
+ * limit), RECOGS_ETIMEOUT (a bounded device wait gave up). In the debug
+ * build (librecogs_debug.so, compiled with RECOGS_DEBUG) also
+ * RECOGS_EBOUNDS: a kernel found a tile number, list range, Gaussian id or
+ * scatter position outside its buffer in the last frame on the context's
+ * main stream, skipped that access and recorded the first such site and
+ * index (the message names them); the frame's image is then not valid. */
 RECOGS_API recogs_status recogs_check(recogs_ctx* ctx, void* stream);
 
 /* One view of a batch: scenes[scene] rendered from `camera` with an optional

@@ -93,6 +93,9 @@ def lib():
                                                 f64p, u8p, i32p, C.c_double, f64p, u8p, C.c_int]
         L.oracle_color_grad_tiles.argtypes = [C.POINTER(Splats), i64p, i32p, C.c_int, C.c_int,
                                               f64p, f64p]
+        L.oracle_color_grad_bound_tiles.argtypes = [C.c_int64, C.POINTER(Splats), i64p, i32p,
+                                                    C.c_int, C.c_int, f64p, C.POINTER(Margins),
+                                                    f64p]
         L.oracle_sh_grad.argtypes = [C.c_int64, f32p, C.POINTER(Camera), f64p, f64p, f64p]
         L.oracle_pixel_outcomes.argtypes = [C.POINTER(Splats), i64p, i32p, C.c_int, C.c_int, i64p,
                                             C.c_int64, C.c_int64, i32p, i32p, f64p,
@@ -418,6 +421,28 @@ def color_grad(splats: SplatResult, offsets, ids, dLdy) -> np.ndarray:
     return out[:3 * n].reshape(n, 3)
 
 
+def color_grad_bound(splats: SplatResult, offsets, ids, dLdy, mg=None) -> np.ndarray:
+    """Per splat and channel ([n, 3]), a bound on how far the colour gradient
+    of a float32 blend may lie from color_grad: float32 alpha and T within
+    the margins of the render's error model, decisions in doubt (alpha
+    against 1/255, the stop, validity, key ties) taken either way, and
+    float32 sums over the pixels in any order."""
+    cam = splats["camera"]
+    n = splats["n"]
+    mg = margins(cam) if mg is None else mg
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    ids = np.ascontiguousarray(ids, np.int32)
+    if len(ids) == 0:
+        ids = np.zeros(1, np.int32)
+    g = np.ascontiguousarray(dLdy, np.float64).reshape(-1)
+    out = np.zeros(3 * max(n, 1))
+    s = splats.struct()
+    lib().oracle_color_grad_bound_tiles(n, C.byref(s), _ptr(offsets, i64p), _ptr(ids, i32p),
+                                        cam.width, cam.height, _ptr(g, f64p), C.byref(mg),
+                                        _ptr(out, f64p))
+    return out[:3 * n].reshape(n, 3)
+
+
 def weight_sums(splats: SplatResult, offsets, ids, pixel_weight, power) -> np.ndarray:
     """Per splat: sum_p pixel_weight[p] (alpha T)^power over its contributions."""
     cam = splats["camera"]
@@ -444,6 +469,39 @@ def sh_grad(scene, splats: SplatResult, grad_rgb) -> np.ndarray:
     lib().oracle_sh_grad(n, _ptr(xyz, f32p), C.byref(camc), _ptr(splats["rgb"], f64p),
                          _ptr(g, f64p), _ptr(out, f64p))
     return out
+
+
+# float32 evaluation of the SH basis at the normalised view direction: within
+# SH_BASIS_ERR of Y_k (absolute; |Y_k| <= 3 for degree 3, a few roundings of
+# the direction and of the polynomial)
+SH_BASIS_ERR = 4e-6
+
+
+def sh_grad_bound(scene, splats: SplatResult, grad_rgb, bound_rgb) -> np.ndarray:
+    """[16][3][n]: a bound on how far a float32 SH gradient Y_k(d) [c > 0]
+    g_c, fed a colour gradient within bound_rgb of grad_rgb, may lie from
+    sh_grad(scene, splats, grad_rgb). The clamp c = max(f + 0.5, 0) may be
+    decided either way where the float32 f + 0.5 may have the other sign
+    (|f + 0.5| <= 2e-6 (1 + sum_k |C_k Y_k|))."""
+    n = splats["n"]
+    xyz = np.ascontiguousarray(scene.xyz, np.float32)
+    ones = np.ones(3 * max(n, 1))
+    Y = np.zeros((16, 3, max(n, 1)))
+    camc = camera_struct(splats["camera"])
+    lib().oracle_sh_grad(n, _ptr(xyz, f32p), C.byref(camc), _ptr(ones, f64p), _ptr(ones, f64p),
+                         _ptr(Y, f64p))
+    Y = Y[:, 0, :n]                                       # [16][n]
+    sh = np.asarray(scene.sh, np.float64)[:, :, :n]       # [16][3][n]
+    terms = sh * Y[:, None, :]
+    f = terms.sum(0) + 0.5                                # [3][n]
+    ef = 2e-6 * (1.0 + np.abs(terms).sum(0))
+    g = np.asarray(grad_rgb, np.float64).reshape(n, 3).T  # [3][n]
+    b = np.asarray(bound_rgb, np.float64).reshape(n, 3).T
+    aY = np.abs(Y)[:, None, :] + SH_BASIS_ERR
+    passed = aY * b + SH_BASIS_ERR * np.abs(g) + 2.0 ** -23 * np.abs(Y)[:, None, :] * (np.abs(g) + b)
+    either = aY * (np.abs(g) + b)
+    out = np.where(f > ef, passed, np.where(f < -ef, 0.0, either))
+    return np.broadcast_to(out, (16, 3, n)).copy()
 
 
 def adam_step(C, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-15):

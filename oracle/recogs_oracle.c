@@ -1047,6 +1047,113 @@ void oracle_color_grad_tiles(const oracle_splats* s, const int64_t* offsets, con
         }
 }
 
+/* Per splat and channel, a bound on how far the colour gradient of a float32
+ * blend (float32 alpha and T, sums over the pixels in any order) may lie
+ * from oracle_color_grad_tiles. It carries the error model of blend_pixel:
+ * each alpha within exp(+-ep) of its value, T within exp(+-eT); a
+ * contribution whose decision may go either way (alpha against 1/255, the
+ * stop, a splat whose validity or range is in doubt) may be present or
+ * absent, so it counts in full and widens the later T of its pixel by
+ * alpha / (1 - alpha); after a stop in doubt every later contribution the
+ * float32 walk could still make counts in full; two contributors whose
+ * float32 keys may tie may swap, which moves either's T by the other's
+ * alpha / (1 - alpha); the sums over pixels add gamma_m of the magnitudes,
+ * m the splat's contributing pixels plus 8, unit roundoff 2^-23. dLdy: HWC
+ * [H*W*3]; bound: [3n], accumulated (the caller zeroes it). */
+void oracle_color_grad_bound_tiles(int64_t n, const oracle_splats* s, const int64_t* offsets,
+                                   const int32_t* ids, int width, int height, const double* dLdy,
+                                   const oracle_margins* mg, double* bound) {
+    const int tiles_x = (width + TILE - 1) / TILE, tiles_y = (height + TILE - 1) / TILE;
+    const double a_min = 1.0 / 255.0;
+    double* absum = (double*)calloc((size_t)(3 * n + 1), sizeof(double));
+    int64_t* cnt = (int64_t*)calloc((size_t)(n + 1), sizeof(int64_t));
+    for (int ty = 0; ty < tiles_y; ++ty)
+        for (int tx = 0; tx < tiles_x; ++tx) {
+            const int64_t t = (int64_t)ty * tiles_x + tx;
+            for (int y = ty * TILE; y < ty * TILE + TILE && y < height; ++y)
+                for (int x = tx * TILE; x < tx * TILE + TILE && x < width; ++x) {
+                    const double* g = &dLdy[3 * ((int64_t)y * width + x)];
+                    double T = 1.0, eT = 0.0;
+                    int after_doubtful_stop = 0;
+                    int64_t prev = -1;
+                    double prev_alpha = 0.0, prev_T = 0.0, prev_eT = 0.0;
+                    for (int64_t k = offsets[t]; k < offsets[t + 1]; ++k) {
+                        const int64_t i = ids[k];
+                        const double dx = x - s->u[i], dy = y - s->v[i];
+                        const double sigma = s->opacity[i];
+                        const double kk = 2.0 * log(255.0 * sigma);
+                        const double A = s->conic[3 * i], B = s->conic[3 * i + 1];
+                        const double Cc = s->conic[3 * i + 2];
+                        double p = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy;
+                        if (p > 0.0) p = 0.0;
+                        double alpha = sigma * exp(p);
+                        if (alpha > 0.99) alpha = 0.99;
+                        const double gx = A * dx + B * dy, gy = B * dx + Cc * dy;
+                        const double a = s->cov2d[3 * i], c = s->cov2d[3 * i + 2];
+                        const double sg = sqrt(a) * fabs(gx) + sqrt(c) * fabs(gy);
+                        const double ep = mg->eps_pix * (fabs(gx) + fabs(gy)) +
+                                          0.5 * mg->eps_cov * sg * sg + mg->eps_exp * (fabs(p) + 1.0);
+                        const int near_threshold = fabs(p + 0.5 * kk) <= ep;
+                        /* the largest this splat's term can be on the float32 side */
+                        const double wmax = alpha * exp(ep) * T * exp(eT);
+                        int in_doubt = after_doubtful_stop || near_threshold || !s->valid[i] ||
+                                       (s->fp_flag[i] & 2);
+                        if (!s->valid[i] || alpha < a_min) {
+                            if (in_doubt && alpha * exp(ep) >= a_min) {
+                                for (int ch = 0; ch < 3; ++ch) {
+                                    bound[3 * i + ch] += fabs(g[ch]) * wmax;
+                                    absum[3 * i + ch] += fabs(g[ch]) * wmax;
+                                }
+                                ++cnt[i];
+                                /* taken on the float32 side, it lowers the later T */
+                                eT += alpha * exp(ep) / (1.0 - alpha * exp(ep));
+                            }
+                            continue;
+                        }
+                        const double ea = alpha < 0.99 ? ep : 0.0;
+                        const double testT = T * (1.0 - alpha);
+                        double eT_next = eT + alpha * ea / (1.0 - alpha) + 2.4e-7;
+                        const int stop_in_doubt = fabs(log(testT / 1e-4)) <= eT_next;
+                        if (testT < 1e-4 && !stop_in_doubt && !after_doubtful_stop) break;
+                        if (after_doubtful_stop && testT < 1e-4 * exp(-eT_next)) break;
+                        in_doubt = in_doubt || stop_in_doubt;
+                        double rel = ea + eT + 4.0 * 0x1p-24;
+                        if (prev >= 0 && keys_may_tie(s->depth[prev], s->depth[i], mg->eps_depth)) {
+                            /* the pair may swap: each one's T by the other's factor */
+                            const double wp = prev_alpha * prev_T * exp(prev_eT);
+                            const double fp = alpha / (1.0 - alpha);
+                            for (int ch = 0; ch < 3; ++ch) {
+                                bound[3 * prev + ch] += fabs(g[ch]) * wp * fp;
+                                absum[3 * prev + ch] += fabs(g[ch]) * wp * fp;
+                            }
+                            rel += prev_alpha / (1.0 - prev_alpha);
+                        }
+                        for (int ch = 0; ch < 3; ++ch) {
+                            const double term = fabs(g[ch]) * alpha * T;
+                            bound[3 * i + ch] += in_doubt ? fabs(g[ch]) * wmax : term * rel;
+                            absum[3 * i + ch] += fabs(g[ch]) * wmax;
+                        }
+                        ++cnt[i];
+                        if (near_threshold) eT_next += alpha / (1.0 - alpha);
+                        if (stop_in_doubt || (testT < 1e-4)) after_doubtful_stop = 1;
+                        prev = i;
+                        prev_alpha = alpha;
+                        prev_T = T;
+                        prev_eT = eT;
+                        T = testT;
+                        eT = eT_next;
+                    }
+                }
+        }
+    for (int64_t i = 0; i < n; ++i) {
+        const double m = (double)(cnt[i] + 8);
+        const double gam = m * 0x1p-23 / (1.0 - m * 0x1p-23);
+        for (int ch = 0; ch < 3; ++ch) bound[3 * i + ch] += gam * absum[3 * i + ch];
+    }
+    free(absum);
+    free(cnt);
+}
+
 /* Per-splat sums of a per-pixel weight times (alpha_i(p) T_i(p))^power over
  * the binned render's contributors (same skip and termination rules).
  * pixel_weight: [H*W]; out: [n], accumulated. power 1 with weights dL/dy

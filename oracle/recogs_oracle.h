@@ -169,6 +169,11 @@ void oracle_pixel_outcomes(const oracle_splats* s, const int64_t* offsets, const
  * (grad_sh [16][3][n]). */
 void oracle_color_grad_tiles(const oracle_splats* s, const int64_t* offsets, const int32_t* ids,
                              int width, int height, const double* dLdy, double* grad_rgb);
+/* Per splat and channel, a bound on a float32 blend's departure from
+ * oracle_color_grad_tiles (see the definition); bound: [3n], accumulated. */
+void oracle_color_grad_bound_tiles(int64_t n, const oracle_splats* s, const int64_t* offsets,
+                                   const int32_t* ids, int width, int height, const double* dLdy,
+                                   const oracle_margins* mg, double* bound);
 void oracle_sh_grad(int64_t n, const float* xyz, const oracle_camera* cam, const double* rgb,
                     const double* grad_rgb, double* grad_sh);
 

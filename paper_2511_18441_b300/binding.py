@@ -13,9 +13,11 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "librecogs.so")
+# RECOGS_LIBRARY=debug selects the bounds-checking build (build.py --debug)
+LIB_PATH = os.path.join(_PKG, "librecogs_debug.so" if os.environ.get("RECOGS_LIBRARY") == "debug"
+                        else "librecogs.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ECAPACITY, ETIMEOUT, EDEVICE = range(7)
+OK, EINVAL, ENOMEM, ECUDA, ECAPACITY, ETIMEOUT, EDEVICE, EBOUNDS = range(8)
 F32, F16, BF16 = 0, 1, 2
 REGION_BOX, REGION_POLYGON = 1, 2
 MAX_POLYGON = 64
@@ -99,6 +101,7 @@ SIGNATURES = {
     "recogs_depth_keys": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "recogs_set_fault": (C.c_int, [C.c_void_p, C.c_char_p]),
     "recogs_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "recogs_set_tracing": (C.c_int, [C.c_void_p, C.c_int]),
     "recogs_set_timed_stages": (C.c_int, [C.c_void_p, C.c_uint32]),
     "recogs_stage_times": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
                                      C.POINTER(C.c_char_p), C.POINTER(C.c_double),
@@ -480,6 +483,10 @@ class Context:
     def set_fault(self, spec: str = ""):
         """Fault injection: "alloc:N", "wait:N" (comma-separated) or "" to clear."""
         self._check(self._L.recogs_set_fault(self._h, spec.encode()))
+
+    def set_tracing(self, enable: bool):
+        """An NVTX range per pipeline stage (for timeline profilers)."""
+        self._check(self._L.recogs_set_tracing(self._h, 1 if enable else 0))
 
     def set_timing(self, enable: bool, stages=None):
         """Event timing of each stage (or only of the named stages)."""

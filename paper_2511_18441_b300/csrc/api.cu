@@ -22,6 +22,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "recogs_internal.cuh"
 
 using namespace recogs;
@@ -152,6 +154,8 @@ struct recogs_ctx {
     int64_t fault_alloc_in = 0;     // > 0: the fault_alloc_in-th device allocation from now fails
     // timing and counts
     bool timing = false;
+    bool tracing = false;          // NVTX range per stage (recogs_set_tracing, RECOGS_NVTX)
+    bool range_open = false;
     uint32_t timed_stages = ~0u;   // bit per Stage
     std::vector<cudaEvent_t> event_pool;
     std::vector<PendingTime> pending;
@@ -245,12 +249,22 @@ cudaEvent_t get_event(recogs_ctx* ctx) {
 }
 
 void stage_begin(recogs_ctx* ctx, int stage, cudaStream_t st) {
+    if (ctx->tracing) {
+        // stages do not nest; a range left open by an error return is closed here
+        if (ctx->range_open) nvtxRangePop();
+        nvtxRangePushA(kStageNames[stage]);
+        ctx->range_open = true;
+    }
     if (!ctx->timing || ctx->capturing || !((ctx->timed_stages >> stage) & 1u)) return;
     ctx->cur_start = get_event(ctx);
     cudaEventRecord(ctx->cur_start, st);
 }
 
 void stage_end(recogs_ctx* ctx, int stage, int launches, cudaStream_t st) {
+    if (ctx->range_open) {
+        nvtxRangePop();
+        ctx->range_open = false;
+    }
     if (ctx->capturing) {
         // counted once per replay of the captured graph
         ctx->batch_graph_launches += launches;
@@ -473,7 +487,7 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
                                         sched.radix_classes, sc.aux[c]);
             // overlapped: each class's tiles are blended as soon as they are sorted
             if (overlapped)
-                l += launch_blend_class(P<uint2>(sc.ranges), P<uint32_t>(sc.order),
+                l += launch_blend_class(n, P<uint2>(sc.ranges), P<uint32_t>(sc.order),
                                         P<uint32_t>(sc.tvals[0]), P<float4>(sc.rec), dc, bgv,
                                         image, final_T, dctr, sched.blend_batch, c,
                                         (int)min(bound, (uint32_t)tiles), sc.aux[c]);
@@ -482,7 +496,7 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
             // the empty tiles (background only) after the classes
             const uint32_t empty = !async && classes ? (uint32_t)tiles - bound_sum
                                                      : (uint32_t)tiles;
-            l += launch_blend_class(P<uint2>(sc.ranges), P<uint32_t>(sc.order),
+            l += launch_blend_class(n, P<uint2>(sc.ranges), P<uint32_t>(sc.order),
                                     P<uint32_t>(sc.tvals[0]), P<float4>(sc.rec), dc, bgv, image,
                                     final_T, dctr, sched.blend_batch, kSortClasses,
                                     (int)min(empty, 1184u), st);
@@ -575,7 +589,7 @@ recogs_status render_device(recogs_ctx* ctx, Scratch& sc, const Schedule& sched,
             ex = *extra;
             ex.zkey = P<uint32_t>(sc.zkey);
         }
-        l = launch_blend(P<uint2>(sc.ranges), P<uint32_t>(sc.order), ids, P<float4>(sc.rec), dc,
+        l = launch_blend(n, P<uint2>(sc.ranges), P<uint32_t>(sc.order), ids, P<float4>(sc.rec), dc,
                          bgv, image, final_T, dctr, sched.blend_batch, extra ? &ex : nullptr, st);
         stage_end(ctx, ST_BLEND, l, st);
     }
@@ -986,7 +1000,7 @@ recogs_status refit(recogs_ctx* ctx, const recogs_scene& s, const recogs_camera&
     const uint32_t* ids = ctx->last_ids;
     stage_begin(ctx, ST_BLEND_GRAD, st);
     // the forward frame's counters: a skipped frame contributes no gradient
-    int l = launch_blend(P<uint2>(ctx->main.ranges), P<uint32_t>(ctx->main.order), ids,
+    int l = launch_blend(n, P<uint2>(ctx->main.ranges), P<uint32_t>(ctx->main.order), ids,
                          P<float4>(ctx->main.rec), dc, bgv, image, nullptr,
                          P<DevCounters>(ctx->main.counters), sched.blend_batch, &ex, st);
     stage_end(ctx, ST_BLEND_GRAD, l, st);
@@ -1045,6 +1059,7 @@ const char* recogs_status_string(recogs_status s) {
         case RECOGS_ECAPACITY: return "RECOGS_ECAPACITY";
         case RECOGS_ETIMEOUT: return "RECOGS_ETIMEOUT";
         case RECOGS_EDEVICE: return "RECOGS_EDEVICE";
+        case RECOGS_EBOUNDS: return "RECOGS_EBOUNDS";
     }
     return "RECOGS_UNKNOWN";
 }
@@ -1127,6 +1142,10 @@ recogs_status recogs_ctx_create(recogs_ctx** out, int device) {
     if (!parse_fault(getenv("RECOGS_FAULT"), c->fault_wait_polls, c->fault_alloc_in)) {
         delete c;
         return create_fail(RECOGS_EINVAL, "RECOGS_FAULT is not a fault specification");
+    }
+    {
+        const char* tr = getenv("RECOGS_NVTX");
+        c->tracing = tr && *tr && strcmp(tr, "0") != 0;
     }
     DeviceGuard g(device);
     if (cudaMallocHost(&c->h_counters, sizeof(DevCounters)) != cudaSuccess) {
@@ -1327,6 +1346,16 @@ recogs_status recogs_set_timing(recogs_ctx* ctx, int enable) {
     return RECOGS_OK;
 }
 
+recogs_status recogs_set_tracing(recogs_ctx* ctx, int enable) {
+    if (!ctx) return RECOGS_EINVAL;
+    if (!enable && ctx->range_open) {
+        nvtxRangePop();
+        ctx->range_open = false;
+    }
+    ctx->tracing = enable != 0;
+    return RECOGS_OK;
+}
+
 recogs_status recogs_stage_times(recogs_ctx* ctx, int32_t max_stages, int32_t* n_stages,
                                  const char** names, double* total_ms, int64_t* launches,
                                  int reset) {
@@ -1384,18 +1413,29 @@ recogs_status recogs_check(recogs_ctx* ctx, void* stream) {
     if (!ctx) return RECOGS_EINVAL;
     DeviceGuard g(ctx->device);
     CK(cudaStreamSynchronize((cudaStream_t)stream));
-    uint32_t bits = 0;
+    uint32_t bits = 0, dbg = 0;
     if (ctx->main.counters.p) {
         DevCounters* d = P<DevCounters>(ctx->main.counters);
         CK(cudaMemcpy(ctx->h_counters, d, sizeof(DevCounters), cudaMemcpyDeviceToHost));
         bits = ctx->h_counters->error;
+        dbg = ctx->h_counters->debug;
         if (bits) CK(cudaMemset(&d->error, 0, sizeof(uint32_t)));
+        if (dbg) CK(cudaMemset(&d->debug, 0, sizeof(uint32_t)));
         // a crowded tile of a frame with the read back took the global path
         if (ctx->sched.pair_capacity == 0) bits &= ~kErrCrowded;
     }
     uint32_t lb = 0;
     CKS(lane_errors(ctx, &lb));
     bits |= lb;
+    if (dbg) {
+        static const char* const kSites[] = {"?", "scatter tile", "scatter position",
+                                             "tile sort range", "blend tile", "blend range",
+                                             "blend Gaussian id"};
+        const uint32_t site = dbg >> 24;
+        return fail(ctx, RECOGS_EBOUNDS,
+                    "debug bounds check failed: %s, index %u (low 24 bits); the access was skipped",
+                    kSites[site < 7 ? site : 0], dbg & 0xffffffu);
+    }
     if (bits & kErrTimeout)
         return fail(ctx, RECOGS_ETIMEOUT, "a bounded device wait gave up; that frame is invalid");
     if (bits & (kErrCapacity | kErrCrowded))
@@ -1724,7 +1764,8 @@ recogs_status recogs_mlp_labels(recogs_ctx* ctx, const recogs_scene* scene,
     ex.cover = true;
     ex.region = P<DevRegion>(ctx->rf_region);
     stage_begin(ctx, ST_MLP, st);
-    int l = launch_blend(P<uint2>(ctx->main.ranges), P<uint32_t>(ctx->main.order), ctx->last_ids,
+    int l = launch_blend((int)n, P<uint2>(ctx->main.ranges), P<uint32_t>(ctx->main.order),
+                         ctx->last_ids,
                          P<float4>(ctx->main.rec), dc, bg0, P<float>(ctx->rf_img), nullptr,
                          P<DevCounters>(ctx->main.counters), sched.blend_batch, &ex, st);
     l += launch_mlp_labels(*scene, dc, dr, P<float>(ctx->rf_grad), labels_out, st);

@@ -254,7 +254,11 @@ __global__ void __launch_bounds__(kScatterThreads)
             if (k < c[g]) {
                 // the k-th tile of the rectangle, row by row
                 const uint32_t t = row[g] + col[g];
-                keys[ranges[t].x + atomicAdd(cur[g] + t, 1u)] = key[g];
+                if (RECOGS_IN_BOUNDS(ctr, t < (uint32_t)tiles, kDbgScatterTile, t)) {
+                    const uint32_t pos = ranges[t].x + atomicAdd(cur[g] + t, 1u);
+                    if (RECOGS_IN_BOUNDS(ctr, pos < ranges[t].y, kDbgScatterPos, pos))
+                        keys[pos] = key[g];
+                }
                 if (++col[g] == w[g]) {
                     col[g] = 0;
                     row[g] += (uint32_t)tiles_x;
@@ -275,7 +279,10 @@ __global__ void __launch_bounds__(kScatterThreads)
         for (uint32_t k = threadIdx.x; k < cb; k += kScatterThreads) {
             const uint32_t dy = k / wb;
             const uint32_t t = (y0 + dy) * (uint32_t)tiles_x + x0 + (k - dy * wb);
-            keys[ranges[t].x + atomicAdd(cb_cur + t, 1u)] = kb;
+            if (RECOGS_IN_BOUNDS(ctr, t < (uint32_t)tiles, kDbgScatterTile, t)) {
+                const uint32_t pos = ranges[t].x + atomicAdd(cb_cur + t, 1u);
+                if (RECOGS_IN_BOUNDS(ctr, pos < ranges[t].y, kDbgScatterPos, pos)) keys[pos] = kb;
+            }
         }
     }
 }
@@ -431,7 +438,11 @@ __global__ void __launch_bounds__(THREADS)
     uint32_t count, first, k = 0;
     class_span(ctr, cls, count, first);
     for (uint32_t item; (item = next_item(work, cls, k, count, &s_item)) != 0xffffffffu;) {
-        tile_sort_one<THREADS>(ranges, (int)order[first + item], keys, ids);
+        const int tile = (int)order[first + item];
+        if (!RECOGS_IN_BOUNDS(ctr, ranges[tile].x <= ranges[tile].y && ranges[tile].y <= ctr->n_pairs,
+                              kDbgSortRange, (uint32_t)tile))
+            continue;
+        tile_sort_one<THREADS>(ranges, tile, keys, ids);
         __syncthreads();
     }
 }
@@ -694,7 +705,11 @@ __global__ void __launch_bounds__(THREADS, (RECOGS_RADIX_WARPS_PER_SM * 32 / THR
     uint32_t count, first, k = 0;
     class_span(ctr, cls, count, first);
     for (uint32_t item; (item = next_item(work, cls, k, count, &s_item)) != 0xffffffffu;) {
-        tile_radix_one<THREADS, ITEMS>(ranges, (int)order[first + item], keys, ids);
+        const int tile = (int)order[first + item];
+        if (!RECOGS_IN_BOUNDS(ctr, ranges[tile].x <= ranges[tile].y && ranges[tile].y <= ctr->n_pairs,
+                              kDbgSortRange, (uint32_t)tile))
+            continue;
+        tile_radix_one<THREADS, ITEMS>(ranges, tile, keys, ids);
         __syncthreads();
     }
 }
@@ -726,6 +741,8 @@ __global__ void __launch_bounds__(1024, 1)
     for (uint32_t item; (item = next_item(work, cls, k, count, &s_item)) != 0xffffffffu;) {
         const int tile = (int)order[first + item];
         const uint2 r = ranges[tile];
+        if (!RECOGS_IN_BOUNDS(ctr, r.x <= r.y && r.y <= ctr->n_pairs, kDbgSortRange, (uint32_t)tile))
+            continue;
         if (r.y - r.x <= 8u * 1024u)
             tile_radix_big8(ranges, tile, keys, ids);
         else

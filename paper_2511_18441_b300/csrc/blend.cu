@@ -68,6 +68,22 @@ __device__ __forceinline__ uint32_t group_mask(float u, float v, float ex, float
     return X * Y;
 }
 
+// The three float4 of Gaussian rid's record. Debug builds check rid < n
+// and give an out-of-range id the record of an invisible splat (alpha 0).
+__device__ __forceinline__ void fetch_record(int n, uint32_t rid, const float4* __restrict__ rec,
+                                             const DevCounters* ctr, float4& ra, float4& rb,
+                                             float4& rc) {
+    if (!RECOGS_IN_BOUNDS(ctr, rid < (uint32_t)n, kDbgBlendId, rid)) {
+        ra = make_float4(0.f, 0.f, 0.f, 0.f);
+        rb = make_float4(0.f, -INFINITY, 0.f, 0.f);
+        rc = ra;
+        return;
+    }
+    ra = __ldg(rec + 3 * (size_t)rid);
+    rb = __ldg(rec + 3 * (size_t)rid + 1);
+    rc = __ldg(rec + 3 * (size_t)rid + 2);
+}
+
 // What a blend launch computes besides the walk itself.
 enum BlendMode {
     kBlendColour = 0,   // image (and final T)
@@ -89,7 +105,7 @@ template <int MODE> struct Accumulates { static constexpr bool value = MODE >= k
 // sentinel entry whose alpha is 0. The four groups then walk their lists in
 // lockstep for as many steps as the longest list of the batch.
 template <int BATCH, int MODE>
-__device__ __forceinline__ void blend_tile(const int tile, const uint2* __restrict__ ranges,
+__device__ __forceinline__ void blend_tile(const int n, const int tile, const uint2* __restrict__ ranges,
                                            const uint32_t* __restrict__ ids,
                                            const float4* __restrict__ rec, int width, int height,
                                            int tiles_x, float bg0, float bg1, float bg2,
@@ -128,8 +144,13 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
     const size_t pix = (size_t)py * width + px;
     uint16_t* const my_list = s_list + (4 * warp + grp) * LSTRIDE;
 
+    if (!RECOGS_IN_BOUNDS(ctr, tile >= 0 && tile < tiles_x * ((height + kTile - 1) / kTile),
+                          kDbgBlendTile, (uint32_t)tile))
+        return;
     uint2 rg = ranges[tile];
     if (ctr && ctr->skip) rg = make_uint2(0u, 0u);  // pairs exceed the buffers: background only
+    if (!RECOGS_IN_BOUNDS(ctr, rg.x <= rg.y && (!ctr || rg.y <= ctr->n_pairs), kDbgBlendRange, rg.y))
+        rg = make_uint2(0u, 0u);
     const uint32_t begin = rg.x, end = rg.y;
 
     // "stopped" is kept in the sign of T (T < 0: stopped at |T|, or outside
@@ -195,9 +216,7 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
     const bool gatherer = threadIdx.x < BATCH;
     if (gatherer && begin + threadIdx.x < end) {
         rid = __ldg(ids + begin + threadIdx.x);
-        ra = __ldg(rec + 3 * (size_t)rid);
-        rb = __ldg(rec + 3 * (size_t)rid + 1);
-        rc = __ldg(rec + 3 * (size_t)rid + 2);
+        fetch_record(n, rid, rec, ctr, ra, rb, rc);
     }
 
     // gradient mode: add the previous batch's per-Gaussian sums to the global
@@ -310,9 +329,7 @@ __device__ __forceinline__ void blend_tile(const int tile, const uint2* __restri
         const uint32_t jn = b + BATCH + threadIdx.x;
         if (gatherer && jn < end) {
             rid = __ldg(ids + jn);
-            ra = __ldg(rec + 3 * (size_t)rid);
-            rb = __ldg(rec + 3 * (size_t)rid + 1);
-            rc = __ldg(rec + 3 * (size_t)rid + 2);
+            fetch_record(n, rid, rec, ctr, ra, rb, rc);
         }
         if (__all_sync(0xffffffffu, stopped())) continue;
         const int cnt = (int)min((uint32_t)BATCH, end - b);
@@ -460,7 +477,8 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
 }
 
 template <int BATCH>
-__device__ __forceinline__ void blend_tile_pairs(const int tile, const uint2* __restrict__ ranges,
+__device__ __forceinline__ void blend_tile_pairs(const int n, const int tile,
+                                                 const uint2* __restrict__ ranges,
                                                  const uint32_t* __restrict__ ids,
                                                  const float4* __restrict__ rec, int width,
                                                  int height, int tiles_x, float bg0, float bg1,
@@ -495,8 +513,13 @@ __device__ __forceinline__ void blend_tile_pairs(const int tile, const uint2* __
     const float2 YY = make_float2(fy * fy, fy * fy);
     uint16_t* const my_list = s_list + (4 * warp + grp) * LSTRIDE;
 
+    if (!RECOGS_IN_BOUNDS(ctr, tile >= 0 && tile < tiles_x * ((height + kTile - 1) / kTile),
+                          kDbgBlendTile, (uint32_t)tile))
+        return;
     uint2 rg = ranges[tile];
     if (ctr && ctr->skip) rg = make_uint2(0u, 0u);  // pairs exceed the buffers: background only
+    if (!RECOGS_IN_BOUNDS(ctr, rg.x <= rg.y && (!ctr || rg.y <= ctr->n_pairs), kDbgBlendRange, rg.y))
+        rg = make_uint2(0u, 0u);
     const uint32_t begin = rg.x, end = rg.y;
 
     // alive (1 or 0) marks a pixel that has not stopped (0 outside the image)
@@ -517,10 +540,7 @@ __device__ __forceinline__ void blend_tile_pairs(const int tile, const uint2* __
     // prefetch the first batch (one Gaussian per thread)
     float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra;
     if (begin + threadIdx.x < end) {
-        const uint32_t rid = __ldg(ids + begin + threadIdx.x);
-        ra = __ldg(rec + 3 * (size_t)rid);
-        rb = __ldg(rec + 3 * (size_t)rid + 1);
-        rc = __ldg(rec + 3 * (size_t)rid + 2);
+        fetch_record(n, __ldg(ids + begin + threadIdx.x), rec, ctr, ra, rb, rc);
     }
 
     // one staged Gaussian at byte offset o against this lane's two pixels
@@ -583,10 +603,7 @@ __device__ __forceinline__ void blend_tile_pairs(const int tile, const uint2* __
         {
             const uint32_t jn = b + BATCH + threadIdx.x;
             if (jn < end) {
-                const uint32_t rid = __ldg(ids + jn);
-                ra = __ldg(rec + 3 * (size_t)rid);
-                rb = __ldg(rec + 3 * (size_t)rid + 1);
-                rc = __ldg(rec + 3 * (size_t)rid + 2);
+                fetch_record(n, __ldg(ids + jn), rec, ctr, ra, rb, rc);
             }
         }
         if (__all_sync(0xffffffffu, stopped())) continue;
@@ -655,24 +672,24 @@ __device__ __forceinline__ void blend_tile_pairs(const int tile, const uint2* __
 #endif
 template <int BATCH>
 __global__ void __launch_bounds__(kPairThreads, RECOGS_PAIR_MIN_BLOCKS)
-    blend_pairs_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+    blend_pairs_kernel(int n, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
                        const uint32_t* __restrict__ ids, const float4* __restrict__ rec, int width,
                        int height, int tiles_x, float bg0, float bg1, float bg2,
                        float* __restrict__ image, float* __restrict__ final_T,
                        DevCounters* __restrict__ ctr) {
-    blend_tile_pairs<BATCH>((int)order[blockIdx.x], ranges, ids, rec, width, height, tiles_x, bg0,
+    blend_tile_pairs<BATCH>(n, (int)order[blockIdx.x], ranges, ids, rec, width, height, tiles_x, bg0,
                             bg1, bg2, image, final_T, ctr);
 }
 
 // One CTA per tile of the tile order.
 template <int BATCH, int MODE>
 __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
-    blend_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+    blend_kernel(int n, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
                  const uint32_t* __restrict__ ids, const float4* __restrict__ rec, int width,
                  int height, int tiles_x, float bg0, float bg1, float bg2,
                  float* __restrict__ image, float* __restrict__ final_T,
                  DevCounters* __restrict__ ctr, BlendExtra ex) {
-    blend_tile<BATCH, MODE>((int)order[blockIdx.x], ranges, ids, rec, width, height, tiles_x, bg0,
+    blend_tile<BATCH, MODE>(n, (int)order[blockIdx.x], ranges, ids, rec, width, height, tiles_x, bg0,
                             bg1, bg2, image, final_T, ctr, ex);
 }
 
@@ -681,7 +698,7 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
 // the run, so any grid covers it (colour mode).
 template <int BATCH>
 __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
-    blend_class_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+    blend_class_kernel(int n, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
                        const uint32_t* __restrict__ ids, const float4* __restrict__ rec,
                        int width, int height, int tiles_x, int tiles, float bg0, float bg1,
                        float bg2, float* __restrict__ image, float* __restrict__ final_T,
@@ -691,14 +708,14 @@ __global__ void __launch_bounds__(kBlendThreads, RECOGS_BLEND_MIN_BLOCKS)
     const uint32_t count = cls < kSortClasses ? ctr->class_tiles[cls] : (uint32_t)tiles - first;
     const BlendExtra ex;
     for (uint32_t item = blockIdx.x; item < count; item += gridDim.x) {
-        blend_tile<BATCH, kBlendColour>((int)order[first + item], ranges, ids, rec, width, height,
+        blend_tile<BATCH, kBlendColour>(n, (int)order[first + item], ranges, ids, rec, width, height,
                                         tiles_x, bg0, bg1, bg2, image, final_T, ctr, ex);
         __syncthreads();
     }
 }
 
 template <int MODE>
-static void blend_launch(int batch, const uint2* ranges, const uint32_t* order,
+static void blend_launch(int n, int batch, const uint2* ranges, const uint32_t* order,
                          const uint32_t* ids, const float4* rec, const DevCamera& cam,
                          const float bg[3], float* image, float* final_T, DevCounters* counters,
                          const BlendExtra& ex, cudaStream_t st) {
@@ -708,21 +725,21 @@ static void blend_launch(int batch, const uint2* ranges, const uint32_t* order,
         // (measured at 3M/1080p: 0.292 ms against 0.345 ms for batches of
         // 256, two per thread; 0.305 ms for the one-pixel walk)
         blend_pairs_kernel<128><<<tiles, kPairThreads, 0, st>>>(
-            ranges, order, ids, rec, cam.width, cam.height, cam.tiles_x, bg[0], bg[1], bg[2], image,
+            n, ranges, order, ids, rec, cam.width, cam.height, cam.tiles_x, bg[0], bg[1], bg[2], image,
             final_T, counters);
         return;
     }
     if (batch == 128)
         blend_kernel<128, MODE><<<tiles, kBlendThreads, 0, st>>>(
-            ranges, order, ids, rec, cam.width, cam.height, cam.tiles_x, bg[0], bg[1], bg[2],
+            n, ranges, order, ids, rec, cam.width, cam.height, cam.tiles_x, bg[0], bg[1], bg[2],
             image, final_T, counters, ex);
     else
         blend_kernel<256, MODE><<<tiles, kBlendThreads, 0, st>>>(
-            ranges, order, ids, rec, cam.width, cam.height, cam.tiles_x, bg[0], bg[1], bg[2],
+            n, ranges, order, ids, rec, cam.width, cam.height, cam.tiles_x, bg[0], bg[1], bg[2],
             image, final_T, counters, ex);
 }
 
-int launch_blend_class(const uint2* ranges, const uint32_t* order, const uint32_t* ids,
+int launch_blend_class(int n, const uint2* ranges, const uint32_t* order, const uint32_t* ids,
                        const float4* rec, const DevCamera& cam, const float bg[3], float* image,
                        float* final_T, DevCounters* counters, int batch, int cls, int grid,
                        cudaStream_t st) {
@@ -730,33 +747,34 @@ int launch_blend_class(const uint2* ranges, const uint32_t* order, const uint32_
     const int tiles = cam.tiles_x * cam.tiles_y;
     if (batch == 128)
         blend_class_kernel<128><<<grid, kBlendThreads, 0, st>>>(
-            ranges, order, ids, rec, cam.width, cam.height, cam.tiles_x, tiles, bg[0], bg[1],
+            n, ranges, order, ids, rec, cam.width, cam.height, cam.tiles_x, tiles, bg[0], bg[1],
             bg[2], image, final_T, counters, cls);
     else
         blend_class_kernel<256><<<grid, kBlendThreads, 0, st>>>(
-            ranges, order, ids, rec, cam.width, cam.height, cam.tiles_x, tiles, bg[0], bg[1],
+            n, ranges, order, ids, rec, cam.width, cam.height, cam.tiles_x, tiles, bg[0], bg[1],
             bg[2], image, final_T, counters, cls);
     return 1;
 }
 
-int launch_blend(const uint2* ranges, const uint32_t* order, const uint32_t* ids, const float4* rec,
-                 const DevCamera& cam, const float bg[3], float* image, float* final_T,
-                 DevCounters* counters, int batch, const BlendExtra* extra, cudaStream_t st) {
+int launch_blend(int n, const uint2* ranges, const uint32_t* order, const uint32_t* ids,
+                 const float4* rec, const DevCamera& cam, const float bg[3], float* image,
+                 float* final_T, DevCounters* counters, int batch, const BlendExtra* extra,
+                 cudaStream_t st) {
     BlendExtra ex;
     if (extra) ex = *extra;
     // every mode honours the frame's skip flag (a frame whose pairs overflowed
     // or whose sort gave up has no valid lists)
     if (ex.grad_rgb && ex.cover)
-        blend_launch<kBlendCover>(batch, ranges, order, ids, rec, cam, bg, image, final_T, counters,
+        blend_launch<kBlendCover>(n, batch, ranges, order, ids, rec, cam, bg, image, final_T, counters,
                                   ex, st);
     else if (ex.grad_rgb)
-        blend_launch<kBlendGrad>(batch, ranges, order, ids, rec, cam, bg, image, final_T, counters,
+        blend_launch<kBlendGrad>(n, batch, ranges, order, ids, rec, cam, bg, image, final_T, counters,
                                  ex, st);
     else if (ex.depth)
-        blend_launch<kBlendDepth>(batch, ranges, order, ids, rec, cam, bg, image, final_T,
+        blend_launch<kBlendDepth>(n, batch, ranges, order, ids, rec, cam, bg, image, final_T,
                                   counters, ex, st);
     else
-        blend_launch<kBlendColour>(batch, ranges, order, ids, rec, cam, bg, image, final_T,
+        blend_launch<kBlendColour>(n, batch, ranges, order, ids, rec, cam, bg, image, final_T,
                                    counters, ex, st);
     return 1;
 }

@@ -231,8 +231,8 @@ extern "C" RECOGS_API recogs_status recogs_render_noalloc(
         ids = tb.vals[tcur];
     }
     NA_CK(cudaGetLastError());
-    launch_blend(ranges, U32(oOrder), ids, rec, dc, bgv, image_hwc_out, final_T_out, dctr, 256, nullptr,
-                 st);
+    launch_blend(n, ranges, U32(oOrder), ids, rec, dc, bgv, image_hwc_out, final_T_out, dctr, 256,
+                 nullptr, st);
     NA_CK(cudaGetLastError());
     // a sort of the global path whose bounded wait gave up left the error
     // word set (and an invalid image): report it from this call

@@ -90,7 +90,8 @@ recogs_status edit_to_dev(const recogs_edit* edit, const recogs_camera& cam, Dev
 // Size classes of the per-tile sort (CTAs of 1024, 512, 256, 128, 64, 32 threads).
 constexpr int kSortClasses = 6;
 
-// Counters written by the kernels of one frame (zeroed at its start, except `error`).
+// Counters written by the kernels of one frame (zeroed at its start, except
+// `error` and `debug`).
 struct DevCounters {
     uint32_t zmin_inv;   // ~(smallest depth bits) of visible Gaussians (atomicMax)
     uint32_t zmax;       // largest depth bits of visible Gaussians
@@ -101,8 +102,30 @@ struct DevCounters {
     uint32_t class_tiles[kSortClasses];  // non-empty tiles per per-tile-sort class
     uint32_t skip;       // 1: the pairs exceed the pair buffers; later stages skip the frame
     uint32_t error;      // kErr* bits; not cleared per frame (the host reads and clears it)
-    uint32_t pad1;
+    uint32_t debug;      // debug builds: first failed bounds check (site << 24 | index), else 0
 };
+// Debug builds (compiled with RECOGS_DEBUG): bounds checks of the indices
+// the hot path reads from its own data (tile numbers, list ranges, Gaussian
+// ids, scatter positions). A failing check records its site and the index
+// in DevCounters::debug (the first failure of the frame) and the access is
+// skipped; nothing traps. Release builds compile the checks away (the
+// condition is not evaluated).
+enum DebugSite : uint32_t {
+    kDbgScatterTile = 1, kDbgScatterPos = 2, kDbgSortRange = 3, kDbgBlendTile = 4,
+    kDbgBlendRange = 5, kDbgBlendId = 6
+};
+#ifdef RECOGS_DEBUG
+__device__ __forceinline__ bool debug_in_bounds(const DevCounters* ctr, bool ok, uint32_t site,
+                                                uint32_t index) {
+    if (!ok && ctr)
+        atomicCAS(const_cast<uint32_t*>(&ctr->debug), 0u, (site << 24) | (index & 0xffffffu));
+    return ok;
+}
+#define RECOGS_IN_BOUNDS(ctr, cond, site, index) ::recogs::debug_in_bounds((ctr), (cond), (site), (index))
+#else
+#define RECOGS_IN_BOUNDS(ctr, cond, site, index) true
+#endif
+
 constexpr uint32_t kErrTimeout = 1u;   // a bounded look-back wait gave up
 constexpr uint32_t kErrCapacity = 2u;  // more pairs than the pair buffers hold
 constexpr uint32_t kErrCrowded = 4u;   // a tile above the per-tile sort's limit
@@ -486,13 +509,14 @@ int launch_recolor_weighted(recogs_scene& s, const float* weights, const float M
 // The blend of one per-tile sort class's tiles (cls < kSortClasses) or of
 // the empty tiles after them (cls == kSortClasses), colour mode, `grid` CTAs
 // looping over the run (any grid covers it).
-int launch_blend_class(const uint2* ranges, const uint32_t* order, const uint32_t* ids,
+int launch_blend_class(int n, const uint2* ranges, const uint32_t* order, const uint32_t* ids,
                        const float4* rec, const DevCamera& cam, const float bg[3], float* image,
                        float* final_T, DevCounters* counters, int batch, int cls, int grid,
                        cudaStream_t st);
 // batch: Gaussians staged in shared memory per blend step, 128 or 256
-int launch_blend(const uint2* ranges, const uint32_t* order, const uint32_t* ids, const float4* rec,
-                 const DevCamera& cam, const float bg[3], float* image, float* final_T,
-                 DevCounters* counters, int batch, const BlendExtra* extra, cudaStream_t st);
+int launch_blend(int n, const uint2* ranges, const uint32_t* order, const uint32_t* ids,
+                 const float4* rec, const DevCamera& cam, const float bg[3], float* image,
+                 float* final_T, DevCounters* counters, int batch, const BlendExtra* extra,
+                 cudaStream_t st);
 
 }  // namespace recogs

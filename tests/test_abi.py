@@ -36,6 +36,17 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
+def test_debug_build_exports_every_declared_symbol():
+    """The bounds-checking build (RECOGS_DEBUG) is the same library: every
+    entry point, and the status string of the code only it returns."""
+    path = build.build(debug=True)
+    dbg = C.CDLL(path)
+    for name in declared_entry_points():
+        assert hasattr(dbg, name), name
+    dbg.recogs_status_string.restype = C.c_char_p
+    assert dbg.recogs_status_string(7) == b"RECOGS_EBOUNDS"
+
+
 def test_binding_covers_every_declared_symbol():
     assert sorted(binding.SIGNATURES) == declared_entry_points()
 
