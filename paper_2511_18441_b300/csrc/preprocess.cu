@@ -24,6 +24,21 @@ __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
 __device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
 
+// to_f32(from_f32<T>(x)) of two values: the storage type's rounding, done
+// for both by one packed conversion (cvt.rn.bf16x2.f32 / cvt.rn.f16x2.f32)
+template <typename T> __device__ __forceinline__ float2 round_pair(float a, float b);
+template <> __device__ __forceinline__ float2 round_pair<float>(float a, float b) {
+    return make_float2(a, b);
+}
+template <> __device__ __forceinline__ float2 round_pair<__nv_bfloat16>(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const uint32_t u = *reinterpret_cast<const uint32_t*>(&h);
+    return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+template <> __device__ __forceinline__ float2 round_pair<__half>(float a, float b) {
+    return __half22float2(__floats2half2_rn(a, b));
+}
+
 template <typename T> __device__ __forceinline__ T from_f32(float v);
 template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
 template <> __device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
@@ -373,7 +388,7 @@ __device__ __forceinline__ uint32_t prep_one(int i, float mx, float my, float mz
     float f0 = 0.f, f1 = 0.f, f2 = 0.f;
     // one branch per warp: a warp with any selected lane recolours in every
     // lane and keeps the unselected lanes' coefficients as read
-    if (__any_sync(__activemask(), sel)) {
+    if (__any_sync(__activemask(), sel) && sizeof(T) == 4) {
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             float c0 = sh(3 * k), c1 = sh(3 * k + 1), c2 = sh(3 * k + 2);
@@ -384,12 +399,40 @@ __device__ __forceinline__ uint32_t prep_one(int i, float mx, float my, float mz
                 r1 = __fadd_rn(r1, edit.dc_fix[1]);
                 r2 = __fadd_rn(r2, edit.dc_fix[2]);
             }
-            c0 = sel ? to_f32(from_f32<T>(r0)) : c0;
-            c1 = sel ? to_f32(from_f32<T>(r1)) : c1;
-            c2 = sel ? to_f32(from_f32<T>(r2)) : c2;
+            c0 = sel ? r0 : c0;
+            c1 = sel ? r1 : c1;
+            c2 = sel ? r2 : c2;
             f0 = fmaf(Y[k], c0, f0);
             f1 = fmaf(Y[k], c1, f1);
             f2 = fmaf(Y[k], c2, f2);
+        }
+    } else if (__any_sync(__activemask(), sel)) {
+        // 16-bit storage: two triples at a time, so that the storage rounding
+        // of their six recoloured values takes three packed conversions
+#pragma unroll
+        for (int k = 0; k < 16; k += 2) {
+            float c[6], r[6];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) c[j] = r[j] = sh(3 * k + j);
+            recolor_triple(edit.M, r[0], r[1], r[2]);
+            recolor_triple(edit.M, r[3], r[4], r[5]);
+            if (k == 0) {
+                r[0] = __fadd_rn(r[0], edit.dc_fix[0]);
+                r[1] = __fadd_rn(r[1], edit.dc_fix[1]);
+                r[2] = __fadd_rn(r[2], edit.dc_fix[2]);
+            }
+#pragma unroll
+            for (int j = 0; j < 6; j += 2) {
+                const float2 q = round_pair<T>(r[j], r[j + 1]);
+                c[j] = sel ? q.x : c[j];
+                c[j + 1] = sel ? q.y : c[j + 1];
+            }
+            f0 = fmaf(Y[k], c[0], f0);
+            f1 = fmaf(Y[k], c[1], f1);
+            f2 = fmaf(Y[k], c[2], f2);
+            f0 = fmaf(Y[k + 1], c[3], f0);
+            f1 = fmaf(Y[k + 1], c[4], f1);
+            f2 = fmaf(Y[k + 1], c[5], f2);
         }
     } else {
 #pragma unroll
