@@ -13,8 +13,9 @@
 // warp iterates as often as its busiest group, not as often as the union of
 // its groups' lists. Pixels stop at the transmittance cut-off, a warp stops
 // when all its pixels have, and the CTA stops fetching when every pixel has.
-// This walk serves the depth, gradient and coverage modes; the colour frame
-// runs the same walk with two pixels per lane (blend_tile_pairs below).
+// This walk serves the depth and coverage modes; the colour frame and the
+// refit's gradient run the same walk with two pixels per lane
+// (blend_tile_pairs below).
 #include "recogs_internal.cuh"
 
 // Resident CTAs per SM the register allocation is held to (a tuning knob).
@@ -476,7 +477,7 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
     return bits_f2(d);
 }
 
-template <int BATCH>
+template <int BATCH, int MODE>
 __device__ __forceinline__ void blend_tile_pairs(const int n, const int tile,
                                                  const uint2* __restrict__ ranges,
                                                  const uint32_t* __restrict__ ids,
@@ -484,8 +485,11 @@ __device__ __forceinline__ void blend_tile_pairs(const int n, const int tile,
                                                  int height, int tiles_x, float bg0, float bg1,
                                                  float bg2, float* __restrict__ image,
                                                  float* __restrict__ final_T,
-                                                 DevCounters* __restrict__ ctr) {
+                                                 DevCounters* __restrict__ ctr,
+                                                 const BlendExtra& ex) {
     static_assert(BATCH == kPairThreads, "one staged Gaussian per thread");
+    static_assert(MODE == kBlendColour || MODE == kBlendGrad, "colour or gradient mode");
+    constexpr bool kGrad = MODE == kBlendGrad;
     // the exponent polynomial's coefficients and the colour, each twice;
     // entry BATCH is the sentinel (alpha = 2^-inf = 0)
     __shared__ float4 s_q0[BATCH + 1];   // (A, A, B, B)
@@ -496,6 +500,11 @@ __device__ __forceinline__ void blend_tile_pairs(const int n, const int tile,
     constexpr int LSTRIDE = BATCH + 8;
     __shared__ __align__(16) uint16_t s_list[16 * LSTRIDE];
     __shared__ uint32_t s_m[BATCH];      // group mask (0 past the batch's end)
+    // gradient mode: each staged Gaussian's colour gradient over this tile,
+    // its id, and the warps' shares of the loss
+    __shared__ float s_g[kGrad ? 3 * BATCH : 1];
+    __shared__ uint32_t s_id[kGrad ? BATCH : 1];
+    __shared__ float s_loss[kGrad ? kPairThreads / 32 : 1];
     constexpr uint32_t kSent = 16u * BATCH;   // byte offset of the sentinel in the float4 arrays
 
     const int tx = tile % tiles_x, ty = tile / tiles_x;
@@ -529,6 +538,39 @@ __device__ __forceinline__ void blend_tile_pairs(const int n, const int tile,
     auto stopped = [&]() { return alive.x == 0.0f && alive.y == 0.0f; };
     uint32_t fetched = begin;
     const float a_min = 1.0f / 255.0f;
+    // gradient mode: dL/dy of the two pixels, sign(y - target) / N (Eq. 6,
+    // L1 term), arranged for the reduce-scatter of blend_tile (lane bit 0
+    // picks the channel pair kept, bit 1 its member) with the two pixels'
+    // values side by side: a hit's group sums are linear in its weights
+    float2 kp0 = make_float2(0.f, 0.f), kp1 = kp0, sp0 = kp0, sp1 = kp0;
+    float l1 = 0.f;
+    const int red_ch = 2 * (lane & 1) + ((lane >> 1) & 1);
+    const bool red_lane = (lane & 4) == 0 && red_ch < 3;
+    if (kGrad) {
+        float g[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            if (q ? in1 : in0) {
+                const size_t pq = (size_t)py * width + px + q;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float d = image[3 * pq + c] - ex.target[3 * pq + c];
+                    g[q][c] = d > 0.f ? ex.inv_n : d < 0.f ? -ex.inv_n : 0.f;
+                    l1 += fabsf(d);
+                }
+            }
+        }
+        const float2 g0 = make_float2(g[0][0], g[1][0]), g1 = make_float2(g[0][1], g[1][1]);
+        const float2 g2 = make_float2(g[0][2], g[1][2]), z = make_float2(0.f, 0.f);
+        const bool rc_ = (lane >> 1) & 1, rb_ = lane & 1;
+        const float2 p0a = rc_ ? g1 : g0, p0b = rc_ ? g0 : g1;
+        const float2 p1a = rc_ ? z : g2, p1b = rc_ ? g2 : z;
+        kp0 = rb_ ? p1a : p0a;
+        kp1 = rb_ ? p1b : p0b;
+        sp0 = rb_ ? p0a : p1a;
+        sp1 = rb_ ? p0b : p1b;
+        for (int k = threadIdx.x; k < 3 * BATCH; k += kPairThreads) s_g[k] = 0.f;
+    }
     if (threadIdx.x == 0) {
         s_q0[BATCH] = make_float4(0.f, 0.f, 0.f, 0.f);
         s_q1[BATCH] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -539,9 +581,26 @@ __device__ __forceinline__ void blend_tile_pairs(const int n, const int tile,
 
     // prefetch the first batch (one Gaussian per thread)
     float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra;
+    uint32_t rid = 0;
     if (begin + threadIdx.x < end) {
-        fetch_record(n, __ldg(ids + begin + threadIdx.x), rec, ctr, ra, rb, rc);
+        rid = __ldg(ids + begin + threadIdx.x);
+        fetch_record(n, rid, rec, ctr, ra, rb, rc);
     }
+
+    // gradient mode: the previous batch's per-Gaussian sums into the global
+    // gradient (one atomic per Gaussian, tile and channel), then cleared
+    auto flush = [&](uint32_t prev_b) {
+        const int k = threadIdx.x;
+        if (prev_b + k < end) {
+            const uint32_t id = s_id[k];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float v = s_g[3 * k + c];
+                if (v != 0.f) atomicAdd(&ex.grad_rgb[3 * (size_t)id + c], v);
+                s_g[3 * k + c] = 0.f;
+            }
+        }
+    };
 
     // one staged Gaussian at byte offset o against this lane's two pixels
     // (the operations of blend_tile's colour mode, two at a time)
@@ -550,8 +609,6 @@ __device__ __forceinline__ void blend_tile_pairs(const int n, const int tile,
         const float4 q0 = *reinterpret_cast<const float4*>(q + o);
         const float4 q1 = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(s_q1) + o);
         const float4 q2 = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(s_q2) + o);
-        const float4 q3 = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(s_q3) + o);
-        const float2 q4 = *reinterpret_cast<const float2*>(reinterpret_cast<const char*>(s_q4) + (o >> 1));
         const float2 p =
             fma2(make_float2(q0.x, q0.y), XX,
                  fma2(make_float2(q0.z, q0.w), XY,
@@ -566,15 +623,35 @@ __device__ __forceinline__ void blend_tile_pairs(const int n, const int tile,
         const float2 nT = sub2(T, wt);
         alive = mul2(alive, make_float2(set_ge(nT.x, 1e-4f), set_ge(nT.y, 1e-4f)));
         const float2 w = mul2(wt, alive);
-        cr = fma2(make_float2(q3.x, q3.y), w, cr);
-        cg = fma2(make_float2(q3.z, q3.w), w, cg);
-        cb = fma2(q4, w, cb);
+        if (!kGrad) {
+            const float4 q3 =
+                *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(s_q3) + o);
+            const float2 q4 =
+                *reinterpret_cast<const float2*>(reinterpret_cast<const char*>(s_q4) + (o >> 1));
+            cr = fma2(make_float2(q3.x, q3.y), w, cr);
+            cg = fma2(make_float2(q3.z, q3.w), w, cg);
+            cb = fma2(q4, w, cb);
+        } else {
+            // g alpha T of both pixels, reduce-scattered over the group
+            const float r0 = __shfl_xor_sync(0xffffffffu, fmaf(sp0.x, w.x, sp0.y * w.y), 1);
+            const float r1 = __shfl_xor_sync(0xffffffffu, fmaf(sp1.x, w.x, sp1.y * w.y), 1);
+            const float u0 = fmaf(kp0.x, w.x, fmaf(kp0.y, w.y, r0));
+            const float u1 = fmaf(kp1.x, w.x, fmaf(kp1.y, w.y, r1));
+            float x = u0 + __shfl_xor_sync(0xffffffffu, u1, 2);
+            x += __shfl_xor_sync(0xffffffffu, x, 4);
+            if (red_lane && o != kSent) atomicAdd(&s_g[3 * (o >> 4) + red_ch], x);
+        }
         T = sub2(T, w);
     };
 
+    uint32_t prev_b = 0xffffffffu;
     for (uint32_t b = begin; b < end; b += BATCH) {
         const int n_done = __syncthreads_count(stopped());
-        if (n_done == kPairThreads) break;
+        if (kGrad && prev_b != 0xffffffffu) flush(prev_b);
+        if (n_done == kPairThreads) {
+            prev_b = 0xffffffffu;
+            break;
+        }
         {
             const int slot = threadIdx.x;
             uint32_t gm = 0u;
@@ -594,16 +671,19 @@ __device__ __forceinline__ void blend_tile_pairs(const int n, const int tile,
                 s_q3[slot] = make_float4(rc.x, rc.x, rc.y, rc.y);
                 s_q4[slot] = make_float2(rc.z, rc.z);
                 gm = group_mask16(u, v, rb.z, rb.w);
+                if (kGrad) s_id[slot] = rid;
             }
             s_m[slot] = gm;
         }
         fetched = min(end, b + BATCH);
+        prev_b = b;
         __syncthreads();
         // prefetch the next batch while this one is blended
         {
             const uint32_t jn = b + BATCH + threadIdx.x;
             if (jn < end) {
-                fetch_record(n, __ldg(ids + jn), rec, ctr, ra, rb, rc);
+                rid = __ldg(ids + jn);
+                fetch_record(n, rid, rec, ctr, ra, rb, rc);
             }
         }
         if (__all_sync(0xffffffffu, stopped())) continue;
@@ -647,6 +727,22 @@ __device__ __forceinline__ void blend_tile_pairs(const int n, const int tile,
             if (__all_sync(0xffffffffu, stopped())) break;
         }
     }
+    if (kGrad) {
+        __syncthreads();
+        if (prev_b != 0xffffffffu) flush(prev_b);
+        // this tile's share of the L1 loss
+        float l = l1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+        if (lane == 0) s_loss[warp] = l;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+            for (int w = 0; w < kPairThreads / 32; ++w) t += s_loss[w];
+            atomicAdd(ex.loss, (double)t);
+        }
+        return;
+    }
     const size_t pix = (size_t)py * width + px;
     if (in0) {
         const float t0 = T.x;
@@ -670,15 +766,15 @@ __device__ __forceinline__ void blend_tile_pairs(const int n, const int tile,
 #ifndef RECOGS_PAIR_MIN_BLOCKS
 #define RECOGS_PAIR_MIN_BLOCKS 7
 #endif
-template <int BATCH>
+template <int BATCH, int MODE>
 __global__ void __launch_bounds__(kPairThreads, RECOGS_PAIR_MIN_BLOCKS)
     blend_pairs_kernel(int n, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
                        const uint32_t* __restrict__ ids, const float4* __restrict__ rec, int width,
                        int height, int tiles_x, float bg0, float bg1, float bg2,
                        float* __restrict__ image, float* __restrict__ final_T,
-                       DevCounters* __restrict__ ctr) {
-    blend_tile_pairs<BATCH>(n, (int)order[blockIdx.x], ranges, ids, rec, width, height, tiles_x, bg0,
-                            bg1, bg2, image, final_T, ctr);
+                       DevCounters* __restrict__ ctr, BlendExtra ex) {
+    blend_tile_pairs<BATCH, MODE>(n, (int)order[blockIdx.x], ranges, ids, rec, width, height,
+                                  tiles_x, bg0, bg1, bg2, image, final_T, ctr, ex);
 }
 
 // One CTA per tile of the tile order.
@@ -720,13 +816,14 @@ static void blend_launch(int n, int batch, const uint2* ranges, const uint32_t* 
                          const float bg[3], float* image, float* final_T, DevCounters* counters,
                          const BlendExtra& ex, cudaStream_t st) {
     const int tiles = cam.tiles_x * cam.tiles_y;
-    if (MODE == kBlendColour) {
+    if (MODE == kBlendColour || MODE == kBlendGrad) {
         // two pixels per lane, batches of 128 Gaussians whatever `batch` says
         // (measured at 3M/1080p: 0.292 ms against 0.345 ms for batches of
         // 256, two per thread; 0.305 ms for the one-pixel walk)
-        blend_pairs_kernel<128><<<tiles, kPairThreads, 0, st>>>(
-            n, ranges, order, ids, rec, cam.width, cam.height, cam.tiles_x, bg[0], bg[1], bg[2], image,
-            final_T, counters);
+        blend_pairs_kernel<128, MODE == kBlendGrad ? kBlendGrad : kBlendColour>
+            <<<tiles, kPairThreads, 0, st>>>(n, ranges, order, ids, rec, cam.width, cam.height,
+                                             cam.tiles_x, bg[0], bg[1], bg[2], image, final_T,
+                                             counters, ex);
         return;
     }
     if (batch == 128)
