@@ -96,6 +96,9 @@ def lib():
         L.oracle_color_grad_bound_tiles.argtypes = [C.c_int64, C.POINTER(Splats), i64p, i32p,
                                                     C.c_int, C.c_int, f64p, C.POINTER(Margins),
                                                     f64p]
+        L.oracle_weight_sums_bound_tiles.argtypes = [C.c_int64, C.POINTER(Splats), i64p, i32p,
+                                                     C.c_int, C.c_int, f64p, f64p, C.c_int,
+                                                     C.POINTER(Margins), f64p]
         L.oracle_sh_grad.argtypes = [C.c_int64, f32p, C.POINTER(Camera), f64p, f64p, f64p]
         L.oracle_pixel_outcomes.argtypes = [C.POINTER(Splats), i64p, i32p, C.c_int, C.c_int, i64p,
                                             C.c_int64, C.c_int64, i32p, i32p, f64p,
@@ -441,6 +444,30 @@ def color_grad_bound(splats: SplatResult, offsets, ids, dLdy, mg=None) -> np.nda
                                         cam.width, cam.height, _ptr(g, f64p), C.byref(mg),
                                         _ptr(out, f64p))
     return out[:3 * n].reshape(n, 3)
+
+
+def weight_sums_bound(splats: SplatResult, offsets, ids, pixel_weight, power, doubt=None,
+                      mg=None) -> np.ndarray:
+    """Per splat ([n]), a bound on how far a float32 blend's sums of
+    weight_sums may lie from the oracle's (the error model of
+    color_grad_bound); doubt ([H*W], optional): the largest change of each
+    pixel's weight on the float32 side."""
+    cam = splats["camera"]
+    n = splats["n"]
+    mg = margins(cam) if mg is None else mg
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    ids = np.ascontiguousarray(ids, np.int32)
+    if len(ids) == 0:
+        ids = np.zeros(1, np.int32)
+    w = np.ascontiguousarray(pixel_weight, np.float64).reshape(-1)
+    d = None if doubt is None else np.ascontiguousarray(doubt, np.float64).reshape(-1)
+    out = np.zeros(max(n, 1))
+    s = splats.struct()
+    lib().oracle_weight_sums_bound_tiles(n, C.byref(s), _ptr(offsets, i64p), _ptr(ids, i32p),
+                                         cam.width, cam.height, _ptr(w, f64p),
+                                         _ptr(d, f64p) if d is not None else None, int(power),
+                                         C.byref(mg), _ptr(out, f64p))
+    return out[:n]
 
 
 def weight_sums(splats: SplatResult, offsets, ids, pixel_weight, power) -> np.ndarray:

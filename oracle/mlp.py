@@ -142,9 +142,8 @@ def radial_frame(u, v, xy):
     return qx / rho, qy / rho, rho
 
 
-def features_and_labels(scene, cam, region_xy):
-    """Returns (F [n, 64], valid [n] bool, sel [n] uint8, coverage [n])."""
-    n = scene.xyz.shape[1]
+def _view_centre(scene, cam):
+    """View-space centre t (3 x n), projected centre (u, v) and validity."""
     xyz = np.asarray(scene.xyz, np.float32).astype(np.float64)
     V = np.asarray(cam.world_to_view, np.float32).astype(np.float64).reshape(3, 4)
     t = V[:, :3] @ xyz + V[:, 3:4]
@@ -153,13 +152,17 @@ def features_and_labels(scene, cam, region_xy):
     with np.errstate(divide="ignore", invalid="ignore"):
         u = float(np.float32(cam.fx)) * t[0] / tz + float(np.float32(cam.cx))
         v = float(np.float32(cam.fy)) * t[1] / tz + float(np.float32(cam.cy))
-    uu, vv = np.where(valid, u, 0.0), np.where(valid, v, 0.0)
-    un, vn, rho = radial_frame(uu, vv, region_xy)
-    sp = _o.preprocess(scene, cam)
-    a, b, c = sp["cov2d"][0::3], sp["cov2d"][1::3], sp["cov2d"][2::3]
+    return xyz, V, t, np.where(valid, u, 0.0), np.where(valid, v, 0.0), valid
+
+
+def _geometry(u, v, tz, a, b, c, valid, region_xy, fx):
+    """Features 0-8 (the splat in the selection view, see the header) from
+    the projected centre, the view depth and the dilated 2D covariance,
+    with the intermediate magnitudes a float32 evaluation rounds."""
+    un, vn, rho = radial_frame(u, v, region_xy)
     a, b, c = np.where(valid, a, 1.0), np.where(valid, b, 0.0), np.where(valid, c, 1.0)
     cen = np.asarray(region_xy, np.float64).reshape(-1, 2).mean(0)
-    qx, qy = uu - cen[0], vv - cen[1]
+    qx, qy = u - cen[0], v - cen[1]
     qn = np.sqrt(qx * qx + qy * qy)
     ux = np.where(qn > 0, qx / np.where(qn > 0, qn, 1.0), 1.0)
     uy = np.where(qn > 0, qy / np.where(qn > 0, qn, 1.0), 0.0)
@@ -171,17 +174,32 @@ def features_and_labels(scene, cam, region_xy):
     c2q, s2q = ux * ux - uy * uy, 2 * ux * uy
     sr = np.sqrt(a * ux * ux + 2 * b * ux * uy + c * uy * uy)
     lr = np.log(rho)
-    F = np.zeros((n, K))
-    F[:, 0] = np.where(valid, un, 0.0)
-    F[:, 1] = np.where(valid, vn, 0.0)
+    G = np.zeros((len(u), 9))
     with np.errstate(divide="ignore", invalid="ignore"):
-        F[:, 2] = np.where(valid, np.log(np.where(valid, tz, 1.0) * rho / float(np.float32(cam.fx))), 0.0)
-    F[:, 3] = np.where(valid, 0.5 * np.log(l1) - lr, 0.0)
-    F[:, 4] = np.where(valid, 0.5 * np.log(l2) - lr, 0.0)
-    F[:, 5] = np.where(valid, np.log(sr) - lr, 0.0)
-    F[:, 6] = np.where(valid, c2p * c2q + s2p * s2q, 0.0)
-    F[:, 7] = np.where(valid, s2p * c2q - c2p * s2q, 0.0)
-    F[:, 8] = np.where(valid, np.clip((rho - qn) / sr, -8.0, 8.0), 0.0)
+        G[:, 0] = np.where(valid, un, 0.0)
+        G[:, 1] = np.where(valid, vn, 0.0)
+        G[:, 2] = np.where(valid, np.log(np.where(valid, tz, 1.0) * rho / fx), 0.0)
+        G[:, 3] = np.where(valid, 0.5 * np.log(l1) - lr, 0.0)
+        G[:, 4] = np.where(valid, 0.5 * np.log(l2) - lr, 0.0)
+        G[:, 5] = np.where(valid, np.log(sr) - lr, 0.0)
+        G[:, 6] = np.where(valid, c2p * c2q + s2p * s2q, 0.0)
+        G[:, 7] = np.where(valid, s2p * c2q - c2p * s2q, 0.0)
+        G[:, 8] = np.where(valid, np.clip((rho - qn) / sr, -8.0, 8.0), 0.0)
+    mags = dict(rho=rho, qn=qn, mid=mid, rad=rad, l1=l1, l2=l2, sr=sr,
+                sq=np.abs(a) * ux * ux + 2 * np.abs(b * ux * uy) + np.abs(c) * uy * uy,
+                ac=np.abs(a) + np.abs(b) + np.abs(c))
+    return G, mags
+
+
+def features_and_labels(scene, cam, region_xy):
+    """Returns (F [n, 64], valid [n] bool, sel [n] uint8, coverage [n])."""
+    n = scene.xyz.shape[1]
+    xyz, V, t, uu, vv, valid = _view_centre(scene, cam)
+    sp = _o.preprocess(scene, cam)
+    a, b, c = sp["cov2d"][0::3], sp["cov2d"][1::3], sp["cov2d"][2::3]
+    G, _ = _geometry(uu, vv, t[2], a, b, c, valid, region_xy, float(np.float32(cam.fx)))
+    F = np.zeros((n, K))
+    F[:, :9] = G
     F[:, 9] = np.asarray(scene.log_scale, np.float32).astype(np.float64).mean(0)
     F[:, 10] = np.asarray(scene.opacity_logit, np.float32)
     F[:, 11:59] = np.asarray(scene.sh, np.float32).reshape(48, n).T
@@ -212,6 +230,118 @@ def rendered_coverage(scene, cam, region_xy, plain_sel):
     den = _o.weight_sums(sp, off, ids, np.ones(H * W), 2)
     with np.errstate(invalid="ignore", divide="ignore"):
         return np.where(den > 0, np.minimum(num / den, 1.0), np.asarray(plain_sel, np.float64))
+
+
+# A float32 evaluation of the features departs from them through (1) its
+# inputs: the view-space centre (three float32 FMAs of the view transform,
+# e_t = 4 u32 (sum_k |V_ik x_k| + |V_i3|)), the projected centre (an
+# approximate reciprocal of t_z, 2^-22 relative, and two roundings) and the
+# dilated 2D covariance (within COV_REL sqrt(a c) per entry, the render's
+# margin), carried through the features by central differences of the FP64
+# features over each input's error (times 2 for the curvature), and (2) the
+# roundings of its own steps, bounded from the magnitudes they act on
+# (cancellations in mid - rad, a - c, rho - |q| and the quadratic form), and
+# the fast logarithms (LOG_ERR absolute).
+U32 = 2.0 ** -24
+COV_REL = 1e-5
+LOG_ERR = 2e-6
+
+
+def feature_bound(scene, cam, region_xy):
+    """(F, valid, E): the features of features_and_labels and, per element,
+    a bound on a float32 implementation's departure from F before its bf16
+    rounding (so its bf16 feature lies in [bf16(F - E), bf16(F + E)])."""
+    n = scene.xyz.shape[1]
+    xyz, V, t, uu, vv, valid = _view_centre(scene, cam)
+    fx, fy = float(np.float32(cam.fx)), float(np.float32(cam.fy))
+    cx, cy = float(np.float32(cam.cx)), float(np.float32(cam.cy))
+    et = 4 * U32 * (np.abs(V[:, :3]) @ np.abs(xyz) + np.abs(V[:, 3:4]))
+    tz = np.where(valid, t[2], 1.0)
+    rel_iz = et[2] / np.abs(tz) + 2.0 ** -22
+    eu = fx * (et[0] / np.abs(tz) + np.abs(t[0] / tz) * rel_iz) + 2 * U32 * (np.abs(uu) + abs(cx))
+    ev = fy * (et[1] / np.abs(tz) + np.abs(t[1] / tz) * rel_iz) + 2 * U32 * (np.abs(vv) + abs(cy))
+    sp = _o.preprocess(scene, cam)
+    a, b, c = sp["cov2d"][0::3], sp["cov2d"][1::3], sp["cov2d"][2::3]
+    ecov = COV_REL * np.sqrt(np.abs(np.where(valid, a, 1.0) * np.where(valid, c, 1.0)))
+    base = (uu, vv, t[2], a, b, c)
+    G, m = _geometry(*base, valid, region_xy, fx)
+    E = np.zeros((n, K))
+    for k, e in enumerate((eu, ev, et[2], ecov, ecov, ecov)):
+        hi = list(base)
+        lo = list(base)
+        hi[k] = base[k] + e
+        lo[k] = base[k] - e
+        Gh, _ = _geometry(*hi, valid, region_xy, fx)
+        Gl, _ = _geometry(*lo, valid, region_xy, fx)
+        E[:, :9] += np.abs(Gh - Gl)       # twice the central difference
+    # the float32 steps' own roundings
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r_eig = 8 * U32 * (m["mid"] + m["rad"])
+        E[:, 0] += 8 * U32 * np.abs(G[:, 0])
+        E[:, 1] += 8 * U32 * np.abs(G[:, 1])
+        E[:, 2] += LOG_ERR + 8 * U32
+        E[:, 3] += 2 * LOG_ERR + 0.5 * r_eig / m["l1"]
+        E[:, 4] += 2 * LOG_ERR + 0.5 * r_eig / np.where(m["l2"] > 0, m["l2"], np.inf)
+        E[:, 5] += 2 * LOG_ERR + 8 * U32 * m["sq"] / (m["sr"] ** 2)
+        rot = 16 * U32 * m["ac"] / np.where(m["rad"] > 0, m["rad"], np.inf)
+        E[:, 6] += rot + 16 * U32
+        E[:, 7] += rot + 16 * U32
+        E[:, 8] += 8 * U32 * (m["rho"] + m["qn"]) / m["sr"] + 8 * U32 * np.abs(G[:, 8])
+    E[:, :9] = np.where(valid[:, None] & np.isfinite(E[:, :9]), E[:, :9],
+                        np.where(valid[:, None], np.inf, 0.0))
+    F = np.zeros((n, K))
+    F[:, :9] = G
+    ls = np.asarray(scene.log_scale, np.float32).astype(np.float64)
+    F[:, 9] = ls.mean(0)
+    E[:, 9] = 4 * U32 * np.abs(ls).sum(0)
+    F[:, 10] = np.asarray(scene.opacity_logit, np.float32)
+    F[:, 11:59] = np.asarray(scene.sh, np.float32).reshape(48, n).T
+    return F, valid, E
+
+
+def bf16_within(x, F, E):
+    """Whether bf16 values x lie in [bf16(F - E), bf16(F + E)] (the bf16
+    rounding of any value within E of F: the rounding is monotone)."""
+    lo, hi = bf16(F - E), bf16(F + E)
+    return (x >= lo) & (x <= hi)
+
+
+def coverage_bound(scene, cam, region_xy, plain_sel, doubt_px=1e-3):
+    """(coverage, lo, hi): rendered_coverage and the interval a float32
+    implementation's label lies in: its two sums within
+    oracle.weight_sums_bound (pixel-centre region tests within doubt_px of
+    the boundary taken either way), the ratio and its float32 division; where
+    the sum over all pixels may be 0, any value in [0, 1] (a splat that may
+    reach no pixel takes its plain bit)."""
+    sp = _o.preprocess(scene, cam)
+    tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
+    off, ids = _o.tile_lists(sp, _o.depth_order(sp), tx, ty)
+    H, W = cam.height, cam.width
+    py, px = np.mgrid[0:H, 0:W]
+    pxf, pyf = px.ravel().astype(np.float64), py.ravel().astype(np.float64)
+    xy = np.asarray(region_xy, np.float64).reshape(-1, 2)
+    inside = point_in_polygon(pxf, pyf, xy).astype(np.float64)
+    dist = np.full(len(pxf), np.inf)
+    for i in range(len(xy)):
+        ax, ay = xy[i - 1]
+        bx, by = xy[i]
+        ex, ey = bx - ax, by - ay
+        tt = np.clip(((pxf - ax) * ex + (pyf - ay) * ey) / (ex * ex + ey * ey), 0.0, 1.0)
+        dist = np.minimum(dist, np.hypot(pxf - ax - tt * ex, pyf - ay - tt * ey))
+    doubt = (dist <= doubt_px).astype(np.float64)
+    num = _o.weight_sums(sp, off, ids, inside, 2)
+    den = _o.weight_sums(sp, off, ids, np.ones(H * W), 2)
+    bn = _o.weight_sums_bound(sp, off, ids, inside, 2, doubt=doubt)
+    bd = _o.weight_sums_bound(sp, off, ids, np.ones(H * W), 2)
+    plain = np.asarray(plain_sel, np.float64)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        cov = np.where(den > 0, np.minimum(num / den, 1.0), plain)
+        sure = den > bd
+        lo = np.where(sure, np.maximum(num - bn, 0.0) / (den + bd) * (1 - 2.0 ** -22), 0.0)
+        hi = np.where(sure, np.minimum((num + bn) / np.where(sure, den - bd, 1.0), 1.0)
+                      * (1 + 2.0 ** -22), 1.0)
+    hi = np.minimum(hi, 1.0)
+    return cov, lo, hi
 
 
 # ---------------------------------------------------------------------------

@@ -1059,10 +1059,14 @@ void oracle_color_grad_tiles(const oracle_splats* s, const int64_t* offsets, con
  * float32 keys may tie may swap, which moves either's T by the other's
  * alpha / (1 - alpha); the sums over pixels add gamma_m of the magnitudes,
  * m the splat's contributing pixels plus 8, unit roundoff 2^-23. dLdy: HWC
- * [H*W*3]; bound: [3n], accumulated (the caller zeroes it). */
-void oracle_color_grad_bound_tiles(int64_t n, const oracle_splats* s, const int64_t* offsets,
-                                   const int32_t* ids, int width, int height, const double* dLdy,
-                                   const oracle_margins* mg, double* bound) {
+ * [H*W*3]; bound: [3n], accumulated (the caller zeroes it). The walk below
+ * serves any per-pixel weight in place of dLdy and terms (alpha T)^power
+ * (power 1 or 2: relative errors scale by the power), with doubt[p] (may be
+ * NULL) the largest change of a weight on the float32 side. */
+static void weight_bound_walk(int64_t n, const oracle_splats* s, const int64_t* offsets,
+                              const int32_t* ids, int width, int height, const double* dLdy,
+                              const double* doubt, int power, const oracle_margins* mg,
+                              double* bound) {
     const int tiles_x = (width + TILE - 1) / TILE, tiles_y = (height + TILE - 1) / TILE;
     const double a_min = 1.0 / 255.0;
     double* absum = (double*)calloc((size_t)(3 * n + 1), sizeof(double));
@@ -1073,6 +1077,8 @@ void oracle_color_grad_bound_tiles(int64_t n, const oracle_splats* s, const int6
             for (int y = ty * TILE; y < ty * TILE + TILE && y < height; ++y)
                 for (int x = tx * TILE; x < tx * TILE + TILE && x < width; ++x) {
                     const double* g = &dLdy[3 * ((int64_t)y * width + x)];
+                    static const double no_doubt[3] = {0.0, 0.0, 0.0};
+                    const double* dg = doubt ? &doubt[3 * ((int64_t)y * width + x)] : no_doubt;
                     double T = 1.0, eT = 0.0;
                     int after_doubtful_stop = 0;
                     int64_t prev = -1;
@@ -1095,14 +1101,14 @@ void oracle_color_grad_bound_tiles(int64_t n, const oracle_splats* s, const int6
                                           0.5 * mg->eps_cov * sg * sg + mg->eps_exp * (fabs(p) + 1.0);
                         const int near_threshold = fabs(p + 0.5 * kk) <= ep;
                         /* the largest this splat's term can be on the float32 side */
-                        const double wmax = alpha * exp(ep) * T * exp(eT);
+                        const double wmax = pow(alpha * exp(ep) * T * exp(eT), (double)power);
                         int in_doubt = after_doubtful_stop || near_threshold || !s->valid[i] ||
                                        (s->fp_flag[i] & 2);
                         if (!s->valid[i] || alpha < a_min) {
                             if (in_doubt && alpha * exp(ep) >= a_min) {
                                 for (int ch = 0; ch < 3; ++ch) {
-                                    bound[3 * i + ch] += fabs(g[ch]) * wmax;
-                                    absum[3 * i + ch] += fabs(g[ch]) * wmax;
+                                    bound[3 * i + ch] += (fabs(g[ch]) + dg[ch]) * wmax;
+                                    absum[3 * i + ch] += (fabs(g[ch]) + dg[ch]) * wmax;
                                 }
                                 ++cnt[i];
                                 /* taken on the float32 side, it lowers the later T */
@@ -1117,21 +1123,22 @@ void oracle_color_grad_bound_tiles(int64_t n, const oracle_splats* s, const int6
                         if (testT < 1e-4 && !stop_in_doubt && !after_doubtful_stop) break;
                         if (after_doubtful_stop && testT < 1e-4 * exp(-eT_next)) break;
                         in_doubt = in_doubt || stop_in_doubt;
-                        double rel = ea + eT + 4.0 * 0x1p-24;
+                        double rel = power * (ea + eT) + 4.0 * power * 0x1p-24;
                         if (prev >= 0 && keys_may_tie(s->depth[prev], s->depth[i], mg->eps_depth)) {
                             /* the pair may swap: each one's T by the other's factor */
-                            const double wp = prev_alpha * prev_T * exp(prev_eT);
-                            const double fp = alpha / (1.0 - alpha);
+                            const double wp = pow(prev_alpha * prev_T * exp(prev_eT), (double)power);
+                            const double fp = pow(1.0 / (1.0 - alpha), (double)power) - 1.0;
                             for (int ch = 0; ch < 3; ++ch) {
                                 bound[3 * prev + ch] += fabs(g[ch]) * wp * fp;
                                 absum[3 * prev + ch] += fabs(g[ch]) * wp * fp;
                             }
-                            rel += prev_alpha / (1.0 - prev_alpha);
+                            rel += pow(1.0 / (1.0 - prev_alpha), (double)power) - 1.0;
                         }
                         for (int ch = 0; ch < 3; ++ch) {
-                            const double term = fabs(g[ch]) * alpha * T;
-                            bound[3 * i + ch] += in_doubt ? fabs(g[ch]) * wmax : term * rel;
-                            absum[3 * i + ch] += fabs(g[ch]) * wmax;
+                            const double term = fabs(g[ch]) * pow(alpha * T, (double)power);
+                            bound[3 * i + ch] += in_doubt ? (fabs(g[ch]) + dg[ch]) * wmax
+                                                          : term * rel + dg[ch] * wmax;
+                            absum[3 * i + ch] += (fabs(g[ch]) + dg[ch]) * wmax;
                         }
                         ++cnt[i];
                         if (near_threshold) eT_next += alpha / (1.0 - alpha);
@@ -1152,6 +1159,36 @@ void oracle_color_grad_bound_tiles(int64_t n, const oracle_splats* s, const int6
     }
     free(absum);
     free(cnt);
+}
+
+void oracle_color_grad_bound_tiles(int64_t n, const oracle_splats* s, const int64_t* offsets,
+                                   const int32_t* ids, int width, int height, const double* dLdy,
+                                   const oracle_margins* mg, double* bound) {
+    weight_bound_walk(n, s, offsets, ids, width, height, dLdy, NULL, 1, mg, bound);
+}
+
+/* The same bound for the sums of oracle_weight_sums_tiles (weights [H*W],
+ * power 1 or 2), with a per-pixel doubt on the weight (doubt [H*W], may be
+ * NULL: a weight that may be off by up to doubt[p] on the float32 side, e.g.
+ * a region test of a pixel centre near the region's boundary). bound: [n],
+ * accumulated. */
+void oracle_weight_sums_bound_tiles(int64_t n, const oracle_splats* s, const int64_t* offsets,
+                                    const int32_t* ids, int width, int height,
+                                    const double* pixel_weight, const double* doubt, int power,
+                                    const oracle_margins* mg, double* bound) {
+    const int64_t np = (int64_t)width * height;
+    double* g3 = (double*)calloc((size_t)(3 * np), sizeof(double));
+    double* d3 = doubt ? (double*)calloc((size_t)(3 * np), sizeof(double)) : NULL;
+    double* b3 = (double*)calloc((size_t)(3 * n + 3), sizeof(double));
+    for (int64_t p = 0; p < np; ++p) {
+        g3[3 * p] = pixel_weight[p];
+        if (d3) d3[3 * p] = doubt[p];
+    }
+    weight_bound_walk(n, s, offsets, ids, width, height, g3, d3, power, mg, b3);
+    for (int64_t i = 0; i < n; ++i) bound[i] += b3[3 * i];
+    free(g3);
+    free(d3);
+    free(b3);
 }
 
 /* Per-splat sums of a per-pixel weight times (alpha_i(p) T_i(p))^power over

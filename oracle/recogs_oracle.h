@@ -174,6 +174,12 @@ void oracle_color_grad_tiles(const oracle_splats* s, const int64_t* offsets, con
 void oracle_color_grad_bound_tiles(int64_t n, const oracle_splats* s, const int64_t* offsets,
                                    const int32_t* ids, int width, int height, const double* dLdy,
                                    const oracle_margins* mg, double* bound);
+/* The same bound for oracle_weight_sums_tiles' sums, with a per-pixel doubt
+ * on the weight (may be NULL); bound: [n], accumulated. */
+void oracle_weight_sums_bound_tiles(int64_t n, const oracle_splats* s, const int64_t* offsets,
+                                    const int32_t* ids, int width, int height,
+                                    const double* pixel_weight, const double* doubt, int power,
+                                    const oracle_margins* mg, double* bound);
 void oracle_sh_grad(int64_t n, const float* xyz, const oracle_camera* cam, const double* rgb,
                     const double* grad_rgb, double* grad_sh);
 

@@ -4,11 +4,11 @@ recolour) against the FP64 oracle in oracle/mlp.py, and the test of what the
 trained network gains over the plain selection.
 
 Tolerances: SH and opacity features are the same bf16 roundings of the same
-float32 inputs (exact); the selection-view geometry within two bf16 ulps
-(99.9%: near-isotropic footprints make the orientation ill-conditioned);
-tint-weight labels (sums of (alpha T)^2 over float32 and FP64 renders)
-within 1e-3 for 99% of the Gaussians (the rest reach pixels whose render the
-oracle flags);
+float32 inputs (exact); the selection-view geometry is the bf16 of a value
+within oracle.mlp.feature_bound of the FP64 features (input errors carried
+through the features, the float32 steps' roundings); tint-weight labels lie
+in the interval oracle.mlp.coverage_bound derives from the bounds on both
+sums of (alpha T)^2 (decisions in doubt taken either way);
 network outputs and gradients are compared on the GPU's own bf16 features,
 element by element within the bounds oracle/mlp.py derives for a float32
 implementation (accumulation order, GELU and sigmoid in float32, bf16
@@ -62,16 +62,21 @@ def test_features_and_labels_match_the_oracle(lib, ctx):
     np.testing.assert_array_equal(Vg, Vo)
     Fo16 = omlp.bf16(Fo)
     np.testing.assert_array_equal(Fg[:, 10:], Fo16[:, 10:])           # opacity, SH, padding
-    # geometry in the selection view: float32 against FP64, then bf16
-    ulp = np.maximum(np.abs(Fo16[:, :10]), 1e-30) * 2.0 ** -7
-    geo = np.abs(Fg[:, :10] - Fo16[:, :10]) <= 2.01 * ulp + 1e-3
-    assert geo[Vo].mean() >= 0.999, np.argwhere(~geo & Vo[:, None])[:5]
+    # geometry in the selection view and the mean log-scale: the bf16 of
+    # any value within the oracle's bound on a float32 implementation
+    Fb, Vb, E = omlp.feature_bound(scene, cam, reg.xy)
+    ok = omlp.bf16_within(Fg[:, :10], Fb[:, :10], E[:, :10])
+    assert ok.all(), np.argwhere(~ok)[:5]
     edit = sg.Edit(reg, np.eye(3, dtype=np.float32), cam)
     _, near = oracle.select(scene, edit, cam)
     ok = near == 0
     np.testing.assert_array_equal(Lg[ok, 0], So[ok].astype(np.float32))
-    close = np.abs(Lg[:, 1] - Co) <= 1e-3
-    assert close.mean() >= 0.99, close.mean()
+    assert np.all((Lg[~ok, 0] == 0) | (Lg[~ok, 0] == 1))
+    # tint-weight labels: within the interval of the bounds on both sums
+    Cb, lo, hi = omlp.coverage_bound(scene, cam, reg.xy, So)
+    np.testing.assert_array_equal(Cb, Co)
+    inside = (Lg[:, 1] >= lo) & (Lg[:, 1] <= hi)
+    assert inside.all(), (Lg[~inside, 1][:5], lo[~inside][:5], hi[~inside][:5])
     assert 0.02 < Co.mean() < 0.9 and ((Co > 0.05) & (Co < 0.95)).sum() > 50
 
 

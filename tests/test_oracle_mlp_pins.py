@@ -331,3 +331,153 @@ def test_grad_bound_covers_a_float32_implementation(scale, monkeypatch):
     monkeypatch.setattr(mlp, "_bf16_spread", lambda v, d: np.zeros_like(np.asarray(v, float)))
     _, g, no_flips = mlp.grad_bound(theta, X, sel, cov, batch=n, depth=depth)
     assert np.any(np.abs(_f32_grad(theta, X, sel, cov, n) - g) > no_flips)
+
+
+def _f32_features(scene, cam, xy):
+    """Features 0-9 of a float32 implementation: the view transform, the
+    projection, the radial frame, the eigen-decomposition and the logs in
+    float32 (numpy rounds each step), from the oracle's 2D covariance
+    rounded to float32."""
+    import oracle as O
+    f32 = np.float32
+    x = np.asarray(scene.xyz, f32)
+    V = np.asarray(cam.world_to_view, f32).reshape(3, 4)
+    t = [(V[i, 0] * x[0] + V[i, 1] * x[1] + V[i, 2] * x[2] + V[i, 3]).astype(f32) for i in range(3)]
+    tz = t[2]
+    valid = tz > f32(cam.z_near)
+    tzs = np.where(valid, tz, f32(1))
+    iz = (f32(1) / tzs).astype(f32)
+    u = (f32(cam.fx) * (t[0] * iz) + f32(cam.cx)).astype(f32)
+    v = (f32(cam.fy) * (t[1] * iz) + f32(cam.cy)).astype(f32)
+    xy = np.asarray(xy, np.float64).reshape(-1, 2)
+    cen = xy.mean(0).astype(f32)
+    qx, qy = (u - cen[0]).astype(f32), (v - cen[1]).astype(f32)
+    lam = np.full(len(u), np.inf, f32)
+    for i in range(len(xy)):
+        ax, ay = (xy[i - 1] - xy.mean(0)).astype(f32)
+        ex, ey = (xy[i] - xy[i - 1]).astype(f32)
+        den = (qx * ey - qy * ex).astype(f32)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            idn = (f32(1) / den).astype(f32)
+            l = ((ax * ey - ay * ex) * idn).astype(f32)
+            sp = ((ax * qy - ay * qx) * idn).astype(f32)
+        ok = (den != 0) & (l > 0) & (sp >= 0) & (sp <= 1) & (l < lam)
+        lam = np.where(ok, l, lam)
+    qn = np.sqrt(qx * qx + qy * qy).astype(f32)
+    mean_r = f32(np.sqrt(((xy - xy.mean(0)) ** 2).sum(1)).mean())
+    rho = np.where(np.isfinite(lam) & (qn > 0), lam * qn, mean_r).astype(f32)
+    sp_ = O.preprocess(scene, cam)
+    a, b, c = (sp_["cov2d"][k::3].astype(f32) for k in range(3))
+    a, b, c = np.where(valid, a, f32(1)), np.where(valid, b, f32(0)), np.where(valid, c, f32(1))
+    iq = np.where(qn > 0, f32(1) / np.where(qn > 0, qn, f32(1)), f32(0)).astype(f32)
+    ux = np.where(qn > 0, qx * iq, f32(1)).astype(f32)
+    uy = np.where(qn > 0, qy * iq, f32(0)).astype(f32)
+    mid = (f32(0.5) * (a + c)).astype(f32)
+    rad = np.sqrt(f32(0.25) * (a - c) * (a - c) + b * b).astype(f32)
+    irad = np.where(rad > 0, f32(1) / np.where(rad > 0, rad, f32(1)), f32(0)).astype(f32)
+    c2p = np.where(rad > 0, f32(0.5) * (a - c) * irad, f32(1)).astype(f32)
+    s2p = np.where(rad > 0, b * irad, f32(0)).astype(f32)
+    c2q, s2q = (ux * ux - uy * uy).astype(f32), (f32(2) * ux * uy).astype(f32)
+    sr = np.sqrt(a * ux * ux + f32(2) * b * ux * uy + c * uy * uy).astype(f32)
+    lr = np.log(rho).astype(f32)
+    G = np.zeros((len(u), 10), f32)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        G[:, 0] = (qx / rho)
+        G[:, 1] = (qy / rho)
+        G[:, 2] = np.log(tzs * rho * (f32(1) / f32(cam.fx)))
+        G[:, 3] = f32(0.5) * np.log(mid + rad) - lr
+        G[:, 4] = f32(0.5) * np.log(mid - rad) - lr
+        G[:, 5] = np.log(sr) - lr
+        G[:, 6] = c2p * c2q + s2p * s2q
+        G[:, 7] = s2p * c2q - c2p * s2q
+        G[:, 8] = np.clip((rho - qn) * (f32(1) / sr), f32(-8), f32(8))
+    G[:, :9] = np.where(valid[:, None], G[:, :9], f32(0))
+    ls = np.asarray(scene.log_scale, f32)
+    G[:, 9] = ((ls[0] + ls[1] + ls[2]) * f32(1.0 / 3.0)).astype(f32)
+    return G.astype(np.float64), valid
+
+
+def test_feature_bound_covers_a_float32_implementation():
+    """Every feature of a float32 implementation, rounded to bf16, lies in
+    the bf16 interval feature_bound gives; the bound is a small fraction of
+    a bf16 step except for the orientation of near-isotropic footprints;
+    without the input-error terms it is exceeded."""
+    from paper_2511_18441_b300 import scenegen as sgen
+    w = sgen.paper_scale_workload(n=20000, seed=7, width=320, height=240)
+    reg = sgen.random_polygons(1, 320, 240, 11)[0]
+    F, valid, E = mlp.feature_bound(w.scene, w.camera, reg.xy)
+    G, v32 = _f32_features(w.scene, w.camera, reg.xy)
+    assert np.array_equal(valid, v32)
+    ok = mlp.bf16_within(mlp.bf16(G), F[:, :10], E[:, :10])
+    assert ok.all(), np.argwhere(~ok)[:5]
+    step = np.maximum(np.abs(F[valid, :6]), 1e-3) * 2.0 ** -8
+    assert np.median(E[valid, :6] / step) < 0.02
+    # the float32 result does move by more than its own roundings would allow
+    loose = np.abs(G[:, :9] - F[:, :9]) > 64 * 2.0 ** -24 * (1 + np.abs(F[:, :9]))
+    assert loose[valid].any()
+
+
+def _f32_weight_sums(sp, off, ids, weight, width, height, power):
+    """Sums of weight (alpha T)^power per splat from a float32 walk (as
+    f32_color_grad of the gradient pins, one channel)."""
+    f32 = np.float32
+    n = sp["n"]
+    u, v = sp["u"].astype(f32), sp["v"].astype(f32)
+    A, B, Cc = (sp["conic"][k::3].astype(f32) for k in range(3))
+    sig = sp["opacity"].astype(f32)
+    valid = sp["valid"].astype(bool)
+    out = np.zeros(n, f32)
+    wgt = np.asarray(weight, f32).reshape(height, width)
+    tx = (width + 15) // 16
+    for t in range(len(off) - 1):
+        x0, y0 = (t % tx) * 16, (t // tx) * 16
+        xs, ys = np.meshgrid(np.arange(x0, min(x0 + 16, width)), np.arange(y0, min(y0 + 16, height)))
+        xs, ys = xs.ravel().astype(f32), ys.ravel().astype(f32)
+        gp = wgt[ys.astype(int), xs.astype(int)]
+        T = np.ones(len(xs), f32)
+        live = np.ones(len(xs), bool)
+        for k in range(off[t], off[t + 1]):
+            i = int(ids[k])
+            if not valid[i]:
+                continue
+            dx, dy = xs - u[i], ys - v[i]
+            p = np.minimum((f32(-0.5) * (A[i] * dx * dx + Cc[i] * dy * dy) - B[i] * dx * dy).astype(f32),
+                           f32(0))
+            al = np.minimum(f32(0.99), (sig[i] * np.exp(p)).astype(f32))
+            take = live & (al >= f32(1.0 / 255.0))
+            nT = (T * (f32(1) - al)).astype(f32)
+            stop = take & (nT < f32(1e-4))
+            live &= ~stop
+            take &= ~stop
+            wv = (al * T).astype(f32)
+            for val in (gp[take] * wv[take] ** power).astype(f32):
+                out[i] = f32(out[i] + val)
+            T = np.where(take, nT, T)
+    return out.astype(np.float64)
+
+
+def test_coverage_bound_covers_a_float32_walk():
+    """The tint-weight label of a float32 walk (sums of (alpha T)^2 inside
+    the polygon and over all pixels, then their ratio) lies in the interval
+    coverage_bound gives, for every splat."""
+    import oracle as O
+    from paper_2511_18441_b300 import scenegen as sgen
+    w = sgen.paper_scale_workload(n=4000, seed=5, width=96, height=64)
+    reg = sgen.random_polygons(1, 96, 64, 3)[0]
+    F, valid, sel, cov = mlp.features_and_labels(w.scene, w.camera, reg.xy)
+    c2, lo, hi = mlp.coverage_bound(w.scene, w.camera, reg.xy, sel)
+    np.testing.assert_array_equal(c2, cov)
+    sp = O.preprocess(w.scene, w.camera)
+    off, ids = O.tile_lists(sp, O.depth_order(sp), 6, 4)
+    py, px = np.mgrid[0:64, 0:96]
+    inside = mlp.point_in_polygon(px.ravel().astype(np.float64), py.ravel().astype(np.float64),
+                                  reg.xy).astype(np.float64)
+    num = _f32_weight_sums(sp, off, ids, inside, 96, 64, 2)
+    den = _f32_weight_sums(sp, off, ids, np.ones(96 * 64), 96, 64, 2)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ratio = np.minimum(num.astype(np.float32) / den.astype(np.float32), 1.0)
+    lab = np.where(den > 0, ratio, sel.astype(np.float64))
+    ok = (lab >= lo) & (lab <= hi)
+    assert ok.all(), (lab[~ok][:5], lo[~ok][:5], hi[~ok][:5])
+    reach = den > 0
+    assert reach.sum() > 500 and np.median((hi - lo)[reach]) < 1e-3
