@@ -102,7 +102,8 @@ def lib():
         L.oracle_sh_grad.argtypes = [C.c_int64, f32p, C.POINTER(Camera), f64p, f64p, f64p]
         L.oracle_pixel_outcomes.argtypes = [C.POINTER(Splats), i64p, i32p, C.c_int, C.c_int, i64p,
                                             C.c_int64, C.c_int64, i32p, i32p, f64p,
-                                            C.POINTER(Margins), C.c_int64, f64p, i64p, C.c_int]
+                                            C.POINTER(Margins), C.c_double, C.c_int64, f64p, i64p,
+                                            C.c_int]
         L.oracle_weight_sums_tiles.argtypes = [C.POINTER(Splats), i64p, i32p, C.c_int, C.c_int,
                                                f64p, C.c_int, f64p]
         _lib = L
@@ -326,11 +327,13 @@ def depth_keys(splats: SplatResult):
 
 
 def pixel_outcomes(splats: SplatResult, offsets, ids, px, py, bg=(0.0, 0.0, 0.0), mg=None,
-                   max_out=256, threads=None):
+                   max_out=256, threads=None, tau=None):
     """Every outcome (r, g, b, T) of the binned render at pixels (px[j],
     py[j]) that the doubtful decisions allow (the oracle's flags): returns
     (outcomes [npix, max_out, 4], counts [npix]; -1 where there are more
-    than max_out)."""
+    than max_out). With tau, each outcome also carries its median depth
+    (outcomes [npix, max_out, 5]), the crossing of tau in doubt branching
+    too."""
     cam = splats["camera"]
     px = np.ascontiguousarray(px, np.int32)
     py = np.ascontiguousarray(py, np.int32)
@@ -344,15 +347,16 @@ def pixel_outcomes(splats: SplatResult, offsets, ids, px, py, bg=(0.0, 0.0, 0.0)
     if n_extra == 0:
         extra = np.zeros(1, np.int64)
     bgv = np.ascontiguousarray(bg, np.float64)
-    out = np.zeros((max(npix, 1), max_out, 4))
+    out = np.zeros((max(npix, 1), max_out, 5))
     cnt = np.zeros(max(npix, 1), np.int64)
     m = mg if mg is not None else splats["margins"]
     s = splats.struct()
     lib().oracle_pixel_outcomes(C.byref(s), _ptr(offsets, i64p), _ptr(ids, i32p), cam.width,
                                 cam.height, _ptr(extra, i64p), n_extra, npix, _ptr(px, i32p),
-                                _ptr(py, i32p), _ptr(bgv, f64p), C.byref(m), int(max_out),
+                                _ptr(py, i32p), _ptr(bgv, f64p), C.byref(m),
+                                float(tau) if tau is not None else 0.0, int(max_out),
                                 _ptr(out, f64p), _ptr(cnt, i64p), _threads(threads))
-    return out[:npix], cnt[:npix]
+    return (out[:npix] if tau is not None else out[:npix, :, :4]), cnt[:npix]
 
 
 def render_tiles(splats: SplatResult, offsets, ids, tiles=None, bg=(0.0, 0.0, 0.0), mg=None,

@@ -791,17 +791,19 @@ typedef struct {
     const double* bg;
     int64_t max_out, n_out;
     int overflow;
-    double* out;              /* max_out x (r, g, b, T) */
+    double* out;              /* max_out x (r, g, b, T, median depth) */
+    double tau;               /* median-depth threshold; <= 0: no depth (0 recorded) */
 } outcome_walk;
 
-static void outcome_emit(outcome_walk* O, const double C[3], double T) {
+static void outcome_emit(outcome_walk* O, const double C[3], double T, double depth) {
     if (O->n_out >= O->max_out) {
         O->overflow = 1;
         return;
     }
-    double* o = O->out + 4 * O->n_out++;
+    double* o = O->out + 5 * O->n_out++;
     for (int ch = 0; ch < 3; ++ch) o[ch] = C[ch] + T * O->bg[ch];
     o[3] = T;
+    o[4] = depth;
 }
 
 static int next_permutation(int* a, int m) {
@@ -818,14 +820,16 @@ static int next_permutation(int* a, int m) {
 }
 
 /* The walk of Eq. 3 from position pos of seq (indices into O->e) with
- * transmittance T, colour C and T's accumulated relative uncertainty eT,
- * branching at each decision that is in doubt. Positions below permuted_to
- * already hold one order of their run. */
+ * transmittance T, colour C, T's accumulated relative uncertainty eT and
+ * the median depth so far (crossed: T has gone below tau), branching at
+ * each decision that is in doubt (with a depth threshold, also the
+ * crossing of tau). Positions below permuted_to already hold one order of
+ * their run. */
 static void outcome_walk_from(outcome_walk* O, int64_t* seq, int64_t pos, int64_t permuted_to,
-                              double T, const double C[3], double eT) {
+                              double T, const double C[3], double eT, double depth, int crossed) {
     if (O->overflow) return;
     if (pos == O->len) {
-        outcome_emit(O, C, T);
+        outcome_emit(O, C, T, depth);
         return;
     }
     const int64_t end = O->run_end[pos];
@@ -839,10 +843,10 @@ static void outcome_walk_from(outcome_walk* O, int64_t* seq, int64_t pos, int64_
             int perm[4] = {0, 1, 2, 3};
             do {
                 for (int k = 0; k < m; ++k) seq2[pos + k] = seq[pos + perm[k]];
-                outcome_walk_from(O, seq2, pos, end, T, C, eT);
+                outcome_walk_from(O, seq2, pos, end, T, C, eT, depth, crossed);
             } while (!O->overflow && next_permutation(perm, m));
         } else {
-            outcome_walk_from(O, seq, pos, end, T, C, eT);
+            outcome_walk_from(O, seq, pos, end, T, C, eT, depth, crossed);
             /* index order: insertion sort of the run by splat index */
             for (int a = 1; a < m; ++a) {
                 int64_t v = seq2[pos + a];
@@ -853,23 +857,37 @@ static void outcome_walk_from(outcome_walk* O, int64_t* seq, int64_t pos, int64_
                 }
                 seq2[pos + b + 1] = v;
             }
-            outcome_walk_from(O, seq2, pos, end, T, C, eT);
+            outcome_walk_from(O, seq2, pos, end, T, C, eT, depth, crossed);
         }
         free(seq2);
         return;
     }
     const outcome_entry* e = &O->e[seq[pos]];
-    if (e->take == 2) outcome_walk_from(O, seq, pos + 1, permuted_to, T, C, eT);  /* skipped */
+    if (e->take == 2)   /* skipped */
+        outcome_walk_from(O, seq, pos + 1, permuted_to, T, C, eT, depth, crossed);
     const double testT = T * (1.0 - e->alpha);
     const double eT_next = eT + e->alpha * e->ea / (1.0 - e->alpha) + 2.4e-7;
     const int near_stop = fabs(log(testT / 1e-4)) <= eT_next;
-    if (testT < 1e-4 || near_stop) outcome_emit(O, C, T);   /* stops before this splat */
+    if (testT < 1e-4 || near_stop) outcome_emit(O, C, T, depth);   /* stops before this splat */
     if (testT >= 1e-4 || near_stop) {
+        /* the median depth: this splat takes T below tau (Sec. 3.2.2), for
+         * sure, not at all, or either way within T's uncertainty */
+        int cross_opts[2], nopt = 0;
+        if (O->tau > 0.0 && !crossed) {
+            const int near_tau = fabs(log(testT / O->tau)) <= eT_next;
+            if (testT < O->tau || near_tau) cross_opts[nopt++] = 1;
+            if (testT >= O->tau || near_tau) cross_opts[nopt++] = 0;
+        } else {
+            cross_opts[nopt++] = 0;
+        }
         for (int k = 0; k < e->ncol; ++k) {
             const double* col = k == 0 ? &O->s->rgb[3 * e->idx] : &O->s->alt_rgb[3 * e->idx];
             double C2[3];
             for (int ch = 0; ch < 3; ++ch) C2[ch] = C[ch] + col[ch] * e->alpha * T;
-            outcome_walk_from(O, seq, pos + 1, permuted_to, testT, C2, eT_next);
+            for (int q = 0; q < nopt; ++q)
+                outcome_walk_from(O, seq, pos + 1, permuted_to, testT, C2, eT_next,
+                                  cross_opts[q] ? O->s->depth[e->idx] : depth,
+                                  crossed || cross_opts[q]);
         }
     }
 }
@@ -893,6 +911,7 @@ typedef struct {
     int64_t max_out;
     double* out;
     int64_t* n_out;
+    double tau;
 } outcomes_ctx;
 
 static void outcomes_range(void* vctx, int64_t b, int64_t e_) {
@@ -986,9 +1005,10 @@ static void outcomes_range(void* vctx, int64_t b, int64_t e_) {
                              : k + 1;
         int64_t* seq = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ne + 1));
         for (int64_t k = 0; k < ne; ++k) seq[k] = k;
-        outcome_walk O = {s, ent, run_end, ne, P->bg, P->max_out, 0, 0, P->out + 4 * P->max_out * j};
+        outcome_walk O = {s, ent, run_end, ne, P->bg, P->max_out, 0, 0,
+                          P->out + 5 * P->max_out * j, P->tau};
         const double C0[3] = {0.0, 0.0, 0.0};
-        outcome_walk_from(&O, seq, 0, 0, 1.0, C0, 0.0);
+        outcome_walk_from(&O, seq, 0, 0, 1.0, C0, 0.0, 0.0, !(1.0 >= P->tau) && P->tau > 0.0);
         P->n_out[j] = O.overflow ? -1 : O.n_out;
         free(seq);
         free(run_end);
@@ -1001,10 +1021,10 @@ static void outcomes_range(void* vctx, int64_t b, int64_t e_) {
 void oracle_pixel_outcomes(const oracle_splats* s, const int64_t* offsets, const int32_t* ids,
                            int width, int height, const int64_t* extra, int64_t n_extra,
                            int64_t npix, const int32_t* px, const int32_t* py, const double bg[3],
-                           const oracle_margins* mg, int64_t max_out, double* out, int64_t* n_out,
-                           int threads) {
+                           const oracle_margins* mg, double tau, int64_t max_out, double* out,
+                           int64_t* n_out, int threads) {
     outcomes_ctx P = {s, offsets, ids, width, height, (width + TILE - 1) / TILE, extra, n_extra,
-                      px, py, bg, mg, max_out, out, n_out};
+                      px, py, bg, mg, max_out, out, n_out, tau};
     parallel_for(npix, 4, threads, outcomes_range, &P);
 }
 

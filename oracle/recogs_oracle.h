@@ -155,13 +155,16 @@ void oracle_render_tiles_depth(const oracle_splats* s, const int64_t* offsets, c
  * splats whose float32 depth keys may be equal (every order of such a run of
  * up to 4 splats; the FP64 and the index order of a longer one), and splats
  * of `extra` (those with an ambiguous tile range or visibility, in any order)
- * that a float32 footprint may list for the pixel's tile. out: npix x max_out
- * x 4; n_out[j]: the number of outcomes, -1 if there are more than max_out. */
+ * that a float32 footprint may list for the pixel's tile; with tau > 0 also
+ * the median depth (Sec. 3.2.2) of each outcome, branching where T after a
+ * splat lies within its uncertainty of tau. out: npix x max_out x 5 (r, g,
+ * b, T, depth; depth 0 without tau); n_out[j]: the number of outcomes, -1
+ * if there are more than max_out. */
 void oracle_pixel_outcomes(const oracle_splats* s, const int64_t* offsets, const int32_t* ids,
                            int width, int height, const int64_t* extra, int64_t n_extra,
                            int64_t npix, const int32_t* px, const int32_t* py, const double bg[3],
-                           const oracle_margins* mg, int64_t max_out, double* out, int64_t* n_out,
-                           int threads);
+                           const oracle_margins* mg, double tau, int64_t max_out, double* out,
+                           int64_t* n_out, int threads);
 
 /* SH-only refit (Sec. 3.3, Eq. 6-7): the colour gradient dL/dc_i =
  * sum_p dL/dy_p alpha_i(p) T_i(p) of the binned render (accumulated into

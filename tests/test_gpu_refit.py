@@ -1,8 +1,9 @@
 """Median depth (Sec. 3.2.2) and the SH-only refit (Sec. 3.3, Eq. 6-7) on
 the GPU against the FP64 oracle.
 
-Depth maps are compared where neither the image nor the depth decision is
-flagged by the oracle; depths are float32 view depths (relative 1e-6).
+Depth maps are the float32 keys of the oracle's FP64 depths (half a float32
+spacing) where no decision is in doubt, and one of the outcomes' depths
+(oracle.pixel_outcomes with tau) where the oracle flags the pixel.
 Gradients are compared on targets that differ from the render by at least
 0.02 per channel, so that sign(y - target) is the same on both sides, and
 every element must lie within the oracle's bound for a float32
@@ -36,19 +37,32 @@ def dscene(scene, kind="f32"):
     return binding.DeviceScene.from_numpy(scene, "cuda", kind)
 
 
-def check_depth(gpu_depth, ref):
+def check_depth(gpu_depth, ref, sp, off, ids, tau, region=None):
     """The GPU's median depth is the float32 nearest the oracle's FP64 depth
     of the same Gaussian (its correctly rounded depth key): within half a
-    float32 spacing, both at a rounding midpoint."""
-    use = (ref["flag"] == 0) & (ref["dflag"] == 0)
+    float32 spacing, both at a rounding midpoint. Where the oracle flags the
+    pixel (a decision of the walk or the crossing of tau in doubt), it must
+    be that of one of the outcomes those decisions allow."""
+    half_ulp = lambda d: 0.5 * np.spacing(np.abs(d).astype(np.float32)).astype(np.float64)
+    sel = np.ones(ref["depth"].shape, bool) if region is None else region
+    clean = sel & (ref["flag"] == 0) & (ref["dflag"] == 0)
     d_or = ref["depth"]
     err = np.abs(gpu_depth.astype(np.float64) - d_or)
-    half_ulp = 0.5 * np.spacing(np.abs(d_or).astype(np.float32)).astype(np.float64)
-    bad = use & (err > half_ulp * (1 + 1e-9))
+    bad = clean & (err > half_ulp(d_or) * (1 + 1e-9))
     assert not bad.any(), (f"{int(bad.sum())} depth pixels differ, e.g. "
                            f"gpu {gpu_depth[bad][:5]} oracle {d_or[bad][:5]}")
-    assert use.mean() > 0.95
-    return float(use.mean())
+    ys, xs = np.nonzero(sel & ~clean)
+    if len(ys):
+        out, cnt = oracle.pixel_outcomes(sp, off, ids, xs, ys, tau=tau)
+        assert cnt.min() >= 1, "an outcome set overflowed"
+        g = gpu_depth[ys, xs].astype(np.float64)[:, None]
+        od = out[:, :, 4]
+        ok = (np.abs(g - od) <= half_ulp(od) * (1 + 1e-9)) & \
+             (np.arange(out.shape[1])[None, :] < cnt[:, None])
+        miss = ~ok.any(1)
+        assert not miss.any(), (f"{int(miss.sum())} flagged depth pixels match no outcome, e.g. "
+                                f"gpu {g[miss][:5, 0]}")
+    return float(clean.sum() / sel.sum()), int(len(ys))
 
 
 @pytest.mark.parametrize("tau", [0.5, 0.2, 0.9])
@@ -60,7 +74,7 @@ def test_median_depth_tiny(ctx, tau):
     sp = oracle.preprocess(w.scene, w.camera, w.edit)
     off, ids = oracle.tile_lists(sp, oracle.depth_order(sp), 16, 16)
     ref = oracle.render_tiles(sp, off, ids, tau=tau)
-    check_depth(parity.to_np(depth), ref)
+    check_depth(parity.to_np(depth), ref, sp, off, ids, tau)
     assert (parity.to_np(depth) > 0).mean() > 0.05
 
 
@@ -78,9 +92,7 @@ def test_median_depth_paper_scale_sampled_tiles(ctx):
     for t in tiles:
         y0, x0 = (t // tx) * 16, (t % tx) * 16
         sel[y0:y0 + 16, x0:x0 + 16] = True
-    d = np.where(sel, parity.to_np(depth), 0.0)
-    ref["flag"] = np.where(sel, ref["flag"], 0)
-    check_depth(d, ref)
+    check_depth(parity.to_np(depth), ref, sp, off, ids, 0.5, region=sel)
 
 
 def test_depth_mode_leaves_the_image_unchanged(ctx):

@@ -175,3 +175,40 @@ def test_depth_keys_round_to_nearest_and_mark_midpoints():
     o_key = np.lexsort((np.arange(2000), kk))
     assert not np.array_equal(o_depth, o_key)
     assert np.array_equal(kk[o_depth], kk[o_key])
+
+
+def test_median_depth_at_tau_gives_both_depths():
+    """Two splats of alpha 1/2 at one pixel and tau = 1/2: after the first
+    T = 1/2 = tau up to rounding, so the median depth (Sec. 3.2.2) is the
+    first splat's or the second's; at tau = 0.6 only the first's."""
+    sc = stack([0.0, 0.05], [0.0, 0.0], [(0.9, 0.1, 0.1), (0.1, 0.9, 0.1)])
+    ref, sp, off, ids = frame(sc, CAM)
+    assert abs(sp["opacity"][0] - 0.5) < 1e-7
+    d1, d2 = sp["depth"][0], sp["depth"][1]
+    out, cnt = oracle.pixel_outcomes(sp, off, ids, [8], [8], tau=0.5)
+    depths = set(np.round(out[0, :cnt[0], 4], 12))
+    assert depths == {round(d1, 12), round(d2, 12)}
+    out, cnt = oracle.pixel_outcomes(sp, off, ids, [8], [8], tau=0.6)
+    assert set(np.round(out[0, :cnt[0], 4], 12)) == {round(d1, 12)}
+    # and the colours are those of the plain walk (the depth branch only)
+    assert np.allclose(out[0, :cnt[0], :3], ref["rgb"][8, 8])
+
+
+def test_every_depth_pixel_has_its_render_among_its_outcomes():
+    """On the 10k-Gaussian workload with tau = 0.5: every pixel whose depth
+    decision is flagged has the binned render's depth among its outcomes'
+    depths."""
+    w = sg.tiny_workload()
+    sp = oracle.preprocess(w.scene, w.camera, w.edit)
+    off, ids = oracle.tile_lists(sp, oracle.depth_order(sp), 16, 16)
+    ref = oracle.render_tiles(sp, off, ids, tau=0.5)
+    ys, xs = np.nonzero(ref["dflag"] > 0)
+    assert len(ys) > 3
+    out, cnt = oracle.pixel_outcomes(sp, off, ids, xs, ys, tau=0.5)
+    assert cnt.min() >= 1
+    d = np.abs(out[:, :, 4] - ref["depth"][ys, xs][:, None])
+    d = np.where(np.arange(out.shape[1])[None, :] < cnt[:, None], d, np.inf)
+    assert d.min(1).max() == 0.0
+    # at least one of them has more than one depth
+    n_depths = [len(set(out[j, :cnt[j], 4])) for j in range(len(ys))]
+    assert max(n_depths) > 1
