@@ -555,6 +555,8 @@ def run_ours(args, rank, world, local):
             if kind == "f32":
                 e["pixels_over_2e-4"] = int((np.abs(d).max(-1) > 2e-4).sum())
                 e["oracle_flagged_pixels"] = int((ref_img["flag"] > 0).sum())
+                # blended contributors per pixel (alpha >= 1/255, before the stop)
+                e["mean_contributors_per_pixel"] = float(ref_img["ncontrib"].mean())
                 accuracy = e
             else:
                 variants[kind]["error"] = e
