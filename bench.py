@@ -561,6 +561,30 @@ def run_ours(args, rank, world, local):
             else:
                 variants[kind]["error"] = e
 
+    # the batched workload and the benchmark spec's combined form (BF16 SH,
+    # learned selection, one graph replay) on one GPU, so that the default
+    # run records them too (each is also a workload of its own)
+    if rank == 0 and world == 1 and not args.no_variants and not args.readback:
+        from paper_2511_18441_b300 import scenegen as sg
+        bw = sg.batched_workload(sizes=BATCH_SIZES, views_per_scene=BATCH_VIEWS_PER_SCENE)
+        sub = argparse.Namespace(**vars(args))
+        sub.sh_dtype, sub.steps, sub.warmup = "f32", 10, 3
+        bl = run_batch(sub, rank, world, local, emit=False, bw=bw)
+        variants["batch_64_views"] = {
+            "views_per_s": bl["value"], "ms_per_step": bl["ms_per_step"],
+            "per_view_views_per_s": bl["per_view_renders"]["views_per_s"],
+            "workload": bl["config"]["workload"], "api": "recogs_render_batch, one graph replay"}
+        sub.steps = 5
+        cl = run_combined(sub, rank, world, local, emit=False, bw=bw)
+        variants["combined_bf16_learned_batched"] = {
+            "views_per_s": cl["value"], "ms_per_step": cl["ms_per_step"],
+            "plain_f32_views_per_s": cl["plain_f32_form"]["views_per_s"],
+            "speedup_vs_plain_f32": cl["speedup_vs_plain_f32"],
+            "psnr_db_vs_fp64_oracle": {q["size"]: q["psnr_combined_db"]
+                                       for q in cl["quality_vs_fp64_oracle_of_the_plain_edit"]},
+            "workload": cl["config"]["workload"], "step": cl["config"]["step"]}
+        torch.cuda.set_device(local)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
@@ -594,7 +618,7 @@ BATCH_SIZES = (500_000, 1_000_000, 2_000_000, 4_000_000)
 BATCH_VIEWS_PER_SCENE = 16
 
 
-def run_batch(args, rank, world, local):
+def run_batch(args, rank, world, local, emit=True, bw=None):
     """4 scenes (0.5M, 1M, 2M, 4M Gaussians, different seeds), 16 ring views
     each at resolutions drawn from 720p/1080p/1440p/2160p, each scene with its
     own selection box and tint; one step renders all 64 views through one
@@ -607,7 +631,8 @@ def run_batch(args, rank, world, local):
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    bw = sg.batched_workload(sizes=BATCH_SIZES, views_per_scene=BATCH_VIEWS_PER_SCENE)
+    if bw is None:
+        bw = sg.batched_workload(sizes=BATCH_SIZES, views_per_scene=BATCH_VIEWS_PER_SCENE)
     scenes = [binding.DeviceScene.from_numpy(sc, dev, args.sh_dtype) for sc in bw.scenes]
     views = [dict(scene=si, camera=cam, edit=edit) for si, cam, edit in bw.views]
     pixels = sum(cam.width * cam.height for _, cam, _ in bw.views)
@@ -674,8 +699,10 @@ def run_batch(args, rank, world, local):
                                  "api": "recogs_render per view, with the read back"},
             "gpu_launches": launches, "clocks": clocks,
         }
-        print(json.dumps(line), flush=True)
+        if emit:
+            print(json.dumps(line), flush=True)
     ctx.close()
+    return line if rank == 0 else None
 
 
 # ---------------------------------------------------------------------------
@@ -1090,7 +1117,7 @@ def psnr_db(a, b):
     return 10.0 * math.log10(1.0 / mse) if mse > 0 else float("inf")
 
 
-def run_combined(args, rank, world, local):
+def run_combined(args, rank, world, local, emit=True, bw=None):
     """The batched workload (4 scenes of 0.5/1/2/4M Gaussians, 16 ring views
     each at 720p-2160p, a box selection and tint per scene) in two forms in
     the same run. Plain FP32: float32 SH, every view through recogs_render
@@ -1108,7 +1135,8 @@ def run_combined(args, rank, world, local):
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    bw = sg.batched_workload(sizes=BATCH_SIZES, views_per_scene=BATCH_VIEWS_PER_SCENE)
+    if bw is None:
+        bw = sg.batched_workload(sizes=BATCH_SIZES, views_per_scene=BATCH_VIEWS_PER_SCENE)
     ctx = binding.Context(local)
     stream = torch.cuda.current_stream(dev)
     nv = len(bw.views)
@@ -1252,9 +1280,11 @@ def run_combined(args, rank, world, local):
             "training_seconds": train_s,
             "gpu_launches": launches, "clocks": clocks,
         }
-        print(json.dumps(line), flush=True)
+        if emit:
+            print(json.dumps(line), flush=True)
     net.close()
     ctx.close()
+    return line if rank == 0 else None
 
 
 def main(argv=None):
