@@ -514,11 +514,10 @@ __global__ void __launch_bounds__(256) mlp_adam_kernel(float* __restrict__ p, fl
 // ---------------------------------------------------------------------------
 // features and labels
 
-// Projected centre and view depth of Gaussian i in the selection view;
-// false if t_z <= z_near (outside the learned domain).
-__device__ __forceinline__ bool sel_view(const DevCamera& cam, const float* xyz, int n, int i,
-                                         float& u, float& v, float& tz) {
-    float tx, ty;
+// Projected centre, view-space centre and view depth of Gaussian i in the
+// selection view; false if t_z <= z_near (outside the learned domain).
+__device__ __forceinline__ bool sel_view_t(const DevCamera& cam, const float* xyz, int n, int i,
+                                           float& u, float& v, float& tx, float& ty, float& tz) {
     view_point(cam, xyz[i], xyz[n + i], xyz[2 * n + i], tx, ty, tz);
     if (!(tz > cam.z_near)) return false;
     // the features are rounded to bf16 (2^-9 relative): an approximate
@@ -528,14 +527,18 @@ __device__ __forceinline__ bool sel_view(const DevCamera& cam, const float* xyz,
     v = __fmaf_rn(cam.fy, ty * iz, cam.cy);
     return true;
 }
+__device__ __forceinline__ bool sel_view(const DevCamera& cam, const float* xyz, int n, int i,
+                                         float& u, float& v, float& tz) {
+    float tx, ty;
+    return sel_view_t(cam, xyz, n, i, u, v, tx, ty, tz);
+}
 
 // The dilated 2D covariance (a, b, c) of Gaussian i in the selection view
-// (Eq. 1 with the EWA projection, the render's formula).
-__device__ __forceinline__ void sel_cov2d(const DevCamera& cam, const float* xyz, const float* lsc,
-                                          const float* quat, int n, int i, float& a, float& b,
-                                          float& c) {
-    float tx, ty, tz;
-    view_point(cam, xyz[i], xyz[n + i], xyz[2 * n + i], tx, ty, tz);
+// (Eq. 1 with the EWA projection, the render's formula), from its view-space
+// centre (tx, ty, tz).
+__device__ __forceinline__ void sel_cov2d(const DevCamera& cam, float tx, float ty, float tz,
+                                          const float* lsc, const float* quat, int n, int i,
+                                          float& a, float& b, float& c) {
     const float qw = quat[i], qx = quat[n + i], qy = quat[2 * n + i], qz = quat[3 * n + i];
     const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
     const float w = qw * qn, x = qx * qn, y = qy * qn, z = qz * qn;
@@ -609,15 +612,15 @@ __device__ __forceinline__ bool mlp_feature_row(int n, int i, const float* __res
                     : sh_dtype == RECOGS_F16 ? __half2float(reinterpret_cast<const __half*>(sh)[o])
                                              : __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(sh)[o]);
     }
-    float u = 0.f, v = 0.f, tz = 0.f;
-    const bool ok = sel_view(cam, xyz, n, i, u, v, tz);
+    float u = 0.f, v = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
+    const bool ok = sel_view_t(cam, xyz, n, i, u, v, tx, ty, tz);
 #pragma unroll
     for (int k = 0; k < 9; ++k) f[k] = 0.f;
     if (ok) {
         float un, vn, rho;
         radial(reg, fr, u, v, un, vn, rho);
         float a, b, c;
-        sel_cov2d(cam, xyz, lsc, quat, n, i, a, b, c);
+        sel_cov2d(cam, tx, ty, tz, lsc, quat, n, i, a, b, c);
         // unit radial direction (the +x axis at the centroid itself)
         const float qx = u - fr.cx, qy = v - fr.cy;
         const float qn = sqrtf(qx * qx + qy * qy);
@@ -883,21 +886,22 @@ __device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
 }
 
 // gelu() of two values, the same operations in pairs
+// (the same approximation of Phi, composed as GELU(z) = max(z, 0) - |z| (1 -
+// Phi(|z|)): z Phi(z) for either sign of z, without a select)
 __device__ __forceinline__ float2 gelu2(float2 z) {
-    const float2 a = make_float2(fabsf(z.x), fabsf(z.y));
-    const float2 d = ffma2(make_float2(0.2316419f, 0.2316419f), a, make_float2(1.0f, 1.0f));
+    const float2 na = make_float2(-fabsf(z.x), -fabsf(z.y));
+    const float2 d = ffma2(make_float2(-0.2316419f, -0.2316419f), na, make_float2(1.0f, 1.0f));
     const float2 t = make_float2(rcp_approx(d.x), rcp_approx(d.y));
     float2 p = ffma2(t, make_float2(0.5307027f, 0.5307027f), make_float2(-0.72657603f, -0.72657603f));
     p = ffma2(t, p, make_float2(0.7107069f, 0.7107069f));
     p = ffma2(t, p, make_float2(-0.14224836f, -0.14224836f));
     p = ffma2(t, p, make_float2(0.1274148f, 0.1274148f));
-    const float2 m = fmul2(fmul2(make_float2(-0.7213475f, -0.7213475f), a), a);
+    const float2 m = fmul2(fmul2(make_float2(-0.7213475f, -0.7213475f), z), z);
     float2 e;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(m.x));
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(m.y));
     const float2 q = fmul2(e, fmul2(p, t));     // 1 - Phi(|z|)
-    const float2 s = ffma2(q, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
-    return fmul2(z, make_float2(z.x >= 0.0f ? s.x : q.x, z.y >= 0.0f ? s.y : q.y));
+    return ffma2(na, q, make_float2(fmaxf(z.x, 0.0f), fmaxf(z.y, 0.0f)));
 }
 
 // D (32 x 2 columns from TMEM, this thread's row) + bias -> GELU -> bf16 row
