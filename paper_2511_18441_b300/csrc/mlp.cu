@@ -118,17 +118,18 @@ __global__ void __launch_bounds__(256) mlp_pack_kernel(const float* __restrict__
 // Below the coefficients b_k are divided by sqrt(2 pi) (the factor of phi).
 // In float32 this GELU stays within 4.1e-7 of the exact one on [-12, 12],
 // far inside the bf16 rounding the activations get next.
+// z Phi(z) = max(z, 0) - |z| (1 - Phi(|z|)) for either sign of z.
 __device__ __forceinline__ float gelu(float z) {
-    const float a = fabsf(z);
-    const float t = rcp_approx(fmaf(0.2316419f, a, 1.0f));
+    const float na = -fabsf(z);
+    const float t = rcp_approx(fmaf(-0.2316419f, na, 1.0f));
     float p = fmaf(t, 0.5307027f, -0.72657603f);
     p = fmaf(t, p, 0.7107069f);
     p = fmaf(t, p, -0.14224836f);
     p = fmaf(t, p, 0.1274148f);
     float e;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-0.7213475f * a * a));  // exp(-a^2 / 2)
-    const float q = e * (p * t);   // 1 - Phi(a)
-    return z * (z >= 0.0f ? 1.0f - q : q);
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-0.7213475f * z * z));  // exp(-z^2 / 2)
+    const float q = e * (p * t);   // 1 - Phi(|z|)
+    return fmaf(na, q, fmaxf(z, 0.0f));
 }
 
 __device__ __forceinline__ float gelu_grad(float z) {
