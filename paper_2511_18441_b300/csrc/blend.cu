@@ -761,13 +761,19 @@ __device__ __forceinline__ void blend_tile_pairs(const int n, const int tile,
     if (threadIdx.x == 0 && ctr) atomicAdd(&ctr->pairs_read, (unsigned long long)(fetched - begin));
 }
 
-// 7 CTAs of 128 threads per SM (72 registers; 8 CTAs at 64 registers spill
-// and ran 1.3% slower)
+// Colour mode: 7 CTAs of 128 threads per SM (72 registers; 8 CTAs at 64
+// registers spill and ran 1.3% slower). Gradient mode: 9 CTAs (56 registers,
+// no spill), whose shared-memory atomics and shuffles want more warps to hide
+// them (3M/1080p: 0.446 ms against 0.457 ms at 8 CTAs and 0.491 ms at 7).
 #ifndef RECOGS_PAIR_MIN_BLOCKS
 #define RECOGS_PAIR_MIN_BLOCKS 7
 #endif
+#ifndef RECOGS_PAIR_GRAD_MIN_BLOCKS
+#define RECOGS_PAIR_GRAD_MIN_BLOCKS 9
+#endif
 template <int BATCH, int MODE>
-__global__ void __launch_bounds__(kPairThreads, RECOGS_PAIR_MIN_BLOCKS)
+__global__ void __launch_bounds__(kPairThreads, MODE == kBlendGrad ? RECOGS_PAIR_GRAD_MIN_BLOCKS
+                                                                   : RECOGS_PAIR_MIN_BLOCKS)
     blend_pairs_kernel(int n, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
                        const uint32_t* __restrict__ ids, const float4* __restrict__ rec, int width,
                        int height, int tiles_x, float bg0, float bg1, float bg2,
