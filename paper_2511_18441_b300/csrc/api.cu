@@ -1641,7 +1641,8 @@ recogs_status recogs_mlp_create(recogs_ctx* ctx, const float* params_host, recog
     if (e == cudaSuccess) e = cudaMemset(m->grad, 0, pb);
     if (e == cudaSuccess) {
         launch_mlp_pack(m->params, m->frags, 0);
-        e = cudaDeviceSynchronize();
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1705,6 +1706,7 @@ recogs_status recogs_mlp_set_state(recogs_mlp* m, const float* params, const flo
     CK(cudaMemcpy(m->m, adam_m, pb, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(m->v, adam_v, pb, cudaMemcpyHostToDevice));
     launch_mlp_pack(m->params, m->frags, 0);
+    CK(cudaGetLastError());
     CK(cudaDeviceSynchronize());
     m->step = step;
     return RECOGS_OK;
