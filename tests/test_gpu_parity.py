@@ -466,6 +466,49 @@ def test_close_depths_in_a_tile(ctx):
         assert np.array_equal(a, b)
 
 
+def test_short_depth_clusters_in_a_tile(ctx):
+    """Clusters of at most 32 Gaussians at close or exactly equal depths: the
+    per-tile counting pass keeps them (no bin above 32 keys) and orders each
+    bin by key and index, as the global path's full sort does; the exact
+    ties come out in index order."""
+    rng = np.random.default_rng(12)
+    n_wide, n_a, n_b = 3000, 30, 24
+    z = np.concatenate([rng.uniform(-1.0, 0.8, n_wide),
+                        0.3 + 1e-6 * rng.permutation(n_a),
+                        np.full(n_b, -0.4)])
+    z = z[rng.permutation(len(z))]
+    n = len(z)
+    xyz = np.stack([rng.normal(0, 0.004, n), rng.normal(0, 0.004, n), z])
+    sc = sg.Scene(xyz.astype(np.float32), np.full((3, n), -5.5, np.float32),
+                  rng.normal(size=(4, n)).astype(np.float32),
+                  rng.normal(-2.0, 1.0, n).astype(np.float32),
+                  rng.normal(0, 0.3, (16, 3, n)).astype(np.float32))
+    cam = sg.axis_camera(64, 64, 60.0, 2.5)
+    ds = dscene(sc)
+    out = {}
+    for path in (1, 2):
+        ctx.set_sort_path(path)
+        img, T, st = render(ctx, ds, cam, None, stats=True)
+        ranges, gids = ctx.tile_lists(st["n_tiles"], st["n_pairs"])
+        keys = ctx.depth_keys(ds.n)
+        torch.cuda.synchronize()
+        out[path] = (img, T, parity.to_np(ranges), parity.to_np(gids), parity.to_np(keys))
+    ctx.set_sort_path(0)
+    r = out[1][2]
+    assert (r[:, 1] - r[:, 0]).max() > 2000
+    for a, b in zip(out[1], out[2]):
+        assert np.array_equal(a, b)
+    # the exact ties: in index order wherever they share a tile
+    zk = out[1][4]
+    g = out[1][3].astype(np.int64)
+    for t in range(len(r)):
+        lst = g[r[t, 0]:r[t, 1]]
+        k = zk[lst].astype(np.float64)
+        assert np.all(np.diff(k) >= 0)
+        same = np.diff(k) == 0
+        assert np.all(np.diff(lst)[same] > 0)
+
+
 def test_large_gaussians_counted_and_scattered_by_the_block(ctx):
     """Gaussians covering hundreds of tiles (their pairs are counted and
     scattered by the whole block): identical to the global path and to the
