@@ -856,16 +856,20 @@ __device__ __forceinline__ bool tile_count_one(const uint2* __restrict__ ranges,
         }
     }
     __syncthreads();
-    // each key's place: its bin's start plus the bin's keys before it
+    // each key's place: its bin's start plus the bin's keys before it, taken
+    // position by position in the binned order, so that the lanes of a warp
+    // walk the same or neighbouring bins (shared loads broadcast or in
+    // distinct banks, stores nearly contiguous)
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        if (warp * PW + i * 32 + lane < n) {
-            const int d = (int)(key[i] >> shift);
+        const int p = warp * PW + i * 32 + lane;
+        if (p < n) {
+            const unsigned long long kv = s_kv[p];
+            const int d = (int)((uint32_t)(kv >> 32) >> shift);
             const uint32_t b0 = bin(d), b1 = bin(d + 1);
-            const unsigned long long kv = ((unsigned long long)key[i] << 32) | val[i];
             uint32_t rank = 0u;
             for (uint32_t q = b0; q < b1; ++q) rank += s_kv[q] < kv ? 1u : 0u;
-            ids[r.x + b0 + rank] = val[i];
+            ids[r.x + b0 + rank] = (uint32_t)kv;
         }
     }
     return true;
