@@ -718,20 +718,20 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
 
 // One tile by a single counting pass (the radix passes above are its
 // fallback): keys relative to the tile's minimum fall into nb bins (the
-// smallest power of two >= 2 n, at most kCountBins) by their top log2(nb)
+// smallest power of two >= n, at most kCountBins) by their top log2(nb)
 // bits; a shared-memory atomic per key gives its bin and its slot there (in
 // no fixed order), a scan of the bins their starts, and each key's place in
 // its bin is the number of the bin's keys that precede it in (key, index)
 // order, so the result is the full (depth, index) order. On the 3M-Gaussian
-// 1080p frame bins hold at most 27 keys (2.4-3.1 on average per key) and the
-// six sort classes take 0.092 instead of 0.115 ms; 1 or 4 bins per key ran
-// the same or slower (more keys per bin to rank against, or a longer scan).
-// False, with nothing written, when some bin holds more than kCountRun keys
-// (e.g. many Gaussians at exactly one depth): the caller then sorts the tile
-// by the radix passes.
+// 1080p frame a key shares its bin with 3.7-9.2 keys on average, about a
+// hundred of the 8160 tiles have a bin above the limit, and the frame runs
+// 0.6079 ms against 0.6112 with two bins per key (a longer scan, fewer
+// fallbacks) and 0.625 with four. False, with nothing written, when some bin
+// holds more than kCountRun keys (e.g. many Gaussians at exactly one depth):
+// the caller then sorts the tile by the radix passes.
 constexpr int kCountBins = 8192;
 constexpr int kCountRun = 32;
-constexpr int kCountPerKey = 2;
+constexpr int kCountPerKey = 1;
 
 __host__ __device__ constexpr int count_max_bins(int maxn) {
     return kCountPerKey * maxn < kCountBins ? kCountPerKey * maxn : kCountBins;
