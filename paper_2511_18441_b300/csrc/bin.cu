@@ -723,14 +723,14 @@ __device__ __forceinline__ void tile_radix_one(const uint2* __restrict__ ranges,
 // no fixed order), a scan of the bins their starts, and each key's place in
 // its bin is the number of the bin's keys that precede it in (key, index)
 // order, so the result is the full (depth, index) order. On the 3M-Gaussian
-// 1080p frame a key shares its bin with 3.7-9.2 keys on average, about a
-// hundred of the 8160 tiles have a bin above the limit, and the frame runs
-// 0.6079 ms against 0.6112 with two bins per key (a longer scan, fewer
-// fallbacks) and 0.625 with four. False, with nothing written, when some bin
-// holds more than kCountRun keys (e.g. many Gaussians at exactly one depth):
-// the caller then sorts the tile by the radix passes.
+// 1080p frame a key shares its bin with 3.7-9.2 keys on average and the
+// frame runs 0.6079 ms against 0.6112 with two bins per key (a longer scan)
+// and 0.625 with four; a limit of 64 keys per bin instead of 32 (a few
+// tiles fewer fall back) took it to 0.607. False, with nothing written, when
+// some bin holds more than kCountRun keys (e.g. many Gaussians at exactly
+// one depth): the caller then sorts the tile by the radix passes.
 constexpr int kCountBins = 8192;
-constexpr int kCountRun = 32;
+constexpr int kCountRun = 64;
 constexpr int kCountPerKey = 1;
 
 __host__ __device__ constexpr int count_max_bins(int maxn) {
