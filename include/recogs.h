@@ -508,10 +508,11 @@ RECOGS_API recogs_status recogs_set_sort_path(recogs_ctx* ctx, int path);
 /* Schedule knobs of recogs_render (the batch autotuner searches them too;
  * every setting gives the same image bit for bit):
  * radix_classes (0..6) = how many of the per-tile sort's six size classes,
- * from the largest tiles (4096 to 16384 pairs) down, are sorted by the
- * shared-memory radix sort rather than the register bitonic network (default
- * 5: all but the tiles below 256 pairs; the largest class always takes the
- * radix sort, which alone holds tiles above 8192 pairs);
+ * from the largest tiles (4096 to 16384 pairs) down, are sorted in shared
+ * memory (one counting pass, radix passes where a bin overflows) rather than
+ * by the register bitonic network (default 6: every class; the largest class
+ * always takes the shared-memory sort, which alone holds tiles above 8192
+ * pairs);
  * blend_batch (128 or 256) = depth-sorted Gaussians staged in shared memory
  * per step of the blend (default 256); overlap (0 or 1) = blend each size
  * class's tiles on the class's stream as soon as they are sorted (stage

@@ -515,7 +515,7 @@ class Context:
         """0 automatic, 1 per-tile shared-memory sort, 2 global radix path."""
         self._check(self._L.recogs_set_sort_path(self._h, int(path)))
 
-    def set_schedule(self, radix_classes: int = 5, blend_batch: int = 256, overlap: bool = False):
+    def set_schedule(self, radix_classes: int = 6, blend_batch: int = 256, overlap: bool = False):
         self._check(self._L.recogs_set_schedule(self._h, int(radix_classes), int(blend_batch),
                                                 1 if overlap else 0))
 

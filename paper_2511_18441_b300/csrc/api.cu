@@ -96,7 +96,7 @@ struct Scratch {
 struct Schedule {
     int sort_path = 0;          // 0 auto, 1 per-tile shared-memory sort, 2 global radix sort
     int64_t pair_capacity = 0;  // > 0: no mid-frame read back, pair buffers of this size
-    int radix_classes = 5;      // per-tile sort classes (largest first) sorted by radix
+    int radix_classes = 6;      // per-tile sort classes (largest first) sorted in shared memory
     int blend_batch = 256;      // Gaussians staged per blend batch (128 or 256)
     bool overlap = false;       // blend each sort class's tiles right after its sort
     const uint32_t* class_hint = nullptr;   // sort class sizes of an earlier frame (grid sizes)
@@ -929,7 +929,7 @@ recogs_status plan_batch(recogs_ctx* ctx, const recogs_scene* scenes, int n_scen
             CKS(trial(lanes, best, &better));
             if (better) best_lanes = lanes;
         }
-        const int radix_opts[2] = {4, 6};
+        const int radix_opts[2] = {4, 5};   // against the default 6
         for (int rc : radix_opts) {
             Schedule sc = best;
             sc.radix_classes = rc;
