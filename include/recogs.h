@@ -574,7 +574,7 @@ typedef struct {
  * count, spreads the views over lanes (each with its own scratch and
  * stream; views run concurrently across lanes) and, with RECOGS_BATCH_GRAPH,
  * captures all lanes as one CUDA graph. With RECOGS_BATCH_TUNE the planning
- * also times candidate schedules (lane count 1/2/4, the per-tile sort's radix
+ * also times candidate schedules (lane count 1/2/4/8, the per-tile sort's radix
  * classes, the blend batch, blending each sort class as it is sorted) and
  * keeps the fastest. Planning waits for the
  * device. Later calls with the same description replay the plan (one graph

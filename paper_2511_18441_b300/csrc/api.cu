@@ -923,7 +923,7 @@ recogs_status plan_batch(recogs_ctx* ctx, const recogs_scene* scenes, int n_scen
         int best_lanes = 1;
         Schedule best = Schedule();
         bool better = false;
-        const int lane_opts[3] = {1, 2, 4};
+        const int lane_opts[4] = {1, 2, 4, 8};   // 16 measured no faster on 64 views
         for (int lanes : lane_opts) {
             if (lanes > 1 && lanes > lane_views) break;
             CKS(trial(lanes, best, &better));
