@@ -181,6 +181,29 @@ RECOGS_API recogs_status recogs_render_host(recogs_ctx* ctx, const recogs_scene*
                                  const float* bg, float* image_hwc_host, float* final_T_host,
                                  recogs_render_stats* stats, void* stream);
 
+/* recogs_render_host over a sequence of n_frames frames, pipelined: frame
+ * f + 1's scene upload (on a context-owned copy stream) overlaps frame f's
+ * render (on `stream`) and its image read back (on a second copy stream),
+ * through two context-owned device copies of the scene arrays and of the
+ * outputs. Each frame's image and T equal recogs_render_host's for the same
+ * arguments bit for bit. host_scenes, cameras: n_frames each (host structs
+ * whose arrays are in host memory; one scene may appear several times and
+ * is then uploaded once per frame); edits: NULL (no edit) or n_frames
+ * pointers, each NULL or an edit; bg: host, 3 floats or NULL;
+ * images_hwc_host: n_frames host pointers (height*width*3 float32 each);
+ * final_T_host: NULL or n_frames host pointers, each NULL or height*width
+ * float32. Every argument is checked before any work is queued (EINVAL);
+ * the call returns after every image (and T) is in host memory, and on an
+ * error after every copy it queued has finished. Pinned host memory makes
+ * the copies asynchronous; pageable buffers serialise them. Calls on one
+ * context must not overlap. */
+RECOGS_API recogs_status recogs_render_host_frames(recogs_ctx* ctx, int32_t n_frames,
+                                                   const recogs_scene* host_scenes,
+                                                   const recogs_camera* cameras,
+                                                   const recogs_edit* const* edits,
+                                                   const float* bg, float* const* images_hwc_host,
+                                                   float* const* final_T_host, void* stream);
+
 /* recogs_render plus the "median" depth map of Sec. 3.2.2: depth_out
  * (device, height*width float32) holds, per pixel, the view depth t_z of
  * the Gaussian whose blending takes the transmittance from >= tau to < tau

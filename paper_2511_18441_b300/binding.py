@@ -94,6 +94,10 @@ SIGNATURES = {
     "recogs_render_host": (C.c_int, [C.c_void_p, C.POINTER(CScene), C.POINTER(CCamera),
                                      C.POINTER(CEdit), C.POINTER(C.c_float), C.c_void_p,
                                      C.c_void_p, C.POINTER(CStats), C.c_void_p]),
+    "recogs_render_host_frames": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(CScene),
+                                            C.POINTER(CCamera), C.c_void_p,
+                                            C.POINTER(C.c_float), C.c_void_p, C.c_void_p,
+                                            C.c_void_p]),
     "recogs_render_noalloc": (C.c_int, [C.POINTER(CScene), C.POINTER(CCamera), C.POINTER(CEdit),
                                         C.POINTER(C.c_float), C.c_void_p, C.c_void_p, C.c_char_p,
                                         C.c_size_t, C.c_void_p]),
@@ -366,6 +370,42 @@ class Context:
             return image_out, dict(n_visible=st.n_visible, n_pairs=st.n_pairs,
                                    n_pairs_read=st.n_pairs_read, n_tiles=st.n_tiles)
         return image_out
+
+    def render_host_frames(self, frames, bg=None, images_out=None, T_out=None, stream=None):
+        """Pipelined recogs_render_host over frames = [(scene, camera, edit), ...]
+        (host scenes, pinned for speed; edit may be None). Returns the list of
+        host images (and of T maps when T_out is given: a list of host tensors
+        or None entries)."""
+        import torch
+        nf = len(frames)
+        if images_out is None:
+            images_out = [torch.empty((int(c.height), int(c.width), 3), dtype=torch.float32)
+                          .pin_memory() for _, c, _ in frames]
+        scenes = (CScene * max(nf, 1))()
+        cams = (CCamera * max(nf, 1))()
+        keep = []
+        edits = (C.POINTER(CEdit) * max(nf, 1))()
+        any_edit = False
+        for i, (sc, cam, edit) in enumerate(frames):
+            scenes[i] = sc.struct()
+            cams[i] = camera_struct(cam)
+            e, k = edit_struct(edit)
+            keep.append(k)
+            if e is not None:
+                keep.append(e)
+                edits[i] = C.pointer(e)
+                any_edit = True
+        imgs = (C.c_void_p * max(nf, 1))(*[t.data_ptr() for t in images_out])
+        Ts = None
+        if T_out is not None:
+            Ts = (C.c_void_p * max(nf, 1))(*[t.data_ptr() if t is not None else None
+                                             for t in T_out])
+        bgv = (C.c_float * 3)(*(np.asarray(bg if bg is not None else (0, 0, 0), np.float32)))
+        self._check(self._L.recogs_render_host_frames(
+            self._h, nf, scenes, cams, C.cast(edits, C.c_void_p) if any_edit else None, bgv,
+            C.cast(imgs, C.c_void_p), C.cast(Ts, C.c_void_p) if Ts is not None else None,
+            _stream_ptr(stream)))
+        return images_out if T_out is None else (images_out, T_out)
 
     def render_depth(self, scene: DeviceScene, cam, edit=None, bg=None, tau=0.5, image_out=None,
                      T_out=None, depth_out=None, stats=False, stream=None):

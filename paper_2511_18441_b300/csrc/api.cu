@@ -139,6 +139,12 @@ struct recogs_ctx {
     int batch_tune_trials = 0;
     // host-memory render staging
     DevBuf hs_xyz, hs_ls, hs_q, hs_op, hs_sh, hs_img, hs_T;
+    // pipelined host-memory frames (recogs_render_host_frames): two slots of
+    // scene and image staging, an upload and a read-back stream, and per slot
+    // the events "uploaded", "rendered" and "read back"
+    DevBuf hf_xyz[2], hf_ls[2], hf_q[2], hf_op[2], hf_sh[2], hf_img[2], hf_T[2];
+    cudaStream_t hf_in = nullptr, hf_out = nullptr;
+    cudaEvent_t hf_uploaded[2] = {}, hf_rendered[2] = {}, hf_read[2] = {};
     // SH refit: forward image, colour gradient, loss
     DevBuf rf_img, rf_grad, rf_loss, rf_region;
     DevCounters* h_counters = nullptr;   // pinned
@@ -1170,6 +1176,17 @@ void recogs_ctx_destroy(recogs_ctx* ctx) {
                       &ctx->rf_region};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
+    for (int k = 0; k < 2; ++k) {
+        DevBuf* hf[] = {&ctx->hf_xyz[k], &ctx->hf_ls[k], &ctx->hf_q[k], &ctx->hf_op[k],
+                        &ctx->hf_sh[k], &ctx->hf_img[k], &ctx->hf_T[k]};
+        for (DevBuf* b : hf)
+            if (b->p) cudaFree(b->p);
+        if (ctx->hf_uploaded[k]) cudaEventDestroy(ctx->hf_uploaded[k]);
+        if (ctx->hf_rendered[k]) cudaEventDestroy(ctx->hf_rendered[k]);
+        if (ctx->hf_read[k]) cudaEventDestroy(ctx->hf_read[k]);
+    }
+    if (ctx->hf_in) cudaStreamDestroy(ctx->hf_in);
+    if (ctx->hf_out) cudaStreamDestroy(ctx->hf_out);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     for (auto& p : ctx->pending) {
         cudaEventDestroy(p.a);
@@ -1296,6 +1313,123 @@ recogs_status recogs_render_host(recogs_ctx* ctx, const recogs_scene* hs,
     if (final_T_host)
         CK(cudaMemcpyAsync(final_T_host, ctx->hs_T.p, 4 * npix, cudaMemcpyDeviceToHost, st));
     stage_end(ctx, ST_D2H, 0, st);
+    CK(cudaStreamSynchronize(st));
+    return RECOGS_OK;
+}
+
+recogs_status recogs_render_host_frames(recogs_ctx* ctx, int32_t n_frames,
+                                        const recogs_scene* host_scenes,
+                                        const recogs_camera* cameras,
+                                        const recogs_edit* const* edits, const float* bg,
+                                        float* const* images_hwc_host,
+                                        float* const* final_T_host, void* stream) {
+    if (!ctx) return RECOGS_EINVAL;
+    if (n_frames < 0) return fail(ctx, RECOGS_EINVAL, "n_frames < 0");
+    if (n_frames == 0) return RECOGS_OK;
+    if (!host_scenes || !cameras || !images_hwc_host)
+        return fail(ctx, RECOGS_EINVAL, "host_scenes, cameras or images_hwc_host is NULL");
+    float bgv[3] = {0.f, 0.f, 0.f};
+    if (bg)
+        for (int k = 0; k < 3; ++k) {
+            if (!finite(bg[k])) return fail(ctx, RECOGS_EINVAL, "bg not finite");
+            bgv[k] = bg[k];
+        }
+    // every argument is checked before any work is queued
+    size_t max_n = 0, max_sh = 0, max_pix = 0;
+    for (int f = 0; f < n_frames; ++f) {
+        CKS(check_scene(ctx, &host_scenes[f]));
+        CKS(check_camera(ctx, &cameras[f], "camera"));
+        if (!images_hwc_host[f]) return fail(ctx, RECOGS_EINVAL, "images_hwc_host[%d] is NULL", f);
+        const size_t n = (size_t)host_scenes[f].n;
+        max_n = std::max(max_n, n);
+        max_sh = std::max(max_sh, 48 * n * sh_elem_size(host_scenes[f].sh_dtype));
+        max_pix = std::max(max_pix, (size_t)cameras[f].width * cameras[f].height);
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!ctx->hf_in) {
+        CK(cudaStreamCreateWithFlags(&ctx->hf_in, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&ctx->hf_out, cudaStreamNonBlocking));
+        for (int k = 0; k < 2; ++k) {
+            CK(cudaEventCreateWithFlags(&ctx->hf_uploaded[k], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&ctx->hf_rendered[k], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&ctx->hf_read[k], cudaEventDisableTiming));
+        }
+    }
+    const bool any_T = final_T_host != nullptr;
+    for (int k = 0; k < 2 && k < n_frames; ++k) {
+        CKS(ensure(ctx, ctx->hf_xyz[k], 12 * max_n));
+        CKS(ensure(ctx, ctx->hf_ls[k], 12 * max_n));
+        CKS(ensure(ctx, ctx->hf_q[k], 16 * max_n));
+        CKS(ensure(ctx, ctx->hf_op[k], 4 * max_n));
+        CKS(ensure(ctx, ctx->hf_sh[k], max_sh));
+        CKS(ensure(ctx, ctx->hf_img[k], 12 * max_pix));
+        if (any_T) CKS(ensure(ctx, ctx->hf_T[k], 4 * max_pix));
+    }
+    // nothing of an earlier call may still use the slots
+    CK(cudaStreamSynchronize(ctx->hf_in));
+    CK(cudaStreamSynchronize(ctx->hf_out));
+    // frame f's scene into slot f % 2, once the frame two before it (same
+    // slot) has been rendered
+    auto upload = [&](int f) -> recogs_status {
+        const int k = f & 1;
+        const recogs_scene& hs = host_scenes[f];
+        const size_t n = (size_t)hs.n;
+        if (f >= 2) CK(cudaStreamWaitEvent(ctx->hf_in, ctx->hf_rendered[k], 0));
+        if (n > 0) {
+            CK(cudaMemcpyAsync(ctx->hf_xyz[k].p, hs.xyz, 12 * n, cudaMemcpyHostToDevice, ctx->hf_in));
+            CK(cudaMemcpyAsync(ctx->hf_ls[k].p, hs.log_scale, 12 * n, cudaMemcpyHostToDevice,
+                               ctx->hf_in));
+            CK(cudaMemcpyAsync(ctx->hf_q[k].p, hs.quat, 16 * n, cudaMemcpyHostToDevice, ctx->hf_in));
+            CK(cudaMemcpyAsync(ctx->hf_op[k].p, hs.opacity_logit, 4 * n, cudaMemcpyHostToDevice,
+                               ctx->hf_in));
+            CK(cudaMemcpyAsync(ctx->hf_sh[k].p, hs.sh, 48 * n * sh_elem_size(hs.sh_dtype),
+                               cudaMemcpyHostToDevice, ctx->hf_in));
+        }
+        CK(cudaEventRecord(ctx->hf_uploaded[k], ctx->hf_in));
+        return RECOGS_OK;
+    };
+    recogs_status status = upload(0);
+    for (int f = 0; f < n_frames && status == RECOGS_OK; ++f) {
+        // the next frame's upload is queued before this frame's render, which
+        // may wait on the host for its counters
+        if (f + 1 < n_frames && (status = upload(f + 1)) != RECOGS_OK) break;
+        const int k = f & 1;
+        const size_t npix = (size_t)cameras[f].width * cameras[f].height;
+        float* T_host = any_T ? final_T_host[f] : nullptr;
+        recogs_scene ds = host_scenes[f];
+        ds.xyz = P<float>(ctx->hf_xyz[k]);
+        ds.log_scale = P<float>(ctx->hf_ls[k]);
+        ds.quat = P<float>(ctx->hf_q[k]);
+        ds.opacity_logit = P<float>(ctx->hf_op[k]);
+        ds.sh = ctx->hf_sh[k].p;
+        cudaError_t e = cudaStreamWaitEvent(st, ctx->hf_uploaded[k], 0);
+        if (e == cudaSuccess && f >= 2) e = cudaStreamWaitEvent(st, ctx->hf_read[k], 0);
+        if (e != cudaSuccess) {
+            status = cuda_check(ctx, e, "cudaStreamWaitEvent");
+            break;
+        }
+        status = render_device(ctx, ctx->main, ctx->sched, ds, cameras[f], edits ? edits[f] : nullptr,
+                               bgv, P<float>(ctx->hf_img[k]), T_host ? P<float>(ctx->hf_T[k]) : nullptr,
+                               nullptr, st);
+        if (status != RECOGS_OK) break;
+        e = cudaEventRecord(ctx->hf_rendered[k], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->hf_out, ctx->hf_rendered[k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(images_hwc_host[f], ctx->hf_img[k].p, 12 * npix,
+                                cudaMemcpyDeviceToHost, ctx->hf_out);
+        if (e == cudaSuccess && T_host)
+            e = cudaMemcpyAsync(T_host, ctx->hf_T[k].p, 4 * npix, cudaMemcpyDeviceToHost,
+                                ctx->hf_out);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->hf_read[k], ctx->hf_out);
+        if (e != cudaSuccess) status = cuda_check(ctx, e, "pipelined read back");
+    }
+    // no copy into the caller's buffers outlives the call, on success or not
+    const cudaError_t eo = cudaStreamSynchronize(ctx->hf_out);
+    const cudaError_t ei = cudaStreamSynchronize(ctx->hf_in);
+    if (status != RECOGS_OK) return status;
+    CK(eo);
+    CK(ei);
     CK(cudaStreamSynchronize(st));
     return RECOGS_OK;
 }

@@ -325,6 +325,39 @@ def test_render_host_matches_device(ctx):
     assert np.array_equal(img_h.numpy(), img_d) and np.array_equal(Th.numpy(), T_d)
 
 
+def test_render_host_frames_matches_single_frames(ctx):
+    """The pipelined host-memory frames (upload of frame f + 1 during frame
+    f's render and read back, two staging slots) give every frame's image and
+    T bit for bit as recogs_render_host does: frames of two scenes, with and
+    without an edit, a 16-bit scene, more frames than slots."""
+    from paper_2511_18441_b300 import binding
+    wa = sg.paper_scale_workload(n=100_000, width=640, height=360, seed=3)
+    wb = sg.paper_scale_workload(n=40_000, width=320, height=200, seed=4)
+    ha = binding.DeviceScene.from_numpy(wa.scene, "cpu", "f32", pin=True)
+    hb = binding.DeviceScene.from_numpy(wb.scene, "cpu", "bf16", pin=True)
+    frames = [(ha, wa.camera, wa.edit), (hb, wb.camera, None), (ha, wa.camera, None),
+              (hb, wb.camera, wb.edit), (ha, wa.camera, wa.edit)]
+    T_out = [torch.empty((int(c.height), int(c.width)), dtype=torch.float32).pin_memory()
+             if i % 2 == 0 else None for i, (_, c, _) in enumerate(frames)]
+    imgs, Ts = ctx.render_host_frames(frames, bg=(0.1, 0.2, 0.3), T_out=T_out)
+    for i, (sc, cam, edit) in enumerate(frames):
+        Th = torch.empty((int(cam.height), int(cam.width)), dtype=torch.float32).pin_memory()
+        ref = ctx.render_host(sc, cam, edit, bg=(0.1, 0.2, 0.3), T_out=Th)
+        assert np.array_equal(imgs[i].numpy(), ref.numpy()), i
+        if Ts[i] is not None:
+            assert np.array_equal(Ts[i].numpy(), Th.numpy()), i
+    # a missing output is refused before any work is queued
+    L = ctx._L
+    scenes = (binding.CScene * 1)(ha.struct())
+    cams = (binding.CCamera * 1)(binding.camera_struct(wa.camera))
+    imgs0 = (binding.C.c_void_p * 1)(None)
+    s = L.recogs_render_host_frames(ctx._h, 1, scenes, cams, None, None,
+                                    binding.C.cast(imgs0, binding.C.c_void_p), None, None)
+    assert s == binding.EINVAL
+    assert L.recogs_render_host_frames(ctx._h, 0, None, None, None, None, None, None,
+                                       None) == 0
+
+
 def test_stage_timing_and_launch_count(ctx):
     w = sg.tiny_workload()
     ds = dscene(w.scene)
