@@ -106,6 +106,29 @@ def test_an_allocation_that_fails_is_reported_and_the_context_recovers(lib, nth)
     ctx.close()
 
 
+@pytest.mark.parametrize("nth", [1, 7, 15])
+def test_a_failed_allocation_in_pipelined_host_frames(lib, nth):
+    """The nth device allocation of a fresh context fails inside the
+    pipelined host-memory frames (their staging slots, or the render's own
+    scratch): RECOGS_ENOMEM, no copy into the caller's buffers after the
+    call, and the next call renders every frame as recogs_render_host does."""
+    w = sg.paper_scale_workload(n=60_000, width=320, height=200, seed=5)
+    hs = lib.DeviceScene.from_numpy(w.scene, "cpu", "f32", pin=True)
+    frames = [(hs, w.camera, w.edit), (hs, w.camera, None), (hs, w.camera, w.edit)]
+    ref_ctx = lib.Context(0)
+    refs = [ref_ctx.render_host(sc, cam, edit).numpy().copy() for sc, cam, edit in frames]
+    ref_ctx.close()
+    ctx = lib.Context(0)
+    ctx.set_fault(f"alloc:{nth}")
+    with pytest.raises(lib.RecogsError) as e:
+        ctx.render_host_frames(frames)
+    assert e.value.status == lib.ENOMEM and "injected" in str(e.value)
+    imgs = ctx.render_host_frames(frames)
+    for img, ref in zip(imgs, refs):
+        assert np.array_equal(img.numpy(), ref)
+    ctx.close()
+
+
 def test_fault_specifications(lib, monkeypatch):
     ctx = lib.Context(0)
     for bad in ("alloc", "alloc:0", "wait:-3", "wait:x", "boom:1", "wait:2000000"):
