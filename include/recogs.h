@@ -537,7 +537,9 @@ RECOGS_API recogs_status recogs_set_sort_path(recogs_ctx* ctx, int path);
  * always takes the shared-memory sort, which alone holds tiles above 8192
  * pairs);
  * blend_batch (128 or 256) = depth-sorted Gaussians staged in shared memory
- * per step of the blend (default 256); overlap (0 or 1) = blend each size
+ * per step of the one-pixel walk (the median-depth and coverage passes and
+ * the overlap schedule's class blends; the colour and gradient walks, two
+ * pixels per lane, always stage 128; default 256); overlap (0 or 1) = blend each size
  * class's tiles on the class's stream as soon as they are sorted (stage
  * timing then reports one "sort_blend" stage) rather than one blend of all
  * tiles, heaviest first, after every sort (default 0: measured faster at

@@ -944,15 +944,17 @@ recogs_status plan_batch(recogs_ctx* ctx, const recogs_scene* scenes, int n_scen
         }
         {
             Schedule sc = best;
-            sc.blend_batch = 128;
-            CKS(trial(best_lanes, sc, &better));
-            if (better) best.blend_batch = 128;
-        }
-        {
-            Schedule sc = best;
             sc.overlap = true;
             CKS(trial(best_lanes, sc, &better));
             if (better) best.overlap = true;
+        }
+        // the blend batch only sizes the overlap schedule's one-pixel class
+        // blends (the colour walk always stages 128)
+        if (best.overlap) {
+            Schedule sc = best;
+            sc.blend_batch = 128;
+            CKS(trial(best_lanes, sc, &better));
+            if (better) best.blend_batch = 128;
         }
         ctx->batch_sched = best;
         ctx->batch_lanes = best_lanes;
