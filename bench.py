@@ -269,6 +269,29 @@ def profiled_traffic(stage):
         return None
 
 
+def profiled_instructions(stage):
+    """Warp instructions per launch from a committed ncu summary, or None if
+    absent or taken on a different version of the kernel's source."""
+    files = {"blend": "blend.cu"}
+    if stage not in files:
+        return None
+    path = os.path.join(ROOT, "profiles", f"issue_{stage}_3m_1080p.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+    if kv.get("source_sha256_16") != kernel_source_sha(files[stage]):
+        return None
+    try:
+        return float(kv["warp_instructions_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def algorithmic_bytes(stage, stats, n, sh_bytes):
     """Bytes a launch of `stage` must move at minimum (per-unit figures of the
     design notes x units per launch)."""
@@ -453,6 +476,22 @@ def run_ours(args, rank, world, local):
                 "timed": f"CUDA events around each {dom} launch of the {args.steps} timed frames"}
     stage_ms = {k: round(v[0] / k_breakdown, 4) for k, v in breakdown.items()}
 
+    # the blend is bound by instruction issue, not by HBM: its warp
+    # instructions per launch (a committed ncu count of this source) over its
+    # measured launch time, against one warp instruction per cycle per SM
+    # sub-partition at the highest SM clock seen
+    roof_issue = None
+    inst = profiled_instructions(dom)
+    if inst is not None and dom_ms > 0:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clocks or {}).get("sm_max_mhz") or 2032
+        peak_issue = 4.0 * sms * mhz * 1e6
+        ach = inst / (dom_ms / 1000.0)
+        roof_issue = {"kernel": dom, "bound": "issue", "achieved": ach, "peak": peak_issue,
+                      "unit": "warp instructions/s", "frac": ach / peak_issue,
+                      "warp_instructions_per_launch": inst, "ms_per_launch": dom_ms,
+                      "peak_source": f"4 issue slots x {sms} SMs x {mhz} MHz"}
+
     # other stages' HBM fractions for context (from the breakdown frames)
     other = {}
     for k in FRAME_STAGES:
@@ -615,6 +654,7 @@ def run_ours(args, rank, world, local):
             "stage_ms_per_step": stage_ms,
             "stage_ms_note": f"every stage timed by events over {k_breakdown} extra frames",
             "roofline": roof,
+            "roofline_issue": roof_issue,
             "roofline_other": other,
             "roofline_frame": whole,
             "accuracy": accuracy,
