@@ -240,6 +240,29 @@ def load_peaks():
     return PEAKS_FALLBACK, "fallback"
 
 
+def issue_roofline(kernel, inst, ms, dev, clocks=None):
+    """Warp instructions per launch over the launch time, against one warp
+    instruction per cycle per SM sub-partition at the highest SM clock (the
+    sampled clocks' maximum, else NVML's, else 2032 MHz)."""
+    if inst is None or not ms or ms <= 0:
+        return None
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz")
+    if not mhz:
+        try:
+            nv = _Nvml()
+            mhz = nv.sm_max_mhz(nv.handle(dev.index if hasattr(dev, "index") else dev))
+        except Exception:
+            mhz = 2032
+    peak = 4.0 * sms * mhz * 1e6
+    ach = inst / (ms / 1000.0)
+    return {"kernel": kernel, "bound": "issue", "achieved": ach, "peak": peak,
+            "unit": "warp instructions/s", "frac": ach / peak,
+            "warp_instructions_per_launch": inst, "ms_per_launch": ms,
+            "peak_source": f"4 issue slots x {sms} SMs x {mhz} MHz"}
+
+
 def kernel_source_sha(kernel_file):
     with open(os.path.join(ROOT, "paper_2511_18441_b300", "csrc", kernel_file), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
@@ -272,10 +295,12 @@ def profiled_traffic(stage):
 def profiled_instructions(stage):
     """Warp instructions per launch from a committed ncu summary, or None if
     absent or taken on a different version of the kernel's source."""
-    files = {"blend": "blend.cu"}
+    files = {"blend": ("blend.cu", "issue_blend_3m_1080p.txt"),
+             "mlp_select": ("mlp.cu", "issue_mlp_select_6m.txt")}
     if stage not in files:
         return None
-    path = os.path.join(ROOT, "profiles", f"issue_{stage}_3m_1080p.txt")
+    src, name = files[stage]
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     kv = {}
@@ -284,7 +309,7 @@ def profiled_instructions(stage):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
-    if kv.get("source_sha256_16") != kernel_source_sha(files[stage]):
+    if kv.get("source_sha256_16") != kernel_source_sha(src):
         return None
     try:
         return float(kv["warp_instructions_per_launch"])
@@ -480,17 +505,7 @@ def run_ours(args, rank, world, local):
     # instructions per launch (a committed ncu count of this source) over its
     # measured launch time, against one warp instruction per cycle per SM
     # sub-partition at the highest SM clock seen
-    roof_issue = None
-    inst = profiled_instructions(dom)
-    if inst is not None and dom_ms > 0:
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        mhz = (clocks or {}).get("sm_max_mhz") or 2032
-        peak_issue = 4.0 * sms * mhz * 1e6
-        ach = inst / (dom_ms / 1000.0)
-        roof_issue = {"kernel": dom, "bound": "issue", "achieved": ach, "peak": peak_issue,
-                      "unit": "warp instructions/s", "frac": ach / peak_issue,
-                      "warp_instructions_per_launch": inst, "ms_per_launch": dom_ms,
-                      "peak_source": f"4 issue slots x {sms} SMs x {mhz} MHz"}
+    roof_issue = issue_roofline(dom, profiled_instructions(dom), dom_ms, dev, clocks)
 
     # other stages' HBM fractions for context (from the breakdown frames)
     other = {}
@@ -1129,6 +1144,8 @@ def run_mlp(args, rank, world, local):
     tflops = n * flop_fwd / (t_fwd / 1000.0) / 1e12
     flop_sel = 2 * (64 * 64 + 64 * 64 + 64 * 16)      # per row, the tcgen05 shapes
     sel_tflops = n * flop_sel / (t_learned / 1000.0) / 1e12
+    issue_roof = issue_roofline("mlp_select_tc_kernel", profiled_instructions("mlp_select")
+                                if n == 6_000_000 else None, t_learned, dev)
     E = {k: float(np.mean([e[k] for e in evals])) for k in evals[0]}
     if rank == 0:
         line = {
@@ -1154,6 +1171,7 @@ def run_mlp(args, rank, world, local):
                          "peak_source": f"{src} cuBLAS bf16 burst", "traffic": None,
                          "note": ("the tensor pipe is far from busy: the kernel is bound by "
                                   "CUDA-core issue (128 GELUs and the features per row)")},
+            "roofline_issue": issue_roof,
             "forward_only_mma_sync": {"kernel": "mlp_forward_kernel (mma.sync bf16, features "
                                                 "read from HBM)",
                                       "achieved_tflops": tflops, "ms": t_fwd},
