@@ -499,13 +499,15 @@ def test_close_depths_in_a_tile(ctx):
         assert np.array_equal(a, b)
 
 
-def test_short_depth_clusters_in_a_tile(ctx):
-    """Clusters of at most 32 Gaussians at close or exactly equal depths: the
-    per-tile counting pass keeps them (no bin above 32 keys) and orders each
-    bin by key and index, as the global path's full sort does; the exact
-    ties come out in index order."""
+@pytest.mark.parametrize("n_b", [24, 63, 64, 65, 200])
+def test_short_depth_clusters_in_a_tile(ctx, n_b):
+    """Clusters of Gaussians at close or exactly equal depths around the
+    counting pass's limit of 64 keys per bin: below it the pass orders each
+    bin by key and index, above it the tile falls back to the radix passes;
+    either way the lists agree with the global path's full sort, and the
+    exact ties come out in index order."""
     rng = np.random.default_rng(12)
-    n_wide, n_a, n_b = 3000, 30, 24
+    n_wide, n_a = 3000, 30
     z = np.concatenate([rng.uniform(-1.0, 0.8, n_wide),
                         0.3 + 1e-6 * rng.permutation(n_a),
                         np.full(n_b, -0.4)])
