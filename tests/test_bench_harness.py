@@ -89,3 +89,28 @@ def test_profiled_traffic_only_for_the_profiled_source(tmp_path, monkeypatch):
     assert bench.profiled_traffic("blend") == 123.0
     assert bench.profiled_traffic("refit") is None        # another source
     assert bench.profiled_traffic("scatter") is None      # never profiled
+
+
+def test_profiled_instructions_only_for_the_profiled_source(tmp_path, monkeypatch):
+    """A committed instruction count is used only while its kernel source is
+    the one it was taken on, and the issue roofline divides it by the launch
+    time against four issue slots per SM and cycle."""
+    import bench
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    sha = bench.kernel_source_sha("blend.cu")
+    (prof / "issue_blend_3m_1080p.txt").write_text(
+        f"# note: with a colon\nsource_sha256_16: {sha}\nwarp_instructions_per_launch: 1000\n")
+    (prof / "issue_mlp_select_6m.txt").write_text(
+        "source_sha256_16: 0000000000000000\nwarp_instructions_per_launch: 7\n")
+    real_join = os.path.join
+
+    def join(*parts):
+        if len(parts) >= 2 and parts[0] == bench.ROOT and parts[1] == "profiles":
+            return real_join(str(tmp_path), *parts[1:])
+        return real_join(*parts)
+    monkeypatch.setattr(bench.os.path, "join", join)
+    assert bench.profiled_instructions("blend") == 1000.0
+    assert bench.profiled_instructions("mlp_select") is None   # another source
+    assert bench.profiled_instructions("scatter") is None      # never counted
+    assert bench.issue_roofline("blend", None, 1.0, None) is None
